@@ -1,0 +1,784 @@
+// MANTRA CPU oracle -- TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, obviously-correct restatement of the per-sample temporal
+// path computation of MANTRA (Cruciani, "MANTRA: Temporal Betweenness
+// Centrality Approximation through Sampling", arXiv 2304.08356) and of the
+// host-side bounds around it.  Only the test-suite, the package's smoke check
+// and the benchmark's CPU-baseline leg may load this library; the product
+// path never calls it.  It shares no code, header or table with the CUDA
+// library.
+//
+// Sections followed (paper numbering):
+//   Sec. 3 "Preliminaries"  -- temporal graph, temporal path, Def. 1
+//                              (sh / sfm / pfm), D, rho, Lemma 1, SD, c-MCERA,
+//                              wimpy variance, Theorem 1 (the SD bound xi).
+//   Sec. 4.2 / App. B       -- the MCERA sample bound omega (closed form at the
+//                              end of the proof of Theorem 3).
+//   Sec. 4.4, Algorithm 1   -- the progressive sampler.
+//   App. C, "temporal Riondato-Kornaropoulos" estimator and Theorem on the
+//                              path sampler -- backward path draw with
+//                              probability 1/sigma_sz.
+//   App. D, Algorithm 2     -- reach counts per hop, D_LB, D_tau, zeta, Psi.
+//
+// Readings where the paper is silent or garbled (same list in the design
+// notes): source appearance (s,-inf); strict time increase; duplicate
+// (u,v,t) triples deduplicated, self loops dropped; sfm = minimum hops first,
+// then earliest arrival at z (Figure "example_tp" caption); canonical
+// predecessor order for the path draw (in-edges by ascending w, then the
+// predecessor's appearances by ascending time); delta_i = delta/2^(i+1);
+// vhat = W; natural logarithms; pfm distance = minimum hops among pfm paths.
+//
+// Integers: path counts are exact unsigned 128-bit; a count that would exceed
+// 2^128-1 is reported as an overflow error.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <set>
+#include <tuple>
+#include <utility>
+#include <vector>
+
+typedef unsigned __int128 u128;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 counter-based generator, written from its published
+// definition (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11): 10 rounds of two 32x32->64 multiplies with the round
+// function (c0,c1,c2,c3) -> (hi(M1*c2)^c1^k0, lo(M1*c2), hi(M0*c0)^c3^k1,
+// lo(M0*c0)), the key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+const uint32_t PHILOX_M0 = 0xD2511F53u;
+const uint32_t PHILOX_M1 = 0xCD9E8D57u;
+const uint32_t PHILOX_W0 = 0x9E3779B9u;
+const uint32_t PHILOX_W1 = 0xBB67AE85u;
+
+void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += PHILOX_W0; k1 += PHILOX_W1; }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c[0];
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        uint32_t n3 = lo0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+// Random-stream domains (counter word 2).
+enum { D_PAIR = 0, D_PATH = 1, D_RADE = 2, D_BOOT_PAIR = 3, D_BOOT_PATH = 4, D_STATS = 5 };
+const uint32_t MAX_ATTEMPTS = 1u << 16;
+
+// One Philox block for (seed, sample index i, domain, attempt).
+void block_for(uint64_t seed, uint64_t i, uint32_t domain, uint32_t attempt, uint32_t out[4]) {
+    uint32_t ctr[4] = {(uint32_t)i, (uint32_t)(i >> 32), domain, attempt};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    philox4x32_10(ctr, key, out);
+}
+
+// Uniform integer in [0, N), N >= 1, by masking the low 64 bits of a block
+// to the smallest 2^k - 1 >= N - 1 and rejecting values >= N (a rejected
+// value moves to the next attempt counter).  Returns false after
+// MAX_ATTEMPTS rejections.
+bool uniform_below64(uint64_t N, uint64_t seed, uint64_t i, uint32_t domain, uint64_t* x) {
+    uint64_t mask = 0;
+    while (mask < N - 1) mask = (mask << 1) | 1u;
+    for (uint32_t a = 0; a < MAX_ATTEMPTS; ++a) {
+        uint32_t w[4];
+        block_for(seed, i, domain, a, w);
+        uint64_t val = ((uint64_t)w[1] << 32) | w[0];
+        val &= mask;
+        if (val < N) { *x = val; return true; }
+    }
+    return false;
+}
+
+// Same with all 128 bits of the block (for path counts).
+bool uniform_below128(u128 N, uint64_t seed, uint64_t i, uint32_t domain, u128* x) {
+    u128 mask = 0;
+    while (mask < N - 1) mask = (mask << 1) | 1u;
+    for (uint32_t a = 0; a < MAX_ATTEMPTS; ++a) {
+        uint32_t w[4];
+        block_for(seed, i, domain, a, w);
+        u128 val = ((u128)w[3] << 96) | ((u128)w[2] << 64) | ((u128)w[1] << 32) | (u128)w[0];
+        val &= mask;
+        if (val < N) { *x = val; return true; }
+    }
+    return false;
+}
+
+// Sample space of the ob / trk estimators (Sec. 4.1): ordered pairs (s,z),
+// s != z, uniform.  x in [0, n(n-1)) ; s = x / (n-1) ; z' = x mod (n-1) ;
+// z = z' + [z' >= s].
+bool draw_pair(uint32_t n, uint64_t seed, uint64_t i, uint32_t domain, uint32_t* s, uint32_t* z) {
+    uint64_t N = (uint64_t)n * (uint64_t)(n - 1);
+    uint64_t x;
+    if (!uniform_below64(N, seed, i, domain, &x)) return false;
+    uint64_t ss = x / (uint64_t)(n - 1);
+    uint64_t zz = x % (uint64_t)(n - 1);
+    if (zz >= ss) zz += 1;
+    *s = (uint32_t)ss; *z = (uint32_t)zz;
+    return true;
+}
+
+// Rademacher sign lambda_{j,i} (Sec. 3, c-MCERA): bit j of the 128-bit block
+// for (seed, i, RADE, 0); bit 1 -> +1, bit 0 -> -1.
+int rademacher(uint64_t seed, uint64_t i, uint32_t j) {
+    uint32_t w[4];
+    block_for(seed, i, D_RADE, 0, w);
+    return ((w[j >> 5] >> (j & 31)) & 1u) ? 1 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Temporal graph (Sec. 3): a set of temporal edges (u,v,t).  Identical triples
+// name the same vertex appearances, so they are kept once; self loops are
+// dropped (the path sampler's theorem assumes none).
+// ---------------------------------------------------------------------------
+struct Graph {
+    uint32_t n = 0;
+    std::vector<std::tuple<uint32_t, uint32_t, uint32_t>> edges;   // (u,v,t), sorted by (t,u,v)
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> out;  // out[u] = (v,t), ascending t
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> in;   // in[v]  = (w,t)
+    uint64_t self_loops = 0;
+    uint64_t duplicates = 0;
+};
+
+const int64_t NEG_INF = -1;                 // the source appearance (s, -inf)
+const int64_t POS_INF = INT64_MAX;
+
+// A vertex appearance (v, t): v reached at time t.
+typedef std::pair<uint32_t, int64_t> App;
+struct State { uint32_t level; u128 sigma; };
+
+bool add_checked(u128 a, u128 b, u128* r) {
+    u128 s = a + b;
+    if (s < a) return false;
+    *r = s;
+    return true;
+}
+
+enum { OPT_SH = 0, OPT_SFM = 1, OPT_PFM = 2 };
+enum { OK = 0, E_INVAL = 1, E_OVERFLOW = 3, E_RNG = 7 };
+
+// Result of a forward search from s (truncated at z when z is given).
+struct Search {
+    // sh / sfm: appearance states with (level, sigma)
+    std::map<App, State> st;
+    uint32_t d = 0;              // level of z's first appearance (0 = not reached)
+    // pfm: earliest arrival, path counts, minimum hops per vertex
+    std::vector<int64_t> fa;
+    std::vector<u128> sig;
+    std::vector<uint32_t> hop;
+    int status = OK;
+};
+
+// (*)-temporal BFS for sh and sfm over vertex appearances.  Level 0 is
+// (s,-inf).  From every appearance (u,t') on level k, each out-edge (u,v,t)
+// with t > t' reaches (v,t); if (v,t) has no level yet it gets level k+1, and
+// every such (appearance, edge) pair adds sigma(u,t') to sigma(v,t).  The
+// additions are grouped by u: an out-edge (u,v,t) adds the total sigma of u's
+// level-k appearances earlier than t (same sum, taken per edge).  With a
+// target z the search stops after the first level that holds an appearance
+// of z; with no target (z = n) it runs until the frontier is empty.
+Search tbfs_levels(const Graph& G, uint32_t s, uint32_t z) {
+    Search R;
+    App src(s, NEG_INF);
+    R.st[src] = State{0, 1};
+    std::vector<App> frontier(1, src);
+    uint32_t k = 0;
+    while (!frontier.empty()) {
+        std::sort(frontier.begin(), frontier.end());
+        std::vector<App> next;
+        size_t g0 = 0;
+        while (g0 < frontier.size()) {
+            const uint32_t u = frontier[g0].first;
+            size_t g1 = g0;
+            while (g1 < frontier.size() && frontier[g1].first == u) ++g1;
+            // running totals of sigma over u's level-k appearances, ascending in time
+            std::vector<int64_t> times;
+            std::vector<u128> prefix;
+            u128 run = 0;
+            for (size_t q = g0; q < g1; ++q) {
+                if (!add_checked(run, R.st[frontier[q]].sigma, &run)) { R.status = E_OVERFLOW; return R; }
+                times.push_back(frontier[q].second);
+                prefix.push_back(run);
+            }
+            for (const auto& e : G.out[u]) {                      // out[u] is sorted by time
+                int64_t t = e.second;
+                size_t cnt = std::lower_bound(times.begin(), times.end(), t) - times.begin();
+                if (cnt == 0) continue;                           // no appearance of u before t
+                const u128 add = prefix[cnt - 1];
+                App b(e.first, t);
+                auto it = R.st.find(b);
+                if (it == R.st.end()) {
+                    R.st[b] = State{k + 1, add};
+                    next.push_back(b);
+                } else if (it->second.level == k + 1) {
+                    if (!add_checked(it->second.sigma, add, &it->second.sigma)) {
+                        R.status = E_OVERFLOW;
+                        return R;
+                    }
+                }
+            }
+            g0 = g1;
+        }
+        k += 1;
+        bool hit_z = false;
+        for (const App& b : next) if (b.first == z) hit_z = true;
+        if (hit_z) { R.d = k; return R; }
+        frontier.swap(next);
+    }
+    return R;
+}
+
+// Prefix-foremost search (Def. 1(3)): scan all temporal edges in time order.
+// fa[s] = -inf; an edge (u,v,t) with v != s, fa[u] < t and fa[v] in {inf, t}
+// sets fa[v] = t, adds sigma[u] to sigma[v] and lowers hop[v] to hop[u]+1.
+// Within one timestamp the test fa[u] < t ignores values set at that
+// timestamp, so the order of equal-time edges does not matter.
+Search pfm_scan(const Graph& G, uint32_t s) {
+    Search R;
+    R.fa.assign(G.n, POS_INF);
+    R.sig.assign(G.n, 0);
+    R.hop.assign(G.n, UINT32_MAX);
+    R.fa[s] = NEG_INF;
+    R.sig[s] = 1;
+    R.hop[s] = 0;
+    for (const auto& e : G.edges) {
+        uint32_t u = std::get<0>(e), v = std::get<1>(e);
+        int64_t t = std::get<2>(e);
+        if (v == s) continue;
+        if (!(R.fa[u] < t)) continue;
+        if (R.fa[v] != POS_INF && R.fa[v] != t) continue;
+        R.fa[v] = t;
+        if (!add_checked(R.sig[v], R.sig[u], &R.sig[v])) { R.status = E_OVERFLOW; return R; }
+        R.hop[v] = std::min(R.hop[v], R.hop[u] + 1);
+    }
+    return R;
+}
+
+// Endpoint appearances of z in the sh / sfm search, ascending in time.
+// sh keeps every appearance of z on level d; sfm only the earliest one.
+std::vector<App> endpoints(const Search& R, uint32_t z, int opt) {
+    std::vector<App> ends;
+    if (R.d == 0) return ends;
+    for (auto it = R.st.lower_bound(App(z, NEG_INF)); it != R.st.end() && it->first.first == z; ++it)
+        if (it->second.level == R.d) ends.push_back(it->first);
+    if (opt == OPT_SFM && !ends.empty()) ends.resize(1);
+    return ends;
+}
+
+// sigma_sz: the number of (*)-optimal temporal paths from s to z.
+int count_paths(const Graph& G, int opt, uint32_t s, uint32_t z, Search* out, u128* sigma) {
+    if (opt == OPT_PFM) {
+        *out = pfm_scan(G, s);
+        if (out->status != OK) return out->status;
+        *sigma = (out->fa[z] == POS_INF) ? 0 : out->sig[z];
+        return OK;
+    }
+    *out = tbfs_levels(G, s, z);
+    if (out->status != OK) return out->status;
+    u128 tot = 0;
+    for (const App& a : endpoints(*out, z, opt))
+        if (!add_checked(tot, out->st.at(a).sigma, &tot)) return E_OVERFLOW;
+    *sigma = tot;
+    return OK;
+}
+
+// Backward draw of one optimal path (App. C, temporal Riondato-Kornaropoulos
+// estimator): x in [0, sigma_sz) names one path.  At each step the candidates
+// are taken in a fixed order, each weighted by its path count, and the first
+// whose running weight exceeds x is chosen (x drops by the weight before it).
+//   sh / sfm end : appearances of z on level d by ascending time.
+//   sh / sfm step: from (v,t_v) on level k, in-edges (w,v,t_v) by ascending w,
+//                  then appearances (w,t_w) on level k-1 with t_w < t_v by
+//                  ascending t_w; on level 0 only (s,-inf), weight 1.
+//   pfm step     : from v (reached at fa[v]), in-edges (w,v,fa[v]) by
+//                  ascending w with fa[w] < fa[v], weight sigma[w].
+// The vertices are returned from s to z.
+int unrank_path(const Graph& G, int opt, uint32_t s, uint32_t z, const Search& R, u128 x,
+                std::vector<uint32_t>* path, std::vector<int64_t>* times = nullptr) {
+    std::vector<uint32_t> rev;
+    std::vector<int64_t> rev_t;
+    if (opt == OPT_PFM) {
+        uint32_t v = z;
+        rev.push_back(z);
+        rev_t.push_back(R.fa[z]);
+        while (v != s) {
+            std::vector<uint32_t> cands;
+            for (const auto& e : G.in[v])
+                if ((int64_t)e.second == R.fa[v] && R.fa[e.first] < R.fa[v]) cands.push_back(e.first);
+            std::sort(cands.begin(), cands.end());
+            u128 cum = 0;
+            bool picked = false;
+            for (uint32_t w : cands) {
+                u128 wt = R.sig[w];
+                if (x < cum + wt) { x -= cum; v = w; picked = true; break; }
+                cum += wt;
+            }
+            if (!picked) return E_INVAL;
+            rev.push_back(v);
+            rev_t.push_back(R.fa[v]);
+        }
+    } else {
+        std::vector<App> ends = endpoints(R, z, opt);
+        App cur;
+        bool picked = false;
+        u128 cum = 0;
+        for (const App& a : ends) {
+            u128 wt = R.st.at(a).sigma;
+            if (x < cum + wt) { x -= cum; cur = a; picked = true; break; }
+            cum += wt;
+        }
+        if (!picked) return E_INVAL;
+        rev.push_back(z);
+        rev_t.push_back(cur.second);
+        uint32_t k = R.d;
+        while (k > 0) {
+            // candidates for (cur.first, cur.second) on level k
+            std::vector<uint32_t> ws;
+            for (const auto& e : G.in[cur.first])
+                if ((int64_t)e.second == cur.second) ws.push_back(e.first);
+            std::sort(ws.begin(), ws.end());
+            cum = 0;
+            picked = false;
+            App nxt;
+            for (uint32_t w : ws) {
+                std::vector<App> apps;
+                if (k - 1 == 0) {
+                    if (w == s) apps.push_back(App(s, NEG_INF));
+                } else {
+                    for (auto it = R.st.lower_bound(App(w, NEG_INF)); it != R.st.end() && it->first.first == w; ++it)
+                        if (it->second.level == k - 1 && it->first.second < cur.second) apps.push_back(it->first);
+                }
+                for (const App& a : apps) {          // map order = ascending time
+                    u128 wt = R.st.at(a).sigma;
+                    if (x < cum + wt) { x -= cum; nxt = a; picked = true; break; }
+                    cum += wt;
+                }
+                if (picked) break;
+            }
+            if (!picked) return E_INVAL;
+            cur = nxt;
+            rev.push_back(cur.first);
+            rev_t.push_back(cur.second);
+            k -= 1;
+        }
+    }
+    path->assign(rev.rbegin(), rev.rend());
+    if (times) times->assign(rev_t.rbegin(), rev_t.rend());
+    return OK;
+}
+
+struct Sample {
+    uint32_t s = 0, z = 0;
+    u128 sigma = 0;
+    std::vector<uint32_t> path;   // s .. z, empty when z is unreachable
+};
+
+// One sample of Algorithm 1's Update step: draw (s,z), count optimal paths,
+// draw x uniform in [0, sigma_sz), unrank the path.
+int one_sample(const Graph& G, int opt, uint64_t seed, uint64_t i, uint32_t dom_pair, uint32_t dom_path,
+               Sample* out) {
+    if (!draw_pair(G.n, seed, i, dom_pair, &out->s, &out->z)) return E_RNG;
+    Search R;
+    int st = count_paths(G, opt, out->s, out->z, &R, &out->sigma);
+    if (st != OK) return st;
+    out->path.clear();
+    if (out->sigma == 0) return OK;                       // unreachable: empty path
+    u128 x;
+    if (!uniform_below128(out->sigma, seed, i, dom_path, &x)) return E_RNG;
+    return unrank_path(G, opt, out->s, out->z, R, x, &out->path);
+}
+
+// ---------------------------------------------------------------------------
+// Bounds (Sec. 3 Theorem 1; proof of Theorem 3).
+// ---------------------------------------------------------------------------
+// xi of Theorem 1 for c-MCERA value Rc, wimpy variance W, variance bound vhat,
+// confidence delta and r samples.
+// Last line of Theorem 1: xi from the Rademacher bound R.
+double xi_from_R(double Rb, double vhat, double delta, double r) {
+    double L = std::log(4.0 / delta);
+    return 2.0 * Rb + std::sqrt(2.0 * L * (vhat + 4.0 * Rb) / r) + L / (3.0 * r);
+}
+
+double sd_bound(double Rc, double W, double vhat, double delta, double r, double c) {
+    double L = std::log(4.0 / delta);
+    double Rt = Rc + std::sqrt(4.0 * W * L / (c * r));
+    double Rb = Rt + L / r + std::sqrt((L / r) * (L / r) + 2.0 * L * Rt / r);
+    return xi_from_R(Rb, vhat, delta, r);
+}
+
+// omega: the closed-form sample bound at the end of the proof of Theorem 3,
+// ((2 vhat + 2 eps / 3) / eps^2) (ln(2 rho / vhat) + ln(1/delta)).
+double omega_bound(double vhat, double rho, double eps, double delta) {
+    return ((2.0 * vhat + 2.0 * eps / 3.0) / (eps * eps)) * (std::log(2.0 * rho / vhat) + std::log(1.0 / delta));
+}
+
+double delta_round(double delta, uint64_t i, int sched) {
+    return sched == 1 ? delta / std::ldexp(1.0, (int)i) : delta / std::ldexp(1.0, (int)(i + 1));
+}
+
+}  // namespace
+
+// ===========================================================================
+// C API for the tests (ctypes)
+// ===========================================================================
+extern "C" {
+
+struct orc_info {
+    uint64_t r, rounds, omega, s1, bootstrap, sum_int_len, max_hits;
+    int64_t rade_num;
+    double xi, vhat, rho_hat;
+};
+
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) { philox4x32_10(ctr, key, out); }
+
+int orc_uniform64(uint64_t N, uint64_t seed, uint64_t i, uint32_t domain, uint64_t* x) {
+    return uniform_below64(N, seed, i, domain, x) ? OK : E_RNG;
+}
+
+int orc_draw_pair(uint32_t n, uint64_t seed, uint64_t i, uint32_t domain, uint32_t* s, uint32_t* z) {
+    return draw_pair(n, seed, i, domain, s, z) ? OK : E_RNG;
+}
+
+int orc_rademacher(uint64_t seed, uint64_t i, uint32_t j) { return rademacher(seed, i, j); }
+
+void* orc_graph_new(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_t m, uint32_t n) {
+    Graph* G = new Graph();
+    uint32_t nn = n;
+    if (nn == 0) for (uint64_t e = 0; e < m; ++e) nn = std::max(nn, std::max(u[e], v[e]) + 1);
+    G->n = nn;
+    std::set<std::tuple<uint32_t, uint32_t, uint32_t>> seen;       // keyed (t,u,v)
+    for (uint64_t e = 0; e < m; ++e) {
+        if (u[e] == v[e]) { G->self_loops++; continue; }
+        if (!seen.insert(std::make_tuple(t[e], u[e], v[e])).second) G->duplicates++;
+    }
+    G->out.assign(nn, {});
+    G->in.assign(nn, {});
+    for (const auto& k : seen) {                                  // ascending (t,u,v)
+        uint32_t tt = std::get<0>(k), uu = std::get<1>(k), vv = std::get<2>(k);
+        G->edges.push_back(std::make_tuple(uu, vv, tt));
+        G->out[uu].push_back(std::make_pair(vv, tt));             // so out[u] ascends in t
+        G->in[vv].push_back(std::make_pair(uu, tt));
+    }
+    return G;
+}
+
+void orc_graph_free(void* g) { delete (Graph*)g; }
+
+void orc_graph_info(const void* g, uint32_t* n, uint64_t* m, uint64_t* slots, uint64_t* self_loops,
+                    uint64_t* duplicates) {
+    const Graph* G = (const Graph*)g;
+    std::set<std::pair<uint32_t, uint32_t>> apps;
+    for (const auto& e : G->edges) apps.insert(std::make_pair(std::get<1>(e), std::get<2>(e)));
+    *n = G->n; *m = G->edges.size(); *slots = apps.size();
+    *self_loops = G->self_loops; *duplicates = G->duplicates;
+}
+
+// Deduplicated edges, sorted by (t,u,v).
+void orc_graph_edges(const void* g, uint32_t* u, uint32_t* v, uint32_t* t) {
+    const Graph* G = (const Graph*)g;
+    for (size_t e = 0; e < G->edges.size(); ++e) {
+        u[e] = std::get<0>(G->edges[e]); v[e] = std::get<1>(G->edges[e]); t[e] = std::get<2>(G->edges[e]);
+    }
+}
+
+// sigma_sz for a given pair and optimality; d = hop length of the optimal
+// paths for sh/sfm (0 when unreachable), fa(z) for pfm (-1 when unreachable).
+int orc_sigma(const void* g, int opt, uint32_t s, uint32_t z, uint64_t* lo, uint64_t* hi, int64_t* d) {
+    const Graph* G = (const Graph*)g;
+    Search R;
+    u128 sg;
+    int st = count_paths(*G, opt, s, z, &R, &sg);
+    if (st != OK) return st;
+    *lo = (uint64_t)sg; *hi = (uint64_t)(sg >> 64);
+    if (opt == OPT_PFM) *d = (R.fa[z] == POS_INF) ? -1 : R.fa[z];
+    else *d = R.d;
+    return OK;
+}
+
+// The path named by integer x (0 <= x < sigma_sz); vertices s..z.
+// times[q] = arrival time at path[q] (-1 for the source appearance).
+int orc_unrank(const void* g, int opt, uint32_t s, uint32_t z, uint64_t x_lo, uint64_t x_hi,
+               uint32_t* path, int64_t* times, uint32_t cap, uint32_t* len) {
+    const Graph* G = (const Graph*)g;
+    Search R;
+    u128 sg;
+    int st = count_paths(*G, opt, s, z, &R, &sg);
+    if (st != OK) return st;
+    u128 x = ((u128)x_hi << 64) | x_lo;
+    if (x >= sg) return E_INVAL;
+    std::vector<uint32_t> p;
+    std::vector<int64_t> tt;
+    st = unrank_path(*G, opt, s, z, R, x, &p, &tt);
+    if (st != OK) return st;
+    if (p.size() > cap) return E_INVAL;
+    for (size_t q = 0; q < p.size(); ++q) { path[q] = p[q]; times[q] = tt[q]; }
+    *len = (uint32_t)p.size();
+    return OK;
+}
+
+// Samples i0 .. i0+count-1 of the given domains: pair, sigma and the drawn
+// path (full vertex list s..z; len 0 when unreachable).
+int orc_samples(const void* g, int opt, uint64_t seed, uint64_t i0, uint64_t count, uint32_t dom_pair,
+                uint32_t dom_path, uint32_t* s, uint32_t* z, uint64_t* sig_lo, uint64_t* sig_hi, uint32_t* len,
+                uint32_t* paths, uint32_t cap) {
+    const Graph* G = (const Graph*)g;
+    for (uint64_t q = 0; q < count; ++q) {
+        Sample S;
+        int st = one_sample(*G, opt, seed, i0 + q, dom_pair, dom_path, &S);
+        if (st != OK) return st;
+        s[q] = S.s; z[q] = S.z;
+        sig_lo[q] = (uint64_t)S.sigma; sig_hi[q] = (uint64_t)(S.sigma >> 64);
+        len[q] = (uint32_t)S.path.size();
+        if (S.path.size() > cap) return E_INVAL;
+        for (size_t p = 0; p < S.path.size(); ++p) paths[q * cap + p] = S.path[p];
+    }
+    return OK;
+}
+
+double orc_sd_bound(double Rc, double W, double vhat, double delta, double r, double c) {
+    return sd_bound(Rc, W, vhat, delta, r, c);
+}
+
+double orc_xi_from_R(double Rb, double vhat, double delta, double r) { return xi_from_R(Rb, vhat, delta, r); }
+
+double orc_omega_bound(double vhat, double rho, double eps, double delta) {
+    return omega_bound(vhat, rho, eps, delta);
+}
+
+// Algorithm 1 (MANTRA).  fixed_r > 0 runs exactly fixed_r samples with no
+// bootstrap and no stopping test.  Outputs est[v] = hits[v] / r.
+int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed, uint32_t c, double growth,
+                 uint64_t fixed_r, uint64_t bootstrap, int delta_sched, double* est, uint64_t* hits_out,
+                 orc_info* info) {
+    const Graph* G = (const Graph*)g;
+    const uint32_t n = G->n;
+    if (n < 2 || !(eps > 0 && eps < 1) || !(delta > 0 && delta < 1) || c < 1 || c > 128) return E_INVAL;
+    std::vector<uint64_t> hits(n, 0);
+    std::vector<std::vector<int64_t>> S(c, std::vector<int64_t>(n, 0));     // S[j][v] = sum_i lambda_{j,i} f_v(s_i)
+    uint64_t sum_int = 0;
+    orc_info I;
+    std::memset(&I, 0, sizeof(I));
+
+    // Update step for samples [a, b): hits and Rademacher sums (Algorithm 1).
+    auto run = [&](uint64_t a, uint64_t b) -> int {
+        for (uint64_t i = a; i < b; ++i) {
+            Sample sm;
+            int st = one_sample(*G, opt, seed, i, D_PAIR, D_PATH, &sm);
+            if (st != OK) return st;
+            if (sm.path.size() < 3) continue;
+            for (size_t p = 1; p + 1 < sm.path.size(); ++p) {
+                uint32_t v = sm.path[p];
+                hits[v] += 1;
+                sum_int += 1;
+                for (uint32_t j = 0; j < c; ++j) S[j][v] += rademacher(seed, i, j);
+            }
+        }
+        return OK;
+    };
+    // N_R = sum_j max_v S[j][v] (sup over all nodes, no absolute value), H = max_v hits[v].
+    auto reduce = [&](int64_t* NR, uint64_t* H) {
+        int64_t tot = 0;
+        for (uint32_t j = 0; j < c; ++j) {
+            int64_t mx = S[j][0];
+            for (uint32_t v = 1; v < n; ++v) mx = std::max(mx, S[j][v]);
+            tot += mx;
+        }
+        uint64_t h = 0;
+        for (uint32_t v = 0; v < n; ++v) h = std::max(h, hits[v]);
+        *NR = tot; *H = h;
+    };
+    auto xi_of = [&](int64_t NR, uint64_t H, uint64_t r, uint64_t round) {
+        double Rc = (double)NR / ((double)c * (double)r);
+        double W = (double)H / (double)r;
+        return sd_bound(Rc, W, W, delta_round(delta, round, delta_sched), (double)r, (double)c);
+    };
+
+    uint64_t r = 0;
+    if (fixed_r > 0) {
+        int st = run(0, fixed_r);
+        if (st != OK) return st;
+        r = fixed_r;
+        int64_t NR; uint64_t H;
+        reduce(&NR, &H);
+        I.rounds = 1; I.rade_num = NR; I.max_hits = H;
+        I.xi = xi_of(NR, H, r, 1);
+        I.vhat = (double)H / (double)r;
+    } else {
+        // Bootstrap (DrawSufficientSampleSize with delta/2): s' samples from
+        // their own streams, not part of S.
+        uint64_t sb = bootstrap ? bootstrap : (uint64_t)std::ceil(std::log(1.0 / delta) / eps);
+        std::vector<uint64_t> hb(n, 0);
+        uint64_t sum_b = 0;
+        for (uint64_t i = 0; i < sb; ++i) {
+            Sample sm;
+            int st = one_sample(*G, opt, seed, i, D_BOOT_PAIR, D_BOOT_PATH, &sm);
+            if (st != OK) return st;
+            for (size_t p = 1; p + 1 < sm.path.size(); ++p) { hb[sm.path[p]] += 1; sum_b += 1; }
+        }
+        uint64_t Hb = 0;
+        for (uint32_t v = 0; v < n; ++v) Hb = std::max(Hb, hb[v]);
+        double v0 = (double)Hb / (double)sb;
+        double rho = (double)sum_b / (double)sb;
+        if (v0 == 0.0 || rho == 0.0) { v0 = 1.0 / (double)sb; rho = std::max(rho, v0); }
+        uint64_t omega = (uint64_t)std::ceil(omega_bound(v0, rho, eps, delta / 2.0));
+        if (omega < 1) omega = 1;
+        // SamplingSchedule: least s in [s', omega] with xi(R = 0) <= eps.
+        uint64_t s1;
+        double d1 = delta_round(delta, 1, delta_sched);
+        // Theorem 1's xi with R set to 0 (Sec. 4.4, bootstrap phase).
+        auto xi0 = [&](uint64_t s) { return xi_from_R(0.0, v0, d1, (double)s); };
+        if (sb >= omega) s1 = omega;
+        else if (xi0(omega) > eps) s1 = omega;
+        else {
+            uint64_t lo = sb, hi = omega;              // xi0(hi) <= eps
+            while (lo < hi) {
+                uint64_t mid = lo + (hi - lo) / 2;
+                if (xi0(mid) <= eps) hi = mid; else lo = mid + 1;
+            }
+            s1 = lo;
+        }
+        I.bootstrap = sb; I.omega = omega; I.s1 = s1; I.rho_hat = rho;
+        uint64_t target = s1, round = 0;
+        while (true) {
+            round += 1;
+            int st = run(r, target);
+            if (st != OK) return st;
+            r = target;
+            int64_t NR; uint64_t H;
+            reduce(&NR, &H);
+            double xi = xi_of(NR, H, r, round);
+            I.rounds = round; I.rade_num = NR; I.max_hits = H; I.xi = xi; I.vhat = (double)H / (double)r;
+            if (r >= omega || xi <= eps) break;
+            uint64_t nt = (uint64_t)std::ceil(growth * (double)target);
+            if (nt <= target) nt = target + 1;
+            target = std::min(omega, nt);
+        }
+    }
+    I.r = r;
+    I.sum_int_len = sum_int;
+    for (uint32_t v = 0; v < n; ++v) {
+        est[v] = (double)hits[v] / (double)r;
+        if (hits_out) hits_out[v] = hits[v];
+    }
+    if (info) *info = I;
+    return OK;
+}
+
+// Algorithm 2: r_s full searches from sources u_k (uniform in [0,n) from the
+// STATS stream, or every node once when all_sources != 0).  cnt[h] counts
+// reached nodes v != u at distance h; reach[h] = sum_{h' <= h} cnt[h'].
+// Distance: sh / sfm -- level of v's first appearance; pfm -- minimum hops
+// among prefix-foremost paths.  reach must hold n entries; returns D_LB.
+int orc_stats(const void* g, int opt, uint64_t seed, uint64_t r_s, int all_sources, uint64_t* reach,
+              uint32_t* d_lb) {
+    const Graph* G = (const Graph*)g;
+    const uint32_t n = G->n;
+    std::vector<uint64_t> cnt(n + 1, 0);
+    uint32_t D = 0;
+    uint64_t count = all_sources ? n : r_s;
+    for (uint64_t k = 0; k < count; ++k) {
+        uint64_t u64;
+        if (all_sources) u64 = k;
+        else if (!uniform_below64(n, seed, k, D_STATS, &u64)) return E_RNG;
+        uint32_t u = (uint32_t)u64;
+        std::vector<uint32_t> dist(n, UINT32_MAX);
+        if (opt == OPT_PFM) {
+            Search R = pfm_scan(*G, u);
+            if (R.status != OK) return R.status;
+            for (uint32_t v = 0; v < n; ++v) if (v != u && R.fa[v] != POS_INF) dist[v] = R.hop[v];
+        } else {
+            Search R = tbfs_levels(*G, u, n);
+            if (R.status != OK) return R.status;
+            for (const auto& kv : R.st)
+                if (kv.first.first != u) dist[kv.first.first] = std::min(dist[kv.first.first], kv.second.level);
+        }
+        for (uint32_t v = 0; v < n; ++v)
+            if (dist[v] != UINT32_MAX) { cnt[dist[v]] += 1; D = std::max(D, dist[v]); }
+    }
+    uint64_t acc = 0;
+    for (uint32_t h = 0; h < n; ++h) { acc += cnt[h]; reach[h] = acc; }
+    *d_lb = D;
+    return OK;
+}
+
+// Exact (*)-temporal betweenness (Sec. 3): b_v = 1/(n(n-1)) sum_{s != v != z}
+// sigma_sz(v) / sigma_sz.  sigma_sz(v) = sum over appearances a of v of
+// (paths s->a) * (optimal continuations a->z); the continuation counts are
+// taken backward from z's endpoint appearances over the optimal-path DAG.
+// Long double accumulation.  Small graphs only.
+int orc_exact_bc(const void* g, int opt, double* bc) {
+    const Graph* G = (const Graph*)g;
+    const uint32_t n = G->n;
+    std::vector<long double> acc(n, 0.0L);
+    for (uint32_t s = 0; s < n; ++s) {
+        for (uint32_t z = 0; z < n; ++z) {
+            if (s == z) continue;
+            Search R;
+            u128 sg;
+            int st = count_paths(*G, opt, s, z, &R, &sg);
+            if (st != OK) return st;
+            if (sg == 0) continue;
+            std::vector<u128> through(n, 0);
+            if (opt == OPT_PFM) {
+                // beta[v] = number of pfm continuations from v to z, over the
+                // DAG of edges (w,v,fa[v]) with fa[w] < fa[v], in decreasing fa.
+                std::vector<u128> beta(n, 0);
+                beta[z] = 1;
+                std::vector<uint32_t> order;
+                for (uint32_t v = 0; v < n; ++v) if (R.fa[v] != POS_INF) order.push_back(v);
+                std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return R.fa[a] > R.fa[b]; });
+                for (uint32_t v : order) {
+                    if (beta[v] == 0 || v == s) continue;
+                    for (const auto& e : G->in[v])
+                        if ((int64_t)e.second == R.fa[v] && R.fa[e.first] < R.fa[v]) beta[e.first] += beta[v];
+                }
+                for (uint32_t v = 0; v < n; ++v) if (v != s && v != z) through[v] = R.sig[v] * beta[v];
+            } else {
+                std::map<App, u128> beta;
+                for (const App& a : endpoints(R, z, opt)) beta[a] = 1;
+                for (uint32_t k = R.d; k >= 1; --k) {
+                    for (auto& kv : R.st) {
+                        if (kv.second.level != k) continue;
+                        auto bi = beta.find(kv.first);
+                        if (bi == beta.end() || bi->second == 0) continue;
+                        for (const auto& e : G->in[kv.first.first]) {
+                            if ((int64_t)e.second != kv.first.second) continue;
+                            uint32_t w = e.first;
+                            if (k - 1 == 0) {
+                                if (w == s) beta[App(s, NEG_INF)] += bi->second;
+                                continue;
+                            }
+                            for (auto it = R.st.lower_bound(App(w, NEG_INF)); it != R.st.end() && it->first.first == w; ++it)
+                                if (it->second.level == k - 1 && it->first.second < kv.first.second) beta[it->first] += bi->second;
+                        }
+                    }
+                }
+                for (auto& kv : beta) {
+                    uint32_t v = kv.first.first;
+                    if (v == s || v == z) continue;
+                    through[v] += R.st.at(kv.first).sigma * kv.second;
+                }
+            }
+            for (uint32_t v = 0; v < n; ++v)
+                if (through[v]) acc[v] += (long double)through[v] / (long double)sg;
+        }
+    }
+    long double norm = (long double)n * (long double)(n - 1);
+    for (uint32_t v = 0; v < n; ++v) bc[v] = (double)(acc[v] / norm);
+    return OK;
+}
+
+}  // extern "C"

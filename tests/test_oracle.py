@@ -1,0 +1,277 @@
+"""Pins of the CPU oracle against values fixed by the paper and by the
+mathematics (no GPU).  Each test names what it pins."""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import bruteforce as BF
+from oracle import oracle as O
+from paper_2304_08356_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10: published known-answer vectors (Salmon et al., SC'11)
+# --------------------------------------------------------------------------
+def test_philox_known_answers():
+    rows = 0
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        assert O.philox(w[0:4], w[4:6]) == w[6:10]
+        rows += 1
+    assert rows == 3
+
+
+def test_uniform_draw_range_and_frequencies():
+    # rejection sampling: values in [0, N) and flat frequencies (chi-square)
+    N, K = 12, 12000
+    xs = np.array([O.uniform64(N, 99, i, O.D_PAIR) for i in range(K)])
+    assert xs.min() >= 0 and xs.max() < N
+    f = np.bincount(xs, minlength=N)
+    chi2 = ((f - K / N) ** 2 / (K / N)).sum()
+    assert chi2 < 40.0          # 11 dof, p ~ 1e-4
+    assert O.uniform64(1, 5, 3, 0) == 0
+
+
+def test_pair_draw_uniform_over_ordered_pairs():
+    n, K = 5, 20000
+    cnt = np.zeros((n, n))
+    for i in range(K):
+        s, z = O.draw_pair(n, 7, i)
+        assert s != z and 0 <= s < n and 0 <= z < n
+        cnt[s, z] += 1
+    assert np.all(np.diag(cnt) == 0)
+    e = K / (n * (n - 1))
+    chi2 = (((cnt - e) ** 2) / e)[~np.eye(n, dtype=bool)].sum()
+    assert chi2 < 60.0          # 19 dof
+
+
+def test_rademacher_is_bit_of_block():
+    for i in (0, 1, 77):
+        w = O.philox([i & 0xFFFFFFFF, i >> 32, O.D_RADE, 0], [1234, 0])
+        for j in range(128):
+            bit = (w[j >> 5] >> (j & 31)) & 1
+            assert O.rademacher(1234, i, j) == (1 if bit else -1)
+
+
+# --------------------------------------------------------------------------
+# Worked example (paper App. A, figure "example_tp")
+# --------------------------------------------------------------------------
+def _example():
+    edges, expect = [], {0: [], 1: [], 2: []}
+    names = {}
+    for line in open(os.path.join(GOLDEN, "example_tp.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if "|" in line:
+            opt, p = [x.strip() for x in line.split("|")]
+            expect[{"sh": 0, "sfm": 1, "pfm": 2}[opt]].append(
+                [(names[tok.split(":")[0]], int(tok.split(":")[1])) for tok in p.split()])
+            continue
+        a, b, t = line.split()
+        for x in (a, b):
+            names.setdefault(x, len(names))
+        edges.append((names[a], names[b], int(t)))
+    return edges, expect, names
+
+
+def test_worked_example_paths():
+    edges, expect, names = _example()
+    u, v, t = zip(*edges)
+    g = O.Graph(u, v, t)
+    s, z = names["s"], names["z"]
+    for opt in (0, 1, 2):
+        sig, d = g.sigma(opt, s, z)
+        assert sig == len(expect[opt])
+        got = []
+        for x in range(sig):
+            p, ts = g.unrank(opt, s, z, x, with_times=True)
+            got.append(list(zip(p, ts)))
+        assert sorted(got) == sorted(expect[opt])
+    assert g.sigma(0, s, z)[1] == 3          # d_sh(s, z) = 3 hops
+    assert g.sigma(2, s, z)[1] == 4          # fa(z) = 4
+
+
+# --------------------------------------------------------------------------
+# Brute force on tiny graphs: sigma for every pair, and the path draw is a
+# bijection x -> optimal path (Theorem on the path sampler, App. C).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(60))
+def test_bruteforce_sigma_and_bijection(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 7))
+    m = int(rng.integers(4, 16))
+    u, v, t = synth.random_tiny(n, m, t_hi=int(rng.integers(2, 7)), seed=1000 + seed, self_loops=(seed % 5 == 0))
+    edges = BF.dedupe(u, v, t)
+    g = O.Graph(u, v, t, n=n)
+    assert g.m == len(edges)
+    for s in range(n):
+        sets = BF.optimal_sets(edges, n, s)
+        for z in range(n):
+            if z == s:
+                continue
+            for opt in (0, 1, 2):
+                want = sets[z][opt] if z in sets else []
+                sig, _ = g.sigma(opt, s, z)
+                assert sig == len(want), (opt, s, z)
+                got = sorted(tuple(zip(*g.unrank(opt, s, z, x, with_times=True))) for x in range(sig))
+                assert got == sorted(tuple(zip(vs, ts)) for vs, ts in want)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_exact_bc_against_bruteforce_and_lemma1(seed):
+    u, v, t = synth.random_tiny(6, 14, t_hi=5, seed=2000 + seed)
+    edges = BF.dedupe(u, v, t)
+    g = O.Graph(u, v, t, n=6)
+    for opt in (0, 1, 2):
+        want = BF.exact_bc(edges, 6, opt)
+        got = g.exact_bc(opt)
+        assert np.allclose(got, [float(x) for x in want], rtol=0, atol=1e-15)
+        # Lemma 1 (Sec. 3): sum_v b_v = rho
+        assert abs(sum(want) - BF.mean_internal(edges, 6, opt)) == 0
+
+
+def test_layered_dag_reduces_to_static_path_counts():
+    # Textbook reduction: in a layered DAG whose edge times equal the head's
+    # layer, every static path is time-respecting and every s->z path has the
+    # same length, so sh sigma equals the static path count (dynamic program).
+    rng = np.random.default_rng(5)
+    widths = [1, 3, 4, 3, 1]
+    ids, base = [], 0
+    for w in widths:
+        ids.append(list(range(base, base + w)))
+        base += w
+    edges = []
+    for L in range(len(widths) - 1):
+        for a in ids[L]:
+            for b in ids[L + 1]:
+                if rng.random() < 0.7 or L in (0, len(widths) - 2):
+                    edges.append((a, b, L + 1))
+    u, v, t = zip(*edges)
+    g = O.Graph(u, v, t, n=base)
+    s, z = ids[0][0], ids[-1][0]
+    cnt = {s: 1}
+    for L in range(1, len(widths)):
+        for b in ids[L]:
+            cnt[b] = sum(cnt.get(a, 0) for (a, bb, _) in edges if bb == b)
+    for opt in (0, 1, 2):
+        assert g.sigma(opt, s, z)[0] == cnt[z]
+
+
+def test_equal_timestamps_single_edge_paths():
+    # All timestamps equal: every temporal path is one edge (strict increase).
+    u, v, _ = synth.uniform_small(n=30, m=200, seed=3)
+    t = np.full(u.size, 7, np.uint32)
+    g = O.Graph(u, v, t, n=30)
+    pairs = {(int(a), int(b)) for a, b in zip(u, v) if a != b}
+    for (s, z) in [(0, 1), (2, 9), (5, 4)]:
+        for opt in (0, 1, 2):
+            assert g.sigma(opt, s, z)[0] == (1 if (s, z) in pairs else 0)
+    est, hits, info = g.estimate(0, 0.1, 0.1, 1, fixed_r=300)
+    assert hits.sum() == 0 and info["sum_int_len"] == 0
+    reach, dlb = g.stats_counts(0, 1, 0, all_sources=True)
+    assert dlb == 1 and int(reach[1]) == len(pairs)
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1 pieces
+# --------------------------------------------------------------------------
+def test_estimate_invariants_and_mcera_recount():
+    u, v, t = synth.uniform_small(n=40, m=500, t_hi=60, seed=11)
+    g = O.Graph(u, v, t, n=40)
+    r, c, seed = 300, 25, 17
+    for opt in (0, 1, 2):
+        est, hits, info = g.estimate(opt, 0.1, 0.1, seed, c=c, fixed_r=r)
+        samples = g.samples(opt, seed, 0, r)
+        # hits = number of samples whose drawn path has v internal
+        H = np.zeros(40, np.int64)
+        S = np.zeros((c, 40), np.int64)
+        for i, (_, _, _, p) in enumerate(samples):
+            lam = [O.rademacher(seed, i, j) for j in range(c)]
+            for x in p[1:-1]:
+                H[x] += 1
+                S[:, x] += lam
+        assert np.array_equal(hits.astype(np.int64), H)
+        assert int(H.sum()) == info["sum_int_len"]                # Lemma 1, sample form
+        assert info["rade_num"] == int(S.max(axis=1).sum())      # sup over all nodes, no |.|
+        assert info["max_hits"] == int(H.max())
+        assert np.array_equal(est, hits.astype(np.float64) / r)
+
+
+def test_sd_bound_special_cases():
+    # Theorem 1 with R = 0 reduces to sqrt(2 ln(4/d) v / r) + ln(4/d)/(3r)
+    L = math.log(4 / 0.05)
+    assert O.xi_from_R(0.0, 0.01, 0.05, 1000) == pytest.approx(math.sqrt(2 * L * 0.01 / 1000) + L / 3000, rel=1e-14)
+    # with W = 0 and Rc = 0: R~ = 0, R = 2 ln(4/d)/r
+    R = 2 * L / 1000
+    assert O.sd_bound(0.0, 0.0, 0.0, 0.05, 1000, 25) == pytest.approx(2 * R + math.sqrt(2 * L * 4 * R / 1000) + L / 3000, rel=1e-14)
+    # decreasing in r
+    xs = [O.sd_bound(0.01, 0.02, 0.02, 0.05, r, 25) for r in (100, 1000, 10000, 100000)]
+    assert all(a > b for a, b in zip(xs, xs[1:]))
+    # hand-evaluated closed form of omega: vhat=0.01, rho=2, eps=0.01, delta=0.05
+    # ((0.02 + 0.0066667)/1e-4) * (ln 400 + ln 20) = 266.6667 * 8.9872 = 2396.6
+    assert O.omega_bound(0.01, 2.0, 0.01, 0.05) == pytest.approx(2396.58, rel=1e-4)
+
+
+def test_progressive_schedule_properties():
+    u, v, t = synth.chung_lu_bursty(n=400, m=6000, seed=3)
+    g = O.Graph(u, v, t)
+    eps, delta = 0.05, 0.1
+    est, hits, info = g.estimate(0, eps, delta, 5)
+    assert info["bootstrap"] == O.sample_size_bootstrap(eps, delta) == 47
+    assert info["s1"] >= info["bootstrap"] or info["s1"] == info["omega"]
+    assert info["r"] <= info["omega"]
+    assert info["xi"] <= eps or info["r"] >= info["omega"]
+    # schedule: r after k rounds follows s_i = min(omega, ceil(1.2 s_{i-1}))
+    s = info["s1"]
+    for _ in range(info["rounds"] - 1):
+        s = min(info["omega"], math.ceil(1.2 * s))
+    assert s == info["r"]
+    # s1 is the least s in [s', omega] with xi(R = 0) <= eps
+    assert np.isclose(est.sum(), info["sum_int_len"] / info["r"])
+
+
+# --------------------------------------------------------------------------
+# Small-config accuracy: Hoeffding / Theorem 1 against exact betweenness
+# --------------------------------------------------------------------------
+def test_small_config_within_hoeffding_and_xi():
+    u, v, t = synth.uniform_small()
+    g = O.Graph(u, v, t, n=100)
+    exact = g.exact_bc(0)
+    est, hits, info = g.estimate(0, 0.05, 0.1, 1, fixed_r=1000)
+    sd = np.abs(est - exact).max()
+    assert sd <= math.sqrt(math.log(2 * 100 / 0.1) / (2 * 1000))   # 0.0617 (Hoeffding + union bound)
+    assert sd <= info["xi"]                                          # Theorem 1
+    # Lemma 1 on the exact side: sum of exact betweenness = rho >= 0
+    assert exact.sum() > 0
+
+
+# --------------------------------------------------------------------------
+# Algorithm 2: with every node as a source the estimates are exact
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(8))
+def test_stats_all_sources_against_bruteforce(seed):
+    n = 6
+    u, v, t = synth.random_tiny(n, 14, t_hi=6, seed=3000 + seed)
+    edges = BF.dedupe(u, v, t)
+    g = O.Graph(u, v, t, n=n)
+    for opt in (0, 1, 2):
+        d = BF.distances(edges, n, opt)
+        reach, dlb = g.stats_counts(opt, 0, 0, all_sources=True)
+        D = max(d.values()) if d else 0
+        assert dlb == D
+        for h in range(D + 1):
+            assert int(reach[h]) == sum(1 for x in d.values() if x <= h)
+        st = O.stats_summary(reach, dlb, n, n)
+        if d:
+            assert st["zeta"] == pytest.approx(len(d) / (n * (n - 1)), rel=1e-14)
+            assert st["psi"] == pytest.approx(sum(d.values()) / len(d), rel=1e-14)
+    # sfm distances equal sh distances
+    assert np.array_equal(g.stats_counts(0, 0, 0, True)[0], g.stats_counts(1, 0, 0, True)[0])
