@@ -1,0 +1,150 @@
+/*
+ * mantra.h -- C ABI of the GB300 MANTRA library (libmantra.so).
+ *
+ * MANTRA (arXiv 2304.08356) estimates the temporal betweenness of every node
+ * of a directed temporal graph by sampling node pairs, drawing one optimal
+ * temporal path per pair and counting how often each node is an internal
+ * node of the drawn paths; progressive sampling stops when a bound built on
+ * Monte Carlo Empirical Rademacher Averages (c-MCERA) reaches the target
+ * accuracy.  All per-sample work runs in CUDA kernels for sm_103a.
+ *
+ * Conventions (every call):
+ *   - returns a status code (MANTRA_OK = 0); nothing is thrown across the ABI;
+ *   - output buffers are caller-allocated HOST memory unless stated otherwise;
+ *   - a graph handle is owned by the library until mantra_graph_free; calls
+ *     on one graph are serialised by the library (a graph may be shared
+ *     between threads);
+ *   - sample i of a run uses Philox4x32-10 blocks with key = seed and counter
+ *     (i_lo, i_hi, domain, attempt), so a result depends only on
+ *     (graph, optimality, eps, delta, seed, options), never on launch shape.
+ *
+ * Optimalities (paper Sec. 3, Def. 1): MANTRA_SH shortest; MANTRA_SFM
+ * shortest-foremost (minimum hops, then earliest arrival at z -- the reading
+ * fixed by the worked example in the paper's App. A figure); MANTRA_PFM
+ * prefix-foremost.  A temporal path uses strictly increasing times and starts
+ * at (s, -inf); identical (u,v,t) triples are one edge; self loops are
+ * dropped.
+ */
+#ifndef MANTRA_H
+#define MANTRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mantra_graph mantra_graph; /* opaque, device resident */
+
+typedef enum { MANTRA_SH = 0, MANTRA_SFM = 1, MANTRA_PFM = 2 } mantra_opt;
+
+enum {
+    MANTRA_OK = 0,
+    MANTRA_E_INVAL = 1,    /* bad argument (NULL pointer, eps/delta outside (0,1), n < 2, id >= n, c outside [1,128], time > 2^32-3) */
+    MANTRA_E_NOMEM = 2,    /* device or host allocation failed */
+    MANTRA_E_OVERFLOW = 3, /* a path count sigma_sz exceeded 2^128 - 1 */
+    MANTRA_E_CUDA = 4,     /* a CUDA runtime call failed */
+    MANTRA_E_TIMEOUT = 5,  /* reserved: a bounded device wait gave up */
+    MANTRA_E_CHECK = 6,    /* an internal consistency check failed on the device */
+    MANTRA_E_RNG = 7       /* 65536 consecutive rejections in a uniform draw */
+};
+
+/* Options of mantra_estimate (paper Algorithm 1).  Zero-initialise and set
+ * fields, or pass NULL for the defaults. */
+typedef struct {
+    uint32_t c;          /* Monte Carlo trials of the c-MCERA; 0 = 25 (paper Sec. 5) */
+    double growth;       /* geometric schedule factor s_i = growth * s_{i-1}; 0 = 1.2 */
+    uint64_t fixed_r;    /* > 0: no bootstrap and no stopping test, exactly fixed_r samples */
+    uint64_t bootstrap;  /* bootstrap sample count s'; 0 = ceil(ln(1/delta)/eps) */
+    int delta_sched;     /* 0: round i uses delta/2^(i+1) (union bound totals delta); 1: delta/2^i as printed */
+    int out_device;      /* 1: est_out / hits_out are DEVICE pointers (no device-to-host copy) */
+    void* stream;        /* cudaStream_t to run on; NULL = the graph's own stream */
+} mantra_opts;
+
+/* Diagnostics of one mantra_estimate call. */
+typedef struct {
+    uint64_t r;              /* samples in the estimate (|S_i| at the stop) */
+    uint64_t rounds;         /* progressive-sampling rounds */
+    uint64_t omega;          /* sample-size cap omega (0 with fixed_r) */
+    uint64_t s1;             /* first schedule size s_1 */
+    uint64_t bootstrap;      /* bootstrap samples s' */
+    uint64_t sum_int_len;    /* sum over samples of |Int(tp_i)| (= sum_v hits_v) */
+    uint64_t max_hits;       /* H = max_v hits_v */
+    int64_t rade_num;        /* N_R = sum_j max_v S[j][v] */
+    double xi;               /* final supremum-deviation bound (Theorem 1) */
+    double vhat;             /* final empirical wimpy variance W = H / r */
+    double rho_hat;          /* bootstrap estimate of the mean internal length */
+    uint64_t edges_scanned;  /* temporal edges examined by the searches (all samples) */
+    uint64_t sigma_adds;     /* path-count additions into states */
+    uint64_t states_new;     /* appearance states discovered (sh/sfm) */
+    uint64_t wide_samples;   /* samples re-run with 128-bit path counts */
+    double seconds;          /* wall time of the call */
+    double kernel_ms;        /* device time of the search kernels (CUDA events) */
+    uint64_t search_launches;/* search-kernel launches */
+    uint64_t alg_bytes;      /* algorithmic bytes of the search kernels (byte model in the design notes) */
+} mantra_info;
+
+/* Output of mantra_temporal_stats (paper App. D, Algorithm 2). */
+typedef struct {
+    uint32_t d_lb;   /* largest hop distance seen (diameter lower bound D_LB) */
+    uint32_t d_tau;  /* effective diameter: least h with Rhat[h]/Rhat[D_LB] >= tau */
+    double zeta;     /* temporal connectivity rate Rhat[D_LB] / (n(n-1)) */
+    double psi;      /* average temporal distance over connected pairs */
+    double rho;      /* zeta * (psi - 1): mean internal-node count over all ordered pairs */
+    uint64_t r;      /* number of sampled sources r_s */
+    double seconds;
+} mantra_tstats;
+
+/* Build the device-resident temporal-edge store from m host triples.
+ * u, v, t: host arrays of m entries (copied; the caller keeps ownership).
+ * n: number of nodes; 0 = max id + 1.  Ids must be < n, times <= 2^32-3.
+ * Duplicate triples are kept once, self loops dropped (counts reported by
+ * mantra_graph_info).  Paper Sec. 3 (temporal graph). */
+int mantra_graph_load(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_t m, uint32_t n,
+                      mantra_graph** out);
+
+/* Sizes: n, deduplicated edges, arrival slots (distinct (v,t) with an in-edge),
+ * dropped self loops, dropped duplicates.  Any output pointer may be NULL. */
+int mantra_graph_info(const mantra_graph* g, uint32_t* n, uint64_t* m_dedup, uint64_t* slots,
+                      uint64_t* self_loops_dropped, uint64_t* duplicates_dropped);
+
+void mantra_graph_free(mantra_graph* g);
+
+/* Algorithm 1 (MANTRA): progressive sampling of (s,z) pairs with the
+ * temporal Riondato-Kornaropoulos estimator (App. C), c-MCERA stopping rule
+ * (Theorem 1) and sample cap omega (Theorem 3's closed form).
+ * est_out: n doubles, est_v = hits_v / r (IEEE division).  hits_out: n
+ * uint64 or NULL.  info: or NULL.  With opts->out_device = 1 both outputs are
+ * device pointers.  Returns MANTRA_E_INVAL for eps/delta outside (0,1),
+ * c outside [1,128], r >= 2^31. */
+int mantra_estimate(const mantra_graph* g, mantra_opt opt, double eps, double delta, uint64_t seed,
+                    const mantra_opts* opts, double* est_out, uint64_t* hits_out, mantra_info* info);
+
+/* Algorithm 2: r_s = r_override (or ceil(ln n / eps^2) when 0) full searches
+ * from sources drawn uniformly from [0,n) (Philox domain 5).  reach_out (or
+ * NULL): reach_cap entries, reach_out[h] = number of (source, v != source)
+ * pairs at distance <= h (cumulative, unscaled), for h <= min(D_LB, cap-1).
+ * Distances: sh / sfm -- hop level of v's first appearance; pfm -- minimum
+ * hops among prefix-foremost paths. */
+int mantra_temporal_stats(const mantra_graph* g, mantra_opt opt, double eps, uint64_t seed, uint64_t r_override,
+                          double tau, mantra_tstats* out, uint64_t* reach_out, uint32_t reach_cap);
+
+/* Diagnostic: run the per-sample path computation of Algorithm 1's Update
+ * step for sample indices i0 .. i0+count-1 of the given Philox domains
+ * (0/1: estimation pair/path, 3/4: bootstrap pair/path) without
+ * accumulating, and return per sample: s, z, sigma_sz (two uint64 words per
+ * sample: low, high), the number of vertices of the drawn path (0 when z is
+ * unreachable) and the path's vertices s .. z (cap per sample; longer paths
+ * are truncated in nodes but len is exact).  All outputs host arrays. */
+int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, uint32_t dom_pair, uint32_t dom_path,
+                        uint64_t i0, uint64_t count, uint32_t* s_out, uint32_t* z_out, uint64_t* sigma_out,
+                        uint32_t* len_out, uint32_t* nodes_out, uint32_t cap);
+
+const char* mantra_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MANTRA_H */

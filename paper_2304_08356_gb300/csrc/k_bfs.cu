@@ -1,0 +1,474 @@
+// (*)-temporal BFS for the shortest (sh) and shortest-foremost (sfm)
+// optimalities (paper Sec. 3 Def. 1; running-time theorem of Sec. 4.4), the
+// backward path draw of the temporal Riondato-Kornaropoulos estimator
+// (App. C, theorem on the path sampler), and the Update step of Algorithm 1
+// (hit counts and Rademacher sums).  Also the full searches of Algorithm 2.
+//
+// One CTA owns one sample at a time (persistent grid, samples taken from an
+// atomic counter).  States are arrival appearances (v, t) ("slots"); level 0
+// is the source appearance (s, -inf).  Per level k:
+//   segments  the level-k frontier F_k is kept sorted by slot id, i.e. grouped
+//             by vertex and ascending in time; per vertex u a running sum of
+//             sigma over its frontier appearances.
+//   pull      before expanding, z's in-edges are checked against F_k: if any
+//             reaches z, level k+1 is z's level d and the search stops (the
+//             last level is never pushed).
+//   push      every out-edge (u, v, t) of a frontier vertex with
+//             t_min'(u) < t < tmax_in(z) adds sigma of u's frontier
+//             appearances earlier than t to slot (v, t) unless that slot
+//             already has a level <= k.  Appearances at or after z's latest
+//             in-edge time cannot lie on an s-z path; they are not created.
+//   compact   the next-level bitmap is compacted in slot order into F_{k+1}.
+// Visited/next bitmaps live in shared memory when 2*ceil(A/32) words fit,
+// else in per-CTA global scratch.
+#include "mantra_dev.cuh"
+
+namespace mantra {
+
+constexpr int BFS_NT = 1024;
+constexpr int BFS_NW = BFS_NT / 32;
+
+template <bool WIDE>
+__global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const DevGraph g, const Job job, const BfsWs ws) {
+    typedef typename SigOps<WIDE>::T Sig;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t n = g.n;
+    const uint32_t words = (g.A + 31) >> 5;
+
+    char* region = ws.base + (size_t)blockIdx.x * ws.stride;
+    Sig* sig = reinterpret_cast<Sig*>(region + ws.o_sig);
+    Sig* Fc = reinterpret_cast<Sig*>(region + ws.o_fc);
+    uint32_t* F = reinterpret_cast<uint32_t*>(region + ws.o_f);
+    uint32_t* Ft = reinterpret_cast<uint32_t*>(region + ws.o_ft);
+    uint32_t* lev = reinterpret_cast<uint32_t*>(region + ws.o_lev);
+    uint32_t* seg_b = reinterpret_cast<uint32_t*>(region + ws.o_segb);
+    uint32_t* seg_u = reinterpret_cast<uint32_t*>(region + ws.o_segu);
+    uint32_t* cs_seg = reinterpret_cast<uint32_t*>(region + ws.o_csseg);
+    uint32_t* cs_first = reinterpret_cast<uint32_t*>(region + ws.o_csfirst);
+    uint32_t* cs_off = reinterpret_cast<uint32_t*>(region + ws.o_csoff);
+    uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path);
+    uint32_t* VB = reinterpret_cast<uint32_t*>(region + ws.o_vb);   // vertex bitmap (stats)
+
+    extern __shared__ uint32_t dyn_smem[];
+    uint32_t* V = ws.bits_in_smem ? dyn_smem : reinterpret_cast<uint32_t*>(region + ws.o_bits);
+    uint32_t* N = V + words;
+
+    __shared__ uint32_t sm_scan[32];
+    __shared__ uint32_t sm_wcnt[BFS_NW];
+    __shared__ uint64_t sh_q;
+    __shared__ uint32_t sh_found, sh_ovf, sh_err;
+    __shared__ uint32_t sh_rade[4];
+    __shared__ uint32_t sh_d, sh_len;
+    __shared__ u128 sh_sigma;
+
+    if (ws.bits_in_smem) {
+        for (uint32_t w = tid; w < 2 * words; w += BFS_NT) V[w] = 0u;
+    }
+    u64 my_escan = 0, my_eadd = 0, my_snew = 0;
+    __syncthreads();
+
+    for (;;) {
+        if (tid == 0) {
+            sh_q = atomicAdd(job.ctr + C_WORK, 1ull);
+            sh_found = 0; sh_ovf = 0; sh_err = 0; sh_d = 0; sh_len = 0; sh_sigma = 0;
+        }
+        __syncthreads();
+        const uint64_t q = sh_q;
+        if (q >= job.count) break;
+        const uint64_t i = job.idx_list ? job.idx_list[q] : job.i0 + q;
+
+        uint32_t s, z;
+        bool ok;
+        if (job.stats) {
+            uint64_t x;
+            ok = draw_below64(n, job.seed, i, DOM_STATS, &x);
+            s = (uint32_t)x; z = NONE;
+        } else {
+            ok = draw_pair(n, job.seed, i, job.dom_pair, &s, &z);
+        }
+        if (!ok) { if (tid == 0) set_status(job.status, ST_RNG); s = 0; z = 1; }
+        const bool stats = job.stats != 0;
+        const uint32_t tz = stats ? NONE : g.tmax_in[z];
+        bool live = ok && (g.out_ptr[s + 1] > g.out_ptr[s]);
+        if (!stats && (g.slot_ptr[z + 1] == g.slot_ptr[z])) live = false;   // z has no in-edges
+
+        // ---------------- level loop ----------------
+        uint32_t k = 0;
+        uint32_t L = 1;                 // |F_k| (level 0: the virtual source)
+        if (tid == 0) { lev[0] = 0; lev[1] = 0; }
+        __syncthreads();
+        while (live) {
+            // ---- segments of level k ----
+            uint32_t G, Gc, E;
+            if (k == 0) {
+                if (tid == 0) {
+                    seg_b[0] = 0; seg_u[0] = s; Fc[0] = (Sig)1; Ft[0] = 0;
+                    const uint32_t lo = g.out_ptr[s], hi = g.out_ptr[s + 1];
+                    const uint32_t last = lower_bound_u32(g.out_t, lo, hi, tz);
+                    cs_seg[0] = 0; cs_first[0] = lo; cs_off[0] = 0; cs_off[1] = last - lo;
+                    sm_scan[0] = (last > lo) ? 1u : 0u;
+                    sm_scan[1] = last - lo;
+                }
+                __syncthreads();
+                G = 1; Gc = sm_scan[0]; E = sm_scan[1];
+                __syncthreads();
+            } else {
+                const uint32_t* Fk = F + lev[k];
+                // B1: frontier attributes and segment heads
+                uint32_t gbase = 0;
+                for (uint32_t it = 0; it < L; it += BFS_NT) {
+                    const uint32_t idx = it + tid;
+                    uint32_t head = 0, u = 0;
+                    if (idx < L) {
+                        const uint32_t a = Fk[idx];
+                        u = g.slot_v[a];
+                        Ft[idx] = g.slot_t[a];
+                        Fc[idx] = sig[a];
+                        head = (idx == 0) || (g.slot_v[Fk[idx - 1]] != u);
+                    }
+                    uint32_t tot;
+                    const uint32_t ex = block_exclusive_scan<BFS_NT>(head, &tot, sm_scan);
+                    if (head) { seg_b[gbase + ex] = idx; seg_u[gbase + ex] = u; }
+                    gbase += tot;
+                }
+                G = gbase;
+                __syncthreads();
+                // B2: running sums per segment, candidate edge ranges, compaction
+                uint32_t cbase = 0, ebase = 0;
+                for (uint32_t it = 0; it < G; it += BFS_NT) {
+                    const uint32_t gi = it + tid;
+                    uint32_t cand = 0, first = 0;
+                    if (gi < G) {
+                        const uint32_t fb = seg_b[gi], fe = (gi + 1 < G) ? seg_b[gi + 1] : L;
+                        const uint32_t u = seg_u[gi];
+                        Sig run = 0;
+                        for (uint32_t x = fb; x < fe; ++x) {
+                            Sig nr;
+                            if (!SigOps<WIDE>::add(run, Fc[x], &nr) && !stats) sh_ovf = 1;
+                            run = nr;
+                            Fc[x] = run;
+                        }
+                        const uint32_t tmin = Ft[fb];
+                        const uint32_t lo = g.out_ptr[u], hi = g.out_ptr[u + 1];
+                        first = upper_bound_u32(g.out_t, lo, hi, tmin);
+                        const uint32_t last = lower_bound_u32(g.out_t, first, hi, tz);
+                        cand = last > first ? last - first : 0;
+                    }
+                    uint32_t tc, te;
+                    const uint32_t exc = block_exclusive_scan<BFS_NT>(cand > 0 ? 1u : 0u, &tc, sm_scan);
+                    const uint32_t exe = block_exclusive_scan<BFS_NT>(cand, &te, sm_scan);
+                    if (cand > 0) {
+                        cs_seg[cbase + exc] = gi; cs_first[cbase + exc] = first; cs_off[cbase + exc] = ebase + exe;
+                    }
+                    cbase += tc; ebase += te;
+                }
+                Gc = cbase; E = ebase;
+                if (tid == 0) cs_off[Gc] = E;
+                __syncthreads();
+            }
+            if (sh_ovf) break;
+
+            // ---- pull: does level k reach z? ----
+            if (!stats) {
+                const uint32_t zs = g.slot_ptr[z], ze = g.slot_ptr[z + 1];
+                const uint32_t e_lo = g.slot_in[zs], e_hi = g.slot_in[ze];
+                for (uint32_t e = e_lo + tid; e < e_hi; e += BFS_NT) {
+                    const uint32_t w = g.in_u[e];
+                    const uint32_t a = g.in_slot[e];
+                    const uint32_t t = g.slot_t[a];
+                    // segment of w (seg_u ascending)
+                    uint32_t lo = 0, hi = G;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (seg_u[mid] < w) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo < G && seg_u[lo] == w) {
+                        const uint32_t fb = seg_b[lo], fe = (lo + 1 < G) ? seg_b[lo + 1] : L;
+                        bool have = true;
+                        uint32_t idx = fb;
+                        if (k > 0) {
+                            const uint32_t c = lower_bound_u32(Ft, fb, fe, t);   // first Ft >= t
+                            if (c == fb) have = false; else idx = c - 1;
+                        }
+                        if (have) {
+                            if (!SigOps<WIDE>::atomic_add(sig + a, Fc[idx])) sh_ovf = 1;
+                            atomicOr(N + (a >> 5), 1u << (a & 31));
+                            sh_found = 1;
+                        }
+                    }
+                    ++my_escan;
+                }
+                __syncthreads();
+                if (sh_found || sh_ovf) break;
+            }
+
+            // ---- push expansion of level k ----
+            for (uint32_t base = (uint32_t)wid * 32u; base < E; base += BFS_NW * 32u) {
+                uint32_t h0 = 0;
+                if (lane == 0) {
+                    uint32_t lo = 0, hi = Gc;       // last h with cs_off[h] <= base
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (cs_off[mid] <= base) lo = mid; else hi = mid;
+                    }
+                    h0 = lo;
+                }
+                h0 = __shfl_sync(0xFFFFFFFFu, h0, 0);
+                const uint32_t j = base + lane;
+                if (j < E) {
+                    uint32_t lo = h0, hi = min(h0 + 33u, Gc);
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (cs_off[mid] <= j) lo = mid; else hi = mid;
+                    }
+                    const uint32_t gi = cs_seg[lo];
+                    const uint32_t e = cs_first[lo] + (j - cs_off[lo]);
+                    const uint32_t a = g.out_slot[e];
+                    ++my_escan;
+                    if (!((V[a >> 5] >> (a & 31)) & 1u)) {
+                        const uint32_t t = g.out_t[e];
+                        const uint32_t fb = seg_b[gi], fe = (gi + 1 < G) ? seg_b[gi + 1] : L;
+                        uint32_t idx = fb;
+                        if (fe - fb > 1) idx = lower_bound_u32(Ft, fb, fe, t) - 1;   // last Ft < t
+                        atomicOr(N + (a >> 5), 1u << (a & 31));
+                        if (!SigOps<WIDE>::atomic_add(sig + a, Fc[idx]) && !stats) sh_ovf = 1;
+                        ++my_eadd;
+                    }
+                }
+            }
+            __syncthreads();
+            if (sh_ovf) break;
+
+            // ---- compact the next-level bitmap into F_{k+1} ----
+            const uint32_t per_w = (((words + BFS_NW - 1) / BFS_NW) + 31u) & ~31u;
+            const uint32_t w_lo = min((uint32_t)wid * per_w, words), w_hi = min(w_lo + per_w, words);
+            uint32_t cnt = 0;
+            for (uint32_t w = w_lo + lane; w < w_hi; w += 32) cnt += __popc(N[w]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+            if (lane == 0) sm_wcnt[wid] = cnt;
+            __syncthreads();
+            if (wid == 0) {
+                uint32_t x = (lane < BFS_NW) ? sm_wcnt[lane] : 0u, incl = x;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (lane < BFS_NW) sm_wcnt[lane] = incl - x;
+                if (lane == 31) sm_scan[0] = incl;
+            }
+            __syncthreads();
+            const uint32_t Lnext = sm_scan[0];
+            const uint32_t fbase = lev[k + 1];
+            uint32_t off = fbase + sm_wcnt[wid];
+            uint32_t newv = 0;
+            for (uint32_t w0 = w_lo; w0 < w_hi; w0 += 32) {
+                const uint32_t w = w0 + lane;
+                uint32_t bits = (w < w_hi) ? N[w] : 0u;
+                if (bits) { V[w] |= bits; N[w] = 0u; }
+                const uint32_t c = __popc(bits);
+                uint32_t incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                uint32_t pos = off + incl - c;
+                while (bits) {
+                    const uint32_t b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const uint32_t a = w * 32u + b;
+                    F[pos++] = a;
+                    if (stats) {
+                        const uint32_t v = g.slot_v[a];
+                        if (v != s) {
+                            const uint32_t old = atomicOr(VB + (v >> 5), 1u << (v & 31));
+                            if (!(old & (1u << (v & 31)))) ++newv;
+                        }
+                    }
+                }
+                off += __shfl_sync(0xFFFFFFFFu, incl, 31);
+            }
+            if (stats) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) newv += __shfl_xor_sync(0xFFFFFFFFu, newv, o);
+                if (lane == 0 && newv) {
+                    atomicAdd(job.cnt + (k + 1), (u64)newv);
+                    atomicMax(job.dmax, (u64)(k + 1));
+                }
+            }
+            if (tid == 0) lev[k + 2] = fbase + Lnext;
+            if (tid == 0) my_snew += Lnext;
+            __syncthreads();
+            if (Lnext == 0) break;
+            k += 1;
+            L = Lnext;
+        }
+        __syncthreads();
+
+        // ---------------- path draw (one thread) ----------------
+        const bool found = sh_found && !sh_ovf;
+        if (found && tid == 0) {
+            const uint32_t d = k + 1;
+            const uint32_t zs = g.slot_ptr[z], ze = g.slot_ptr[z + 1];
+            Sig tot = 0;
+            for (uint32_t a = zs; a < ze; ++a) {
+                if (!((N[a >> 5] >> (a & 31)) & 1u)) continue;
+                Sig nt;
+                if (!SigOps<WIDE>::add(tot, sig[a], &nt)) sh_ovf = 1;
+                tot = nt;
+                if (job.opt == 1) break;                       // sfm: earliest endpoint only
+            }
+            if (!sh_ovf) {
+                u128 x;
+                if (!draw_below128(SigOps<WIDE>::wide(tot), job.seed, i, job.dom_path, &x)) {
+                    set_status(job.status, ST_RNG); sh_err = 1;
+                }
+                Sig xs = (Sig)x;
+                uint32_t cur = NONE;
+                Sig cum = 0;
+                for (uint32_t a = zs; a < ze && !sh_err; ++a) {
+                    if (!((N[a >> 5] >> (a & 31)) & 1u)) continue;
+                    const Sig wt = sig[a];
+                    if (xs < cum + wt) { xs -= cum; cur = a; break; }
+                    cum += wt;
+                    if (job.opt == 1) break;
+                }
+                if (cur == NONE) sh_err = 1;
+                path[d] = z;
+                uint32_t lvl = d;
+                while (!sh_err && lvl > 1) {
+                    const uint32_t tv = g.slot_t[cur];
+                    const uint32_t* Fp = F + lev[lvl - 1];
+                    const uint32_t Lp = lev[lvl] - lev[lvl - 1];
+                    cum = 0;
+                    uint32_t nxt = NONE;
+                    for (uint32_t e = g.slot_in[cur]; e < g.slot_in[cur + 1] && nxt == NONE; ++e) {
+                        const uint32_t w = g.in_u[e];
+                        const uint32_t ws0 = g.slot_ptr[w], ws1 = g.slot_ptr[w + 1];
+                        for (uint32_t p = lower_bound_u32(Fp, 0, Lp, ws0); p < Lp; ++p) {
+                            const uint32_t a2 = Fp[p];
+                            if (a2 >= ws1 || g.slot_t[a2] >= tv) break;
+                            const Sig wt = sig[a2];
+                            if (xs < cum + wt) { xs -= cum; nxt = a2; break; }
+                            cum += wt;
+                        }
+                    }
+                    if (nxt == NONE) { sh_err = 1; break; }
+                    cur = nxt;
+                    lvl -= 1;
+                    path[lvl] = g.slot_v[cur];
+                }
+                path[0] = s;
+                if (sh_err) set_status(job.status, ST_CHECK);
+                sh_d = d;
+                sh_len = d + 1;
+                sh_sigma = SigOps<WIDE>::wide(tot);
+                if (!sh_err) {
+                    uint32_t w4[4];
+                    philox_block(job.seed, i, DOM_RADE, 0, w4);
+                    sh_rade[0] = w4[0]; sh_rade[1] = w4[1]; sh_rade[2] = w4[2]; sh_rade[3] = w4[3];
+                }
+            }
+        }
+        __syncthreads();
+
+        if (sh_ovf) {
+            if (tid == 0) {
+                if (WIDE) set_status(job.status, ST_OVERFLOW);
+                else job.ovf_list[atomicAdd(job.ctr + C_NOVF, 1ull)] = i;
+            }
+        } else if (!sh_err) {
+            const bool drawn = found && sh_len > 0;
+            // ---------------- hits and Rademacher sums ----------------
+            if (drawn && job.hits && sh_d >= 2) {
+                const uint32_t nint = sh_d - 1;
+                const uint32_t rows = 1 + (job.S ? job.c : 0);
+                for (uint32_t it = tid; it < nint * rows; it += BFS_NT) {
+                    const uint32_t p = it % nint, j = it / nint;
+                    const uint32_t v = path[1 + p];
+                    if (j == 0) atomicAdd(job.hits + v, 1ull);
+                    else {
+                        const uint32_t jj = j - 1;
+                        const int lam = ((sh_rade[jj >> 5] >> (jj & 31)) & 1u) ? 1 : -1;
+                        atomicAdd(job.S + (size_t)jj * n + v, lam);
+                    }
+                }
+                if (tid == 0) atomicAdd(job.ctr + C_SUMINT, (u64)nint);
+            }
+            // ---------------- per-sample record ----------------
+            if (job.rec_len) {
+                const uint64_t r = i - job.i0;
+                const uint32_t len = drawn ? sh_len : 0;
+                if (tid == 0) {
+                    job.rec_s[r] = s; job.rec_z[r] = z;
+                    job.rec_sig[2 * r] = (u64)sh_sigma; job.rec_sig[2 * r + 1] = (u64)(sh_sigma >> 64);
+                    job.rec_len[r] = len;
+                }
+                for (uint32_t p = tid; p < len && p < job.rec_cap; p += BFS_NT)
+                    job.rec_nodes[r * job.rec_cap + p] = path[p];
+            }
+        }
+
+        // ---------------- cleanup: sigma of every touched slot, bitmaps ----------------
+        for (uint32_t w = tid; w < words; w += BFS_NT) {
+            uint32_t bits = V[w] | N[w];
+            if (bits) {
+                V[w] = 0u; N[w] = 0u;
+                while (bits) {
+                    const uint32_t b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    sig[w * 32u + b] = (Sig)0;
+                }
+            }
+        }
+        if (stats) {
+            for (uint32_t w = tid; w < (n + 31) / 32; w += BFS_NT) VB[w] = 0u;
+        }
+        __syncthreads();
+    }
+    if (my_escan) atomicAdd(job.ctr + C_ESCAN, my_escan);
+    if (my_eadd) atomicAdd(job.ctr + C_EADD, my_eadd);
+    if (my_snew) atomicAdd(job.ctr + C_SNEW, my_snew);
+}
+
+// Host-side launch helpers -------------------------------------------------
+
+size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t o = 0;
+    ws->o_sig = o;     o = al(o + (size_t)A * 16);
+    ws->o_fc = o;      o = al(o + (size_t)(A + 1) * 16);
+    ws->o_f = o;       o = al(o + (size_t)(A + 1) * 4);
+    ws->o_ft = o;      o = al(o + (size_t)(A + 1) * 4);
+    ws->o_lev = o;     o = al(o + (size_t)(n + 3) * 4);
+    ws->o_segb = o;    o = al(o + (size_t)(n + 2) * 4);
+    ws->o_segu = o;    o = al(o + (size_t)(n + 2) * 4);
+    ws->o_csseg = o;   o = al(o + (size_t)(n + 2) * 4);
+    ws->o_csfirst = o; o = al(o + (size_t)(n + 2) * 4);
+    ws->o_csoff = o;   o = al(o + (size_t)(n + 2) * 4);
+    ws->o_path = o;    o = al(o + (size_t)(n + 2) * 4);
+    ws->o_vb = o;      o = al(o + (size_t)((n + 31) / 32 + 1) * 4);
+    ws->o_bits = o;
+    if (!bits_in_smem) o = al(o + (size_t)2 * ((A + 31) / 32) * 4);
+    ws->bits_in_smem = bits_in_smem ? 1 : 0;
+    return o;
+}
+
+size_t bfs_smem_bytes(uint32_t A) { return (size_t)2 * ((A + 31) / 32) * 4; }
+
+cudaError_t bfs_configure(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_bfs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_bfs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_bfs(const DevGraph& g, const Job& job, const BfsWs& ws, int grid, size_t smem, bool wide,
+                       cudaStream_t st) {
+    if (wide) k_bfs<true><<<grid, BFS_NT, smem, st>>>(g, job, ws);
+    else k_bfs<false><<<grid, BFS_NT, smem, st>>>(g, job, ws);
+    return cudaGetLastError();
+}
+
+}  // namespace mantra

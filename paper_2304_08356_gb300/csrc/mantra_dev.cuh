@@ -1,0 +1,249 @@
+// Internal device-side declarations of the MANTRA GB300 library.
+//
+// Graph store (built once at load, resident in HBM):
+//   out-CSR  by (u, t, v): out_ptr[n+1], out_v[m], out_t[m], out_slot[m]
+//   slots    distinct arrival appearances (v, t) sorted by (v, t):
+//            slot_ptr[n+1], slot_t[A], slot_v[A], slot_in[A+1]
+//   in-CSR   by (v, t, u): in_u[m], in_slot[m]  (slot a's in-edges are
+//            in_u[slot_in[a] .. slot_in[a+1]), ascending u)
+//   stream   by (t, u, v): st_u[m], st_v[m], st_t[m]
+//   tmax_in[n]  latest in-edge time of v (valid when v has a slot)
+//   tmin_out[n] earliest out-edge time of u (valid when u has out-edges)
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mantra {
+
+typedef unsigned long long u64;
+typedef unsigned __int128 u128;
+
+// Random-stream domains: word 2 of the Philox counter.
+enum : uint32_t { DOM_PAIR = 0, DOM_PATH = 1, DOM_RADE = 2, DOM_BOOT_PAIR = 3, DOM_BOOT_PATH = 4, DOM_STATS = 5 };
+constexpr uint32_t RNG_MAX_ATTEMPTS = 1u << 16;
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+
+// Device status word values (same numbers as the public error codes).
+enum : int { ST_OK = 0, ST_OVERFLOW = 3, ST_CHECK = 6, ST_RNG = 7 };
+
+// Counter slots of a launch (u64 each).
+enum : int { C_WORK = 0, C_SUMINT = 1, C_ESCAN = 2, C_EADD = 3, C_SNEW = 4, C_NOVF = 5, C_NCOUNT = 8 };
+
+struct DevGraph {
+    uint32_t n;
+    uint32_t A;       // number of arrival slots
+    uint32_t m;       // deduplicated temporal edges
+    const uint32_t* out_ptr;
+    const uint32_t* out_v;
+    const uint32_t* out_t;
+    const uint32_t* out_slot;
+    const uint32_t* slot_ptr;
+    const uint32_t* slot_t;
+    const uint32_t* slot_v;
+    const uint32_t* slot_in;
+    const uint32_t* in_u;
+    const uint32_t* in_slot;
+    const uint32_t* st_u;
+    const uint32_t* st_v;
+    const uint32_t* st_t;
+    const uint32_t* tmax_in;
+    const uint32_t* tmin_out;
+};
+
+// One launch over a range (or list) of sample indices.
+struct Job {
+    uint64_t seed;
+    uint64_t i0;               // sample index of position 0
+    uint64_t count;            // number of samples in this launch
+    const uint64_t* idx_list;  // optional: explicit sample indices (count entries)
+    uint32_t dom_pair, dom_path;
+    int opt;                   // 0 sh, 1 sfm, 2 pfm
+    uint32_t c;                // Rademacher trials (S updated when S != nullptr)
+    u64* hits;                 // n, or nullptr: no accumulation
+    int* S;                    // c*n, row j at S + j*n, or nullptr
+    u64* ctr;                  // C_NCOUNT counters
+    uint64_t* ovf_list;        // sample indices whose 64-bit path counts overflowed
+    int* status;
+    // optional per-sample records, indexed by (sample index - i0)
+    uint32_t* rec_s;
+    uint32_t* rec_z;
+    u64* rec_sig;              // 2 per sample: low, high 64 bits of sigma_sz
+    uint32_t* rec_len;         // number of path vertices (0 if unreachable)
+    uint32_t* rec_nodes;       // rec_cap per sample, s .. z
+    uint32_t rec_cap;
+    // Algorithm 2 mode: full searches from sources, reach histogram per hop
+    int stats;
+    u64* cnt;                  // n+1
+    u64* dmax;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), device side.
+// Counter (i_lo, i_hi, domain, attempt), key (seed_lo, seed_hi).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox_block(uint64_t seed, uint64_t i, uint32_t dom, uint32_t attempt,
+                                             uint32_t out[4]) {
+    uint32_t x0 = (uint32_t)i, x1 = (uint32_t)(i >> 32), x2 = dom, x3 = attempt;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a = 0xD2511F53u * x0, ah = __umulhi(0xD2511F53u, x0);
+        const uint32_t b = 0xCD9E8D57u * x2, bh = __umulhi(0xCD9E8D57u, x2);
+        const uint32_t y0 = bh ^ x1 ^ k0, y2 = ah ^ x3 ^ k1;
+        x0 = y0; x1 = b; x2 = y2; x3 = a;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+// Uniform in [0, N) (N >= 1): low 64 bits of a block masked to the smallest
+// all-ones value >= N-1, rejected when >= N (next attempt counter).
+__device__ __forceinline__ bool draw_below64(uint64_t N, uint64_t seed, uint64_t i, uint32_t dom, uint64_t* x) {
+    const uint64_t span = N - 1;
+    const uint64_t mask = span ? (~0ull >> __clzll((long long)span)) : 0ull;
+    for (uint32_t att = 0; att < RNG_MAX_ATTEMPTS; ++att) {
+        uint32_t w[4];
+        philox_block(seed, i, dom, att, w);
+        const uint64_t val = (((uint64_t)w[1] << 32) | w[0]) & mask;
+        if (val < N) { *x = val; return true; }
+    }
+    return false;
+}
+
+// Same over all 128 bits of the block.
+__device__ __forceinline__ bool draw_below128(u128 N, uint64_t seed, uint64_t i, uint32_t dom, u128* x) {
+    const u128 span = N - 1;
+    const uint64_t sh = (uint64_t)(span >> 64), sl = (uint64_t)span;
+    u128 mask;
+    if (sh) mask = ((u128)(~0ull >> __clzll((long long)sh)) << 64) | (u128)~0ull;
+    else mask = sl ? (u128)(~0ull >> __clzll((long long)sl)) : (u128)0;
+    for (uint32_t att = 0; att < RNG_MAX_ATTEMPTS; ++att) {
+        uint32_t w[4];
+        philox_block(seed, i, dom, att, w);
+        const u128 val = (((u128)w[3] << 96) | ((u128)w[2] << 64) | ((u128)w[1] << 32) | (u128)w[0]) & mask;
+        if (val < N) { *x = val; return true; }
+    }
+    return false;
+}
+
+// Ordered pair (s, z), s != z, uniform over the n(n-1) choices.
+__device__ __forceinline__ bool draw_pair(uint32_t n, uint64_t seed, uint64_t i, uint32_t dom, uint32_t* s,
+                                          uint32_t* z) {
+    uint64_t x;
+    if (!draw_below64((uint64_t)n * (uint64_t)(n - 1), seed, i, dom, &x)) return false;
+    const uint64_t a = x / (uint64_t)(n - 1), b = x - a * (uint64_t)(n - 1);
+    *s = (uint32_t)a;
+    *z = (uint32_t)(b + (b >= a ? 1 : 0));
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Path-count arithmetic: 64-bit fast path and 128-bit wide path.
+// ---------------------------------------------------------------------------
+template <bool WIDE> struct SigOps;
+
+template <> struct SigOps<false> {
+    typedef u64 T;
+    __device__ static __forceinline__ bool add(T a, T b, T* r) { *r = a + b; return *r >= a; }
+    // atomic sig[a] += v; returns false when the true sum no longer fits
+    __device__ static __forceinline__ bool atomic_add(T* p, T v) {
+        const T old = atomicAdd(p, v);
+        return old + v >= old;
+    }
+    __device__ static __forceinline__ u128 wide(T a) { return (u128)a; }
+};
+
+template <> struct SigOps<true> {
+    typedef u128 T;
+    __device__ static __forceinline__ bool add(T a, T b, T* r) { *r = a + b; return *r >= a; }
+    __device__ static __forceinline__ bool atomic_add(T* p, T v) {
+        u64* w = reinterpret_cast<u64*>(p);
+        const u64 lo = (u64)v, hi = (u64)(v >> 64);
+        const u64 old_lo = atomicAdd(w, lo);
+        const u64 carry = (old_lo + lo < old_lo) ? 1ull : 0ull;
+        const u64 add_hi = hi + carry;
+        if (add_hi == 0) return !(hi == ~0ull && carry);   // hi + carry wrapped to 0 only if hi was all ones
+        const u64 old_hi = atomicAdd(w + 1, add_hi);
+        return old_hi + add_hi >= old_hi;
+    }
+    __device__ static __forceinline__ u128 wide(T a) { return a; }
+};
+
+// Block-wide exclusive scan of one uint32 per thread.  NT threads; `scratch`
+// holds 32 words of shared memory.  Every thread gets its prefix and the
+// total.  Contains barriers: call from block-uniform control flow only.
+template <int NT>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total, uint32_t* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) scratch[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = (lane < NT / 32) ? scratch[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= o) w += y;
+        }
+        scratch[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t before = wid ? scratch[wid - 1] : 0u;
+    *total = scratch[NT / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// First index in [lo, hi) with a[idx] > key (a ascending).
+__device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t key) {
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (a[mid] <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// First index in [lo, hi) with a[idx] >= key.
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t key) {
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, ST_OK, code); }
+
+// Per-CTA scratch of the sh/sfm search kernel (one region per CTA).
+struct BfsWs {
+    char* base;          // CTA b uses base + b * stride
+    size_t stride;
+    size_t o_sig, o_fc, o_f, o_ft, o_lev, o_segb, o_segu, o_csseg, o_csfirst, o_csoff, o_path, o_bits, o_vb;
+    int bits_in_smem;    // visited / next bitmaps in dynamic shared memory
+};
+
+// Per-warp scratch of the pfm search kernel.
+struct PfmWs {
+    char* base;          // warp w uses base + w * stride
+    size_t stride;
+    size_t o_fa, o_sig, o_hop, o_path;
+};
+
+size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws);
+size_t bfs_smem_bytes(uint32_t A);
+cudaError_t bfs_configure(size_t smem);
+cudaError_t launch_bfs(const DevGraph& g, const Job& job, const BfsWs& ws, int grid, size_t smem, bool wide,
+                       cudaStream_t st);
+size_t pfm_region_bytes(uint32_t n, PfmWs* ws);
+int pfm_threads();
+cudaError_t launch_pfm(const DevGraph& g, const Job& job, const PfmWs& ws, int grid, bool wide, cudaStream_t st);
+cudaError_t launch_round_reduce(const int* S, const u64* hits, uint32_t n, uint32_t c, long long* rowmax, u64* hmax,
+                                cudaStream_t st);
+cudaError_t launch_normalise(const u64* hits, uint32_t n, uint64_t r, double* est, cudaStream_t st);
+
+}  // namespace mantra

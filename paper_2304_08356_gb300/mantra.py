@@ -1,0 +1,174 @@
+"""Thin ctypes binding of libmantra.so (include/mantra.h).
+
+Argument marshalling only: every step of the sampler runs in the library's
+CUDA kernels.  Loading fails loudly when the library is missing; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmantra.so")
+
+SH, SFM, PFM = 0, 1, 2
+OPT_NAMES = {"sh": SH, "sfm": SFM, "pfm": PFM}
+D_PAIR, D_PATH, D_RADE, D_BOOT_PAIR, D_BOOT_PATH, D_STATS = range(6)
+
+ERRORS = {0: "MANTRA_OK", 1: "MANTRA_E_INVAL", 2: "MANTRA_E_NOMEM", 3: "MANTRA_E_OVERFLOW", 4: "MANTRA_E_CUDA",
+          5: "MANTRA_E_TIMEOUT", 6: "MANTRA_E_CHECK", 7: "MANTRA_E_RNG"}
+
+
+class MantraError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__("%s: %s (%d)" % (where, ERRORS.get(code, "?"), code))
+        self.code = code
+
+
+class Opts(C.Structure):
+    _fields_ = [("c", C.c_uint32), ("growth", C.c_double), ("fixed_r", C.c_uint64), ("bootstrap", C.c_uint64),
+                ("delta_sched", C.c_int), ("out_device", C.c_int), ("stream", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("r", C.c_uint64), ("rounds", C.c_uint64), ("omega", C.c_uint64), ("s1", C.c_uint64),
+                ("bootstrap", C.c_uint64), ("sum_int_len", C.c_uint64), ("max_hits", C.c_uint64),
+                ("rade_num", C.c_int64), ("xi", C.c_double), ("vhat", C.c_double), ("rho_hat", C.c_double),
+                ("edges_scanned", C.c_uint64), ("sigma_adds", C.c_uint64), ("states_new", C.c_uint64),
+                ("wide_samples", C.c_uint64), ("seconds", C.c_double), ("kernel_ms", C.c_double),
+                ("search_launches", C.c_uint64), ("alg_bytes", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TStats(C.Structure):
+    _fields_ = [("d_lb", C.c_uint32), ("d_tau", C.c_uint32), ("zeta", C.c_double), ("psi", C.c_double),
+                ("rho", C.c_double), ("r", C.c_uint64), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["mantra_graph_load", "mantra_graph_info", "mantra_graph_free", "mantra_estimate",
+           "mantra_temporal_stats", "mantra_sample_paths", "mantra_strerror"]
+
+_lib = None
+
+
+def lib():
+    """Load libmantra.so (built by paper_2304_08356_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libmantra.so is not built (%s); run paper_2304_08356_gb300.build.build()" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    u32p, u64p, dp = C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_double)
+    L.mantra_graph_load.argtypes = [u32p, u32p, u32p, C.c_uint64, C.c_uint32, C.POINTER(C.c_void_p)]
+    L.mantra_graph_info.argtypes = [C.c_void_p, u32p, u64p, u64p, u64p, u64p]
+    L.mantra_graph_free.argtypes = [C.c_void_p]
+    L.mantra_graph_free.restype = None
+    L.mantra_estimate.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_uint64, C.POINTER(Opts),
+                                  C.c_void_p, C.c_void_p, C.POINTER(Info)]
+    L.mantra_temporal_stats.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_uint64, C.c_double,
+                                        C.POINTER(TStats), u64p, C.c_uint32]
+    L.mantra_sample_paths.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
+                                      C.c_uint64, u32p, u32p, u64p, u32p, u32p, C.c_uint32]
+    L.mantra_strerror.restype = C.c_char_p
+    L.mantra_strerror.argtypes = [C.c_int]
+    _lib = L
+    return L
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _chk(code, where):
+    if code != 0:
+        raise MantraError(code, where)
+
+
+def _opt(opt):
+    return OPT_NAMES[opt] if isinstance(opt, str) else int(opt)
+
+
+def strerror(code: int) -> str:
+    return lib().mantra_strerror(code).decode()
+
+
+class Graph:
+    """A device-resident temporal graph (mantra_graph_load)."""
+
+    def __init__(self, u, v, t, n: int = 0):
+        u = np.ascontiguousarray(u, dtype=np.uint32)
+        v = np.ascontiguousarray(v, dtype=np.uint32)
+        t = np.ascontiguousarray(t, dtype=np.uint32)
+        h = C.c_void_p()
+        _chk(lib().mantra_graph_load(_p(u, C.c_uint32), _p(v, C.c_uint32), _p(t, C.c_uint32), u.size, n,
+                                     C.byref(h)), "mantra_graph_load")
+        self.h = h
+        nn, m, sl, lp, dp_ = C.c_uint32(), C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _chk(lib().mantra_graph_info(self.h, C.byref(nn), C.byref(m), C.byref(sl), C.byref(lp), C.byref(dp_)),
+             "mantra_graph_info")
+        self.n, self.m, self.slots, self.self_loops, self.duplicates = nn.value, m.value, sl.value, lp.value, dp_.value
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().mantra_graph_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def estimate(self, opt, eps, delta, seed, c=0, growth=0.0, fixed_r=0, bootstrap=0, delta_sched=0,
+                 est_out=None, hits_out=None, stream=None):
+        """mantra_estimate.  With est_out / hits_out given as integers they are
+        device pointers (out_device = 1); otherwise host numpy arrays are
+        returned.  Returns (est, hits, info dict)."""
+        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, stream)
+        info = Info()
+        if isinstance(est_out, int):
+            o.out_device = 1
+            _chk(lib().mantra_estimate(self.h, _opt(opt), eps, delta, seed, C.byref(o), C.c_void_p(est_out),
+                                       C.c_void_p(hits_out) if hits_out else None, C.byref(info)),
+                 "mantra_estimate")
+            return None, None, info.as_dict()
+        est = np.zeros(self.n, np.float64)
+        hits = np.zeros(self.n, np.uint64)
+        _chk(lib().mantra_estimate(self.h, _opt(opt), eps, delta, seed, C.byref(o), est.ctypes.data,
+                                   hits.ctypes.data, C.byref(info)), "mantra_estimate")
+        return est, hits, info.as_dict()
+
+    def temporal_stats(self, opt, eps, seed, r_override=0, tau=0.9, reach_cap=None):
+        """mantra_temporal_stats -> (stats dict, reach array)."""
+        cap = reach_cap if reach_cap is not None else self.n
+        reach = np.zeros(max(cap, 1), np.uint64)
+        st = TStats()
+        _chk(lib().mantra_temporal_stats(self.h, _opt(opt), eps, seed, r_override, tau, C.byref(st),
+                                         _p(reach, C.c_uint64), cap), "mantra_temporal_stats")
+        d = st.as_dict()
+        return d, reach[:min(cap, d["d_lb"] + 1)].copy()
+
+    def sample_paths(self, opt, seed, i0, count, dom_pair=D_PAIR, dom_path=D_PATH, cap=None):
+        """mantra_sample_paths -> list of (s, z, sigma, path) per sample."""
+        cap = cap if cap is not None else min(self.n + 1, 4096)
+        s = np.zeros(count, np.uint32); z = np.zeros(count, np.uint32)
+        sig = np.zeros(2 * count, np.uint64); ln = np.zeros(count, np.uint32)
+        nodes = np.zeros(max(count * cap, 1), np.uint32)
+        _chk(lib().mantra_sample_paths(self.h, _opt(opt), seed, dom_pair, dom_path, i0, count,
+                                       _p(s, C.c_uint32), _p(z, C.c_uint32), _p(sig, C.c_uint64),
+                                       _p(ln, C.c_uint32), _p(nodes, C.c_uint32), cap), "mantra_sample_paths")
+        out = []
+        for q in range(count):
+            L = int(ln[q])
+            out.append((int(s[q]), int(z[q]), (int(sig[2 * q + 1]) << 64) | int(sig[2 * q]),
+                        [int(x) for x in nodes[q * cap:q * cap + min(L, cap)]]))
+        return out
