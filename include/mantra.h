@@ -82,6 +82,7 @@ typedef struct {
     double seconds;          /* wall time of the call */
     double kernel_ms;        /* device time of the search kernels (CUDA events) */
     uint64_t search_launches;/* search-kernel launches */
+    uint64_t kernel_launches;/* all kernel launches of the call (search, reduction, normalisation) */
     uint64_t alg_bytes;      /* algorithmic bytes of the search kernels (byte model in the design notes) */
 } mantra_info;
 

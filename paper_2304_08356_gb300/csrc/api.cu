@@ -152,7 +152,7 @@ size_t free_device_bytes() {
 // Search workspaces: one region per CTA (sh/sfm) or per warp (pfm), sized to
 // at most `budget` bytes.  The sigma arrays and global bitmaps start zeroed;
 // every sample leaves them zeroed.
-int ensure_bfs_ws(mantra_graph* G) {
+int ensure_bfs_ws(mantra_graph* G, cudaStream_t st) {
     if (G->bfs_mem) return MANTRA_OK;
     const size_t smem = bfs_smem_bytes(G->A);
     const bool in_smem = smem + 1024 <= G->smem_optin;
@@ -161,7 +161,7 @@ int ensure_bfs_ws(mantra_graph* G) {
     int grid = G->num_sms;
     if ((size_t)grid * region > budget) grid = (int)std::max<size_t>(1, budget / region);
     if (cudaMalloc(&G->bfs_mem, (size_t)grid * region) != cudaSuccess) { G->bfs_mem = nullptr; return MANTRA_E_NOMEM; }
-    CU(cudaMemsetAsync(G->bfs_mem, 0, (size_t)grid * region, G->stream));
+    CU(cudaMemsetAsync(G->bfs_mem, 0, (size_t)grid * region, st));
     G->bws.base = G->bfs_mem;
     G->bws.stride = region;
     G->bfs_grid = grid;
@@ -230,7 +230,7 @@ struct LaunchTotals {
 int run_samples(mantra_graph* G, Job job, cudaStream_t st, LaunchTotals* tot) {
     if (job.count == 0) return MANTRA_OK;
     const bool pfm = job.opt == MANTRA_PFM;
-    int rc = pfm ? ensure_pfm_ws(G) : ensure_bfs_ws(G);
+    int rc = pfm ? ensure_pfm_ws(G) : ensure_bfs_ws(G, st);
     if (rc != MANTRA_OK) return rc;
     if (job.count > G->run_cap) return MANTRA_E_INVAL;
     job.ctr = G->ctr; job.status = G->status; job.ovf_list = G->ovf;
@@ -412,7 +412,7 @@ int mantra_estimate(const mantra_graph* gc, mantra_opt opt, double eps, double d
     Job base{};
     base.seed = seed; base.opt = (int)opt; base.c = c;
 
-    uint64_t r = 0;
+    uint64_t r = 0, reduces = 0;
     int rc;
     if (o.fixed_r > 0) {
         if (o.fixed_r > RMAX) return MANTRA_E_INVAL;
@@ -426,6 +426,7 @@ int mantra_estimate(const mantra_graph* gc, mantra_opt opt, double eps, double d
         r = o.fixed_r;
         int64_t NR; uint64_t H;
         if ((rc = round_reduce(G, c, true, st, &NR, &H)) != MANTRA_OK) return rc;
+        reduces += 1;
         I.rounds = 1; I.rade_num = NR; I.max_hits = H;
         const double W = (double)H / (double)r;
         I.vhat = W;
@@ -444,6 +445,7 @@ int mantra_estimate(const mantra_graph* gc, mantra_opt opt, double eps, double d
         if ((rc = run_samples(G, jb, st, &TB)) != MANTRA_OK) return rc;
         int64_t NRb; uint64_t Hb;
         if ((rc = round_reduce(G, c, false, st, &NRb, &Hb)) != MANTRA_OK) return rc;
+        reduces += 1;
         double v0 = (double)Hb / (double)sb;
         double rho = (double)TB.sum_int / (double)sb;
         if (v0 == 0.0 || rho == 0.0) { v0 = 1.0 / (double)sb; rho = std::max(rho, v0); }
@@ -478,6 +480,7 @@ int mantra_estimate(const mantra_graph* gc, mantra_opt opt, double eps, double d
             r = target;
             int64_t NR; uint64_t H;
             if ((rc = round_reduce(G, c, true, st, &NR, &H)) != MANTRA_OK) return rc;
+            reduces += 1;
             const double W = (double)H / (double)r;
             const double xi = xi_from_mcera((double)NR / ((double)c * (double)r), W, W,
                                             delta_of_round(delta, round, o.delta_sched), (double)r, (double)c);
@@ -501,6 +504,7 @@ int mantra_estimate(const mantra_graph* gc, mantra_opt opt, double eps, double d
     if (info) {
         I.edges_scanned = T.escan; I.sigma_adds = T.eadd; I.states_new = T.snew; I.wide_samples = T.wide;
         I.kernel_ms = T.kernel_ms; I.search_launches = T.launches;
+        I.kernel_launches = T.launches + reduces + 1;
         if (opt == MANTRA_PFM) I.alg_bytes = 16ull * T.escan + 28ull * T.eadd;
         else I.alg_bytes = 12ull * T.escan + 16ull * T.eadd + 24ull * T.snew;
         I.seconds = now_s() - t0;
