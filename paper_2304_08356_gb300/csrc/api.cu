@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -26,7 +28,7 @@ struct mantra_graph {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // search workspaces (allocated on first use, kept with the graph)
     char* bfs_mem = nullptr; BfsWs bws{}; int bfs_grid = 0; size_t bfs_smem = 0;
-    char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0;
+    char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; size_t pfm_bytes = 0;
     // run buffers
     char* run_mem = nullptr; size_t run_bytes = 0; uint32_t run_c = 0; uint64_t run_cap = 0;
     u64* hits = nullptr; int* S = nullptr; u64* ctr = nullptr; int* status = nullptr;
@@ -170,17 +172,26 @@ int ensure_bfs_ws(mantra_graph* G, cudaStream_t st) {
     return MANTRA_OK;
 }
 
-int ensure_pfm_ws(mantra_graph* G) {
-    if (G->pfm_mem) return MANTRA_OK;
-    const size_t region = pfm_region_bytes(G->n, &G->pws);
+// pfm: one region per warp (32 samples), grown to the largest launch seen, at
+// most one warp slot per 32 resident threads and at most a third of free memory.
+int ensure_pfm_ws(mantra_graph* G, uint64_t count) {
     const int wpb = pfm_threads() / 32;
+    const uint64_t max_warps = (uint64_t)G->num_sms * 32;
+    const uint64_t want = std::min<uint64_t>(std::max<uint64_t>((count + 31) / 32, 1), max_warps);
+    const uint64_t have = (uint64_t)G->pfm_grid * wpb;
+    if (G->pfm_mem && have >= want) return MANTRA_OK;
+    const size_t region = pfm_region_bytes(G->n, &G->pws);
+    if (G->pfm_mem) { cudaFree(G->pfm_mem); G->pfm_mem = nullptr; }
     const size_t budget = free_device_bytes() / 3;
-    int blocks = G->num_sms * 4;
-    if ((size_t)blocks * wpb * region > budget) blocks = (int)std::max<size_t>(1, budget / (region * wpb));
-    if (cudaMalloc(&G->pfm_mem, (size_t)blocks * wpb * region) != cudaSuccess) { G->pfm_mem = nullptr; return MANTRA_E_NOMEM; }
+    uint64_t warps = std::min<uint64_t>(want, std::max<size_t>(budget / region, (size_t)wpb));
+    const int blocks = (int)((warps + wpb - 1) / wpb);
+    if (cudaMalloc(&G->pfm_mem, (size_t)blocks * wpb * region) != cudaSuccess) {
+        G->pfm_mem = nullptr; G->pfm_grid = 0; return MANTRA_E_NOMEM;
+    }
     G->pws.base = G->pfm_mem;
     G->pws.stride = region;
     G->pfm_grid = blocks;
+    G->pfm_bytes = (size_t)blocks * wpb * region;
     return MANTRA_OK;
 }
 
@@ -220,9 +231,29 @@ int ensure_run(mantra_graph* G, uint32_t c, uint64_t cap) {
 }
 
 struct LaunchTotals {
-    uint64_t sum_int = 0, escan = 0, eadd = 0, snew = 0, wide = 0, launches = 0;
+    uint64_t sum_int = 0, escan = 0, eadd = 0, snew = 0, fseg = 0, wide = 0, launches = 0;
     double kernel_ms = 0;
 };
+
+// Algorithmic bytes of search work (64-bit path counts):
+//   pfm    4 B fa(u) per (sample, edge) + the 12 B edge shared by the 32 samples of a
+//          warp + 24 B per path-count update (sigma(u) read, sigma(v) read-modify-write)
+//   sh/sfm 12 B edge record + 12 B level test and path-count update per examined edge,
+//          8 B row bounds per frontier vertex, 12 B per discovered state
+uint64_t alg_bytes_of(bool pfm, uint64_t escan, uint64_t eadd, uint64_t snew, uint64_t fseg) {
+    if (pfm) return 4ull * escan + (12ull * escan) / 32 + 24ull * eadd;
+    return 24ull * escan + 8ull * fseg + 12ull * snew;
+}
+
+void log_launch(bool pfm, bool wide, const Job& j, const u64* h, float ms) {
+    static const bool on = std::getenv("MANTRA_LOG_LAUNCHES") != nullptr;
+    if (!on) return;
+    std::fprintf(stderr, "mantra-launch kernel=%s%s samples=%llu escan=%llu eadd=%llu snew=%llu fseg=%llu "
+                 "alg_bytes=%llu ms=%.4f\n", pfm ? "k_pfm" : "k_bfs", wide ? "<wide>" : "",
+                 (unsigned long long)j.count, (unsigned long long)h[C_ESCAN], (unsigned long long)h[C_EADD],
+                 (unsigned long long)h[C_SNEW], (unsigned long long)h[C_FSEG],
+                 (unsigned long long)alg_bytes_of(pfm, h[C_ESCAN], h[C_EADD], h[C_SNEW], h[C_FSEG]), ms);
+}
 
 // One search launch over sample indices [i0, i0+count) (Algorithm 1's
 // Update step, or Algorithm 2's searches when job.stats), followed by a
@@ -230,7 +261,7 @@ struct LaunchTotals {
 int run_samples(mantra_graph* G, Job job, cudaStream_t st, LaunchTotals* tot) {
     if (job.count == 0) return MANTRA_OK;
     const bool pfm = job.opt == MANTRA_PFM;
-    int rc = pfm ? ensure_pfm_ws(G) : ensure_bfs_ws(G, st);
+    int rc = pfm ? ensure_pfm_ws(G, job.count) : ensure_bfs_ws(G, st);
     if (rc != MANTRA_OK) return rc;
     if (job.count > G->run_cap) return MANTRA_E_INVAL;
     job.ctr = G->ctr; job.status = G->status; job.ovf_list = G->ovf;
@@ -247,9 +278,11 @@ int run_samples(mantra_graph* G, Job job, cudaStream_t st, LaunchTotals* tot) {
     tot->launches += 1;
     u64 h[9];
     std::memcpy(h, G->host_ctr, 72);
+    log_launch(pfm, false, job, h, ms);
     int status = (int)(h[8] & 0xFFFFFFFFu);
     if (status != 0) return status;
     tot->sum_int += h[C_SUMINT]; tot->escan += h[C_ESCAN]; tot->eadd += h[C_EADD]; tot->snew += h[C_SNEW];
+    tot->fseg += h[C_FSEG];
     const uint64_t novf = h[C_NOVF];
     if (novf) {
         Job w = job;
@@ -267,9 +300,11 @@ int run_samples(mantra_graph* G, Job job, cudaStream_t st, LaunchTotals* tot) {
         tot->kernel_ms += ms;
         tot->launches += 1;
         std::memcpy(h, G->host_ctr, 72);
+        log_launch(pfm, true, w, h, ms);
         status = (int)(h[8] & 0xFFFFFFFFu);
         if (status != 0) return status;
         tot->sum_int += h[C_SUMINT]; tot->escan += h[C_ESCAN]; tot->eadd += h[C_EADD]; tot->snew += h[C_SNEW];
+        tot->fseg += h[C_FSEG];
         tot->wide += novf;
     }
     return MANTRA_OK;
@@ -466,7 +501,7 @@ int mantra_estimate(const mantra_graph* gc, mantra_opt opt, double eps, double d
         }
         I.bootstrap = sb; I.omega = omega; I.s1 = s1; I.rho_hat = rho;
         T.kernel_ms += TB.kernel_ms; T.launches += TB.launches; T.escan += TB.escan; T.eadd += TB.eadd;
-        T.snew += TB.snew; T.wide += TB.wide;
+        T.snew += TB.snew; T.fseg += TB.fseg; T.wide += TB.wide;
         if ((rc = ensure_run(G, c, omega)) != MANTRA_OK) return rc;
         CU(cudaMemsetAsync(G->hits, 0, (size_t)n * 8, st));
         CU(cudaMemsetAsync(G->S, 0, (size_t)c * n * 4, st));
@@ -505,8 +540,7 @@ int mantra_estimate(const mantra_graph* gc, mantra_opt opt, double eps, double d
         I.edges_scanned = T.escan; I.sigma_adds = T.eadd; I.states_new = T.snew; I.wide_samples = T.wide;
         I.kernel_ms = T.kernel_ms; I.search_launches = T.launches;
         I.kernel_launches = T.launches + reduces + 1;
-        if (opt == MANTRA_PFM) I.alg_bytes = 16ull * T.escan + 28ull * T.eadd;
-        else I.alg_bytes = 12ull * T.escan + 16ull * T.eadd + 24ull * T.snew;
+        I.alg_bytes = alg_bytes_of(opt == MANTRA_PFM, T.escan, T.eadd, T.snew, T.fseg);
         I.seconds = now_s() - t0;
         *info = I;
     }

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const DevGraph g, const Job j
     if (ws.bits_in_smem) {
         for (uint32_t w = tid; w < 2 * words; w += BFS_NT) V[w] = 0u;
     }
-    u64 my_escan = 0, my_eadd = 0, my_snew = 0;
+    u64 my_escan = 0, my_eadd = 0, my_snew = 0, my_fseg = 0;
     __syncthreads();
 
     for (;;) {
@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const DevGraph g, const Job j
                 __syncthreads();
                 G = 1; Gc = sm_scan[0]; E = sm_scan[1];
                 __syncthreads();
+                if (tid == 0) my_fseg += 1;
             } else {
                 const uint32_t* Fk = F + lev[k];
                 // B1: frontier attributes and segment heads
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const DevGraph g, const Job j
                     gbase += tot;
                 }
                 G = gbase;
+                if (tid == 0) my_fseg += G;
                 __syncthreads();
                 // B2: running sums per segment, candidate edge ranges, compaction
                 uint32_t cbase = 0, ebase = 0;
@@ -431,6 +433,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const DevGraph g, const Job j
     if (my_escan) atomicAdd(job.ctr + C_ESCAN, my_escan);
     if (my_eadd) atomicAdd(job.ctr + C_EADD, my_eadd);
     if (my_snew) atomicAdd(job.ctr + C_SNEW, my_snew);
+    if (my_fseg) atomicAdd(job.ctr + C_FSEG, my_fseg);
 }
 
 // Host-side launch helpers -------------------------------------------------

@@ -4,23 +4,25 @@
 // sampler) and the Update step of Algorithm 1.  Also the pfm full searches of
 // Algorithm 2 (distance = minimum hops among prefix-foremost paths).
 //
-// One warp owns one sample.  Per vertex: fa (earliest arrival, encoded
-// fa' = fa + 1, 0 for the source, NONE when unreached), sigma (number of pfm
-// paths) and hop (minimum hops).  The warp walks the stream (t, u, v) in
-// chunks of 32 edges, from the first edge at the source's earliest out-edge
-// time to the last edge at z's latest in-edge time, and stops after the
-// timestamp group at which z is reached.  Inside a chunk an edge (u, v, t)
-// is live when fa(u) < t; arrival times are settled by a fixpoint of
-// atomicMin(fa'(v), t + 1) over live edges (edges in one chunk can chain
-// only across different timestamps), then the edges with fa(v) = t add
-// sigma(u) to sigma(v) one at a time in stream order.
+// One lane owns one sample; a warp walks the time-sorted stream (t, u, v)
+// once for its 32 samples.  Per-sample state is laid out [v][lane] so the
+// warp's 32 reads of fa(u) for one edge are one 128-byte row:
+//   fa'   earliest arrival + 1 (0 for the source, NONE when unreached)
+//   sigma number of pfm paths (64-bit, or 128-bit on the wide re-run)
+//   hop   minimum hops (Algorithm 2 only)
+// An edge (u, v, t) with v != s and fa(u) < t reaches v at t when v is
+// unreached, and adds sigma(u) to sigma(v) when fa(v) = t; within one
+// timestamp fa(u) < t ignores values set at that timestamp, so edge order
+// inside a group does not matter.  A lane is active from its source's
+// earliest out-edge time to z's latest in-edge time and stops after the
+// group at which z is reached.  fa rows of 8 edges are loaded together; the
+// lane's own updates inside those 8 edges are forwarded in registers.
 #include "mantra_dev.cuh"
 
 namespace mantra {
 
-constexpr int PFM_NT = 256;
-
-__device__ __forceinline__ uint32_t ld_fa(const uint32_t* p) { return __ldcg(p); }
+constexpr int PFM_NT = 128;
+constexpr int PFM_ILP = 8;
 
 template <bool WIDE>
 __global__ void __launch_bounds__(PFM_NT) k_pfm(const DevGraph g, const Job job, const PfmWs ws) {
@@ -30,135 +32,158 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const DevGraph g, const Job job,
     const uint64_t gw = ((uint64_t)blockIdx.x * PFM_NT + threadIdx.x) >> 5;
     const uint32_t n = g.n;
     char* region = ws.base + gw * ws.stride;
-    uint32_t* fa = reinterpret_cast<uint32_t*>(region + ws.o_fa);
-    Sig* sig = reinterpret_cast<Sig*>(region + ws.o_sig);
-    uint32_t* hop = reinterpret_cast<uint32_t*>(region + ws.o_hop);
-    uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path);
-    u64 my_escan = 0, my_eadd = 0;
+    uint32_t* fa = reinterpret_cast<uint32_t*>(region + ws.o_fa) + lane;     // fa[v * 32]
+    Sig* sig = reinterpret_cast<Sig*>(region + ws.o_sig) + lane;             // sig[v * 32]
+    uint32_t* hop = reinterpret_cast<uint32_t*>(region + ws.o_hop) + lane;   // hop[v * 32]
+    uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path) + (size_t)lane * (n + 2);
     const bool stats = job.stats != 0;
+    u64 my_escan = 0, my_eadd = 0;
 
     for (;;) {
-        uint64_t q = 0;
-        if (lane == 0) q = atomicAdd(job.ctr + C_WORK, 1ull);
-        q = __shfl_sync(FULL, q, 0);
-        if (q >= job.count) break;
-        const uint64_t i = job.idx_list ? job.idx_list[q] : job.i0 + q;
+        uint64_t q0 = 0;
+        if (lane == 0) q0 = atomicAdd(job.ctr + C_WORK, 32ull);
+        q0 = __shfl_sync(FULL, q0, 0);
+        if (q0 >= job.count) break;
+        const uint64_t q = q0 + lane;
+        const bool have = q < job.count;
+        const uint64_t i = have ? (job.idx_list ? job.idx_list[q] : job.i0 + q) : 0;
 
-        uint32_t s, z;
-        bool ok;
-        if (stats) {
-            uint64_t x;
-            ok = draw_below64(n, job.seed, i, DOM_STATS, &x);
-            s = (uint32_t)x; z = NONE;
-        } else {
-            ok = draw_pair(n, job.seed, i, job.dom_pair, &s, &z);
+        uint32_t s = 0, z = 1;
+        bool ok = true;
+        if (have) {
+            if (stats) {
+                uint64_t x;
+                ok = draw_below64(n, job.seed, i, DOM_STATS, &x);
+                s = (uint32_t)x; z = NONE;
+            } else {
+                ok = draw_pair(n, job.seed, i, job.dom_pair, &s, &z);
+            }
+            if (!ok) { set_status(job.status, ST_RNG); s = 0; z = 1; }
         }
-        if (!ok) { if (lane == 0) set_status(job.status, ST_RNG); s = 0; z = 1; }
+        bool live = have && ok && g.out_ptr[s + 1] > g.out_ptr[s];
+        if (!stats && live && g.slot_ptr[z + 1] == g.slot_ptr[z]) live = false;
+        const uint32_t ts = live ? g.tmin_out[s] : NONE;
+        const uint32_t te = live ? (stats ? NONE - 1 : g.tmax_in[z]) : 0;
 
-        for (uint32_t v = lane; v < n; v += 32) { fa[v] = NONE; sig[v] = (Sig)0; hop[v] = NONE; }
-        __syncwarp();
-        if (lane == 0) { fa[s] = 0u; sig[s] = (Sig)1; hop[s] = 0u; }
+        for (uint32_t v = 0; v < n; ++v) fa[(size_t)v * 32] = NONE;
+        if (live) { fa[(size_t)s * 32] = 0u; sig[(size_t)s * 32] = (Sig)1; hop[(size_t)s * 32] = 0u; }
         __syncwarp();
 
-        bool live = ok && g.out_ptr[s + 1] > g.out_ptr[s];
-        if (!stats && g.slot_ptr[z + 1] == g.slot_ptr[z]) live = false;
-        uint32_t ovf = 0;
-        uint32_t fz = NONE;
-        if (live) {
-            const uint32_t ts = g.tmin_out[s];
-            const uint32_t tz = stats ? (NONE - 1) : g.tmax_in[z];
-            uint32_t e_lo = 0, e_hi = 0;
+        // stream window of the warp: union of the lanes' windows
+        uint32_t wlo = ts, whi = te;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            wlo = min(wlo, __shfl_xor_sync(FULL, wlo, o));
+            whi = max(whi, __shfl_xor_sync(FULL, whi, o));
+        }
+        uint32_t e_lo = 0, e_hi = 0;
+        if (__any_sync(FULL, live)) {
             if (lane == 0) {
-                e_lo = lower_bound_u32(g.st_t, 0, g.m, ts);
-                e_hi = upper_bound_u32(g.st_t, 0, g.m, tz);
+                e_lo = lower_bound_u32(g.st_t, 0, g.m, wlo);
+                e_hi = upper_bound_u32(g.st_t, 0, g.m, whi);
             }
             e_lo = __shfl_sync(FULL, e_lo, 0);
             e_hi = __shfl_sync(FULL, e_hi, 0);
-            for (uint32_t base = e_lo; base < e_hi; base += 32) {
-                const uint32_t e = base + lane;
-                bool valid = e < e_hi;
-                uint32_t u = 0, v = 0, t = 0;
-                if (valid) { u = g.st_u[e]; v = g.st_v[e]; t = g.st_t[e]; }
-                valid = valid && (t < fz);                 // past z's arrival group: nothing left to do
-                if (!__any_sync(FULL, valid)) break;
-                my_escan += valid ? 1 : 0;
-                valid = valid && (v != s);
-                // arrival times inside the chunk
-                unsigned prev = 0;
-                bool act = false;
-                for (int rep = 0; rep < 33; ++rep) {
-                    act = valid && ld_fa(fa + u) <= t;
-                    const unsigned bal = __ballot_sync(FULL, act);
-                    if (bal == prev) break;
-                    if (act) atomicMin(fa + v, t + 1u);
-                    prev = bal;
-                    __syncwarp();
+        }
+        uint32_t fz = NONE;        // fa'(z) once reached
+        uint32_t ovf = 0;
+        for (uint32_t base = e_lo; base < e_hi; base += 32) {
+            const uint32_t e = base + lane;
+            uint32_t eu = 0, ev = 0, et = NONE;
+            if (e < e_hi) { eu = g.st_u[e]; ev = g.st_v[e]; et = g.st_t[e]; }
+            // lanes still scanning at this chunk's first time
+            const uint32_t t0 = __shfl_sync(FULL, et, 0);
+            const bool running = live && t0 <= te && t0 < fz;
+            if (!__any_sync(FULL, running)) break;
+            const uint32_t kmax = min(32u, e_hi - base);
+            for (uint32_t k0 = 0; k0 < kmax; k0 += PFM_ILP) {
+                uint32_t U[PFM_ILP], Vv[PFM_ILP], T[PFM_ILP], FU[PFM_ILP], FV[PFM_ILP];
+                bool on[PFM_ILP];
+#pragma unroll
+                for (int j = 0; j < PFM_ILP; ++j) {
+                    U[j] = __shfl_sync(FULL, eu, (k0 + j) & 31);
+                    Vv[j] = __shfl_sync(FULL, ev, (k0 + j) & 31);
+                    T[j] = __shfl_sync(FULL, et, (k0 + j) & 31);
+                    on[j] = (k0 + j < kmax) && live && T[j] >= ts && T[j] <= te && T[j] < fz && Vv[j] != s;
+                    FU[j] = on[j] ? fa[(size_t)U[j] * 32] : NONE;
+                    FV[j] = on[j] ? fa[(size_t)Vv[j] * 32] : NONE;
                 }
-                __syncwarp();
-                const bool contrib = act && ld_fa(fa + v) == t + 1u;
-                unsigned cm = __ballot_sync(FULL, contrib);
-                my_eadd += contrib ? 1 : 0;
-                while (cm) {
-                    const int l = __ffs(cm) - 1;
-                    if (lane == l) {
-                        Sig nv;
-                        if (!SigOps<WIDE>::add(sig[v], sig[u], &nv) && !stats) ovf = 1;
-                        sig[v] = nv;
-                        const uint32_t hu = hop[u] + 1u;
-                        if (hu < hop[v]) hop[v] = hu;
+                uint32_t newf[PFM_ILP];
+                bool upd[PFM_ILP];
+#pragma unroll
+                for (int j = 0; j < PFM_ILP; ++j) {
+                    uint32_t fu = FU[j], fv = FV[j];
+#pragma unroll
+                    for (int k = 0; k < j; ++k) {          // this lane's own earlier updates in the group
+                        if (upd[k] && Vv[k] == U[j]) fu = newf[k];
+                        if (upd[k] && Vv[k] == Vv[j]) fv = newf[k];
                     }
-                    __syncwarp();
-                    cm &= cm - 1;
+                    upd[j] = false;
+                    newf[j] = 0;
+                    const uint32_t t = T[j];
+                    // fz may have been set by an earlier edge of this group
+                    if (on[j] && t < fz && fu <= t) {
+                        const uint32_t u = U[j], v = Vv[j];
+                        if (fv == NONE) {
+                            fa[(size_t)v * 32] = t + 1u;
+                            sig[(size_t)v * 32] = sig[(size_t)u * 32];
+                            if (stats) hop[(size_t)v * 32] = hop[(size_t)u * 32] + 1u;
+                            upd[j] = true;
+                            newf[j] = t + 1u;
+                            if (v == z) fz = t + 1u;
+                            ++my_eadd;
+                        } else if (fv == t + 1u) {
+                            Sig nv;
+                            if (!SigOps<WIDE>::add(sig[(size_t)v * 32], sig[(size_t)u * 32], &nv) && !stats) ovf = 1;
+                            sig[(size_t)v * 32] = nv;
+                            if (stats) {
+                                const uint32_t hu = hop[(size_t)u * 32] + 1u;
+                                if (hu < hop[(size_t)v * 32]) hop[(size_t)v * 32] = hu;
+                            }
+                            ++my_eadd;
+                        }
+                    }
+                    my_escan += on[j] ? 1 : 0;
                 }
-                if (!stats) fz = ld_fa(fa + z);
-                if (__any_sync(FULL, ovf)) break;
             }
         }
-        ovf = __any_sync(FULL, ovf) ? 1u : 0u;
+        __syncwarp();
 
         if (stats) {
-            if (!ovf && live) {
-                uint32_t dloc = 0;
-                for (uint32_t v0 = 0; v0 < n; v0 += 32) {
-                    const uint32_t v = v0 + lane;
-                    const bool r = v < n && v != s && ld_fa(fa + v) != NONE;
-                    const uint32_t h = r ? hop[v] : NONE;
-                    const unsigned grp = __match_any_sync(FULL, h);
-                    if (r && lane == __ffs(grp) - 1) atomicAdd(job.cnt + h, (u64)__popc(grp));
-                    if (r && h > dloc) dloc = h;
-                }
+            uint32_t dloc = 0;
+            for (uint32_t v = 0; v < n; ++v) {
+                const bool r = live && v != s && fa[(size_t)v * 32] != NONE;
+                const uint32_t h = r ? hop[(size_t)v * 32] : NONE;
+                const unsigned grp = __match_any_sync(FULL, h);
+                if (r && lane == __ffs(grp) - 1) atomicAdd(job.cnt + h, (u64)__popc(grp));
+                if (r && h > dloc) dloc = h;
+            }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) dloc = max(dloc, __shfl_xor_sync(FULL, dloc, o));
-                if (lane == 0 && dloc) atomicMax(job.dmax, (u64)dloc);
-            }
-            if (ovf && lane == 0) {
-                if (WIDE) set_status(job.status, ST_OVERFLOW);
-                else job.ovf_list[atomicAdd(job.ctr + C_NOVF, 1ull)] = i;
-            }
+            for (int o = 16; o > 0; o >>= 1) dloc = max(dloc, __shfl_xor_sync(FULL, dloc, o));
+            if (lane == 0 && dloc) atomicMax(job.dmax, (u64)dloc);
             continue;
         }
 
-        // ---------------- path draw (lane 0) ----------------
+        // ---------------- path draw, one lane per sample ----------------
         uint32_t len = 0, err = 0;
         u128 sigma_sz = 0;
-        if (!ovf && lane == 0 && live && fz != NONE) {
-            const Sig tot = sig[z];
+        if (have && !ovf && live && fz != NONE) {
+            const Sig tot = sig[(size_t)z * 32];
             sigma_sz = SigOps<WIDE>::wide(tot);
             u128 x;
             if (!draw_below128(sigma_sz, job.seed, i, job.dom_path, &x)) { err = 1; set_status(job.status, ST_RNG); }
             Sig xs = (Sig)x;
-            // walk back from z; path[] collects z .. s, reversed below
             uint32_t v = z, cnt = 0;
             path[cnt++] = z;
             while (!err && v != s) {
-                const uint32_t fv = ld_fa(fa + v);
+                const uint32_t fv = fa[(size_t)v * 32];
                 const uint32_t a = lower_bound_u32(g.slot_t, g.slot_ptr[v], g.slot_ptr[v + 1], fv - 1u);
                 Sig cum = 0;
                 uint32_t nxt = NONE;
                 for (uint32_t e = g.slot_in[a]; e < g.slot_in[a + 1]; ++e) {
                     const uint32_t w = g.in_u[e];
-                    if (!(ld_fa(fa + w) < fv)) continue;
-                    const Sig wt = sig[w];
+                    if (!(fa[(size_t)w * 32] < fv)) continue;
+                    const Sig wt = sig[(size_t)w * 32];
                     if (xs < cum + wt) { xs -= cum; nxt = w; break; }
                     cum += wt;
                 }
@@ -174,43 +199,32 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const DevGraph g, const Job job,
                 len = cnt;
             }
         }
-        len = __shfl_sync(FULL, len, 0);
-        err = __shfl_sync(FULL, err, 0);
-        __syncwarp();
-
-        if (ovf) {
-            if (lane == 0) {
-                if (WIDE) set_status(job.status, ST_OVERFLOW);
-                else job.ovf_list[atomicAdd(job.ctr + C_NOVF, 1ull)] = i;
-            }
-            continue;
+        if (have && ovf) {
+            if (WIDE) set_status(job.status, ST_OVERFLOW);
+            else job.ovf_list[atomicAdd(job.ctr + C_NOVF, 1ull)] = i;
         }
-        if (err) continue;
-        if (job.hits && len >= 3) {
-            uint32_t w4[4];
-            philox_block(job.seed, i, DOM_RADE, 0, w4);
-            const uint32_t nint = len - 2;
-            const uint32_t rows = 1 + (job.S ? job.c : 0);
-            for (uint32_t it = lane; it < nint * rows; it += 32) {
-                const uint32_t p = it % nint, j = it / nint;
-                const uint32_t v = path[1 + p];
-                if (j == 0) atomicAdd(job.hits + v, 1ull);
-                else {
-                    const uint32_t jj = j - 1;
-                    const int lam = ((w4[jj >> 5] >> (jj & 31)) & 1u) ? 1 : -1;
-                    atomicAdd(job.S + (size_t)jj * n + v, lam);
+        if (have && !ovf && !err) {
+            if (job.hits && len >= 3) {
+                uint32_t w4[4];
+                philox_block(job.seed, i, DOM_RADE, 0, w4);
+                for (uint32_t p = 1; p + 1 < len; ++p) {
+                    const uint32_t v = path[p];
+                    atomicAdd(job.hits + v, 1ull);
+                    if (job.S)
+                        for (uint32_t jj = 0; jj < job.c; ++jj) {
+                            const int lam = ((w4[jj >> 5] >> (jj & 31)) & 1u) ? 1 : -1;
+                            atomicAdd(job.S + (size_t)jj * n + v, lam);
+                        }
                 }
+                atomicAdd(job.ctr + C_SUMINT, (u64)(len - 2));
             }
-            if (lane == 0) atomicAdd(job.ctr + C_SUMINT, (u64)nint);
-        }
-        if (job.rec_len) {
-            const uint64_t r = i - job.i0;
-            if (lane == 0) {
+            if (job.rec_len) {
+                const uint64_t r = i - job.i0;
                 job.rec_s[r] = s; job.rec_z[r] = z;
                 job.rec_sig[2 * r] = (u64)sigma_sz; job.rec_sig[2 * r + 1] = (u64)(sigma_sz >> 64);
                 job.rec_len[r] = len;
+                for (uint32_t p = 0; p < len && p < job.rec_cap; ++p) job.rec_nodes[r * job.rec_cap + p] = path[p];
             }
-            for (uint32_t p = lane; p < len && p < job.rec_cap; p += 32) job.rec_nodes[r * job.rec_cap + p] = path[p];
         }
         __syncwarp();
     }
@@ -225,13 +239,14 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const DevGraph g, const Job job,
     }
 }
 
+// Per-warp region: 32 lanes' state rows plus one path buffer per lane.
 size_t pfm_region_bytes(uint32_t n, PfmWs* ws) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t o = 0;
-    ws->o_fa = o;   o = al(o + (size_t)n * 4);
-    ws->o_sig = o;  o = al(o + (size_t)n * 16);
-    ws->o_hop = o;  o = al(o + (size_t)n * 4);
-    ws->o_path = o; o = al(o + (size_t)(n + 2) * 4);
+    ws->o_fa = o;   o = al(o + (size_t)n * 32 * 4);
+    ws->o_sig = o;  o = al(o + (size_t)n * 32 * 16);
+    ws->o_hop = o;  o = al(o + (size_t)n * 32 * 4);
+    ws->o_path = o; o = al(o + (size_t)32 * (n + 2) * 4);
     return o;
 }
 

@@ -27,7 +27,7 @@ constexpr uint32_t NONE = 0xFFFFFFFFu;
 enum : int { ST_OK = 0, ST_OVERFLOW = 3, ST_CHECK = 6, ST_RNG = 7 };
 
 // Counter slots of a launch (u64 each).
-enum : int { C_WORK = 0, C_SUMINT = 1, C_ESCAN = 2, C_EADD = 3, C_SNEW = 4, C_NOVF = 5, C_NCOUNT = 8 };
+enum : int { C_WORK = 0, C_SUMINT = 1, C_ESCAN = 2, C_EADD = 3, C_SNEW = 4, C_NOVF = 5, C_FSEG = 6, C_NCOUNT = 8 };
 
 struct DevGraph {
     uint32_t n;
