@@ -54,6 +54,11 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const DevGraph g, const Job j
     uint32_t* N = V + words;
 
     __shared__ uint32_t sm_scan[32];
+    __shared__ u64 sm_scan64[32];
+    __shared__ Sig sm_segx[32];
+    __shared__ uint32_t sm_segf[32];
+    __shared__ Sig sh_carry;
+    __shared__ uint32_t sh_scan_ovf;
     __shared__ uint32_t sm_wcnt[BFS_NW];
     __shared__ uint64_t sh_q;
     __shared__ uint32_t sh_found, sh_ovf, sh_err;
@@ -115,54 +120,59 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const DevGraph g, const Job j
                 if (tid == 0) my_fseg += 1;
             } else {
                 const uint32_t* Fk = F + lev[k];
-                // B1: frontier attributes and segment heads
+                // B1: frontier attributes, segment heads and per-vertex running sums
+                // of sigma (block-wide segmented scan, one tile of BFS_NT per pass)
                 uint32_t gbase = 0;
+                if (tid == 0) { sh_carry = (Sig)0; sh_scan_ovf = 0; }
+                __syncthreads();
                 for (uint32_t it = 0; it < L; it += BFS_NT) {
                     const uint32_t idx = it + tid;
-                    uint32_t head = 0, u = 0;
+                    uint32_t head = 1, u = 0;
+                    Sig val = 0;
                     if (idx < L) {
                         const uint32_t a = Fk[idx];
                         u = g.slot_v[a];
                         Ft[idx] = g.slot_t[a];
-                        Fc[idx] = sig[a];
+                        val = sig[a];
                         head = (idx == 0) || (g.slot_v[Fk[idx - 1]] != u);
                     }
+                    const Sig run = block_segmented_scan<BFS_NT, Sig>(val, head, sm_segx, sm_segf, &sh_carry,
+                                                                       &sh_scan_ovf);
+                    if (idx < L) Fc[idx] = run;
+                    const uint32_t hd = (idx < L) ? head : 0u;
                     uint32_t tot;
-                    const uint32_t ex = block_exclusive_scan<BFS_NT>(head, &tot, sm_scan);
-                    if (head) { seg_b[gbase + ex] = idx; seg_u[gbase + ex] = u; }
+                    const uint32_t ex = block_exclusive_scan<BFS_NT>(hd, &tot, sm_scan);
+                    if (hd) { seg_b[gbase + ex] = idx; seg_u[gbase + ex] = u; }
                     gbase += tot;
                 }
                 G = gbase;
-                if (tid == 0) my_fseg += G;
+                if (tid == 0) {
+                    my_fseg += G;
+                    if (sh_scan_ovf && !stats) sh_ovf = 1;
+                }
                 __syncthreads();
-                // B2: running sums per segment, candidate edge ranges, compaction
+                // B2: candidate edge ranges per segment and their compaction
                 uint32_t cbase = 0, ebase = 0;
                 for (uint32_t it = 0; it < G; it += BFS_NT) {
                     const uint32_t gi = it + tid;
                     uint32_t cand = 0, first = 0;
                     if (gi < G) {
-                        const uint32_t fb = seg_b[gi], fe = (gi + 1 < G) ? seg_b[gi + 1] : L;
+                        const uint32_t fb = seg_b[gi];
                         const uint32_t u = seg_u[gi];
-                        Sig run = 0;
-                        for (uint32_t x = fb; x < fe; ++x) {
-                            Sig nr;
-                            if (!SigOps<WIDE>::add(run, Fc[x], &nr) && !stats) sh_ovf = 1;
-                            run = nr;
-                            Fc[x] = run;
-                        }
                         const uint32_t tmin = Ft[fb];
                         const uint32_t lo = g.out_ptr[u], hi = g.out_ptr[u + 1];
                         first = upper_bound_u32(g.out_t, lo, hi, tmin);
                         const uint32_t last = lower_bound_u32(g.out_t, first, hi, tz);
                         cand = last > first ? last - first : 0;
                     }
-                    uint32_t tc, te;
-                    const uint32_t exc = block_exclusive_scan<BFS_NT>(cand > 0 ? 1u : 0u, &tc, sm_scan);
-                    const uint32_t exe = block_exclusive_scan<BFS_NT>(cand, &te, sm_scan);
+                    u64 tot;
+                    const u64 ex = block_exclusive_scan64<BFS_NT>(((u64)(cand > 0 ? 1u : 0u) << 32) | cand, &tot,
+                                                                  sm_scan64);
+                    const uint32_t exc = (uint32_t)(ex >> 32), exe = (uint32_t)ex;
                     if (cand > 0) {
                         cs_seg[cbase + exc] = gi; cs_first[cbase + exc] = first; cs_off[cbase + exc] = ebase + exe;
                     }
-                    cbase += tc; ebase += te;
+                    cbase += (uint32_t)(tot >> 32); ebase += (uint32_t)tot;
                 }
                 Gc = cbase; E = ebase;
                 if (tid == 0) cs_off[Gc] = E;
@@ -309,65 +319,115 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const DevGraph g, const Job j
         }
         __syncthreads();
 
-        // ---------------- path draw (one thread) ----------------
+        // ---------------- path draw (warp 0) ----------------
         const bool found = sh_found && !sh_ovf;
-        if (found && tid == 0) {
+        if (found && wid == 0) {
+            const uint32_t FULL = 0xFFFFFFFFu;
             const uint32_t d = k + 1;
             const uint32_t zs = g.slot_ptr[z], ze = g.slot_ptr[z + 1];
-            Sig tot = 0;
-            for (uint32_t a = zs; a < ze; ++a) {
-                if (!((N[a >> 5] >> (a & 31)) & 1u)) continue;
-                Sig nt;
-                if (!SigOps<WIDE>::add(tot, sig[a], &nt)) sh_ovf = 1;
-                tot = nt;
-                if (job.opt == 1) break;                       // sfm: earliest endpoint only
+            bool bad = false, err = false;
+            // endpoints: z's slots on level d, ascending in time (sfm: the first only)
+            uint32_t first = NONE;
+            for (uint32_t a0 = zs; a0 < ze && first == NONE; a0 += 32) {
+                const uint32_t a = a0 + lane;
+                const bool b = a < ze && ((N[a >> 5] >> (a & 31)) & 1u);
+                const unsigned msk = __ballot_sync(FULL, b);
+                if (msk) first = a0 + __ffs(msk) - 1;
             }
-            if (!sh_ovf) {
-                u128 x;
-                if (!draw_below128(SigOps<WIDE>::wide(tot), job.seed, i, job.dom_path, &x)) {
-                    set_status(job.status, ST_RNG); sh_err = 1;
+            Sig tot = 0;
+            if (job.opt == 1) tot = sig[first];
+            else {
+                for (uint32_t a = zs + lane; a < ze; a += 32)
+                    if ((N[a >> 5] >> (a & 31)) & 1u) { const Sig sm = tot + sig[a]; bad |= sm < tot; tot = sm; }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const Sig y = shfl_xor_w(tot, o);
+                    const Sig sm = tot + y;
+                    bad |= sm < tot;
+                    tot = sm;
                 }
-                Sig xs = (Sig)x;
+            }
+            if (__any_sync(FULL, bad)) {
+                if (lane == 0) sh_ovf = 1;
+            } else {
+                u128 x = 0;
+                uint32_t rng_ok = 1;
+                if (lane == 0) rng_ok = draw_below128(SigOps<WIDE>::wide(tot), job.seed, i, job.dom_path, &x) ? 1u : 0u;
+                rng_ok = __shfl_sync(FULL, rng_ok, 0);
+                Sig xs = shfl_idx_w((Sig)x, 0);
+                if (!rng_ok) { err = true; if (lane == 0) set_status(job.status, ST_RNG); }
                 uint32_t cur = NONE;
-                Sig cum = 0;
-                for (uint32_t a = zs; a < ze && !sh_err; ++a) {
-                    if (!((N[a >> 5] >> (a & 31)) & 1u)) continue;
-                    const Sig wt = sig[a];
-                    if (xs < cum + wt) { xs -= cum; cur = a; break; }
-                    cum += wt;
-                    if (job.opt == 1) break;
+                const uint32_t ze_end = (job.opt == 1) ? first + 1 : ze;
+                for (uint32_t a0 = (job.opt == 1 ? first : zs); !err && a0 < ze_end && cur == NONE; a0 += 32) {
+                    const uint32_t a = a0 + lane;
+                    const Sig wt = (a < ze_end && ((N[a >> 5] >> (a & 31)) & 1u)) ? sig[a] : (Sig)0;
+                    const Sig incl = warp_inclusive_sum(wt);
+                    const unsigned msk = __ballot_sync(FULL, xs < incl);
+                    if (msk) {
+                        const int l = __ffs(msk) - 1;
+                        const Sig before = shfl_idx_w(incl - wt, l);
+                        cur = a0 + l;
+                        xs -= before;
+                    } else {
+                        xs -= shfl_idx_w(incl, 31);
+                    }
                 }
-                if (cur == NONE) sh_err = 1;
-                path[d] = z;
+                if (cur == NONE) err = true;
+                if (lane == 0) path[d] = z;
                 uint32_t lvl = d;
-                while (!sh_err && lvl > 1) {
+                while (!err && lvl > 1) {
                     const uint32_t tv = g.slot_t[cur];
                     const uint32_t* Fp = F + lev[lvl - 1];
                     const uint32_t Lp = lev[lvl] - lev[lvl - 1];
-                    cum = 0;
+                    const uint32_t e_lo = g.slot_in[cur], e_hi = g.slot_in[cur + 1];
                     uint32_t nxt = NONE;
-                    for (uint32_t e = g.slot_in[cur]; e < g.slot_in[cur + 1] && nxt == NONE; ++e) {
-                        const uint32_t w = g.in_u[e];
-                        const uint32_t ws0 = g.slot_ptr[w], ws1 = g.slot_ptr[w + 1];
-                        for (uint32_t p = lower_bound_u32(Fp, 0, Lp, ws0); p < Lp; ++p) {
-                            const uint32_t a2 = Fp[p];
-                            if (a2 >= ws1 || g.slot_t[a2] >= tv) break;
-                            const Sig wt = sig[a2];
-                            if (xs < cum + wt) { xs -= cum; nxt = a2; break; }
-                            cum += wt;
+                    for (uint32_t e0 = e_lo; e0 < e_hi && nxt == NONE; e0 += 32) {
+                        const uint32_t e = e0 + lane;
+                        Sig wt = 0;
+                        uint32_t p0 = 0, ws1 = 0;
+                        if (e < e_hi) {
+                            const uint32_t w = g.in_u[e];
+                            ws1 = g.slot_ptr[w + 1];
+                            p0 = lower_bound_u32(Fp, 0, Lp, g.slot_ptr[w]);
+                            for (uint32_t p = p0; p < Lp; ++p) {
+                                const uint32_t a2 = Fp[p];
+                                if (a2 >= ws1 || g.slot_t[a2] >= tv) break;
+                                wt += sig[a2];
+                            }
                         }
+                        const Sig incl = warp_inclusive_sum(wt);
+                        const unsigned msk = __ballot_sync(FULL, xs < incl);
+                        if (msk) {
+                            const int l = __ffs(msk) - 1;
+                            uint32_t pick = NONE;
+                            Sig xr = xs - (incl - wt);
+                            if (lane == l) {
+                                for (uint32_t p = p0; p < Lp; ++p) {
+                                    const uint32_t a2 = Fp[p];
+                                    if (a2 >= ws1 || g.slot_t[a2] >= tv) break;
+                                    const Sig w2 = sig[a2];
+                                    if (xr < w2) { pick = a2; break; }
+                                    xr -= w2;
+                                }
+                            }
+                            nxt = __shfl_sync(FULL, pick, l);
+                            xs = shfl_idx_w(xr, l);
+                            if (nxt == NONE) err = true;
+                            break;
+                        }
+                        xs -= shfl_idx_w(incl, 31);
                     }
-                    if (nxt == NONE) { sh_err = 1; break; }
+                    if (nxt == NONE) { err = true; break; }
                     cur = nxt;
                     lvl -= 1;
-                    path[lvl] = g.slot_v[cur];
+                    if (lane == 0) path[lvl] = g.slot_v[cur];
                 }
-                path[0] = s;
-                if (sh_err) set_status(job.status, ST_CHECK);
-                sh_d = d;
-                sh_len = d + 1;
-                sh_sigma = SigOps<WIDE>::wide(tot);
-                if (!sh_err) {
+                if (lane == 0) {
+                    path[0] = s;
+                    if (err) { sh_err = 1; set_status(job.status, ST_CHECK); }
+                    sh_d = d;
+                    sh_len = d + 1;
+                    sh_sigma = SigOps<WIDE>::wide(tot);
                     uint32_t w4[4];
                     philox_block(job.seed, i, DOM_RADE, 0, w4);
                     sh_rade[0] = w4[0]; sh_rade[1] = w4[1]; sh_rade[2] = w4[2]; sh_rade[3] = w4[3];

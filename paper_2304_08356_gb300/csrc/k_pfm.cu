@@ -22,7 +22,7 @@
 namespace mantra {
 
 constexpr int PFM_NT = 128;
-constexpr int PFM_ILP = 8;
+constexpr int PFM_G = 16;      // edges per prefetch group
 
 template <bool WIDE>
 __global__ void __launch_bounds__(PFM_NT) k_pfm(const DevGraph g, const Job job, const PfmWs ws) {
@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const DevGraph g, const Job job,
     uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path) + (size_t)lane * (n + 2);
     const bool stats = job.stats != 0;
     u64 my_escan = 0, my_eadd = 0;
+    __shared__ uint4 stage_all[PFM_NT];      // one 32-edge chunk per warp
 
     for (;;) {
         uint64_t q0 = 0;
@@ -87,67 +88,114 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const DevGraph g, const Job job,
         }
         uint32_t fz = NONE;        // fa'(z) once reached
         uint32_t ovf = 0;
+        uint4* stage = stage_all + (threadIdx.x >> 5) * 32;
         for (uint32_t base = e_lo; base < e_hi; base += 32) {
             const uint32_t e = base + lane;
-            uint32_t eu = 0, ev = 0, et = NONE;
-            if (e < e_hi) { eu = g.st_u[e]; ev = g.st_v[e]; et = g.st_t[e]; }
+            uint4 me = make_uint4(0u, 0u, NONE, 0u);
+            if (e < e_hi) { me.x = g.st_u[e]; me.y = g.st_v[e]; me.z = g.st_t[e]; }
+            __syncwarp();
+            stage[lane] = me;
+            __syncwarp();
             // lanes still scanning at this chunk's first time
-            const uint32_t t0 = __shfl_sync(FULL, et, 0);
+            const uint32_t t0 = stage[0].z;
             const bool running = live && t0 <= te && t0 < fz;
             if (!__any_sync(FULL, running)) break;
-            const uint32_t kmax = min(32u, e_hi - base);
-            for (uint32_t k0 = 0; k0 < kmax; k0 += PFM_ILP) {
-                uint32_t U[PFM_ILP], Vv[PFM_ILP], T[PFM_ILP], FU[PFM_ILP], FV[PFM_ILP];
-                bool on[PFM_ILP];
+#pragma unroll 1
+            for (int h = 0; h < 32; h += PFM_G) {
+                // (1) arrival-time rows of both endpoints for PFM_G edges
+                uint32_t FU[PFM_G], FV[PFM_G];
+                unsigned onm = 0;
+                const uint32_t hi_t = min(te, fz - 1u);      // fz = NONE: te
 #pragma unroll
-                for (int j = 0; j < PFM_ILP; ++j) {
-                    U[j] = __shfl_sync(FULL, eu, (k0 + j) & 31);
-                    Vv[j] = __shfl_sync(FULL, ev, (k0 + j) & 31);
-                    T[j] = __shfl_sync(FULL, et, (k0 + j) & 31);
-                    on[j] = (k0 + j < kmax) && live && T[j] >= ts && T[j] <= te && T[j] < fz && Vv[j] != s;
-                    FU[j] = on[j] ? fa[(size_t)U[j] * 32] : NONE;
-                    FV[j] = on[j] ? fa[(size_t)Vv[j] * 32] : NONE;
+                for (int j = 0; j < PFM_G; ++j) {
+                    const uint4 E = stage[h + j];
+                    const bool on = live && E.z >= ts && E.z <= hi_t && E.y != s;
+                    FU[j] = on ? fa[(size_t)E.x * 32] : NONE;
+                    FV[j] = on ? fa[(size_t)E.y * 32] : NONE;
+                    onm |= on ? (1u << j) : 0u;
                 }
-                uint32_t newf[PFM_ILP];
-                bool upd[PFM_ILP];
+                my_escan += __popc(onm);
+                // (2) arrival decisions in stream order; this lane's own updates
+                //     inside the group are forwarded from registers
+                unsigned cm = 0, fm = 0;
+                uint32_t uv[4], uf[4];
+                int nu = 0;
 #pragma unroll
-                for (int j = 0; j < PFM_ILP; ++j) {
+                for (int j = 0; j < PFM_G; ++j) {
+                    if (!((onm >> j) & 1u)) continue;
+                    const uint4 E = stage[h + j];
                     uint32_t fu = FU[j], fv = FV[j];
-#pragma unroll
-                    for (int k = 0; k < j; ++k) {          // this lane's own earlier updates in the group
-                        if (upd[k] && Vv[k] == U[j]) fu = newf[k];
-                        if (upd[k] && Vv[k] == Vv[j]) fv = newf[k];
-                    }
-                    upd[j] = false;
-                    newf[j] = 0;
-                    const uint32_t t = T[j];
-                    // fz may have been set by an earlier edge of this group
-                    if (on[j] && t < fz && fu <= t) {
-                        const uint32_t u = U[j], v = Vv[j];
-                        if (fv == NONE) {
-                            fa[(size_t)v * 32] = t + 1u;
-                            sig[(size_t)v * 32] = sig[(size_t)u * 32];
-                            if (stats) hop[(size_t)v * 32] = hop[(size_t)u * 32] + 1u;
-                            upd[j] = true;
-                            newf[j] = t + 1u;
-                            if (v == z) fz = t + 1u;
-                            ++my_eadd;
-                        } else if (fv == t + 1u) {
-                            Sig nv;
-                            if (!SigOps<WIDE>::add(sig[(size_t)v * 32], sig[(size_t)u * 32], &nv) && !stats) ovf = 1;
-                            sig[(size_t)v * 32] = nv;
-                            if (stats) {
-                                const uint32_t hu = hop[(size_t)u * 32] + 1u;
-                                if (hu < hop[(size_t)v * 32]) hop[(size_t)v * 32] = hu;
-                            }
-                            ++my_eadd;
+                    if (nu > 4) { fu = fa[(size_t)E.x * 32]; fv = fa[(size_t)E.y * 32]; }
+                    else {
+                        for (int q = 0; q < nu; ++q) {
+                            if (uv[q] == E.x) fu = uf[q];
+                            if (uv[q] == E.y) fv = uf[q];
                         }
                     }
-                    my_escan += on[j] ? 1 : 0;
+                    if (E.z < fz && fu <= E.z) {
+                        if (fv == NONE) {
+                            fa[(size_t)E.y * 32] = E.z + 1u;
+                            if (nu < 4) { uv[nu] = E.y; uf[nu] = E.z + 1u; }
+                            ++nu;
+                            fm |= 1u << j;
+                            cm |= 1u << j;
+                            if (E.y == z) fz = E.z + 1u;
+                        } else if (fv == E.z + 1u) {
+                            cm |= 1u << j;
+                        }
+                    }
+                }
+                // (3) path counts of the contributing edges, in stream order, up to
+                //     4 prefetched at a time; forwarding of this lane's new counts
+                my_eadd += __popc(cm);
+                while (cm) {
+                    int jj[4];
+                    Sig SU[4], SV[4];
+                    int k = 0;
+                    unsigned rest = cm;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        jj[q] = -1;
+                        if (rest) {
+                            const int j = __ffs(rest) - 1;
+                            rest &= rest - 1;
+                            jj[q] = j;
+                            const uint4 E = stage[h + j];
+                            SU[q] = sig[(size_t)E.x * 32];
+                            SV[q] = ((fm >> j) & 1u) ? (Sig)0 : sig[(size_t)E.y * 32];
+                            k = q + 1;
+                        }
+                    }
+                    cm = rest;
+                    uint32_t wv[4];
+                    Sig wsig[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (q >= k) break;
+                        const uint4 E = stage[h + jj[q]];
+                        Sig su = SU[q], sv = SV[q];
+#pragma unroll
+                        for (int r = 0; r < q; ++r) {
+                            if (wv[r] == E.x) su = wsig[r];
+                            if (wv[r] == E.y) sv = wsig[r];
+                        }
+                        Sig nv;
+                        if (!SigOps<WIDE>::add(sv, su, &nv) && !stats) ovf = 1;
+                        sig[(size_t)E.y * 32] = nv;
+                        wv[q] = E.y;
+                        wsig[q] = nv;
+                        if (stats) {
+                            const uint32_t hu = hop[(size_t)E.x * 32] + 1u;
+                            if ((fm >> jj[q]) & 1u) hop[(size_t)E.y * 32] = hu;
+                            else if (hu < hop[(size_t)E.y * 32]) hop[(size_t)E.y * 32] = hu;
+                        }
+                    }
                 }
             }
+            if (__any_sync(FULL, ovf)) break;
         }
         __syncwarp();
+        ovf = __any_sync(FULL, ovf) ? 1u : 0u;
 
         if (stats) {
             uint32_t dloc = 0;

@@ -199,6 +199,114 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
     return before + x - v;
 }
 
+// Warp shuffles of 64- and 128-bit path counts.
+__device__ __forceinline__ u64 shfl_up_w(u64 x, int o) { return __shfl_up_sync(0xFFFFFFFFu, x, o); }
+__device__ __forceinline__ u128 shfl_up_w(u128 x, int o) {
+    const u64 lo = __shfl_up_sync(0xFFFFFFFFu, (u64)x, o), hi = __shfl_up_sync(0xFFFFFFFFu, (u64)(x >> 64), o);
+    return ((u128)hi << 64) | lo;
+}
+__device__ __forceinline__ u64 shfl_idx_w(u64 x, int l) { return __shfl_sync(0xFFFFFFFFu, x, l); }
+__device__ __forceinline__ u128 shfl_idx_w(u128 x, int l) {
+    const u64 lo = __shfl_sync(0xFFFFFFFFu, (u64)x, l), hi = __shfl_sync(0xFFFFFFFFu, (u64)(x >> 64), l);
+    return ((u128)hi << 64) | lo;
+}
+__device__ __forceinline__ u64 shfl_xor_w(u64 x, int o) { return __shfl_xor_sync(0xFFFFFFFFu, x, o); }
+__device__ __forceinline__ u128 shfl_xor_w(u128 x, int o) {
+    const u64 lo = __shfl_xor_sync(0xFFFFFFFFu, (u64)x, o), hi = __shfl_xor_sync(0xFFFFFFFFu, (u64)(x >> 64), o);
+    return ((u128)hi << 64) | lo;
+}
+
+// Inclusive warp scan of unsigned path counts (callers guarantee no wrap).
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_sum(T x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = shfl_up_w(x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Block-wide exclusive scan of one uint64 per thread (same contract as the
+// 32-bit scan; `scratch` holds 32 uint64 of shared memory).
+template <int NT>
+__device__ __forceinline__ u64 block_exclusive_scan64(u64 v, u64* total, u64* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    u64 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) scratch[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        u64 w = (lane < NT / 32) ? scratch[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u64 y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= o) w += y;
+        }
+        scratch[lane] = w;
+    }
+    __syncthreads();
+    const u64 before = wid ? scratch[wid - 1] : 0ull;
+    *total = scratch[NT / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// Block-wide inclusive segmented scan: f = 1 starts a new segment at this
+// thread; the running sum continues across calls through *carry (the value
+// entering thread 0 when its f = 0).  Any wrapped addition sets *ovf (exact:
+// every partial sum is a sum inside one segment).  wx / wf: 32 entries of
+// shared memory.  Contains barriers.
+template <int NT, typename T>
+__device__ __forceinline__ T block_segmented_scan(T x, uint32_t f, T* wx, uint32_t* wf, T* carry, uint32_t* ovf) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    bool bad = false;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = shfl_up_w(x, o);
+        const uint32_t g = __shfl_up_sync(0xFFFFFFFFu, f, o);
+        if (lane >= o) {
+            if (!f) { const T sm = x + y; bad |= sm < x; x = sm; }
+            f |= g;
+        }
+    }
+    if (lane == 31) { wx[wid] = x; wf[wid] = f; }
+    __syncthreads();
+    if (wid == 0) {
+        T X = (lane < NT / 32) ? wx[lane] : (T)0;
+        uint32_t F = (lane < NT / 32) ? wf[lane] : 1u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = shfl_up_w(X, o);
+            const uint32_t g = __shfl_up_sync(0xFFFFFFFFu, F, o);
+            if (lane >= o) {
+                if (!F) { const T sm = X + y; bad |= sm < X; X = sm; }
+                F |= g;
+            }
+        }
+        const T Xp = shfl_up_w(X, 1);
+        const uint32_t Fp = __shfl_up_sync(0xFFFFFFFFu, F, 1);
+        const T c = *carry;
+        T P = c;
+        if (lane > 0) {
+            if (Fp) P = Xp;
+            else { P = c + Xp; bad |= P < c; }
+        }
+        if (lane < NT / 32) wx[lane] = P;
+    }
+    __syncthreads();
+    if (!f) { const T sm = x + wx[wid]; bad |= sm < x; x = sm; }
+    if (bad) *ovf = 1u;
+    __syncthreads();
+    if (threadIdx.x == NT - 1) *carry = x;
+    return x;
+}
+
 // First index in [lo, hi) with a[idx] > key (a ascending).
 __device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t key) {
     while (lo < hi) {
