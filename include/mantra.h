@@ -142,6 +142,32 @@ int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, ui
                         uint64_t i0, uint64_t count, uint32_t* s_out, uint32_t* z_out, uint64_t* sigma_out,
                         uint32_t* len_out, uint32_t* nodes_out, uint32_t cap);
 
+/* Allocation-free variant of mantra_sample_paths for MANTRA_SH and
+ * MANTRA_SFM.  The paper has no counterpart.  It is for callers that cannot
+ * call cudaMalloc once they are running: a process whose device memory is
+ * fixed after start-up, or code that must not pay an allocator's latency or
+ * risk its failure between requests.  The call allocates nothing: the search
+ * scratch and launch counters live in one fixed 64 MiB __device__ array that
+ * every GPU loading the library holds until exit.
+ *   g: a graph loaded earlier with mantra_graph_load; s_dev, z_dev, len_dev:
+ *   count uint32 DEVICE buffers; sigma_dev: 2*count uint64 (low, high words);
+ *   nodes_dev: count*cap uint32 (may be NULL when cap = 0); stream: a
+ *   cudaStream_t or NULL (legacy default stream).  Outputs are those of
+ *   mantra_sample_paths, indexed by (sample index - i0).
+ * The first call made on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array and leaves its contents behind; each call
+ * clears what must start at zero.  Calls that overlap on the GPU (two streams,
+ * two threads, two graphs) race on the array: serialise them.
+ * Returns MANTRA_E_INVAL for pfm, for a graph whose search scratch does not
+ * fit the fixed array (roughly 40 bytes per arrival slot plus 28 per node
+ * for one CTA, plus 8 bytes per requested sample), and MANTRA_E_OVERFLOW
+ * when a path count exceeds 64 bits (this variant has no 128-bit re-run). */
+int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt, uint64_t seed, uint32_t dom_pair,
+                                uint32_t dom_path, uint64_t i0, uint64_t count, uint32_t* s_dev, uint32_t* z_dev,
+                                uint64_t* sigma_dev, uint32_t* len_dev, uint32_t* nodes_dev, uint32_t cap,
+                                void* stream);
+
 const char* mantra_strerror(int code);
 
 #ifdef __cplusplus

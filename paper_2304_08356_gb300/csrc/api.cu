@@ -369,6 +369,18 @@ int init_graph_device(mantra_graph* G) {
 
 }  // namespace
 
+namespace mantra {
+
+// Read-only view of a loaded graph for the library's other translation units.
+const DevGraph* graph_view(const mantra_graph* g, uint32_t* n, uint32_t* A, int* num_sms, size_t* smem_optin,
+                           std::mutex** mu) {
+    mantra_graph* G = const_cast<mantra_graph*>(g);
+    *n = G->n; *A = G->A; *num_sms = G->num_sms; *smem_optin = G->smem_optin; *mu = &G->mu;
+    return &G->dg;
+}
+
+}  // namespace mantra
+
 extern "C" {
 
 const char* mantra_strerror(int code) {

@@ -54,7 +54,7 @@ class TStats(C.Structure):
 
 
 EXPORTS = ["mantra_graph_load", "mantra_graph_info", "mantra_graph_free", "mantra_estimate",
-           "mantra_temporal_stats", "mantra_sample_paths", "mantra_strerror"]
+           "mantra_temporal_stats", "mantra_sample_paths", "mantra_sample_paths_noalloc", "mantra_strerror"]
 
 _lib = None
 
@@ -78,6 +78,9 @@ def lib():
                                         C.POINTER(TStats), u64p, C.c_uint32]
     L.mantra_sample_paths.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
                                       C.c_uint64, u32p, u32p, u64p, u32p, u32p, C.c_uint32]
+    L.mantra_sample_paths_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
+                                              C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_uint32, C.c_void_p]
     L.mantra_strerror.restype = C.c_char_p
     L.mantra_strerror.argtypes = [C.c_int]
     _lib = L
