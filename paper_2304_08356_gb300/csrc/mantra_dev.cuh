@@ -48,6 +48,8 @@ struct DevGraph {
     const uint32_t* st_t;
     const uint32_t* tmax_in;
     const uint32_t* tmin_out;
+    uint32_t cbound;  // sum over v of the largest in-degree of v's slots: bounds the
+                      // path-count additions of one prefix-foremost search
 };
 
 // One launch over a range (or list) of sample indices.
@@ -339,7 +341,8 @@ struct BfsWs {
 struct PfmWs {
     char* base;          // warp w uses base + w * stride
     size_t stride;
-    size_t o_fa, o_sig, o_hop, o_path;
+    size_t o_fa, o_sig, o_hop, o_path, o_list;
+    uint32_t list_cap;   // contributing-edge list entries per lane (fast pfm kernel)
 };
 
 size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws);
@@ -347,9 +350,10 @@ size_t bfs_smem_bytes(uint32_t A);
 cudaError_t bfs_configure(size_t smem);
 cudaError_t launch_bfs(const DevGraph& g, const Job& job, const BfsWs& ws, int grid, size_t smem, bool wide,
                        cudaStream_t st);
-size_t pfm_region_bytes(uint32_t n, PfmWs* ws);
+size_t pfm_region_bytes(uint32_t n, uint32_t list_cap, PfmWs* ws);
 int pfm_threads();
 cudaError_t launch_pfm(const DevGraph& g, const Job& job, const PfmWs& ws, int grid, bool wide, cudaStream_t st);
+cudaError_t launch_pfm_fast(const DevGraph& g, const Job& job, const PfmWs& ws, int grid, cudaStream_t st);
 cudaError_t launch_round_reduce(const int* S, const u64* hits, uint32_t n, uint32_t c, long long* rowmax, u64* hmax,
                                 cudaStream_t st);
 cudaError_t launch_normalise(const u64* hits, uint32_t n, uint64_t r, double* est, cudaStream_t st);
