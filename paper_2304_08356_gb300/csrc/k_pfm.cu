@@ -303,11 +303,14 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const DevGraph g, const Job job,
 // is handed to the in-order kernel above (overflow list).
 // ---------------------------------------------------------------------------
 constexpr uint32_t LIST_FIRST = 0x80000000u;
+constexpr size_t PFM_BUF_BYTES = 64 * 32 * 4;                       // one chunk's rows
+constexpr size_t PFM_WARP_SMEM = 2 * PFM_BUF_BYTES + 512 + 128;    // two buffers, edges, barriers
+constexpr size_t PFM_FAST_SMEM = (PFM_NT / 32) * PFM_WARP_SMEM;
 
 __global__ void __launch_bounds__(PFM_NT) k_pfm_fast(const DevGraph g, const Job job, const PfmWs ws) {
     typedef u64 Sig;
     const uint32_t FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t gw = ((uint64_t)blockIdx.x * PFM_NT + threadIdx.x) >> 5;
     const uint32_t n = g.n;
     char* region = ws.base + gw * ws.stride;
@@ -316,10 +319,20 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm_fast(const DevGraph g, const Job
     uint32_t* hop = reinterpret_cast<uint32_t*>(region + ws.o_hop) + lane;
     uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path) + (size_t)lane * (n + 2);
     uint32_t* list = reinterpret_cast<uint32_t*>(region + ws.o_list) + lane;      // list[p * 32]
+    const uint32_t* fa_rows = reinterpret_cast<const uint32_t*>(region + ws.o_fa);
     const uint32_t cap = ws.list_cap;
     const bool stats = job.stats != 0;
     u64 my_escan = 0, my_eadd = 0;
-    __shared__ uint4 stage_all[PFM_NT];
+
+    // per warp: two row buffers [64 rows][32 lanes] (rows 0..31: fa'(u_j), 32..63: fa'(v_j)),
+    // the chunk's edges and one mbarrier per buffer
+    extern __shared__ __align__(128) unsigned char pfm_smem[];
+    uint32_t* rowbuf = reinterpret_cast<uint32_t*>(pfm_smem + (size_t)wib * PFM_WARP_SMEM);
+    uint4* stage = reinterpret_cast<uint4*>(pfm_smem + (size_t)wib * PFM_WARP_SMEM + 2 * PFM_BUF_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(pfm_smem + (size_t)wib * PFM_WARP_SMEM + 2 * PFM_BUF_BYTES + 512);
+    if (lane == 0) { mbar_init(bars, 32); mbar_init(bars + 1, 32); fence_mbar_init(); }
+    __syncwarp();
+    uint32_t phase = 0;      // bit b: parity of buffer b's next completion
 
     for (;;) {
         uint64_t q0 = 0;
@@ -349,6 +362,7 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm_fast(const DevGraph g, const Job
 
         for (uint32_t v = 0; v < n; ++v) fa[(size_t)v * 32] = NONE;
         if (live) fa[(size_t)s * 32] = 0u;
+        fence_proxy_async();          // these stores before the first row copies
         __syncwarp();
 
         uint32_t wlo = ts, whi = te;
@@ -366,50 +380,93 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm_fast(const DevGraph g, const Job
             e_lo = __shfl_sync(FULL, e_lo, 0);
             e_hi = __shfl_sync(FULL, e_hi, 0);
         }
+        const uint32_t nchunks = (e_hi - e_lo + 31) / 32;
         uint32_t fz = NONE;
         uint32_t nlist = 0;
         bool lovf = false;
-        uint4* stage = stage_all + (threadIdx.x >> 5) * 32;
-        for (uint32_t base = e_lo; base < e_hi; base += 32) {
-            const uint32_t e = base + lane;
-            uint4 me = make_uint4(0u, 0u, NONE, 0u);
-            if (e < e_hi) { me.x = g.st_u[e]; me.y = g.st_v[e]; me.z = g.st_t[e]; }
+        bool timed_out = false;
+        uint32_t pv[4], pf[4];     // this lane's first arrivals of the previous chunk (patch list)
+        int np = 0;
+        // edge of lane l in chunk c: e_lo + 32 c + l (sentinel row 0, time NONE past e_hi)
+        auto load_edge = [&](uint32_t e) {
+            uint4 r = make_uint4(0u, 0u, NONE, 0u);
+            if (e < e_hi) { r.x = g.st_u[e]; r.y = g.st_v[e]; r.z = g.st_t[e]; }
+            return r;
+        };
+        // rows of both endpoints of this lane's edge into buffer b
+        auto issue = [&](int b, const uint4& me) {
+            uint32_t* dst = rowbuf + (size_t)b * (PFM_BUF_BYTES / 4);
+            mbar_arrive_expect_tx(bars + b, 256u);
+            bulk_copy_g2s(dst + lane * 32, fa_rows + (size_t)me.x * 32, 128u, bars + b);
+            bulk_copy_g2s(dst + (32 + lane) * 32, fa_rows + (size_t)me.y * 32, 128u, bars + b);
+        };
+        uint4 cur = make_uint4(0u, 0u, NONE, 0u);
+        if (nchunks > 0) {
+            cur = load_edge(e_lo + lane);
+            issue(0, cur);
+        }
+        for (uint32_t c = 0; c < nchunks; ++c) {
+            const uint32_t base = e_lo + c * 32;
+            const int b = (int)(c & 1u);
             __syncwarp();
-            stage[lane] = me;
+            stage[lane] = cur;
             __syncwarp();
+            const bool landed = mbar_wait_bounded(bars + b, (phase >> b) & 1u, 1u << 24);
+            if (!__all_sync(FULL, landed)) {
+                timed_out = true;
+                break;
+            }
+            phase ^= 1u << b;
             const uint32_t t0 = stage[0].z;
             const bool running = live && t0 <= te && t0 < fz;
             if (!__any_sync(FULL, running)) break;
+            uint4 nxt = make_uint4(0u, 0u, NONE, 0u);
+            if (c + 1 < nchunks) {
+                nxt = load_edge(base + 32 + lane);
+                issue(b ^ 1, nxt);
+            }
+            uint32_t* RU = rowbuf + (size_t)b * (PFM_BUF_BYTES / 4) + lane;        // RU[j * 32]: fa'(u_j)
+            uint32_t* RV = RU + 32 * 32;                                            // RV[j * 32]: fa'(v_j)
+            // rows were copied before the previous chunk's stores: patch them
+            if (np > 4) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const uint4 E = stage[j];
+                    RU[j * 32] = fa[(size_t)E.x * 32];
+                    RV[j * 32] = fa[(size_t)E.y * 32];
+                }
+            } else {
+                for (int qq = 0; qq < np; ++qq) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const uint4 E = stage[j];
+                        if (E.x == pv[qq]) RU[j * 32] = pf[qq];
+                        if (E.y == pv[qq]) RV[j * 32] = pf[qq];
+                    }
+                }
+            }
+            np = 0;
             // later edges of the chunk that touch this edge's head
             uint32_t coll = 0;
 #pragma unroll
             for (int o = 1; o < 32; ++o) {
-                const uint32_t uj = __shfl_down_sync(FULL, me.x, o);
-                const uint32_t vj = __shfl_down_sync(FULL, me.y, o);
-                if (lane + o < 32 && (uj == me.y || vj == me.y)) coll |= 1u << (lane + o);
+                const uint32_t uj = __shfl_down_sync(FULL, cur.x, o);
+                const uint32_t vj = __shfl_down_sync(FULL, cur.y, o);
+                if (lane + o < 32 && (uj == cur.y || vj == cur.y)) coll |= 1u << (lane + o);
             }
-            // arrival rows of all 32 edges
             const uint32_t hi_t = min(te, fz - 1u);
-            uint32_t FU[32], FV[32];
-            unsigned onm = 0;
+            unsigned onm = 0, fm = 0, am = 0;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const uint4 E = stage[j];
                 const bool on = live && E.z >= ts && E.z <= hi_t && E.y != s;
-                FU[j] = on ? fa[(size_t)E.x * 32] : NONE;
-                FV[j] = on ? fa[(size_t)E.y * 32] : NONE;
+                const uint32_t fu = RU[j * 32], fv = RV[j * 32];
+                const bool act = on && fu <= E.z;
                 onm |= on ? (1u << j) : 0u;
+                fm |= (act && fv == NONE) ? (1u << j) : 0u;
+                am |= (act && fv == E.z + 1u) ? (1u << j) : 0u;
             }
             my_escan += __popc(onm);
-            unsigned fm = 0, am = 0;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const uint32_t t = stage[j].z;
-                const bool act = ((onm >> j) & 1u) && FU[j] <= t;
-                fm |= (act && FV[j] == NONE) ? (1u << j) : 0u;
-                am |= (act && FV[j] == t + 1u) ? (1u << j) : 0u;
-            }
-            // conflicts: this lane's first arrivals that later edges depend on
             bool conflict = false;
             unsigned rem = fm;
             int rounds = __popc(fm);
@@ -430,6 +487,8 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm_fast(const DevGraph g, const Job
                     w &= w - 1;
                     const uint4 E = stage[k];
                     fa[(size_t)E.y * 32] = E.z + 1u;
+                    if (np < 4) { pv[np] = E.y; pf[np] = E.z + 1u; }
+                    ++np;
                 }
                 w = fm | am;
                 my_eadd += __popc(w);
@@ -442,26 +501,23 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm_fast(const DevGraph g, const Job
                 }
             } else {
                 // in-order pass of this lane over the chunk
-                uint32_t uv[4], uf[4];
-                int nu = 0;
-#pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     if (!((onm >> j) & 1u)) continue;
                     const uint4 E = stage[j];
-                    uint32_t fu = FU[j], fv = FV[j];
-                    if (nu > 4) { fu = fa[(size_t)E.x * 32]; fv = fa[(size_t)E.y * 32]; }
+                    uint32_t fu = RU[j * 32], fv = RV[j * 32];
+                    if (np > 4) { fu = fa[(size_t)E.x * 32]; fv = fa[(size_t)E.y * 32]; }
                     else {
-                        for (int qq = 0; qq < nu; ++qq) {
-                            if (uv[qq] == E.x) fu = uf[qq];
-                            if (uv[qq] == E.y) fv = uf[qq];
+                        for (int qq = 0; qq < np; ++qq) {
+                            if (pv[qq] == E.x) fu = pf[qq];
+                            if (pv[qq] == E.y) fv = pf[qq];
                         }
                     }
                     if (!(E.z < fz && fu <= E.z)) continue;
                     bool first = false;
                     if (fv == NONE) {
                         fa[(size_t)E.y * 32] = E.z + 1u;
-                        if (nu < 4) { uv[nu] = E.y; uf[nu] = E.z + 1u; }
-                        ++nu;
+                        if (np < 4) { pv[np] = E.y; pf[np] = E.z + 1u; }
+                        ++np;
                         first = true;
                         if (E.y == z) fz = E.z + 1u;
                     } else if (fv != E.z + 1u) {
@@ -473,8 +529,14 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm_fast(const DevGraph g, const Job
                     ++nlist;
                 }
             }
+            fence_proxy_async();      // this chunk's row stores and buffer reads before later copies
+            cur = nxt;
         }
         __syncwarp();
+        if (__any_sync(FULL, timed_out)) {
+            if (lane == 0) set_status(job.status, ST_TIMEOUT);
+            return;
+        }
 
         // path counts (and hops) from the lane's contribution list, in stream order
         uint32_t ovf = lovf ? 1u : 0u;
@@ -629,7 +691,14 @@ size_t pfm_region_bytes(uint32_t n, uint32_t list_cap, PfmWs* ws) {
 int pfm_threads() { return PFM_NT; }
 
 cudaError_t launch_pfm_fast(const DevGraph& g, const Job& job, const PfmWs& ws, int grid, cudaStream_t st) {
-    k_pfm_fast<<<grid, PFM_NT, 0, st>>>(g, job, ws);
+    static bool configured = false;
+    if (!configured) {
+        const cudaError_t e = cudaFuncSetAttribute(k_pfm_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)PFM_FAST_SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_pfm_fast<<<grid, PFM_NT, PFM_FAST_SMEM, st>>>(g, job, ws);
     return cudaGetLastError();
 }
 

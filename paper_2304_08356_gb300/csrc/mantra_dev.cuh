@@ -24,7 +24,7 @@ constexpr uint32_t RNG_MAX_ATTEMPTS = 1u << 16;
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 
 // Device status word values (same numbers as the public error codes).
-enum : int { ST_OK = 0, ST_OVERFLOW = 3, ST_CHECK = 6, ST_RNG = 7 };
+enum : int { ST_OK = 0, ST_OVERFLOW = 3, ST_TIMEOUT = 5, ST_CHECK = 6, ST_RNG = 7 };
 
 // Counter slots of a launch (u64 each).
 enum : int { C_WORK = 0, C_SUMINT = 1, C_ESCAN = 2, C_EADD = 3, C_SNEW = 4, C_NOVF = 5, C_FSEG = 6, C_NCOUNT = 8 };
@@ -328,6 +328,57 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t 
 }
 
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, ST_OK, code); }
+
+// ---------------------------------------------------------------------------
+// 1-D bulk copies (TMA) global -> shared with mbarrier completion.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    uint64_t state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state)
+                 : "r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    (void)state;
+}
+
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Polls for the phase with the given parity; gives up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it)
+        if (mbar_test_wait(bar, parity)) return true;
+    return false;
+}
+
+// bytes (multiple of 16) from 16-byte aligned global src to 16-byte aligned shared dst.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses (global and shared)
+// before later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
 // Per-CTA scratch of the sh/sfm search kernel (one region per CTA).
 struct BfsWs {
