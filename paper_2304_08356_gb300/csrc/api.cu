@@ -118,15 +118,10 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
     }
     for (uint32_t x = 0; x < n; ++x) out_ptr[x + 1] += out_ptr[x];
     std::vector<uint32_t> tmax_in(n, 0), tmin_out(n, 0);
-    uint64_t cbound = 0;
     for (uint32_t x = 0; x < n; ++x) {
         if (slot_ptr[x + 1] > slot_ptr[x]) tmax_in[x] = slot_t[slot_ptr[x + 1] - 1];
         if (out_ptr[x + 1] > out_ptr[x]) tmin_out[x] = out_t[out_ptr[x]];
-        uint32_t mx = 0;
-        for (uint32_t a = slot_ptr[x]; a < slot_ptr[x + 1]; ++a) mx = std::max(mx, slot_in[a + 1] - slot_in[a]);
-        cbound += mx;
     }
-    G->dg.cbound = (uint32_t)std::min<uint64_t>(cbound, 0xFFFFFFFFull);
 
     // one device allocation for the whole store
     struct Arr { const std::vector<uint32_t>* h; const uint32_t** d; };
@@ -185,14 +180,7 @@ int ensure_pfm_ws(mantra_graph* G, uint64_t count) {
     const uint64_t want = std::min<uint64_t>(std::max<uint64_t>((count + 31) / 32, 1), max_warps);
     const uint64_t have = (uint64_t)G->pfm_grid * wpb;
     if (G->pfm_mem && have >= want) return MANTRA_OK;
-    uint32_t list_cap = std::max<uint32_t>(32, std::min<uint32_t>(G->dg.cbound, 1u << 20));
-    // MANTRA_PFM_LIST_CAP lowers the per-sample contribution-list capacity (tests of the
-    // in-order fallback that takes samples whose list would overflow)
-    if (const char* env = std::getenv("MANTRA_PFM_LIST_CAP")) {
-        const long v = std::strtol(env, nullptr, 10);
-        if (v > 0 && (uint64_t)v < list_cap) list_cap = (uint32_t)v;
-    }
-    const size_t region = pfm_region_bytes(G->n, list_cap, &G->pws);
+    const size_t region = pfm_region_bytes(G->n, &G->pws);
     if (G->pfm_mem) { cudaFree(G->pfm_mem); G->pfm_mem = nullptr; }
     const size_t budget = free_device_bytes() / 3;
     uint64_t warps = std::min<uint64_t>(want, std::max<size_t>(budget / region, (size_t)wpb));
@@ -279,7 +267,7 @@ int run_samples(mantra_graph* G, Job job, cudaStream_t st, LaunchTotals* tot) {
     job.ctr = G->ctr; job.status = G->status; job.ovf_list = G->ovf;
     CU(cudaMemsetAsync(G->ctr, 0, 64 + 4, st));
     CU(cudaEventRecord(G->ev0, st));
-    if (pfm) CU(launch_pfm_fast(G->dg, job, G->pws, G->pfm_grid, st));
+    if (pfm) CU(launch_pfm(G->dg, job, G->pws, G->pfm_grid, false, st));
     else CU(launch_bfs(G->dg, job, G->bws, G->bfs_grid, G->bfs_smem, false, st));
     CU(cudaEventRecord(G->ev1, st));
     CU(cudaMemcpyAsync(G->host_ctr, G->ctr, 72, cudaMemcpyDeviceToHost, st));

@@ -48,8 +48,6 @@ struct DevGraph {
     const uint32_t* st_t;
     const uint32_t* tmax_in;
     const uint32_t* tmin_out;
-    uint32_t cbound;  // sum over v of the largest in-degree of v's slots: bounds the
-                      // path-count additions of one prefix-foremost search
 };
 
 // One launch over a range (or list) of sample indices.
@@ -329,56 +327,6 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t 
 
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, ST_OK, code); }
 
-// ---------------------------------------------------------------------------
-// 1-D bulk copies (TMA) global -> shared with mbarrier completion.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    uint64_t state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state)
-                 : "r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-    (void)state;
-}
-
-// Non-blocking test of the phase with the given parity.
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Polls for the phase with the given parity; gives up after `limit` polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
-    for (uint32_t it = 0; it < limit; ++it)
-        if (mbar_test_wait(bar, parity)) return true;
-    return false;
-}
-
-// bytes (multiple of 16) from 16-byte aligned global src to 16-byte aligned shared dst.
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-// Orders this thread's earlier generic-proxy accesses (global and shared)
-// before later async-proxy (bulk copy) accesses.
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
 // Per-CTA scratch of the sh/sfm search kernel (one region per CTA).
 struct BfsWs {
@@ -392,8 +340,7 @@ struct BfsWs {
 struct PfmWs {
     char* base;          // warp w uses base + w * stride
     size_t stride;
-    size_t o_fa, o_sig, o_hop, o_path, o_list;
-    uint32_t list_cap;   // contributing-edge list entries per lane (fast pfm kernel)
+    size_t o_fa, o_sig, o_hop, o_path;
 };
 
 size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws);
@@ -401,10 +348,9 @@ size_t bfs_smem_bytes(uint32_t A);
 cudaError_t bfs_configure(size_t smem);
 cudaError_t launch_bfs(const DevGraph& g, const Job& job, const BfsWs& ws, int grid, size_t smem, bool wide,
                        cudaStream_t st);
-size_t pfm_region_bytes(uint32_t n, uint32_t list_cap, PfmWs* ws);
+size_t pfm_region_bytes(uint32_t n, PfmWs* ws);
 int pfm_threads();
 cudaError_t launch_pfm(const DevGraph& g, const Job& job, const PfmWs& ws, int grid, bool wide, cudaStream_t st);
-cudaError_t launch_pfm_fast(const DevGraph& g, const Job& job, const PfmWs& ws, int grid, cudaStream_t st);
 cudaError_t launch_round_reduce(const int* S, const u64* hits, uint32_t n, uint32_t c, long long* rowmax, u64* hmax,
                                 cudaStream_t st);
 cudaError_t launch_normalise(const u64* hits, uint32_t n, uint64_t r, double* est, cudaStream_t st);
