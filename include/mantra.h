@@ -47,7 +47,8 @@ enum {
     MANTRA_E_CUDA = 4,     /* a CUDA runtime call failed */
     MANTRA_E_TIMEOUT = 5,  /* reserved: a bounded device wait gave up */
     MANTRA_E_CHECK = 6,    /* an internal consistency check failed on the device */
-    MANTRA_E_RNG = 7       /* 65536 consecutive rejections in a uniform draw */
+    MANTRA_E_RNG = 7,      /* 65536 consecutive rejections in a uniform draw */
+    MANTRA_PENDING = 8     /* serving: the request has not finished yet (not an error) */
 };
 
 /* Options of mantra_estimate (paper Algorithm 1).  Zero-initialise and set
@@ -121,6 +122,29 @@ void mantra_graph_free(mantra_graph* g);
  * c outside [1,128], r >= 2^31. */
 int mantra_estimate(const mantra_graph* g, mantra_opt opt, double eps, double delta, uint64_t seed,
                     const mantra_opts* opts, double* est_out, uint64_t* hits_out, mantra_info* info);
+
+/* One problem of mantra_estimate_batch: the arguments of mantra_estimate,
+ * plus the per-problem status written by the call. */
+typedef struct {
+    const mantra_graph* graph;
+    mantra_opt opt;
+    double eps, delta;
+    uint64_t seed;
+    const mantra_opts* opts;   /* NULL = defaults; stream is ignored */
+    double* est_out;           /* n entries (host, or device with opts->out_device) */
+    uint64_t* hits_out;        /* n entries or NULL */
+    mantra_info* info;         /* or NULL */
+    int status;                /* out: this problem's status code */
+} mantra_problem;
+
+/* Algorithm 1 for `count` problems at once (batched, on one device).  Every
+ * launch carries the pending samples of all unfinished problems: one
+ * persistent launch per search kernel over a device task table (graph,
+ * sample range), one reduction for all problems' rounds, one readback; each
+ * problem follows its own bootstrap, schedule and stopping rule, so each
+ * result is identical to mantra_estimate on the same arguments.  Returns the
+ * first failing problem's status (each problem's own status is in .status). */
+int mantra_estimate_batch(mantra_problem* probs, uint32_t count);
 
 /* Algorithm 2: r_s = r_override (or ceil(ln n / eps^2) when 0) full searches
  * from sources drawn uniformly from [0,n) (Philox domain 5).  reach_out (or

@@ -1,15 +1,20 @@
-// Host side of libmantra.so: the temporal-edge store, the Algorithm 1 driver
-// (bootstrap, sampling schedule, rounds, stopping test), Algorithm 2's host
-// formulas and the C ABI declared in include/mantra.h.
+// Host side of libmantra.so: the temporal-edge store, the per-device engine
+// that runs every search as a tick over a task table (one persistent launch
+// per kernel family, a multi-problem round reduction and one readback,
+// captured once as a CUDA graph and replayed), the Algorithm 1 state machine
+// (bootstrap, sampling schedule, rounds, stopping test) for one or many
+// problems at once, Algorithm 2's host formulas and the C ABI declared in
+// include/mantra.h.
 #include "mantra.h"
 #include "mantra_dev.cuh"
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
-#include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -21,20 +26,7 @@ struct mantra_graph {
     uint64_t self_loops = 0, duplicates = 0;
     DevGraph dg{};
     void* dmem = nullptr;
-    cudaStream_t stream = nullptr;
-    int device = 0, num_sms = 0;
-    size_t smem_optin = 0;
-    std::mutex mu;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // search workspaces (allocated on first use, kept with the graph)
-    char* bfs_mem = nullptr; BfsWs bws{}; int bfs_grid = 0; size_t bfs_smem = 0;
-    char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; size_t pfm_bytes = 0;
-    // run buffers
-    char* run_mem = nullptr; size_t run_bytes = 0; uint32_t run_c = 0; uint64_t run_cap = 0;
-    u64* hits = nullptr; int* S = nullptr; u64* ctr = nullptr; int* status = nullptr;
-    long long* rowmax = nullptr; u64* hmax = nullptr; uint64_t* ovf = nullptr; uint64_t* ovf2 = nullptr;
-    u64* cnt = nullptr; u64* dmax = nullptr; double* est = nullptr;
-    u64* host_ctr = nullptr;   // pinned mirror: counters, status, rowmax, hmax
+    int device = 0;
 };
 
 namespace {
@@ -50,7 +42,8 @@ struct HostEdge { uint32_t t, u, v; };
 // keeps a sparse n x |T| table, here every arrival appearance (v,t) gets a
 // dense slot id).
 // ---------------------------------------------------------------------------
-int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_t m, uint32_t n, mantra_graph* G) {
+int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_t m, uint32_t n, mantra_graph* G,
+                cudaStream_t st) {
     if (n == 0) {
         for (uint64_t e = 0; e < m; ++e) n = std::max(n, std::max(u[e], v[e]) + 1);
     }
@@ -136,14 +129,15 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
     size_t off = 0;
     for (auto& a : arrs) {
         char* p = (char*)G->dmem + off;
-        if (!a.h->empty()) CU(cudaMemcpyAsync(p, a.h->data(), a.h->size() * 4, cudaMemcpyHostToDevice, G->stream));
+        if (!a.h->empty()) CU(cudaMemcpyAsync(p, a.h->data(), a.h->size() * 4, cudaMemcpyHostToDevice, st));
         *a.d = (const uint32_t*)p;
         off += al256((a.h->size() + 1) * 4);
     }
-    CU(cudaStreamSynchronize(G->stream));
+    CU(cudaStreamSynchronize(st));
     G->dg.n = n; G->dg.A = A; G->dg.m = M;
     return MANTRA_OK;
 }
+
 
 size_t free_device_bytes() {
     size_t fr = 0, tot = 0;
@@ -151,88 +145,60 @@ size_t free_device_bytes() {
     return fr;
 }
 
-// Search workspaces: one region per CTA (sh/sfm) or per warp (pfm), sized to
-// at most `budget` bytes.  The sigma arrays and global bitmaps start zeroed;
-// every sample leaves them zeroed.
-int ensure_bfs_ws(mantra_graph* G, cudaStream_t st) {
-    if (G->bfs_mem) return MANTRA_OK;
-    const size_t smem = bfs_smem_bytes(G->A);
-    const bool in_smem = smem + 1024 <= G->smem_optin;
-    const size_t region = bfs_region_bytes(G->n, G->A, in_smem, &G->bws);
-    const size_t budget = free_device_bytes() / 3;
-    int grid = G->num_sms;
-    if ((size_t)grid * region > budget) grid = (int)std::max<size_t>(1, budget / region);
-    if (cudaMalloc(&G->bfs_mem, (size_t)grid * region) != cudaSuccess) { G->bfs_mem = nullptr; return MANTRA_E_NOMEM; }
-    CU(cudaMemsetAsync(G->bfs_mem, 0, (size_t)grid * region, st));
-    G->bws.base = G->bfs_mem;
-    G->bws.stride = region;
-    G->bfs_grid = grid;
-    G->bfs_smem = in_smem ? smem : 0;
-    CU(bfs_configure(G->bfs_smem));
-    return MANTRA_OK;
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// pfm: one region per warp (32 samples), grown to the largest launch seen, at
-// most one warp slot per 32 resident threads and at most a third of free memory.
-int ensure_pfm_ws(mantra_graph* G, uint64_t count) {
-    const int wpb = pfm_threads() / 32;
-    const uint64_t max_warps = (uint64_t)G->num_sms * 32;
-    const uint64_t want = std::min<uint64_t>(std::max<uint64_t>((count + 31) / 32, 1), max_warps);
-    const uint64_t have = (uint64_t)G->pfm_grid * wpb;
-    if (G->pfm_mem && have >= want) return MANTRA_OK;
-    const size_t region = pfm_region_bytes(G->n, &G->pws);
-    if (G->pfm_mem) { cudaFree(G->pfm_mem); G->pfm_mem = nullptr; }
-    const size_t budget = free_device_bytes() / 3;
-    uint64_t warps = std::min<uint64_t>(want, std::max<size_t>(budget / region, (size_t)wpb));
-    const int blocks = (int)((warps + wpb - 1) / wpb);
-    if (cudaMalloc(&G->pfm_mem, (size_t)blocks * wpb * region) != cudaSuccess) {
-        G->pfm_mem = nullptr; G->pfm_grid = 0; return MANTRA_E_NOMEM;
-    }
-    G->pws.base = G->pfm_mem;
-    G->pws.stride = region;
-    G->pfm_grid = blocks;
-    G->pfm_bytes = (size_t)blocks * wpb * region;
-    return MANTRA_OK;
-}
+// ---------------------------------------------------------------------------
+// Device memory pool: blocks kept by exact (256-rounded) size and reused by
+// later problems; at most kPoolCacheBytes stay cached.
+// ---------------------------------------------------------------------------
+constexpr size_t kPoolCacheBytes = (size_t)8 << 30;
 
-// Run buffers for n nodes, c trials and up to `cap` samples per launch.
-int ensure_run(mantra_graph* G, uint32_t c, uint64_t cap) {
-    if (G->run_mem && G->run_c >= c && G->run_cap >= cap) return MANTRA_OK;
-    if (G->run_mem) { cudaFree(G->run_mem); G->run_mem = nullptr; }
-    if (!G->host_ctr) {
-        if (cudaMallocHost(&G->host_ctr, 4096) != cudaSuccess) { G->host_ctr = nullptr; return MANTRA_E_NOMEM; }
+struct DevPool {
+    std::multimap<size_t, void*> free_blocks;
+    size_t cached = 0;
+    void* get(size_t bytes) {
+        bytes = al256(std::max<size_t>(bytes, 256));
+        auto it = free_blocks.find(bytes);
+        if (it != free_blocks.end()) {
+            void* p = it->second;
+            free_blocks.erase(it);
+            cached -= bytes;
+            return p;
+        }
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            release_all();
+            if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        }
+        return p;
     }
-    const uint32_t n = G->n;
-    c = std::max(c, 25u);
-    cap = std::max<uint64_t>(cap, 1024);
-    size_t o = 0;
-    const size_t o_hits = o; o = al256(o + (size_t)n * 8);
-    const size_t o_S = o;    o = al256(o + (size_t)c * n * 4);
-    const size_t o_ctr = o;  o = al256(o + 4096);   // counters + status + rowmax + hmax + dmax (mirrors host_ctr)
-    const size_t o_ovf = o;  o = al256(o + cap * 8);
-    const size_t o_ovf2 = o; o = al256(o + cap * 8);
-    const size_t o_cnt = o;  o = al256(o + ((size_t)n + 2) * 8);
-    const size_t o_est = o;  o = al256(o + (size_t)n * 8);
-    if (cudaMalloc(&G->run_mem, o) != cudaSuccess) { G->run_mem = nullptr; return MANTRA_E_NOMEM; }
-    char* b = G->run_mem;
-    G->hits = (u64*)(b + o_hits);
-    G->S = (int*)(b + o_S);
-    G->ctr = (u64*)(b + o_ctr);                     // [0, 8): counters
-    G->status = (int*)(b + o_ctr + 64);             // one int
-    G->hmax = (u64*)(b + o_ctr + 128);
-    G->dmax = (u64*)(b + o_ctr + 136);
-    G->rowmax = (long long*)(b + o_ctr + 256);      // up to 128 rows
-    G->ovf = (uint64_t*)(b + o_ovf);
-    G->ovf2 = (uint64_t*)(b + o_ovf2);
-    G->cnt = (u64*)(b + o_cnt);
-    G->est = (double*)(b + o_est);
-    G->run_bytes = o; G->run_c = c; G->run_cap = cap;
-    return MANTRA_OK;
-}
+    void put(void* p, size_t bytes) {
+        if (!p) return;
+        bytes = al256(std::max<size_t>(bytes, 256));
+        if (cached + bytes > kPoolCacheBytes) { cudaFree(p); return; }
+        free_blocks.emplace(bytes, p);
+        cached += bytes;
+    }
+    void release_all() {
+        for (auto& kv : free_blocks) cudaFree(kv.second);
+        free_blocks.clear();
+        cached = 0;
+    }
+};
+
+// Per-problem result slot of a tick: search counters, device status word,
+// and the round reduction's outputs.
+constexpr size_t SLOT_BYTES = 1152;
+constexpr size_t SLOT_STATUS = 64, SLOT_HMAX = 72, SLOT_ROWMAX = 80;
 
 struct LaunchTotals {
     uint64_t sum_int = 0, escan = 0, eadd = 0, snew = 0, fseg = 0, wide = 0, launches = 0;
     double kernel_ms = 0;
+    void add_counters(const u64* c) {
+        sum_int += c[C_SUMINT]; escan += c[C_ESCAN]; eadd += c[C_EADD]; snew += c[C_SNEW]; fseg += c[C_FSEG];
+    }
 };
 
 // Algorithmic bytes of search work (64-bit path counts):
@@ -245,87 +211,345 @@ uint64_t alg_bytes_of(bool pfm, uint64_t escan, uint64_t eadd, uint64_t snew, ui
     return 24ull * escan + 8ull * fseg + 12ull * snew;
 }
 
-void log_launch(bool pfm, bool wide, const Job& j, const u64* h, float ms) {
-    static const bool on = std::getenv("MANTRA_LOG_LAUNCHES") != nullptr;
-    if (!on) return;
-    std::fprintf(stderr, "mantra-launch kernel=%s%s samples=%llu escan=%llu eadd=%llu snew=%llu fseg=%llu "
-                 "alg_bytes=%llu ms=%.4f\n", pfm ? "k_pfm" : "k_bfs", wide ? "<wide>" : "",
-                 (unsigned long long)j.count, (unsigned long long)h[C_ESCAN], (unsigned long long)h[C_EADD],
-                 (unsigned long long)h[C_SNEW], (unsigned long long)h[C_FSEG],
-                 (unsigned long long)alg_bytes_of(pfm, h[C_ESCAN], h[C_EADD], h[C_SNEW], h[C_FSEG]), ms);
-}
+// One entry of a tick: a graph and a sample range, plus an optional round
+// reduction over its hits (and red_c rows of S).
+struct TickItem {
+    const mantra_graph* G = nullptr;
+    Job job{};
+    bool reduce = false;
+    uint32_t red_c = 0;
+};
 
-// One search launch over sample indices [i0, i0+count) (Algorithm 1's
-// Update step, or Algorithm 2's searches when job.stats), followed by a
-// 128-bit re-run of the samples whose 64-bit path counts overflowed.
-int run_samples(mantra_graph* G, Job job, cudaStream_t st, LaunchTotals* tot) {
-    if (job.count == 0) return MANTRA_OK;
-    const bool pfm = job.opt == MANTRA_PFM;
-    int rc = pfm ? ensure_pfm_ws(G, job.count) : ensure_bfs_ws(G, st);
-    if (rc != MANTRA_OK) return rc;
-    if (job.count > G->run_cap) return MANTRA_E_INVAL;
-    job.ctr = G->ctr; job.status = G->status; job.ovf_list = G->ovf;
-    CU(cudaMemsetAsync(G->ctr, 0, 64 + 4, st));
-    CU(cudaEventRecord(G->ev0, st));
-    if (pfm) CU(launch_pfm(G->dg, job, G->pws, G->pfm_grid, false, st));
-    else CU(launch_bfs(G->dg, job, G->bws, G->bfs_grid, G->bfs_smem, false, st));
-    CU(cudaEventRecord(G->ev1, st));
-    CU(cudaMemcpyAsync(G->host_ctr, G->ctr, 72, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    float ms = 0;
-    CU(cudaEventElapsedTime(&ms, G->ev0, G->ev1));
-    tot->kernel_ms += ms;
-    tot->launches += 1;
-    u64 h[9];
-    std::memcpy(h, G->host_ctr, 72);
-    log_launch(pfm, false, job, h, ms);
-    int status = (int)(h[8] & 0xFFFFFFFFu);
-    if (status != 0) return status;
-    tot->sum_int += h[C_SUMINT]; tot->escan += h[C_ESCAN]; tot->eadd += h[C_EADD]; tot->snew += h[C_SNEW];
-    tot->fseg += h[C_FSEG];
-    const uint64_t novf = h[C_NOVF];
-    if (novf) {
-        Job w = job;
-        w.idx_list = G->ovf;
-        w.count = novf;
-        w.ovf_list = G->ovf2;
-        CU(cudaMemsetAsync(G->ctr, 0, 64 + 4, st));
-        CU(cudaEventRecord(G->ev0, st));
-        if (pfm) CU(launch_pfm(G->dg, w, G->pws, G->pfm_grid, true, st));
-        else CU(launch_bfs(G->dg, w, G->bws, G->bfs_grid, G->bfs_smem, true, st));
-        CU(cudaEventRecord(G->ev1, st));
-        CU(cudaMemcpyAsync(G->host_ctr, G->ctr, 72, cudaMemcpyDeviceToHost, st));
-        CU(cudaStreamSynchronize(st));
-        CU(cudaEventElapsedTime(&ms, G->ev0, G->ev1));
-        tot->kernel_ms += ms;
-        tot->launches += 1;
-        std::memcpy(h, G->host_ctr, 72);
-        log_launch(pfm, true, w, h, ms);
-        status = (int)(h[8] & 0xFFFFFFFFu);
-        if (status != 0) return status;
-        tot->sum_int += h[C_SUMINT]; tot->escan += h[C_ESCAN]; tot->eadd += h[C_EADD]; tot->snew += h[C_SNEW];
-        tot->fseg += h[C_FSEG];
-        tot->wide += novf;
+struct TickOut {
+    std::vector<const char*> slot;   // host copy of each item's result slot
+    double bfs_ms = 0, pfm_ms = 0;
+    bool had_bfs = false, had_pfm = false;
+};
+
+// ---------------------------------------------------------------------------
+// Engine: one per device.  Owns the search workspaces (sized for the largest
+// graph seen), the task tables of a tick (pinned host copy + device copy) and
+// the captured tick graph.  Every public call locks `mu` for its duration.
+// ---------------------------------------------------------------------------
+struct Engine {
+    std::mutex mu;
+    int device = -1, num_sms = 0;
+    size_t smem_optin = 0;
+    cudaStream_t sa = nullptr, sb = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, e_b0 = nullptr, e_b1 = nullptr, e_p0 = nullptr, e_p1 = nullptr;
+    // search workspaces
+    char* bfs_mem = nullptr; BfsWs bws{}; int bfs_grid = 0; size_t bfs_smem = 0; uint32_t bfs_n = 0, bfs_A = 0;
+    char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; uint32_t pfm_n = 0; uint64_t pfm_warps = 0;
+    // tick tables
+    uint32_t cap = 0;
+    char* tab_h = nullptr; char* tab_d = nullptr; size_t tab_bytes = 0;
+    char* slot_h = nullptr; char* slot_d = nullptr;
+    size_t o_hdr = 0, o_work = 0, o_ub = 0, o_up = 0, o_tb = 0, o_tp = 0, o_ri = 0, o_rs = 0;
+    int red_grid = 0;
+    // captured tick
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_ok = false;
+    bool use_graph = true;
+    DevPool pool;
+
+    int init(int dev) {
+        device = dev;
+        CU(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+        int optin = 0;
+        CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        smem_optin = (size_t)optin;
+        CU(cudaStreamCreateWithFlags(&sa, cudaStreamNonBlocking));
+        CU(cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+        CU(cudaEventCreate(&e_b0)); CU(cudaEventCreate(&e_b1));
+        CU(cudaEventCreate(&e_p0)); CU(cudaEventCreate(&e_p1));
+        red_grid = num_sms * 4;
+        if (const char* env = std::getenv("MANTRA_NO_GRAPH")) use_graph = env[0] == '0';
+        return MANTRA_OK;
     }
+
+    void invalidate_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        graph_ok = false;
+    }
+
+    // Table block layout: header | 2 work counters | unit starts (bfs, pfm) |
+    // tasks (bfs, pfm) | reduction items | reduction row starts.
+    int ensure_tables(uint32_t need) {
+        if (tab_h && need <= cap) return MANTRA_OK;
+        uint32_t nc = std::max<uint32_t>(64, cap);
+        while (nc < need) nc *= 2;
+        if (tab_h) { cudaFreeHost(tab_h); tab_h = nullptr; }
+        if (tab_d) { cudaFree(tab_d); tab_d = nullptr; }
+        if (slot_h) { cudaFreeHost(slot_h); slot_h = nullptr; }
+        if (slot_d) { cudaFree(slot_d); slot_d = nullptr; }
+        size_t o = 0;
+        o_hdr = o;  o = al256(o + 16);
+        o_work = o; o = al256(o + 16);
+        o_ub = o;   o = al256(o + (size_t)(nc + 1) * 8);
+        o_up = o;   o = al256(o + (size_t)(nc + 1) * 8);
+        o_tb = o;   o = al256(o + (size_t)nc * sizeof(Task));
+        o_tp = o;   o = al256(o + (size_t)nc * sizeof(Task));
+        o_ri = o;   o = al256(o + (size_t)nc * sizeof(ReduceItem));
+        o_rs = o;   o = al256(o + (size_t)(nc + 1) * 4);
+        tab_bytes = o;
+        if (cudaMallocHost((void**)&tab_h, tab_bytes) != cudaSuccess) { tab_h = nullptr; return MANTRA_E_NOMEM; }
+        if (cudaMalloc((void**)&tab_d, tab_bytes) != cudaSuccess) { tab_d = nullptr; return MANTRA_E_NOMEM; }
+        if (cudaMallocHost((void**)&slot_h, (size_t)nc * SLOT_BYTES) != cudaSuccess) { slot_h = nullptr; return MANTRA_E_NOMEM; }
+        if (cudaMalloc((void**)&slot_d, (size_t)nc * SLOT_BYTES) != cudaSuccess) { slot_d = nullptr; return MANTRA_E_NOMEM; }
+        std::memset(tab_h, 0, tab_bytes);
+        cap = nc;
+        invalidate_graph();
+        return MANTRA_OK;
+    }
+
+    // sh/sfm: one region per CTA, one CTA per SM, at most a third of free memory.
+    int ensure_bfs(uint32_t n, uint32_t A) {
+        if (bfs_mem && n <= bfs_n && A <= bfs_A) return MANTRA_OK;
+        n = std::max(n, bfs_n);
+        A = std::max(A, bfs_A);
+        if (bfs_mem) { cudaStreamSynchronize(sa); cudaFree(bfs_mem); bfs_mem = nullptr; }
+        const size_t smem = bfs_smem_bytes(A);
+        const bool in_smem = smem + 2048 <= smem_optin;
+        const size_t region = bfs_region_bytes(n, A, in_smem, &bws);
+        const size_t budget = free_device_bytes() / 3;
+        int grid = num_sms;
+        if ((size_t)grid * region > budget) grid = (int)std::max<size_t>(1, budget / region);
+        if (cudaMalloc(&bfs_mem, (size_t)grid * region) != cudaSuccess) { bfs_mem = nullptr; return MANTRA_E_NOMEM; }
+        CU(cudaMemsetAsync(bfs_mem, 0, (size_t)grid * region, sa));
+        bws.base = bfs_mem;
+        bws.stride = region;
+        bfs_grid = grid;
+        bfs_smem = in_smem ? smem : 0;
+        bfs_n = n; bfs_A = A;
+        CU(bfs_configure(bfs_smem));
+        invalidate_graph();
+        return MANTRA_OK;
+    }
+
+    // pfm: one region per warp (32 samples), at most one warp per 32 resident
+    // threads of the GPU and at most a third of free memory.
+    int ensure_pfm(uint32_t n, uint64_t warps) {
+        const int wpb = pfm_threads() / 32;
+        warps = std::min<uint64_t>(std::max<uint64_t>(warps, (uint64_t)wpb), (uint64_t)num_sms * 32);
+        if (pfm_mem && n <= pfm_n && warps <= pfm_warps) return MANTRA_OK;
+        n = std::max(n, pfm_n);
+        warps = std::max<uint64_t>(warps, pfm_warps);
+        if (pfm_mem) { cudaStreamSynchronize(sb); cudaStreamSynchronize(sa); cudaFree(pfm_mem); pfm_mem = nullptr; }
+        const size_t region = pfm_region_bytes(n, &pws);
+        const size_t budget = free_device_bytes() / 3;
+        uint64_t w = std::min<uint64_t>(warps, std::max<size_t>(budget / region, (size_t)wpb));
+        const int blocks = (int)((w + wpb - 1) / wpb);
+        if (cudaMalloc(&pfm_mem, (size_t)blocks * wpb * region) != cudaSuccess) { pfm_mem = nullptr; return MANTRA_E_NOMEM; }
+        pws.base = pfm_mem;
+        pws.stride = region;
+        pfm_grid = blocks;
+        pfm_n = n;
+        pfm_warps = (uint64_t)blocks * wpb;
+        invalidate_graph();
+        return MANTRA_OK;
+    }
+
+    // The tick as stream work: tables up, slots cleared, both search
+    // families on two streams, the round reduction, slots down.
+    int enqueue(bool wide) {
+        CU(cudaMemcpyAsync(tab_d, tab_h, tab_bytes, cudaMemcpyHostToDevice, sa));
+        CU(cudaMemsetAsync(slot_d, 0, (size_t)cap * SLOT_BYTES, sa));
+        CU(cudaEventRecord(ev_fork, sa));
+        CU(cudaStreamWaitEvent(sb, ev_fork, 0));
+        const uint32_t* hdr = (const uint32_t*)(tab_d + o_hdr);
+        u64* work = (u64*)(tab_d + o_work);
+        if (bfs_mem) {
+            CU(cudaEventRecord(e_b0, sa));
+            CU(launch_bfs((const Task*)(tab_d + o_tb), (const uint64_t*)(tab_d + o_ub), hdr + 0, work + 0, bws,
+                          bfs_grid, bfs_smem, wide, sa));
+            CU(cudaEventRecord(e_b1, sa));
+        }
+        if (pfm_mem) {
+            CU(cudaEventRecord(e_p0, sb));
+            CU(launch_pfm((const Task*)(tab_d + o_tp), (const uint64_t*)(tab_d + o_up), hdr + 1, work + 1, pws,
+                          pfm_grid, wide, sb));
+            CU(cudaEventRecord(e_p1, sb));
+        }
+        CU(cudaEventRecord(ev_join, sb));
+        CU(cudaStreamWaitEvent(sa, ev_join, 0));
+        CU(launch_round_reduce((const ReduceItem*)(tab_d + o_ri), (const uint32_t*)(tab_d + o_rs), hdr + 2, red_grid,
+                               sa));
+        CU(cudaMemcpyAsync(slot_h, slot_d, (size_t)cap * SLOT_BYTES, cudaMemcpyDeviceToHost, sa));
+        return MANTRA_OK;
+    }
+
+    int launch_tick(bool wide) {
+        if (wide || !use_graph) return enqueue(wide);
+        if (!graph_ok) {
+            cudaGraph_t graph = nullptr;
+            CU(cudaStreamBeginCapture(sa, cudaStreamCaptureModeThreadLocal));
+            const int rc = enqueue(false);
+            const cudaError_t e = cudaStreamEndCapture(sa, &graph);
+            if (rc != MANTRA_OK || e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                use_graph = false;                    // capture unavailable: run the same work directly
+                return enqueue(false);
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) { gexec = nullptr; use_graph = false; return enqueue(false); }
+            graph_ok = true;
+        }
+        CU(cudaGraphLaunch(gexec, sa));
+        return MANTRA_OK;
+    }
+};
+
+std::mutex g_engines_mu;
+Engine* g_engines[64];
+
+int engine_for(int dev, Engine** out) {
+    if (dev < 0 || dev >= 64) return MANTRA_E_CUDA;
+    std::lock_guard<std::mutex> lock(g_engines_mu);
+    if (!g_engines[dev]) {
+        Engine* E = new (std::nothrow) Engine();
+        if (!E) return MANTRA_E_NOMEM;
+        int cur = 0;
+        CU(cudaGetDevice(&cur));
+        if (cur != dev) CU(cudaSetDevice(dev));
+        const int rc = E->init(dev);
+        if (cur != dev) cudaSetDevice(cur);
+        if (rc != MANTRA_OK) { delete E; return rc; }
+        g_engines[dev] = E;
+    }
+    *out = g_engines[dev];
     return MANTRA_OK;
 }
 
-// Reduction after a round: N_R = sum_j max_v S[j][v] and H = max_v hits[v].
-int round_reduce(mantra_graph* G, uint32_t c, bool with_S, cudaStream_t st, int64_t* NR, uint64_t* H) {
-    CU(launch_round_reduce(with_S ? G->S : nullptr, G->hits, G->n, with_S ? c : 0, G->rowmax, G->hmax, st));
-    CU(cudaMemcpyAsync((char*)G->host_ctr + 128, G->hmax, 8, cudaMemcpyDeviceToHost, st));
-    if (with_S) CU(cudaMemcpyAsync((char*)G->host_ctr + 256, G->rowmax, (size_t)c * 8, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    std::memcpy(H, (char*)G->host_ctr + 128, 8);
-    int64_t s = 0;
-    if (with_S) {
-        for (uint32_t j = 0; j < c; ++j) {
-            long long x;
-            std::memcpy(&x, (char*)G->host_ctr + 256 + 8 * j, 8);
-            s += x;
+void log_item(const TickItem& it, bool wide, const u64* c, double ms) {
+    static const bool on = std::getenv("MANTRA_LOG_LAUNCHES") != nullptr;
+    if (!on) return;
+    const bool pfm = it.job.opt == MANTRA_PFM;
+    std::fprintf(stderr, "mantra-launch kernel=%s%s samples=%llu escan=%llu eadd=%llu snew=%llu fseg=%llu "
+                 "alg_bytes=%llu ms=%.4f\n", pfm ? "k_pfm" : "k_bfs", wide ? "<wide>" : "",
+                 (unsigned long long)it.job.count, (unsigned long long)c[C_ESCAN], (unsigned long long)c[C_EADD],
+                 (unsigned long long)c[C_SNEW], (unsigned long long)c[C_FSEG],
+                 (unsigned long long)alg_bytes_of(pfm, c[C_ESCAN], c[C_EADD], c[C_SNEW], c[C_FSEG]), ms);
+}
+
+// One tick over `items` (narrow kernels, captured graph), or with `wide` the
+// 128-bit kernels launched directly.  Fills each item's ctr/status pointers.
+int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
+    const uint32_t k = (uint32_t)items.size();
+    int rc;
+    if ((rc = E.ensure_tables(std::max<uint32_t>(k, 1))) != MANTRA_OK) return rc;
+    uint32_t bn = 0, bA = 0, pn = 0;
+    uint64_t pwarps = 0;
+    bool any_b = false, any_p = false;
+    for (const TickItem& it : items) {
+        if (it.job.opt == MANTRA_PFM) {
+            any_p = true; pn = std::max(pn, it.G->n); pwarps += (it.job.count + 31) / 32;
+        } else {
+            any_b = true; bn = std::max(bn, it.G->n); bA = std::max(bA, it.G->A);
         }
     }
-    *NR = s;
+    if (any_b && (rc = E.ensure_bfs(bn, bA)) != MANTRA_OK) return rc;
+    if (any_p && (rc = E.ensure_pfm(pn, pwarps)) != MANTRA_OK) return rc;
+    // host tables
+    uint32_t* hdr = (uint32_t*)(E.tab_h + E.o_hdr);
+    u64* work = (u64*)(E.tab_h + E.o_work);
+    uint64_t* ub = (uint64_t*)(E.tab_h + E.o_ub);
+    uint64_t* up = (uint64_t*)(E.tab_h + E.o_up);
+    Task* tb = (Task*)(E.tab_h + E.o_tb);
+    Task* tp = (Task*)(E.tab_h + E.o_tp);
+    ReduceItem* ri = (ReduceItem*)(E.tab_h + E.o_ri);
+    uint32_t* rs = (uint32_t*)(E.tab_h + E.o_rs);
+    uint32_t nb = 0, np = 0, nr = 0;
+    ub[0] = 0; up[0] = 0; rs[0] = 0;
+    for (uint32_t x = 0; x < k; ++x) {
+        TickItem& it = items[x];
+        char* slot = E.slot_d + (size_t)x * SLOT_BYTES;
+        it.job.ctr = (u64*)slot;
+        it.job.status = (int*)(slot + SLOT_STATUS);
+        Task t{it.G->dg, it.job};
+        if (it.job.opt == MANTRA_PFM) { tp[np] = t; up[np + 1] = up[np] + (it.job.count + 31) / 32; ++np; }
+        else { tb[nb] = t; ub[nb + 1] = ub[nb] + it.job.count; ++nb; }
+        if (it.reduce) {
+            ri[nr] = ReduceItem{it.job.S, it.job.hits, it.G->n, it.red_c, (long long*)(slot + SLOT_ROWMAX),
+                                (u64*)(slot + SLOT_HMAX)};
+            rs[nr + 1] = rs[nr] + it.red_c + 1;
+            ++nr;
+        }
+    }
+    hdr[0] = nb; hdr[1] = np; hdr[2] = nr;
+    work[0] = 0; work[1] = 0;
+    if ((rc = E.launch_tick(wide)) != MANTRA_OK) return rc;
+    CU(cudaStreamSynchronize(E.sa));
+    out->slot.resize(k);
+    for (uint32_t x = 0; x < k; ++x) out->slot[x] = E.slot_h + (size_t)x * SLOT_BYTES;
+    out->had_bfs = nb > 0 && E.bfs_mem;
+    out->had_pfm = np > 0 && E.pfm_mem;
+    float ms = 0;
+    out->bfs_ms = (out->had_bfs && cudaEventElapsedTime(&ms, E.e_b0, E.e_b1) == cudaSuccess) ? ms : 0.0;
+    out->pfm_ms = (out->had_pfm && cudaEventElapsedTime(&ms, E.e_p0, E.e_p1) == cudaSuccess) ? ms : 0.0;
+    for (uint32_t x = 0; x < k; ++x)
+        log_item(items[x], wide, (const u64*)out->slot[x],
+                 items[x].job.opt == MANTRA_PFM ? out->pfm_ms : out->bfs_ms);
+    return MANTRA_OK;
+}
+
+// A tick followed, for items whose 64-bit path counts overflowed, by a
+// 128-bit re-run of those samples (and their reductions).  counters[x]
+// receives both passes' counters; slot_out[x] the slot whose reduction
+// outputs are current.
+struct TickResult {
+    std::vector<std::vector<char>> slot;   // current reduction outputs per item (copied)
+    std::vector<LaunchTotals> tot;         // per item counters, kernel time and launches
+    std::vector<int> status;
+};
+
+int run_tick_full(Engine& E, std::vector<TickItem>& items, uint64_t** ovf_lists, TickResult* R) {
+    TickOut out;
+    int rc = run_tick(E, items, false, &out);
+    if (rc != MANTRA_OK) return rc;
+    const uint32_t k = (uint32_t)items.size();
+    R->slot.assign(k, std::vector<char>(SLOT_BYTES));
+    R->tot.assign(k, LaunchTotals());
+    R->status.assign(k, MANTRA_OK);
+    std::vector<uint32_t> wide_ix;
+    std::vector<TickItem> witems;
+    for (uint32_t x = 0; x < k; ++x) {
+        std::memcpy(R->slot[x].data(), out.slot[x], SLOT_BYTES);
+        const u64* c = (const u64*)out.slot[x];
+        int st;
+        std::memcpy(&st, out.slot[x] + SLOT_STATUS, 4);
+        R->status[x] = st;
+        R->tot[x].add_counters(c);
+        R->tot[x].launches += 1;
+        R->tot[x].kernel_ms += items[x].job.opt == MANTRA_PFM ? out.pfm_ms : out.bfs_ms;
+        if (st == MANTRA_OK && c[C_NOVF] > 0) {
+            TickItem w = items[x];
+            w.job.idx_list = ovf_lists[x];
+            w.job.count = c[C_NOVF];
+            wide_ix.push_back(x);
+            witems.push_back(w);
+        }
+    }
+    if (!witems.empty()) {
+        TickOut wout;
+        if ((rc = run_tick(E, witems, true, &wout)) != MANTRA_OK) return rc;
+        for (size_t y = 0; y < witems.size(); ++y) {
+            const uint32_t x = wide_ix[y];
+            const u64* c = (const u64*)wout.slot[y];
+            int st;
+            std::memcpy(&st, wout.slot[y] + SLOT_STATUS, 4);
+            if (st != MANTRA_OK) R->status[x] = st;
+            R->tot[x].add_counters(c);
+            R->tot[x].launches += 1;
+            R->tot[x].wide += witems[y].job.count;
+            R->tot[x].kernel_ms += witems[y].job.opt == MANTRA_PFM ? wout.pfm_ms : wout.bfs_ms;
+            // reduction outputs of the wide tick include every sample of the round
+            std::memcpy(R->slot[x].data() + SLOT_HMAX, wout.slot[y] + SLOT_HMAX, SLOT_BYTES - SLOT_HMAX);
+        }
+    }
     return MANTRA_OK;
 }
 
@@ -351,20 +575,261 @@ double delta_of_round(double delta, uint64_t i, int sched) {
     return sched == 1 ? delta / std::ldexp(1.0, (int)i) : delta / std::ldexp(1.0, (int)(i + 1));
 }
 
-double now_s() {
-    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+// ---------------------------------------------------------------------------
+// Algorithm 1 for one problem, as a state machine advanced by ticks:
+// BOOT (s' bootstrap samples) -> ROUND (schedule s_1, s_2, ...) -> DONE.
+// ---------------------------------------------------------------------------
+constexpr uint64_t RMAX = 0x7FFFFFFFull;
+
+struct Problem {
+    const mantra_graph* G = nullptr;
+    int opt = 0;
+    double eps = 0, delta = 0;
+    uint64_t seed = 0;
+    uint32_t c = 25;
+    double growth = 1.2;
+    uint64_t fixed_r = 0, boot = 0;
+    int dsched = 0;
+    double* est_out = nullptr;
+    uint64_t* hits_out = nullptr;
+    bool out_device = false;
+    mantra_info* info_out = nullptr;
+    // device state
+    u64* hits = nullptr; int* S = nullptr; double* est = nullptr; uint64_t* ovf = nullptr;
+    size_t b_hits = 0, b_S = 0, b_est = 0, b_ovf = 0;
+    uint64_t ovf_cap = 0;
+    // progress
+    enum { BOOT, ROUND, DONE } phase = BOOT;
+    uint64_t sb = 0, omega = 0, s1 = 0, r = 0, target = 0, round = 0, reduces = 0;
+    LaunchTotals T;
+    mantra_info I{};
+    int status = MANTRA_OK;
+    double t0 = 0;
+
+    int validate() const {
+        if (!G || (!est_out && !out_device)) return MANTRA_E_INVAL;
+        if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0)) return MANTRA_E_INVAL;
+        if (opt != MANTRA_SH && opt != MANTRA_SFM && opt != MANTRA_PFM) return MANTRA_E_INVAL;
+        if (c < 1 || c > 128 || !(growth > 1.0)) return MANTRA_E_INVAL;
+        if (fixed_r > RMAX) return MANTRA_E_INVAL;
+        if (out_device && !est_out) return MANTRA_E_INVAL;
+        return MANTRA_OK;
+    }
+
+    // bytes of device state held while the problem runs (admission footprint)
+    size_t footprint() const {
+        const size_t n = G->n;
+        return al256(n * 8) * 2 + al256((size_t)c * n * 4) + al256(8 * 4096);
+    }
+
+    int grow_ovf(Engine& E, uint64_t need) {
+        if (need <= ovf_cap) return MANTRA_OK;
+        uint64_t nc = std::max<uint64_t>(4096, ovf_cap);
+        while (nc < need) nc *= 2;
+        if (ovf) E.pool.put(ovf, b_ovf);
+        b_ovf = nc * 8;
+        ovf = (uint64_t*)E.pool.get(b_ovf);
+        if (!ovf) { ovf_cap = 0; return MANTRA_E_NOMEM; }
+        ovf_cap = nc;
+        return MANTRA_OK;
+    }
+
+    int start(Engine& E) {
+        t0 = now_s();
+        const size_t n = G->n;
+        b_hits = n * 8; b_S = (size_t)c * n * 4; b_est = n * 8;
+        hits = (u64*)E.pool.get(b_hits);
+        S = (int*)E.pool.get(b_S);
+        est = out_device ? nullptr : (double*)E.pool.get(b_est);
+        if (!hits || !S || (!out_device && !est)) return MANTRA_E_NOMEM;
+        CU(cudaMemsetAsync(hits, 0, b_hits, E.sa));
+        CU(cudaMemsetAsync(S, 0, b_S, E.sa));
+        if (fixed_r > 0) {
+            phase = ROUND; target = fixed_r; r = 0;
+        } else {
+            sb = boot ? boot : (uint64_t)std::ceil(std::log(1.0 / delta) / eps);
+            if (sb > RMAX) return MANTRA_E_INVAL;
+            phase = BOOT;
+        }
+        return grow_ovf(E, phase == BOOT ? sb : target);
+    }
+
+    int item(Engine& E, TickItem* it) {
+        it->G = G;
+        Job& j = it->job;
+        j = Job{};
+        j.seed = seed; j.opt = opt; j.c = c; j.hits = hits;
+        if (phase == BOOT) {
+            j.i0 = 0; j.count = sb; j.dom_pair = DOM_BOOT_PAIR; j.dom_path = DOM_BOOT_PATH; j.S = nullptr;
+            it->red_c = 0;
+        } else {
+            j.i0 = r; j.count = target - r; j.dom_pair = DOM_PAIR; j.dom_path = DOM_PATH; j.S = S;
+            it->red_c = c;
+        }
+        it->reduce = true;
+        const int rc = grow_ovf(E, j.count);
+        j.ovf_list = ovf;
+        return rc;
+    }
+
+    // Advances the state after a tick (slot: counters + reduction outputs).
+    int consume(Engine& E, const char* slot, const LaunchTotals& tt) {
+        const u64* ctr = (const u64*)slot;
+        u64 H;
+        std::memcpy(&H, slot + SLOT_HMAX, 8);
+        reduces += 1;
+        if (phase == BOOT) {
+            // DrawSufficientSampleSize(G, s', delta/2) and SamplingSchedule
+            double v0 = (double)H / (double)sb;
+            double rho = (double)tt.sum_int / (double)sb;
+            if (v0 == 0.0 || rho == 0.0) { v0 = 1.0 / (double)sb; rho = std::max(rho, v0); }
+            const double om = std::ceil(omega_closed_form(v0, rho, eps, delta / 2.0));
+            if (!(om <= (double)RMAX)) return MANTRA_E_INVAL;
+            omega = std::max<uint64_t>(1, (uint64_t)om);
+            const double d1 = delta_of_round(delta, 1, dsched);
+            if (sb >= omega || xi_given_R(0.0, v0, d1, (double)omega) > eps) s1 = omega;
+            else {
+                uint64_t lo = sb, hi = omega;
+                while (lo < hi) {
+                    const uint64_t mid = lo + (hi - lo) / 2;
+                    if (xi_given_R(0.0, v0, d1, (double)mid) <= eps) hi = mid; else lo = mid + 1;
+                }
+                s1 = lo;
+            }
+            I.bootstrap = sb; I.omega = omega; I.s1 = s1; I.rho_hat = rho;
+            T.kernel_ms += tt.kernel_ms; T.launches += tt.launches; T.escan += tt.escan; T.eadd += tt.eadd;
+            T.snew += tt.snew; T.fseg += tt.fseg; T.wide += tt.wide;
+            CU(cudaMemsetAsync(hits, 0, b_hits, E.sa));
+            phase = ROUND; r = 0; target = s1; round = 0;
+            return MANTRA_OK;
+        }
+        (void)ctr;
+        T.kernel_ms += tt.kernel_ms; T.launches += tt.launches; T.escan += tt.escan; T.eadd += tt.eadd;
+        T.snew += tt.snew; T.fseg += tt.fseg; T.wide += tt.wide; T.sum_int += tt.sum_int;
+        r = target;
+        round += 1;
+        int64_t NR = 0;
+        for (uint32_t jj = 0; jj < c; ++jj) {
+            long long x;
+            std::memcpy(&x, slot + SLOT_ROWMAX + 8 * jj, 8);
+            NR += x;
+        }
+        const double W = (double)H / (double)r;
+        const double xi = xi_from_mcera((double)NR / ((double)c * (double)r), W, W, delta_of_round(delta, round, dsched),
+                                        (double)r, (double)c);
+        I.rounds = round; I.rade_num = NR; I.max_hits = H; I.xi = xi; I.vhat = W;
+        if (fixed_r > 0 || r >= omega || xi <= eps) { phase = DONE; return MANTRA_OK; }
+        uint64_t nt = (uint64_t)std::ceil(growth * (double)target);
+        if (nt <= target) nt = target + 1;
+        target = std::min(omega, nt);
+        return MANTRA_OK;
+    }
+
+    // est = hits / r, outputs copied (enqueued on E.sa; caller synchronises).
+    int finish(Engine& E) {
+        I.r = r;
+        I.sum_int_len = T.sum_int;
+        double* dst = out_device ? est_out : est;
+        CU(launch_normalise(hits, G->n, r, dst, E.sa));
+        if (!out_device) CU(cudaMemcpyAsync(est_out, est, b_est, cudaMemcpyDeviceToHost, E.sa));
+        if (hits_out)
+            CU(cudaMemcpyAsync(hits_out, hits, b_hits, out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               E.sa));
+        I.edges_scanned = T.escan; I.sigma_adds = T.eadd; I.states_new = T.snew; I.wide_samples = T.wide;
+        I.kernel_ms = T.kernel_ms; I.search_launches = T.launches;
+        I.kernel_launches = T.launches + reduces + 1;
+        I.alg_bytes = alg_bytes_of(opt == MANTRA_PFM, T.escan, T.eadd, T.snew, T.fseg);
+        return MANTRA_OK;
+    }
+
+    void release(Engine& E) {
+        E.pool.put(hits, b_hits); E.pool.put(S, b_S); E.pool.put(est, b_est); E.pool.put(ovf, b_ovf);
+        hits = nullptr; S = nullptr; est = nullptr; ovf = nullptr; ovf_cap = 0;
+    }
+};
+
+int problem_from(const mantra_graph* g, mantra_opt opt, double eps, double delta, uint64_t seed,
+                 const mantra_opts* opts, double* est_out, uint64_t* hits_out, mantra_info* info, Problem* p) {
+    mantra_opts o{};
+    if (opts) o = *opts;
+    p->G = g; p->opt = (int)opt; p->eps = eps; p->delta = delta; p->seed = seed;
+    p->c = o.c ? o.c : 25;
+    p->growth = o.growth > 0 ? o.growth : 1.2;
+    p->fixed_r = o.fixed_r; p->boot = o.bootstrap; p->dsched = o.delta_sched;
+    p->est_out = est_out; p->hits_out = hits_out; p->out_device = o.out_device != 0; p->info_out = info;
+    return p->validate();
 }
 
-int init_graph_device(mantra_graph* G) {
-    CU(cudaGetDevice(&G->device));
-    CU(cudaDeviceGetAttribute(&G->num_sms, cudaDevAttrMultiProcessorCount, G->device));
-    int optin = 0;
-    CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, G->device));
-    G->smem_optin = (size_t)optin;
-    CU(cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking));
-    CU(cudaEventCreate(&G->ev0));
-    CU(cudaEventCreate(&G->ev1));
-    return MANTRA_OK;
+// Runs Algorithm 1 for every problem together: each tick carries the next
+// sample range of every unfinished problem.  Per-problem statuses are kept;
+// the return value is the first failure, or MANTRA_OK.
+int run_problems(Engine& E, std::vector<Problem*>& ps) {
+    int first_err = MANTRA_OK;
+    for (Problem* p : ps) {
+        if (p->status == MANTRA_OK) p->status = p->start(E);
+    }
+    std::vector<Problem*> act;
+    std::vector<TickItem> items;
+    std::vector<uint64_t*> ovfs;
+    while (true) {
+        act.clear(); items.clear(); ovfs.clear();
+        for (Problem* p : ps) {
+            if (p->status != MANTRA_OK || p->phase == Problem::DONE) continue;
+            TickItem it;
+            const int rc = p->item(E, &it);
+            if (rc != MANTRA_OK) { p->status = rc; continue; }
+            act.push_back(p); items.push_back(it); ovfs.push_back(p->ovf);
+        }
+        if (act.empty()) break;
+        TickResult R;
+        const int rc = run_tick_full(E, items, ovfs.data(), &R);
+        if (rc != MANTRA_OK) { for (Problem* p : act) p->status = rc; break; }
+        for (size_t x = 0; x < act.size(); ++x) {
+            if (R.status[x] != MANTRA_OK) { act[x]->status = R.status[x]; continue; }
+            const int st = act[x]->consume(E, R.slot[x].data(), R.tot[x]);
+            if (st != MANTRA_OK) act[x]->status = st;
+        }
+    }
+    for (Problem* p : ps)
+        if (p->status == MANTRA_OK) p->status = p->finish(E);
+    const cudaError_t se = cudaStreamSynchronize(E.sa);
+    for (Problem* p : ps) {
+        if (se != cudaSuccess && p->status == MANTRA_OK) p->status = MANTRA_E_CUDA;
+        p->I.seconds = now_s() - p->t0;
+        if (p->info_out && p->status == MANTRA_OK) *p->info_out = p->I;
+        p->release(E);
+        if (first_err == MANTRA_OK && p->status != MANTRA_OK) first_err = p->status;
+    }
+    return first_err;
+}
+
+// Orders the engine's streams after a caller stream, and the caller stream
+// after the engine's work.
+struct StreamJoin {
+    Engine& E;
+    cudaStream_t user;
+    cudaEvent_t ev = nullptr;
+    StreamJoin(Engine& e, void* s) : E(e), user((cudaStream_t)s) {
+        if (user && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(ev, user);
+            cudaStreamWaitEvent(E.sa, ev, 0);
+        }
+    }
+    ~StreamJoin() {
+        if (ev) {
+            cudaEventRecord(ev, E.sa);
+            cudaStreamWaitEvent(user, ev, 0);
+            cudaEventDestroy(ev);
+        }
+    }
+};
+
+int current_engine(const mantra_graph* g, Engine** E) {
+    int dev = g ? g->device : 0;
+    if (!g) {
+        if (cudaGetDevice(&dev) != cudaSuccess) return MANTRA_E_CUDA;
+    }
+    return engine_for(dev, E);
 }
 
 }  // namespace
@@ -374,9 +839,13 @@ namespace mantra {
 // Read-only view of a loaded graph for the library's other translation units.
 const DevGraph* graph_view(const mantra_graph* g, uint32_t* n, uint32_t* A, int* num_sms, size_t* smem_optin,
                            std::mutex** mu) {
-    mantra_graph* G = const_cast<mantra_graph*>(g);
-    *n = G->n; *A = G->A; *num_sms = G->num_sms; *smem_optin = G->smem_optin; *mu = &G->mu;
-    return &G->dg;
+    Engine* E = nullptr;
+    engine_for(g->device, &E);
+    *n = g->n; *A = g->A;
+    *num_sms = E ? E->num_sms : 1;
+    *smem_optin = E ? E->smem_optin : 48 * 1024;
+    *mu = E ? &E->mu : nullptr;
+    return &g->dg;
 }
 
 }  // namespace mantra
@@ -393,6 +862,7 @@ const char* mantra_strerror(int code) {
         case MANTRA_E_TIMEOUT: return "device wait timed out";
         case MANTRA_E_CHECK: return "device consistency check failed";
         case MANTRA_E_RNG: return "random draw rejected too often";
+        case MANTRA_PENDING: return "request still running";
         default: return "unknown error";
     }
 }
@@ -403,8 +873,14 @@ int mantra_graph_load(const uint32_t* u, const uint32_t* v, const uint32_t* t, u
     *out = nullptr;
     mantra_graph* G = new (std::nothrow) mantra_graph();
     if (!G) return MANTRA_E_NOMEM;
-    int rc = init_graph_device(G);
-    if (rc == MANTRA_OK) rc = build_store(u, v, t, m, n, G);
+    Engine* E = nullptr;
+    int rc = MANTRA_OK;
+    if (cudaGetDevice(&G->device) != cudaSuccess) rc = MANTRA_E_CUDA;
+    if (rc == MANTRA_OK) rc = engine_for(G->device, &E);
+    if (rc == MANTRA_OK) {
+        std::lock_guard<std::mutex> lock(E->mu);
+        rc = build_store(u, v, t, m, n, G, E->sa);
+    }
     if (rc != MANTRA_OK) { mantra_graph_free(G); return rc; }
     *out = G;
     return MANTRA_OK;
@@ -423,174 +899,108 @@ int mantra_graph_info(const mantra_graph* g, uint32_t* n, uint64_t* m_dedup, uin
 
 void mantra_graph_free(mantra_graph* g) {
     if (!g) return;
-    if (g->stream) cudaStreamSynchronize(g->stream);
-    if (g->dmem) cudaFree(g->dmem);
-    if (g->bfs_mem) cudaFree(g->bfs_mem);
-    if (g->pfm_mem) cudaFree(g->pfm_mem);
-    if (g->run_mem) cudaFree(g->run_mem);
-    if (g->host_ctr) cudaFreeHost(g->host_ctr);
-    if (g->ev0) cudaEventDestroy(g->ev0);
-    if (g->ev1) cudaEventDestroy(g->ev1);
-    if (g->stream) cudaStreamDestroy(g->stream);
+    Engine* E = nullptr;
+    if (g->dmem && engine_for(g->device, &E) == MANTRA_OK) {
+        std::lock_guard<std::mutex> lock(E->mu);
+        cudaStreamSynchronize(E->sa);
+        cudaStreamSynchronize(E->sb);
+        cudaFree(g->dmem);
+    } else if (g->dmem) {
+        cudaFree(g->dmem);
+    }
     delete g;
 }
 
-int mantra_estimate(const mantra_graph* gc, mantra_opt opt, double eps, double delta, uint64_t seed,
+int mantra_estimate(const mantra_graph* g, mantra_opt opt, double eps, double delta, uint64_t seed,
                     const mantra_opts* opts, double* est_out, uint64_t* hits_out, mantra_info* info) {
-    if (!gc || !est_out) return MANTRA_E_INVAL;
-    if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0)) return MANTRA_E_INVAL;
-    if (opt != MANTRA_SH && opt != MANTRA_SFM && opt != MANTRA_PFM) return MANTRA_E_INVAL;
-    mantra_opts o{};
-    if (opts) o = *opts;
-    const uint32_t c = o.c ? o.c : 25;
-    const double growth = o.growth > 0 ? o.growth : 1.2;
-    if (c < 1 || c > 128 || growth <= 1.0) return MANTRA_E_INVAL;
-    mantra_graph* G = const_cast<mantra_graph*>(gc);
-    std::lock_guard<std::mutex> lock(G->mu);
-    const double t0 = now_s();
-    cudaStream_t st = o.stream ? (cudaStream_t)o.stream : G->stream;
-    const uint32_t n = G->n;
-    const uint64_t RMAX = 0x7FFFFFFFull;
-
-    mantra_info I;
-    std::memset(&I, 0, sizeof(I));
-    LaunchTotals T;
-
-    Job base{};
-    base.seed = seed; base.opt = (int)opt; base.c = c;
-
-    uint64_t r = 0, reduces = 0;
-    int rc;
-    if (o.fixed_r > 0) {
-        if (o.fixed_r > RMAX) return MANTRA_E_INVAL;
-        if ((rc = ensure_run(G, c, o.fixed_r)) != MANTRA_OK) return rc;
-        CU(cudaMemsetAsync(G->hits, 0, (size_t)n * 8, st));
-        CU(cudaMemsetAsync(G->S, 0, (size_t)c * n * 4, st));
-        Job j = base;
-        j.i0 = 0; j.count = o.fixed_r; j.dom_pair = DOM_PAIR; j.dom_path = DOM_PATH;
-        j.hits = G->hits; j.S = G->S;
-        if ((rc = run_samples(G, j, st, &T)) != MANTRA_OK) return rc;
-        r = o.fixed_r;
-        int64_t NR; uint64_t H;
-        if ((rc = round_reduce(G, c, true, st, &NR, &H)) != MANTRA_OK) return rc;
-        reduces += 1;
-        I.rounds = 1; I.rade_num = NR; I.max_hits = H;
-        const double W = (double)H / (double)r;
-        I.vhat = W;
-        I.xi = xi_from_mcera((double)NR / ((double)c * (double)r), W, W, delta_of_round(delta, 1, o.delta_sched),
-                             (double)r, (double)c);
-    } else {
-        // bootstrap: DrawSufficientSampleSize(G, s', delta/2)
-        const uint64_t sb = o.bootstrap ? o.bootstrap : (uint64_t)std::ceil(std::log(1.0 / delta) / eps);
-        if (sb > RMAX) return MANTRA_E_INVAL;
-        if ((rc = ensure_run(G, c, std::max<uint64_t>(sb, 4096))) != MANTRA_OK) return rc;
-        CU(cudaMemsetAsync(G->hits, 0, (size_t)n * 8, st));
-        Job jb = base;
-        jb.i0 = 0; jb.count = sb; jb.dom_pair = DOM_BOOT_PAIR; jb.dom_path = DOM_BOOT_PATH;
-        jb.hits = G->hits; jb.S = nullptr;
-        LaunchTotals TB;
-        if ((rc = run_samples(G, jb, st, &TB)) != MANTRA_OK) return rc;
-        int64_t NRb; uint64_t Hb;
-        if ((rc = round_reduce(G, c, false, st, &NRb, &Hb)) != MANTRA_OK) return rc;
-        reduces += 1;
-        double v0 = (double)Hb / (double)sb;
-        double rho = (double)TB.sum_int / (double)sb;
-        if (v0 == 0.0 || rho == 0.0) { v0 = 1.0 / (double)sb; rho = std::max(rho, v0); }
-        const double om = std::ceil(omega_closed_form(v0, rho, eps, delta / 2.0));
-        if (!(om <= (double)RMAX)) return MANTRA_E_INVAL;
-        const uint64_t omega = std::max<uint64_t>(1, (uint64_t)om);
-        // SamplingSchedule: least s in [s', omega] with xi(R = 0) <= eps
-        const double d1 = delta_of_round(delta, 1, o.delta_sched);
-        uint64_t s1;
-        if (sb >= omega || xi_given_R(0.0, v0, d1, (double)omega) > eps) s1 = omega;
-        else {
-            uint64_t lo = sb, hi = omega;
-            while (lo < hi) {
-                const uint64_t mid = lo + (hi - lo) / 2;
-                if (xi_given_R(0.0, v0, d1, (double)mid) <= eps) hi = mid; else lo = mid + 1;
-            }
-            s1 = lo;
-        }
-        I.bootstrap = sb; I.omega = omega; I.s1 = s1; I.rho_hat = rho;
-        T.kernel_ms += TB.kernel_ms; T.launches += TB.launches; T.escan += TB.escan; T.eadd += TB.eadd;
-        T.snew += TB.snew; T.fseg += TB.fseg; T.wide += TB.wide;
-        if ((rc = ensure_run(G, c, omega)) != MANTRA_OK) return rc;
-        CU(cudaMemsetAsync(G->hits, 0, (size_t)n * 8, st));
-        CU(cudaMemsetAsync(G->S, 0, (size_t)c * n * 4, st));
-        uint64_t target = s1, round = 0;
-        while (true) {
-            round += 1;
-            Job j = base;
-            j.i0 = r; j.count = target - r; j.dom_pair = DOM_PAIR; j.dom_path = DOM_PATH;
-            j.hits = G->hits; j.S = G->S;
-            if ((rc = run_samples(G, j, st, &T)) != MANTRA_OK) return rc;
-            r = target;
-            int64_t NR; uint64_t H;
-            if ((rc = round_reduce(G, c, true, st, &NR, &H)) != MANTRA_OK) return rc;
-            reduces += 1;
-            const double W = (double)H / (double)r;
-            const double xi = xi_from_mcera((double)NR / ((double)c * (double)r), W, W,
-                                            delta_of_round(delta, round, o.delta_sched), (double)r, (double)c);
-            I.rounds = round; I.rade_num = NR; I.max_hits = H; I.xi = xi; I.vhat = W;
-            if (r >= omega || xi <= eps) break;
-            uint64_t nt = (uint64_t)std::ceil(growth * (double)target);
-            if (nt <= target) nt = target + 1;
-            target = std::min(omega, nt);
-        }
-    }
-    I.r = r;
-    I.sum_int_len = T.sum_int;
-    // est_v = hits_v / r
-    double* est_dev = o.out_device ? est_out : G->est;
-    CU(launch_normalise(G->hits, n, r, est_dev, st));
-    if (!o.out_device) CU(cudaMemcpyAsync(est_out, G->est, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
-    if (hits_out)
-        CU(cudaMemcpyAsync(hits_out, G->hits, (size_t)n * 8,
-                           o.out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    if (info) {
-        I.edges_scanned = T.escan; I.sigma_adds = T.eadd; I.states_new = T.snew; I.wide_samples = T.wide;
-        I.kernel_ms = T.kernel_ms; I.search_launches = T.launches;
-        I.kernel_launches = T.launches + reduces + 1;
-        I.alg_bytes = alg_bytes_of(opt == MANTRA_PFM, T.escan, T.eadd, T.snew, T.fseg);
-        I.seconds = now_s() - t0;
-        *info = I;
-    }
-    return MANTRA_OK;
+    if (!g || !est_out) return MANTRA_E_INVAL;
+    Problem p;
+    int rc = problem_from(g, opt, eps, delta, seed, opts, est_out, hits_out, info, &p);
+    if (rc != MANTRA_OK) return rc;
+    Engine* E = nullptr;
+    if ((rc = current_engine(g, &E)) != MANTRA_OK) return rc;
+    std::lock_guard<std::mutex> lock(E->mu);
+    StreamJoin join(*E, opts ? opts->stream : nullptr);
+    std::vector<Problem*> ps{&p};
+    return run_problems(*E, ps);
 }
 
-int mantra_temporal_stats(const mantra_graph* gc, mantra_opt opt, double eps, uint64_t seed, uint64_t r_override,
+int mantra_estimate_batch(mantra_problem* probs, uint32_t count) {
+    if (!probs && count) return MANTRA_E_INVAL;
+    if (count == 0) return MANTRA_OK;
+    std::vector<Problem> P(count);
+    std::vector<Problem*> ptrs;
+    Engine* E = nullptr;
+    int first = MANTRA_OK;
+    for (uint32_t x = 0; x < count; ++x) {
+        mantra_problem& q = probs[x];
+        q.status = problem_from(q.graph, q.opt, q.eps, q.delta, q.seed, q.opts, q.est_out, q.hits_out, q.info, &P[x]);
+        if (q.status == MANTRA_OK && q.graph) {
+            Engine* e = nullptr;
+            q.status = current_engine(q.graph, &e);
+            if (q.status == MANTRA_OK && E && e != E) q.status = MANTRA_E_INVAL;   // one device per batch
+            if (q.status == MANTRA_OK) E = e;
+        }
+        if (q.status == MANTRA_OK) ptrs.push_back(&P[x]);
+        else if (first == MANTRA_OK) first = q.status;
+    }
+    if (!E) return first == MANTRA_OK ? MANTRA_E_INVAL : first;
+    {
+        std::lock_guard<std::mutex> lock(E->mu);
+        const int rc = run_problems(*E, ptrs);
+        if (first == MANTRA_OK) first = rc;
+    }
+    for (uint32_t x = 0; x < count; ++x)
+        if (probs[x].status == MANTRA_OK) probs[x].status = P[x].status;
+    return first;
+}
+
+int mantra_temporal_stats(const mantra_graph* g, mantra_opt opt, double eps, uint64_t seed, uint64_t r_override,
                           double tau, mantra_tstats* out, uint64_t* reach_out, uint32_t reach_cap) {
-    if (!gc || !out) return MANTRA_E_INVAL;
+    if (!g || !out) return MANTRA_E_INVAL;
     if (!(eps > 0.0 && eps < 1.0) || !(tau >= 0.0 && tau <= 1.0)) return MANTRA_E_INVAL;
     if (opt != MANTRA_SH && opt != MANTRA_SFM && opt != MANTRA_PFM) return MANTRA_E_INVAL;
-    mantra_graph* G = const_cast<mantra_graph*>(gc);
-    std::lock_guard<std::mutex> lock(G->mu);
-    const double t0 = now_s();
-    const uint32_t n = G->n;
-    const uint64_t rs = r_override ? r_override : (uint64_t)std::ceil(std::log((double)n) / (eps * eps));
+    Engine* E = nullptr;
     int rc;
-    if ((rc = ensure_run(G, 25, rs)) != MANTRA_OK) return rc;
-    cudaStream_t st = G->stream;
-    CU(cudaMemsetAsync(G->cnt, 0, ((size_t)n + 2) * 8, st));
-    CU(cudaMemsetAsync(G->dmax, 0, 8, st));
-    Job j{};
+    if ((rc = current_engine(g, &E)) != MANTRA_OK) return rc;
+    std::lock_guard<std::mutex> lock(E->mu);
+    const double t0 = now_s();
+    const uint32_t n = g->n;
+    const uint64_t rs = r_override ? r_override : (uint64_t)std::ceil(std::log((double)n) / (eps * eps));
+    const size_t b_cnt = ((size_t)n + 2) * 8;
+    u64* cnt = (u64*)E->pool.get(b_cnt + 256);
+    if (!cnt) return MANTRA_E_NOMEM;
+    u64* dmax = (u64*)((char*)cnt + al256(b_cnt));
+    CU(cudaMemsetAsync(cnt, 0, b_cnt + 256, E->sa));
+    std::vector<TickItem> items(1);
+    items[0].G = g;
+    Job& j = items[0].job;
     j.seed = seed; j.i0 = 0; j.count = rs; j.opt = (opt == MANTRA_PFM) ? MANTRA_PFM : MANTRA_SH;
-    j.stats = 1; j.cnt = G->cnt; j.dmax = G->dmax;
-    LaunchTotals T;
-    if ((rc = run_samples(G, j, st, &T)) != MANTRA_OK) return rc;
-    std::vector<u64> cnt((size_t)n + 1);
-    u64 dmax = 0;
-    CU(cudaMemcpyAsync(cnt.data(), G->cnt, ((size_t)n + 1) * 8, cudaMemcpyDeviceToHost, st));
-    CU(cudaMemcpyAsync(&dmax, G->dmax, 8, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    const uint32_t D = (uint32_t)dmax;
+    j.stats = 1; j.cnt = cnt; j.dmax = dmax;
+    TickOut to;
+    rc = run_tick(*E, items, false, &to);
+    std::vector<u64> hc((size_t)n + 1);
+    u64 dm = 0;
+    if (rc == MANTRA_OK) {
+        int st;
+        std::memcpy(&st, to.slot[0] + SLOT_STATUS, 4);
+        if (st != MANTRA_OK) rc = st;
+    }
+    if (rc == MANTRA_OK) {
+        if (cudaMemcpyAsync(hc.data(), cnt, ((size_t)n + 1) * 8, cudaMemcpyDeviceToHost, E->sa) != cudaSuccess ||
+            cudaMemcpyAsync(&dm, dmax, 8, cudaMemcpyDeviceToHost, E->sa) != cudaSuccess ||
+            cudaStreamSynchronize(E->sa) != cudaSuccess)
+            rc = MANTRA_E_CUDA;
+    }
+    E->pool.put(cnt, b_cnt + 256);
+    if (rc != MANTRA_OK) return rc;
+    const uint32_t D = (uint32_t)dm;
     std::vector<u64> R((size_t)D + 1);
     u64 acc = 0;
-    for (uint32_t h = 0; h <= D; ++h) { acc += cnt[h]; R[h] = acc; }
+    for (uint32_t h = 0; h <= D; ++h) { acc += hc[h]; R[h] = acc; }
     if (reach_out)
         for (uint32_t h = 0; h < reach_cap; ++h) reach_out[h] = (h <= D) ? R[h] : acc;
-    // Algorithm 2's host formulas: Rhat[h] = (n/r) R[h]
+    // Algorithm 2's host formulas: Rhat[h] = (n / r) R[h]
     std::vector<double> Rh((size_t)D + 1);
     for (uint32_t h = 0; h <= D; ++h) Rh[h] = ((double)n / (double)rs) * (double)R[h];
     mantra_tstats S{};
@@ -611,45 +1021,49 @@ int mantra_temporal_stats(const mantra_graph* gc, mantra_opt opt, double eps, ui
     return MANTRA_OK;
 }
 
-int mantra_sample_paths(const mantra_graph* gc, mantra_opt opt, uint64_t seed, uint32_t dom_pair, uint32_t dom_path,
+int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, uint32_t dom_pair, uint32_t dom_path,
                         uint64_t i0, uint64_t count, uint32_t* s_out, uint32_t* z_out, uint64_t* sigma_out,
                         uint32_t* len_out, uint32_t* nodes_out, uint32_t cap) {
-    if (!gc || !s_out || !z_out || !sigma_out || !len_out || (cap > 0 && !nodes_out)) return MANTRA_E_INVAL;
+    if (!g || !s_out || !z_out || !sigma_out || !len_out || (cap > 0 && !nodes_out)) return MANTRA_E_INVAL;
     if (opt != MANTRA_SH && opt != MANTRA_SFM && opt != MANTRA_PFM) return MANTRA_E_INVAL;
     if (dom_pair > 5 || dom_path > 5) return MANTRA_E_INVAL;
     if (count == 0) return MANTRA_OK;
-    mantra_graph* G = const_cast<mantra_graph*>(gc);
-    std::lock_guard<std::mutex> lock(G->mu);
+    Engine* E = nullptr;
     int rc;
-    if ((rc = ensure_run(G, 25, count)) != MANTRA_OK) return rc;
-    cudaStream_t st = G->stream;
+    if ((rc = current_engine(g, &E)) != MANTRA_OK) return rc;
+    std::lock_guard<std::mutex> lock(E->mu);
     const size_t capn = std::max<uint32_t>(cap, 1);
-    const size_t bytes = al256(count * 4) * 3 + al256(count * 16) + al256(count * capn * 4);
-    char* d = nullptr;
-    if (cudaMalloc(&d, bytes) != cudaSuccess) return MANTRA_E_NOMEM;
-    Job j{};
+    const size_t bytes = al256(count * 4) * 3 + al256(count * 16) + al256(count * capn * 4) + al256(count * 8);
+    char* d = (char*)E->pool.get(bytes);
+    if (!d) return MANTRA_E_NOMEM;
+    std::vector<TickItem> items(1);
+    items[0].G = g;
+    Job& j = items[0].job;
     j.seed = seed; j.i0 = i0; j.count = count; j.dom_pair = dom_pair; j.dom_path = dom_path; j.opt = (int)opt;
     size_t o = 0;
     j.rec_s = (uint32_t*)(d + o); o += al256(count * 4);
     j.rec_z = (uint32_t*)(d + o); o += al256(count * 4);
     j.rec_len = (uint32_t*)(d + o); o += al256(count * 4);
     j.rec_sig = (u64*)(d + o); o += al256(count * 16);
-    j.rec_nodes = (uint32_t*)(d + o);
+    j.rec_nodes = (uint32_t*)(d + o); o += al256(count * capn * 4);
+    j.ovf_list = (uint64_t*)(d + o);
     j.rec_cap = (uint32_t)capn;
-    LaunchTotals T;
-    rc = run_samples(G, j, st, &T);
+    TickResult R;
+    uint64_t* ovfs[1] = {j.ovf_list};
+    rc = run_tick_full(*E, items, ovfs, &R);
+    if (rc == MANTRA_OK && R.status[0] != MANTRA_OK) rc = R.status[0];
     if (rc == MANTRA_OK) {
         cudaError_t e = cudaSuccess;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(s_out, j.rec_s, count * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(z_out, j.rec_z, count * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(len_out, j.rec_len, count * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(sigma_out, j.rec_sig, count * 16, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s_out, j.rec_s, count * 4, cudaMemcpyDeviceToHost, E->sa);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(z_out, j.rec_z, count * 4, cudaMemcpyDeviceToHost, E->sa);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(len_out, j.rec_len, count * 4, cudaMemcpyDeviceToHost, E->sa);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sigma_out, j.rec_sig, count * 16, cudaMemcpyDeviceToHost, E->sa);
         if (e == cudaSuccess && cap > 0)
-            e = cudaMemcpyAsync(nodes_out, j.rec_nodes, count * (size_t)cap * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            e = cudaMemcpyAsync(nodes_out, j.rec_nodes, count * (size_t)cap * 4, cudaMemcpyDeviceToHost, E->sa);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(E->sa);
         if (e != cudaSuccess) rc = MANTRA_E_CUDA;
     }
-    cudaFree(d);
+    E->pool.put(d, bytes);
     return rc;
 }
 

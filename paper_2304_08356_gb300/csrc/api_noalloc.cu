@@ -27,7 +27,10 @@ using namespace mantra;
 namespace {
 
 constexpr size_t kScratchBytes = (size_t)64 << 20;     // 64 MiB per device
-constexpr size_t kHeadBytes = 256;                      // launch counters + status word
+constexpr size_t kCtrBytes = 256;                       // launch counters + status word
+constexpr size_t kTaskOff = kCtrBytes;                  // one-entry task table
+constexpr size_t kUnitOff = kTaskOff + ((sizeof(Task) + 255) / 256) * 256;   // unit starts, task count, work counter
+constexpr size_t kHeadBytes = kUnitOff + 256;
 constexpr int kMaxDevices = 64;
 
 }  // namespace
@@ -75,7 +78,7 @@ extern "C" int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt
     std::mutex* gmu = nullptr;
     const DevGraph* dg = graph_view(g, &n, &A, &num_sms, &smem_optin, &gmu);
 
-    // layout: [counters | overflow list (count entries) | per-CTA search regions]
+    // layout: [counters | task table (one task) | overflow list (count entries) | per-CTA search regions]
     const size_t smem = bfs_smem_bytes(A);
     const bool in_smem = smem + 1024 <= smem_optin;
     BfsWs ws{};
@@ -97,16 +100,26 @@ extern "C" int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt
     if (cudaMemsetAsync(scratch, 0, used, st) != cudaSuccess) return MANTRA_E_CUDA;
     if (bfs_configure(in_smem ? smem : 0) != cudaSuccess) return MANTRA_E_CUDA;
 
-    Job j{};
+    Task task{};
+    task.g = *dg;
+    Job& j = task.job;
     j.seed = seed; j.i0 = i0; j.count = count; j.dom_pair = dom_pair; j.dom_path = dom_path; j.opt = (int)opt;
     j.ctr = (u64*)scratch;
     j.status = (int*)(scratch + 64);
     j.ovf_list = (uint64_t*)(scratch + kHeadBytes);
     j.rec_s = s_dev; j.rec_z = z_dev; j.rec_sig = (u64*)sigma_dev; j.rec_len = len_dev;
     j.rec_nodes = nodes_dev; j.rec_cap = cap;
+    struct { uint64_t unit_start[2]; uint32_t ntasks; uint32_t pad; u64 work; } units = {{0, count}, 1u, 0u, 0ull};
+    if (cudaMemcpyAsync(scratch + kTaskOff, &task, sizeof(Task), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return MANTRA_E_CUDA;
+    if (cudaMemcpyAsync(scratch + kUnitOff, &units, sizeof(units), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return MANTRA_E_CUDA;
     ws.base = scratch + head;
     ws.stride = region;
-    if (launch_bfs(*dg, j, ws, grid, in_smem ? smem : 0, false, st) != cudaSuccess) return MANTRA_E_CUDA;
+    char* ub = scratch + kUnitOff;
+    if (launch_bfs((const Task*)(scratch + kTaskOff), (const uint64_t*)ub, (const uint32_t*)(ub + 16), (u64*)(ub + 24),
+                   ws, grid, in_smem ? smem : 0, false, st) != cudaSuccess)
+        return MANTRA_E_CUDA;
 
     u64 h[9];
     if (cudaMemcpyAsync(h, scratch, 72, cudaMemcpyDeviceToHost, st) != cudaSuccess) return MANTRA_E_CUDA;

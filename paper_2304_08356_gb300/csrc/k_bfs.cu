@@ -29,11 +29,14 @@ constexpr int BFS_NT = 1024;
 constexpr int BFS_NW = BFS_NT / 32;
 
 template <bool WIDE>
-__global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const DevGraph g, const Job job, const BfsWs ws) {
+__global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint64_t* unit_start,
+                                                   const uint32_t* ntasks_p, u64* work, const BfsWs ws) {
     typedef typename SigOps<WIDE>::T Sig;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const uint32_t n = g.n;
-    const uint32_t words = (g.A + 31) >> 5;
+    __shared__ __align__(16) Task sh_task;
+    __shared__ int sh_t;
+    const DevGraph& g = sh_task.g;
+    const Job& job = sh_task.job;
 
     char* region = ws.base + (size_t)blockIdx.x * ws.stride;
     Sig* sig = reinterpret_cast<Sig*>(region + ws.o_sig);
@@ -51,7 +54,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const DevGraph g, const Job j
 
     extern __shared__ uint32_t dyn_smem[];
     uint32_t* V = ws.bits_in_smem ? dyn_smem : reinterpret_cast<uint32_t*>(region + ws.o_bits);
-    uint32_t* N = V + words;
+    uint32_t* N = V + ws.bits_words;
 
     __shared__ uint32_t sm_scan[32];
     __shared__ u64 sm_scan64[32];
@@ -67,19 +70,34 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const DevGraph g, const Job j
     __shared__ u128 sh_sigma;
 
     if (ws.bits_in_smem) {
-        for (uint32_t w = tid; w < 2 * words; w += BFS_NT) V[w] = 0u;
+        for (uint32_t w = tid; w < 2 * ws.bits_words; w += BFS_NT) V[w] = 0u;
     }
-    u64 my_escan = 0, my_eadd = 0, my_snew = 0, my_fseg = 0;
+    const uint32_t ntasks = *ntasks_p;
     __syncthreads();
 
     for (;;) {
         if (tid == 0) {
-            sh_q = atomicAdd(job.ctr + C_WORK, 1ull);
+            const uint64_t u = atomicAdd(work, 1ull);
+            int t = -1;
+            if (ntasks > 0 && u < unit_start[ntasks]) {
+                t = task_of_unit(unit_start, ntasks, u);
+                sh_q = u - unit_start[t];
+            }
+            sh_t = t;
             sh_found = 0; sh_ovf = 0; sh_err = 0; sh_d = 0; sh_len = 0; sh_sigma = 0;
         }
         __syncthreads();
+        if (sh_t < 0) break;
+        if (wid == 0) {
+            const u64* src = reinterpret_cast<const u64*>(tasks + sh_t);
+            u64* dst = reinterpret_cast<u64*>(&sh_task);
+            for (uint32_t w = lane; w < sizeof(Task) / 8; w += 32) dst[w] = src[w];
+        }
+        __syncthreads();
+        const uint32_t n = g.n;
+        const uint32_t words = (g.A + 31) >> 5;
+        u64 my_escan = 0, my_eadd = 0, my_snew = 0, my_fseg = 0;
         const uint64_t q = sh_q;
-        if (q >= job.count) break;
         const uint64_t i = job.idx_list ? job.idx_list[q] : job.i0 + q;
 
         uint32_t s, z;
@@ -488,17 +506,18 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const DevGraph g, const Job j
         if (stats) {
             for (uint32_t w = tid; w < (n + 31) / 32; w += BFS_NT) VB[w] = 0u;
         }
+        if (my_escan) atomicAdd(job.ctr + C_ESCAN, my_escan);
+        if (my_eadd) atomicAdd(job.ctr + C_EADD, my_eadd);
+        if (my_snew) atomicAdd(job.ctr + C_SNEW, my_snew);
+        if (my_fseg) atomicAdd(job.ctr + C_FSEG, my_fseg);
         __syncthreads();
     }
-    if (my_escan) atomicAdd(job.ctr + C_ESCAN, my_escan);
-    if (my_eadd) atomicAdd(job.ctr + C_EADD, my_eadd);
-    if (my_snew) atomicAdd(job.ctr + C_SNEW, my_snew);
-    if (my_fseg) atomicAdd(job.ctr + C_FSEG, my_fseg);
 }
 
 // Host-side launch helpers -------------------------------------------------
 
 size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws) {
+    ws->bits_words = (A + 31) / 32;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t o = 0;
     ws->o_sig = o;     o = al(o + (size_t)A * 16);
@@ -527,10 +546,10 @@ cudaError_t bfs_configure(size_t smem) {
     return cudaFuncSetAttribute(k_bfs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t launch_bfs(const DevGraph& g, const Job& job, const BfsWs& ws, int grid, size_t smem, bool wide,
-                       cudaStream_t st) {
-    if (wide) k_bfs<true><<<grid, BFS_NT, smem, st>>>(g, job, ws);
-    else k_bfs<false><<<grid, BFS_NT, smem, st>>>(g, job, ws);
+cudaError_t launch_bfs(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
+                       const BfsWs& ws, int grid, size_t smem, bool wide, cudaStream_t st) {
+    if (wide) k_bfs<true><<<grid, BFS_NT, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+    else k_bfs<false><<<grid, BFS_NT, smem, st>>>(tasks, unit_start, ntasks, work, ws);
     return cudaGetLastError();
 }
 

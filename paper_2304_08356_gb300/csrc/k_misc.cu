@@ -4,44 +4,56 @@
 
 namespace mantra {
 
-constexpr int RED_NT = 1024;
+constexpr int RED_NT = 512;
 
-// Block j < c: rowmax[j] = max_v S[j][v] (the sup over all nodes, nodes never
-// hit contribute 0; no absolute value -- paper Sec. 3 c-MCERA).
-// Block c: out_hmax = max_v hits[v] (empirical wimpy variance numerator).
-__global__ void __launch_bounds__(RED_NT) k_round_reduce(const int* S, const u64* hits, uint32_t n, uint32_t c,
-                                                          long long* rowmax, u64* hmax) {
+// One reduction row: rows 0..c-1 are S[j][*] (max over all n nodes -- nodes
+// never hit contribute 0, no absolute value: the sup of the c-MCERA, paper
+// Sec. 3); row c is hits[*] (its max is the empirical wimpy variance's
+// numerator).  row_start[p] is the first row of problem p (np + 1 entries).
+__global__ void __launch_bounds__(RED_NT) k_round_reduce(const ReduceItem* items, const uint32_t* row_start,
+                                                          const uint32_t* np_p) {
     __shared__ long long red_i[RED_NT / 32];
     __shared__ u64 red_u[RED_NT / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const uint32_t j = blockIdx.x;
-    if (j < c) {
-        const int* row = S + (size_t)j * n;
-        int mx = INT_MIN;
-        for (uint32_t v = tid; v < n; v += RED_NT) mx = max(mx, row[v]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
-        if (lane == 0) red_i[wid] = mx;
-        __syncthreads();
-        if (wid == 0) {
-            long long x = (lane < RED_NT / 32) ? red_i[lane] : (long long)INT_MIN;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
-            if (lane == 0) rowmax[j] = x;
+    const uint32_t np = *np_p;
+    const uint32_t rows = np ? row_start[np] : 0;
+    for (uint32_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        uint32_t lo = 0, hi = np;                       // row_start[lo] <= row < row_start[hi]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (row_start[mid] <= row) lo = mid; else hi = mid;
         }
-    } else {
-        u64 mx = 0;
-        for (uint32_t v = tid; v < n; v += RED_NT) mx = max(mx, hits[v]);
+        const ReduceItem it = items[lo];
+        const uint32_t j = row - row_start[lo];
+        if (j < it.c) {
+            const int* r = it.S + (size_t)j * it.n;
+            int mx = INT_MIN;
+            for (uint32_t v = tid; v < it.n; v += RED_NT) mx = max(mx, r[v]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
-        if (lane == 0) red_u[wid] = mx;
-        __syncthreads();
-        if (wid == 0) {
-            u64 x = (lane < RED_NT / 32) ? red_u[lane] : 0ull;
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+            if (lane == 0) red_i[wid] = mx;
+            __syncthreads();
+            if (wid == 0) {
+                long long x = (lane < RED_NT / 32) ? red_i[lane] : (long long)INT_MIN;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
-            if (lane == 0) *hmax = x;
+                for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
+                if (lane == 0) it.rowmax[j] = x;
+            }
+        } else {
+            u64 mx = 0;
+            for (uint32_t v = tid; v < it.n; v += RED_NT) mx = max(mx, it.hits[v]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+            if (lane == 0) red_u[wid] = mx;
+            __syncthreads();
+            if (wid == 0) {
+                u64 x = (lane < RED_NT / 32) ? red_u[lane] : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
+                if (lane == 0) *it.hmax = x;
+            }
         }
+        __syncthreads();
     }
 }
 
@@ -51,9 +63,9 @@ __global__ void k_normalise(const u64* hits, uint32_t n, uint64_t r, double* est
     if (v < n) est[v] = (double)hits[v] / (double)r;
 }
 
-cudaError_t launch_round_reduce(const int* S, const u64* hits, uint32_t n, uint32_t c, long long* rowmax, u64* hmax,
+cudaError_t launch_round_reduce(const ReduceItem* items, const uint32_t* row_start, const uint32_t* np, int grid,
                                 cudaStream_t st) {
-    k_round_reduce<<<c + 1, RED_NT, 0, st>>>(S, hits, n, c, rowmax, hmax);
+    k_round_reduce<<<grid, RED_NT, 0, st>>>(items, row_start, np);
     return cudaGetLastError();
 }
 

@@ -25,25 +25,47 @@ constexpr int PFM_NT = 128;
 constexpr int PFM_ILP = 8;
 
 template <bool WIDE>
-__global__ void __launch_bounds__(PFM_NT) k_pfm(const DevGraph g, const Job job, const PfmWs ws) {
+__global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_t* unit_start,
+                                                const uint32_t* ntasks_p, u64* work, const PfmWs ws) {
     typedef typename SigOps<WIDE>::T Sig;
     const uint32_t FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const uint64_t gw = ((uint64_t)blockIdx.x * PFM_NT + threadIdx.x) >> 5;
-    const uint32_t n = g.n;
     char* region = ws.base + gw * ws.stride;
     uint32_t* fa = reinterpret_cast<uint32_t*>(region + ws.o_fa) + lane;     // fa[v * 32]
     Sig* sig = reinterpret_cast<Sig*>(region + ws.o_sig) + lane;             // sig[v * 32]
     uint32_t* hop = reinterpret_cast<uint32_t*>(region + ws.o_hop) + lane;   // hop[v * 32]
-    uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path) + (size_t)lane * (n + 2);
-    const bool stats = job.stats != 0;
-    u64 my_escan = 0, my_eadd = 0;
+    uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path) + (size_t)lane * (ws.n_cap + 2);
+    __shared__ __align__(16) Task sh_tasks[PFM_NT / 32];
+    Task& T = sh_tasks[threadIdx.x >> 5];
+    const DevGraph& g = T.g;
+    const Job& job = T.job;
+    const uint32_t ntasks = *ntasks_p;
 
     for (;;) {
-        uint64_t q0 = 0;
-        if (lane == 0) q0 = atomicAdd(job.ctr + C_WORK, 32ull);
-        q0 = __shfl_sync(FULL, q0, 0);
-        if (q0 >= job.count) break;
+        int t = -1;
+        uint64_t unit = 0;
+        if (lane == 0) {
+            const uint64_t u = atomicAdd(work, 1ull);
+            if (ntasks > 0 && u < unit_start[ntasks]) {
+                t = task_of_unit(unit_start, ntasks, u);
+                unit = u - unit_start[t];
+            }
+        }
+        t = __shfl_sync(FULL, t, 0);
+        unit = __shfl_sync(FULL, unit, 0);
+        if (t < 0) break;
+        __syncwarp();
+        {
+            const u64* src = reinterpret_cast<const u64*>(tasks + t);
+            u64* dst = reinterpret_cast<u64*>(&T);
+            for (uint32_t w = lane; w < sizeof(Task) / 8; w += 32) dst[w] = src[w];
+        }
+        __syncwarp();
+        const uint32_t n = g.n;
+        const bool stats = job.stats != 0;
+        u64 my_escan = 0, my_eadd = 0;
+        const uint64_t q0 = unit * 32;
         const uint64_t q = q0 + lane;
         const bool have = q < job.count;
         const uint64_t i = have ? (job.idx_list ? job.idx_list[q] : job.i0 + q) : 0;
@@ -148,6 +170,15 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const DevGraph g, const Job job,
             }
         }
         __syncwarp();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            my_escan += __shfl_xor_sync(FULL, my_escan, o);
+            my_eadd += __shfl_xor_sync(FULL, my_eadd, o);
+        }
+        if (lane == 0) {
+            if (my_escan) atomicAdd(job.ctr + C_ESCAN, my_escan);
+            if (my_eadd) atomicAdd(job.ctr + C_EADD, my_eadd);
+        }
 
         if (stats) {
             uint32_t dloc = 0;
@@ -228,20 +259,12 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const DevGraph g, const Job job,
         }
         __syncwarp();
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_escan += __shfl_xor_sync(FULL, my_escan, o);
-        my_eadd += __shfl_xor_sync(FULL, my_eadd, o);
-    }
-    if (lane == 0) {
-        if (my_escan) atomicAdd(job.ctr + C_ESCAN, my_escan);
-        if (my_eadd) atomicAdd(job.ctr + C_EADD, my_eadd);
-    }
 }
 
 // Per-warp region: 32 lanes' state rows plus one path buffer per lane.
 size_t pfm_region_bytes(uint32_t n, PfmWs* ws) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    ws->n_cap = n;
     size_t o = 0;
     ws->o_fa = o;   o = al(o + (size_t)n * 32 * 4);
     ws->o_sig = o;  o = al(o + (size_t)n * 32 * 16);
@@ -252,9 +275,10 @@ size_t pfm_region_bytes(uint32_t n, PfmWs* ws) {
 
 int pfm_threads() { return PFM_NT; }
 
-cudaError_t launch_pfm(const DevGraph& g, const Job& job, const PfmWs& ws, int grid, bool wide, cudaStream_t st) {
-    if (wide) k_pfm<true><<<grid, PFM_NT, 0, st>>>(g, job, ws);
-    else k_pfm<false><<<grid, PFM_NT, 0, st>>>(g, job, ws);
+cudaError_t launch_pfm(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
+                       const PfmWs& ws, int grid, bool wide, cudaStream_t st) {
+    if (wide) k_pfm<true><<<grid, PFM_NT, 0, st>>>(tasks, unit_start, ntasks, work, ws);
+    else k_pfm<false><<<grid, PFM_NT, 0, st>>>(tasks, unit_start, ntasks, work, ws);
     return cudaGetLastError();
 }
 

@@ -77,6 +77,24 @@ struct Job {
     u64* dmax;
 };
 
+// One entry of a launch's task table: a graph and a range of its samples.
+struct Task {
+    DevGraph g;
+    Job job;
+};
+static_assert(sizeof(Task) % 8 == 0, "Task is copied as 8-byte words");
+
+// Task of work unit u: the last t with unit_start[t] <= u (unit_start ascending,
+// ntasks + 1 entries).
+__device__ __forceinline__ int task_of_unit(const uint64_t* unit_start, uint32_t ntasks, uint64_t u) {
+    uint32_t lo = 0, hi = ntasks;          // unit_start[lo] <= u < unit_start[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (unit_start[mid] <= u) lo = mid; else hi = mid;
+    }
+    return (int)lo;
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), device side.
 // Counter (i_lo, i_hi, domain, attempt), key (seed_lo, seed_hi).
@@ -334,6 +352,7 @@ struct BfsWs {
     size_t stride;
     size_t o_sig, o_fc, o_f, o_ft, o_lev, o_segb, o_segu, o_csseg, o_csfirst, o_csoff, o_path, o_bits, o_vb;
     int bits_in_smem;    // visited / next bitmaps in dynamic shared memory
+    uint32_t bits_words; // capacity of each bitmap (words): ceil(A_max / 32)
 };
 
 // Per-warp scratch of the pfm search kernel.
@@ -341,17 +360,30 @@ struct PfmWs {
     char* base;          // warp w uses base + w * stride
     size_t stride;
     size_t o_fa, o_sig, o_hop, o_path;
+    uint32_t n_cap;      // node capacity of a region (largest graph of the launch)
 };
 
 size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws);
 size_t bfs_smem_bytes(uint32_t A);
 cudaError_t bfs_configure(size_t smem);
-cudaError_t launch_bfs(const DevGraph& g, const Job& job, const BfsWs& ws, int grid, size_t smem, bool wide,
-                       cudaStream_t st);
+// Task-table launches: work unit u of the launch belongs to task
+// task_of_unit(unit_start, *ntasks, u); the first unused unit ends a CTA/warp.
+// sh/sfm: one unit per sample; pfm: one unit per 32 consecutive samples of a task.
+cudaError_t launch_bfs(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
+                       const BfsWs& ws, int grid, size_t smem, bool wide, cudaStream_t st);
 size_t pfm_region_bytes(uint32_t n, PfmWs* ws);
 int pfm_threads();
-cudaError_t launch_pfm(const DevGraph& g, const Job& job, const PfmWs& ws, int grid, bool wide, cudaStream_t st);
-cudaError_t launch_round_reduce(const int* S, const u64* hits, uint32_t n, uint32_t c, long long* rowmax, u64* hmax,
+cudaError_t launch_pfm(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
+                       const PfmWs& ws, int grid, bool wide, cudaStream_t st);
+// One problem of a multi-problem round reduction.
+struct ReduceItem {
+    const int* S;        // c rows of n (unused when c = 0)
+    const u64* hits;     // n
+    uint32_t n, c;
+    long long* rowmax;   // c results: max_v S[j][v]
+    u64* hmax;           // max_v hits[v]
+};
+cudaError_t launch_round_reduce(const ReduceItem* items, const uint32_t* row_start, const uint32_t* np, int grid,
                                 cudaStream_t st);
 cudaError_t launch_normalise(const u64* hits, uint32_t n, uint64_t r, double* est, cudaStream_t st);
 

@@ -19,7 +19,7 @@ OPT_NAMES = {"sh": SH, "sfm": SFM, "pfm": PFM}
 D_PAIR, D_PATH, D_RADE, D_BOOT_PAIR, D_BOOT_PATH, D_STATS = range(6)
 
 ERRORS = {0: "MANTRA_OK", 1: "MANTRA_E_INVAL", 2: "MANTRA_E_NOMEM", 3: "MANTRA_E_OVERFLOW", 4: "MANTRA_E_CUDA",
-          5: "MANTRA_E_TIMEOUT", 6: "MANTRA_E_CHECK", 7: "MANTRA_E_RNG"}
+          5: "MANTRA_E_TIMEOUT", 6: "MANTRA_E_CHECK", 7: "MANTRA_E_RNG", 8: "MANTRA_PENDING"}
 
 
 class MantraError(RuntimeError):
@@ -45,6 +45,12 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Problem(C.Structure):
+    _fields_ = [("graph", C.c_void_p), ("opt", C.c_int), ("eps", C.c_double), ("delta", C.c_double),
+                ("seed", C.c_uint64), ("opts", C.POINTER(Opts)), ("est_out", C.c_void_p), ("hits_out", C.c_void_p),
+                ("info", C.POINTER(Info)), ("status", C.c_int)]
+
+
 class TStats(C.Structure):
     _fields_ = [("d_lb", C.c_uint32), ("d_tau", C.c_uint32), ("zeta", C.c_double), ("psi", C.c_double),
                 ("rho", C.c_double), ("r", C.c_uint64), ("seconds", C.c_double)]
@@ -53,7 +59,7 @@ class TStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["mantra_graph_load", "mantra_graph_info", "mantra_graph_free", "mantra_estimate",
+EXPORTS = ["mantra_graph_load", "mantra_graph_info", "mantra_graph_free", "mantra_estimate", "mantra_estimate_batch",
            "mantra_temporal_stats", "mantra_sample_paths", "mantra_sample_paths_noalloc", "mantra_strerror"]
 
 _lib = None
@@ -74,6 +80,7 @@ def lib():
     L.mantra_graph_free.restype = None
     L.mantra_estimate.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_uint64, C.POINTER(Opts),
                                   C.c_void_p, C.c_void_p, C.POINTER(Info)]
+    L.mantra_estimate_batch.argtypes = [C.POINTER(Problem), C.c_uint32]
     L.mantra_temporal_stats.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_uint64, C.c_double,
                                         C.POINTER(TStats), u64p, C.c_uint32]
     L.mantra_sample_paths.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
@@ -175,3 +182,33 @@ class Graph:
             out.append((int(s[q]), int(z[q]), (int(sig[2 * q + 1]) << 64) | int(sig[2 * q]),
                         [int(x) for x in nodes[q * cap:q * cap + min(L, cap)]]))
         return out
+
+
+def estimate_batch(problems):
+    """mantra_estimate_batch over a list of dicts with keys graph (Graph), opt,
+    eps, delta, seed and optional c, growth, fixed_r, bootstrap, delta_sched.
+    Returns a list of (est, hits, info dict, status)."""
+    k = len(problems)
+    arr = (Problem * k)()
+    keep = []
+    outs = []
+    for x, p in enumerate(problems):
+        g = p["graph"]
+        o = Opts(p.get("c", 0), p.get("growth", 0.0), p.get("fixed_r", 0), p.get("bootstrap", 0),
+                 p.get("delta_sched", 0), 0, None)
+        est = np.zeros(g.n, np.float64)
+        hits = np.zeros(g.n, np.uint64)
+        info = Info()
+        keep += [o, est, hits, info]
+        arr[x].graph = g.h.value if isinstance(g.h, C.c_void_p) else g.h
+        arr[x].opt = _opt(p["opt"])
+        arr[x].eps = p["eps"]
+        arr[x].delta = p["delta"]
+        arr[x].seed = p["seed"]
+        arr[x].opts = C.pointer(o)
+        arr[x].est_out = est.ctypes.data
+        arr[x].hits_out = hits.ctypes.data
+        arr[x].info = C.pointer(info)
+        outs.append((est, hits, info))
+    lib().mantra_estimate_batch(arr, k)
+    return [(e, h, i.as_dict(), arr[x].status) for x, (e, h, i) in enumerate(outs)]

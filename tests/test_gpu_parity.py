@@ -263,3 +263,31 @@ def test_repeatable(M):
     b = g.estimate(0, 0.05, 0.1, 11)
     assert np.array_equal(a[1], b[1]) and a[2]["r"] == b[2]["r"]
 
+
+
+def test_batch_equals_solo_and_oracle(M):
+    """mantra_estimate_batch: uneven graphs, mixed optimalities and eps in one
+    batch; every problem's result equals its solo mantra_estimate (bit for
+    bit) and, for the small ones, the oracle."""
+    specs = [(synth.chung_lu_bursty(n=600, m=9000, seed=41), 0, 0.08, 3),
+             (synth.chung_lu_bursty(n=1500, m=30000, seed=42), 2, 0.05, 4),
+             (synth.uniform_small(), 1, 0.06, 5),
+             (synth.chung_lu_bursty(n=900, m=18000, seed=43), 2, 0.1, 6),
+             (synth.chung_lu_bursty(n=3000, m=60000, seed=44), 1, 0.05, 7),
+             (synth.uniform_small(n=50, m=600, seed=9), 0, 0.1, 8)]
+    graphs = [M.Graph(*uvt) for uvt, _, _, _ in specs]
+    probs = [dict(graph=g, opt=o, eps=e, delta=0.1, seed=sd) for g, (_, o, e, sd) in zip(graphs, specs)]
+    probs.append(dict(graph=graphs[0], opt=2, eps=0.1, delta=0.1, seed=1, fixed_r=700))
+    res = M.estimate_batch(probs)
+    for p, (est, hits, info, st) in zip(probs, res):
+        assert st == 0
+        e2, h2, i2 = p["graph"].estimate(p["opt"], p["eps"], p["delta"], p["seed"], fixed_r=p.get("fixed_r", 0))
+        assert np.array_equal(hits, h2) and np.array_equal(est.view(np.uint64), e2.view(np.uint64))
+        for k in ("r", "rounds", "omega", "s1", "rade_num", "max_hits", "sum_int_len"):
+            assert info[k] == i2[k], k
+    for x in (0, 2, 5, 6):
+        (u, v, t) = specs[min(x, 5)][0] if x < 6 else specs[0][0]
+        p = probs[x]
+        o = O.Graph(u, v, t, n=p["graph"].n)
+        _, oh, oi = o.estimate(p["opt"], p["eps"], p["delta"], p["seed"], fixed_r=p.get("fixed_r", 0))
+        assert np.array_equal(res[x][1], oh) and res[x][2]["r"] == oi["r"]
