@@ -23,6 +23,8 @@
 // else in per-CTA global scratch.
 #include "mantra_dev.cuh"
 
+#include <mutex>
+
 namespace mantra {
 
 constexpr int BFS_NT = 1024;
@@ -540,10 +542,18 @@ size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws) {
 
 size_t bfs_smem_bytes(uint32_t A) { return (size_t)2 * ((A + 31) / 32) * 4; }
 
+// Raises (never lowers) the kernels' dynamic shared-memory limit, so callers
+// with different graph sizes do not undo each other's setting.
 cudaError_t bfs_configure(size_t smem) {
+    static std::mutex mu;
+    static size_t configured = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem <= configured) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_bfs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_bfs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_bfs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) configured = smem;
+    return e;
 }
 
 cudaError_t launch_bfs(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
