@@ -37,8 +37,6 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     __shared__ __align__(16) Task sh_task;
     __shared__ int sh_t;
-    const DevGraph& g = sh_task.g;
-    const Job& job = sh_task.job;
 
     char* region = ws.base + (size_t)blockIdx.x * ws.stride;
     Sig* sig = reinterpret_cast<Sig*>(region + ws.o_sig);
@@ -96,6 +94,8 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
             for (uint32_t w = lane; w < sizeof(Task) / 8; w += 32) dst[w] = src[w];
         }
         __syncthreads();
+        const DevGraph& g = sh_task.g;
+        const Job& job = sh_task.job;
         const uint32_t n = g.n;
         const uint32_t words = (g.A + 31) >> 5;
         u64 my_escan = 0, my_eadd = 0, my_snew = 0, my_fseg = 0;
@@ -145,16 +145,18 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                 uint32_t gbase = 0;
                 if (tid == 0) { sh_carry = (Sig)0; sh_scan_ovf = 0; }
                 __syncthreads();
+                const uint32_t* const g_slot_v = g.slot_v;
+                const uint32_t* const g_slot_t = g.slot_t;
                 for (uint32_t it = 0; it < L; it += BFS_NT) {
                     const uint32_t idx = it + tid;
                     uint32_t head = 1, u = 0;
                     Sig val = 0;
                     if (idx < L) {
                         const uint32_t a = Fk[idx];
-                        u = g.slot_v[a];
-                        Ft[idx] = g.slot_t[a];
+                        u = g_slot_v[a];
+                        Ft[idx] = g_slot_t[a];
                         val = sig[a];
-                        head = (idx == 0) || (g.slot_v[Fk[idx - 1]] != u);
+                        head = (idx == 0) || (g_slot_v[Fk[idx - 1]] != u);
                     }
                     const Sig run = block_segmented_scan<BFS_NT, Sig>(val, head, sm_segx, sm_segf, &sh_carry,
                                                                        &sh_scan_ovf);
@@ -173,6 +175,8 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                 __syncthreads();
                 // B2: candidate edge ranges per segment and their compaction
                 uint32_t cbase = 0, ebase = 0;
+                const uint32_t* const g_out_ptr = g.out_ptr;
+                const uint32_t* const g_out_t = g.out_t;
                 for (uint32_t it = 0; it < G; it += BFS_NT) {
                     const uint32_t gi = it + tid;
                     uint32_t cand = 0, first = 0;
@@ -180,9 +184,9 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                         const uint32_t fb = seg_b[gi];
                         const uint32_t u = seg_u[gi];
                         const uint32_t tmin = Ft[fb];
-                        const uint32_t lo = g.out_ptr[u], hi = g.out_ptr[u + 1];
-                        first = upper_bound_u32(g.out_t, lo, hi, tmin);
-                        const uint32_t last = lower_bound_u32(g.out_t, first, hi, tz);
+                        const uint32_t lo = g_out_ptr[u], hi = g_out_ptr[u + 1];
+                        first = upper_bound_u32(g_out_t, lo, hi, tmin);
+                        const uint32_t last = lower_bound_u32(g_out_t, first, hi, tz);
                         cand = last > first ? last - first : 0;
                     }
                     u64 tot;
@@ -204,10 +208,13 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
             if (!stats) {
                 const uint32_t zs = g.slot_ptr[z], ze = g.slot_ptr[z + 1];
                 const uint32_t e_lo = g.slot_in[zs], e_hi = g.slot_in[ze];
+                const uint32_t* const g_in_u = g.in_u;
+                const uint32_t* const g_in_slot = g.in_slot;
+                const uint32_t* const g_slot_t = g.slot_t;
                 for (uint32_t e = e_lo + tid; e < e_hi; e += BFS_NT) {
-                    const uint32_t w = g.in_u[e];
-                    const uint32_t a = g.in_slot[e];
-                    const uint32_t t = g.slot_t[a];
+                    const uint32_t w = g_in_u[e];
+                    const uint32_t a = g_in_slot[e];
+                    const uint32_t t = g_slot_t[a];
                     // segment of w (seg_u ascending)
                     uint32_t lo = 0, hi = G;
                     while (lo < hi) {
@@ -235,6 +242,8 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
             }
 
             // ---- push expansion of level k ----
+            const uint32_t* const g_out_slot = g.out_slot;
+            const uint32_t* const g_out_t2 = g.out_t;
             for (uint32_t base = (uint32_t)wid * 32u; base < E; base += BFS_NW * 32u) {
                 uint32_t h0 = 0;
                 if (lane == 0) {
@@ -255,10 +264,10 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                     }
                     const uint32_t gi = cs_seg[lo];
                     const uint32_t e = cs_first[lo] + (j - cs_off[lo]);
-                    const uint32_t a = g.out_slot[e];
+                    const uint32_t a = g_out_slot[e];
                     ++my_escan;
                     if (!((V[a >> 5] >> (a & 31)) & 1u)) {
-                        const uint32_t t = g.out_t[e];
+                        const uint32_t t = g_out_t2[e];
                         const uint32_t fb = seg_b[gi], fe = (gi + 1 < G) ? seg_b[gi + 1] : L;
                         uint32_t idx = fb;
                         if (fe - fb > 1) idx = lower_bound_u32(Ft, fb, fe, t) - 1;   // last Ft < t
@@ -295,6 +304,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
             const uint32_t fbase = lev[k + 1];
             uint32_t off = fbase + sm_wcnt[wid];
             uint32_t newv = 0;
+            const uint32_t* const g_slot_v2 = g.slot_v;
             for (uint32_t w0 = w_lo; w0 < w_hi; w0 += 32) {
                 const uint32_t w = w0 + lane;
                 uint32_t bits = (w < w_hi) ? N[w] : 0u;
@@ -313,7 +323,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                     const uint32_t a = w * 32u + b;
                     F[pos++] = a;
                     if (stats) {
-                        const uint32_t v = g.slot_v[a];
+                        const uint32_t v = g_slot_v2[a];
                         if (v != s) {
                             const uint32_t old = atomicOr(VB + (v >> 5), 1u << (v & 31));
                             if (!(old & (1u << (v & 31)))) ++newv;

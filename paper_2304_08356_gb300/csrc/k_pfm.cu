@@ -38,8 +38,6 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
     uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path) + (size_t)lane * (ws.n_cap + 2);
     __shared__ __align__(16) Task sh_tasks[PFM_NT / 32];
     Task& T = sh_tasks[threadIdx.x >> 5];
-    const DevGraph& g = T.g;
-    const Job& job = T.job;
     const uint32_t ntasks = *ntasks_p;
 
     for (;;) {
@@ -62,7 +60,12 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
             for (uint32_t w = lane; w < sizeof(Task) / 8; w += 32) dst[w] = src[w];
         }
         __syncwarp();
+        const DevGraph& g = T.g;
+        const Job& job = T.job;
         const uint32_t n = g.n;
+        const uint32_t* const st_u = g.st_u;   // hot pointers in registers
+        const uint32_t* const st_v = g.st_v;
+        const uint32_t* const st_t = g.st_t;
         const bool stats = job.stats != 0;
         u64 my_escan = 0, my_eadd = 0;
         const uint64_t q0 = unit * 32;
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
         for (uint32_t base = e_lo; base < e_hi; base += 32) {
             const uint32_t e = base + lane;
             uint32_t eu = 0, ev = 0, et = NONE;
-            if (e < e_hi) { eu = g.st_u[e]; ev = g.st_v[e]; et = g.st_t[e]; }
+            if (e < e_hi) { eu = st_u[e]; ev = st_v[e]; et = st_t[e]; }
             // lanes still scanning at this chunk's first time
             const uint32_t t0 = __shfl_sync(FULL, et, 0);
             const bool running = live && t0 <= te && t0 < fz;
