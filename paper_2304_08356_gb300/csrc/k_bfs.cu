@@ -73,6 +73,18 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
         for (uint32_t w = tid; w < 2 * ws.bits_words; w += BFS_NT) V[w] = 0u;
     }
     const uint32_t ntasks = *ntasks_p;
+    // per-thread work counters, added to the current task's counters when the
+    // CTA moves to another task and at exit
+    u64* flush_ctr = nullptr;
+    u64 my_escan = 0, my_eadd = 0, my_snew = 0, my_fseg = 0;
+    auto flush = [&]() {
+        if (!flush_ctr) return;
+        if (my_escan) atomicAdd(flush_ctr + C_ESCAN, my_escan);
+        if (my_eadd) atomicAdd(flush_ctr + C_EADD, my_eadd);
+        if (my_snew) atomicAdd(flush_ctr + C_SNEW, my_snew);
+        if (my_fseg) atomicAdd(flush_ctr + C_FSEG, my_fseg);
+        my_escan = my_eadd = my_snew = my_fseg = 0;
+    };
     __syncthreads();
 
     for (;;) {
@@ -98,7 +110,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
         const Job& job = sh_task.job;
         const uint32_t n = g.n;
         const uint32_t words = (g.A + 31) >> 5;
-        u64 my_escan = 0, my_eadd = 0, my_snew = 0, my_fseg = 0;
+        if (job.ctr != flush_ctr) { flush(); flush_ctr = job.ctr; }
         const uint64_t q = sh_q;
         const uint64_t i = job.idx_list ? job.idx_list[q] : job.i0 + q;
 
@@ -518,12 +530,9 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
         if (stats) {
             for (uint32_t w = tid; w < (n + 31) / 32; w += BFS_NT) VB[w] = 0u;
         }
-        if (my_escan) atomicAdd(job.ctr + C_ESCAN, my_escan);
-        if (my_eadd) atomicAdd(job.ctr + C_EADD, my_eadd);
-        if (my_snew) atomicAdd(job.ctr + C_SNEW, my_snew);
-        if (my_fseg) atomicAdd(job.ctr + C_FSEG, my_fseg);
         __syncthreads();
     }
+    flush();
 }
 
 // Host-side launch helpers -------------------------------------------------
