@@ -3,10 +3,12 @@
 Workload (default): Chung-Lu temporal graph, n = 20,000, degree exponent 2.3,
 500,000 bursty contacts (K ~ Geometric(0.3) per static edge, Exp(mean 1000)
 gaps, t in [0, 1e6]); progressive MCERA sampling at eps = 0.01, delta = 0.1,
-c = 25.  One step = one complete mantra_estimate (bootstrap, schedule, rounds
-until the stopping rule) for each of sh, sfm and pfm, with a fresh seed per
-step.  Metric: sampled (s,z) pairs per second, bootstrap and estimation
-samples of the three optimalities together.  Inputs are synthetic (the
+c = 25.  One step = one complete Algorithm 1 run (bootstrap, schedule, rounds
+until the stopping rule) for each of sh, sfm and pfm with a fresh seed per
+step, run as one mantra_estimate_batch (default) or as three mantra_estimate
+calls (--mode sequential; also timed after the main region on the same seeds).
+Metric: sampled (s,z) pairs per second, bootstrap and estimation samples of the
+three optimalities together.  Inputs are synthetic (the
 paper's data sets are not available).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -209,6 +211,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--opts", default="sh,sfm,pfm", help="optimalities per step (profiling subsets)")
+    ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
+                    help="batched: one mantra_estimate_batch over the optimalities per step; "
+                         "sequential: one mantra_estimate per optimality")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -236,13 +241,23 @@ def main():
     hits_dev = torch.empty(g.n, dtype=torch.int64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def step(seed):
+    def step_sequential(seed):
         infos = {}
         for name in OPTS:
             _, _, info = g.estimate(name, EPS, DELTA, seed, c=C_TRIALS, est_out=est_dev.data_ptr(),
                                     hits_out=hits_dev.data_ptr(), stream=stream.cuda_stream)
             infos[name] = info
         return infos
+
+    def step_batched(seed):
+        res = M.estimate_batch([dict(graph=g, opt=name, eps=EPS, delta=DELTA, seed=seed, c=C_TRIALS)
+                                for name in OPTS])
+        for (_, _, _, st) in res:
+            if st != 0:
+                raise M.MantraError(st, "mantra_estimate_batch")
+        return {name: r[2] for name, r in zip(OPTS, res)}
+
+    step = step_batched if args.mode == "batched" else step_sequential
 
     seed0 = 1_000_003 * (rank + 1)
     for w in range(args.warmup):
@@ -271,18 +286,34 @@ def main():
     samples_all = sum_over_ranks(float(samples), world)
     value = samples_all / t_max
 
-    # dominant kernel: search kernel time per optimality family
+    # sequential pass on the same seeds: one mantra_estimate per optimality, each
+    # tick running a single kernel family -- its tick times give the per-kernel
+    # durations of the roofline, and its rate is the plain (unbatched) figure
+    seq_infos, seq_ms = [], []
+    n_seq = min(args.steps, 2)
+    for k in range(n_seq):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        seq_infos.append(step_sequential(seed0 + 1000 + k))
+        e1.record(stream)
+        e1.synchronize()
+        seq_ms.append(e0.elapsed_time(e1))
+    seq_rate = sum(i["r"] + i["bootstrap"] for st in seq_infos for i in st.values()) / (sum(seq_ms) / 1000.0)
+
+    # dominant kernel: search time per optimality family (sequential pass)
     fam = {k: tuple(o for o in v_ if o in OPTS) for k, v_ in {"k_bfs": ("sh", "sfm"), "k_pfm": ("pfm",)}.items()}
     fam = {k: v_ for k, v_ in fam.items() if v_}
-    kms = {k: sum(st[o]["kernel_ms"] for st in infos_all for o in os_) for k, os_ in fam.items()}
-    kbytes = {k: sum(st[o]["alg_bytes"] for st in infos_all for o in os_) for k, os_ in fam.items()}
-    klaunch = {k: sum(st[o]["search_launches"] for st in infos_all for o in os_) for k, os_ in fam.items()}
+    kms = {k: sum(st[o]["kernel_ms"] for st in seq_infos for o in os_) for k, os_ in fam.items()}
+    kbytes = {k: sum(st[o]["alg_bytes"] for st in seq_infos for o in os_) for k, os_ in fam.items()}
+    klaunch = {k: sum(st[o]["search_launches"] for st in seq_infos for o in os_) for k, os_ in fam.items()}
     dom = max(kms, key=kms.get)
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = (kbytes[dom] / klaunch[dom]) / (kms[dom] / klaunch[dom] / 1000.0) / 1e9
     traffic = recorded_traffic(dom)
-    alg_gbps = sum(kbytes.values()) / (total_ms / 1000.0) / 1e9
+    alg_gbps = sum(st[o]["alg_bytes"] for st in infos_all for o in OPTS) / (total_ms / 1000.0) / 1e9
     edges = sum(st[o]["edges_scanned"] for st in infos_all for o in OPTS)
     launches = sum(st[o]["kernel_launches"] for st in infos_all for o in OPTS)
 
@@ -296,9 +327,14 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g2 = M.Graph(pin_u, pin_v, pin_t)
-        for name in OPTS:
-            est, hits, info = g2.estimate(name, EPS, DELTA, seed0 + 5000 + k, c=C_TRIALS)
-            e2e_n += info["r"] + info["bootstrap"]
+        if args.mode == "batched":
+            res = M.estimate_batch([dict(graph=g2, opt=name, eps=EPS, delta=DELTA, seed=seed0 + 5000 + k,
+                                         c=C_TRIALS) for name in OPTS])
+            e2e_n += sum(r[2]["r"] + r[2]["bootstrap"] for r in res)
+        else:
+            for name in OPTS:
+                est, hits, info = g2.estimate(name, EPS, DELTA, seed0 + 5000 + k, c=C_TRIALS)
+                e2e_n += info["r"] + info["bootstrap"]
         g2.free()
         e2e_s += time.perf_counter() - t0
     e2e_val = sum_over_ranks(float(e2e_n), world) / max(max_over_ranks(e2e_s, world), 1e-9)
@@ -324,9 +360,10 @@ def main():
                            "samples_per_step": samples / args.steps,
                            "per_opt_r": {o: [st[o]["r"] for st in infos_all] for o in OPTS}},
                 "secondary": {"temporal_edge_GBps": alg_gbps, "edges_per_s": edges / (total_ms / 1000.0),
-                              "kernel_ms": kms},
+                              "sequential_pairs_per_s": seq_rate, "sequential_kernel_ms": kms,
+                              "mode": args.mode},
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": traffic,
+                             "frac": achieved / peak, "traffic": traffic, "timing": "sequential pass, tick events",
                              "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -267,8 +267,12 @@ struct Engine {
         int optin = 0;
         CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         smem_optin = (size_t)optin;
-        CU(cudaStreamCreateWithFlags(&sa, cudaStreamNonBlocking));
-        CU(cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking));
+        // the pfm stream gets the higher priority: its small latency-bound blocks are
+        // placed first and the persistent sh/sfm CTAs take the remaining SMs
+        int lo_pri = 0, hi_pri = 0;
+        CU(cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri));
+        CU(cudaStreamCreateWithPriority(&sa, cudaStreamNonBlocking, lo_pri));
+        CU(cudaStreamCreateWithPriority(&sb, cudaStreamNonBlocking, hi_pri));
         CU(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
         CU(cudaEventCreate(&e_b0)); CU(cudaEventCreate(&e_b1));
