@@ -192,6 +192,41 @@ int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt, uint64_t 
                                 uint64_t* sigma_dev, uint32_t* len_dev, uint32_t* nodes_dev, uint32_t cap,
                                 void* stream);
 
+/* ---- Serving (continuous batching over resident graphs) ----
+ * A server owns a host thread that runs Algorithm 1 for many requests at
+ * once.  Requests queue in arrival order and are admitted while their device
+ * state (hits, Rademacher sums, estimates: about 16 + 4c bytes per node)
+ * fits `hbm_budget` bytes (0 = half of free device memory) and fewer than
+ * `max_active` (0 = 256) run; a request is always admitted when none is
+ * running.  Each tick launches the pending samples of every running request
+ * together; finished requests leave between ticks and queued ones join at the
+ * next tick.  A request's result equals mantra_estimate on the same
+ * arguments.  Graphs must stay loaded while their requests are pending. */
+typedef struct mantra_server mantra_server;
+
+int mantra_server_create(size_t hbm_budget, uint32_t max_active, mantra_server** out);
+
+/* Queues a request (opts: as mantra_estimate; out_device must be 0; stream is
+ * ignored).  req_id receives its id. */
+int mantra_server_submit(mantra_server* srv, const mantra_graph* g, mantra_opt opt, double eps, double delta,
+                         uint64_t seed, const mantra_opts* opts, uint64_t* req_id);
+
+/* MANTRA_PENDING while the request runs or waits; otherwise the request's
+ * status, with est_out (n doubles), hits_out (n, or NULL) and info (or NULL)
+ * filled when it is MANTRA_OK.  A finished request is retired by this call. */
+int mantra_server_poll(mantra_server* srv, uint64_t req_id, double* est_out, uint64_t* hits_out, mantra_info* info);
+
+/* As poll, blocking up to timeout_s seconds (<= 0: no limit). */
+int mantra_server_wait(mantra_server* srv, uint64_t req_id, double timeout_s, double* est_out, uint64_t* hits_out,
+                       mantra_info* info);
+
+/* Queue length, running requests, finished requests, ticks run, admitted footprint. */
+int mantra_server_stats(mantra_server* srv, uint64_t* queued, uint64_t* active, uint64_t* finished,
+                        uint64_t* ticks, uint64_t* bytes_in_use);
+
+/* Drops queued requests, lets running ones finish, stops the thread. */
+void mantra_server_destroy(mantra_server* srv);
+
 const char* mantra_strerror(int code);
 
 #ifdef __cplusplus

@@ -11,6 +11,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <thread>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -801,33 +804,37 @@ int problem_from(const mantra_graph* g, mantra_opt opt, double eps, double delta
 // Runs Algorithm 1 for every problem together: each tick carries the next
 // sample range of every unfinished problem.  Per-problem statuses are kept;
 // the return value is the first failure, or MANTRA_OK.
-int run_problems(Engine& E, std::vector<Problem*>& ps) {
-    int first_err = MANTRA_OK;
-    for (Problem* p : ps) {
-        if (p->status == MANTRA_OK) p->status = p->start(E);
-    }
+// One tick for every running problem of `ps`: each contributes its next
+// sample range; results advance each problem's state.  Returns false when no
+// problem had work.
+bool tick_problems(Engine& E, std::vector<Problem*>& ps) {
     std::vector<Problem*> act;
     std::vector<TickItem> items;
     std::vector<uint64_t*> ovfs;
-    while (true) {
-        act.clear(); items.clear(); ovfs.clear();
-        for (Problem* p : ps) {
-            if (p->status != MANTRA_OK || p->phase == Problem::DONE) continue;
-            TickItem it;
-            const int rc = p->item(E, &it);
-            if (rc != MANTRA_OK) { p->status = rc; continue; }
-            act.push_back(p); items.push_back(it); ovfs.push_back(p->ovf);
-        }
-        if (act.empty()) break;
-        TickResult R;
-        const int rc = run_tick_full(E, items, ovfs.data(), &R);
-        if (rc != MANTRA_OK) { for (Problem* p : act) p->status = rc; break; }
-        for (size_t x = 0; x < act.size(); ++x) {
-            if (R.status[x] != MANTRA_OK) { act[x]->status = R.status[x]; continue; }
-            const int st = act[x]->consume(E, R.slot[x].data(), R.tot[x]);
-            if (st != MANTRA_OK) act[x]->status = st;
-        }
+    for (Problem* p : ps) {
+        if (p->status != MANTRA_OK || p->phase == Problem::DONE) continue;
+        TickItem it;
+        const int rc = p->item(E, &it);
+        if (rc != MANTRA_OK) { p->status = rc; continue; }
+        act.push_back(p); items.push_back(it); ovfs.push_back(p->ovf);
     }
+    if (act.empty()) return false;
+    TickResult R;
+    const int rc = run_tick_full(E, items, ovfs.data(), &R);
+    if (rc != MANTRA_OK) {
+        for (Problem* p : act) p->status = rc;
+        return true;
+    }
+    for (size_t x = 0; x < act.size(); ++x) {
+        if (R.status[x] != MANTRA_OK) { act[x]->status = R.status[x]; continue; }
+        const int st = act[x]->consume(E, R.slot[x].data(), R.tot[x]);
+        if (st != MANTRA_OK) act[x]->status = st;
+    }
+    return true;
+}
+
+// Outputs of finished (or failed) problems, buffers returned to the pool.
+void finish_problems(Engine& E, std::vector<Problem*>& ps) {
     for (Problem* p : ps)
         if (p->status == MANTRA_OK) p->status = p->finish(E);
     const cudaError_t se = cudaStreamSynchronize(E.sa);
@@ -836,9 +843,21 @@ int run_problems(Engine& E, std::vector<Problem*>& ps) {
         p->I.seconds = now_s() - p->t0;
         if (p->info_out && p->status == MANTRA_OK) *p->info_out = p->I;
         p->release(E);
-        if (first_err == MANTRA_OK && p->status != MANTRA_OK) first_err = p->status;
     }
-    return first_err;
+}
+
+// Runs Algorithm 1 for every problem together: each tick carries the next
+// sample range of every unfinished problem.  Per-problem statuses are kept;
+// the return value is the first failure, or MANTRA_OK.
+int run_problems(Engine& E, std::vector<Problem*>& ps) {
+    for (Problem* p : ps)
+        if (p->status == MANTRA_OK) p->status = p->start(E);
+    while (tick_problems(E, ps)) {
+    }
+    finish_problems(E, ps);
+    for (Problem* p : ps)
+        if (p->status != MANTRA_OK) return p->status;
+    return MANTRA_OK;
 }
 
 // Orders the engine's streams after a caller stream, and the caller stream
@@ -868,6 +887,106 @@ int current_engine(const mantra_graph* g, Engine** E) {
         if (cudaGetDevice(&dev) != cudaSuccess) return MANTRA_E_CUDA;
     }
     return engine_for(dev, E);
+}
+
+// ---------------------------------------------------------------------------
+// Serving loop (continuous batching).  Requests wait in a FIFO queue and are
+// admitted while their device-state footprint fits the budget (one request is
+// always admitted when none is running).  Every tick carries the pending
+// sample range of every running request; finished requests leave between
+// ticks and queued ones join at the next tick.  Results wait on the host
+// until polled.
+// ---------------------------------------------------------------------------
+struct Request {
+    uint64_t id = 0;
+    Problem p;
+    std::vector<double> est;
+    std::vector<uint64_t> hits;
+    mantra_info info{};
+    int state = 0;            // 0 queued, 1 running, 2 finished
+    bool started = false;
+    size_t footprint = 0;
+};
+
+struct Server {
+    Engine* E = nullptr;
+    size_t budget = 0;
+    uint32_t max_active = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> queue;
+    std::vector<Request*> active;
+    std::map<uint64_t, Request*> reqs;
+    size_t used = 0;
+    uint64_t next_id = 1, ticks = 0, finished = 0;
+    bool stop = false;
+    std::thread th;
+
+    void loop() {
+        std::unique_lock<std::mutex> lk(mu);
+        while (true) {
+            while (!queue.empty() && active.size() < max_active) {
+                Request* r = queue.front();
+                if (!active.empty() && used + r->footprint > budget) break;
+                queue.pop_front();
+                r->state = 1;
+                used += r->footprint;
+                active.push_back(r);
+            }
+            if (active.empty()) {
+                if (stop) break;
+                cv_work.wait(lk);
+                continue;
+            }
+            std::vector<Request*> batch = active;
+            lk.unlock();
+            {
+                std::lock_guard<std::mutex> elk(E->mu);
+                std::vector<Problem*> ps;
+                for (Request* r : batch) {
+                    if (!r->started) {
+                        r->started = true;
+                        if (r->p.status == MANTRA_OK) r->p.status = r->p.start(*E);
+                    }
+                    ps.push_back(&r->p);
+                }
+                tick_problems(*E, ps);
+                std::vector<Problem*> fin;
+                for (Request* r : batch)
+                    if (r->p.status != MANTRA_OK || r->p.phase == Problem::DONE) fin.push_back(&r->p);
+                if (!fin.empty()) finish_problems(*E, fin);
+            }
+            lk.lock();
+            ++ticks;
+            for (auto it = active.begin(); it != active.end();) {
+                Request* r = *it;
+                if (r->p.status != MANTRA_OK || r->p.phase == Problem::DONE) {
+                    r->state = 2;
+                    used -= r->footprint;
+                    ++finished;
+                    it = active.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+            cv_done.notify_all();
+        }
+    }
+};
+
+// Copies a finished request's outputs and retires it (server lock held).
+int take_result(Server* S, std::map<uint64_t, Request*>::iterator it, double* est_out, uint64_t* hits_out,
+                mantra_info* info) {
+    Request* r = it->second;
+    const int st = r->p.status;
+    if (st == MANTRA_OK) {
+        if (est_out) std::memcpy(est_out, r->est.data(), r->est.size() * 8);
+        if (hits_out) std::memcpy(hits_out, r->hits.data(), r->hits.size() * 8);
+        if (info) *info = r->info;
+    }
+    S->reqs.erase(it);
+    delete r;
+    return st;
 }
 
 }  // namespace
@@ -1103,6 +1222,115 @@ int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, ui
     }
     E->pool.put(d, bytes);
     return rc;
+}
+
+int mantra_server_create(size_t hbm_budget, uint32_t max_active, mantra_server** out) {
+    if (!out) return MANTRA_E_INVAL;
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MANTRA_E_CUDA;
+    Engine* E = nullptr;
+    int rc = engine_for(dev, &E);
+    if (rc != MANTRA_OK) return rc;
+    Server* S = new (std::nothrow) Server();
+    if (!S) return MANTRA_E_NOMEM;
+    S->E = E;
+    S->budget = hbm_budget ? hbm_budget : free_device_bytes() / 2;
+    S->max_active = max_active ? max_active : 256;
+    try {
+        S->th = std::thread([S, dev]() {
+            cudaSetDevice(dev);
+            S->loop();
+        });
+    } catch (...) {
+        delete S;
+        return MANTRA_E_NOMEM;
+    }
+    *out = reinterpret_cast<mantra_server*>(S);
+    return MANTRA_OK;
+}
+
+int mantra_server_submit(mantra_server* srv, const mantra_graph* g, mantra_opt opt, double eps, double delta,
+                         uint64_t seed, const mantra_opts* opts, uint64_t* req_id) {
+    Server* S = reinterpret_cast<Server*>(srv);
+    if (!S || !g || !req_id) return MANTRA_E_INVAL;
+    if (opts && opts->out_device) return MANTRA_E_INVAL;     // served results are host arrays
+    Request* r = new (std::nothrow) Request();
+    if (!r) return MANTRA_E_NOMEM;
+    try {
+        r->est.assign(g->n, 0.0);
+        r->hits.assign(g->n, 0);
+    } catch (...) {
+        delete r;
+        return MANTRA_E_NOMEM;
+    }
+    const int rc = problem_from(g, opt, eps, delta, seed, opts, r->est.data(), r->hits.data(), &r->info, &r->p);
+    if (rc != MANTRA_OK) { delete r; return rc; }
+    r->footprint = r->p.footprint();
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) { delete r; return MANTRA_E_INVAL; }
+    r->id = S->next_id++;
+    S->reqs[r->id] = r;
+    S->queue.push_back(r);
+    *req_id = r->id;
+    S->cv_work.notify_one();
+    return MANTRA_OK;
+}
+
+int mantra_server_poll(mantra_server* srv, uint64_t req_id, double* est_out, uint64_t* hits_out, mantra_info* info) {
+    Server* S = reinterpret_cast<Server*>(srv);
+    if (!S) return MANTRA_E_INVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(req_id);
+    if (it == S->reqs.end()) return MANTRA_E_INVAL;
+    if (it->second->state != 2) return MANTRA_PENDING;
+    return take_result(S, it, est_out, hits_out, info);
+}
+
+int mantra_server_wait(mantra_server* srv, uint64_t req_id, double timeout_s, double* est_out, uint64_t* hits_out,
+                       mantra_info* info) {
+    Server* S = reinterpret_cast<Server*>(srv);
+    if (!S) return MANTRA_E_INVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(req_id);
+    if (it == S->reqs.end()) return MANTRA_E_INVAL;
+    Request* r = it->second;
+    const auto deadline = std::chrono::steady_clock::now() +
+                          std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                              std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 1e9));
+    while (r->state != 2) {
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && r->state != 2) return MANTRA_PENDING;
+    }
+    return take_result(S, S->reqs.find(req_id), est_out, hits_out, info);
+}
+
+int mantra_server_stats(mantra_server* srv, uint64_t* queued, uint64_t* active, uint64_t* finished,
+                        uint64_t* ticks, uint64_t* bytes_in_use) {
+    Server* S = reinterpret_cast<Server*>(srv);
+    if (!S) return MANTRA_E_INVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (queued) *queued = S->queue.size();
+    if (active) *active = S->active.size();
+    if (finished) *finished = S->finished;
+    if (ticks) *ticks = S->ticks;
+    if (bytes_in_use) *bytes_in_use = S->used;
+    return MANTRA_OK;
+}
+
+void mantra_server_destroy(mantra_server* srv) {
+    Server* S = reinterpret_cast<Server*>(srv);
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        // queued requests are dropped; running ones finish
+        for (Request* r : S->queue) { S->reqs.erase(r->id); delete r; }
+        S->queue.clear();
+        S->cv_work.notify_all();
+    }
+    if (S->th.joinable()) S->th.join();
+    for (auto& kv : S->reqs) delete kv.second;
+    delete S;
 }
 
 }  // extern "C"

@@ -60,7 +60,9 @@ class TStats(C.Structure):
 
 
 EXPORTS = ["mantra_graph_load", "mantra_graph_info", "mantra_graph_free", "mantra_estimate", "mantra_estimate_batch",
-           "mantra_temporal_stats", "mantra_sample_paths", "mantra_sample_paths_noalloc", "mantra_strerror"]
+           "mantra_temporal_stats", "mantra_sample_paths", "mantra_sample_paths_noalloc", "mantra_strerror",
+           "mantra_server_create", "mantra_server_submit", "mantra_server_poll", "mantra_server_wait",
+           "mantra_server_stats", "mantra_server_destroy"]
 
 _lib = None
 
@@ -88,6 +90,14 @@ def lib():
     L.mantra_sample_paths_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
                                               C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p, C.c_uint32, C.c_void_p]
+    L.mantra_server_create.argtypes = [C.c_size_t, C.c_uint32, C.POINTER(C.c_void_p)]
+    L.mantra_server_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_uint64,
+                                       C.POINTER(Opts), C.POINTER(C.c_uint64)]
+    L.mantra_server_poll.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.POINTER(Info)]
+    L.mantra_server_wait.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_void_p, C.c_void_p, C.POINTER(Info)]
+    L.mantra_server_stats.argtypes = [C.c_void_p] + [C.POINTER(C.c_uint64)] * 5
+    L.mantra_server_destroy.argtypes = [C.c_void_p]
+    L.mantra_server_destroy.restype = None
     L.mantra_strerror.restype = C.c_char_p
     L.mantra_strerror.argtypes = [C.c_int]
     _lib = L
@@ -212,3 +222,59 @@ def estimate_batch(problems):
         outs.append((est, hits, info))
     lib().mantra_estimate_batch(arr, k)
     return [(e, h, i.as_dict(), arr[x].status) for x, (e, h, i) in enumerate(outs)]
+
+
+PENDING = 8
+
+
+class Server:
+    """Continuous-batching request server (mantra_server_*)."""
+
+    def __init__(self, hbm_budget: int = 0, max_active: int = 0):
+        h = C.c_void_p()
+        _chk(lib().mantra_server_create(hbm_budget, max_active, C.byref(h)), "mantra_server_create")
+        self.h = h
+        self._n = {}
+
+    def submit(self, graph, opt, eps, delta, seed, c=0, growth=0.0, fixed_r=0, bootstrap=0, delta_sched=0):
+        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, None)
+        rid = C.c_uint64()
+        _chk(lib().mantra_server_submit(self.h, graph.h, _opt(opt), eps, delta, seed, C.byref(o), C.byref(rid)),
+             "mantra_server_submit")
+        self._n[rid.value] = graph.n
+        return rid.value
+
+    def _result(self, rc, rid, est, hits, info):
+        if rc == PENDING:
+            return None
+        self._n.pop(rid, None)
+        _chk(rc, "mantra_server result")
+        return est, hits, info.as_dict()
+
+    def poll(self, rid):
+        n = self._n[rid]
+        est = np.zeros(n, np.float64); hits = np.zeros(n, np.uint64); info = Info()
+        rc = lib().mantra_server_poll(self.h, rid, est.ctypes.data, hits.ctypes.data, C.byref(info))
+        return self._result(rc, rid, est, hits, info)
+
+    def wait(self, rid, timeout=0.0):
+        n = self._n[rid]
+        est = np.zeros(n, np.float64); hits = np.zeros(n, np.uint64); info = Info()
+        rc = lib().mantra_server_wait(self.h, rid, timeout, est.ctypes.data, hits.ctypes.data, C.byref(info))
+        return self._result(rc, rid, est, hits, info)
+
+    def stats(self):
+        v = [C.c_uint64() for _ in range(5)]
+        _chk(lib().mantra_server_stats(self.h, *[C.byref(x) for x in v]), "mantra_server_stats")
+        return dict(zip(("queued", "active", "finished", "ticks", "bytes_in_use"), [x.value for x in v]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mantra_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
