@@ -36,6 +36,7 @@ if ROOT not in sys.path:
 
 EPS, DELTA, C_TRIALS = 0.01, 0.1, 25
 OPTS = ("sh", "sfm", "pfm")
+OPTS_ALL = ("sh", "sfm", "pfm")
 METRIC = "sampled pairs/sec at eps=0.01 (sh+sfm+pfm)"
 WORKLOAD = "chung_lu_bursty n=20000 gamma=2.3 m=500000 eps=0.01 delta=0.1 c=25"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -154,6 +155,88 @@ def recorded_traffic(kernel: str):
     return None
 
 
+def serving_workload(num_graphs, n_lo, n_hi, edges_per_node, num_requests, rate, seed=7):
+    """Resident bursty Chung-Lu graphs (n log-spaced, m = edges_per_node * n) and
+    Poisson-arriving requests: (arrival time, graph, optimality, eps, seed)."""
+    from paper_2304_08356_gb300 import synth
+    ns = np.unique(np.round(np.exp(np.linspace(np.log(n_lo), np.log(n_hi), num_graphs))).astype(int))
+    graphs = [synth.chung_lu_bursty(n=int(n), m=edges_per_node * int(n), gamma=2.3, seed=500 + k)
+              for k, n in enumerate(ns)]
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=num_requests))
+    reqs = [(float(arrivals[k]), int(rng.integers(0, len(graphs))), OPTS_ALL[int(rng.integers(0, 3))],
+             float(rng.choice([0.05, 0.02, 0.01])), 10_000 + k) for k in range(num_requests)]
+    return graphs, reqs
+
+
+def run_serving(M, graphs_uvt, reqs):
+    """p50/p99 latency and throughput of the served (continuous batching) and
+    the plain one-request-at-a-time GPU paths on the same request trace."""
+    import threading as th
+    gs = [M.Graph(*uvt) for uvt in graphs_uvt]
+    # warm both paths (workspaces, captured tick)
+    for g in gs[:2]:
+        g.estimate("pfm", 0.05, DELTA, 1, c=C_TRIALS)
+        g.estimate("sh", 0.05, DELTA, 1, c=C_TRIALS)
+
+    def summarize(lat, t_first, t_last, samples):
+        lat = np.sort(np.array(lat))
+        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(lat.mean()), "requests_per_s": len(lat) / (t_last - t_first),
+                "pairs_per_s": samples / (t_last - t_first)}
+
+    # plain: requests in arrival order, one mantra_estimate at a time
+    t0 = time.perf_counter()
+    lat, samples, t_end = [], 0, t0
+    for (arr, gi, opt, eps, sd) in reqs:
+        now = time.perf_counter() - t0
+        if now < arr:
+            time.sleep(arr - now)
+        _, _, info = gs[gi].estimate(opt, eps, DELTA, sd, c=C_TRIALS)
+        t_end = time.perf_counter()
+        lat.append(t_end - t0 - arr)
+        samples += info["r"] + info["bootstrap"]
+    plain = summarize(lat, t0 + reqs[0][0], t_end, samples)
+
+    # served: submissions at arrival times, completions collected by a waiter
+    srv = M.Server()
+    ids = [None] * len(reqs)
+    done_t = [None] * len(reqs)
+    infos = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def client():
+        for k, (arr, gi, opt, eps, sd) in enumerate(reqs):
+            now = time.perf_counter() - t0
+            if now < arr:
+                time.sleep(arr - now)
+            ids[k] = srv.submit(gs[gi], opt, eps, DELTA, sd, c=C_TRIALS)
+
+    ct = th.Thread(target=client)
+    ct.start()
+    pending = set(range(len(reqs)))
+    while pending:
+        for k in list(pending):
+            if ids[k] is None:
+                continue
+            r = srv.poll(ids[k])
+            if r is not None:
+                done_t[k] = time.perf_counter()
+                infos[k] = r[2]
+                pending.discard(k)
+        time.sleep(0.0005)
+    ct.join()
+    st = srv.stats()
+    srv.close()
+    lat = [done_t[k] - t0 - reqs[k][0] for k in range(len(reqs))]
+    samples = sum(i["r"] + i["bootstrap"] for i in infos)
+    served = summarize(lat, t0 + reqs[0][0], max(done_t), samples)
+    served["ticks"] = st["ticks"]
+    for g in gs:
+        g.free()
+    return plain, served
+
+
 def cpu_oracle_rates(u, v, t, seed, budget_s=6.0):
     """Oracle pairs/s per optimality on a bounded prefix of the estimation
     samples (single thread)."""
@@ -211,6 +294,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--opts", default="sh,sfm,pfm", help="optimalities per step (profiling subsets)")
+    ap.add_argument("--serve-graphs", type=int, default=16, help="serving leg: resident graphs (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=120, help="serving leg: requests")
+    ap.add_argument("--serve-nmax", type=int, default=20000, help="serving leg: largest graph's n")
     ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
                     help="batched: one mantra_estimate_batch over the optimalities per step; "
                          "sequential: one mantra_estimate per optimality")
@@ -341,6 +427,15 @@ def main():
     h2d = 4 * (8 * g.m + 3 * g.slots + 4 * g.n + 3)
     d2h = 3 * 8 * g.n
 
+    serving = None
+    if args.serve_graphs > 0 and rank == 0:
+        sg, sr = serving_workload(args.serve_graphs, 1000, args.serve_nmax, 25, args.serve_requests, 200.0)
+        plain, served = run_serving(M, sg, sr)
+        serving = {"workload": "%d resident bursty Chung-Lu graphs, n log-spaced in [1000, %d], m = 25 n; "
+                               "%d Poisson requests at 200/s, optimality uniform, eps uniform in "
+                               "{0.05, 0.02, 0.01}, delta 0.1" % (len(sg), args.serve_nmax, len(sr)),
+                   "served": served, "plain": plain}
+
     line = None
     if rank == 0:
         cpu = None
@@ -368,6 +463,7 @@ def main():
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
+                "serving": serving,
                 "clocks": clk.summary()}
         print(json.dumps(line))
     g.free()
