@@ -121,10 +121,15 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
     }
     for (uint32_t x = 0; x < n; ++x) out_ptr[x + 1] += out_ptr[x];
     std::vector<uint32_t> tmax_in(n, 0), tmin_out(n, 0);
+    uint64_t cbound = 0;
     for (uint32_t x = 0; x < n; ++x) {
         if (slot_ptr[x + 1] > slot_ptr[x]) tmax_in[x] = slot_t[slot_ptr[x + 1] - 1];
         if (out_ptr[x + 1] > out_ptr[x]) tmin_out[x] = out_t[out_ptr[x]];
+        uint32_t mx = 0;
+        for (uint32_t a = slot_ptr[x]; a < slot_ptr[x + 1]; ++a) mx = std::max(mx, slot_in[a + 1] - slot_in[a]);
+        cbound += mx;
     }
+    G->dg.cbound = (uint32_t)std::min<uint64_t>(cbound, 0xFFFFFFFFull);
 
     // one device allocation for the whole store
     struct Arr { const std::vector<uint32_t>* h; const uint32_t** d; };
@@ -251,7 +256,7 @@ struct Engine {
     bool last_tick_graph = false;
     // search workspaces
     char* bfs_mem = nullptr; BfsWs bws{}; int bfs_grid = 0; size_t bfs_smem = 0; uint32_t bfs_n = 0, bfs_A = 0;
-    char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; uint32_t pfm_n = 0; uint64_t pfm_warps = 0;
+    char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; uint32_t pfm_n = 0, pfm_lcap = 0; uint64_t pfm_warps = 0;
     // tick tables
     uint32_t cap = 0;
     char* tab_h = nullptr; char* tab_d = nullptr; size_t tab_bytes = 0;
@@ -348,14 +353,22 @@ struct Engine {
 
     // pfm: one region per warp (32 samples), at most one warp per 32 resident
     // threads of the GPU and at most a third of free memory.
-    int ensure_pfm(uint32_t n, uint64_t warps) {
+    int ensure_pfm(uint32_t n, uint32_t lcap, uint64_t warps) {
         const int wpb = pfm_threads() / 32;
         warps = std::min<uint64_t>(std::max<uint64_t>(warps, (uint64_t)wpb), (uint64_t)num_sms * 32);
-        if (pfm_mem && n <= pfm_n && warps <= pfm_warps) return MANTRA_OK;
+        // MANTRA_PFM_LIST_CAP lowers the contribution-list capacity (tests of the
+        // in-order fallback taken by samples whose list would overflow)
+        if (const char* env = std::getenv("MANTRA_PFM_LIST_CAP")) {
+            const long v = std::strtol(env, nullptr, 10);
+            if (v > 0 && (uint64_t)v < lcap) lcap = (uint32_t)v;
+        }
+        lcap = std::max<uint32_t>(32, std::min<uint32_t>(lcap, 1u << 20));
+        if (pfm_mem && n <= pfm_n && lcap <= pfm_lcap && warps <= pfm_warps) return MANTRA_OK;
         n = std::max(n, pfm_n);
+        lcap = std::max(lcap, pfm_lcap);
         warps = std::max<uint64_t>(warps, pfm_warps);
         if (pfm_mem) { cudaStreamSynchronize(sb); cudaStreamSynchronize(sa); cudaFree(pfm_mem); pfm_mem = nullptr; }
-        const size_t region = pfm_region_bytes(n, &pws);
+        const size_t region = pfm_region_bytes(n, lcap, &pws);
         const size_t budget = free_device_bytes() / 3;
         uint64_t w = std::min<uint64_t>(warps, std::max<size_t>(budget / region, (size_t)wpb));
         const int blocks = (int)((w + wpb - 1) / wpb);
@@ -364,6 +377,7 @@ struct Engine {
         pws.stride = region;
         pfm_grid = blocks;
         pfm_n = n;
+        pfm_lcap = lcap;
         pfm_warps = (uint64_t)blocks * wpb;
         invalidate_graph();
         return MANTRA_OK;
@@ -476,18 +490,19 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     const uint32_t k = (uint32_t)items.size();
     int rc;
     if ((rc = E.ensure_tables(std::max<uint32_t>(k, 1))) != MANTRA_OK) return rc;
-    uint32_t bn = 0, bA = 0, pn = 0;
+    uint32_t bn = 0, bA = 0, pn = 0, plc = 0;
     uint64_t pwarps = 0;
     bool any_b = false, any_p = false;
     for (const TickItem& it : items) {
         if (it.job.opt == MANTRA_PFM) {
-            any_p = true; pn = std::max(pn, it.G->n); pwarps += (it.job.count + 31) / 32;
+            any_p = true; pn = std::max(pn, it.G->n); plc = std::max(plc, it.G->dg.cbound);
+            pwarps += (it.job.count + 31) / 32;
         } else {
             any_b = true; bn = std::max(bn, it.G->n); bA = std::max(bA, it.G->A);
         }
     }
     if (any_b && (rc = E.ensure_bfs(bn, bA)) != MANTRA_OK) return rc;
-    if (any_p && (rc = E.ensure_pfm(pn, pwarps)) != MANTRA_OK) return rc;
+    if (any_p && (rc = E.ensure_pfm(pn, plc, pwarps)) != MANTRA_OK) return rc;
     // host tables
     uint32_t* hdr = (uint32_t*)(E.tab_h + E.o_hdr);
     u64* work = (u64*)(E.tab_h + E.o_work);

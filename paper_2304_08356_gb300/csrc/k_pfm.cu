@@ -24,7 +24,13 @@ namespace mantra {
 constexpr int PFM_NT = 128;
 constexpr int PFM_ILP = 8;
 
-template <bool WIDE>
+constexpr uint32_t LIST_FIRST = 0x80000000u;
+
+// DEFER (64-bit counts only): arrival decisions in the scan, path counts (and
+// hops) afterwards from the lane's ordered list of contributing edges, so the
+// scan never waits on a path-count load.  A lane whose list would exceed
+// list_cap is handed to the in-order kernel (overflow list).
+template <bool WIDE, bool DEFER>
 __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_t* unit_start,
                                                 const uint32_t* ntasks_p, u64* work, const PfmWs ws) {
     typedef typename SigOps<WIDE>::T Sig;
@@ -36,6 +42,7 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
     Sig* sig = reinterpret_cast<Sig*>(region + ws.o_sig) + lane;             // sig[v * 32]
     uint32_t* hop = reinterpret_cast<uint32_t*>(region + ws.o_hop) + lane;   // hop[v * 32]
     uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path) + (size_t)lane * (ws.n_cap + 2);
+    uint32_t* list = reinterpret_cast<uint32_t*>(region + ws.o_list) + lane;     // list[p * 32]
     __shared__ __align__(16) Task sh_tasks[PFM_NT / 32];
     Task& T = sh_tasks[threadIdx.x >> 5];
     const uint32_t ntasks = *ntasks_p;
@@ -112,6 +119,8 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
         }
         uint32_t fz = NONE;        // fa'(z) once reached
         uint32_t ovf = 0;
+        uint32_t nlist = 0;
+        bool lovf = false;
         for (uint32_t base = e_lo; base < e_hi; base += 32) {
             const uint32_t e = base + lane;
             uint32_t eu = 0, ev = 0, et = NONE;
@@ -147,7 +156,20 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
                     newf[j] = 0;
                     const uint32_t t = T[j];
                     // fz may have been set by an earlier edge of this group
-                    if (on[j] && t < fz && fu <= t) {
+                    if (DEFER && on[j] && t < fz && fu <= t && (fv == NONE || fv == t + 1u)) {
+                        const uint32_t v = Vv[j];
+                        const bool first = fv == NONE;
+                        if (first) {
+                            fa[(size_t)v * 32] = t + 1u;
+                            upd[j] = true;
+                            newf[j] = t + 1u;
+                            if (v == z) fz = t + 1u;
+                        }
+                        if (nlist < ws.list_cap) list[(size_t)nlist * 32] = (base + k0 + j) | (first ? LIST_FIRST : 0u);
+                        else lovf = true;
+                        ++nlist;
+                        ++my_eadd;
+                    } else if (!DEFER && on[j] && t < fz && fu <= t) {
                         const uint32_t u = U[j], v = Vv[j];
                         if (fv == NONE) {
                             fa[(size_t)v * 32] = t + 1u;
@@ -173,6 +195,54 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
             }
         }
         __syncwarp();
+        if (DEFER) {
+            // path counts (and hops) from the contribution list, in stream order,
+            // 8 entries per batch; this lane's updates inside a batch are forwarded
+            if (lovf) ovf = 1;
+            else if (live) {
+                for (uint32_t p0 = 0; p0 < nlist; p0 += 8) {
+                    uint32_t LU[8], LV[8], LF[8];
+                    Sig SU[8], SV[8];
+                    const uint32_t cnt = min(8u, nlist - p0);
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        LU[b] = 0; LV[b] = 0; LF[b] = 0;
+                        if (b < (int)cnt) {
+                            const uint32_t ent = list[(size_t)(p0 + b) * 32];
+                            const uint32_t ee = ent & ~LIST_FIRST;
+                            LF[b] = ent & LIST_FIRST;
+                            LU[b] = st_u[ee];
+                            LV[b] = st_v[ee];
+                        }
+                    }
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        SU[b] = (b < (int)cnt) ? sig[(size_t)LU[b] * 32] : (Sig)0;
+                        SV[b] = (b < (int)cnt && !LF[b]) ? sig[(size_t)LV[b] * 32] : (Sig)0;
+                    }
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        if (b >= (int)cnt) break;
+                        Sig su = SU[b], sv = SV[b];
+#pragma unroll
+                        for (int r = 0; r < b; ++r) {
+                            if (LV[r] == LU[b]) su = SV[r];          // SV[r] now holds entry r's new count
+                            if (LV[r] == LV[b] && !LF[b]) sv = SV[r];
+                        }
+                        Sig nv;
+                        if (!SigOps<WIDE>::add(sv, su, &nv) && !stats) ovf = 1;
+                        SV[b] = nv;
+                        sig[(size_t)LV[b] * 32] = nv;
+                        if (stats) {
+                            const uint32_t hu = hop[(size_t)LU[b] * 32] + 1u;
+                            if (LF[b]) hop[(size_t)LV[b] * 32] = hu;
+                            else if (hu < hop[(size_t)LV[b] * 32]) hop[(size_t)LV[b] * 32] = hu;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             my_escan += __shfl_xor_sync(FULL, my_escan, o);
@@ -184,9 +254,11 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
         }
 
         if (stats) {
+            // a lane whose contribution list overflowed is re-run by the in-order kernel
+            if (have && ovf) job.ovf_list[atomicAdd(job.ctr + C_NOVF, 1ull)] = i;
             uint32_t dloc = 0;
             for (uint32_t v = 0; v < n; ++v) {
-                const bool r = live && v != s && fa[(size_t)v * 32] != NONE;
+                const bool r = live && !ovf && v != s && fa[(size_t)v * 32] != NONE;
                 const uint32_t h = r ? hop[(size_t)v * 32] : NONE;
                 const unsigned grp = __match_any_sync(FULL, h);
                 if (r && lane == __ffs(grp) - 1) atomicAdd(job.cnt + h, (u64)__popc(grp));
@@ -265,14 +337,16 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
 }
 
 // Per-warp region: 32 lanes' state rows plus one path buffer per lane.
-size_t pfm_region_bytes(uint32_t n, PfmWs* ws) {
+size_t pfm_region_bytes(uint32_t n, uint32_t list_cap, PfmWs* ws) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     ws->n_cap = n;
+    ws->list_cap = list_cap;
     size_t o = 0;
     ws->o_fa = o;   o = al(o + (size_t)n * 32 * 4);
     ws->o_sig = o;  o = al(o + (size_t)n * 32 * 16);
     ws->o_hop = o;  o = al(o + (size_t)n * 32 * 4);
     ws->o_path = o; o = al(o + (size_t)32 * (n + 2) * 4);
+    ws->o_list = o; o = al(o + (size_t)32 * list_cap * 4);
     return o;
 }
 
@@ -280,8 +354,10 @@ int pfm_threads() { return PFM_NT; }
 
 cudaError_t launch_pfm(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
                        const PfmWs& ws, int grid, bool wide, cudaStream_t st) {
-    if (wide) k_pfm<true><<<grid, PFM_NT, 0, st>>>(tasks, unit_start, ntasks, work, ws);
-    else k_pfm<false><<<grid, PFM_NT, 0, st>>>(tasks, unit_start, ntasks, work, ws);
+    // narrow launches defer path counts; the 128-bit re-run takes overflowed
+    // counts and overflowed contribution lists, in order
+    if (wide) k_pfm<true, false><<<grid, PFM_NT, 0, st>>>(tasks, unit_start, ntasks, work, ws);
+    else k_pfm<false, true><<<grid, PFM_NT, 0, st>>>(tasks, unit_start, ntasks, work, ws);
     return cudaGetLastError();
 }
 

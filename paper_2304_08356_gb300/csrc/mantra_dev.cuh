@@ -48,6 +48,9 @@ struct DevGraph {
     const uint32_t* st_t;
     const uint32_t* tmax_in;
     const uint32_t* tmin_out;
+    uint32_t cbound;  // sum over v of the largest in-edge count of v's slots: bounds the
+                      // path-count additions of one prefix-foremost search
+    uint32_t pad_;
 };
 
 // One launch over a range (or list) of sample indices.
@@ -359,8 +362,9 @@ struct BfsWs {
 struct PfmWs {
     char* base;          // warp w uses base + w * stride
     size_t stride;
-    size_t o_fa, o_sig, o_hop, o_path;
+    size_t o_fa, o_sig, o_hop, o_path, o_list;
     uint32_t n_cap;      // node capacity of a region (largest graph of the launch)
+    uint32_t list_cap;   // contributing-edge entries per lane (deferred path counts)
 };
 
 size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws);
@@ -371,7 +375,7 @@ cudaError_t bfs_configure(size_t smem);
 // sh/sfm: one unit per sample; pfm: one unit per 32 consecutive samples of a task.
 cudaError_t launch_bfs(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
                        const BfsWs& ws, int grid, size_t smem, bool wide, cudaStream_t st);
-size_t pfm_region_bytes(uint32_t n, PfmWs* ws);
+size_t pfm_region_bytes(uint32_t n, uint32_t list_cap, PfmWs* ws);
 int pfm_threads();
 cudaError_t launch_pfm(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
                        const PfmWs& ws, int grid, bool wide, cudaStream_t st);

@@ -291,3 +291,37 @@ def test_batch_equals_solo_and_oracle(M):
         o = O.Graph(u, v, t, n=p["graph"].n)
         _, oh, oi = o.estimate(p["opt"], p["eps"], p["delta"], p["seed"], fixed_r=p.get("fixed_r", 0))
         assert np.array_equal(res[x][1], oh) and res[x][2]["r"] == oi["r"]
+
+
+def test_pfm_list_overflow_fallback_bit_exact():
+    """pfm samples whose contribution list would overflow are re-run by the
+    in-order kernel; a child process with a tiny list capacity must give the
+    oracle's per-sample results, estimates and Algorithm 2 counts."""
+    import json
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import json, sys
+sys.path.insert(0, ".")
+import numpy as np
+from paper_2304_08356_gb300 import build as B, synth
+B.build()
+from paper_2304_08356_gb300 import mantra as M
+from oracle import oracle as O
+u, v, t = synth.chung_lu_bursty(n=900, m=20000, seed=33)
+g = M.Graph(u, v, t); o = O.Graph(u, v, t)
+ok = g.sample_paths(2, 4, 0, 300, cap=g.n + 1) == o.samples(2, 4, 0, 300, cap=o.n + 1)
+_, h, info = g.estimate(2, 0.1, 0.1, 4, fixed_r=400)
+_, oh, _ = o.estimate(2, 0.1, 0.1, 4, fixed_r=400)
+st, reach = g.temporal_stats(2, 0.1, 5, r_override=100)
+oreach, _ = o.stats_counts(2, 5, 100)
+print(json.dumps({"ok": bool(ok and np.array_equal(h, oh) and np.array_equal(reach, oreach)),
+                  "wide": info["wide_samples"]}))
+'''
+    env = dict(os.environ, MANTRA_PFM_LIST_CAP="40")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    assert res["ok"] and res["wide"] > 0
