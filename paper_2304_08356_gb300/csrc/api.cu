@@ -1140,31 +1140,31 @@ int mantra_temporal_stats(const mantra_graph* g, mantra_opt opt, double eps, uin
     const uint32_t n = g->n;
     const uint64_t rs = r_override ? r_override : (uint64_t)std::ceil(std::log((double)n) / (eps * eps));
     const size_t b_cnt = ((size_t)n + 2) * 8;
-    u64* cnt = (u64*)E->pool.get(b_cnt + 256);
-    if (!cnt) return MANTRA_E_NOMEM;
-    u64* dmax = (u64*)((char*)cnt + al256(b_cnt));
-    CU(cudaMemsetAsync(cnt, 0, b_cnt + 256, E->sa));
+    const size_t b_all = al256(b_cnt) + 256 + al256(rs * 8);
+    char* blk = (char*)E->pool.get(b_all);
+    if (!blk) return MANTRA_E_NOMEM;
+    u64* cnt = (u64*)blk;
+    u64* dmax = (u64*)(blk + al256(b_cnt));
+    CU(cudaMemsetAsync(blk, 0, al256(b_cnt) + 256, E->sa));
     std::vector<TickItem> items(1);
     items[0].G = g;
     Job& j = items[0].job;
     j.seed = seed; j.i0 = 0; j.count = rs; j.opt = (opt == MANTRA_PFM) ? MANTRA_PFM : MANTRA_SH;
     j.stats = 1; j.cnt = cnt; j.dmax = dmax;
-    TickOut to;
-    rc = run_tick(*E, items, false, &to);
+    j.ovf_list = (uint64_t*)(blk + al256(b_cnt) + 256);       // pfm lists that overflowed: re-run in order
+    TickResult TR;
+    uint64_t* ovfs[1] = {j.ovf_list};
+    rc = run_tick_full(*E, items, ovfs, &TR);
     std::vector<u64> hc((size_t)n + 1);
     u64 dm = 0;
-    if (rc == MANTRA_OK) {
-        int st;
-        std::memcpy(&st, to.slot[0] + SLOT_STATUS, 4);
-        if (st != MANTRA_OK) rc = st;
-    }
+    if (rc == MANTRA_OK && TR.status[0] != MANTRA_OK) rc = TR.status[0];
     if (rc == MANTRA_OK) {
         if (cudaMemcpyAsync(hc.data(), cnt, ((size_t)n + 1) * 8, cudaMemcpyDeviceToHost, E->sa) != cudaSuccess ||
             cudaMemcpyAsync(&dm, dmax, 8, cudaMemcpyDeviceToHost, E->sa) != cudaSuccess ||
             cudaStreamSynchronize(E->sa) != cudaSuccess)
             rc = MANTRA_E_CUDA;
     }
-    E->pool.put(cnt, b_cnt + 256);
+    E->pool.put(blk, b_all);
     if (rc != MANTRA_OK) return rc;
     const uint32_t D = (uint32_t)dm;
     std::vector<u64> R((size_t)D + 1);

@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
         if (sh_ovf) {
             if (tid == 0) {
                 if (WIDE) set_status(job.status, ST_OVERFLOW);
-                else job.ovf_list[atomicAdd(job.ctr + C_NOVF, 1ull)] = i;
+                else push_overflow(job, i);
             }
         } else if (!sh_err) {
             const bool drawn = found && sh_len > 0;

@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
 
         if (stats) {
             // a lane whose contribution list overflowed is re-run by the in-order kernel
-            if (have && ovf) job.ovf_list[atomicAdd(job.ctr + C_NOVF, 1ull)] = i;
+            if (have && ovf) push_overflow(job, i);
             uint32_t dloc = 0;
             for (uint32_t v = 0; v < n; ++v) {
                 const bool r = live && !ovf && v != s && fa[(size_t)v * 32] != NONE;
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
         }
         if (have && ovf) {
             if (WIDE) set_status(job.status, ST_OVERFLOW);
-            else job.ovf_list[atomicAdd(job.ctr + C_NOVF, 1ull)] = i;
+            else push_overflow(job, i);
         }
         if (have && !ovf && !err) {
             if (job.hits && len >= 3) {

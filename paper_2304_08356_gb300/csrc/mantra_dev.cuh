@@ -348,6 +348,13 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t 
 
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, ST_OK, code); }
 
+// Records sample i for the 128-bit / in-order re-run (a job without a list
+// reports a consistency error instead).
+__device__ __forceinline__ void push_overflow(const Job& job, uint64_t i) {
+    if (job.ovf_list) job.ovf_list[atomicAdd(job.ctr + C_NOVF, 1ull)] = i;
+    else set_status(job.status, ST_CHECK);
+}
+
 
 // Per-CTA scratch of the sh/sfm search kernel (one region per CTA).
 struct BfsWs {
