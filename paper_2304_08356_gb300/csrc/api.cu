@@ -257,15 +257,17 @@ struct Engine {
     // search workspaces
     char* bfs_mem = nullptr; BfsWs bws{}; int bfs_grid = 0; size_t bfs_smem = 0; uint32_t bfs_n = 0, bfs_A = 0;
     char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; uint32_t pfm_n = 0, pfm_lcap = 0; uint64_t pfm_warps = 0;
+    char* pc_mem = nullptr; PfmCtaWs pcws{}; int pc_grid = 0; uint32_t pc_n = 0;
+    bool tick_cta = false;   // pfm samples of the current tick run one per CTA
     // tick tables
     uint32_t cap = 0;
     char* tab_h = nullptr; char* tab_d = nullptr; size_t tab_bytes = 0;
     char* slot_h = nullptr; char* slot_d = nullptr;
     size_t o_hdr = 0, o_work = 0, o_ub = 0, o_up = 0, o_tb = 0, o_tp = 0, o_ri = 0, o_rs = 0;
     int red_grid = 0;
-    // captured tick
-    cudaGraphExec_t gexec = nullptr;
-    bool graph_ok = false;
+    // captured ticks, one per pfm kernel (lane / CTA per sample)
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    bool graph_ok[2] = {false, false};
     bool use_graph = true;
     DevPool pool;
 
@@ -292,9 +294,11 @@ struct Engine {
     }
 
     void invalidate_graph() {
-        if (gexec) cudaGraphExecDestroy(gexec);
-        gexec = nullptr;
-        graph_ok = false;
+        for (int k = 0; k < 2; ++k) {
+            if (gexec[k]) cudaGraphExecDestroy(gexec[k]);
+            gexec[k] = nullptr;
+            graph_ok[k] = false;
+        }
     }
 
     // Table block layout: header | 2 work counters | unit starts (bfs, pfm) |
@@ -383,6 +387,30 @@ struct Engine {
         return MANTRA_OK;
     }
 
+    // pfm with one CTA per sample: one region per resident CTA, at most a third
+    // of free memory; fa' and the frontier bitmap in shared memory when they fit.
+    int ensure_pfm_cta(uint32_t n) {
+        if (pc_mem && n <= pc_n) return MANTRA_OK;
+        n = std::max(n, pc_n);
+        if (pc_mem) { cudaStreamSynchronize(sb); cudaStreamSynchronize(sa); cudaFree(pc_mem); pc_mem = nullptr; }
+        const size_t smem = pfm_cta_smem_bytes(n);
+        const bool in_smem = smem + 4096 <= smem_optin;
+        const size_t region = pfm_cta_region_bytes(n, in_smem, &pcws);
+        CU(pfm_cta_configure(in_smem ? smem : 0));
+        int per_sm = 0;
+        CU(pfm_cta_blocks_per_sm(in_smem, in_smem ? smem : 0, &per_sm));
+        int grid = num_sms * std::max(per_sm, 1);
+        const size_t budget = free_device_bytes() / 3;
+        if ((size_t)grid * region > budget) grid = (int)std::max<size_t>(1, budget / region);
+        if (cudaMalloc(&pc_mem, (size_t)grid * region) != cudaSuccess) { pc_mem = nullptr; return MANTRA_E_NOMEM; }
+        pcws.base = pc_mem;
+        pcws.stride = region;
+        pc_grid = grid;
+        pc_n = n;
+        invalidate_graph();
+        return MANTRA_OK;
+    }
+
     // The tick as stream work: tables up, slots cleared, both search
     // families on two streams, the round reduction, slots down.
     int enqueue(bool wide) {
@@ -398,7 +426,12 @@ struct Engine {
                           bfs_grid, bfs_smem, wide, sa));
             CU(cudaEventRecord(e_b1, sa));
         }
-        if (pfm_mem) {
+        if (tick_cta && !wide && pc_mem) {
+            CU(cudaEventRecord(e_p0, sb));
+            CU(launch_pfm_cta((const Task*)(tab_d + o_tp), (const uint64_t*)(tab_d + o_up), hdr + 1, work + 1, pcws,
+                              pc_grid, sb));
+            CU(cudaEventRecord(e_p1, sb));
+        } else if (!tick_cta && pfm_mem) {
             CU(cudaEventRecord(e_p0, sb));
             CU(launch_pfm((const Task*)(tab_d + o_tp), (const uint64_t*)(tab_d + o_up), hdr + 1, work + 1, pws,
                           pfm_grid, wide, sb));
@@ -415,7 +448,8 @@ struct Engine {
     int launch_tick(bool wide) {
         last_tick_graph = false;
         if (wide || !use_graph) return enqueue(wide);
-        if (!graph_ok) {
+        const int gk = tick_cta ? 1 : 0;
+        if (!graph_ok[gk]) {
             cudaGraph_t graph = nullptr;
             CU(cudaStreamBeginCapture(sa, cudaStreamCaptureModeThreadLocal));
             const int rc = enqueue(false);
@@ -425,13 +459,13 @@ struct Engine {
                 use_graph = false;                    // capture unavailable: run the same work directly
                 return enqueue(false);
             }
-            const cudaError_t ei = cudaGraphInstantiate(&gexec, graph, 0);
+            const cudaError_t ei = cudaGraphInstantiate(&gexec[gk], graph, 0);
             cudaGraphDestroy(graph);
-            if (ei != cudaSuccess) { gexec = nullptr; use_graph = false; return enqueue(false); }
-            graph_ok = true;
+            if (ei != cudaSuccess) { gexec[gk] = nullptr; use_graph = false; return enqueue(false); }
+            graph_ok[gk] = true;
         }
         CU(cudaEventRecord(e_t0, sa));
-        CU(cudaGraphLaunch(gexec, sa));
+        CU(cudaGraphLaunch(gexec[gk], sa));
         CU(cudaEventRecord(e_t1, sa));
         last_tick_graph = true;
         return MANTRA_OK;
@@ -473,15 +507,28 @@ double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
     return ms;
 }
 
-void log_item(const TickItem& it, bool wide, const u64* c, double ms) {
+void log_item(const TickItem& it, bool wide, bool cta, const u64* c, double ms) {
     static const bool on = std::getenv("MANTRA_LOG_LAUNCHES") != nullptr;
     if (!on) return;
     const bool pfm = it.job.opt == MANTRA_PFM;
     std::fprintf(stderr, "mantra-launch kernel=%s%s samples=%llu escan=%llu eadd=%llu snew=%llu fseg=%llu "
-                 "alg_bytes=%llu ms=%.4f\n", pfm ? "k_pfm" : "k_bfs", wide ? "<wide>" : "",
-                 (unsigned long long)it.job.count, (unsigned long long)c[C_ESCAN], (unsigned long long)c[C_EADD],
-                 (unsigned long long)c[C_SNEW], (unsigned long long)c[C_FSEG],
+                 "xedge=%llu alg_bytes=%llu ms=%.4f\n", pfm ? (cta ? "k_pfm_cta" : "k_pfm") : "k_bfs",
+                 wide ? "<wide>" : "", (unsigned long long)it.job.count, (unsigned long long)c[C_ESCAN],
+                 (unsigned long long)c[C_EADD], (unsigned long long)c[C_SNEW], (unsigned long long)c[C_FSEG],
+                 (unsigned long long)c[C_XEDGE],
                  (unsigned long long)alg_bytes_of(pfm, c[C_ESCAN], c[C_EADD], c[C_SNEW], c[C_FSEG]), ms);
+}
+
+// Which pfm kernel a narrow tick with `samples` pfm samples (largest graph n)
+// uses.  The lane kernel's launch costs at least one warp's serial walk over
+// the stream, the CTA kernel's about one sample's search per resident CTA;
+// MANTRA_PFM_KERNEL=lane|cta forces one of them.
+bool pfm_use_cta(const Engine& E, uint64_t samples, uint32_t n) {
+    const char* env = std::getenv("MANTRA_PFM_KERNEL");
+    if (env && std::strcmp(env, "lane") == 0) return false;
+    if (env && std::strcmp(env, "cta") == 0) return true;
+    (void)n;
+    return samples <= (uint64_t)E.num_sms * 16;
 }
 
 // One tick over `items` (narrow kernels, captured graph), or with `wide` the
@@ -491,18 +538,22 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     int rc;
     if ((rc = E.ensure_tables(std::max<uint32_t>(k, 1))) != MANTRA_OK) return rc;
     uint32_t bn = 0, bA = 0, pn = 0, plc = 0;
-    uint64_t pwarps = 0;
+    uint64_t pwarps = 0, psamples = 0;
     bool any_b = false, any_p = false;
     for (const TickItem& it : items) {
         if (it.job.opt == MANTRA_PFM) {
             any_p = true; pn = std::max(pn, it.G->n); plc = std::max(plc, it.G->dg.cbound);
             pwarps += (it.job.count + 31) / 32;
+            psamples += it.job.count;
         } else {
             any_b = true; bn = std::max(bn, it.G->n); bA = std::max(bA, it.G->A);
         }
     }
+    const bool cta = any_p && !wide && pfm_use_cta(E, psamples, pn);
     if (any_b && (rc = E.ensure_bfs(bn, bA)) != MANTRA_OK) return rc;
-    if (any_p && (rc = E.ensure_pfm(pn, plc, pwarps)) != MANTRA_OK) return rc;
+    if (any_p && cta && (rc = E.ensure_pfm_cta(pn)) != MANTRA_OK) return rc;
+    if (any_p && !cta && (rc = E.ensure_pfm(pn, plc, pwarps)) != MANTRA_OK) return rc;
+    E.tick_cta = cta;
     // host tables
     uint32_t* hdr = (uint32_t*)(E.tab_h + E.o_hdr);
     u64* work = (u64*)(E.tab_h + E.o_work);
@@ -520,7 +571,11 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
         it.job.ctr = (u64*)slot;
         it.job.status = (int*)(slot + SLOT_STATUS);
         Task t{it.G->dg, it.job};
-        if (it.job.opt == MANTRA_PFM) { tp[np] = t; up[np + 1] = up[np] + (it.job.count + 31) / 32; ++np; }
+        if (it.job.opt == MANTRA_PFM) {
+            tp[np] = t;
+            up[np + 1] = up[np] + (cta ? it.job.count : (it.job.count + 31) / 32);
+            ++np;
+        }
         else { tb[nb] = t; ub[nb + 1] = ub[nb] + it.job.count; ++nb; }
         if (it.reduce) {
             ri[nr] = ReduceItem{it.job.S, it.job.hits, it.G->n, it.red_c, (long long*)(slot + SLOT_ROWMAX),
@@ -536,7 +591,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     out->slot.resize(k);
     for (uint32_t x = 0; x < k; ++x) out->slot[x] = E.slot_h + (size_t)x * SLOT_BYTES;
     out->had_bfs = nb > 0 && E.bfs_mem;
-    out->had_pfm = np > 0 && E.pfm_mem;
+    out->had_pfm = np > 0 && (cta ? E.pc_mem != nullptr : E.pfm_mem != nullptr);
     if (E.last_tick_graph) {
         // a graph tick is timed as a whole: table upload, searches, reduction, readback
         const double t = elapsed_ms(E.e_t0, E.e_t1);
@@ -547,7 +602,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
         out->pfm_ms = out->had_pfm ? elapsed_ms(E.e_p0, E.e_p1) : 0.0;
     }
     for (uint32_t x = 0; x < k; ++x)
-        log_item(items[x], wide, (const u64*)out->slot[x],
+        log_item(items[x], wide, cta, (const u64*)out->slot[x],
                  items[x].job.opt == MANTRA_PFM ? out->pfm_ms : out->bfs_ms);
     return MANTRA_OK;
 }

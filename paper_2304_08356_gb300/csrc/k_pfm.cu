@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
                             ++my_eadd;
                         }
                     }
-                    my_escan += on[j] ? 1 : 0;
+                    my_escan += (on[j] && t < fz) ? 1 : 0;     // scan window ends at fa(z)
                 }
             }
         }

@@ -1,0 +1,483 @@
+// Prefix-foremost search with one CTA per sample (paper Sec. 3 Def. 1(3)).
+// The lane-per-sample kernel walks the time-sorted stream serially, so one
+// of its launches costs at least one warp's walk however few samples it has;
+// this kernel spreads each sample over a CTA instead.  Per sample:
+//   arrivals  label-correcting rounds over the out-CSR.  A vertex u whose
+//             earliest arrival fa(u) improved is expanded over its out-edges
+//             with fa(u) < t <= bound; an edge (u, v, t), v != s, lowers
+//             fa(v) to t.  An improvement of fa(u) from a to b only adds the
+//             times in (b, a], so every out-edge is expanded at most once.
+//             bound = the latest in-edge time of z, then fa(z) once z is
+//             reached (later edges reach no vertex earlier than z).
+//   counts    pfm paths use the edges (w, v, fa(v)) with fa(w) < fa(v): a DAG.
+//             pend(v) = number of such in-edges; a vertex whose in-edges are
+//             all counted is expanded (Kahn levels) and adds sigma(u) to
+//             sigma(v) over its DAG out-edges (hop(v) = min hop(u) + 1 for the
+//             Algorithm 2 searches).
+//   draw      backward over DAG in-edges by ascending w, weight sigma(w)
+//             (App. C path sampler), then the Update step of Algorithm 1.
+// Path counts are 64-bit; a sample whose count overflows goes to the
+// overflow list for the 128-bit lane kernel.
+// State fa' = fa + 1 (0 for the source, NONE when unreached).
+#include "mantra_dev.cuh"
+
+#include <mutex>
+
+namespace mantra {
+
+constexpr int PC_NT = 512;
+constexpr int PC_NW = PC_NT / 32;
+
+template <bool SM>
+__device__ __forceinline__ uint32_t ld_fa(const uint32_t* p) {
+    if (SM) return *p;
+    return __ldcg(p);
+}
+
+template <bool FA_SMEM>
+__global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const uint64_t* unit_start,
+                                                     const uint32_t* ntasks_p, u64* work, const PfmCtaWs ws) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t FULL = 0xFFFFFFFFu;
+    __shared__ __align__(16) Task sh_task;
+    __shared__ int sh_t;
+    __shared__ uint64_t sh_q;
+    __shared__ u64 sm_scan64[32];
+    __shared__ uint32_t sm_wcnt[PC_NW];
+    __shared__ uint32_t sh_L, sh_Gc, sh_ovf, sh_err, sh_len;
+    __shared__ uint32_t sh_rade[4];
+    __shared__ u64 sh_sigma;
+    extern __shared__ __align__(16) uint32_t pc_dyn[];
+
+    char* region = ws.base + (size_t)blockIdx.x * ws.stride;
+    uint32_t* fa = FA_SMEM ? pc_dyn : reinterpret_cast<uint32_t*>(region + ws.o_fa);
+    uint32_t* NB = FA_SMEM ? pc_dyn + ws.n_cap : reinterpret_cast<uint32_t*>(region + ws.o_bits);  // next frontier
+    uint32_t* xp = reinterpret_cast<uint32_t*>(region + ws.o_exp);      // fa' at the last expansion
+    u64* sig = reinterpret_cast<u64*>(region + ws.o_sig);
+    uint32_t* hop = reinterpret_cast<uint32_t*>(region + ws.o_hop);
+    uint32_t* pend = reinterpret_cast<uint32_t*>(region + ws.o_pend);
+    uint32_t* Fl = reinterpret_cast<uint32_t*>(region + ws.o_list);     // frontier vertices
+    uint32_t* cs_first = reinterpret_cast<uint32_t*>(region + ws.o_first);
+    uint32_t* cs_off = reinterpret_cast<uint32_t*>(region + ws.o_off);
+    uint32_t* cs_u = reinterpret_cast<uint32_t*>(region + ws.o_cu);
+    uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path);
+
+    const uint32_t ntasks = *ntasks_p;
+    u64* flush_ctr = nullptr;
+    u64 my_escan = 0, my_eadd = 0, my_x = 0, my_rounds = 0;   // my_x, my_rounds: thread 0
+    // the bitmap is all zero between samples (every compaction clears what it reads)
+    for (uint32_t w = tid; w < ws.bits_words; w += PC_NT) NB[w] = 0u;
+    __syncthreads();
+
+    // Compacts the next-frontier bitmap (nwords words) into Fl in vertex order
+    // and clears it; returns the number of vertices.  Contains barriers.
+    auto compact = [&](uint32_t nwords) -> uint32_t {
+        const uint32_t per_w = (((nwords + PC_NW - 1) / PC_NW) + 31u) & ~31u;
+        const uint32_t w_lo = min((uint32_t)wid * per_w, nwords), w_hi = min(w_lo + per_w, nwords);
+        uint32_t cnt = 0;
+        for (uint32_t w = w_lo + lane; w < w_hi; w += 32) cnt += __popc(NB[w]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+        if (lane == 0) sm_wcnt[wid] = cnt;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t x = (lane < PC_NW) ? sm_wcnt[lane] : 0u;
+            uint32_t incl = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane < PC_NW) sm_wcnt[lane] = incl - x;
+            if (lane == 31) sh_L = incl;
+        }
+        __syncthreads();
+        uint32_t off = sm_wcnt[wid];
+        for (uint32_t w0 = w_lo; w0 < w_hi; w0 += 32) {
+            const uint32_t w = w0 + lane;
+            uint32_t bits = (w < w_hi) ? NB[w] : 0u;
+            if (bits) NB[w] = 0u;
+            const uint32_t c = __popc(bits);
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            uint32_t pos = off + incl - c;
+            while (bits) {
+                const uint32_t b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                Fl[pos++] = w * 32u + b;
+            }
+            off += __shfl_sync(FULL, incl, 31);
+        }
+        const uint32_t L = sh_L;
+        __syncthreads();
+        return L;
+    };
+
+    // Out-edge ranges [lo, hi) of the L listed vertices, compacted to the
+    // non-empty ones with exclusive edge offsets; returns the edge total.
+    // range(u, &lo, &hi) gives one vertex's range.  Contains barriers.
+    auto build_ranges = [&](uint32_t L, auto range) -> uint32_t {
+        uint32_t cbase = 0, ebase = 0;
+        for (uint32_t it = 0; it < L; it += PC_NT) {
+            const uint32_t x = it + tid;
+            uint32_t lo = 0, hi = 0, u = 0;
+            if (x < L) { u = Fl[x]; range(u, &lo, &hi); }
+            const uint32_t cand = hi > lo ? hi - lo : 0u;
+            u64 tot;
+            const u64 ex = block_exclusive_scan64<PC_NT>(((u64)(cand > 0 ? 1u : 0u) << 32) | cand, &tot, sm_scan64);
+            const uint32_t exc = (uint32_t)(ex >> 32), exe = (uint32_t)ex;
+            if (cand > 0) { cs_first[cbase + exc] = lo; cs_off[cbase + exc] = ebase + exe; cs_u[cbase + exc] = u; }
+            cbase += (uint32_t)(tot >> 32);
+            ebase += (uint32_t)tot;
+        }
+        if (tid == 0) { cs_off[cbase] = ebase; sh_Gc = cbase; }
+        __syncthreads();
+        return ebase;
+    };
+
+    // Every candidate edge once, in warp windows of 32 consecutive edges; the
+    // owning range of edge j is the last g with cs_off[g] <= j.  Ends with a barrier.
+    auto expand = [&](uint32_t E, auto edge) {
+        const uint32_t Gc = sh_Gc;
+        for (uint32_t base = (uint32_t)wid * 32u; base < E; base += PC_NW * 32u) {
+            uint32_t h0 = 0;
+            if (lane == 0) {
+                uint32_t lo = 0, hi = Gc;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (cs_off[mid] <= base) lo = mid; else hi = mid;
+                }
+                h0 = lo;
+            }
+            h0 = __shfl_sync(FULL, h0, 0);
+            const uint32_t j = base + lane;
+            if (j < E) {
+                // the window's 32 edges lie in ranges h0 .. h0 + 31 (each range is non-empty)
+                uint32_t lo = h0, hi = min(h0 + 33u, Gc);
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (cs_off[mid] <= j) lo = mid; else hi = mid;
+                }
+                edge(cs_u[lo], cs_first[lo] + (j - cs_off[lo]));
+            }
+        }
+        __syncthreads();
+    };
+
+    for (;;) {
+        if (tid == 0) {
+            const uint64_t u = atomicAdd(work, 1ull);
+            int t = -1;
+            if (ntasks > 0 && u < unit_start[ntasks]) {
+                t = task_of_unit(unit_start, ntasks, u);
+                sh_q = u - unit_start[t];
+            }
+            sh_t = t;
+            sh_ovf = 0; sh_err = 0; sh_len = 0; sh_sigma = 0;
+        }
+        __syncthreads();
+        if (sh_t < 0) break;
+        if (wid == 0) {
+            const u64* src = reinterpret_cast<const u64*>(tasks + sh_t);
+            u64* dst = reinterpret_cast<u64*>(&sh_task);
+            for (uint32_t w = lane; w < sizeof(Task) / 8; w += 32) dst[w] = src[w];
+        }
+        __syncthreads();
+        const DevGraph& g = sh_task.g;
+        const Job& job = sh_task.job;
+        if (job.ctr != flush_ctr) {
+            if (flush_ctr) {
+                if (my_escan) atomicAdd(flush_ctr + C_ESCAN, my_escan);
+                if (my_eadd) atomicAdd(flush_ctr + C_EADD, my_eadd);
+                if (my_x) atomicAdd(flush_ctr + C_XEDGE, my_x);
+                if (my_rounds) atomicAdd(flush_ctr + C_FSEG, my_rounds);
+            }
+            my_escan = my_eadd = my_x = my_rounds = 0;
+            flush_ctr = job.ctr;
+        }
+        const uint32_t n = g.n;
+        const uint32_t nwords = (n + 31) >> 5;
+        const bool stats = job.stats != 0;
+        const uint64_t q = sh_q;
+        const uint64_t i = job.idx_list ? job.idx_list[q] : job.i0 + q;
+        uint32_t s, z;
+        bool ok;
+        if (stats) {
+            uint64_t x;
+            ok = draw_below64(n, job.seed, i, DOM_STATS, &x);
+            s = (uint32_t)x; z = NONE;
+        } else {
+            ok = draw_pair(n, job.seed, i, job.dom_pair, &s, &z);
+        }
+        if (!ok) { if (tid == 0) set_status(job.status, ST_RNG); s = 0; z = 1; }
+        bool live = ok && g.out_ptr[s + 1] > g.out_ptr[s];
+        if (!stats && live && g.slot_ptr[z + 1] == g.slot_ptr[z]) live = false;
+        const uint32_t* const out_ptr = g.out_ptr;
+        const uint32_t* const out_t = g.out_t;
+        const uint32_t* const out_v = g.out_v;
+
+        for (uint32_t v = tid; v < n; v += PC_NT) { fa[v] = NONE; xp[v] = NONE; }
+        __syncthreads();
+        if (tid == 0 && live) { fa[s] = 0u; NB[s >> 5] |= 1u << (s & 31); }
+        __syncthreads();
+
+        // ---- earliest arrivals ----
+        uint32_t bound = live ? (stats ? NONE - 1u : g.tmax_in[z]) : 0u;
+        while (live) {
+            const uint32_t L = compact(nwords);
+            if (L == 0) break;
+            const uint32_t E = build_ranges(L, [&](uint32_t u, uint32_t* lo, uint32_t* hi) {
+                const uint32_t fu = fa[u], pu = xp[u];
+                xp[u] = fu;
+                const uint32_t r0 = out_ptr[u], r1 = out_ptr[u + 1];
+                *lo = (fu == 0u) ? r0 : upper_bound_u32(out_t, r0, r1, fu - 1u);   // t > fa(u)
+                const uint32_t top = (pu == NONE) ? bound : min(bound, pu - 1u);  // t <= previous fa(u)
+                *hi = upper_bound_u32(out_t, *lo, r1, top);
+            });
+            if (tid == 0) { my_x += E; ++my_rounds; }
+            expand(E, [&](uint32_t, uint32_t e) {
+                const uint32_t v = out_v[e];
+                if (v == s) return;
+                const uint32_t nv = out_t[e] + 1u;
+                if (nv >= ld_fa<FA_SMEM>(fa + v)) return;
+                if (nv < atomicMin(fa + v, nv)) atomicOr(NB + (v >> 5), 1u << (v & 31));
+            });
+            if (!stats) {
+                const uint32_t fz = ld_fa<FA_SMEM>(fa + z);
+                if (fz != NONE) bound = min(bound, fz - 1u);
+            }
+        }
+        const bool reached = live && (stats || ld_fa<FA_SMEM>(fa + z) != NONE);
+
+        // edges of the prefix-foremost scan window (same count as the lane kernel):
+        // stream edges with tmin_out(s) <= t <= fa(z) (z's latest in-edge time when
+        // unreached), not into s
+        if (tid == 0 && live) {
+            const uint32_t ts = g.tmin_out[s];
+            const uint32_t te = stats ? NONE - 1u : (reached ? bound : g.tmax_in[z]);
+            if (ts <= te) {
+                const uint32_t a = lower_bound_u32(g.st_t, 0, g.m, ts), b = upper_bound_u32(g.st_t, a, g.m, te);
+                const uint32_t s0 = g.slot_ptr[s], s1 = g.slot_ptr[s + 1];
+                const uint32_t sa = lower_bound_u32(g.slot_t, s0, s1, ts), sb = upper_bound_u32(g.slot_t, sa, s1, te);
+                my_escan += (u64)(b - a) - (u64)(g.slot_in[sb] - g.slot_in[sa]);
+            }
+        }
+
+        // ---- path counts over the prefix-foremost DAG (Kahn levels) ----
+        // pend(v) for every v with fa(v) <= bound; their sum is the scan's number
+        // of path-count updates, counted also when z is not reached
+        if (live) {
+            for (uint32_t v = tid; v < n; v += PC_NT) {
+                const uint32_t fv = ld_fa<FA_SMEM>(fa + v);
+                if (fv == NONE || v == s || fv - 1u > bound) continue;
+                const uint32_t a = lower_bound_u32(g.slot_t, g.slot_ptr[v], g.slot_ptr[v + 1], fv - 1u);
+                uint32_t c = 0;
+                for (uint32_t e = g.slot_in[a]; e < g.slot_in[a + 1]; ++e)
+                    if (ld_fa<FA_SMEM>(fa + g.in_u[e]) < fv) ++c;
+                my_eadd += c;
+                if (reached) {
+                    pend[v] = c;
+                    sig[v] = 0ull;
+                    hop[v] = NONE;
+                }
+            }
+        }
+        if (reached) {
+            if (tid == 0) { sig[s] = 1ull; hop[s] = 0u; NB[s >> 5] |= 1u << (s & 31); }
+            __syncthreads();
+            for (;;) {
+                const uint32_t L = compact(nwords);
+                if (L == 0) break;
+                const uint32_t E = build_ranges(L, [&](uint32_t u, uint32_t* lo, uint32_t* hi) {
+                    const uint32_t fu = fa[u];
+                    const uint32_t r0 = out_ptr[u], r1 = out_ptr[u + 1];
+                    *lo = (fu == 0u) ? r0 : upper_bound_u32(out_t, r0, r1, fu - 1u);
+                    *hi = upper_bound_u32(out_t, *lo, r1, bound);
+                });
+                if (tid == 0) { my_x += E; ++my_rounds; }
+                expand(E, [&](uint32_t u, uint32_t e) {
+                    const uint32_t v = out_v[e];
+                    if (v == s || ld_fa<FA_SMEM>(fa + v) != out_t[e] + 1u) return;   // not v's earliest arrival
+                    if (stats) atomicMin(hop + v, __ldcg(hop + u) + 1u);
+                    else if (!SigOps<false>::atomic_add(sig + v, __ldcg(sig + u))) sh_ovf = 1;
+                    if (atomicSub(pend + v, 1u) == 1u) atomicOr(NB + (v >> 5), 1u << (v & 31));
+                });
+            }
+        }
+
+        if (stats) {
+            uint32_t dloc = 0;
+            if (reached) {
+                for (uint32_t v0 = 0; v0 < n; v0 += PC_NT) {
+                    const uint32_t v = v0 + tid;
+                    const bool r = v < n && v != s && ld_fa<FA_SMEM>(fa + v) != NONE;
+                    const uint32_t h = r ? __ldcg(hop + v) : NONE;
+                    const unsigned grp = __match_any_sync(FULL, h);
+                    if (r && lane == __ffs(grp) - 1) atomicAdd(job.cnt + h, (u64)__popc(grp));
+                    if (r && h > dloc) dloc = h;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dloc = max(dloc, __shfl_xor_sync(FULL, dloc, o));
+            if (lane == 0 && dloc) atomicMax(job.dmax, (u64)dloc);
+            __syncthreads();
+            continue;
+        }
+        __syncthreads();
+
+        // ---- backward draw (warp 0) ----
+        if (reached && !sh_ovf && wid == 0) {
+            const u64 tot = __ldcg(sig + z);
+            u128 x = 0;
+            uint32_t rng_ok = 1;
+            if (lane == 0) rng_ok = draw_below128((u128)tot, job.seed, i, job.dom_path, &x) ? 1u : 0u;
+            rng_ok = __shfl_sync(FULL, rng_ok, 0);
+            u64 xs = shfl_idx_w((u64)x, 0);
+            bool err = !rng_ok;
+            if (err && lane == 0) set_status(job.status, ST_RNG);
+            uint32_t v = z, cnt = 1;
+            if (lane == 0) path[0] = z;
+            while (!err && v != s) {
+                const uint32_t fv = ld_fa<FA_SMEM>(fa + v);
+                const uint32_t a = lower_bound_u32(g.slot_t, g.slot_ptr[v], g.slot_ptr[v + 1], fv - 1u);
+                const uint32_t e_lo = g.slot_in[a], e_hi = g.slot_in[a + 1];
+                uint32_t nxt = NONE;
+                for (uint32_t e0 = e_lo; e0 < e_hi; e0 += 32) {
+                    const uint32_t e = e0 + lane;
+                    u64 wt = 0;
+                    uint32_t w = 0;
+                    if (e < e_hi) {
+                        w = g.in_u[e];
+                        if (ld_fa<FA_SMEM>(fa + w) < fv) wt = __ldcg(sig + w);
+                    }
+                    const u64 incl = warp_inclusive_sum(wt);
+                    const unsigned msk = __ballot_sync(FULL, xs < incl);
+                    if (msk) {
+                        const int l = __ffs(msk) - 1;
+                        nxt = __shfl_sync(FULL, w, l);
+                        xs -= shfl_idx_w(incl - wt, l);
+                        break;
+                    }
+                    xs -= shfl_idx_w(incl, 31);
+                }
+                if (nxt == NONE || cnt > n) { err = true; break; }
+                v = nxt;
+                if (lane == 0) path[cnt] = v;
+                ++cnt;
+            }
+            if (lane == 0) {
+                if (err) {
+                    sh_err = 1;
+                    set_status(job.status, ST_CHECK);
+                } else {
+                    for (uint32_t p = 0; p < cnt / 2; ++p) {
+                        const uint32_t tmp = path[p]; path[p] = path[cnt - 1 - p]; path[cnt - 1 - p] = tmp;
+                    }
+                    sh_len = cnt;
+                    sh_sigma = tot;
+                    uint32_t w4[4];
+                    philox_block(job.seed, i, DOM_RADE, 0, w4);
+                    sh_rade[0] = w4[0]; sh_rade[1] = w4[1]; sh_rade[2] = w4[2]; sh_rade[3] = w4[3];
+                }
+            }
+        }
+        __syncthreads();
+
+        if (sh_ovf) {
+            if (tid == 0) push_overflow(job, i);
+        } else if (!sh_err) {
+            const uint32_t len = sh_len;
+            if (job.hits && len >= 3) {
+                const uint32_t nint = len - 2;
+                const uint32_t rows = 1 + (job.S ? job.c : 0);
+                for (uint32_t it = tid; it < nint * rows; it += PC_NT) {
+                    const uint32_t p = it % nint, jrow = it / nint;
+                    const uint32_t v = path[1 + p];
+                    if (jrow == 0) {
+                        atomicAdd(job.hits + v, 1ull);
+                    } else {
+                        const uint32_t jj = jrow - 1;
+                        const int lam = ((sh_rade[jj >> 5] >> (jj & 31)) & 1u) ? 1 : -1;
+                        atomicAdd(job.S + (size_t)jj * n + v, lam);
+                    }
+                }
+                if (tid == 0) atomicAdd(job.ctr + C_SUMINT, (u64)nint);
+            }
+            if (job.rec_len) {
+                const uint64_t r = i - job.i0;
+                if (tid == 0) {
+                    job.rec_s[r] = s; job.rec_z[r] = z;
+                    job.rec_sig[2 * r] = sh_sigma; job.rec_sig[2 * r + 1] = 0ull;
+                    job.rec_len[r] = len;
+                }
+                for (uint32_t p = tid; p < len && p < job.rec_cap; p += PC_NT)
+                    job.rec_nodes[r * job.rec_cap + p] = path[p];
+            }
+        }
+        __syncthreads();
+    }
+    if (flush_ctr) {
+        if (my_escan) atomicAdd(flush_ctr + C_ESCAN, my_escan);
+        if (my_eadd) atomicAdd(flush_ctr + C_EADD, my_eadd);
+        if (my_x) atomicAdd(flush_ctr + C_XEDGE, my_x);
+        if (my_rounds) atomicAdd(flush_ctr + C_FSEG, my_rounds);
+    }
+}
+
+// Region of one CTA (global memory); fa' and the frontier bitmap are in
+// shared memory instead when fa_in_smem.
+size_t pfm_cta_region_bytes(uint32_t n, bool fa_in_smem, PfmCtaWs* ws) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t o = 0;
+    ws->n_cap = n;
+    ws->bits_words = (n + 31) / 32;
+    ws->fa_in_smem = fa_in_smem ? 1 : 0;
+    ws->o_fa = o;    if (!fa_in_smem) o = al(o + (size_t)n * 4);
+    ws->o_bits = o;  if (!fa_in_smem) o = al(o + (size_t)ws->bits_words * 4);
+    ws->o_exp = o;   o = al(o + (size_t)n * 4);
+    ws->o_sig = o;   o = al(o + (size_t)n * 8);
+    ws->o_hop = o;   o = al(o + (size_t)n * 4);
+    ws->o_pend = o;  o = al(o + (size_t)n * 4);
+    ws->o_list = o;  o = al(o + (size_t)(n + 1) * 4);
+    ws->o_first = o; o = al(o + (size_t)(n + 1) * 4);
+    ws->o_off = o;   o = al(o + (size_t)(n + 2) * 4);
+    ws->o_cu = o;    o = al(o + (size_t)(n + 1) * 4);
+    ws->o_path = o;  o = al(o + (size_t)(n + 2) * 4);
+    return o;
+}
+
+// Dynamic shared memory of the variant with fa' in shared memory.
+size_t pfm_cta_smem_bytes(uint32_t n) { return ((size_t)n + (n + 31) / 32) * 4; }
+
+int pfm_cta_threads() { return PC_NT; }
+
+// Raises (never lowers) the dynamic shared-memory limit of that variant.
+cudaError_t pfm_cta_configure(size_t smem) {
+    static std::mutex mu;
+    static size_t configured = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (smem <= configured) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k_pfm_cta<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) configured = smem;
+    return e;
+}
+
+cudaError_t pfm_cta_blocks_per_sm(bool fa_in_smem, size_t smem, int* out) {
+    return fa_in_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<true>, PC_NT, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<false>, PC_NT, 0);
+}
+
+cudaError_t launch_pfm_cta(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
+                           const PfmCtaWs& ws, int grid, cudaStream_t st) {
+    if (ws.fa_in_smem)
+        k_pfm_cta<true><<<grid, PC_NT, pfm_cta_smem_bytes(ws.n_cap), st>>>(tasks, unit_start, ntasks, work, ws);
+    else
+        k_pfm_cta<false><<<grid, PC_NT, 0, st>>>(tasks, unit_start, ntasks, work, ws);
+    return cudaGetLastError();
+}
+
+}  // namespace mantra

@@ -27,7 +27,10 @@ constexpr uint32_t NONE = 0xFFFFFFFFu;
 enum : int { ST_OK = 0, ST_OVERFLOW = 3, ST_TIMEOUT = 5, ST_CHECK = 6, ST_RNG = 7 };
 
 // Counter slots of a launch (u64 each).
-enum : int { C_WORK = 0, C_SUMINT = 1, C_ESCAN = 2, C_EADD = 3, C_SNEW = 4, C_NOVF = 5, C_FSEG = 6, C_NCOUNT = 8 };
+// C_FSEG: sh/sfm frontier vertices; CTA pfm kernel: frontier rounds.
+// C_XEDGE: CTA pfm kernel, out-edges expanded (both passes); diagnostics only.
+enum : int { C_WORK = 0, C_SUMINT = 1, C_ESCAN = 2, C_EADD = 3, C_SNEW = 4, C_NOVF = 5, C_FSEG = 6, C_XEDGE = 7,
+             C_NCOUNT = 8 };
 
 struct DevGraph {
     uint32_t n;
@@ -374,6 +377,16 @@ struct PfmWs {
     uint32_t list_cap;   // contributing-edge entries per lane (deferred path counts)
 };
 
+// Per-CTA scratch of the pfm search kernel with one CTA per sample.
+struct PfmCtaWs {
+    char* base;          // CTA b uses base + b * stride
+    size_t stride;
+    size_t o_fa, o_exp, o_sig, o_hop, o_pend, o_list, o_first, o_off, o_cu, o_path, o_bits;
+    uint32_t n_cap;      // node capacity of a region
+    uint32_t bits_words; // frontier bitmap words: ceil(n_cap / 32)
+    int fa_in_smem;      // fa' and the frontier bitmap in dynamic shared memory
+};
+
 size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws);
 size_t bfs_smem_bytes(uint32_t A);
 cudaError_t bfs_configure(size_t smem);
@@ -386,6 +399,13 @@ size_t pfm_region_bytes(uint32_t n, uint32_t list_cap, PfmWs* ws);
 int pfm_threads();
 cudaError_t launch_pfm(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
                        const PfmWs& ws, int grid, bool wide, cudaStream_t st);
+size_t pfm_cta_region_bytes(uint32_t n, bool fa_in_smem, PfmCtaWs* ws);
+size_t pfm_cta_smem_bytes(uint32_t n);
+int pfm_cta_threads();
+cudaError_t pfm_cta_configure(size_t smem);
+cudaError_t pfm_cta_blocks_per_sm(bool fa_in_smem, size_t smem, int* out);
+cudaError_t launch_pfm_cta(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
+                           const PfmCtaWs& ws, int grid, cudaStream_t st);
 // One problem of a multi-problem round reduction.
 struct ReduceItem {
     const int* S;        // c rows of n (unused when c = 0)

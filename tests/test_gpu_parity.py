@@ -319,7 +319,7 @@ oreach, _ = o.stats_counts(2, 5, 100)
 print(json.dumps({"ok": bool(ok and np.array_equal(h, oh) and np.array_equal(reach, oreach)),
                   "wide": info["wide_samples"]}))
 '''
-    env = dict(os.environ, MANTRA_PFM_LIST_CAP="40")
+    env = dict(os.environ, MANTRA_PFM_LIST_CAP="40", MANTRA_PFM_KERNEL="lane")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
