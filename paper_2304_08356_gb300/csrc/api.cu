@@ -394,7 +394,9 @@ struct Engine {
         n = std::max(n, pc_n);
         if (pc_mem) { cudaStreamSynchronize(sb); cudaStreamSynchronize(sa); cudaFree(pc_mem); pc_mem = nullptr; }
         const size_t smem = pfm_cta_smem_bytes(n);
-        const bool in_smem = smem + 4096 <= smem_optin;
+        bool in_smem = smem + pfm_cta_static_smem() + 1024 <= smem_optin;
+        // MANTRA_PFM_CTA_SMEM=0 keeps the arrival state in global memory (tests of that variant)
+        if (const char* env = std::getenv("MANTRA_PFM_CTA_SMEM")) in_smem = in_smem && env[0] != '0';
         const size_t region = pfm_cta_region_bytes(n, in_smem, &pcws);
         CU(pfm_cta_configure(in_smem ? smem : 0));
         int per_sm = 0;
@@ -519,16 +521,15 @@ void log_item(const TickItem& it, bool wide, bool cta, const u64* c, double ms) 
                  (unsigned long long)alg_bytes_of(pfm, c[C_ESCAN], c[C_EADD], c[C_SNEW], c[C_FSEG]), ms);
 }
 
-// Which pfm kernel a narrow tick with `samples` pfm samples (largest graph n)
-// uses.  The lane kernel's launch costs at least one warp's serial walk over
-// the stream, the CTA kernel's about one sample's search per resident CTA;
+// Which pfm kernel a narrow tick uses.  The lane kernel's launch costs at
+// least one warp's serial walk over the stream and its per-warp state grows
+// with 32 n; the CTA kernel measured faster at every launch size on the
+// n = 20,000 bursty graph (1.8 vs 70 ms for 231 samples, 82 vs 126 ms for
+// 42,521).  The lane kernel stays the 128-bit re-run.
 // MANTRA_PFM_KERNEL=lane|cta forces one of them.
-bool pfm_use_cta(const Engine& E, uint64_t samples, uint32_t n) {
+bool pfm_use_cta() {
     const char* env = std::getenv("MANTRA_PFM_KERNEL");
-    if (env && std::strcmp(env, "lane") == 0) return false;
-    if (env && std::strcmp(env, "cta") == 0) return true;
-    (void)n;
-    return samples <= (uint64_t)E.num_sms * 16;
+    return !(env && std::strcmp(env, "lane") == 0);
 }
 
 // One tick over `items` (narrow kernels, captured graph), or with `wide` the
@@ -538,18 +539,17 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     int rc;
     if ((rc = E.ensure_tables(std::max<uint32_t>(k, 1))) != MANTRA_OK) return rc;
     uint32_t bn = 0, bA = 0, pn = 0, plc = 0;
-    uint64_t pwarps = 0, psamples = 0;
+    uint64_t pwarps = 0;
     bool any_b = false, any_p = false;
     for (const TickItem& it : items) {
         if (it.job.opt == MANTRA_PFM) {
             any_p = true; pn = std::max(pn, it.G->n); plc = std::max(plc, it.G->dg.cbound);
             pwarps += (it.job.count + 31) / 32;
-            psamples += it.job.count;
         } else {
             any_b = true; bn = std::max(bn, it.G->n); bA = std::max(bA, it.G->A);
         }
     }
-    const bool cta = any_p && !wide && pfm_use_cta(E, psamples, pn);
+    const bool cta = any_p && !wide && pfm_use_cta();
     if (any_b && (rc = E.ensure_bfs(bn, bA)) != MANTRA_OK) return rc;
     if (any_p && cta && (rc = E.ensure_pfm_cta(pn)) != MANTRA_OK) return rc;
     if (any_p && !cta && (rc = E.ensure_pfm(pn, plc, pwarps)) != MANTRA_OK) return rc;

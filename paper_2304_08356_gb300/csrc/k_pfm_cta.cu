@@ -4,8 +4,8 @@
 // this kernel spreads each sample over a CTA instead.  Per sample:
 //   arrivals  label-correcting rounds over the out-CSR.  A vertex u whose
 //             earliest arrival fa(u) improved is expanded over its out-edges
-//             with fa(u) < t <= bound; an edge (u, v, t), v != s, lowers
-//             fa(v) to t.  An improvement of fa(u) from a to b only adds the
+//             with fa(u) < t <= bound; an edge (u, v, t), v != s, lowers v's
+//             arrival to t.  An improvement of fa(u) from a to b only adds the
 //             times in (b, a], so every out-edge is expanded at most once.
 //             bound = the latest in-edge time of z, then fa(z) once z is
 //             reached (later edges reach no vertex earlier than z).
@@ -18,7 +18,18 @@
 //             (App. C path sampler), then the Update step of Algorithm 1.
 // Path counts are 64-bit; a sample whose count overflows goes to the
 // overflow list for the 128-bit lane kernel.
-// State fa' = fa + 1 (0 for the source, NONE when unreached).
+//
+// Arrival state: fsl(v) = the arrival slot of v's earliest arrival (slots of
+// one vertex are numbered in time order, so the minimum slot is the earliest
+// time), NONE when unreached, SRC for s.  An edge carries the slot of its head
+// appearance (out_slot), so expansion never reads edge times, and the DAG
+// test of an edge is out_slot(e) == fsl(v).  A round processes its frontier
+// in chunks of CHUNK vertices: the out-edge ranges of a chunk go to shared
+// memory and every warp walks a contiguous slice of the chunk's edges,
+// tracking the owning range with one ballot per 32 edges.  The first usable
+// out-edge of each expansion is kept (lo_prev), so a re-expansion and the
+// Kahn pass need at most one search of an out-row; searches of several
+// vertices run interleaved.
 #include "mantra_dev.cuh"
 
 #include <mutex>
@@ -27,11 +38,39 @@ namespace mantra {
 
 constexpr int PC_NT = 512;
 constexpr int PC_NW = PC_NT / 32;
+constexpr uint32_t CHUNK = 2 * PC_NT;      // frontier vertices per range table
+constexpr uint32_t SRC = NONE - 1u;        // fsl of the source
 
 template <bool SM>
-__device__ __forceinline__ uint32_t ld_fa(const uint32_t* p) {
+__device__ __forceinline__ uint32_t ldv(const uint32_t* p) {
     if (SM) return *p;
     return __ldcg(p);
+}
+
+// For each k: the first index in [lo[k], hi[k]) whose value exceeds key[k]
+// (hi[k] if none), left in lo[k].  The K searches advance together so their
+// loads overlap.
+template <int K>
+__device__ __forceinline__ void upper_bounds(const uint32_t* __restrict__ a, uint32_t (&lo)[K], uint32_t (&hi)[K],
+                                             const uint32_t (&key)[K]) {
+    for (;;) {
+        bool any = false;
+        uint32_t mid[K], val[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const bool act = lo[k] < hi[k];
+            any |= act;
+            mid[k] = lo[k] + ((hi[k] - lo[k]) >> 1);
+            val[k] = act ? __ldg(a + mid[k]) : 0u;
+        }
+        if (!any) break;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (lo[k] < hi[k]) {
+                if (val[k] <= key[k]) lo[k] = mid[k] + 1u;
+                else hi[k] = mid[k];
+            }
+    }
 }
 
 template <bool FA_SMEM>
@@ -47,25 +86,25 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
     __shared__ uint32_t sh_L, sh_Gc, sh_ovf, sh_err, sh_len;
     __shared__ uint32_t sh_rade[4];
     __shared__ u64 sh_sigma;
+    __shared__ uint32_t cs_off[CHUNK + 1], cs_first[CHUNK], cs_u[CHUNK];   // range table of a chunk
     extern __shared__ __align__(16) uint32_t pc_dyn[];
 
     char* region = ws.base + (size_t)blockIdx.x * ws.stride;
-    uint32_t* fa = FA_SMEM ? pc_dyn : reinterpret_cast<uint32_t*>(region + ws.o_fa);
+    uint32_t* fsl = FA_SMEM ? pc_dyn : reinterpret_cast<uint32_t*>(region + ws.o_fa);
     uint32_t* NB = FA_SMEM ? pc_dyn + ws.n_cap : reinterpret_cast<uint32_t*>(region + ws.o_bits);  // next frontier
-    uint32_t* xp = reinterpret_cast<uint32_t*>(region + ws.o_exp);      // fa' at the last expansion
+    uint32_t* XB = NB + ws.bits_words;                                                              // expanded before
+    uint32_t* lo_prev = reinterpret_cast<uint32_t*>(region + ws.o_exp);  // first out-edge of the last expansion
+    uint32_t* fat = reinterpret_cast<uint32_t*>(region + ws.o_fat);      // fa' = fa + 1 (0: s, NONE: unreached)
     u64* sig = reinterpret_cast<u64*>(region + ws.o_sig);
     uint32_t* hop = reinterpret_cast<uint32_t*>(region + ws.o_hop);
     uint32_t* pend = reinterpret_cast<uint32_t*>(region + ws.o_pend);
-    uint32_t* Fl = reinterpret_cast<uint32_t*>(region + ws.o_list);     // frontier vertices
-    uint32_t* cs_first = reinterpret_cast<uint32_t*>(region + ws.o_first);
-    uint32_t* cs_off = reinterpret_cast<uint32_t*>(region + ws.o_off);
-    uint32_t* cs_u = reinterpret_cast<uint32_t*>(region + ws.o_cu);
+    uint32_t* Fl = reinterpret_cast<uint32_t*>(region + ws.o_list);      // frontier vertices
     uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path);
 
     const uint32_t ntasks = *ntasks_p;
     u64* flush_ctr = nullptr;
     u64 my_escan = 0, my_eadd = 0, my_x = 0, my_rounds = 0;   // my_x, my_rounds: thread 0
-    // the bitmap is all zero between samples (every compaction clears what it reads)
+    // the next-frontier bitmap is all zero between samples (compaction clears what it reads)
     for (uint32_t w = tid; w < ws.bits_words; w += PC_NT) NB[w] = 0u;
     __syncthreads();
 
@@ -75,7 +114,7 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
         const uint32_t per_w = (((nwords + PC_NW - 1) / PC_NW) + 31u) & ~31u;
         const uint32_t w_lo = min((uint32_t)wid * per_w, nwords), w_hi = min(w_lo + per_w, nwords);
         uint32_t cnt = 0;
-        for (uint32_t w = w_lo + lane; w < w_hi; w += 32) cnt += __popc(NB[w]);
+        for (uint32_t w = w_lo + lane; w < w_hi; w += 32) cnt += __popc(ldv<FA_SMEM>(NB + w));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
         if (lane == 0) sm_wcnt[wid] = cnt;
@@ -95,7 +134,7 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
         uint32_t off = sm_wcnt[wid];
         for (uint32_t w0 = w_lo; w0 < w_hi; w0 += 32) {
             const uint32_t w = w0 + lane;
-            uint32_t bits = (w < w_hi) ? NB[w] : 0u;
+            uint32_t bits = (w < w_hi) ? ldv<FA_SMEM>(NB + w) : 0u;
             if (bits) NB[w] = 0u;
             const uint32_t c = __popc(bits);
             uint32_t incl = c;
@@ -117,52 +156,45 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
         return L;
     };
 
-    // Out-edge ranges [lo, hi) of the L listed vertices, compacted to the
-    // non-empty ones with exclusive edge offsets; returns the edge total.
-    // range(u, &lo, &hi) gives one vertex's range.  Contains barriers.
-    auto build_ranges = [&](uint32_t L, auto range) -> uint32_t {
-        uint32_t cbase = 0, ebase = 0;
-        for (uint32_t it = 0; it < L; it += PC_NT) {
-            const uint32_t x = it + tid;
-            uint32_t lo = 0, hi = 0, u = 0;
-            if (x < L) { u = Fl[x]; range(u, &lo, &hi); }
-            const uint32_t cand = hi > lo ? hi - lo : 0u;
-            u64 tot;
-            const u64 ex = block_exclusive_scan64<PC_NT>(((u64)(cand > 0 ? 1u : 0u) << 32) | cand, &tot, sm_scan64);
-            const uint32_t exc = (uint32_t)(ex >> 32), exe = (uint32_t)ex;
-            if (cand > 0) { cs_first[cbase + exc] = lo; cs_off[cbase + exc] = ebase + exe; cs_u[cbase + exc] = u; }
-            cbase += (uint32_t)(tot >> 32);
-            ebase += (uint32_t)tot;
-        }
-        if (tid == 0) { cs_off[cbase] = ebase; sh_Gc = cbase; }
+    // Writes the range table of this thread's (up to) two ranges [lo_j, hi_j)
+    // of vertices u_j; returns the chunk's edge total.  Contains barriers.
+    auto table = [&](const uint32_t (&u)[2], const uint32_t (&lo)[2], const uint32_t (&hi)[2]) -> uint32_t {
+        const uint32_t c0 = hi[0] > lo[0] ? hi[0] - lo[0] : 0u, c1 = hi[1] > lo[1] ? hi[1] - lo[1] : 0u;
+        const uint32_t nr = (c0 > 0) + (c1 > 0);
+        u64 tot;
+        const u64 ex = block_exclusive_scan64<PC_NT>(((u64)nr << 32) | (c0 + c1), &tot, sm_scan64);
+        uint32_t g = (uint32_t)(ex >> 32), e = (uint32_t)ex;
+        if (c0 > 0) { cs_first[g] = lo[0]; cs_off[g] = e; cs_u[g] = u[0]; ++g; e += c0; }
+        if (c1 > 0) { cs_first[g] = lo[1]; cs_off[g] = e; cs_u[g] = u[1]; }
+        const uint32_t Gc = (uint32_t)(tot >> 32), E = (uint32_t)tot;
+        if (tid == 0) { cs_off[Gc] = E; sh_Gc = Gc; }
         __syncthreads();
-        return ebase;
+        return E;
     };
 
-    // Every candidate edge once, in warp windows of 32 consecutive edges; the
-    // owning range of edge j is the last g with cs_off[g] <= j.  Ends with a barrier.
+    // Every edge of the range table once: warp w walks a contiguous slice in
+    // windows of 32; h is the range holding the window's first edge.  Ends
+    // with a barrier.
     auto expand = [&](uint32_t E, auto edge) {
-        const uint32_t Gc = sh_Gc;
-        for (uint32_t base = (uint32_t)wid * 32u; base < E; base += PC_NW * 32u) {
-            uint32_t h0 = 0;
-            if (lane == 0) {
-                uint32_t lo = 0, hi = Gc;
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (cs_off[mid] <= base) lo = mid; else hi = mid;
-                }
-                h0 = lo;
+        const uint32_t per = ((E + PC_NW * 32u - 1u) / (PC_NW * 32u)) * 32u;
+        const uint32_t w_lo = min((uint32_t)wid * per, E), w_hi = min(w_lo + per, E);
+        if (w_lo < w_hi) {
+            const uint32_t Gc = sh_Gc;           // number of ranges; cs_off[Gc] = E
+            uint32_t lo = 0, hi = Gc;            // cs_off[lo] <= w_lo < cs_off[hi]
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (cs_off[mid] <= w_lo) lo = mid; else hi = mid;
             }
-            h0 = __shfl_sync(FULL, h0, 0);
-            const uint32_t j = base + lane;
-            if (j < E) {
-                // the window's 32 edges lie in ranges h0 .. h0 + 31 (each range is non-empty)
-                uint32_t lo = h0, hi = min(h0 + 33u, Gc);
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (cs_off[mid] <= j) lo = mid; else hi = mid;
-                }
-                edge(cs_u[lo], cs_first[lo] + (j - cs_off[lo]));
+            uint32_t h = lo;
+            for (uint32_t base = w_lo; base < w_hi; base += 32u) {
+                const uint32_t k = h + 1u + lane;
+                const uint32_t o = (k <= Gc) ? cs_off[k] : NONE;     // > base for every k
+                const uint32_t d = o - base;
+                const uint32_t mask = __reduce_or_sync(FULL, d < 32u ? (1u << d) : 0u);
+                const uint32_t r = h + __popc(mask & ((2u << lane) - 1u));
+                const uint32_t j = base + lane;
+                if (j < w_hi) edge(cs_u[r], cs_first[r] + (j - cs_off[r]));
+                h += __popc(__ballot_sync(FULL, o <= base + 32u));
             }
         }
         __syncthreads();
@@ -219,10 +251,13 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
         const uint32_t* const out_ptr = g.out_ptr;
         const uint32_t* const out_t = g.out_t;
         const uint32_t* const out_v = g.out_v;
+        const uint32_t* const out_slot = g.out_slot;
+        const uint32_t* const slot_t = g.slot_t;
 
-        for (uint32_t v = tid; v < n; v += PC_NT) { fa[v] = NONE; xp[v] = NONE; }
+        for (uint32_t v = tid; v < n; v += PC_NT) fsl[v] = NONE;
+        for (uint32_t w = tid; w < nwords; w += PC_NT) XB[w] = 0u;
         __syncthreads();
-        if (tid == 0 && live) { fa[s] = 0u; NB[s >> 5] |= 1u << (s & 31); }
+        if (tid == 0 && live) { fsl[s] = SRC; NB[s >> 5] |= 1u << (s & 31); }
         __syncthreads();
 
         // ---- earliest arrivals ----
@@ -230,28 +265,62 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
         while (live) {
             const uint32_t L = compact(nwords);
             if (L == 0) break;
-            const uint32_t E = build_ranges(L, [&](uint32_t u, uint32_t* lo, uint32_t* hi) {
-                const uint32_t fu = fa[u], pu = xp[u];
-                xp[u] = fu;
-                const uint32_t r0 = out_ptr[u], r1 = out_ptr[u + 1];
-                *lo = (fu == 0u) ? r0 : upper_bound_u32(out_t, r0, r1, fu - 1u);   // t > fa(u)
-                const uint32_t top = (pu == NONE) ? bound : min(bound, pu - 1u);  // t <= previous fa(u)
-                *hi = upper_bound_u32(out_t, *lo, r1, top);
-            });
-            if (tid == 0) { my_x += E; ++my_rounds; }
-            expand(E, [&](uint32_t, uint32_t e) {
-                const uint32_t v = out_v[e];
-                if (v == s) return;
-                const uint32_t nv = out_t[e] + 1u;
-                if (nv >= ld_fa<FA_SMEM>(fa + v)) return;
-                if (nv < atomicMin(fa + v, nv)) atomicOr(NB + (v >> 5), 1u << (v & 31));
-            });
+            if (tid == 0) ++my_rounds;
+            for (uint32_t c0 = 0; c0 < L; c0 += CHUNK) {
+                // ranges of this thread's two vertices: lo = first t > fa(u) (search 2j),
+                // hi = first t > bound below the previous expansion's lo (search 2j+1)
+                uint32_t u[2], lo[4], hi[4], key[4];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const uint32_t x = c0 + (uint32_t)tid + (uint32_t)j * PC_NT;
+                    lo[2 * j] = hi[2 * j] = lo[2 * j + 1] = hi[2 * j + 1] = 0u;
+                    key[2 * j] = key[2 * j + 1] = 0u;
+                    u[j] = NONE;
+                    if (x < L) {
+                        const uint32_t uu = Fl[x];
+                        u[j] = uu;
+                        const uint32_t r0 = out_ptr[uu], r1 = out_ptr[uu + 1];
+                        const bool again = (ldv<FA_SMEM>(XB + (uu >> 5)) >> (uu & 31)) & 1u;
+                        const uint32_t cap = again ? lo_prev[uu] : r1;
+                        const uint32_t fu = ldv<FA_SMEM>(fsl + uu);
+                        lo[2 * j] = hi[2 * j] = r0;
+                        if (fu != SRC) { hi[2 * j] = r1; key[2 * j] = __ldg(slot_t + fu); }
+                        lo[2 * j + 1] = r0; hi[2 * j + 1] = cap; key[2 * j + 1] = bound;
+                    }
+                }
+                upper_bounds<4>(out_t, lo, hi, key);
+                uint32_t rl[2], rh[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    rl[j] = lo[2 * j]; rh[j] = lo[2 * j + 1];
+                    if (u[j] != NONE) {
+                        lo_prev[u[j]] = rl[j];
+                        atomicOr(XB + (u[j] >> 5), 1u << (u[j] & 31));
+                    }
+                }
+                const uint32_t E = table(u, rl, rh);
+                if (tid == 0) my_x += E;
+                expand(E, [&](uint32_t, uint32_t e) {
+                    const uint32_t v = __ldg(out_v + e), sl = __ldg(out_slot + e);
+                    if (v == s || sl >= ldv<FA_SMEM>(fsl + v)) return;
+                    if (sl < atomicMin(fsl + v, sl)) atomicOr(NB + (v >> 5), 1u << (v & 31));
+                });
+            }
             if (!stats) {
-                const uint32_t fz = ld_fa<FA_SMEM>(fa + z);
-                if (fz != NONE) bound = min(bound, fz - 1u);
+                const uint32_t fz = ldv<FA_SMEM>(fsl + z);
+                if (fz != NONE) bound = min(bound, __ldg(slot_t + fz));
             }
         }
-        const bool reached = live && (stats || ld_fa<FA_SMEM>(fa + z) != NONE);
+        const bool reached = live && (stats || ldv<FA_SMEM>(fsl + z) != NONE);
+
+        // fa' of every vertex, for the DAG tests of in-edges
+        if (live) {
+            for (uint32_t v = tid; v < n; v += PC_NT) {
+                const uint32_t f = ldv<FA_SMEM>(fsl + v);
+                fat[v] = f == SRC ? 0u : (f == NONE ? NONE : __ldg(slot_t + f) + 1u);
+            }
+            __syncthreads();
+        }
 
         // edges of the prefix-foremost scan window (same count as the lane kernel):
         // stream edges with tmin_out(s) <= t <= fa(z) (z's latest in-edge time when
@@ -272,12 +341,13 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
         // of path-count updates, counted also when z is not reached
         if (live) {
             for (uint32_t v = tid; v < n; v += PC_NT) {
-                const uint32_t fv = ld_fa<FA_SMEM>(fa + v);
+                const uint32_t fv = __ldcg(fat + v);
                 if (fv == NONE || v == s || fv - 1u > bound) continue;
-                const uint32_t a = lower_bound_u32(g.slot_t, g.slot_ptr[v], g.slot_ptr[v + 1], fv - 1u);
+                const uint32_t a = ldv<FA_SMEM>(fsl + v);
+                const uint32_t e1 = __ldg(g.slot_in + a + 1);
                 uint32_t c = 0;
-                for (uint32_t e = g.slot_in[a]; e < g.slot_in[a + 1]; ++e)
-                    if (ld_fa<FA_SMEM>(fa + g.in_u[e]) < fv) ++c;
+                for (uint32_t e = __ldg(g.slot_in + a); e < e1; ++e)
+                    if (__ldcg(fat + __ldg(g.in_u + e)) < fv) ++c;
                 my_eadd += c;
                 if (reached) {
                     pend[v] = c;
@@ -292,20 +362,36 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
             for (;;) {
                 const uint32_t L = compact(nwords);
                 if (L == 0) break;
-                const uint32_t E = build_ranges(L, [&](uint32_t u, uint32_t* lo, uint32_t* hi) {
-                    const uint32_t fu = fa[u];
-                    const uint32_t r0 = out_ptr[u], r1 = out_ptr[u + 1];
-                    *lo = (fu == 0u) ? r0 : upper_bound_u32(out_t, r0, r1, fu - 1u);
-                    *hi = upper_bound_u32(out_t, *lo, r1, bound);
-                });
-                if (tid == 0) { my_x += E; ++my_rounds; }
-                expand(E, [&](uint32_t u, uint32_t e) {
-                    const uint32_t v = out_v[e];
-                    if (v == s || ld_fa<FA_SMEM>(fa + v) != out_t[e] + 1u) return;   // not v's earliest arrival
-                    if (stats) atomicMin(hop + v, __ldcg(hop + u) + 1u);
-                    else if (!SigOps<false>::atomic_add(sig + v, __ldcg(sig + u))) sh_ovf = 1;
-                    if (atomicSub(pend + v, 1u) == 1u) atomicOr(NB + (v >> 5), 1u << (v & 31));
-                });
+                if (tid == 0) ++my_rounds;
+                for (uint32_t c0 = 0; c0 < L; c0 += CHUNK) {
+                    // [lo_prev(u), first t > bound): u's out-edges after its arrival
+                    uint32_t u[2], lo[2], hi[2], key[2];
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const uint32_t x = c0 + (uint32_t)tid + (uint32_t)j * PC_NT;
+                        lo[j] = hi[j] = key[j] = 0u;
+                        u[j] = NONE;
+                        if (x < L) {
+                            const uint32_t uu = Fl[x];
+                            u[j] = uu;
+                            lo[j] = lo_prev[uu];
+                            hi[j] = out_ptr[uu + 1];
+                            key[j] = bound;
+                        }
+                    }
+                    uint32_t rl[2] = {lo[0], lo[1]};
+                    upper_bounds<2>(out_t, lo, hi, key);
+                    const uint32_t rh[2] = {lo[0], lo[1]};
+                    const uint32_t E = table(u, rl, rh);
+                    if (tid == 0) my_x += E;
+                    expand(E, [&](uint32_t uu, uint32_t e) {
+                        const uint32_t v = __ldg(out_v + e), sl = __ldg(out_slot + e);
+                        if (v == s || ldv<FA_SMEM>(fsl + v) != sl) return;   // not v's earliest arrival
+                        if (stats) atomicMin(hop + v, __ldcg(hop + uu) + 1u);
+                        else if (!SigOps<false>::atomic_add(sig + v, __ldcg(sig + uu))) sh_ovf = 1;
+                        if (atomicSub(pend + v, 1u) == 1u) atomicOr(NB + (v >> 5), 1u << (v & 31));
+                    });
+                }
             }
         }
 
@@ -314,7 +400,7 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
             if (reached) {
                 for (uint32_t v0 = 0; v0 < n; v0 += PC_NT) {
                     const uint32_t v = v0 + tid;
-                    const bool r = v < n && v != s && ld_fa<FA_SMEM>(fa + v) != NONE;
+                    const bool r = v < n && v != s && ldv<FA_SMEM>(fsl + v) != NONE;
                     const uint32_t h = r ? __ldcg(hop + v) : NONE;
                     const unsigned grp = __match_any_sync(FULL, h);
                     if (r && lane == __ffs(grp) - 1) atomicAdd(job.cnt + h, (u64)__popc(grp));
@@ -342,8 +428,8 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
             uint32_t v = z, cnt = 1;
             if (lane == 0) path[0] = z;
             while (!err && v != s) {
-                const uint32_t fv = ld_fa<FA_SMEM>(fa + v);
-                const uint32_t a = lower_bound_u32(g.slot_t, g.slot_ptr[v], g.slot_ptr[v + 1], fv - 1u);
+                const uint32_t fv = __ldcg(fat + v);
+                const uint32_t a = ldv<FA_SMEM>(fsl + v);
                 const uint32_t e_lo = g.slot_in[a], e_hi = g.slot_in[a + 1];
                 uint32_t nxt = NONE;
                 for (uint32_t e0 = e_lo; e0 < e_hi; e0 += 32) {
@@ -352,7 +438,7 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
                     uint32_t w = 0;
                     if (e < e_hi) {
                         w = g.in_u[e];
-                        if (ld_fa<FA_SMEM>(fa + w) < fv) wt = __ldcg(sig + w);
+                        if (__ldcg(fat + w) < fv) wt = __ldcg(sig + w);
                     }
                     const u64 incl = warp_inclusive_sum(wt);
                     const unsigned msk = __ballot_sync(FULL, xs < incl);
@@ -428,8 +514,9 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
     }
 }
 
-// Region of one CTA (global memory); fa' and the frontier bitmap are in
-// shared memory instead when fa_in_smem.
+// Region of one CTA (global memory).  The arrival slots and the two bitmaps
+// (next frontier, expanded before) are in shared memory instead when
+// fa_in_smem.
 size_t pfm_cta_region_bytes(uint32_t n, bool fa_in_smem, PfmCtaWs* ws) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t o = 0;
@@ -437,21 +524,25 @@ size_t pfm_cta_region_bytes(uint32_t n, bool fa_in_smem, PfmCtaWs* ws) {
     ws->bits_words = (n + 31) / 32;
     ws->fa_in_smem = fa_in_smem ? 1 : 0;
     ws->o_fa = o;    if (!fa_in_smem) o = al(o + (size_t)n * 4);
-    ws->o_bits = o;  if (!fa_in_smem) o = al(o + (size_t)ws->bits_words * 4);
+    ws->o_bits = o;  if (!fa_in_smem) o = al(o + (size_t)ws->bits_words * 8);
     ws->o_exp = o;   o = al(o + (size_t)n * 4);
+    ws->o_fat = o;   o = al(o + (size_t)n * 4);
     ws->o_sig = o;   o = al(o + (size_t)n * 8);
     ws->o_hop = o;   o = al(o + (size_t)n * 4);
     ws->o_pend = o;  o = al(o + (size_t)n * 4);
     ws->o_list = o;  o = al(o + (size_t)(n + 1) * 4);
-    ws->o_first = o; o = al(o + (size_t)(n + 1) * 4);
-    ws->o_off = o;   o = al(o + (size_t)(n + 2) * 4);
-    ws->o_cu = o;    o = al(o + (size_t)(n + 1) * 4);
     ws->o_path = o;  o = al(o + (size_t)(n + 2) * 4);
     return o;
 }
 
-// Dynamic shared memory of the variant with fa' in shared memory.
-size_t pfm_cta_smem_bytes(uint32_t n) { return ((size_t)n + (n + 31) / 32) * 4; }
+// Dynamic shared memory of the variant with the arrival state in shared memory.
+size_t pfm_cta_smem_bytes(uint32_t n) { return ((size_t)n + 2 * ((n + 31) / 32)) * 4; }
+
+// Static shared memory of the kernel (range table, task copy, scratch).
+size_t pfm_cta_static_smem() {
+    cudaFuncAttributes a{};
+    return cudaFuncGetAttributes(&a, k_pfm_cta<true>) == cudaSuccess ? a.sharedSizeBytes : 16384;
+}
 
 int pfm_cta_threads() { return PC_NT; }
 

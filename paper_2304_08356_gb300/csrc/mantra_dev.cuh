@@ -381,10 +381,10 @@ struct PfmWs {
 struct PfmCtaWs {
     char* base;          // CTA b uses base + b * stride
     size_t stride;
-    size_t o_fa, o_exp, o_sig, o_hop, o_pend, o_list, o_first, o_off, o_cu, o_path, o_bits;
+    size_t o_fa, o_bits, o_exp, o_fat, o_sig, o_hop, o_pend, o_list, o_path;
     uint32_t n_cap;      // node capacity of a region
-    uint32_t bits_words; // frontier bitmap words: ceil(n_cap / 32)
-    int fa_in_smem;      // fa' and the frontier bitmap in dynamic shared memory
+    uint32_t bits_words; // words of each bitmap: ceil(n_cap / 32)
+    int fa_in_smem;      // arrival slots and bitmaps in dynamic shared memory
 };
 
 size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws);
@@ -401,6 +401,7 @@ cudaError_t launch_pfm(const Task* tasks, const uint64_t* unit_start, const uint
                        const PfmWs& ws, int grid, bool wide, cudaStream_t st);
 size_t pfm_cta_region_bytes(uint32_t n, bool fa_in_smem, PfmCtaWs* ws);
 size_t pfm_cta_smem_bytes(uint32_t n);
+size_t pfm_cta_static_smem();
 int pfm_cta_threads();
 cudaError_t pfm_cta_configure(size_t smem);
 cudaError_t pfm_cta_blocks_per_sm(bool fa_in_smem, size_t smem, int* out);

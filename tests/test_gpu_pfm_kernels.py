@@ -111,3 +111,42 @@ def test_pfm_kernels_agree_on_counters(M, monkeypatch):
     assert np.array_equal(h0, h1)
     for key in ("edges_scanned", "sigma_adds", "sum_int_len", "rade_num"):
         assert i0[key] == i1[key], key
+
+
+def test_pfm_cta_global_state_variant():
+    """The CTA kernel with its arrival state in global memory (the variant
+    graphs too large for shared memory take), forced in a child process."""
+    import json
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import json, sys
+sys.path.insert(0, ".")
+sys.path.insert(0, "tests")
+import numpy as np
+from paper_2304_08356_gb300 import build as B, synth
+B.build()
+from paper_2304_08356_gb300 import mantra as M
+from oracle import oracle as O
+from test_gpu_parity import _graphs
+ok = True
+for case in (0, 2, 4, 5):
+    _, (u, v, t), n = _graphs()[case]
+    g = M.Graph(u, v, t, n=n); o = O.Graph(u, v, t, n=n)
+    ok &= g.sample_paths(2, 6, 0, 400, cap=g.n + 1) == o.samples(2, 6, 0, 400, cap=o.n + 1)
+    st, reach = g.temporal_stats(2, 0.1, 5, r_override=80)
+    oreach, _ = o.stats_counts(2, 5, 80)
+    ok &= bool(np.array_equal(reach, oreach))
+u, v, t = synth.chung_lu_bursty(n=1500, m=30000, seed=21)
+g = M.Graph(u, v, t); o = O.Graph(u, v, t)
+_, h, _ = g.estimate(2, 0.1, 0.1, 4, fixed_r=600)
+_, oh, _ = o.estimate(2, 0.1, 0.1, 4, fixed_r=600)
+ok &= bool(np.array_equal(h, oh))
+print(json.dumps({"ok": bool(ok)}))
+'''
+    env = dict(os.environ, MANTRA_PFM_KERNEL="cta", MANTRA_PFM_CTA_SMEM="0")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert json.loads(r.stdout.strip().splitlines()[-1])["ok"]
