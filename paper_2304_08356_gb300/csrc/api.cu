@@ -338,7 +338,7 @@ struct Engine {
         A = std::max(A, bfs_A);
         if (bfs_mem) { cudaStreamSynchronize(sa); cudaFree(bfs_mem); bfs_mem = nullptr; }
         const size_t smem = bfs_smem_bytes(A);
-        const bool in_smem = smem + 2048 <= smem_optin;
+        const bool in_smem = smem + bfs_static_smem() + 1024 <= smem_optin;
         const size_t region = bfs_region_bytes(n, A, in_smem, &bws);
         const size_t budget = free_device_bytes() / 3;
         int grid = num_sms;

@@ -46,9 +46,6 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
     uint32_t* lev = reinterpret_cast<uint32_t*>(region + ws.o_lev);
     uint32_t* seg_b = reinterpret_cast<uint32_t*>(region + ws.o_segb);
     uint32_t* seg_u = reinterpret_cast<uint32_t*>(region + ws.o_segu);
-    uint32_t* cs_seg = reinterpret_cast<uint32_t*>(region + ws.o_csseg);
-    uint32_t* cs_first = reinterpret_cast<uint32_t*>(region + ws.o_csfirst);
-    uint32_t* cs_off = reinterpret_cast<uint32_t*>(region + ws.o_csoff);
     uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path);
     uint32_t* VB = reinterpret_cast<uint32_t*>(region + ws.o_vb);   // vertex bitmap (stats)
 
@@ -68,6 +65,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
     __shared__ uint32_t sh_rade[4];
     __shared__ uint32_t sh_d, sh_len;
     __shared__ u128 sh_sigma;
+    __shared__ uint32_t cs_off[BFS_NT + 1], cs_first[BFS_NT], cs_fb[BFS_NT], cs_fe[BFS_NT];   // range table
 
     if (ws.bits_in_smem) {
         for (uint32_t w = tid; w < 2 * ws.bits_words; w += BFS_NT) V[w] = 0u;
@@ -136,20 +134,11 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
         __syncthreads();
         while (live) {
             // ---- segments of level k ----
-            uint32_t G, Gc, E;
+            uint32_t G;
             if (k == 0) {
-                if (tid == 0) {
-                    seg_b[0] = 0; seg_u[0] = s; Fc[0] = (Sig)1; Ft[0] = 0;
-                    const uint32_t lo = g.out_ptr[s], hi = g.out_ptr[s + 1];
-                    const uint32_t last = lower_bound_u32(g.out_t, lo, hi, tz);
-                    cs_seg[0] = 0; cs_first[0] = lo; cs_off[0] = 0; cs_off[1] = last - lo;
-                    sm_scan[0] = (last > lo) ? 1u : 0u;
-                    sm_scan[1] = last - lo;
-                }
+                if (tid == 0) { seg_b[0] = 0; seg_u[0] = s; Fc[0] = (Sig)1; Ft[0] = 0; my_fseg += 1; }
                 __syncthreads();
-                G = 1; Gc = sm_scan[0]; E = sm_scan[1];
-                __syncthreads();
-                if (tid == 0) my_fseg += 1;
+                G = 1;
             } else {
                 const uint32_t* Fk = F + lev[k];
                 // B1: frontier attributes, segment heads and per-vertex running sums
@@ -184,34 +173,6 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                     my_fseg += G;
                     if (sh_scan_ovf && !stats) sh_ovf = 1;
                 }
-                __syncthreads();
-                // B2: candidate edge ranges per segment and their compaction
-                uint32_t cbase = 0, ebase = 0;
-                const uint32_t* const g_out_ptr = g.out_ptr;
-                const uint32_t* const g_out_t = g.out_t;
-                for (uint32_t it = 0; it < G; it += BFS_NT) {
-                    const uint32_t gi = it + tid;
-                    uint32_t cand = 0, first = 0;
-                    if (gi < G) {
-                        const uint32_t fb = seg_b[gi];
-                        const uint32_t u = seg_u[gi];
-                        const uint32_t tmin = Ft[fb];
-                        const uint32_t lo = g_out_ptr[u], hi = g_out_ptr[u + 1];
-                        first = upper_bound_u32(g_out_t, lo, hi, tmin);
-                        const uint32_t last = lower_bound_u32(g_out_t, first, hi, tz);
-                        cand = last > first ? last - first : 0;
-                    }
-                    u64 tot;
-                    const u64 ex = block_exclusive_scan64<BFS_NT>(((u64)(cand > 0 ? 1u : 0u) << 32) | cand, &tot,
-                                                                  sm_scan64);
-                    const uint32_t exc = (uint32_t)(ex >> 32), exe = (uint32_t)ex;
-                    if (cand > 0) {
-                        cs_seg[cbase + exc] = gi; cs_first[cbase + exc] = first; cs_off[cbase + exc] = ebase + exe;
-                    }
-                    cbase += (uint32_t)(tot >> 32); ebase += (uint32_t)tot;
-                }
-                Gc = cbase; E = ebase;
-                if (tid == 0) cs_off[Gc] = E;
                 __syncthreads();
             }
             if (sh_ovf) break;
@@ -253,43 +214,55 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                 if (sh_found || sh_ovf) break;
             }
 
-            // ---- push expansion of level k ----
+            // ---- push expansion of level k, BFS_NT segments per range table ----
+            // candidate out-edges of segment gi (vertex u): first t > u's earliest
+            // frontier time (every out-edge of s at level 0) up to the first t >= tz
+            const uint32_t* const g_out_ptr = g.out_ptr;
+            const uint32_t* const g_out_t = g.out_t;
             const uint32_t* const g_out_slot = g.out_slot;
-            const uint32_t* const g_out_t2 = g.out_t;
-            for (uint32_t base = (uint32_t)wid * 32u; base < E; base += BFS_NW * 32u) {
-                uint32_t h0 = 0;
-                if (lane == 0) {
-                    uint32_t lo = 0, hi = Gc;       // last h with cs_off[h] <= base
-                    while (hi - lo > 1) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (cs_off[mid] <= base) lo = mid; else hi = mid;
-                    }
-                    h0 = lo;
+            for (uint32_t c0 = 0; c0 < G; c0 += BFS_NT) {
+                const uint32_t gi = c0 + tid;
+                uint32_t lo2[2] = {0u, 0u}, hi2[2] = {0u, 0u}, key2[2] = {0u, 0u};
+                uint32_t fb = 0, fe = 0;
+                if (gi < G) {
+                    fb = seg_b[gi];
+                    fe = (gi + 1 < G) ? seg_b[gi + 1] : L;
+                    const uint32_t u = seg_u[gi];
+                    const uint32_t r0 = g_out_ptr[u], r1 = g_out_ptr[u + 1];
+                    lo2[0] = r0; hi2[0] = (k == 0) ? r0 : r1; key2[0] = (k == 0) ? 0u : Ft[fb];
+                    lo2[1] = r0; hi2[1] = (tz == 0) ? r0 : r1; key2[1] = tz - 1u;
                 }
-                h0 = __shfl_sync(0xFFFFFFFFu, h0, 0);
-                const uint32_t j = base + lane;
-                if (j < E) {
-                    uint32_t lo = h0, hi = min(h0 + 33u, Gc);
-                    while (hi - lo > 1) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (cs_off[mid] <= j) lo = mid; else hi = mid;
-                    }
-                    const uint32_t gi = cs_seg[lo];
-                    const uint32_t e = cs_first[lo] + (j - cs_off[lo]);
-                    const uint32_t a = g_out_slot[e];
+                upper_bounds<2>(g_out_t, lo2, hi2, key2);
+                const uint32_t first = lo2[0], last = lo2[1];
+                const uint32_t cand = (gi < G && last > first) ? last - first : 0u;
+                u64 tot;
+                const u64 ex = block_exclusive_scan64<BFS_NT>(((u64)(cand > 0 ? 1u : 0u) << 32) | cand, &tot,
+                                                              sm_scan64);
+                if (cand > 0) {
+                    const uint32_t x = (uint32_t)(ex >> 32);
+                    cs_first[x] = first; cs_off[x] = (uint32_t)ex; cs_fb[x] = fb; cs_fe[x] = fe;
+                }
+                const uint32_t Gc = (uint32_t)(tot >> 32), E = (uint32_t)tot;
+                if (tid == 0) cs_off[Gc] = E;
+                __syncthreads();
+                const uint32_t per = ((E + BFS_NW * 32u - 1u) / (BFS_NW * 32u)) * 32u;
+                const uint32_t w_lo = min((uint32_t)wid * per, E), w_hi = min(w_lo + per, E);
+                lbs_walk(cs_off, Gc, w_lo, w_hi, [&](uint32_t r, uint32_t j) {
+                    const uint32_t e = cs_first[r] + (j - cs_off[r]);
+                    const uint32_t a = __ldg(g_out_slot + e), t = __ldg(g_out_t + e);
                     ++my_escan;
                     if (!((V[a >> 5] >> (a & 31)) & 1u)) {
-                        const uint32_t t = g_out_t2[e];
-                        const uint32_t fb = seg_b[gi], fe = (gi + 1 < G) ? seg_b[gi + 1] : L;
-                        uint32_t idx = fb;
-                        if (fe - fb > 1) idx = lower_bound_u32(Ft, fb, fe, t) - 1;   // last Ft < t
+                        const uint32_t rb = cs_fb[r], re = cs_fe[r];
+                        uint32_t idx = rb;
+                        if (re - rb > 1) idx = lower_bound_u32(Ft, rb, re, t) - 1;   // last Ft < t
                         atomicOr(N + (a >> 5), 1u << (a & 31));
                         if (!SigOps<WIDE>::atomic_add(sig + a, Fc[idx]) && !stats) sh_ovf = 1;
                         ++my_eadd;
                     }
-                }
+                });
+                __syncthreads();
+                if (sh_ovf) break;
             }
-            __syncthreads();
             if (sh_ovf) break;
 
             // ---- compact the next-level bitmap into F_{k+1} ----
@@ -548,9 +521,6 @@ size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws) {
     ws->o_lev = o;     o = al(o + (size_t)(n + 3) * 4);
     ws->o_segb = o;    o = al(o + (size_t)(n + 2) * 4);
     ws->o_segu = o;    o = al(o + (size_t)(n + 2) * 4);
-    ws->o_csseg = o;   o = al(o + (size_t)(n + 2) * 4);
-    ws->o_csfirst = o; o = al(o + (size_t)(n + 2) * 4);
-    ws->o_csoff = o;   o = al(o + (size_t)(n + 2) * 4);
     ws->o_path = o;    o = al(o + (size_t)(n + 2) * 4);
     ws->o_vb = o;      o = al(o + (size_t)((n + 31) / 32 + 1) * 4);
     ws->o_bits = o;
@@ -560,6 +530,12 @@ size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws) {
 }
 
 size_t bfs_smem_bytes(uint32_t A) { return (size_t)2 * ((A + 31) / 32) * 4; }
+
+// Static shared memory of the kernel (range table, task copy, scan scratch).
+size_t bfs_static_smem() {
+    cudaFuncAttributes a{};
+    return cudaFuncGetAttributes(&a, k_bfs<true>) == cudaSuccess ? a.sharedSizeBytes : 32768;
+}
 
 // Raises (never lowers) the kernels' dynamic shared-memory limit, so callers
 // with different graph sizes do not undo each other's setting.

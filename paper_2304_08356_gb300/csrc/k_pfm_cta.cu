@@ -47,32 +47,6 @@ __device__ __forceinline__ uint32_t ldv(const uint32_t* p) {
     return __ldcg(p);
 }
 
-// For each k: the first index in [lo[k], hi[k]) whose value exceeds key[k]
-// (hi[k] if none), left in lo[k].  The K searches advance together so their
-// loads overlap.
-template <int K>
-__device__ __forceinline__ void upper_bounds(const uint32_t* __restrict__ a, uint32_t (&lo)[K], uint32_t (&hi)[K],
-                                             const uint32_t (&key)[K]) {
-    for (;;) {
-        bool any = false;
-        uint32_t mid[K], val[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const bool act = lo[k] < hi[k];
-            any |= act;
-            mid[k] = lo[k] + ((hi[k] - lo[k]) >> 1);
-            val[k] = act ? __ldg(a + mid[k]) : 0u;
-        }
-        if (!any) break;
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-            if (lo[k] < hi[k]) {
-                if (val[k] <= key[k]) lo[k] = mid[k] + 1u;
-                else hi[k] = mid[k];
-            }
-    }
-}
-
 template <bool FA_SMEM>
 __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const uint64_t* unit_start,
                                                      const uint32_t* ntasks_p, u64* work, const PfmCtaWs ws) {
@@ -178,25 +152,7 @@ __global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const u
     auto expand = [&](uint32_t E, auto edge) {
         const uint32_t per = ((E + PC_NW * 32u - 1u) / (PC_NW * 32u)) * 32u;
         const uint32_t w_lo = min((uint32_t)wid * per, E), w_hi = min(w_lo + per, E);
-        if (w_lo < w_hi) {
-            const uint32_t Gc = sh_Gc;           // number of ranges; cs_off[Gc] = E
-            uint32_t lo = 0, hi = Gc;            // cs_off[lo] <= w_lo < cs_off[hi]
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (cs_off[mid] <= w_lo) lo = mid; else hi = mid;
-            }
-            uint32_t h = lo;
-            for (uint32_t base = w_lo; base < w_hi; base += 32u) {
-                const uint32_t k = h + 1u + lane;
-                const uint32_t o = (k <= Gc) ? cs_off[k] : NONE;     // > base for every k
-                const uint32_t d = o - base;
-                const uint32_t mask = __reduce_or_sync(FULL, d < 32u ? (1u << d) : 0u);
-                const uint32_t r = h + __popc(mask & ((2u << lane) - 1u));
-                const uint32_t j = base + lane;
-                if (j < w_hi) edge(cs_u[r], cs_first[r] + (j - cs_off[r]));
-                h += __popc(__ballot_sync(FULL, o <= base + 32u));
-            }
-        }
+        lbs_walk(cs_off, sh_Gc, w_lo, w_hi, [&](uint32_t r, uint32_t j) { edge(cs_u[r], cs_first[r] + (j - cs_off[r])); });
         __syncthreads();
     };
 

@@ -349,6 +349,60 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t 
     return lo;
 }
 
+// For each k: the first index in [lo[k], hi[k]) whose value exceeds key[k]
+// (hi[k] if none), left in lo[k].  The K searches advance together so their
+// loads overlap.
+template <int K>
+__device__ __forceinline__ void upper_bounds(const uint32_t* __restrict__ a, uint32_t (&lo)[K], uint32_t (&hi)[K],
+                                             const uint32_t (&key)[K]) {
+    for (;;) {
+        bool any = false;
+        uint32_t mid[K], val[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const bool act = lo[k] < hi[k];
+            any |= act;
+            mid[k] = lo[k] + ((hi[k] - lo[k]) >> 1);
+            val[k] = act ? __ldg(a + mid[k]) : 0u;
+        }
+        if (!any) break;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (lo[k] < hi[k]) {
+                if (val[k] <= key[k]) lo[k] = mid[k] + 1u;
+                else hi[k] = mid[k];
+            }
+    }
+}
+
+// Walks the edges [w_lo, w_hi) of a range table -- Gc ranges, range g owns
+// the edges [off[g], off[g+1]), off[Gc] = the edge total -- in windows of 32
+// consecutive edges, calling edge(g, j) for every edge j.  The window's range
+// starts are found with one reduce-or over the next 32 offsets (every range
+// is non-empty, so at most 32 start inside a window).  Called by a whole warp
+// with warp-uniform bounds.
+template <typename F>
+__device__ __forceinline__ void lbs_walk(const uint32_t* off, uint32_t Gc, uint32_t w_lo, uint32_t w_hi, F edge) {
+    const uint32_t lane = threadIdx.x & 31;
+    if (w_lo >= w_hi) return;
+    uint32_t lo = 0, hi = Gc;                 // off[lo] <= w_lo < off[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= w_lo) lo = mid; else hi = mid;
+    }
+    uint32_t h = lo;
+    for (uint32_t base = w_lo; base < w_hi; base += 32u) {
+        const uint32_t k = h + 1u + lane;
+        const uint32_t o = (k <= Gc) ? off[k] : 0xFFFFFFFFu;   // > base for every k
+        const uint32_t d = o - base;
+        const uint32_t mask = __reduce_or_sync(0xFFFFFFFFu, d < 32u ? (1u << d) : 0u);
+        const uint32_t g = h + __popc(mask & ((2u << lane) - 1u));
+        const uint32_t j = base + lane;
+        if (j < w_hi) edge(g, j);
+        h += __popc(__ballot_sync(0xFFFFFFFFu, o <= base + 32u));
+    }
+}
+
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, ST_OK, code); }
 
 // Records sample i for the 128-bit / in-order re-run (a job without a list
@@ -363,7 +417,7 @@ __device__ __forceinline__ void push_overflow(const Job& job, uint64_t i) {
 struct BfsWs {
     char* base;          // CTA b uses base + b * stride
     size_t stride;
-    size_t o_sig, o_fc, o_f, o_ft, o_lev, o_segb, o_segu, o_csseg, o_csfirst, o_csoff, o_path, o_bits, o_vb;
+    size_t o_sig, o_fc, o_f, o_ft, o_lev, o_segb, o_segu, o_path, o_bits, o_vb;
     int bits_in_smem;    // visited / next bitmaps in dynamic shared memory
     uint32_t bits_words; // capacity of each bitmap (words): ceil(A_max / 32)
 };
@@ -389,6 +443,7 @@ struct PfmCtaWs {
 
 size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws);
 size_t bfs_smem_bytes(uint32_t A);
+size_t bfs_static_smem();
 cudaError_t bfs_configure(size_t smem);
 // Task-table launches: work unit u of the launch belongs to task
 // task_of_unit(unit_start, *ntasks, u); the first unused unit ends a CTA/warp.
