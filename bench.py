@@ -136,22 +136,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_source_digest():
+KSRC = {"k_bfs": "k_bfs.cu", "k_pfm_cta": "k_pfm_cta.cu", "k_pfm": "k_pfm.cu"}
+
+
+def kernel_source_digest(kernel: str):
+    """Digest of one kernel's source and the shared device header."""
     h = hashlib.sha256()
-    for f in ("k_bfs.cu", "k_pfm.cu", "mantra_dev.cuh"):
+    for f in (KSRC[kernel], "mantra_dev.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2304_08356_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """ncu DRAM bytes per launch recorded for this kernel source, or None."""
+def recorded_traffic(kernel: str, alg_bytes_per_launch: float):
+    """DRAM bytes per launch for this kernel source, or None.
+
+    profiles/traffic.txt holds, per kernel and source digest, the ratio of
+    ncu's dram__bytes_read.sum + dram__bytes_write.sum to the library's
+    algorithmic bytes over the same launches; a launch's traffic is that
+    ratio times its algorithmic bytes."""
     if not os.path.exists(TRAFFIC):
         return None
-    dig = kernel_source_digest()
+    dig = kernel_source_digest(kernel)
     for line in open(TRAFFIC):
         f = line.split()
         if len(f) >= 3 and not line.startswith("#") and f[0] == kernel and f[1] == dig:
-            return float(f[2])
+            return float(f[2]) * alg_bytes_per_launch
     return None
 
 
@@ -389,7 +398,8 @@ def main():
     seq_rate = sum(i["r"] + i["bootstrap"] for st in seq_infos for i in st.values()) / (sum(seq_ms) / 1000.0)
 
     # dominant kernel: search time per optimality family (sequential pass)
-    fam = {k: tuple(o for o in v_ if o in OPTS) for k, v_ in {"k_bfs": ("sh", "sfm"), "k_pfm": ("pfm",)}.items()}
+    pfm_kernel = "k_pfm" if os.environ.get("MANTRA_PFM_KERNEL") == "lane" else "k_pfm_cta"
+    fam = {k: tuple(o for o in v_ if o in OPTS) for k, v_ in {"k_bfs": ("sh", "sfm"), pfm_kernel: ("pfm",)}.items()}
     fam = {k: v_ for k, v_ in fam.items() if v_}
     kms = {k: sum(st[o]["kernel_ms"] for st in seq_infos for o in os_) for k, os_ in fam.items()}
     kbytes = {k: sum(st[o]["alg_bytes"] for st in seq_infos for o in os_) for k, os_ in fam.items()}
@@ -398,7 +408,7 @@ def main():
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = (kbytes[dom] / klaunch[dom]) / (kms[dom] / klaunch[dom] / 1000.0) / 1e9
-    traffic = recorded_traffic(dom)
+    traffic = recorded_traffic(dom, kbytes[dom] / klaunch[dom])
     alg_gbps = sum(st[o]["alg_bytes"] for st in infos_all for o in OPTS) / (total_ms / 1000.0) / 1e9
     edges = sum(st[o]["edges_scanned"] for st in infos_all for o in OPTS)
     launches = sum(st[o]["kernel_launches"] for st in infos_all for o in OPTS)

@@ -122,14 +122,17 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
     for (uint32_t x = 0; x < n; ++x) out_ptr[x + 1] += out_ptr[x];
     std::vector<uint32_t> tmax_in(n, 0), tmin_out(n, 0);
     uint64_t cbound = 0;
+    uint32_t max_slot_in = 0;
     for (uint32_t x = 0; x < n; ++x) {
         if (slot_ptr[x + 1] > slot_ptr[x]) tmax_in[x] = slot_t[slot_ptr[x + 1] - 1];
         if (out_ptr[x + 1] > out_ptr[x]) tmin_out[x] = out_t[out_ptr[x]];
         uint32_t mx = 0;
         for (uint32_t a = slot_ptr[x]; a < slot_ptr[x + 1]; ++a) mx = std::max(mx, slot_in[a + 1] - slot_in[a]);
         cbound += mx;
+        max_slot_in = std::max(max_slot_in, mx);
     }
     G->dg.cbound = (uint32_t)std::min<uint64_t>(cbound, 0xFFFFFFFFull);
+    G->dg.max_slot_in = max_slot_in;
 
     // one device allocation for the whole store
     struct Arr { const std::vector<uint32_t>* h; const uint32_t** d; };
@@ -388,7 +391,7 @@ struct Engine {
     }
 
     // pfm with one CTA per sample: one region per resident CTA, at most a third
-    // of free memory; fa' and the frontier bitmap in shared memory when they fit.
+    // of free memory; arrival slots and flag bitmaps in shared memory when they fit.
     int ensure_pfm_cta(uint32_t n) {
         if (pc_mem && n <= pc_n) return MANTRA_OK;
         n = std::max(n, pc_n);

@@ -23,12 +23,14 @@
 // else in per-CTA global scratch.
 #include "mantra_dev.cuh"
 
+#include <algorithm>
 #include <mutex>
 
 namespace mantra {
 
 constexpr int BFS_NT = 1024;
 constexpr int BFS_NW = BFS_NT / 32;
+constexpr uint32_t FCAP = 4096;   // frontier states whose times and running sums fit in shared memory
 
 template <bool WIDE>
 __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint64_t* unit_start,
@@ -48,6 +50,8 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
     uint32_t* seg_u = reinterpret_cast<uint32_t*>(region + ws.o_segu);
     uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path);
     uint32_t* VB = reinterpret_cast<uint32_t*>(region + ws.o_vb);   // vertex bitmap (stats)
+    u64* segmap = reinterpret_cast<u64*>(region + ws.o_segmap);      // vertex -> (level stamp, frontier segment)
+    uint32_t* stamp_p = reinterpret_cast<uint32_t*>(region + ws.o_stamp);
 
     extern __shared__ uint32_t dyn_smem[];
     uint32_t* V = ws.bits_in_smem ? dyn_smem : reinterpret_cast<uint32_t*>(region + ws.o_bits);
@@ -66,10 +70,30 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
     __shared__ uint32_t sh_d, sh_len;
     __shared__ u128 sh_sigma;
     __shared__ uint32_t cs_off[BFS_NT + 1], cs_first[BFS_NT], cs_fb[BFS_NT], cs_fe[BFS_NT];   // range table
+    __shared__ uint32_t sh_stamp, sh_wrap;
+    __shared__ u64 sh_fcmax;
+    __shared__ uint32_t sm_Ft[WIDE ? 1 : FCAP];   // level times and running sums (64-bit counts, L <= FCAP)
+    __shared__ u64 sm_Fc[WIDE ? 1 : FCAP];
 
     if (ws.bits_in_smem) {
         for (uint32_t w = tid; w < 2 * ws.bits_words; w += BFS_NT) V[w] = 0u;
     }
+    if (tid == 0) sh_stamp = *stamp_p;
+    // Next level stamp (segmap entries of older levels never match it) and the
+    // level's scan scratch; on wrap-around the map is cleared once.
+    auto advance_stamp = [&]() {
+        if (tid == 0) {
+            const uint32_t st = sh_stamp + 1u;
+            sh_wrap = st == 0u;
+            sh_stamp = st == 0u ? 1u : st;
+            sh_carry = (Sig)0; sh_scan_ovf = 0; sh_fcmax = 0;
+        }
+        __syncthreads();
+        if (sh_wrap) {
+            for (uint32_t v = tid; v < ws.n_cap; v += BFS_NT) segmap[v] = 0ull;
+            __syncthreads();
+        }
+    };
     const uint32_t ntasks = *ntasks_p;
     // per-thread work counters, added to the current task's counters when the
     // CTA moves to another task and at exit
@@ -135,8 +159,18 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
         while (live) {
             // ---- segments of level k ----
             uint32_t G;
+            // this level's frontier times and running sums: shared memory when they fit
+            const bool fsm = !WIDE && L <= FCAP;
+            uint32_t* const FtL = fsm ? sm_Ft : Ft;
+            Sig* const FcL = fsm ? reinterpret_cast<Sig*>(sm_Fc) : Fc;
+            advance_stamp();
+            const uint32_t stamp = sh_stamp;
             if (k == 0) {
-                if (tid == 0) { seg_b[0] = 0; seg_u[0] = s; Fc[0] = (Sig)1; Ft[0] = 0; my_fseg += 1; }
+                if (tid == 0) {
+                    seg_b[0] = 0; seg_u[0] = s; FcL[0] = (Sig)1; FtL[0] = 0; my_fseg += 1;
+                    segmap[s] = ((u64)stamp << 32);
+                    sh_fcmax = 1;
+                }
                 __syncthreads();
                 G = 1;
             } else {
@@ -144,8 +178,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                 // B1: frontier attributes, segment heads and per-vertex running sums
                 // of sigma (block-wide segmented scan, one tile of BFS_NT per pass)
                 uint32_t gbase = 0;
-                if (tid == 0) { sh_carry = (Sig)0; sh_scan_ovf = 0; }
-                __syncthreads();
+                u64 fcmax = 0;
                 const uint32_t* const g_slot_v = g.slot_v;
                 const uint32_t* const g_slot_t = g.slot_t;
                 for (uint32_t it = 0; it < L; it += BFS_NT) {
@@ -155,26 +188,41 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                     if (idx < L) {
                         const uint32_t a = Fk[idx];
                         u = g_slot_v[a];
-                        Ft[idx] = g_slot_t[a];
+                        FtL[idx] = g_slot_t[a];
                         val = sig[a];
                         head = (idx == 0) || (g_slot_v[Fk[idx - 1]] != u);
                     }
                     const Sig run = block_segmented_scan<BFS_NT, Sig>(val, head, sm_segx, sm_segf, &sh_carry,
                                                                        &sh_scan_ovf);
-                    if (idx < L) Fc[idx] = run;
+                    if (idx < L) {
+                        FcL[idx] = run;
+                        if (!WIDE && (u64)run > fcmax) fcmax = (u64)run;
+                    }
                     const uint32_t hd = (idx < L) ? head : 0u;
                     uint32_t tot;
                     const uint32_t ex = block_exclusive_scan<BFS_NT>(hd, &tot, sm_scan);
-                    if (hd) { seg_b[gbase + ex] = idx; seg_u[gbase + ex] = u; }
+                    if (hd) {
+                        seg_b[gbase + ex] = idx; seg_u[gbase + ex] = u;
+                        segmap[u] = ((u64)stamp << 32) | (gbase + ex);
+                    }
                     gbase += tot;
                 }
                 G = gbase;
+                if (!WIDE) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) fcmax = max(fcmax, (u64)__shfl_xor_sync(0xFFFFFFFFu, fcmax, o));
+                    if (lane == 0 && fcmax) atomicMax(&sh_fcmax, fcmax);
+                }
                 if (tid == 0) {
                     my_fseg += G;
                     if (sh_scan_ovf && !stats) sh_ovf = 1;
                 }
                 __syncthreads();
             }
+            // 64-bit path counts of the next level cannot wrap when every running sum
+            // times the largest in-edge count of a slot stays below 2^64: the push then
+            // adds without reading the old value back
+            const bool fast_add = !WIDE && __umul64hi(sh_fcmax, (u64)g.max_slot_in) == 0ull;
             if (sh_ovf) break;
 
             // ---- pull: does level k reach z? ----
@@ -188,22 +236,19 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                     const uint32_t w = g_in_u[e];
                     const uint32_t a = g_in_slot[e];
                     const uint32_t t = g_slot_t[a];
-                    // segment of w (seg_u ascending)
-                    uint32_t lo = 0, hi = G;
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (seg_u[mid] < w) lo = mid + 1; else hi = mid;
-                    }
-                    if (lo < G && seg_u[lo] == w) {
+                    // frontier segment of w, if w is on this level
+                    const u64 mw = __ldcg(segmap + w);
+                    if ((uint32_t)(mw >> 32) == stamp) {
+                        const uint32_t lo = (uint32_t)mw;
                         const uint32_t fb = seg_b[lo], fe = (lo + 1 < G) ? seg_b[lo + 1] : L;
                         bool have = true;
                         uint32_t idx = fb;
                         if (k > 0) {
-                            const uint32_t c = lower_bound_u32(Ft, fb, fe, t);   // first Ft >= t
+                            const uint32_t c = lower_bound_u32(FtL, fb, fe, t);   // first Ft >= t
                             if (c == fb) have = false; else idx = c - 1;
                         }
                         if (have) {
-                            if (!SigOps<WIDE>::atomic_add(sig + a, Fc[idx])) sh_ovf = 1;
+                            if (!SigOps<WIDE>::atomic_add(sig + a, FcL[idx])) sh_ovf = 1;
                             atomicOr(N + (a >> 5), 1u << (a & 31));
                             sh_found = 1;
                         }
@@ -229,7 +274,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                     fe = (gi + 1 < G) ? seg_b[gi + 1] : L;
                     const uint32_t u = seg_u[gi];
                     const uint32_t r0 = g_out_ptr[u], r1 = g_out_ptr[u + 1];
-                    lo2[0] = r0; hi2[0] = (k == 0) ? r0 : r1; key2[0] = (k == 0) ? 0u : Ft[fb];
+                    lo2[0] = r0; hi2[0] = (k == 0) ? r0 : r1; key2[0] = (k == 0) ? 0u : FtL[fb];
                     lo2[1] = r0; hi2[1] = (tz == 0) ? r0 : r1; key2[1] = tz - 1u;
                 }
                 upper_bounds<2>(g_out_t, lo2, hi2, key2);
@@ -252,11 +297,18 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                     const uint32_t a = __ldg(g_out_slot + e), t = __ldg(g_out_t + e);
                     ++my_escan;
                     if (!((V[a >> 5] >> (a & 31)) & 1u)) {
-                        const uint32_t rb = cs_fb[r], re = cs_fe[r];
-                        uint32_t idx = rb;
-                        if (re - rb > 1) idx = lower_bound_u32(Ft, rb, re, t) - 1;   // last Ft < t
                         atomicOr(N + (a >> 5), 1u << (a & 31));
-                        if (!SigOps<WIDE>::atomic_add(sig + a, Fc[idx]) && !stats) sh_ovf = 1;
+                        if (!stats) {          // Algorithm 2 needs reach only, no path counts
+                            const uint32_t rb = cs_fb[r], re = cs_fe[r];
+                            uint32_t idx = rb;
+                            if (re - rb > 1) idx = lower_bound_u32(FtL, rb, re, t) - 1;   // last Ft < t
+                            if constexpr (!WIDE) {
+                                if (fast_add) atomicAdd(sig + a, FcL[idx]);
+                                else if (!SigOps<WIDE>::atomic_add(sig + a, FcL[idx])) sh_ovf = 1;
+                            } else {
+                                if (!SigOps<WIDE>::atomic_add(sig + a, FcL[idx])) sh_ovf = 1;
+                            }
+                        }
                         ++my_eadd;
                     }
                 });
@@ -493,7 +545,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
             uint32_t bits = V[w] | N[w];
             if (bits) {
                 V[w] = 0u; N[w] = 0u;
-                while (bits) {
+                while (bits && !stats) {
                     const uint32_t b = __ffs(bits) - 1;
                     bits &= bits - 1;
                     sig[w * 32u + b] = (Sig)0;
@@ -506,6 +558,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
         __syncthreads();
     }
     flush();
+    if (tid == 0) *stamp_p = sh_stamp;
 }
 
 // Host-side launch helpers -------------------------------------------------
@@ -523,6 +576,9 @@ size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws) {
     ws->o_segu = o;    o = al(o + (size_t)(n + 2) * 4);
     ws->o_path = o;    o = al(o + (size_t)(n + 2) * 4);
     ws->o_vb = o;      o = al(o + (size_t)((n + 31) / 32 + 1) * 4);
+    ws->o_segmap = o;  o = al(o + (size_t)n * 8);
+    ws->o_stamp = o;   o = al(o + 4);
+    ws->n_cap = n;
     ws->o_bits = o;
     if (!bits_in_smem) o = al(o + (size_t)2 * ((A + 31) / 32) * 4);
     ws->bits_in_smem = bits_in_smem ? 1 : 0;
@@ -533,8 +589,10 @@ size_t bfs_smem_bytes(uint32_t A) { return (size_t)2 * ((A + 31) / 32) * 4; }
 
 // Static shared memory of the kernel (range table, task copy, scan scratch).
 size_t bfs_static_smem() {
-    cudaFuncAttributes a{};
-    return cudaFuncGetAttributes(&a, k_bfs<true>) == cudaSuccess ? a.sharedSizeBytes : 32768;
+    cudaFuncAttributes a{}, b{};
+    if (cudaFuncGetAttributes(&a, k_bfs<false>) != cudaSuccess || cudaFuncGetAttributes(&b, k_bfs<true>) != cudaSuccess)
+        return 96 * 1024;
+    return std::max(a.sharedSizeBytes, b.sharedSizeBytes);
 }
 
 // Raises (never lowers) the kernels' dynamic shared-memory limit, so callers

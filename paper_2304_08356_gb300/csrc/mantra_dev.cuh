@@ -53,7 +53,7 @@ struct DevGraph {
     const uint32_t* tmin_out;
     uint32_t cbound;  // sum over v of the largest in-edge count of v's slots: bounds the
                       // path-count additions of one prefix-foremost search
-    uint32_t pad_;
+    uint32_t max_slot_in;   // largest in-edge count of one arrival slot
 };
 
 // One launch over a range (or list) of sample indices.
@@ -417,9 +417,10 @@ __device__ __forceinline__ void push_overflow(const Job& job, uint64_t i) {
 struct BfsWs {
     char* base;          // CTA b uses base + b * stride
     size_t stride;
-    size_t o_sig, o_fc, o_f, o_ft, o_lev, o_segb, o_segu, o_path, o_bits, o_vb;
+    size_t o_sig, o_fc, o_f, o_ft, o_lev, o_segb, o_segu, o_path, o_bits, o_vb, o_segmap, o_stamp;
     int bits_in_smem;    // visited / next bitmaps in dynamic shared memory
     uint32_t bits_words; // capacity of each bitmap (words): ceil(A_max / 32)
+    uint32_t n_cap;      // node capacity of a region
 };
 
 // Per-warp scratch of the pfm search kernel.
