@@ -345,6 +345,8 @@ struct Engine {
         const size_t region = bfs_region_bytes(n, A, in_smem, &bws);
         const size_t budget = free_device_bytes() / 3;
         int grid = num_sms;
+        // MANTRA_BFS_GRID caps the resident CTAs (fewer samples in flight, less L2 pressure)
+        if (const char* env = std::getenv("MANTRA_BFS_GRID")) grid = std::max(1, std::min(grid, std::atoi(env)));
         if ((size_t)grid * region > budget) grid = (int)std::max<size_t>(1, budget / region);
         if (cudaMalloc(&bfs_mem, (size_t)grid * region) != cudaSuccess) { bfs_mem = nullptr; return MANTRA_E_NOMEM; }
         CU(cudaMemsetAsync(bfs_mem, 0, (size_t)grid * region, sa));
@@ -396,15 +398,20 @@ struct Engine {
         if (pc_mem && n <= pc_n) return MANTRA_OK;
         n = std::max(n, pc_n);
         if (pc_mem) { cudaStreamSynchronize(sb); cudaStreamSynchronize(sa); cudaFree(pc_mem); pc_mem = nullptr; }
+        // MANTRA_PFM_CTA_NT=256 takes 256-thread CTAs (four per SM);
+        // MANTRA_PFM_CTA_SMEM=0 keeps the arrival state in global memory
+        int nt = 512;
+        if (const char* env = std::getenv("MANTRA_PFM_CTA_NT")) nt = std::atoi(env) == 256 ? 256 : 512;
         const size_t smem = pfm_cta_smem_bytes(n);
-        bool in_smem = smem + pfm_cta_static_smem() + 1024 <= smem_optin;
-        // MANTRA_PFM_CTA_SMEM=0 keeps the arrival state in global memory (tests of that variant)
+        bool in_smem = smem + pfm_cta_static_smem(nt) + 1024 <= smem_optin;
         if (const char* env = std::getenv("MANTRA_PFM_CTA_SMEM")) in_smem = in_smem && env[0] != '0';
         const size_t region = pfm_cta_region_bytes(n, in_smem, &pcws);
+        pcws.nt = nt;
         CU(pfm_cta_configure(in_smem ? smem : 0));
         int per_sm = 0;
-        CU(pfm_cta_blocks_per_sm(in_smem, in_smem ? smem : 0, &per_sm));
+        CU(pfm_cta_blocks_per_sm(nt, in_smem, in_smem ? smem : 0, &per_sm));
         int grid = num_sms * std::max(per_sm, 1);
+        if (const char* env = std::getenv("MANTRA_PFM_GRID")) grid = std::max(1, std::min(grid, std::atoi(env)));
         const size_t budget = free_device_bytes() / 3;
         if ((size_t)grid * region > budget) grid = (int)std::max<size_t>(1, budget / region);
         if (cudaMalloc(&pc_mem, (size_t)grid * region) != cudaSuccess) { pc_mem = nullptr; return MANTRA_E_NOMEM; }

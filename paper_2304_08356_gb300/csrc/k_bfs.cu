@@ -31,6 +31,7 @@ namespace mantra {
 constexpr int BFS_NT = 1024;
 constexpr int BFS_NW = BFS_NT / 32;
 constexpr uint32_t FCAP = 4096;   // frontier states whose times and running sums fit in shared memory
+constexpr int IPT = 2;            // frontier states per thread in a segmented-scan tile
 
 template <bool WIDE>
 __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint64_t* unit_start,
@@ -62,6 +63,8 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
     __shared__ Sig sm_segx[32];
     __shared__ uint32_t sm_segf[32];
     __shared__ Sig sh_carry;
+    __shared__ Sig sm_lastx[BFS_NW];
+    __shared__ Sig sh_cin;
     __shared__ uint32_t sh_scan_ovf;
     __shared__ uint32_t sm_wcnt[BFS_NW];
     __shared__ uint64_t sh_q;
@@ -176,34 +179,76 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
             } else {
                 const uint32_t* Fk = F + lev[k];
                 // B1: frontier attributes, segment heads and per-vertex running sums
-                // of sigma (block-wide segmented scan, one tile of BFS_NT per pass)
+                // of sigma.  Each thread takes IPT consecutive states of a tile: a
+                // thread-local segmented scan, one block-wide segmented scan of the
+                // thread aggregates, and the value carried into each thread.
                 uint32_t gbase = 0;
                 u64 fcmax = 0;
                 const uint32_t* const g_slot_v = g.slot_v;
                 const uint32_t* const g_slot_t = g.slot_t;
-                for (uint32_t it = 0; it < L; it += BFS_NT) {
-                    const uint32_t idx = it + tid;
-                    uint32_t head = 1, u = 0;
-                    Sig val = 0;
-                    if (idx < L) {
-                        const uint32_t a = Fk[idx];
-                        u = g_slot_v[a];
-                        FtL[idx] = g_slot_t[a];
-                        val = sig[a];
-                        head = (idx == 0) || (g_slot_v[Fk[idx - 1]] != u);
+                for (uint32_t it = 0; it < L; it += BFS_NT * IPT) {
+                    const uint32_t i0 = it + (uint32_t)tid * IPT;
+                    uint32_t uq[IPT];
+                    Sig vq[IPT];
+                    {
+                        uint32_t aq[IPT];
+#pragma unroll
+                        for (int q = 0; q < IPT; ++q) aq[q] = (i0 + q < L) ? Fk[i0 + q] : 0u;
+#pragma unroll
+                        for (int q = 0; q < IPT; ++q) {
+                            uq[q] = 0u; vq[q] = (Sig)0;
+                            if (i0 + q < L) {
+                                uq[q] = g_slot_v[aq[q]];
+                                FtL[i0 + q] = g_slot_t[aq[q]];
+                                vq[q] = sig[aq[q]];
+                            }
+                        }
                     }
-                    const Sig run = block_segmented_scan<BFS_NT, Sig>(val, head, sm_segx, sm_segf, &sh_carry,
-                                                                       &sh_scan_ovf);
-                    if (idx < L) {
-                        FcL[idx] = run;
-                        if (!WIDE && (u64)run > fcmax) fcmax = (u64)run;
+                    const uint32_t uprev = (i0 > 0 && i0 < L) ? g_slot_v[Fk[i0 - 1]] : NONE;
+                    // heads (bit q): a state whose vertex differs from the previous state's
+                    // (states past L are heads of value 0); agg = the thread's running sum
+                    // since its last head
+                    uint32_t hm = 0, nh = 0;
+                    bool bad = false;
+                    Sig agg = 0;
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q) {
+                        const uint32_t idx = i0 + q;
+                        const uint32_t up = q == 0 ? uprev : uq[q - 1];
+                        const bool h = (idx >= L) || idx == 0 || up != uq[q];
+                        if (h) { hm |= 1u << q; agg = vq[q]; }
+                        else { const Sig sm = agg + vq[q]; bad |= sm < agg; agg = sm; }
+                        if (idx < L && h) ++nh;
                     }
-                    const uint32_t hd = (idx < L) ? head : 0u;
+                    if (tid == 0) sh_cin = sh_carry;          // carried into the tile
+                    const Sig incl = block_segmented_scan<BFS_NT, Sig>(agg, hm != 0u, sm_segx, sm_segf, &sh_carry,
+                                                                        &sh_scan_ovf);
+                    // value carried into this thread: the previous thread's inclusive value
+                    Sig run = shfl_up_w(incl, 1);
+                    if (lane == 31) sm_lastx[wid] = incl;
+                    __syncthreads();
+                    if (lane == 0) run = wid ? sm_lastx[wid - 1] : sh_cin;
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q) {
+                        const uint32_t idx = i0 + q;
+                        if ((hm >> q) & 1u) run = vq[q];
+                        else { const Sig sm = run + vq[q]; bad |= sm < run; run = sm; }
+                        if (idx < L) {
+                            FcL[idx] = run;
+                            if (!WIDE && (u64)run > fcmax) fcmax = (u64)run;
+                        }
+                    }
+                    if (bad) sh_scan_ovf = 1u;
                     uint32_t tot;
-                    const uint32_t ex = block_exclusive_scan<BFS_NT>(hd, &tot, sm_scan);
-                    if (hd) {
-                        seg_b[gbase + ex] = idx; seg_u[gbase + ex] = u;
-                        segmap[u] = ((u64)stamp << 32) | (gbase + ex);
+                    uint32_t ex = block_exclusive_scan<BFS_NT>(nh, &tot, sm_scan);
+#pragma unroll
+                    for (int q = 0; q < IPT; ++q) {
+                        const uint32_t idx = i0 + q;
+                        if (idx < L && ((hm >> q) & 1u)) {
+                            seg_b[gbase + ex] = idx; seg_u[gbase + ex] = uq[q];
+                            segmap[uq[q]] = ((u64)stamp << 32) | (gbase + ex);
+                            ++ex;
+                        }
                     }
                     gbase += tot;
                 }

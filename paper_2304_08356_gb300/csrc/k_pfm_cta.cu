@@ -36,9 +36,6 @@
 
 namespace mantra {
 
-constexpr int PC_NT = 512;
-constexpr int PC_NW = PC_NT / 32;
-constexpr uint32_t CHUNK = 2 * PC_NT;      // frontier vertices per range table
 constexpr uint32_t SRC = NONE - 1u;        // fsl of the source
 
 template <bool SM>
@@ -47,9 +44,12 @@ __device__ __forceinline__ uint32_t ldv(const uint32_t* p) {
     return __ldcg(p);
 }
 
-template <bool FA_SMEM>
-__global__ void __launch_bounds__(PC_NT, 2) k_pfm_cta(const Task* tasks, const uint64_t* unit_start,
-                                                     const uint32_t* ntasks_p, u64* work, const PfmCtaWs ws) {
+// PC_NT threads per CTA, 1024 / PC_NT CTAs per SM at 64 registers.
+template <int PC_NT, bool FA_SMEM>
+__global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tasks, const uint64_t* unit_start,
+                                                                const uint32_t* ntasks_p, u64* work, const PfmCtaWs ws) {
+    constexpr int PC_NW = PC_NT / 32;
+    constexpr uint32_t CHUNK = 2 * PC_NT;      // frontier vertices per range table
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const uint32_t FULL = 0xFFFFFFFFu;
     __shared__ __align__(16) Task sh_task;
@@ -495,35 +495,44 @@ size_t pfm_cta_region_bytes(uint32_t n, bool fa_in_smem, PfmCtaWs* ws) {
 size_t pfm_cta_smem_bytes(uint32_t n) { return ((size_t)n + 2 * ((n + 31) / 32)) * 4; }
 
 // Static shared memory of the kernel (range table, task copy, scratch).
-size_t pfm_cta_static_smem() {
+size_t pfm_cta_static_smem(int nt) {
     cudaFuncAttributes a{};
-    return cudaFuncGetAttributes(&a, k_pfm_cta<true>) == cudaSuccess ? a.sharedSizeBytes : 16384;
+    const cudaError_t e = nt == 256 ? cudaFuncGetAttributes(&a, k_pfm_cta<256, true>)
+                                    : cudaFuncGetAttributes(&a, k_pfm_cta<512, true>);
+    return e == cudaSuccess ? a.sharedSizeBytes : 16384;
 }
 
-int pfm_cta_threads() { return PC_NT; }
-
-// Raises (never lowers) the dynamic shared-memory limit of that variant.
+// Raises (never lowers) the dynamic shared-memory limit of the shared-memory variants.
 cudaError_t pfm_cta_configure(size_t smem) {
     static std::mutex mu;
     static size_t configured = 0;
     std::lock_guard<std::mutex> lk(mu);
     if (smem <= configured) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(k_pfm_cta<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_pfm_cta<512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pfm_cta<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) configured = smem;
     return e;
 }
 
-cudaError_t pfm_cta_blocks_per_sm(bool fa_in_smem, size_t smem, int* out) {
-    return fa_in_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<true>, PC_NT, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<false>, PC_NT, 0);
+cudaError_t pfm_cta_blocks_per_sm(int nt, bool fa_in_smem, size_t smem, int* out) {
+    if (nt == 256)
+        return fa_in_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<256, true>, 256, smem)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<256, false>, 256, 0);
+    return fa_in_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<512, true>, 512, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<512, false>, 512, 0);
 }
 
 cudaError_t launch_pfm_cta(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
                            const PfmCtaWs& ws, int grid, cudaStream_t st) {
-    if (ws.fa_in_smem)
-        k_pfm_cta<true><<<grid, PC_NT, pfm_cta_smem_bytes(ws.n_cap), st>>>(tasks, unit_start, ntasks, work, ws);
-    else
-        k_pfm_cta<false><<<grid, PC_NT, 0, st>>>(tasks, unit_start, ntasks, work, ws);
+    const size_t smem = ws.fa_in_smem ? pfm_cta_smem_bytes(ws.n_cap) : 0;
+    if (ws.nt == 256) {
+        if (ws.fa_in_smem) k_pfm_cta<256, true><<<grid, 256, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else k_pfm_cta<256, false><<<grid, 256, 0, st>>>(tasks, unit_start, ntasks, work, ws);
+    } else {
+        if (ws.fa_in_smem) k_pfm_cta<512, true><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else k_pfm_cta<512, false><<<grid, 512, 0, st>>>(tasks, unit_start, ntasks, work, ws);
+    }
     return cudaGetLastError();
 }
 

@@ -440,6 +440,7 @@ struct PfmCtaWs {
     uint32_t n_cap;      // node capacity of a region
     uint32_t bits_words; // words of each bitmap: ceil(n_cap / 32)
     int fa_in_smem;      // arrival slots and bitmaps in dynamic shared memory
+    int nt;              // threads per CTA (256 or 512)
 };
 
 size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws);
@@ -457,10 +458,9 @@ cudaError_t launch_pfm(const Task* tasks, const uint64_t* unit_start, const uint
                        const PfmWs& ws, int grid, bool wide, cudaStream_t st);
 size_t pfm_cta_region_bytes(uint32_t n, bool fa_in_smem, PfmCtaWs* ws);
 size_t pfm_cta_smem_bytes(uint32_t n);
-size_t pfm_cta_static_smem();
-int pfm_cta_threads();
+size_t pfm_cta_static_smem(int nt);
 cudaError_t pfm_cta_configure(size_t smem);
-cudaError_t pfm_cta_blocks_per_sm(bool fa_in_smem, size_t smem, int* out);
+cudaError_t pfm_cta_blocks_per_sm(int nt, bool fa_in_smem, size_t smem, int* out);
 cudaError_t launch_pfm_cta(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
                            const PfmCtaWs& ws, int grid, cudaStream_t st);
 // One problem of a multi-problem round reduction.
