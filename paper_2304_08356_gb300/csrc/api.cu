@@ -259,6 +259,8 @@ struct Engine {
     bool last_tick_graph = false;
     // search workspaces
     char* bfs_mem = nullptr; BfsWs bws{}; int bfs_grid = 0; size_t bfs_smem = 0; uint32_t bfs_n = 0, bfs_A = 0;
+    int bfs_grid_big = 0;      // resident 1024-thread CTAs (the regions of the first ones)
+    int tick_bfs_nt = 512;     // sh/sfm CTA size of the current tick
     char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; uint32_t pfm_n = 0, pfm_lcap = 0; uint64_t pfm_warps = 0;
     char* pc_mem = nullptr; PfmCtaWs pcws{}; int pc_grid = 0; uint32_t pc_n = 0;
     bool tick_cta = false;   // pfm samples of the current tick run one per CTA
@@ -269,8 +271,9 @@ struct Engine {
     size_t o_hdr = 0, o_work = 0, o_ub = 0, o_up = 0, o_tb = 0, o_tp = 0, o_ri = 0, o_rs = 0;
     int red_grid = 0;
     // captured ticks, one per pfm kernel (lane / CTA per sample)
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    bool graph_ok[2] = {false, false};
+    // captured ticks, by (pfm kernel, sh/sfm CTA size)
+    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool graph_ok[4] = {false, false, false, false};
     bool use_graph = true;
     DevPool pool;
 
@@ -297,7 +300,7 @@ struct Engine {
     }
 
     void invalidate_graph() {
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 4; ++k) {
             if (gexec[k]) cudaGraphExecDestroy(gexec[k]);
             gexec[k] = nullptr;
             graph_ok[k] = false;
@@ -340,12 +343,18 @@ struct Engine {
         n = std::max(n, bfs_n);
         A = std::max(A, bfs_A);
         if (bfs_mem) { cudaStreamSynchronize(sa); cudaFree(bfs_mem); bfs_mem = nullptr; }
+        // regions for the 512-thread shape (two CTAs per SM); the 1024-thread
+        // shape (one per SM) uses the first of them
         const size_t smem = bfs_smem_bytes(A);
-        const bool in_smem = smem + bfs_static_smem() + 1024 <= smem_optin;
+        const bool in_smem = smem + std::max(bfs_static_smem(512), bfs_static_smem(1024)) + 1024 <= smem_optin;
         const size_t region = bfs_region_bytes(n, A, in_smem, &bws);
+        CU(bfs_configure(in_smem ? smem : 0));
+        int per_sm = 0, per_sm_big = 0;
+        CU(bfs_blocks_per_sm(512, in_smem ? smem : 0, &per_sm));
+        CU(bfs_blocks_per_sm(1024, in_smem ? smem : 0, &per_sm_big));
         const size_t budget = free_device_bytes() / 3;
-        int grid = num_sms;
-        // MANTRA_BFS_GRID caps the resident CTAs (fewer samples in flight, less L2 pressure)
+        int grid = num_sms * std::max(per_sm, 1);
+        // MANTRA_BFS_GRID caps the resident CTAs
         if (const char* env = std::getenv("MANTRA_BFS_GRID")) grid = std::max(1, std::min(grid, std::atoi(env)));
         if ((size_t)grid * region > budget) grid = (int)std::max<size_t>(1, budget / region);
         if (cudaMalloc(&bfs_mem, (size_t)grid * region) != cudaSuccess) { bfs_mem = nullptr; return MANTRA_E_NOMEM; }
@@ -353,9 +362,9 @@ struct Engine {
         bws.base = bfs_mem;
         bws.stride = region;
         bfs_grid = grid;
+        bfs_grid_big = std::min(grid, num_sms * std::max(per_sm_big, 1));
         bfs_smem = in_smem ? smem : 0;
         bfs_n = n; bfs_A = A;
-        CU(bfs_configure(bfs_smem));
         invalidate_graph();
         return MANTRA_OK;
     }
@@ -434,8 +443,10 @@ struct Engine {
         u64* work = (u64*)(tab_d + o_work);
         if (bfs_mem) {
             CU(cudaEventRecord(e_b0, sa));
-            CU(launch_bfs((const Task*)(tab_d + o_tb), (const uint64_t*)(tab_d + o_ub), hdr + 0, work + 0, bws,
-                          bfs_grid, bfs_smem, wide, sa));
+            BfsWs w = bws;
+            w.nt = tick_bfs_nt;
+            CU(launch_bfs((const Task*)(tab_d + o_tb), (const uint64_t*)(tab_d + o_ub), hdr + 0, work + 0, w,
+                          tick_bfs_nt == 1024 ? bfs_grid_big : bfs_grid, bfs_smem, wide, sa));
             CU(cudaEventRecord(e_b1, sa));
         }
         if (tick_cta && !wide && pc_mem) {
@@ -460,7 +471,7 @@ struct Engine {
     int launch_tick(bool wide) {
         last_tick_graph = false;
         if (wide || !use_graph) return enqueue(wide);
-        const int gk = tick_cta ? 1 : 0;
+        const int gk = (tick_cta ? 1 : 0) + (tick_bfs_nt == 1024 ? 2 : 0);
         if (!graph_ok[gk]) {
             cudaGraph_t graph = nullptr;
             CU(cudaStreamBeginCapture(sa, cudaStreamCaptureModeThreadLocal));
@@ -549,7 +560,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     int rc;
     if ((rc = E.ensure_tables(std::max<uint32_t>(k, 1))) != MANTRA_OK) return rc;
     uint32_t bn = 0, bA = 0, pn = 0, plc = 0;
-    uint64_t pwarps = 0;
+    uint64_t pwarps = 0, bsamples = 0;
     bool any_b = false, any_p = false;
     for (const TickItem& it : items) {
         if (it.job.opt == MANTRA_PFM) {
@@ -557,6 +568,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
             pwarps += (it.job.count + 31) / 32;
         } else {
             any_b = true; bn = std::max(bn, it.G->n); bA = std::max(bA, it.G->A);
+            bsamples += it.job.count;
         }
     }
     const bool cta = any_p && !wide && pfm_use_cta();
@@ -564,6 +576,15 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     if (any_p && cta && (rc = E.ensure_pfm_cta(pn)) != MANTRA_OK) return rc;
     if (any_p && !cta && (rc = E.ensure_pfm(pn, plc, pwarps)) != MANTRA_OK) return rc;
     E.tick_cta = cta;
+    // sh/sfm CTA shape: 1024 threads for ticks of at most two samples per resident
+    // 1024-thread CTA (shorter per-sample latency), else two 512-thread CTAs per SM
+    // (measured on the n = 20,000 bursty graph: 1.9 vs 2.7 ms for 231 samples,
+    // 42.5 vs 40.4 ms for 26,702); MANTRA_BFS_NT=512|1024 forces one
+    {
+        int nt = bsamples <= 2ull * (uint64_t)E.bfs_grid_big ? 1024 : 512;
+        if (const char* env = std::getenv("MANTRA_BFS_NT")) nt = std::atoi(env) == 1024 ? 1024 : 512;
+        E.tick_bfs_nt = nt;
+    }
     // host tables
     uint32_t* hdr = (uint32_t*)(E.tab_h + E.o_hdr);
     u64* work = (u64*)(E.tab_h + E.o_work);
@@ -719,9 +740,11 @@ struct Problem {
     u64* hits = nullptr; int* S = nullptr; double* est = nullptr; uint64_t* ovf = nullptr;
     size_t b_hits = 0, b_S = 0, b_est = 0, b_ovf = 0;
     uint64_t ovf_cap = 0;
-    // progress
+    // progress: the current phase covers sample indices [phase_begin, phase_end);
+    // pos = the next index to run (a phase may span several ticks)
     enum { BOOT, ROUND, DONE } phase = BOOT;
     uint64_t sb = 0, omega = 0, s1 = 0, r = 0, target = 0, round = 0, reduces = 0;
+    uint64_t pos = 0, boot_sum_int = 0;
     LaunchTotals T;
     mantra_info I{};
     int status = MANTRA_OK;
@@ -765,6 +788,7 @@ struct Problem {
         if (!hits || !S || (!out_device && !est)) return MANTRA_E_NOMEM;
         CU(cudaMemsetAsync(hits, 0, b_hits, E.sa));
         CU(cudaMemsetAsync(S, 0, b_S, E.sa));
+        pos = 0; boot_sum_int = 0;
         if (fixed_r > 0) {
             phase = ROUND; target = fixed_r; r = 0;
         } else {
@@ -775,34 +799,47 @@ struct Problem {
         return grow_ovf(E, phase == BOOT ? sb : target);
     }
 
-    int item(Engine& E, TickItem* it) {
+    // Samples left in the current phase.
+    uint64_t remaining() const { return phase == BOOT ? sb - pos : (phase == ROUND ? target - pos : 0); }
+
+    // The next sample range, at most quota samples; the round reduction runs
+    // on the tick that completes the phase.
+    int item(Engine& E, TickItem* it, uint64_t quota = ~0ull) {
         it->G = G;
         Job& j = it->job;
         j = Job{};
         j.seed = seed; j.opt = opt; j.c = c; j.hits = hits;
+        const uint64_t left = remaining();
+        j.i0 = pos; j.count = std::min(left, quota);
         if (phase == BOOT) {
-            j.i0 = 0; j.count = sb; j.dom_pair = DOM_BOOT_PAIR; j.dom_path = DOM_BOOT_PATH; j.S = nullptr;
+            j.dom_pair = DOM_BOOT_PAIR; j.dom_path = DOM_BOOT_PATH; j.S = nullptr;
             it->red_c = 0;
         } else {
-            j.i0 = r; j.count = target - r; j.dom_pair = DOM_PAIR; j.dom_path = DOM_PATH; j.S = S;
+            j.dom_pair = DOM_PAIR; j.dom_path = DOM_PATH; j.S = S;
             it->red_c = c;
         }
-        it->reduce = true;
+        it->reduce = j.count == left;
         const int rc = grow_ovf(E, j.count);
         j.ovf_list = ovf;
         return rc;
     }
 
-    // Advances the state after a tick (slot: counters + reduction outputs).
-    int consume(Engine& E, const char* slot, const LaunchTotals& tt) {
-        const u64* ctr = (const u64*)slot;
+    // Advances the state after a tick of `count` samples (slot: counters, and
+    // the reduction outputs when the tick completed the phase).
+    int consume(Engine& E, const char* slot, const LaunchTotals& tt, uint64_t count) {
+        T.kernel_ms += tt.kernel_ms; T.launches += tt.launches; T.escan += tt.escan; T.eadd += tt.eadd;
+        T.snew += tt.snew; T.fseg += tt.fseg; T.wide += tt.wide;
+        if (phase == BOOT) boot_sum_int += tt.sum_int;
+        else T.sum_int += tt.sum_int;
+        pos += count;
+        if (remaining() > 0) return MANTRA_OK;
         u64 H;
         std::memcpy(&H, slot + SLOT_HMAX, 8);
         reduces += 1;
         if (phase == BOOT) {
             // DrawSufficientSampleSize(G, s', delta/2) and SamplingSchedule
             double v0 = (double)H / (double)sb;
-            double rho = (double)tt.sum_int / (double)sb;
+            double rho = (double)boot_sum_int / (double)sb;
             if (v0 == 0.0 || rho == 0.0) { v0 = 1.0 / (double)sb; rho = std::max(rho, v0); }
             const double om = std::ceil(omega_closed_form(v0, rho, eps, delta / 2.0));
             if (!(om <= (double)RMAX)) return MANTRA_E_INVAL;
@@ -818,15 +855,10 @@ struct Problem {
                 s1 = lo;
             }
             I.bootstrap = sb; I.omega = omega; I.s1 = s1; I.rho_hat = rho;
-            T.kernel_ms += tt.kernel_ms; T.launches += tt.launches; T.escan += tt.escan; T.eadd += tt.eadd;
-            T.snew += tt.snew; T.fseg += tt.fseg; T.wide += tt.wide;
             CU(cudaMemsetAsync(hits, 0, b_hits, E.sa));
-            phase = ROUND; r = 0; target = s1; round = 0;
+            phase = ROUND; r = 0; pos = 0; target = s1; round = 0;
             return MANTRA_OK;
         }
-        (void)ctr;
-        T.kernel_ms += tt.kernel_ms; T.launches += tt.launches; T.escan += tt.escan; T.eadd += tt.eadd;
-        T.snew += tt.snew; T.fseg += tt.fseg; T.wide += tt.wide; T.sum_int += tt.sum_int;
         r = target;
         round += 1;
         int64_t NR = 0;
@@ -887,15 +919,18 @@ int problem_from(const mantra_graph* g, mantra_opt opt, double eps, double delta
 // One tick for every running problem of `ps`: each contributes its next
 // sample range; results advance each problem's state.  Returns false when no
 // problem had work.
-bool tick_problems(Engine& E, std::vector<Problem*>& ps) {
+bool tick_problems(Engine& E, std::vector<Problem*>& ps, uint64_t budget_bfs = ~0ull, uint64_t budget_pfm = ~0ull) {
     std::vector<Problem*> act;
     std::vector<TickItem> items;
     std::vector<uint64_t*> ovfs;
     for (Problem* p : ps) {
         if (p->status != MANTRA_OK || p->phase == Problem::DONE) continue;
+        uint64_t& left = p->opt == MANTRA_PFM ? budget_pfm : budget_bfs;
+        if (left == 0) continue;                      // waits for a later tick
         TickItem it;
-        const int rc = p->item(E, &it);
+        const int rc = p->item(E, &it, left);
         if (rc != MANTRA_OK) { p->status = rc; continue; }
+        left -= it.job.count;
         act.push_back(p); items.push_back(it); ovfs.push_back(p->ovf);
     }
     if (act.empty()) return false;
@@ -907,7 +942,7 @@ bool tick_problems(Engine& E, std::vector<Problem*>& ps) {
     }
     for (size_t x = 0; x < act.size(); ++x) {
         if (R.status[x] != MANTRA_OK) { act[x]->status = R.status[x]; continue; }
-        const int st = act[x]->consume(E, R.slot[x].data(), R.tot[x]);
+        const int st = act[x]->consume(E, R.slot[x].data(), R.tot[x], items[x].job.count);
         if (st != MANTRA_OK) act[x]->status = st;
     }
     return true;
@@ -972,11 +1007,16 @@ int current_engine(const mantra_graph* g, Engine** E) {
 // ---------------------------------------------------------------------------
 // Serving loop (continuous batching).  Requests wait in a FIFO queue and are
 // admitted while their device-state footprint fits the budget (one request is
-// always admitted when none is running).  Every tick carries the pending
-// sample range of every running request; finished requests leave between
-// ticks and queued ones join at the next tick.  Results wait on the host
-// until polled.
+// always admitted when none is running).  A tick carries a bounded number of
+// samples per search family, about SERVER_TICK_PER_CTA per resident CTA,
+// handed out in arrival order: the oldest running requests get their whole
+// pending range first (a round may span ticks), so requests complete close
+// to arrival order while every tick still fills the GPU.  Finished requests
+// leave between ticks and queued ones join at the next tick.  Results wait
+// on the host until polled.
 // ---------------------------------------------------------------------------
+constexpr uint64_t SERVER_TICK_PER_CTA = 32;
+
 struct Request {
     uint64_t id = 0;
     Problem p;
@@ -1030,7 +1070,14 @@ struct Server {
                     }
                     ps.push_back(&r->p);
                 }
-                tick_problems(*E, ps);
+                // per-family tick budgets (MANTRA_SERVER_TICK_SAMPLES overrides)
+                uint64_t bb = SERVER_TICK_PER_CTA * (uint64_t)(E->bfs_grid ? E->bfs_grid : 2 * E->num_sms);
+                uint64_t bp = SERVER_TICK_PER_CTA * (uint64_t)(E->pc_grid ? E->pc_grid : 2 * E->num_sms);
+                if (const char* env = std::getenv("MANTRA_SERVER_TICK_SAMPLES")) {
+                    const long long v = std::atoll(env);
+                    if (v > 0) bb = bp = (uint64_t)v;
+                }
+                tick_problems(*E, ps, bb, bp);
                 std::vector<Problem*> fin;
                 for (Request* r : batch)
                     if (r->p.status != MANTRA_OK || r->p.phase == Problem::DONE) fin.push_back(&r->p);

@@ -80,9 +80,10 @@ extern "C" int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt
 
     // layout: [counters | task table (one task) | overflow list (count entries) | per-CTA search regions]
     const size_t smem = bfs_smem_bytes(A);
-    const bool in_smem = smem + bfs_static_smem() + 1024 <= smem_optin;
+    const bool in_smem = smem + bfs_static_smem(512) + 1024 <= smem_optin;
     BfsWs ws{};
     const size_t region = bfs_region_bytes(n, A, in_smem, &ws);
+    ws.nt = 512;
     const size_t head = kHeadBytes + round256(count * 8);
     if (head >= kScratchBytes || region > kScratchBytes - head) return MANTRA_E_INVAL;   // exceeds the fixed scratch
     int grid = (int)std::min<size_t>((size_t)num_sms, (kScratchBytes - head) / region);

@@ -28,15 +28,15 @@
 
 namespace mantra {
 
-constexpr int BFS_NT = 1024;
-constexpr int BFS_NW = BFS_NT / 32;
-constexpr uint32_t FCAP = 4096;   // frontier states whose times and running sums fit in shared memory
 constexpr int IPT = 2;            // frontier states per thread in a segmented-scan tile
 
-template <bool WIDE>
-__global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint64_t* unit_start,
+// BFS_NT threads per CTA, 1024 / BFS_NT CTAs per SM at 64 registers.
+template <bool WIDE, int BFS_NT>
+__global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks, const uint64_t* unit_start,
                                                    const uint32_t* ntasks_p, u64* work, const BfsWs ws) {
     typedef typename SigOps<WIDE>::T Sig;
+    constexpr int BFS_NW = BFS_NT / 32;
+    constexpr uint32_t FCAP = BFS_NT * 4;   // frontier states whose times and running sums fit in shared memory
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     __shared__ __align__(16) Task sh_task;
     __shared__ int sh_t;
@@ -55,8 +55,8 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
     uint32_t* stamp_p = reinterpret_cast<uint32_t*>(region + ws.o_stamp);
 
     extern __shared__ uint32_t dyn_smem[];
-    uint32_t* V = ws.bits_in_smem ? dyn_smem : reinterpret_cast<uint32_t*>(region + ws.o_bits);
-    uint32_t* N = V + ws.bits_words;
+    uint32_t* V = ws.bits_in_smem ? dyn_smem : reinterpret_cast<uint32_t*>(region + ws.o_bits);   // visited
+    uint32_t* N = reinterpret_cast<uint32_t*>(region + ws.o_nbits);   // next level (written by fire-and-forget atomics)
 
     __shared__ uint32_t sm_scan[32];
     __shared__ u64 sm_scan64[32];
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
     __shared__ u64 sm_Fc[WIDE ? 1 : FCAP];
 
     if (ws.bits_in_smem) {
-        for (uint32_t w = tid; w < 2 * ws.bits_words; w += BFS_NT) V[w] = 0u;
+        for (uint32_t w = tid; w < ws.bits_words; w += BFS_NT) V[w] = 0u;
     }
     if (tid == 0) sh_stamp = *stamp_p;
     // Next level stamp (segmap entries of older levels never match it) and the
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
             const uint32_t per_w = (((words + BFS_NW - 1) / BFS_NW) + 31u) & ~31u;
             const uint32_t w_lo = min((uint32_t)wid * per_w, words), w_hi = min(w_lo + per_w, words);
             uint32_t cnt = 0;
-            for (uint32_t w = w_lo + lane; w < w_hi; w += 32) cnt += __popc(N[w]);
+            for (uint32_t w = w_lo + lane; w < w_hi; w += 32) cnt += __popc(__ldcg(N + w));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
             if (lane == 0) sm_wcnt[wid] = cnt;
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
             const uint32_t* const g_slot_v2 = g.slot_v;
             for (uint32_t w0 = w_lo; w0 < w_hi; w0 += 32) {
                 const uint32_t w = w0 + lane;
-                uint32_t bits = (w < w_hi) ? N[w] : 0u;
+                uint32_t bits = (w < w_hi) ? __ldcg(N + w) : 0u;
                 if (bits) { V[w] |= bits; N[w] = 0u; }
                 const uint32_t c = __popc(bits);
                 uint32_t incl = c;
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
             uint32_t first = NONE;
             for (uint32_t a0 = zs; a0 < ze && first == NONE; a0 += 32) {
                 const uint32_t a = a0 + lane;
-                const bool b = a < ze && ((N[a >> 5] >> (a & 31)) & 1u);
+                const bool b = a < ze && ((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u);
                 const unsigned msk = __ballot_sync(FULL, b);
                 if (msk) first = a0 + __ffs(msk) - 1;
             }
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
             if (job.opt == 1) tot = sig[first];
             else {
                 for (uint32_t a = zs + lane; a < ze; a += 32)
-                    if ((N[a >> 5] >> (a & 31)) & 1u) { const Sig sm = tot + sig[a]; bad |= sm < tot; tot = sm; }
+                    if ((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u) { const Sig sm = tot + sig[a]; bad |= sm < tot; tot = sm; }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     const Sig y = shfl_xor_w(tot, o);
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
                 const uint32_t ze_end = (job.opt == 1) ? first + 1 : ze;
                 for (uint32_t a0 = (job.opt == 1 ? first : zs); !err && a0 < ze_end && cur == NONE; a0 += 32) {
                     const uint32_t a = a0 + lane;
-                    const Sig wt = (a < ze_end && ((N[a >> 5] >> (a & 31)) & 1u)) ? sig[a] : (Sig)0;
+                    const Sig wt = (a < ze_end && ((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u)) ? sig[a] : (Sig)0;
                     const Sig incl = warp_inclusive_sum(wt);
                     const unsigned msk = __ballot_sync(FULL, xs < incl);
                     if (msk) {
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
 
         // ---------------- cleanup: sigma of every touched slot, bitmaps ----------------
         for (uint32_t w = tid; w < words; w += BFS_NT) {
-            uint32_t bits = V[w] | N[w];
+            uint32_t bits = V[w] | __ldcg(N + w);
             if (bits) {
                 V[w] = 0u; N[w] = 0u;
                 while (bits && !stats) {
@@ -608,6 +608,8 @@ __global__ void __launch_bounds__(BFS_NT, 1) k_bfs(const Task* tasks, const uint
 
 // Host-side launch helpers -------------------------------------------------
 
+// Region of one CTA.  The visited bitmap is in shared memory when
+// bits_in_smem; the next-level bitmap is always in the region.
 size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws) {
     ws->bits_words = (A + 31) / 32;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -623,20 +625,25 @@ size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws) {
     ws->o_vb = o;      o = al(o + (size_t)((n + 31) / 32 + 1) * 4);
     ws->o_segmap = o;  o = al(o + (size_t)n * 8);
     ws->o_stamp = o;   o = al(o + 4);
+    ws->o_nbits = o;   o = al(o + (size_t)ws->bits_words * 4);
     ws->n_cap = n;
     ws->o_bits = o;
-    if (!bits_in_smem) o = al(o + (size_t)2 * ((A + 31) / 32) * 4);
+    if (!bits_in_smem) o = al(o + (size_t)ws->bits_words * 4);
     ws->bits_in_smem = bits_in_smem ? 1 : 0;
     return o;
 }
 
-size_t bfs_smem_bytes(uint32_t A) { return (size_t)2 * ((A + 31) / 32) * 4; }
+size_t bfs_smem_bytes(uint32_t A) { return (size_t)((A + 31) / 32) * 4; }
 
-// Static shared memory of the kernel (range table, task copy, scan scratch).
-size_t bfs_static_smem() {
+// Static shared memory of the nt-thread kernels (range table, task copy,
+// level scratch).
+size_t bfs_static_smem(int nt) {
     cudaFuncAttributes a{}, b{};
-    if (cudaFuncGetAttributes(&a, k_bfs<false>) != cudaSuccess || cudaFuncGetAttributes(&b, k_bfs<true>) != cudaSuccess)
-        return 96 * 1024;
+    const cudaError_t e1 = nt == 1024 ? cudaFuncGetAttributes(&a, k_bfs<false, 1024>)
+                                      : cudaFuncGetAttributes(&a, k_bfs<false, 512>);
+    const cudaError_t e2 = nt == 1024 ? cudaFuncGetAttributes(&b, k_bfs<true, 1024>)
+                                      : cudaFuncGetAttributes(&b, k_bfs<true, 512>);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return 96 * 1024;
     return std::max(a.sharedSizeBytes, b.sharedSizeBytes);
 }
 
@@ -647,17 +654,30 @@ cudaError_t bfs_configure(size_t smem) {
     static size_t configured = 0;
     std::lock_guard<std::mutex> lock(mu);
     if (smem <= configured) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_bfs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_bfs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) configured = smem;
-    return e;
+    const void* ks[4] = {(const void*)k_bfs<false, 512>, (const void*)k_bfs<true, 512>,
+                         (const void*)k_bfs<false, 1024>, (const void*)k_bfs<true, 1024>};
+    for (const void* k : ks) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    configured = smem;
+    return cudaSuccess;
+}
+
+cudaError_t bfs_blocks_per_sm(int nt, size_t smem, int* out) {
+    return nt == 1024 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bfs<false, 1024>, 1024, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bfs<false, 512>, 512, smem);
 }
 
 cudaError_t launch_bfs(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
                        const BfsWs& ws, int grid, size_t smem, bool wide, cudaStream_t st) {
-    if (wide) k_bfs<true><<<grid, BFS_NT, smem, st>>>(tasks, unit_start, ntasks, work, ws);
-    else k_bfs<false><<<grid, BFS_NT, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+    if (ws.nt == 1024) {
+        if (wide) k_bfs<true, 1024><<<grid, 1024, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else k_bfs<false, 1024><<<grid, 1024, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+    } else {
+        if (wide) k_bfs<true, 512><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else k_bfs<false, 512><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+    }
     return cudaGetLastError();
 }
 

@@ -417,10 +417,11 @@ __device__ __forceinline__ void push_overflow(const Job& job, uint64_t i) {
 struct BfsWs {
     char* base;          // CTA b uses base + b * stride
     size_t stride;
-    size_t o_sig, o_fc, o_f, o_ft, o_lev, o_segb, o_segu, o_path, o_bits, o_vb, o_segmap, o_stamp;
-    int bits_in_smem;    // visited / next bitmaps in dynamic shared memory
+    size_t o_sig, o_fc, o_f, o_ft, o_lev, o_segb, o_segu, o_path, o_bits, o_vb, o_segmap, o_stamp, o_nbits;
+    int bits_in_smem;    // visited bitmap in dynamic shared memory (the next-level bitmap is in the region)
     uint32_t bits_words; // capacity of each bitmap (words): ceil(A_max / 32)
     uint32_t n_cap;      // node capacity of a region
+    int nt;              // threads per CTA (512 or 1024)
 };
 
 // Per-warp scratch of the pfm search kernel.
@@ -445,7 +446,8 @@ struct PfmCtaWs {
 
 size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws);
 size_t bfs_smem_bytes(uint32_t A);
-size_t bfs_static_smem();
+size_t bfs_static_smem(int nt);
+cudaError_t bfs_blocks_per_sm(int nt, size_t smem, int* out);
 cudaError_t bfs_configure(size_t smem);
 // Task-table launches: work unit u of the launch belongs to task
 // task_of_unit(unit_start, *ntasks, u); the first unused unit ends a CTA/warp.
