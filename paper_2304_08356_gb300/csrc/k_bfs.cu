@@ -29,6 +29,7 @@
 namespace mantra {
 
 constexpr int IPT = 2;            // frontier states per thread in a segmented-scan tile
+constexpr int WALK_K = 2;         // edge windows with loads in flight per warp in the push
 
 // BFS_NT threads per CTA, 1024 / BFS_NT CTAs per SM at 64 registers.
 template <bool WIDE, int BFS_NT>
@@ -337,9 +338,8 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 __syncthreads();
                 const uint32_t per = ((E + BFS_NW * 32u - 1u) / (BFS_NW * 32u)) * 32u;
                 const uint32_t w_lo = min((uint32_t)wid * per, E), w_hi = min(w_lo + per, E);
-                lbs_walk(cs_off, Gc, w_lo, w_hi, [&](uint32_t r, uint32_t j) {
-                    const uint32_t e = cs_first[r] + (j - cs_off[r]);
-                    const uint32_t a = __ldg(g_out_slot + e), t = __ldg(g_out_t + e);
+                lbs_walk_batched<WALK_K>(cs_off, Gc, cs_first, w_lo, w_hi, g_out_slot, g_out_t,
+                                         [&](uint32_t r, uint32_t, uint32_t a, uint32_t t) {
                     ++my_escan;
                     if (!((V[a >> 5] >> (a & 31)) & 1u)) {
                         atomicOr(N + (a >> 5), 1u << (a & 31));

@@ -37,6 +37,7 @@
 namespace mantra {
 
 constexpr uint32_t SRC = NONE - 1u;        // fsl of the source
+constexpr int WALK_K = 2;                  // edge windows with loads in flight per warp
 
 template <bool SM>
 __device__ __forceinline__ uint32_t ldv(const uint32_t* p) {
@@ -149,10 +150,13 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
     // Every edge of the range table once: warp w walks a contiguous slice in
     // windows of 32; h is the range holding the window's first edge.  Ends
     // with a barrier.
-    auto expand = [&](uint32_t E, auto edge) {
+    // edge(u, v, slot) for every out-edge (u, v) of the table, head's arrival slot
+    // loaded; WALK_K windows of loads in flight per warp.
+    auto expand = [&](uint32_t E, const uint32_t* out_v, const uint32_t* out_slot, auto edge) {
         const uint32_t per = ((E + PC_NW * 32u - 1u) / (PC_NW * 32u)) * 32u;
         const uint32_t w_lo = min((uint32_t)wid * per, E), w_hi = min(w_lo + per, E);
-        lbs_walk(cs_off, sh_Gc, w_lo, w_hi, [&](uint32_t r, uint32_t j) { edge(cs_u[r], cs_first[r] + (j - cs_off[r])); });
+        lbs_walk_batched<WALK_K>(cs_off, sh_Gc, cs_first, w_lo, w_hi, out_v, out_slot,
+                                 [&](uint32_t r, uint32_t, uint32_t v, uint32_t sl) { edge(cs_u[r], v, sl); });
         __syncthreads();
     };
 
@@ -256,8 +260,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                 }
                 const uint32_t E = table(u, rl, rh);
                 if (tid == 0) my_x += E;
-                expand(E, [&](uint32_t, uint32_t e) {
-                    const uint32_t v = __ldg(out_v + e), sl = __ldg(out_slot + e);
+                expand(E, out_v, out_slot, [&](uint32_t, uint32_t v, uint32_t sl) {
                     if (v == s || sl >= ldv<FA_SMEM>(fsl + v)) return;
                     if (sl < atomicMin(fsl + v, sl)) atomicOr(NB + (v >> 5), 1u << (v & 31));
                 });
@@ -340,8 +343,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                     const uint32_t rh[2] = {lo[0], lo[1]};
                     const uint32_t E = table(u, rl, rh);
                     if (tid == 0) my_x += E;
-                    expand(E, [&](uint32_t uu, uint32_t e) {
-                        const uint32_t v = __ldg(out_v + e), sl = __ldg(out_slot + e);
+                    expand(E, out_v, out_slot, [&](uint32_t uu, uint32_t v, uint32_t sl) {
                         if (v == s || ldv<FA_SMEM>(fsl + v) != sl) return;   // not v's earliest arrival
                         if (stats) atomicMin(hop + v, __ldcg(hop + uu) + 1u);
                         else if (!SigOps<false>::atomic_add(sig + v, __ldcg(sig + uu))) sh_ovf = 1;

@@ -403,6 +403,54 @@ __device__ __forceinline__ void lbs_walk(const uint32_t* off, uint32_t Gc, uint3
     }
 }
 
+// lbs_walk over K windows at a time with the edge loads batched: the range
+// and edge index of every edge of the K windows come from the table first
+// (shared memory), then pa[e] and pb[e] are loaded for all of them, then
+// edge(g, e, pa[e], pb[e]) runs for each valid edge -- K times the loads in
+// flight per warp.  first[g] is the first edge of range g.
+template <int K, typename F>
+__device__ __forceinline__ void lbs_walk_batched(const uint32_t* off, uint32_t Gc, const uint32_t* first, uint32_t w_lo,
+                                                 uint32_t w_hi, const uint32_t* __restrict__ pa,
+                                                 const uint32_t* __restrict__ pb, F edge) {
+    const uint32_t lane = threadIdx.x & 31;
+    if (w_lo >= w_hi) return;
+    uint32_t lo = 0, hi = Gc;                 // off[lo] <= w_lo < off[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= w_lo) lo = mid; else hi = mid;
+    }
+    uint32_t h = lo;
+    for (uint32_t base = w_lo; base < w_hi; base += 32u * K) {
+        uint32_t rr[K], ee[K];
+        bool ok[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const uint32_t b = base + 32u * k;
+            ok[k] = false; rr[k] = 0u; ee[k] = 0u;
+            if (b < w_hi) {                       // the same for the whole warp
+                const uint32_t kk = h + 1u + lane;
+                const uint32_t o = (kk <= Gc) ? off[kk] : 0xFFFFFFFFu;   // > b for every kk
+                const uint32_t d = o - b;
+                const uint32_t mask = __reduce_or_sync(0xFFFFFFFFu, d < 32u ? (1u << d) : 0u);
+                const uint32_t g = h + __popc(mask & ((2u << lane) - 1u));
+                const uint32_t j = b + lane;
+                ok[k] = j < w_hi;
+                if (ok[k]) { rr[k] = g; ee[k] = first[g] + (j - off[g]); }
+                h += __popc(__ballot_sync(0xFFFFFFFFu, o <= b + 32u));
+            }
+        }
+        uint32_t va[K], vb[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            va[k] = ok[k] ? __ldg(pa + ee[k]) : 0u;
+            vb[k] = ok[k] ? __ldg(pb + ee[k]) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (ok[k]) edge(rr[k], ee[k], va[k], vb[k]);
+    }
+}
+
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, ST_OK, code); }
 
 // Records sample i for the 128-bit / in-order re-run (a job without a list
