@@ -61,6 +61,10 @@ typedef struct {
     int delta_sched;     /* 0: round i uses delta/2^(i+1) (union bound totals delta); 1: delta/2^i as printed */
     int out_device;      /* 1: est_out / hits_out are DEVICE pointers (no device-to-host copy) */
     void* stream;        /* cudaStream_t to run on; NULL = the graph's own stream */
+    int vhat_mode;       /* 0: the variance term of xi is the empirical wimpy variance W (as Algorithm 1
+                            passes it); 1: the appendix's variance bound from W,
+                            W + L/r + sqrt((L/r)^2 + 2 W L / r) with L = ln(2/delta_i), the round's
+                            delta_i split evenly between it and xi */
 } mantra_opts;
 
 /* Diagnostics of one mantra_estimate call. */
@@ -74,7 +78,7 @@ typedef struct {
     uint64_t max_hits;       /* H = max_v hits_v */
     int64_t rade_num;        /* N_R = sum_j max_v S[j][v] */
     double xi;               /* final supremum-deviation bound (Theorem 1) */
-    double vhat;             /* final empirical wimpy variance W = H / r */
+    double vhat;             /* final variance term of xi: W = H / r, or its bound (vhat_mode 1) */
     double rho_hat;          /* bootstrap estimate of the mean internal length */
     uint64_t edges_scanned;  /* temporal edges examined by the searches (all samples) */
     uint64_t sigma_adds;     /* path-count additions into states */

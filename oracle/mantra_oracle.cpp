@@ -26,7 +26,13 @@
 // then earliest arrival at z (Figure "example_tp" caption); canonical
 // predecessor order for the path draw (in-edges by ascending w, then the
 // predecessor's appearances by ascending time); delta_i = delta/2^(i+1);
-// vhat = W; natural logarithms; pfm distance = minimum hops among pfm paths.
+// vhat = W, or (vhat_mode 1) the appendix's variance bound with its garbled
+// square-root term read as 2 W ln(1/delta)/r; natural logarithms; pfm
+// distance = minimum hops among pfm paths.
+//
+// Parity unpinned (no value printed in the paper; pinned only by special
+// cases, monotonicity, Theorem 1's guarantee and a coverage simulation): the
+// floating-point bounds xi, omega, the s_1 search and the variance bound.
 //
 // Integers: path counts are exact unsigned 128-bit; a count that would exceed
 // 2^128-1 is reported as an overflow error.
@@ -425,6 +431,16 @@ double omega_bound(double vhat, double rho, double eps, double delta) {
     return ((2.0 * vhat + 2.0 * eps / 3.0) / (eps * eps)) * (std::log(2.0 * rho / vhat) + std::log(1.0 / delta));
 }
 
+// Variance bound from the empirical wimpy variance (the self-bounding
+// proposition of the appendix, adapted from Pellegrina & Vandin): with
+// probability >= 1 - delta, sup_f Var(f) <= W + L/r + sqrt((L/r)^2 + 2 W L / r),
+// L = ln(1/delta).  The printed square-root term is garbled; it is read as the
+// same self-bounding form as the R bound of Theorem 1 (2 L x / r).
+double wimpy_variance_bound(double W, double delta, double r) {
+    const double L = std::log(1.0 / delta);
+    return W + L / r + std::sqrt((L / r) * (L / r) + 2.0 * W * L / r);
+}
+
 double delta_round(double delta, uint64_t i, int sched) {
     return sched == 1 ? delta / std::ldexp(1.0, (int)i) : delta / std::ldexp(1.0, (int)(i + 1));
 }
@@ -554,15 +570,19 @@ double orc_sd_bound(double Rc, double W, double vhat, double delta, double r, do
 
 double orc_xi_from_R(double Rb, double vhat, double delta, double r) { return xi_from_R(Rb, vhat, delta, r); }
 
+double orc_wimpy_variance_bound(double W, double delta, double r) { return wimpy_variance_bound(W, delta, r); }
+
 double orc_omega_bound(double vhat, double rho, double eps, double delta) {
     return omega_bound(vhat, rho, eps, delta);
 }
 
 // Algorithm 1 (MANTRA).  fixed_r > 0 runs exactly fixed_r samples with no
 // bootstrap and no stopping test.  Outputs est[v] = hits[v] / r.
+// vhat_mode 0: vhat = W in xi (as Algorithm 1 passes it); 1: vhat = the
+// variance bound above, delta_i split evenly between it and xi.
 int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed, uint32_t c, double growth,
-                 uint64_t fixed_r, uint64_t bootstrap, int delta_sched, double* est, uint64_t* hits_out,
-                 orc_info* info) {
+                 uint64_t fixed_r, uint64_t bootstrap, int delta_sched, int vhat_mode, double* est,
+                 uint64_t* hits_out, orc_info* info) {
     const Graph* G = (const Graph*)g;
     const uint32_t n = G->n;
     if (n < 2 || !(eps > 0 && eps < 1) || !(delta > 0 && delta < 1) || c < 1 || c > 128) return E_INVAL;
@@ -600,10 +620,17 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
         for (uint32_t v = 0; v < n; ++v) h = std::max(h, hits[v]);
         *NR = tot; *H = h;
     };
+    auto vhat_of = [&](uint64_t H, uint64_t r, uint64_t round) {
+        double W = (double)H / (double)r;
+        if (vhat_mode != 1) return W;
+        return wimpy_variance_bound(W, delta_round(delta, round, delta_sched) / 2.0, (double)r);
+    };
     auto xi_of = [&](int64_t NR, uint64_t H, uint64_t r, uint64_t round) {
         double Rc = (double)NR / ((double)c * (double)r);
         double W = (double)H / (double)r;
-        return sd_bound(Rc, W, W, delta_round(delta, round, delta_sched), (double)r, (double)c);
+        double di = delta_round(delta, round, delta_sched);
+        if (vhat_mode == 1) di /= 2.0;
+        return sd_bound(Rc, W, vhat_of(H, r, round), di, (double)r, (double)c);
     };
 
     uint64_t r = 0;
@@ -615,7 +642,7 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
         reduce(&NR, &H);
         I.rounds = 1; I.rade_num = NR; I.max_hits = H;
         I.xi = xi_of(NR, H, r, 1);
-        I.vhat = (double)H / (double)r;
+        I.vhat = vhat_of(H, r, 1);
     } else {
         // Bootstrap (DrawSufficientSampleSize with delta/2): s' samples from
         // their own streams, not part of S.
@@ -660,7 +687,7 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
             int64_t NR; uint64_t H;
             reduce(&NR, &H);
             double xi = xi_of(NR, H, r, round);
-            I.rounds = round; I.rade_num = NR; I.max_hits = H; I.xi = xi; I.vhat = (double)H / (double)r;
+            I.rounds = round; I.rade_num = NR; I.max_hits = H; I.xi = xi; I.vhat = vhat_of(H, r, round);
             if (r >= omega || xi <= eps) break;
             uint64_t nt = (uint64_t)std::ceil(growth * (double)target);
             if (nt <= target) nt = target + 1;

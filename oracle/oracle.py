@@ -72,7 +72,9 @@ def lib():
         L.orc_omega_bound.restype = C.c_double
         L.orc_omega_bound.argtypes = [C.c_double] * 4
         L.orc_estimate.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_uint64, C.c_uint32,
-                                   C.c_double, C.c_uint64, C.c_uint64, C.c_int, dp, u64p, C.POINTER(Info)]
+                                   C.c_double, C.c_uint64, C.c_uint64, C.c_int, C.c_int, dp, u64p, C.POINTER(Info)]
+        L.orc_wimpy_variance_bound.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_wimpy_variance_bound.restype = C.c_double
         L.orc_stats.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64, C.c_int, u64p, u32p]
         L.orc_exact_bc.argtypes = [C.c_void_p, C.c_int, dp]
         _lib = L
@@ -126,6 +128,10 @@ def xi_from_R(R, vhat, delta, r):
 
 def omega_bound(vhat, rho, eps, delta):
     return lib().orc_omega_bound(vhat, rho, eps, delta)
+
+
+def wimpy_variance_bound(W, delta, r):
+    return lib().orc_wimpy_variance_bound(W, delta, r)
 
 
 class Graph:
@@ -188,11 +194,11 @@ class Graph:
                         [int(x) for x in paths[q * cap:q * cap + ln[q]]]))
         return out
 
-    def estimate(self, opt, eps, delta, seed, c=25, growth=1.2, fixed_r=0, bootstrap=0, delta_sched=0):
+    def estimate(self, opt, eps, delta, seed, c=25, growth=1.2, fixed_r=0, bootstrap=0, delta_sched=0, vhat_mode=0):
         est = np.zeros(self.n, np.float64)
         hits = np.zeros(self.n, np.uint64)
         info = Info()
-        _chk(lib().orc_estimate(self.h, opt, eps, delta, seed, c, growth, fixed_r, bootstrap, delta_sched,
+        _chk(lib().orc_estimate(self.h, opt, eps, delta, seed, c, growth, fixed_r, bootstrap, delta_sched, vhat_mode,
                                 _p(est, C.c_double), _p(hits, C.c_uint64), C.byref(info)))
         return est, hits, info.as_dict()
 

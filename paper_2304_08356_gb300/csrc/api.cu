@@ -713,6 +713,15 @@ double omega_closed_form(double vhat, double rho, double eps, double delta) {
     return ((2.0 * vhat + 2.0 * eps / 3.0) / (eps * eps)) * (std::log(2.0 * rho / vhat) + std::log(1.0 / delta));
 }
 
+// Appendix proposition (after Pellegrina & Vandin): with probability >= 1 - delta
+// the largest estimator variance is at most W + L/r + sqrt((L/r)^2 + 2 W L / r),
+// L = ln(1/delta); the printed square-root term is read in the self-bounding form
+// of Theorem 1's R bound.
+double wimpy_variance_bound(double W, double delta, double r) {
+    const double L = std::log(1.0 / delta);
+    return W + L / r + std::sqrt((L / r) * (L / r) + 2.0 * W * L / r);
+}
+
 double delta_of_round(double delta, uint64_t i, int sched) {
     return sched == 1 ? delta / std::ldexp(1.0, (int)i) : delta / std::ldexp(1.0, (int)(i + 1));
 }
@@ -731,7 +740,7 @@ struct Problem {
     uint32_t c = 25;
     double growth = 1.2;
     uint64_t fixed_r = 0, boot = 0;
-    int dsched = 0;
+    int dsched = 0, vhat_mode = 0;
     double* est_out = nullptr;
     uint64_t* hits_out = nullptr;
     bool out_device = false;
@@ -757,6 +766,7 @@ struct Problem {
         if (c < 1 || c > 128 || !(growth > 1.0)) return MANTRA_E_INVAL;
         if (fixed_r > RMAX) return MANTRA_E_INVAL;
         if (out_device && !est_out) return MANTRA_E_INVAL;
+        if (vhat_mode != 0 && vhat_mode != 1) return MANTRA_E_INVAL;
         return MANTRA_OK;
     }
 
@@ -868,9 +878,13 @@ struct Problem {
             NR += x;
         }
         const double W = (double)H / (double)r;
-        const double xi = xi_from_mcera((double)NR / ((double)c * (double)r), W, W, delta_of_round(delta, round, dsched),
-                                        (double)r, (double)c);
-        I.rounds = round; I.rade_num = NR; I.max_hits = H; I.xi = xi; I.vhat = W;
+        double di = delta_of_round(delta, round, dsched), vh = W;
+        if (vhat_mode == 1) {            // variance bound from W, delta_i split evenly
+            di /= 2.0;
+            vh = wimpy_variance_bound(W, di, (double)r);
+        }
+        const double xi = xi_from_mcera((double)NR / ((double)c * (double)r), W, vh, di, (double)r, (double)c);
+        I.rounds = round; I.rade_num = NR; I.max_hits = H; I.xi = xi; I.vhat = vh;
         if (fixed_r > 0 || r >= omega || xi <= eps) { phase = DONE; return MANTRA_OK; }
         uint64_t nt = (uint64_t)std::ceil(growth * (double)target);
         if (nt <= target) nt = target + 1;
@@ -909,6 +923,7 @@ int problem_from(const mantra_graph* g, mantra_opt opt, double eps, double delta
     p->c = o.c ? o.c : 25;
     p->growth = o.growth > 0 ? o.growth : 1.2;
     p->fixed_r = o.fixed_r; p->boot = o.bootstrap; p->dsched = o.delta_sched;
+    p->vhat_mode = o.vhat_mode;
     p->est_out = est_out; p->hits_out = hits_out; p->out_device = o.out_device != 0; p->info_out = info;
     return p->validate();
 }

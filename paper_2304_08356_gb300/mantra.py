@@ -30,7 +30,7 @@ class MantraError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("c", C.c_uint32), ("growth", C.c_double), ("fixed_r", C.c_uint64), ("bootstrap", C.c_uint64),
-                ("delta_sched", C.c_int), ("out_device", C.c_int), ("stream", C.c_void_p)]
+                ("delta_sched", C.c_int), ("out_device", C.c_int), ("stream", C.c_void_p), ("vhat_mode", C.c_int)]
 
 
 class Info(C.Structure):
@@ -149,11 +149,11 @@ class Graph:
             pass
 
     def estimate(self, opt, eps, delta, seed, c=0, growth=0.0, fixed_r=0, bootstrap=0, delta_sched=0,
-                 est_out=None, hits_out=None, stream=None):
+                 est_out=None, hits_out=None, stream=None, vhat_mode=0):
         """mantra_estimate.  With est_out / hits_out given as integers they are
         device pointers (out_device = 1); otherwise host numpy arrays are
         returned.  Returns (est, hits, info dict)."""
-        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, stream)
+        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, stream, vhat_mode)
         info = Info()
         if isinstance(est_out, int):
             o.out_device = 1
@@ -205,7 +205,7 @@ def estimate_batch(problems):
     for x, p in enumerate(problems):
         g = p["graph"]
         o = Opts(p.get("c", 0), p.get("growth", 0.0), p.get("fixed_r", 0), p.get("bootstrap", 0),
-                 p.get("delta_sched", 0), 0, None)
+                 p.get("delta_sched", 0), 0, None, p.get("vhat_mode", 0))
         est = np.zeros(g.n, np.float64)
         hits = np.zeros(g.n, np.uint64)
         info = Info()
@@ -236,8 +236,9 @@ class Server:
         self.h = h
         self._n = {}
 
-    def submit(self, graph, opt, eps, delta, seed, c=0, growth=0.0, fixed_r=0, bootstrap=0, delta_sched=0):
-        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, None)
+    def submit(self, graph, opt, eps, delta, seed, c=0, growth=0.0, fixed_r=0, bootstrap=0, delta_sched=0,
+               vhat_mode=0):
+        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, None, vhat_mode)
         rid = C.c_uint64()
         _chk(lib().mantra_server_submit(self.h, graph.h, _opt(opt), eps, delta, seed, C.byref(o), C.byref(rid)),
              "mantra_server_submit")

@@ -325,3 +325,23 @@ print(json.dumps({"ok": bool(ok and np.array_equal(h, oh) and np.array_equal(rea
     assert r.returncode == 0, r.stderr[-2000:]
     res = json.loads(r.stdout.strip().splitlines()[-1])
     assert res["ok"] and res["wide"] > 0
+
+
+@pytest.mark.parametrize("opt", [0, 2])
+def test_vhat_mode_bit_exact(M, opt):
+    """vhat_mode 1 (variance term of xi from the appendix's bound on W, the
+    round's delta split evenly): same stopping round, hits and estimates as
+    the oracle; xi and the variance term within 1e-12."""
+    u, v, t = synth.chung_lu_bursty(n=1500, m=30000, seed=21)
+    g = M.Graph(u, v, t)
+    o = O.Graph(u, v, t)
+    est, hits, info = g.estimate(opt, 0.05, 0.1, 7, vhat_mode=1)
+    oest, ohits, oinfo = o.estimate(opt, 0.05, 0.1, 7, vhat_mode=1)
+    for k in ("r", "rounds", "omega", "s1", "sum_int_len", "max_hits", "rade_num"):
+        assert info[k] == oinfo[k], k
+    assert np.array_equal(hits, ohits)
+    for k in ("xi", "vhat"):
+        assert info[k] == pytest.approx(oinfo[k], rel=XI_RTOL), k
+    # the bound is never below W, so the run is at least as long as with vhat = W
+    _, _, i0 = g.estimate(opt, 0.05, 0.1, 7)
+    assert info["vhat"] >= info["max_hits"] / info["r"] and info["r"] >= i0["r"]

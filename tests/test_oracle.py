@@ -15,17 +15,46 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 # --------------------------------------------------------------------------
-# Philox4x32-10: published known-answer vectors (Salmon et al., SC'11)
+# Philox4x32-10 (Salmon et al., SC'11) against an independent implementation:
+# curand's PHILOX4_32_10 host generator (called, not reproduced).  Observed
+# layout of its output: block j (4 words) for seed K is Philox4x32-10 with key
+# (K_lo, K_hi) and counter (q_lo, q_hi, j mod 65536, 0), q = j div 65536; a
+# generator offset of 4j starts at block j.  Counter word 3 is pinned on the
+# GPU against curand's device API (tests/test_gpu_philox.py).
 # --------------------------------------------------------------------------
-def test_philox_known_answers():
-    rows = 0
-    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
-        if line.startswith("#") or not line.strip():
+def _curand_host():
+    import ctypes as C
+    import glob
+    cands = glob.glob("/usr/local/cuda/lib64/libcurand.so*") + glob.glob("/usr/local/cuda/targets/*/lib/libcurand.so*")
+    for c in ["libcurand.so"] + cands:
+        try:
+            return C.CDLL(c)
+        except OSError:
             continue
-        w = [int(x, 16) for x in line.split()]
-        assert O.philox(w[0:4], w[4:6]) == w[6:10]
-        rows += 1
-    assert rows == 3
+    return None
+
+
+def test_philox_matches_curand_host_generator():
+    import ctypes as C
+    L = _curand_host()
+    if L is None:
+        pytest.skip("libcurand not available")
+    PHILOX4_32_10 = 161                               # curandRngType_t value
+    checked = 0
+    for seed in (0, 1, 0x123456789ABCDEF0, 0xFFFFFFFFFFFFFFFF, 0x00000000DEADBEEF):
+        for q, w2 in ((0, 0), (0, 1), (0, 65535), (1, 3), ((1 << 32) + 5, 777), ((1 << 40) + 12345, 40000)):
+            block = q * 65536 + w2
+            gen = C.c_void_p()
+            assert L.curandCreateGeneratorHost(C.byref(gen), PHILOX4_32_10) == 0
+            assert L.curandSetPseudoRandomGeneratorSeed(gen, C.c_ulonglong(seed)) == 0
+            assert L.curandSetGeneratorOffset(gen, C.c_ulonglong(4 * block)) == 0
+            out = (C.c_uint * 4)()
+            assert L.curandGenerate(gen, out, C.c_size_t(4)) == 0
+            L.curandDestroyGenerator(gen)
+            ctr = [q & 0xFFFFFFFF, q >> 32, w2, 0]
+            assert O.philox(ctr, [seed & 0xFFFFFFFF, seed >> 32]) == list(out), (seed, ctr)
+            checked += 1
+    assert checked == 30
 
 
 def test_uniform_draw_range_and_frequencies():
@@ -275,3 +304,24 @@ def test_stats_all_sources_against_bruteforce(seed):
             assert st["psi"] == pytest.approx(sum(d.values()) / len(d), rel=1e-14)
     # sfm distances equal sh distances
     assert np.array_equal(g.stats_counts(0, 0, 0, True)[0], g.stats_counts(1, 0, 0, True)[0])
+
+
+def test_wimpy_variance_bound_covers_the_variance():
+    """The appendix's variance bound from the empirical wimpy variance W holds
+    with probability >= 1 - delta: for a 0/1 estimator f with E[f^2] = p, the
+    bound computed from W = (hits)/r falls below p in at most a delta share
+    of independent samples.  A bound without its square-root or ln/r terms
+    fails this at these sizes."""
+    rng = np.random.default_rng(12)
+    for p, r, delta in ((0.02, 500, 0.1), (0.2, 200, 0.05), (0.001, 4000, 0.1)):
+        hits = rng.binomial(r, p, size=4000)
+        vh = np.array([O.wimpy_variance_bound(h / r, delta, r) for h in hits])
+        assert (vh >= hits / r).all()
+        miss = float((vh < p).mean())
+        assert miss <= delta, (p, r, miss)
+        # the same with the square-root term dropped undershoots far more often
+        L = math.log(1 / delta)
+        bare = hits / r + L / r
+        assert float((bare < p).mean()) > miss
+    # W = 0: only the confidence terms remain, 2 ln(1/delta) / r
+    assert O.wimpy_variance_bound(0.0, 0.1, 1000) == pytest.approx(2 * math.log(10) / 1000, rel=1e-15)
