@@ -157,6 +157,11 @@ struct Graph {
     std::vector<std::vector<std::pair<uint32_t, uint32_t>>> in;   // in[v]  = (w,t)
     uint64_t self_loops = 0;
     uint64_t duplicates = 0;
+    // Edge betweenness (App. A): temporal edge (u,v,t) -> id = its rank in
+    // (v,t,u) order; underlying edge (u,v) -> id = its rank in (v,u) order.
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t>, uint32_t> tid;   // key (v,t,u)
+    std::map<std::pair<uint32_t, uint32_t>, uint32_t> uid;              // key (v,u)
+    std::vector<uint32_t> t2u;                                          // temporal id -> underlying id
 };
 
 const int64_t NEG_INF = -1;                 // the source appearance (s, -inf)
@@ -390,6 +395,7 @@ struct Sample {
     uint32_t s = 0, z = 0;
     u128 sigma = 0;
     std::vector<uint32_t> path;   // s .. z, empty when z is unreachable
+    std::vector<uint32_t> edges;  // temporal edge ids of the path, s to z
 };
 
 // One sample of Algorithm 1's Update step: draw (s,z), count optimal paths,
@@ -404,7 +410,13 @@ int one_sample(const Graph& G, int opt, uint64_t seed, uint64_t i, uint32_t dom_
     if (out->sigma == 0) return OK;                       // unreachable: empty path
     u128 x;
     if (!uniform_below128(out->sigma, seed, i, dom_path, &x)) return E_RNG;
-    return unrank_path(G, opt, out->s, out->z, R, x, &out->path);
+    std::vector<int64_t> times;
+    int st2 = unrank_path(G, opt, out->s, out->z, R, x, &out->path, &times);
+    if (st2 != OK) return st2;
+    out->edges.clear();
+    for (size_t k = 0; k + 1 < out->path.size(); ++k)          // edge (path[k], path[k+1], times[k+1])
+        out->edges.push_back(G.tid.at(std::make_tuple(out->path[k + 1], (uint32_t)times[k + 1], out->path[k])));
+    return OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -488,6 +500,17 @@ void* orc_graph_new(const uint32_t* u, const uint32_t* v, const uint32_t* t, uin
         G->out[uu].push_back(std::make_pair(vv, tt));             // so out[u] ascends in t
         G->in[vv].push_back(std::make_pair(uu, tt));
     }
+    for (const auto& k : seen) {
+        G->tid[std::make_tuple(std::get<2>(k), std::get<0>(k), std::get<1>(k))] = 0;
+        G->uid[std::make_pair(std::get<2>(k), std::get<1>(k))] = 0;
+    }
+    uint32_t r = 0;
+    for (auto& kv : G->tid) kv.second = r++;
+    r = 0;
+    for (auto& kv : G->uid) kv.second = r++;
+    G->t2u.assign(G->tid.size(), 0);
+    for (const auto& kv : G->tid)
+        G->t2u[kv.second] = G->uid.at(std::make_pair(std::get<0>(kv.first), std::get<2>(kv.first)));
     return G;
 }
 
@@ -547,9 +570,11 @@ int orc_unrank(const void* g, int opt, uint32_t s, uint32_t z, uint64_t x_lo, ui
 
 // Samples i0 .. i0+count-1 of the given domains: pair, sigma and the drawn
 // path (full vertex list s..z; len 0 when unreachable).
+// Per-sample results; path_edges (optional) receives the temporal edge ids of
+// each path (len - 1 of them) at the same offsets as paths.
 int orc_samples(const void* g, int opt, uint64_t seed, uint64_t i0, uint64_t count, uint32_t dom_pair,
                 uint32_t dom_path, uint32_t* s, uint32_t* z, uint64_t* sig_lo, uint64_t* sig_hi, uint32_t* len,
-                uint32_t* paths, uint32_t cap) {
+                uint32_t* paths, uint32_t cap, uint32_t* path_edges) {
     const Graph* G = (const Graph*)g;
     for (uint64_t q = 0; q < count; ++q) {
         Sample S;
@@ -560,8 +585,22 @@ int orc_samples(const void* g, int opt, uint64_t seed, uint64_t i0, uint64_t cou
         len[q] = (uint32_t)S.path.size();
         if (S.path.size() > cap) return E_INVAL;
         for (size_t p = 0; p < S.path.size(); ++p) paths[q * cap + p] = S.path[p];
+        if (path_edges)
+            for (size_t p = 0; p < S.edges.size(); ++p) path_edges[q * cap + p] = S.edges[p];
     }
     return OK;
+}
+
+// Edge ids: for temporal edge id e, its (u, v, t) and its underlying edge id;
+// *n_underlying = the number of underlying edges.
+void orc_edge_ids(const void* g, uint32_t* u, uint32_t* v, uint32_t* t, uint32_t* uedge, uint32_t* n_underlying) {
+    const Graph* G = (const Graph*)g;
+    for (const auto& kv : G->tid) {
+        const uint32_t e = kv.second;
+        v[e] = std::get<0>(kv.first); t[e] = std::get<1>(kv.first); u[e] = std::get<2>(kv.first);
+        uedge[e] = G->t2u[e];
+    }
+    *n_underlying = (uint32_t)G->uid.size();
 }
 
 double orc_sd_bound(double Rc, double W, double vhat, double delta, double r, double c) {
@@ -577,47 +616,63 @@ double orc_omega_bound(double vhat, double rho, double eps, double delta) {
 }
 
 // Algorithm 1 (MANTRA).  fixed_r > 0 runs exactly fixed_r samples with no
-// bootstrap and no stopping test.  Outputs est[v] = hits[v] / r.
+// bootstrap and no stopping test.  Outputs est[x] = hits[x] / r.
 // vhat_mode 0: vhat = W in xi (as Algorithm 1 passes it); 1: vhat = the
 // variance bound above, delta_i split evenly between it and xi.
+// target 0: the functions are the nodes (f_v = 1 when v is an internal node
+// of the drawn path); 1: the underlying edges, 2: the temporal edges (App. A;
+// f_e = 1 when the drawn path uses e, first and last edge included), indexed
+// by the ids of the Graph.
 int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed, uint32_t c, double growth,
-                 uint64_t fixed_r, uint64_t bootstrap, int delta_sched, int vhat_mode, double* est,
+                 uint64_t fixed_r, uint64_t bootstrap, int delta_sched, int vhat_mode, int target, double* est,
                  uint64_t* hits_out, orc_info* info) {
     const Graph* G = (const Graph*)g;
     const uint32_t n = G->n;
     if (n < 2 || !(eps > 0 && eps < 1) || !(delta > 0 && delta < 1) || c < 1 || c > 128) return E_INVAL;
-    std::vector<uint64_t> hits(n, 0);
-    std::vector<std::vector<int64_t>> S(c, std::vector<int64_t>(n, 0));     // S[j][v] = sum_i lambda_{j,i} f_v(s_i)
+    if (target < 0 || target > 2) return E_INVAL;
+    const uint32_t F = target == 0 ? n : (uint32_t)(target == 1 ? G->uid.size() : G->tid.size());
+    std::vector<uint64_t> hits(F, 0);
+    std::vector<std::vector<int64_t>> S(c, std::vector<int64_t>(F, 0));     // S[j][x] = sum_i lambda_{j,i} f_x(s_i)
     uint64_t sum_int = 0;
     orc_info I;
     std::memset(&I, 0, sizeof(I));
 
+    // The functions of the family that are 1 on a sample.
+    auto items_of = [&](const Sample& sm, std::vector<uint32_t>* it) {
+        it->clear();
+        if (target == 0) {
+            for (size_t p = 1; p + 1 < sm.path.size(); ++p) it->push_back(sm.path[p]);
+        } else {
+            for (uint32_t e : sm.edges) it->push_back(target == 1 ? G->t2u[e] : e);
+        }
+    };
     // Update step for samples [a, b): hits and Rademacher sums (Algorithm 1).
     auto run = [&](uint64_t a, uint64_t b) -> int {
+        std::vector<uint32_t> it;
         for (uint64_t i = a; i < b; ++i) {
             Sample sm;
             int st = one_sample(*G, opt, seed, i, D_PAIR, D_PATH, &sm);
             if (st != OK) return st;
-            if (sm.path.size() < 3) continue;
-            for (size_t p = 1; p + 1 < sm.path.size(); ++p) {
-                uint32_t v = sm.path[p];
-                hits[v] += 1;
+            items_of(sm, &it);
+            for (uint32_t x : it) {
+                hits[x] += 1;
                 sum_int += 1;
-                for (uint32_t j = 0; j < c; ++j) S[j][v] += rademacher(seed, i, j);
+                for (uint32_t j = 0; j < c; ++j) S[j][x] += rademacher(seed, i, j);
             }
         }
         return OK;
     };
-    // N_R = sum_j max_v S[j][v] (sup over all nodes, no absolute value), H = max_v hits[v].
+    // N_R = sum_j max_x S[j][x] (sup over the whole family, no absolute value),
+    // H = max_x hits[x]; both 0 for an empty family.
     auto reduce = [&](int64_t* NR, uint64_t* H) {
         int64_t tot = 0;
-        for (uint32_t j = 0; j < c; ++j) {
+        for (uint32_t j = 0; j < c && F > 0; ++j) {
             int64_t mx = S[j][0];
-            for (uint32_t v = 1; v < n; ++v) mx = std::max(mx, S[j][v]);
+            for (uint32_t x = 1; x < F; ++x) mx = std::max(mx, S[j][x]);
             tot += mx;
         }
         uint64_t h = 0;
-        for (uint32_t v = 0; v < n; ++v) h = std::max(h, hits[v]);
+        for (uint32_t x = 0; x < F; ++x) h = std::max(h, hits[x]);
         *NR = tot; *H = h;
     };
     auto vhat_of = [&](uint64_t H, uint64_t r, uint64_t round) {
@@ -647,16 +702,18 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
         // Bootstrap (DrawSufficientSampleSize with delta/2): s' samples from
         // their own streams, not part of S.
         uint64_t sb = bootstrap ? bootstrap : (uint64_t)std::ceil(std::log(1.0 / delta) / eps);
-        std::vector<uint64_t> hb(n, 0);
+        std::vector<uint64_t> hb(F, 0);
         uint64_t sum_b = 0;
+        std::vector<uint32_t> it;
         for (uint64_t i = 0; i < sb; ++i) {
             Sample sm;
             int st = one_sample(*G, opt, seed, i, D_BOOT_PAIR, D_BOOT_PATH, &sm);
             if (st != OK) return st;
-            for (size_t p = 1; p + 1 < sm.path.size(); ++p) { hb[sm.path[p]] += 1; sum_b += 1; }
+            items_of(sm, &it);
+            for (uint32_t x : it) { hb[x] += 1; sum_b += 1; }
         }
         uint64_t Hb = 0;
-        for (uint32_t v = 0; v < n; ++v) Hb = std::max(Hb, hb[v]);
+        for (uint32_t x = 0; x < F; ++x) Hb = std::max(Hb, hb[x]);
         double v0 = (double)Hb / (double)sb;
         double rho = (double)sum_b / (double)sb;
         if (v0 == 0.0 || rho == 0.0) { v0 = 1.0 / (double)sb; rho = std::max(rho, v0); }
@@ -696,9 +753,9 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
     }
     I.r = r;
     I.sum_int_len = sum_int;
-    for (uint32_t v = 0; v < n; ++v) {
-        est[v] = (double)hits[v] / (double)r;
-        if (hits_out) hits_out[v] = hits[v];
+    for (uint32_t x = 0; x < F; ++x) {
+        est[x] = (double)hits[x] / (double)r;
+        if (hits_out) hits_out[x] = hits[x];
     }
     if (info) *info = I;
     return OK;

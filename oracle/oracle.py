@@ -64,7 +64,8 @@ def lib():
         L.orc_unrank.argtypes = [C.c_void_p, C.c_int, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64,
                                  u32p, C.POINTER(C.c_int64), C.c_uint32, u32p]
         L.orc_samples.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32,
-                                  C.c_uint32, u32p, u32p, u64p, u64p, u32p, u32p, C.c_uint32]
+                                  C.c_uint32, u32p, u32p, u64p, u64p, u32p, u32p, C.c_uint32, u32p]
+        L.orc_edge_ids.argtypes = [C.c_void_p, u32p, u32p, u32p, u32p, u32p]
         L.orc_sd_bound.restype = C.c_double
         L.orc_sd_bound.argtypes = [C.c_double] * 6
         L.orc_xi_from_R.restype = C.c_double
@@ -72,7 +73,8 @@ def lib():
         L.orc_omega_bound.restype = C.c_double
         L.orc_omega_bound.argtypes = [C.c_double] * 4
         L.orc_estimate.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_uint64, C.c_uint32,
-                                   C.c_double, C.c_uint64, C.c_uint64, C.c_int, C.c_int, dp, u64p, C.POINTER(Info)]
+                                   C.c_double, C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.c_int, dp, u64p,
+                                   C.POINTER(Info)]
         L.orc_wimpy_variance_bound.argtypes = [C.c_double, C.c_double, C.c_double]
         L.orc_wimpy_variance_bound.restype = C.c_double
         L.orc_stats.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64, C.c_int, u64p, u32p]
@@ -179,27 +181,45 @@ class Graph:
             return path, [int(q) for q in tim[:ln.value]]
         return path
 
-    def samples(self, opt, seed, i0, count, dom_pair=D_PAIR, dom_path=D_PATH, cap=None):
-        """Per-sample (s, z, sigma, path) for sample indices i0..i0+count-1."""
+    def samples(self, opt, seed, i0, count, dom_pair=D_PAIR, dom_path=D_PATH, cap=None, edges=False):
+        """Per-sample (s, z, sigma, path) for sample indices i0..i0+count-1;
+        with edges=True a fifth entry, the path's temporal edge ids."""
         cap = cap or min(self.n + 1, 4096)
         s = np.zeros(count, np.uint32); z = np.zeros(count, np.uint32)
         lo = np.zeros(count, np.uint64); hi = np.zeros(count, np.uint64)
         ln = np.zeros(count, np.uint32); paths = np.zeros(count * cap, np.uint32)
+        pe = np.zeros(count * cap, np.uint32) if edges else None
         _chk(lib().orc_samples(self.h, opt, seed, i0, count, dom_pair, dom_path, _p(s, C.c_uint32),
                                _p(z, C.c_uint32), _p(lo, C.c_uint64), _p(hi, C.c_uint64), _p(ln, C.c_uint32),
-                               _p(paths, C.c_uint32), cap))
+                               _p(paths, C.c_uint32), cap, _p(pe, C.c_uint32) if edges else None))
         out = []
         for q in range(count):
-            out.append((int(s[q]), int(z[q]), (int(hi[q]) << 64) | int(lo[q]),
-                        [int(x) for x in paths[q * cap:q * cap + ln[q]]]))
+            row = (int(s[q]), int(z[q]), (int(hi[q]) << 64) | int(lo[q]),
+                   [int(x) for x in paths[q * cap:q * cap + ln[q]]])
+            if edges:
+                row = row + ([int(x) for x in pe[q * cap:q * cap + max(int(ln[q]) - 1, 0)]],)
+            out.append(row)
         return out
 
-    def estimate(self, opt, eps, delta, seed, c=25, growth=1.2, fixed_r=0, bootstrap=0, delta_sched=0, vhat_mode=0):
-        est = np.zeros(self.n, np.float64)
-        hits = np.zeros(self.n, np.uint64)
+    def edge_ids(self):
+        """(u, v, t, underlying id) per temporal edge id, and the number of
+        underlying edges."""
+        u = np.zeros(self.m, np.uint32); v = np.zeros(self.m, np.uint32); t = np.zeros(self.m, np.uint32)
+        ue = np.zeros(self.m, np.uint32); nu = C.c_uint32()
+        lib().orc_edge_ids(self.h, _p(u, C.c_uint32), _p(v, C.c_uint32), _p(t, C.c_uint32), _p(ue, C.c_uint32),
+                           C.byref(nu))
+        return u, v, t, ue, nu.value
+
+    def estimate(self, opt, eps, delta, seed, c=25, growth=1.2, fixed_r=0, bootstrap=0, delta_sched=0, vhat_mode=0,
+                 target=0):
+        """Algorithm 1; target 0 nodes, 1 underlying edges, 2 temporal edges."""
+        F = self.n if target == 0 else (self.edge_ids()[4] if target == 1 else self.m)
+        est = np.zeros(max(F, 1), np.float64)
+        hits = np.zeros(max(F, 1), np.uint64)
         info = Info()
         _chk(lib().orc_estimate(self.h, opt, eps, delta, seed, c, growth, fixed_r, bootstrap, delta_sched, vhat_mode,
-                                _p(est, C.c_double), _p(hits, C.c_uint64), C.byref(info)))
+                                target, _p(est, C.c_double), _p(hits, C.c_uint64), C.byref(info)))
+        est, hits = est[:F], hits[:F]
         return est, hits, info.as_dict()
 
     def stats_counts(self, opt, seed, r_s, all_sources=False):

@@ -119,3 +119,36 @@ def distances(edges, n, opt):
             if lst:
                 d[(u, z)] = min(len(vs) - 1 for vs, _ in lst)
     return d
+
+
+def exact_edge_bc(edges, n, opt, temporal):
+    """Temporal edge betweenness (paper App. A), as Fractions: with
+    temporal=True, b_(u,v,t) for every temporal edge; otherwise b_(u,v) for
+    every underlying edge: 1/(n(n-1)) sum_{s != z} #(optimal walks using the
+    edge) / sigma_sz.  Every edge of a walk counts, the first and last too."""
+    acc = defaultdict(Fraction)
+    for s in range(n):
+        for z, d in optimal_sets(edges, n, s).items():
+            lst = d[opt]
+            if not lst:
+                continue
+            through = defaultdict(int)
+            for vs, ts in lst:
+                keys = {(vs[k], vs[k + 1], ts[k + 1]) if temporal else (vs[k], vs[k + 1]) for k in range(len(vs) - 1)}
+                for key in keys:
+                    through[key] += 1
+            for key, k in through.items():
+                acc[key] += Fraction(k, len(lst))
+    return {key: a / (n * (n - 1)) for key, a in acc.items()}
+
+
+def mean_edges(edges, n, opt):
+    """1/(n(n-1)) sum_{s != z} mean over optimal walks of the number of
+    distinct underlying edges they use (App. A's Psi)."""
+    acc = Fraction(0)
+    for s in range(n):
+        for z, d in optimal_sets(edges, n, s).items():
+            lst = d[opt]
+            if lst:
+                acc += Fraction(sum(len({(vs[k], vs[k + 1]) for k in range(len(vs) - 1)}) for vs, _ in lst), len(lst))
+    return acc / (n * (n - 1))

@@ -325,3 +325,68 @@ def test_wimpy_variance_bound_covers_the_variance():
         assert float((bare < p).mean()) > miss
     # W = 0: only the confidence terms remain, 2 ln(1/delta) / r
     assert O.wimpy_variance_bound(0.0, 0.1, 1000) == pytest.approx(2 * math.log(10) / 1000, rel=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Temporal edge betweenness (App. A): edge ids, the two lemmas, estimates.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(8))
+def test_edge_ids_follow_the_drawn_paths(seed):
+    u, v, t = synth.random_tiny(6, 16, t_hi=5, seed=3000 + seed)
+    g = O.Graph(u, v, t, n=6)
+    eu, ev, et, ue, nu = g.edge_ids()
+    # ids: temporal edges in (v, t, u) order, underlying edges in (v, u) order
+    assert sorted(zip(ev, et, eu)) == list(zip(ev, et, eu))
+    und = sorted({(int(b), int(a)) for a, b in zip(eu, ev)})
+    assert nu == len(und) and all(und[ue[e]] == (int(ev[e]), int(eu[e])) for e in range(g.m))
+    for opt in (0, 1, 2):
+        for (s, z, sig, path, pe) in g.samples(opt, 4, 0, 300, cap=8, edges=True):
+            assert len(pe) == max(len(path) - 1, 0)
+            ts = [int(et[e]) for e in pe]
+            assert all(int(eu[e]) == path[k] and int(ev[e]) == path[k + 1] for k, e in enumerate(pe))
+            assert all(a < b for a, b in zip(ts, ts[1:]))
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_edge_betweenness_lemmas_on_bruteforce(seed):
+    """App. A: b_e = sum_t b_(e,t) and sum_e b_e = Psi (mean edges of an
+    optimal path over all ordered pairs), exactly."""
+    u, v, t = synth.random_tiny(6, 14, t_hi=5, seed=4000 + seed)
+    edges = BF.dedupe(u, v, t)
+    for opt in (0, 1, 2):
+        bt = BF.exact_edge_bc(edges, 6, opt, temporal=True)
+        bu = BF.exact_edge_bc(edges, 6, opt, temporal=False)
+        agg = {}
+        for (a, b, _), x in bt.items():
+            agg[(a, b)] = agg.get((a, b), 0) + x
+        assert agg == bu
+        assert sum(bu.values()) == BF.mean_edges(edges, 6, opt)
+
+
+@pytest.mark.parametrize("target", [1, 2])
+def test_edge_estimates_within_hoeffding(target):
+    """Fixed-r estimates of edge betweenness against the brute-force values:
+    max error within Hoeffding's bound at delta = 1e-3 (one-sided union over
+    the family), and the hit totals equal the drawn paths' edge counts."""
+    u, v, t = synth.random_tiny(6, 14, t_hi=5, seed=4100)
+    edges = BF.dedupe(u, v, t)
+    g = O.Graph(u, v, t, n=6)
+    eu, ev, et, ue, nu = g.edge_ids()
+    r = 20000
+    for opt in (0, 2):
+        est, hits, info = g.estimate(opt, 0.05, 0.1, 3, fixed_r=r, target=target)
+        exact = BF.exact_edge_bc(edges, 6, opt, temporal=(target == 2))
+        F = len(est)
+        assert F == (g.m if target == 2 else nu)
+        want = np.zeros(F)
+        for e in range(g.m):
+            key = (int(eu[e]), int(ev[e]), int(et[e])) if target == 2 else (int(eu[e]), int(ev[e]))
+            want[e if target == 2 else ue[e]] = float(exact.get(key, 0))
+        bound = math.sqrt(math.log(2 * F / 1e-3) / (2 * r))
+        assert np.abs(est - want).max() <= bound
+        rows = g.samples(opt, 3, 0, r, cap=8)
+        assert hits.sum() == info["sum_int_len"] == sum(max(len(p) - 1, 0) for (_, _, _, p) in rows)
+    # underlying hits are the temporal hits summed per underlying edge
+    _, ht, _ = g.estimate(2, 0.05, 0.1, 5, fixed_r=3000, target=2)
+    _, hu, _ = g.estimate(2, 0.05, 0.1, 5, fixed_r=3000, target=1)
+    assert np.array_equal(np.bincount(ue, weights=ht, minlength=nu).astype(np.uint64), hu)
