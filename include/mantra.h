@@ -65,6 +65,12 @@ typedef struct {
                             passes it); 1: the appendix's variance bound from W,
                             W + L/r + sqrt((L/r)^2 + 2 W L / r) with L = ln(2/delta_i), the round's
                             delta_i split evenly between it and xi */
+    int target;          /* what is estimated (paper App. A): 0 = temporal betweenness of the n
+                            nodes (Sec. 3); 1 = of the underlying edges (u,v), one entry per
+                            distinct ordered pair with a temporal edge, id = rank in (v,u) order;
+                            2 = of the m temporal edges, id = rank in (v,t,u) order.  An edge
+                            counts once for every sampled path that traverses it, first and last
+                            edge included.  Ids: mantra_graph_edges. */
 } mantra_opts;
 
 /* Diagnostics of one mantra_estimate call. */
@@ -115,12 +121,24 @@ int mantra_graph_load(const uint32_t* u, const uint32_t* v, const uint32_t* t, u
 int mantra_graph_info(const mantra_graph* g, uint32_t* n, uint64_t* m_dedup, uint64_t* slots,
                       uint64_t* self_loops_dropped, uint64_t* duplicates_dropped);
 
+/* The edge ids of mantra_opts.target 1 and 2 (paper App. A).  Temporal edge
+ * e (0 <= e < m_dedup) is (u_out[e], v_out[e], t_out[e]); the m_dedup triples
+ * come in (v, t, u) order, so e is the triple's rank in that order.
+ * uedge_out[e] is the id of its underlying edge (u,v): the rank of (v,u) among
+ * the distinct ordered pairs, sorted by v then u; *n_underlying receives their
+ * number.  u_out, v_out, t_out, uedge_out: host arrays of m_dedup entries
+ * (may be NULL only when m_dedup = 0). */
+int mantra_graph_edges(const mantra_graph* g, uint32_t* u_out, uint32_t* v_out, uint32_t* t_out,
+                       uint32_t* uedge_out, uint32_t* n_underlying);
+
 void mantra_graph_free(mantra_graph* g);
 
 /* Algorithm 1 (MANTRA): progressive sampling of (s,z) pairs with the
  * temporal Riondato-Kornaropoulos estimator (App. C), c-MCERA stopping rule
  * (Theorem 1) and sample cap omega (Theorem 3's closed form).
- * est_out: n doubles, est_v = hits_v / r (IEEE division).  hits_out: n
+ * est_out: F doubles, est_x = hits_x / r (IEEE division), where F is the size
+ * of the estimated family (opts->target: n nodes, the underlying edges, or
+ * m_dedup temporal edges); nothing is written when F = 0.  hits_out: F
  * uint64 or NULL.  info: or NULL.  With opts->out_device = 1 both outputs are
  * device pointers.  Returns MANTRA_E_INVAL for eps/delta outside (0,1),
  * c outside [1,128], r >= 2^31. */
@@ -135,8 +153,8 @@ typedef struct {
     double eps, delta;
     uint64_t seed;
     const mantra_opts* opts;   /* NULL = defaults; stream is ignored */
-    double* est_out;           /* n entries (host, or device with opts->out_device) */
-    uint64_t* hits_out;        /* n entries or NULL */
+    double* est_out;           /* F entries (see mantra_estimate; host, or device with opts->out_device) */
+    uint64_t* hits_out;        /* F entries or NULL */
     mantra_info* info;         /* or NULL */
     int status;                /* out: this problem's status code */
 } mantra_problem;
@@ -165,10 +183,12 @@ int mantra_temporal_stats(const mantra_graph* g, mantra_opt opt, double eps, uin
  * accumulating, and return per sample: s, z, sigma_sz (two uint64 words per
  * sample: low, high), the number of vertices of the drawn path (0 when z is
  * unreachable) and the path's vertices s .. z (cap per sample; longer paths
- * are truncated in nodes but len is exact).  All outputs host arrays. */
+ * are truncated in nodes but len is exact).  edges_out (or NULL): cap per
+ * sample, the temporal-edge ids (mantra_graph_edges) of the path's len-1
+ * edges in order from s, truncated at cap.  All outputs host arrays. */
 int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, uint32_t dom_pair, uint32_t dom_path,
                         uint64_t i0, uint64_t count, uint32_t* s_out, uint32_t* z_out, uint64_t* sigma_out,
-                        uint32_t* len_out, uint32_t* nodes_out, uint32_t cap);
+                        uint32_t* len_out, uint32_t* nodes_out, uint32_t cap, uint32_t* edges_out);
 
 /* Allocation-free variant of mantra_sample_paths for MANTRA_SH and
  * MANTRA_SFM.  The paper has no counterpart.  It is for callers that cannot
@@ -188,7 +208,7 @@ int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, ui
  * clears what must start at zero.  Calls that overlap on the GPU (two streams,
  * two threads, two graphs) race on the array: serialise them.
  * Returns MANTRA_E_INVAL for pfm, for a graph whose search scratch does not
- * fit the fixed array (roughly 40 bytes per arrival slot plus 28 per node
+ * fit the fixed array (roughly 40 bytes per arrival slot plus 32 per node
  * for one CTA, plus 8 bytes per requested sample), and MANTRA_E_OVERFLOW
  * when a path count exceeds 64 bits (this variant has no 128-bit re-run). */
 int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt, uint64_t seed, uint32_t dom_pair,
@@ -199,7 +219,8 @@ int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt, uint64_t 
 /* ---- Serving (continuous batching over resident graphs) ----
  * A server owns a host thread that runs Algorithm 1 for many requests at
  * once.  Requests queue in arrival order and are admitted while their device
- * state (hits, Rademacher sums, estimates: about 16 + 4c bytes per node)
+ * state (hits, Rademacher sums, estimates: about 16 + 4c bytes per entry of
+ * the estimated family)
  * fits `hbm_budget` bytes (0 = half of free device memory) and fewer than
  * `max_active` (0 = 256) run; a request is always admitted when none is
  * running.  Each tick launches the pending samples of every running request
@@ -216,7 +237,8 @@ int mantra_server_submit(mantra_server* srv, const mantra_graph* g, mantra_opt o
                          uint64_t seed, const mantra_opts* opts, uint64_t* req_id);
 
 /* MANTRA_PENDING while the request runs or waits; otherwise the request's
- * status, with est_out (n doubles), hits_out (n, or NULL) and info (or NULL)
+ * status, with est_out (F doubles, F as in mantra_estimate), hits_out (F, or
+ * NULL) and info (or NULL)
  * filled when it is MANTRA_OK.  A finished request is retired by this call. */
 int mantra_server_poll(mantra_server* srv, uint64_t req_id, double* est_out, uint64_t* hits_out, mantra_info* info);
 

@@ -25,7 +25,7 @@
 using namespace mantra;
 
 struct mantra_graph {
-    uint32_t n = 0, A = 0, m = 0;
+    uint32_t n = 0, A = 0, m = 0, n_uedge = 0;
     uint64_t self_loops = 0, duplicates = 0;
     DevGraph dg{};
     void* dmem = nullptr;
@@ -104,6 +104,21 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
     for (uint32_t x = 0; x < n; ++x) slot_ptr[x + 1] += slot_ptr[x];
     G->A = A;
 
+    // underlying-edge ids (App. A): the distinct in-neighbours of each v in
+    // ascending order get consecutive ids, v by v -- the rank of (v, u)
+    std::vector<uint32_t> in_uedge(M), nb;
+    uint32_t n_uedge = 0;
+    for (uint32_t x = 0; x < n; ++x) {
+        const uint32_t e_lo = slot_in[slot_ptr[x]], e_hi = slot_in[slot_ptr[x + 1]];
+        nb.assign(in_u.begin() + e_lo, in_u.begin() + e_hi);
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        for (uint32_t e = e_lo; e < e_hi; ++e)
+            in_uedge[e] = n_uedge + (uint32_t)(std::lower_bound(nb.begin(), nb.end(), in_u[e]) - nb.begin());
+        n_uedge += (uint32_t)nb.size();
+    }
+    G->n_uedge = n_uedge;
+
     // out-CSR by (u, t, v)
     std::vector<HostEdge> eo(std::move(ein));
     std::sort(eo.begin(), eo.end(), [](const HostEdge& a, const HostEdge& b) {
@@ -140,7 +155,8 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
                   {&out_slot, &G->dg.out_slot}, {&slot_ptr, &G->dg.slot_ptr}, {&slot_t, &G->dg.slot_t},
                   {&slot_v, &G->dg.slot_v}, {&slot_in, &G->dg.slot_in}, {&in_u, &G->dg.in_u},
                   {&in_slot, &G->dg.in_slot}, {&st_u, &G->dg.st_u}, {&st_v, &G->dg.st_v},
-                  {&st_t, &G->dg.st_t}, {&tmax_in, &G->dg.tmax_in}, {&tmin_out, &G->dg.tmin_out}};
+                  {&st_t, &G->dg.st_t}, {&tmax_in, &G->dg.tmax_in}, {&tmin_out, &G->dg.tmin_out},
+                  {&in_uedge, &G->dg.in_uedge}};
     size_t total = 0;
     for (auto& a : arrs) total += al256((a.h->size() + 1) * 4);
     if (cudaMalloc(&G->dmem, total) != cudaSuccess) return MANTRA_E_NOMEM;
@@ -152,7 +168,7 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
         off += al256((a.h->size() + 1) * 4);
     }
     CU(cudaStreamSynchronize(st));
-    G->dg.n = n; G->dg.A = A; G->dg.m = M;
+    G->dg.n = n; G->dg.A = A; G->dg.m = M; G->dg.n_uedge = n_uedge;
     return MANTRA_OK;
 }
 
@@ -609,7 +625,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
         }
         else { tb[nb] = t; ub[nb + 1] = ub[nb] + it.job.count; ++nb; }
         if (it.reduce) {
-            ri[nr] = ReduceItem{it.job.S, it.job.hits, it.G->n, it.red_c, (long long*)(slot + SLOT_ROWMAX),
+            ri[nr] = ReduceItem{it.job.S, it.job.hits, it.job.fam, it.red_c, (long long*)(slot + SLOT_ROWMAX),
                                 (u64*)(slot + SLOT_HMAX)};
             rs[nr + 1] = rs[nr] + it.red_c + 1;
             ++nr;
@@ -741,6 +757,7 @@ struct Problem {
     double growth = 1.2;
     uint64_t fixed_r = 0, boot = 0;
     int dsched = 0, vhat_mode = 0;
+    int fam_target = 0;       // mantra_opts.target: 0 nodes, 1 underlying edges, 2 temporal edges
     double* est_out = nullptr;
     uint64_t* hits_out = nullptr;
     bool out_device = false;
@@ -767,13 +784,17 @@ struct Problem {
         if (fixed_r > RMAX) return MANTRA_E_INVAL;
         if (out_device && !est_out) return MANTRA_E_INVAL;
         if (vhat_mode != 0 && vhat_mode != 1) return MANTRA_E_INVAL;
+        if (fam_target < 0 || fam_target > 2) return MANTRA_E_INVAL;
         return MANTRA_OK;
     }
 
+    // Size F of the estimated family (App. A for the edge families).
+    uint32_t family() const { return fam_target == 0 ? G->n : (fam_target == 1 ? G->n_uedge : G->m); }
+
     // bytes of device state held while the problem runs (admission footprint)
     size_t footprint() const {
-        const size_t n = G->n;
-        return al256(n * 8) * 2 + al256((size_t)c * n * 4) + al256(8 * 4096);
+        const size_t f = std::max<uint32_t>(family(), 1);
+        return al256(f * 8) * 2 + al256((size_t)c * f * 4) + al256(8 * 4096);
     }
 
     int grow_ovf(Engine& E, uint64_t need) {
@@ -790,8 +811,8 @@ struct Problem {
 
     int start(Engine& E) {
         t0 = now_s();
-        const size_t n = G->n;
-        b_hits = n * 8; b_S = (size_t)c * n * 4; b_est = n * 8;
+        const size_t f = std::max<uint32_t>(family(), 1);
+        b_hits = f * 8; b_S = (size_t)c * f * 4; b_est = f * 8;
         hits = (u64*)E.pool.get(b_hits);
         S = (int*)E.pool.get(b_S);
         est = out_device ? nullptr : (double*)E.pool.get(b_est);
@@ -819,6 +840,7 @@ struct Problem {
         Job& j = it->job;
         j = Job{};
         j.seed = seed; j.opt = opt; j.c = c; j.hits = hits;
+        j.target = fam_target; j.fam = family();
         const uint64_t left = remaining();
         j.i0 = pos; j.count = std::min(left, quota);
         if (phase == BOOT) {
@@ -897,14 +919,17 @@ struct Problem {
         I.r = r;
         I.sum_int_len = T.sum_int;
         double* dst = out_device ? est_out : est;
-        CU(launch_normalise(hits, G->n, r, dst, E.sa));
-        if (!out_device) CU(cudaMemcpyAsync(est_out, est, b_est, cudaMemcpyDeviceToHost, E.sa));
-        if (hits_out)
-            CU(cudaMemcpyAsync(hits_out, hits, b_hits, out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                               E.sa));
+        const uint32_t f = family();
+        if (f > 0) {
+            CU(launch_normalise(hits, f, r, dst, E.sa));
+            if (!out_device) CU(cudaMemcpyAsync(est_out, est, (size_t)f * 8, cudaMemcpyDeviceToHost, E.sa));
+            if (hits_out)
+                CU(cudaMemcpyAsync(hits_out, hits, (size_t)f * 8,
+                                   out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, E.sa));
+        }
         I.edges_scanned = T.escan; I.sigma_adds = T.eadd; I.states_new = T.snew; I.wide_samples = T.wide;
         I.kernel_ms = T.kernel_ms; I.search_launches = T.launches;
-        I.kernel_launches = T.launches + reduces + 1;
+        I.kernel_launches = T.launches + reduces + (f > 0 ? 1 : 0);
         I.alg_bytes = alg_bytes_of(opt == MANTRA_PFM, T.escan, T.eadd, T.snew, T.fseg);
         return MANTRA_OK;
     }
@@ -924,6 +949,7 @@ int problem_from(const mantra_graph* g, mantra_opt opt, double eps, double delta
     p->growth = o.growth > 0 ? o.growth : 1.2;
     p->fixed_r = o.fixed_r; p->boot = o.bootstrap; p->dsched = o.delta_sched;
     p->vhat_mode = o.vhat_mode;
+    p->fam_target = o.target;
     p->est_out = est_out; p->hits_out = hits_out; p->out_device = o.out_device != 0; p->info_out = info;
     return p->validate();
 }
@@ -1122,8 +1148,9 @@ int take_result(Server* S, std::map<uint64_t, Request*>::iterator it, double* es
     Request* r = it->second;
     const int st = r->p.status;
     if (st == MANTRA_OK) {
-        if (est_out) std::memcpy(est_out, r->est.data(), r->est.size() * 8);
-        if (hits_out) std::memcpy(hits_out, r->hits.data(), r->hits.size() * 8);
+        const size_t f = r->p.family();
+        if (est_out && f) std::memcpy(est_out, r->est.data(), f * 8);
+        if (hits_out && f) std::memcpy(hits_out, r->hits.data(), f * 8);
         if (info) *info = r->info;
     }
     S->reqs.erase(it);
@@ -1193,6 +1220,25 @@ int mantra_graph_info(const mantra_graph* g, uint32_t* n, uint64_t* m_dedup, uin
     if (slots) *slots = g->A;
     if (self_loops_dropped) *self_loops_dropped = g->self_loops;
     if (duplicates_dropped) *duplicates_dropped = g->duplicates;
+    return MANTRA_OK;
+}
+
+int mantra_graph_edges(const mantra_graph* g, uint32_t* u_out, uint32_t* v_out, uint32_t* t_out,
+                       uint32_t* uedge_out, uint32_t* n_underlying) {
+    if (!g || !n_underlying) return MANTRA_E_INVAL;
+    *n_underlying = g->n_uedge;
+    const uint32_t M = g->m;
+    if (M == 0) return MANTRA_OK;
+    if (!u_out || !v_out || !t_out || !uedge_out) return MANTRA_E_INVAL;
+    std::vector<uint32_t> slot_v, slot_t, in_slot;
+    try { slot_v.resize(g->A); slot_t.resize(g->A); in_slot.resize(M); } catch (...) { return MANTRA_E_NOMEM; }
+    if (cudaMemcpy(u_out, g->dg.in_u, (size_t)M * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(uedge_out, g->dg.in_uedge, (size_t)M * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(in_slot.data(), g->dg.in_slot, (size_t)M * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(slot_v.data(), g->dg.slot_v, (size_t)g->A * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(slot_t.data(), g->dg.slot_t, (size_t)g->A * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MANTRA_E_CUDA;
+    for (uint32_t e = 0; e < M; ++e) { v_out[e] = slot_v[in_slot[e]]; t_out[e] = slot_t[in_slot[e]]; }
     return MANTRA_OK;
 }
 
@@ -1322,7 +1368,7 @@ int mantra_temporal_stats(const mantra_graph* g, mantra_opt opt, double eps, uin
 
 int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, uint32_t dom_pair, uint32_t dom_path,
                         uint64_t i0, uint64_t count, uint32_t* s_out, uint32_t* z_out, uint64_t* sigma_out,
-                        uint32_t* len_out, uint32_t* nodes_out, uint32_t cap) {
+                        uint32_t* len_out, uint32_t* nodes_out, uint32_t cap, uint32_t* edges_out) {
     if (!g || !s_out || !z_out || !sigma_out || !len_out || (cap > 0 && !nodes_out)) return MANTRA_E_INVAL;
     if (opt != MANTRA_SH && opt != MANTRA_SFM && opt != MANTRA_PFM) return MANTRA_E_INVAL;
     if (dom_pair > 5 || dom_path > 5) return MANTRA_E_INVAL;
@@ -1332,7 +1378,7 @@ int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, ui
     if ((rc = current_engine(g, &E)) != MANTRA_OK) return rc;
     std::lock_guard<std::mutex> lock(E->mu);
     const size_t capn = std::max<uint32_t>(cap, 1);
-    const size_t bytes = al256(count * 4) * 3 + al256(count * 16) + al256(count * capn * 4) + al256(count * 8);
+    const size_t bytes = al256(count * 4) * 3 + al256(count * 16) + al256(count * capn * 4) * 2 + al256(count * 8);
     char* d = (char*)E->pool.get(bytes);
     if (!d) return MANTRA_E_NOMEM;
     std::vector<TickItem> items(1);
@@ -1345,6 +1391,7 @@ int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, ui
     j.rec_len = (uint32_t*)(d + o); o += al256(count * 4);
     j.rec_sig = (u64*)(d + o); o += al256(count * 16);
     j.rec_nodes = (uint32_t*)(d + o); o += al256(count * capn * 4);
+    j.rec_edges = edges_out ? (uint32_t*)(d + o) : nullptr; o += al256(count * capn * 4);
     j.ovf_list = (uint64_t*)(d + o);
     j.rec_cap = (uint32_t)capn;
     TickResult R;
@@ -1359,6 +1406,8 @@ int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, ui
         if (e == cudaSuccess) e = cudaMemcpyAsync(sigma_out, j.rec_sig, count * 16, cudaMemcpyDeviceToHost, E->sa);
         if (e == cudaSuccess && cap > 0)
             e = cudaMemcpyAsync(nodes_out, j.rec_nodes, count * (size_t)cap * 4, cudaMemcpyDeviceToHost, E->sa);
+        if (e == cudaSuccess && cap > 0 && edges_out)
+            e = cudaMemcpyAsync(edges_out, j.rec_edges, count * (size_t)cap * 4, cudaMemcpyDeviceToHost, E->sa);
         if (e == cudaSuccess) e = cudaStreamSynchronize(E->sa);
         if (e != cudaSuccess) rc = MANTRA_E_CUDA;
     }
@@ -1399,9 +1448,11 @@ int mantra_server_submit(mantra_server* srv, const mantra_graph* g, mantra_opt o
     if (opts && opts->out_device) return MANTRA_E_INVAL;     // served results are host arrays
     Request* r = new (std::nothrow) Request();
     if (!r) return MANTRA_E_NOMEM;
+    const int tgt = opts ? opts->target : 0;
+    const uint32_t fam = tgt == 1 ? g->n_uedge : (tgt == 2 ? g->m : g->n);
     try {
-        r->est.assign(g->n, 0.0);
-        r->hits.assign(g->n, 0);
+        r->est.assign(std::max<uint32_t>(fam, 1), 0.0);
+        r->hits.assign(std::max<uint32_t>(fam, 1), 0);
     } catch (...) {
         delete r;
         return MANTRA_E_NOMEM;

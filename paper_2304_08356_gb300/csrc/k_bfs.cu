@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
     uint32_t* seg_b = reinterpret_cast<uint32_t*>(region + ws.o_segb);
     uint32_t* seg_u = reinterpret_cast<uint32_t*>(region + ws.o_segu);
     uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path);
+    uint32_t* pathe = reinterpret_cast<uint32_t*>(region + ws.o_pathe);   // in-CSR index of path edge k
     uint32_t* VB = reinterpret_cast<uint32_t*>(region + ws.o_vb);   // vertex bitmap (stats)
     u64* segmap = reinterpret_cast<u64*>(region + ws.o_segmap);      // vertex -> (level stamp, frontier segment)
     uint32_t* stamp_p = reinterpret_cast<uint32_t*>(region + ws.o_stamp);
@@ -525,6 +526,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                             nxt = __shfl_sync(FULL, pick, l);
                             xs = shfl_idx_w(xr, l);
                             if (nxt == NONE) err = true;
+                            else if (lane == 0) pathe[lvl - 1] = e0 + l;
                             break;
                         }
                         xs -= shfl_idx_w(incl, 31);
@@ -536,6 +538,11 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 }
                 if (lane == 0) {
                     path[0] = s;
+                    if (!err) {   // the first edge: s's in-edge of the level-1 slot
+                        const uint32_t e = lower_bound_u32(g.in_u, g.slot_in[cur], g.slot_in[cur + 1], s);
+                        if (e < g.slot_in[cur + 1] && g.in_u[e] == s) pathe[0] = e;
+                        else err = true;
+                    }
                     if (err) { sh_err = 1; set_status(job.status, ST_CHECK); }
                     sh_d = d;
                     sh_len = d + 1;
@@ -556,17 +563,17 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
         } else if (!sh_err) {
             const bool drawn = found && sh_len > 0;
             // ---------------- hits and Rademacher sums ----------------
-            if (drawn && job.hits && sh_d >= 2) {
-                const uint32_t nint = sh_d - 1;
+            const uint32_t nint = drawn ? family_count(job, sh_len) : 0u;
+            if (job.hits && nint > 0) {
                 const uint32_t rows = 1 + (job.S ? job.c : 0);
                 for (uint32_t it = tid; it < nint * rows; it += BFS_NT) {
                     const uint32_t p = it % nint, j = it / nint;
-                    const uint32_t v = path[1 + p];
-                    if (j == 0) atomicAdd(job.hits + v, 1ull);
+                    const uint32_t x = family_item(job, g, path, pathe, p);
+                    if (j == 0) atomicAdd(job.hits + x, 1ull);
                     else {
                         const uint32_t jj = j - 1;
                         const int lam = ((sh_rade[jj >> 5] >> (jj & 31)) & 1u) ? 1 : -1;
-                        atomicAdd(job.S + (size_t)jj * n + v, lam);
+                        atomicAdd(job.S + (size_t)jj * job.fam + x, lam);
                     }
                 }
                 if (tid == 0) atomicAdd(job.ctr + C_SUMINT, (u64)nint);
@@ -582,6 +589,9 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 }
                 for (uint32_t p = tid; p < len && p < job.rec_cap; p += BFS_NT)
                     job.rec_nodes[r * job.rec_cap + p] = path[p];
+                if (job.rec_edges)
+                    for (uint32_t p = tid; p + 1 < len && p < job.rec_cap; p += BFS_NT)
+                        job.rec_edges[r * job.rec_cap + p] = pathe[p];
             }
         }
 
@@ -622,6 +632,7 @@ size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws) {
     ws->o_segb = o;    o = al(o + (size_t)(n + 2) * 4);
     ws->o_segu = o;    o = al(o + (size_t)(n + 2) * 4);
     ws->o_path = o;    o = al(o + (size_t)(n + 2) * 4);
+    ws->o_pathe = o;   o = al(o + (size_t)(n + 2) * 4);
     ws->o_vb = o;      o = al(o + (size_t)((n + 31) / 32 + 1) * 4);
     ws->o_segmap = o;  o = al(o + (size_t)n * 8);
     ws->o_stamp = o;   o = al(o + 4);

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(RED_NT) k_round_reduce(const ReduceItem* items
                 long long x = (lane < RED_NT / 32) ? red_i[lane] : (long long)INT_MIN;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
-                if (lane == 0) it.rowmax[j] = x;
+                if (lane == 0) it.rowmax[j] = it.n ? x : 0;     // an empty family: 0
             }
         } else {
             u64 mx = 0;

@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
     Sig* sig = reinterpret_cast<Sig*>(region + ws.o_sig) + lane;             // sig[v * 32]
     uint32_t* hop = reinterpret_cast<uint32_t*>(region + ws.o_hop) + lane;   // hop[v * 32]
     uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path) + (size_t)lane * (ws.n_cap + 2);
+    uint32_t* pathe = reinterpret_cast<uint32_t*>(region + ws.o_pathe) + (size_t)lane * (ws.n_cap + 2);
     uint32_t* list = reinterpret_cast<uint32_t*>(region + ws.o_list) + lane;     // list[p * 32]
     __shared__ __align__(16) Task sh_tasks[PFM_NT / 32];
     Task& T = sh_tasks[threadIdx.x >> 5];
@@ -285,22 +286,26 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
                 const uint32_t fv = fa[(size_t)v * 32];
                 const uint32_t a = lower_bound_u32(g.slot_t, g.slot_ptr[v], g.slot_ptr[v + 1], fv - 1u);
                 Sig cum = 0;
-                uint32_t nxt = NONE;
+                uint32_t nxt = NONE, ech = NONE;
                 for (uint32_t e = g.slot_in[a]; e < g.slot_in[a + 1]; ++e) {
                     const uint32_t w = g.in_u[e];
                     if (!(fa[(size_t)w * 32] < fv)) continue;
                     const Sig wt = sig[(size_t)w * 32];
-                    if (xs < cum + wt) { xs -= cum; nxt = w; break; }
+                    if (xs < cum + wt) { xs -= cum; nxt = w; ech = e; break; }
                     cum += wt;
                 }
                 if (nxt == NONE || cnt > n) { err = 1; break; }
                 v = nxt;
+                pathe[cnt - 1] = ech;
                 path[cnt++] = v;
             }
             if (err) set_status(job.status, ST_CHECK);
             else {
                 for (uint32_t p = 0; p < cnt / 2; ++p) {
                     const uint32_t tmp = path[p]; path[p] = path[cnt - 1 - p]; path[cnt - 1 - p] = tmp;
+                }
+                for (uint32_t p = 0; p < (cnt - 1) / 2; ++p) {
+                    const uint32_t tmp = pathe[p]; pathe[p] = pathe[cnt - 2 - p]; pathe[cnt - 2 - p] = tmp;
                 }
                 len = cnt;
             }
@@ -310,19 +315,20 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
             else push_overflow(job, i);
         }
         if (have && !ovf && !err) {
-            if (job.hits && len >= 3) {
+            const uint32_t nint = family_count(job, len);
+            if (job.hits && nint > 0) {
                 uint32_t w4[4];
                 philox_block(job.seed, i, DOM_RADE, 0, w4);
-                for (uint32_t p = 1; p + 1 < len; ++p) {
-                    const uint32_t v = path[p];
-                    atomicAdd(job.hits + v, 1ull);
+                for (uint32_t k = 0; k < nint; ++k) {
+                    const uint32_t x = family_item(job, g, path, pathe, k);
+                    atomicAdd(job.hits + x, 1ull);
                     if (job.S)
                         for (uint32_t jj = 0; jj < job.c; ++jj) {
                             const int lam = ((w4[jj >> 5] >> (jj & 31)) & 1u) ? 1 : -1;
-                            atomicAdd(job.S + (size_t)jj * n + v, lam);
+                            atomicAdd(job.S + (size_t)jj * job.fam + x, lam);
                         }
                 }
-                atomicAdd(job.ctr + C_SUMINT, (u64)(len - 2));
+                atomicAdd(job.ctr + C_SUMINT, (u64)nint);
             }
             if (job.rec_len) {
                 const uint64_t r = i - job.i0;
@@ -330,6 +336,8 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
                 job.rec_sig[2 * r] = (u64)sigma_sz; job.rec_sig[2 * r + 1] = (u64)(sigma_sz >> 64);
                 job.rec_len[r] = len;
                 for (uint32_t p = 0; p < len && p < job.rec_cap; ++p) job.rec_nodes[r * job.rec_cap + p] = path[p];
+                if (job.rec_edges)
+                    for (uint32_t p = 0; p + 1 < len && p < job.rec_cap; ++p) job.rec_edges[r * job.rec_cap + p] = pathe[p];
             }
         }
         __syncwarp();
@@ -346,6 +354,7 @@ size_t pfm_region_bytes(uint32_t n, uint32_t list_cap, PfmWs* ws) {
     ws->o_sig = o;  o = al(o + (size_t)n * 32 * 16);
     ws->o_hop = o;  o = al(o + (size_t)n * 32 * 4);
     ws->o_path = o; o = al(o + (size_t)32 * (n + 2) * 4);
+    ws->o_pathe = o; o = al(o + (size_t)32 * (n + 2) * 4);
     ws->o_list = o; o = al(o + (size_t)32 * list_cap * 4);
     return o;
 }

@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
     uint32_t* pend = reinterpret_cast<uint32_t*>(region + ws.o_pend);
     uint32_t* Fl = reinterpret_cast<uint32_t*>(region + ws.o_list);      // frontier vertices
     uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path);
+    uint32_t* pathe = reinterpret_cast<uint32_t*>(region + ws.o_pathe);   // in-CSR index of path edge k
 
     const uint32_t ntasks = *ntasks_p;
     u64* flush_ctr = nullptr;
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                 const uint32_t fv = __ldcg(fat + v);
                 const uint32_t a = ldv<FA_SMEM>(fsl + v);
                 const uint32_t e_lo = g.slot_in[a], e_hi = g.slot_in[a + 1];
-                uint32_t nxt = NONE;
+                uint32_t nxt = NONE, ech = NONE;
                 for (uint32_t e0 = e_lo; e0 < e_hi; e0 += 32) {
                     const uint32_t e = e0 + lane;
                     u64 wt = 0;
@@ -403,6 +404,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                     if (msk) {
                         const int l = __ffs(msk) - 1;
                         nxt = __shfl_sync(FULL, w, l);
+                        ech = e0 + l;
                         xs -= shfl_idx_w(incl - wt, l);
                         break;
                     }
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                 }
                 if (nxt == NONE || cnt > n) { err = true; break; }
                 v = nxt;
-                if (lane == 0) path[cnt] = v;
+                if (lane == 0) { path[cnt] = v; pathe[cnt - 1] = ech; }
                 ++cnt;
             }
             if (lane == 0) {
@@ -420,6 +422,9 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                 } else {
                     for (uint32_t p = 0; p < cnt / 2; ++p) {
                         const uint32_t tmp = path[p]; path[p] = path[cnt - 1 - p]; path[cnt - 1 - p] = tmp;
+                    }
+                    for (uint32_t p = 0; p < (cnt - 1) / 2; ++p) {
+                        const uint32_t tmp = pathe[p]; pathe[p] = pathe[cnt - 2 - p]; pathe[cnt - 2 - p] = tmp;
                     }
                     sh_len = cnt;
                     sh_sigma = tot;
@@ -435,18 +440,18 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
             if (tid == 0) push_overflow(job, i);
         } else if (!sh_err) {
             const uint32_t len = sh_len;
-            if (job.hits && len >= 3) {
-                const uint32_t nint = len - 2;
+            const uint32_t nint = family_count(job, len);
+            if (job.hits && nint > 0) {
                 const uint32_t rows = 1 + (job.S ? job.c : 0);
                 for (uint32_t it = tid; it < nint * rows; it += PC_NT) {
                     const uint32_t p = it % nint, jrow = it / nint;
-                    const uint32_t v = path[1 + p];
+                    const uint32_t x = family_item(job, g, path, pathe, p);
                     if (jrow == 0) {
-                        atomicAdd(job.hits + v, 1ull);
+                        atomicAdd(job.hits + x, 1ull);
                     } else {
                         const uint32_t jj = jrow - 1;
                         const int lam = ((sh_rade[jj >> 5] >> (jj & 31)) & 1u) ? 1 : -1;
-                        atomicAdd(job.S + (size_t)jj * n + v, lam);
+                        atomicAdd(job.S + (size_t)jj * job.fam + x, lam);
                     }
                 }
                 if (tid == 0) atomicAdd(job.ctr + C_SUMINT, (u64)nint);
@@ -460,6 +465,9 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                 }
                 for (uint32_t p = tid; p < len && p < job.rec_cap; p += PC_NT)
                     job.rec_nodes[r * job.rec_cap + p] = path[p];
+                if (job.rec_edges)
+                    for (uint32_t p = tid; p + 1 < len && p < job.rec_cap; p += PC_NT)
+                        job.rec_edges[r * job.rec_cap + p] = pathe[p];
             }
         }
         __syncthreads();
@@ -490,6 +498,7 @@ size_t pfm_cta_region_bytes(uint32_t n, bool fa_in_smem, PfmCtaWs* ws) {
     ws->o_pend = o;  o = al(o + (size_t)n * 4);
     ws->o_list = o;  o = al(o + (size_t)(n + 1) * 4);
     ws->o_path = o;  o = al(o + (size_t)(n + 2) * 4);
+    ws->o_pathe = o; o = al(o + (size_t)(n + 2) * 4);
     return o;
 }
 

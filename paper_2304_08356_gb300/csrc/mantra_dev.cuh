@@ -5,7 +5,9 @@
 //   slots    distinct arrival appearances (v, t) sorted by (v, t):
 //            slot_ptr[n+1], slot_t[A], slot_v[A], slot_in[A+1]
 //   in-CSR   by (v, t, u): in_u[m], in_slot[m]  (slot a's in-edges are
-//            in_u[slot_in[a] .. slot_in[a+1]), ascending u)
+//            in_u[slot_in[a] .. slot_in[a+1]), ascending u); the in-CSR index
+//            of an edge is its temporal-edge id, in_uedge[m] the id of its
+//            underlying edge (u, v) (rank of (v, u) among the distinct pairs)
 //   stream   by (t, u, v): st_u[m], st_v[m], st_t[m]
 //   tmax_in[n]  latest in-edge time of v (valid when v has a slot)
 //   tmin_out[n] earliest out-edge time of u (valid when u has out-edges)
@@ -54,6 +56,9 @@ struct DevGraph {
     uint32_t cbound;  // sum over v of the largest in-edge count of v's slots: bounds the
                       // path-count additions of one prefix-foremost search
     uint32_t max_slot_in;   // largest in-edge count of one arrival slot
+    const uint32_t* in_uedge;
+    uint32_t n_uedge;       // distinct ordered pairs (u, v) with a temporal edge
+    uint32_t pad_;
 };
 
 // One launch over a range (or list) of sample indices.
@@ -65,8 +70,10 @@ struct Job {
     uint32_t dom_pair, dom_path;
     int opt;                   // 0 sh, 1 sfm, 2 pfm
     uint32_t c;                // Rademacher trials (S updated when S != nullptr)
-    u64* hits;                 // n, or nullptr: no accumulation
-    int* S;                    // c*n, row j at S + j*n, or nullptr
+    int target;                // estimated family: 0 nodes, 1 underlying edges, 2 temporal edges
+    uint32_t fam;              // its size F (n, n_uedge or m)
+    u64* hits;                 // F, or nullptr: no accumulation
+    int* S;                    // c*F, row j at S + j*F, or nullptr
     u64* ctr;                  // C_NCOUNT counters
     uint64_t* ovf_list;        // sample indices whose 64-bit path counts overflowed
     int* status;
@@ -76,6 +83,7 @@ struct Job {
     u64* rec_sig;              // 2 per sample: low, high 64 bits of sigma_sz
     uint32_t* rec_len;         // number of path vertices (0 if unreachable)
     uint32_t* rec_nodes;       // rec_cap per sample, s .. z
+    uint32_t* rec_edges;       // optional: rec_cap per sample, the path's temporal-edge ids from s
     uint32_t rec_cap;
     // Algorithm 2 mode: full searches from sources, reach histogram per hop
     int stats;
@@ -460,12 +468,27 @@ __device__ __forceinline__ void push_overflow(const Job& job, uint64_t i) {
     else set_status(job.status, ST_CHECK);
 }
 
+// Entries of the estimated family that a drawn path of len vertices adds one
+// hit to: its len-2 internal vertices (Sec. 3) or its len-1 edges (App. A).
+__device__ __forceinline__ uint32_t family_count(const Job& job, uint32_t len) {
+    if (len < 2) return 0;
+    return job.target == 0 ? len - 2 : len - 1;
+}
+
+// The k-th of them; path holds the vertices s .. z, pe the in-CSR indices of
+// the edges (path[k] -> path[k+1]).
+__device__ __forceinline__ uint32_t family_item(const Job& job, const DevGraph& g, const uint32_t* path,
+                                                const uint32_t* pe, uint32_t k) {
+    if (job.target == 0) return path[1 + k];
+    return job.target == 2 ? pe[k] : g.in_uedge[pe[k]];
+}
+
 
 // Per-CTA scratch of the sh/sfm search kernel (one region per CTA).
 struct BfsWs {
     char* base;          // CTA b uses base + b * stride
     size_t stride;
-    size_t o_sig, o_fc, o_f, o_ft, o_lev, o_segb, o_segu, o_path, o_bits, o_vb, o_segmap, o_stamp, o_nbits;
+    size_t o_sig, o_fc, o_f, o_ft, o_lev, o_segb, o_segu, o_path, o_pathe, o_bits, o_vb, o_segmap, o_stamp, o_nbits;
     int bits_in_smem;    // visited bitmap in dynamic shared memory (the next-level bitmap is in the region)
     uint32_t bits_words; // capacity of each bitmap (words): ceil(A_max / 32)
     uint32_t n_cap;      // node capacity of a region
@@ -476,7 +499,7 @@ struct BfsWs {
 struct PfmWs {
     char* base;          // warp w uses base + w * stride
     size_t stride;
-    size_t o_fa, o_sig, o_hop, o_path, o_list;
+    size_t o_fa, o_sig, o_hop, o_path, o_pathe, o_list;
     uint32_t n_cap;      // node capacity of a region (largest graph of the launch)
     uint32_t list_cap;   // contributing-edge entries per lane (deferred path counts)
 };
@@ -485,7 +508,7 @@ struct PfmWs {
 struct PfmCtaWs {
     char* base;          // CTA b uses base + b * stride
     size_t stride;
-    size_t o_fa, o_bits, o_exp, o_fat, o_sig, o_hop, o_pend, o_list, o_path;
+    size_t o_fa, o_bits, o_exp, o_fat, o_sig, o_hop, o_pend, o_list, o_path, o_pathe;
     uint32_t n_cap;      // node capacity of a region
     uint32_t bits_words; // words of each bitmap: ceil(n_cap / 32)
     int fa_in_smem;      // arrival slots and bitmaps in dynamic shared memory
@@ -517,7 +540,7 @@ cudaError_t launch_pfm_cta(const Task* tasks, const uint64_t* unit_start, const 
 struct ReduceItem {
     const int* S;        // c rows of n (unused when c = 0)
     const u64* hits;     // n
-    uint32_t n, c;
+    uint32_t n, c;       // n: the family size (0: every maximum is 0)
     long long* rowmax;   // c results: max_v S[j][v]
     u64* hmax;           // max_v hits[v]
 };

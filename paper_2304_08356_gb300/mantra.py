@@ -30,7 +30,8 @@ class MantraError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("c", C.c_uint32), ("growth", C.c_double), ("fixed_r", C.c_uint64), ("bootstrap", C.c_uint64),
-                ("delta_sched", C.c_int), ("out_device", C.c_int), ("stream", C.c_void_p), ("vhat_mode", C.c_int)]
+                ("delta_sched", C.c_int), ("out_device", C.c_int), ("stream", C.c_void_p), ("vhat_mode", C.c_int),
+                ("target", C.c_int)]
 
 
 class Info(C.Structure):
@@ -59,7 +60,7 @@ class TStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["mantra_graph_load", "mantra_graph_info", "mantra_graph_free", "mantra_estimate", "mantra_estimate_batch",
+EXPORTS = ["mantra_graph_load", "mantra_graph_info", "mantra_graph_edges", "mantra_graph_free", "mantra_estimate", "mantra_estimate_batch",
            "mantra_temporal_stats", "mantra_sample_paths", "mantra_sample_paths_noalloc", "mantra_strerror",
            "mantra_server_create", "mantra_server_submit", "mantra_server_poll", "mantra_server_wait",
            "mantra_server_stats", "mantra_server_destroy"]
@@ -78,6 +79,7 @@ def lib():
     u32p, u64p, dp = C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.POINTER(C.c_double)
     L.mantra_graph_load.argtypes = [u32p, u32p, u32p, C.c_uint64, C.c_uint32, C.POINTER(C.c_void_p)]
     L.mantra_graph_info.argtypes = [C.c_void_p, u32p, u64p, u64p, u64p, u64p]
+    L.mantra_graph_edges.argtypes = [C.c_void_p, u32p, u32p, u32p, u32p, u32p]
     L.mantra_graph_free.argtypes = [C.c_void_p]
     L.mantra_graph_free.restype = None
     L.mantra_estimate.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_uint64, C.POINTER(Opts),
@@ -86,7 +88,7 @@ def lib():
     L.mantra_temporal_stats.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_uint64, C.c_double,
                                         C.POINTER(TStats), u64p, C.c_uint32]
     L.mantra_sample_paths.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
-                                      C.c_uint64, u32p, u32p, u64p, u32p, u32p, C.c_uint32]
+                                      C.c_uint64, u32p, u32p, u64p, u32p, u32p, C.c_uint32, u32p]
     L.mantra_sample_paths_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
                                               C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p, C.c_uint32, C.c_void_p]
@@ -136,6 +138,22 @@ class Graph:
         _chk(lib().mantra_graph_info(self.h, C.byref(nn), C.byref(m), C.byref(sl), C.byref(lp), C.byref(dp_)),
              "mantra_graph_info")
         self.n, self.m, self.slots, self.self_loops, self.duplicates = nn.value, m.value, sl.value, lp.value, dp_.value
+        self._edges = None
+
+    def edge_ids(self):
+        """mantra_graph_edges -> (u, v, t, underlying id) per temporal edge id,
+        and the number of underlying edges."""
+        if self._edges is None:
+            u = np.zeros(max(self.m, 1), np.uint32); v = np.zeros_like(u); t = np.zeros_like(u)
+            ue = np.zeros_like(u); nu = C.c_uint32()
+            _chk(lib().mantra_graph_edges(self.h, _p(u, C.c_uint32), _p(v, C.c_uint32), _p(t, C.c_uint32),
+                                          _p(ue, C.c_uint32), C.byref(nu)), "mantra_graph_edges")
+            self._edges = (u[:self.m], v[:self.m], t[:self.m], ue[:self.m], nu.value)
+        return self._edges
+
+    def family_size(self, target=0):
+        """Entries of an estimate: nodes (0), underlying edges (1) or temporal edges (2)."""
+        return self.n if target == 0 else (self.edge_ids()[4] if target == 1 else self.m)
 
     def free(self):
         if getattr(self, "h", None):
@@ -149,11 +167,12 @@ class Graph:
             pass
 
     def estimate(self, opt, eps, delta, seed, c=0, growth=0.0, fixed_r=0, bootstrap=0, delta_sched=0,
-                 est_out=None, hits_out=None, stream=None, vhat_mode=0):
+                 est_out=None, hits_out=None, stream=None, vhat_mode=0, target=0):
         """mantra_estimate.  With est_out / hits_out given as integers they are
         device pointers (out_device = 1); otherwise host numpy arrays are
-        returned.  Returns (est, hits, info dict)."""
-        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, stream, vhat_mode)
+        returned.  target: 0 nodes, 1 underlying edges, 2 temporal edges.
+        Returns (est, hits, info dict)."""
+        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, stream, vhat_mode, target)
         info = Info()
         if isinstance(est_out, int):
             o.out_device = 1
@@ -161,11 +180,12 @@ class Graph:
                                        C.c_void_p(hits_out) if hits_out else None, C.byref(info)),
                  "mantra_estimate")
             return None, None, info.as_dict()
-        est = np.zeros(self.n, np.float64)
-        hits = np.zeros(self.n, np.uint64)
+        F = self.family_size(target) if target in (0, 1, 2) else self.n
+        est = np.zeros(max(F, 1), np.float64)
+        hits = np.zeros(max(F, 1), np.uint64)
         _chk(lib().mantra_estimate(self.h, _opt(opt), eps, delta, seed, C.byref(o), est.ctypes.data,
                                    hits.ctypes.data, C.byref(info)), "mantra_estimate")
-        return est, hits, info.as_dict()
+        return est[:F], hits[:F], info.as_dict()
 
     def temporal_stats(self, opt, eps, seed, r_override=0, tau=0.9, reach_cap=None):
         """mantra_temporal_stats -> (stats dict, reach array)."""
@@ -177,27 +197,33 @@ class Graph:
         d = st.as_dict()
         return d, reach[:min(cap, d["d_lb"] + 1)].copy()
 
-    def sample_paths(self, opt, seed, i0, count, dom_pair=D_PAIR, dom_path=D_PATH, cap=None):
-        """mantra_sample_paths -> list of (s, z, sigma, path) per sample."""
+    def sample_paths(self, opt, seed, i0, count, dom_pair=D_PAIR, dom_path=D_PATH, cap=None, edges=False):
+        """mantra_sample_paths -> list of (s, z, sigma, path) per sample; with
+        edges=True a fifth entry, the path's temporal edge ids."""
         cap = cap if cap is not None else min(self.n + 1, 4096)
         s = np.zeros(count, np.uint32); z = np.zeros(count, np.uint32)
         sig = np.zeros(2 * count, np.uint64); ln = np.zeros(count, np.uint32)
         nodes = np.zeros(max(count * cap, 1), np.uint32)
+        pe = np.zeros(max(count * cap, 1), np.uint32) if edges else None
         _chk(lib().mantra_sample_paths(self.h, _opt(opt), seed, dom_pair, dom_path, i0, count,
                                        _p(s, C.c_uint32), _p(z, C.c_uint32), _p(sig, C.c_uint64),
-                                       _p(ln, C.c_uint32), _p(nodes, C.c_uint32), cap), "mantra_sample_paths")
+                                       _p(ln, C.c_uint32), _p(nodes, C.c_uint32), cap,
+                                       _p(pe, C.c_uint32) if edges else None), "mantra_sample_paths")
         out = []
         for q in range(count):
             L = int(ln[q])
-            out.append((int(s[q]), int(z[q]), (int(sig[2 * q + 1]) << 64) | int(sig[2 * q]),
-                        [int(x) for x in nodes[q * cap:q * cap + min(L, cap)]]))
+            row = (int(s[q]), int(z[q]), (int(sig[2 * q + 1]) << 64) | int(sig[2 * q]),
+                   [int(x) for x in nodes[q * cap:q * cap + min(L, cap)]])
+            if edges:
+                row = row + ([int(x) for x in pe[q * cap:q * cap + min(max(L - 1, 0), cap)]],)
+            out.append(row)
         return out
 
 
 def estimate_batch(problems):
     """mantra_estimate_batch over a list of dicts with keys graph (Graph), opt,
-    eps, delta, seed and optional c, growth, fixed_r, bootstrap, delta_sched.
-    Returns a list of (est, hits, info dict, status)."""
+    eps, delta, seed and optional c, growth, fixed_r, bootstrap, delta_sched,
+    vhat_mode, target.  Returns a list of (est, hits, info dict, status)."""
     k = len(problems)
     arr = (Problem * k)()
     keep = []
@@ -205,9 +231,10 @@ def estimate_batch(problems):
     for x, p in enumerate(problems):
         g = p["graph"]
         o = Opts(p.get("c", 0), p.get("growth", 0.0), p.get("fixed_r", 0), p.get("bootstrap", 0),
-                 p.get("delta_sched", 0), 0, None, p.get("vhat_mode", 0))
-        est = np.zeros(g.n, np.float64)
-        hits = np.zeros(g.n, np.uint64)
+                 p.get("delta_sched", 0), 0, None, p.get("vhat_mode", 0), p.get("target", 0))
+        F = g.family_size(p.get("target", 0))
+        est = np.zeros(max(F, 1), np.float64)
+        hits = np.zeros(max(F, 1), np.uint64)
         info = Info()
         keep += [o, est, hits, info]
         arr[x].graph = g.h.value if isinstance(g.h, C.c_void_p) else g.h
@@ -219,7 +246,7 @@ def estimate_batch(problems):
         arr[x].est_out = est.ctypes.data
         arr[x].hits_out = hits.ctypes.data
         arr[x].info = C.pointer(info)
-        outs.append((est, hits, info))
+        outs.append((est[:F], hits[:F], info))
     lib().mantra_estimate_batch(arr, k)
     return [(e, h, i.as_dict(), arr[x].status) for x, (e, h, i) in enumerate(outs)]
 
@@ -237,12 +264,12 @@ class Server:
         self._n = {}
 
     def submit(self, graph, opt, eps, delta, seed, c=0, growth=0.0, fixed_r=0, bootstrap=0, delta_sched=0,
-               vhat_mode=0):
-        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, None, vhat_mode)
+               vhat_mode=0, target=0):
+        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, None, vhat_mode, target)
         rid = C.c_uint64()
         _chk(lib().mantra_server_submit(self.h, graph.h, _opt(opt), eps, delta, seed, C.byref(o), C.byref(rid)),
              "mantra_server_submit")
-        self._n[rid.value] = graph.n
+        self._n[rid.value] = graph.family_size(target)
         return rid.value
 
     def _result(self, rc, rid, est, hits, info):
@@ -254,15 +281,15 @@ class Server:
 
     def poll(self, rid):
         n = self._n[rid]
-        est = np.zeros(n, np.float64); hits = np.zeros(n, np.uint64); info = Info()
+        est = np.zeros(max(n, 1), np.float64); hits = np.zeros(max(n, 1), np.uint64); info = Info()
         rc = lib().mantra_server_poll(self.h, rid, est.ctypes.data, hits.ctypes.data, C.byref(info))
-        return self._result(rc, rid, est, hits, info)
+        return self._result(rc, rid, est[:n], hits[:n], info)
 
     def wait(self, rid, timeout=0.0):
         n = self._n[rid]
-        est = np.zeros(n, np.float64); hits = np.zeros(n, np.uint64); info = Info()
+        est = np.zeros(max(n, 1), np.float64); hits = np.zeros(max(n, 1), np.uint64); info = Info()
         rc = lib().mantra_server_wait(self.h, rid, timeout, est.ctypes.data, hits.ctypes.data, C.byref(info))
-        return self._result(rc, rid, est, hits, info)
+        return self._result(rc, rid, est[:n], hits[:n], info)
 
     def stats(self):
         v = [C.c_uint64() for _ in range(5)]
