@@ -18,6 +18,8 @@
 //   App. C, "temporal Riondato-Kornaropoulos" estimator and Theorem on the
 //                              path sampler -- backward path draw with
 //                              probability 1/sigma_sz.
+//   Sec. 4.1, the ob estimator -- f_v(s,z) = sigma_sz(v) / sigma_sz, carried
+//                              as fixed point with 32 fraction bits.
 //   App. D, Algorithm 2     -- reach counts per hop, D_LB, D_tau, zeta, Psi.
 //
 // Readings where the paper is silent or garbled (same list in the design
@@ -28,7 +30,9 @@
 // predecessor's appearances by ascending time); delta_i = delta/2^(i+1);
 // vhat = W, or (vhat_mode 1) the appendix's variance bound with its garbled
 // square-root term read as 2 W ln(1/delta)/r; natural logarithms; pfm
-// distance = minimum hops among pfm paths.
+// distance = minimum hops among pfm paths; ob values rounded to the nearest
+// multiple of 2^-32 (ties up), their squares for the wimpy variance rounded
+// the same way from the rounded value.
 //
 // Parity unpinned (no value printed in the paper; pinned only by special
 // cases, monotonicity, Theorem 1's guarantee and a coverage simulation): the
@@ -419,6 +423,99 @@ int one_sample(const Graph& G, int opt, uint64_t seed, uint64_t i, uint32_t dom_
     return OK;
 }
 
+// sigma_sz(v) for every v (Sec. 3): the number of (*)-optimal paths from s to
+// z with v as an internal node.  A path through an appearance a of v splits
+// into an optimal path s -> a (counted by the forward search) and an optimal
+// continuation a -> z; the continuations beta are counted backward from z's
+// endpoint appearances over the optimal-path DAG (Brandes-style).  A path
+// visits v at most once, so the products over v's appearances add up.
+// `through` gets n entries (0 for s, z and vertices on no optimal path).
+void through_counts(const Graph& G, int opt, uint32_t s, uint32_t z, const Search& R, std::vector<u128>* through) {
+    const uint32_t n = G.n;
+    through->assign(n, 0);
+    if (opt == OPT_PFM) {
+        // beta[v] = number of pfm continuations from v to z, over the DAG of
+        // edges (w,v,fa[v]) with fa[w] < fa[v], in decreasing fa.
+        if (R.fa[z] == POS_INF) return;
+        std::vector<u128> beta(n, 0);
+        beta[z] = 1;
+        std::vector<uint32_t> order;
+        for (uint32_t v = 0; v < n; ++v) if (R.fa[v] != POS_INF) order.push_back(v);
+        std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return R.fa[a] > R.fa[b]; });
+        for (uint32_t v : order) {
+            if (beta[v] == 0 || v == s) continue;
+            for (const auto& e : G.in[v])
+                if ((int64_t)e.second == R.fa[v] && R.fa[e.first] < R.fa[v]) beta[e.first] += beta[v];
+        }
+        for (uint32_t v = 0; v < n; ++v) if (v != s && v != z) (*through)[v] = R.sig[v] * beta[v];
+        return;
+    }
+    std::map<App, u128> beta;
+    for (const App& a : endpoints(R, z, opt)) beta[a] = 1;
+    for (uint32_t k = R.d; k >= 1; --k) {
+        for (auto& kv : R.st) {
+            if (kv.second.level != k) continue;
+            auto bi = beta.find(kv.first);
+            if (bi == beta.end() || bi->second == 0) continue;
+            for (const auto& e : G.in[kv.first.first]) {
+                if ((int64_t)e.second != kv.first.second) continue;
+                uint32_t w = e.first;
+                if (k - 1 == 0) {
+                    if (w == s) beta[App(s, NEG_INF)] += bi->second;
+                    continue;
+                }
+                for (auto it = R.st.lower_bound(App(w, NEG_INF)); it != R.st.end() && it->first.first == w; ++it)
+                    if (it->second.level == k - 1 && it->first.second < kv.first.second) beta[it->first] += bi->second;
+            }
+        }
+    }
+    for (auto& kv : beta) {
+        uint32_t v = kv.first.first;
+        if (v == s || v == z) continue;
+        (*through)[v] += R.st.at(kv.first).sigma * kv.second;
+    }
+}
+
+// a / b (0 <= a <= b, b >= 1) as a multiple of 2^-32, rounded to nearest with
+// ties up: the integer nearest to 2^32 a / b.  Binary long division of a * 2^32
+// by b, one quotient bit per step, then one more step decides the rounding;
+// the remainder is kept below b, so 2 * remainder fits in 129 bits (the
+// carry out of bit 127 is tracked).
+uint64_t fixed32(u128 a, u128 b) {
+    if (a >= b) return (uint64_t)1 << 32;
+    u128 rem = a;               // invariant: rem < b
+    uint64_t q = 0;
+    for (int bit = 0; bit < 33; ++bit) {
+        const bool carry = (rem >> 127) != 0;
+        rem <<= 1;              // true value: rem + carry * 2^128
+        const bool ge = carry || rem >= b;
+        if (ge) rem -= b;       // wraps back below b when carry is set
+        if (bit < 32) q = (q << 1) | (ge ? 1u : 0u);
+        else if (ge) q += 1;    // the 33rd bit: 2 * remainder >= b rounds up
+    }
+    return q;
+}
+
+// The ob functions of one sample (Sec. 4.1): q[v] = fixed32(sigma_sz(v), sigma_sz)
+// for the internal vertices v on some optimal path (all 0 when z is
+// unreachable).
+int ob_values(const Graph& G, int opt, uint64_t seed, uint64_t i, uint32_t dom_pair,
+              std::vector<std::pair<uint32_t, uint64_t>>* vals) {
+    vals->clear();
+    uint32_t s, z;
+    if (!draw_pair(G.n, seed, i, dom_pair, &s, &z)) return E_RNG;
+    Search R;
+    u128 sg;
+    int st = count_paths(G, opt, s, z, &R, &sg);
+    if (st != OK) return st;
+    if (sg == 0) return OK;
+    std::vector<u128> th;
+    through_counts(G, opt, s, z, R, &th);
+    for (uint32_t v = 0; v < G.n; ++v)
+        if (th[v] != 0) vals->push_back(std::make_pair(v, fixed32(th[v], sg)));
+    return OK;
+}
+
 // ---------------------------------------------------------------------------
 // Bounds (Sec. 3 Theorem 1; proof of Theorem 3).
 // ---------------------------------------------------------------------------
@@ -603,6 +700,26 @@ void orc_edge_ids(const void* g, uint32_t* u, uint32_t* v, uint32_t* t, uint32_t
     *n_underlying = (uint32_t)G->uid.size();
 }
 
+// sigma_sz(v) for all v (lo/hi 64-bit halves, n entries each); returns the
+// status, sigma_sz in *sig_lo / *sig_hi.
+int orc_through(const void* g, int opt, uint32_t s, uint32_t z, uint64_t* lo, uint64_t* hi, uint64_t* sig_lo,
+                uint64_t* sig_hi) {
+    const Graph* G = (const Graph*)g;
+    Search R;
+    u128 sg;
+    int st = count_paths(*G, opt, s, z, &R, &sg);
+    if (st != OK) return st;
+    *sig_lo = (uint64_t)sg; *sig_hi = (uint64_t)(sg >> 64);
+    std::vector<u128> th(G->n, 0);
+    if (sg != 0) through_counts(*G, opt, s, z, R, &th);
+    for (uint32_t v = 0; v < G->n; ++v) { lo[v] = (uint64_t)th[v]; hi[v] = (uint64_t)(th[v] >> 64); }
+    return OK;
+}
+
+uint64_t orc_fixed32(uint64_t a_lo, uint64_t a_hi, uint64_t b_lo, uint64_t b_hi) {
+    return fixed32(((u128)a_hi << 64) | a_lo, ((u128)b_hi << 64) | b_lo);
+}
+
 double orc_sd_bound(double Rc, double W, double vhat, double delta, double r, double c) {
     return sd_bound(Rc, W, vhat, delta, r, c);
 }
@@ -623,15 +740,27 @@ double orc_omega_bound(double vhat, double rho, double eps, double delta) {
 // of the drawn path); 1: the underlying edges, 2: the temporal edges (App. A;
 // f_e = 1 when the drawn path uses e, first and last edge included), indexed
 // by the ids of the Graph.
+// estimator 0: trk (App. C, the drawn path's hits); 1: ob (Sec. 4.1, nodes
+// only): f_v = sigma_sz(v) / sigma_sz as q = fixed32(.) in 2^-32 units, so
+// hits, S, N_R, the wimpy sums (of square32(q)) and sum_int_len are all in
+// 2^-32 units and est = hits / (r 2^32); no path is drawn.  ob needs c r < 2^31
+// (fixed_r, and omega) so that |N_R| fits int64; max_hits then reports the
+// largest wimpy sum.
 int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed, uint32_t c, double growth,
-                 uint64_t fixed_r, uint64_t bootstrap, int delta_sched, int vhat_mode, int target, double* est,
-                 uint64_t* hits_out, orc_info* info) {
+                 uint64_t fixed_r, uint64_t bootstrap, int delta_sched, int vhat_mode, int target, int estimator,
+                 double* est, uint64_t* hits_out, orc_info* info) {
     const Graph* G = (const Graph*)g;
     const uint32_t n = G->n;
     if (n < 2 || !(eps > 0 && eps < 1) || !(delta > 0 && delta < 1) || c < 1 || c > 128) return E_INVAL;
     if (target < 0 || target > 2) return E_INVAL;
+    if (estimator < 0 || estimator > 1 || (estimator == 1 && target != 0)) return E_INVAL;
+    const bool ob = estimator == 1;
+    // ob sums are in units of 2^-32; |N_R| <= c r 2^32 must fit int64
+    const double scale = ob ? 4294967296.0 : 1.0;
+    if (ob && (double)fixed_r * (double)c >= 2147483648.0) return E_INVAL;
     const uint32_t F = target == 0 ? n : (uint32_t)(target == 1 ? G->uid.size() : G->tid.size());
     std::vector<uint64_t> hits(F, 0);
+    std::vector<uint64_t> wsq(F, 0);                                        // ob: sum_i f_x(s_i)^2 (2^-32 units)
     std::vector<std::vector<int64_t>> S(c, std::vector<int64_t>(F, 0));     // S[j][x] = sum_i lambda_{j,i} f_x(s_i)
     uint64_t sum_int = 0;
     orc_info I;
@@ -646,10 +775,24 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
             for (uint32_t e : sm.edges) it->push_back(target == 1 ? G->t2u[e] : e);
         }
     };
+    // f^2 of an ob value q = 2^32 f, rounded back to 2^-32 units (ties up).
+    auto square32 = [](uint64_t q) { return (uint64_t)(((u128)q * q + ((u128)1 << 31)) >> 32); };
     // Update step for samples [a, b): hits and Rademacher sums (Algorithm 1).
     auto run = [&](uint64_t a, uint64_t b) -> int {
         std::vector<uint32_t> it;
+        std::vector<std::pair<uint32_t, uint64_t>> vals;
         for (uint64_t i = a; i < b; ++i) {
+            if (ob) {
+                int st = ob_values(*G, opt, seed, i, D_PAIR, &vals);
+                if (st != OK) return st;
+                for (const auto& vq : vals) {
+                    hits[vq.first] += vq.second;
+                    wsq[vq.first] += square32(vq.second);
+                    sum_int += vq.second;
+                    for (uint32_t j = 0; j < c; ++j) S[j][vq.first] += rademacher(seed, i, j) * (int64_t)vq.second;
+                }
+                continue;
+            }
             Sample sm;
             int st = one_sample(*G, opt, seed, i, D_PAIR, D_PATH, &sm);
             if (st != OK) return st;
@@ -672,17 +815,17 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
             tot += mx;
         }
         uint64_t h = 0;
-        for (uint32_t x = 0; x < F; ++x) h = std::max(h, hits[x]);
+        for (uint32_t x = 0; x < F; ++x) h = std::max(h, ob ? wsq[x] : hits[x]);   // trk: f^2 = f
         *NR = tot; *H = h;
     };
     auto vhat_of = [&](uint64_t H, uint64_t r, uint64_t round) {
-        double W = (double)H / (double)r;
+        double W = (double)H / ((double)r * scale);
         if (vhat_mode != 1) return W;
         return wimpy_variance_bound(W, delta_round(delta, round, delta_sched) / 2.0, (double)r);
     };
     auto xi_of = [&](int64_t NR, uint64_t H, uint64_t r, uint64_t round) {
-        double Rc = (double)NR / ((double)c * (double)r);
-        double W = (double)H / (double)r;
+        double Rc = (double)NR / ((double)c * (double)r * scale);
+        double W = (double)H / ((double)r * scale);
         double di = delta_round(delta, round, delta_sched);
         if (vhat_mode == 1) di /= 2.0;
         return sd_bound(Rc, W, vhat_of(H, r, round), di, (double)r, (double)c);
@@ -705,7 +848,14 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
         std::vector<uint64_t> hb(F, 0);
         uint64_t sum_b = 0;
         std::vector<uint32_t> it;
+        std::vector<std::pair<uint32_t, uint64_t>> vals;
         for (uint64_t i = 0; i < sb; ++i) {
+            if (ob) {                       // hb: sum of f^2 (the wimpy numerator), sum_b: sum of f
+                int st = ob_values(*G, opt, seed, i, D_BOOT_PAIR, &vals);
+                if (st != OK) return st;
+                for (const auto& vq : vals) { hb[vq.first] += square32(vq.second); sum_b += vq.second; }
+                continue;
+            }
             Sample sm;
             int st = one_sample(*G, opt, seed, i, D_BOOT_PAIR, D_BOOT_PATH, &sm);
             if (st != OK) return st;
@@ -714,11 +864,12 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
         }
         uint64_t Hb = 0;
         for (uint32_t x = 0; x < F; ++x) Hb = std::max(Hb, hb[x]);
-        double v0 = (double)Hb / (double)sb;
-        double rho = (double)sum_b / (double)sb;
+        double v0 = (double)Hb / ((double)sb * scale);
+        double rho = (double)sum_b / ((double)sb * scale);
         if (v0 == 0.0 || rho == 0.0) { v0 = 1.0 / (double)sb; rho = std::max(rho, v0); }
         uint64_t omega = (uint64_t)std::ceil(omega_bound(v0, rho, eps, delta / 2.0));
         if (omega < 1) omega = 1;
+        if (ob && (double)omega * (double)c >= 2147483648.0) return E_INVAL;
         // SamplingSchedule: least s in [s', omega] with xi(R = 0) <= eps.
         uint64_t s1;
         double d1 = delta_round(delta, 1, delta_sched);
@@ -754,7 +905,7 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
     I.r = r;
     I.sum_int_len = sum_int;
     for (uint32_t x = 0; x < F; ++x) {
-        est[x] = (double)hits[x] / (double)r;
+        est[x] = (double)hits[x] / ((double)r * scale);
         if (hits_out) hits_out[x] = hits[x];
     }
     if (info) *info = I;
@@ -799,10 +950,8 @@ int orc_stats(const void* g, int opt, uint64_t seed, uint64_t r_s, int all_sourc
 }
 
 // Exact (*)-temporal betweenness (Sec. 3): b_v = 1/(n(n-1)) sum_{s != v != z}
-// sigma_sz(v) / sigma_sz.  sigma_sz(v) = sum over appearances a of v of
-// (paths s->a) * (optimal continuations a->z); the continuation counts are
-// taken backward from z's endpoint appearances over the optimal-path DAG.
-// Long double accumulation.  Small graphs only.
+// sigma_sz(v) / sigma_sz, with sigma_sz(v) from through_counts.  Long double
+// accumulation.  Small graphs only.
 int orc_exact_bc(const void* g, int opt, double* bc) {
     const Graph* G = (const Graph*)g;
     const uint32_t n = G->n;
@@ -815,47 +964,8 @@ int orc_exact_bc(const void* g, int opt, double* bc) {
             int st = count_paths(*G, opt, s, z, &R, &sg);
             if (st != OK) return st;
             if (sg == 0) continue;
-            std::vector<u128> through(n, 0);
-            if (opt == OPT_PFM) {
-                // beta[v] = number of pfm continuations from v to z, over the
-                // DAG of edges (w,v,fa[v]) with fa[w] < fa[v], in decreasing fa.
-                std::vector<u128> beta(n, 0);
-                beta[z] = 1;
-                std::vector<uint32_t> order;
-                for (uint32_t v = 0; v < n; ++v) if (R.fa[v] != POS_INF) order.push_back(v);
-                std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return R.fa[a] > R.fa[b]; });
-                for (uint32_t v : order) {
-                    if (beta[v] == 0 || v == s) continue;
-                    for (const auto& e : G->in[v])
-                        if ((int64_t)e.second == R.fa[v] && R.fa[e.first] < R.fa[v]) beta[e.first] += beta[v];
-                }
-                for (uint32_t v = 0; v < n; ++v) if (v != s && v != z) through[v] = R.sig[v] * beta[v];
-            } else {
-                std::map<App, u128> beta;
-                for (const App& a : endpoints(R, z, opt)) beta[a] = 1;
-                for (uint32_t k = R.d; k >= 1; --k) {
-                    for (auto& kv : R.st) {
-                        if (kv.second.level != k) continue;
-                        auto bi = beta.find(kv.first);
-                        if (bi == beta.end() || bi->second == 0) continue;
-                        for (const auto& e : G->in[kv.first.first]) {
-                            if ((int64_t)e.second != kv.first.second) continue;
-                            uint32_t w = e.first;
-                            if (k - 1 == 0) {
-                                if (w == s) beta[App(s, NEG_INF)] += bi->second;
-                                continue;
-                            }
-                            for (auto it = R.st.lower_bound(App(w, NEG_INF)); it != R.st.end() && it->first.first == w; ++it)
-                                if (it->second.level == k - 1 && it->first.second < kv.first.second) beta[it->first] += bi->second;
-                        }
-                    }
-                }
-                for (auto& kv : beta) {
-                    uint32_t v = kv.first.first;
-                    if (v == s || v == z) continue;
-                    through[v] += R.st.at(kv.first).sigma * kv.second;
-                }
-            }
+            std::vector<u128> through;
+            through_counts(*G, opt, s, z, R, &through);
             for (uint32_t v = 0; v < n; ++v)
                 if (through[v]) acc[v] += (long double)through[v] / (long double)sg;
         }

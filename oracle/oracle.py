@@ -73,8 +73,11 @@ def lib():
         L.orc_omega_bound.restype = C.c_double
         L.orc_omega_bound.argtypes = [C.c_double] * 4
         L.orc_estimate.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_uint64, C.c_uint32,
-                                   C.c_double, C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.c_int, dp, u64p,
-                                   C.POINTER(Info)]
+                                   C.c_double, C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, dp,
+                                   u64p, C.POINTER(Info)]
+        L.orc_through.argtypes = [C.c_void_p, C.c_int, C.c_uint32, C.c_uint32, u64p, u64p, u64p, u64p]
+        L.orc_fixed32.argtypes = [C.c_uint64] * 4
+        L.orc_fixed32.restype = C.c_uint64
         L.orc_wimpy_variance_bound.argtypes = [C.c_double, C.c_double, C.c_double]
         L.orc_wimpy_variance_bound.restype = C.c_double
         L.orc_stats.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64, C.c_int, u64p, u32p]
@@ -211,16 +214,25 @@ class Graph:
         return u, v, t, ue, nu.value
 
     def estimate(self, opt, eps, delta, seed, c=25, growth=1.2, fixed_r=0, bootstrap=0, delta_sched=0, vhat_mode=0,
-                 target=0):
-        """Algorithm 1; target 0 nodes, 1 underlying edges, 2 temporal edges."""
+                 target=0, estimator=0):
+        """Algorithm 1; target 0 nodes, 1 underlying edges, 2 temporal edges;
+        estimator 0 trk (App. C), 1 ob (Sec. 4.1; hits in 2^-32 units)."""
         F = self.n if target == 0 else (self.edge_ids()[4] if target == 1 else self.m)
         est = np.zeros(max(F, 1), np.float64)
         hits = np.zeros(max(F, 1), np.uint64)
         info = Info()
         _chk(lib().orc_estimate(self.h, opt, eps, delta, seed, c, growth, fixed_r, bootstrap, delta_sched, vhat_mode,
-                                target, _p(est, C.c_double), _p(hits, C.c_uint64), C.byref(info)))
+                                target, estimator, _p(est, C.c_double), _p(hits, C.c_uint64), C.byref(info)))
         est, hits = est[:F], hits[:F]
         return est, hits, info.as_dict()
+
+    def through(self, opt, s, z):
+        """(sigma_sz, [sigma_sz(v) for v in range(n)]): optimal paths through v."""
+        lo = np.zeros(self.n, np.uint64); hi = np.zeros(self.n, np.uint64)
+        slo = C.c_uint64(); shi = C.c_uint64()
+        _chk(lib().orc_through(self.h, opt, s, z, _p(lo, C.c_uint64), _p(hi, C.c_uint64), C.byref(slo),
+                               C.byref(shi)))
+        return (shi.value << 64) | slo.value, [(int(b) << 64) | int(a) for a, b in zip(lo, hi)]
 
     def stats_counts(self, opt, seed, r_s, all_sources=False):
         """(reach[0..D_LB], D_LB): cumulative reach counts per hop (Algorithm 2)."""
@@ -257,3 +269,9 @@ def stats_summary(reach, d_lb, n, r_s, tau=0.9):
 def sample_size_bootstrap(eps, delta):
     """s' = ceil(ln(1/delta) / eps) (footnote of Sec. 4.4)."""
     return int(math.ceil(math.log(1.0 / delta) / eps))
+
+
+def fixed32(a: int, b: int) -> int:
+    """The oracle's ob rounding: the integer nearest 2^32 a / b (ties up), 0 <= a <= b < 2^128."""
+    M = (1 << 64) - 1
+    return lib().orc_fixed32(a & M, a >> 64, b & M, b >> 64)

@@ -390,3 +390,104 @@ def test_edge_estimates_within_hoeffding(target):
     _, ht, _ = g.estimate(2, 0.05, 0.1, 5, fixed_r=3000, target=2)
     _, hu, _ = g.estimate(2, 0.05, 0.1, 5, fixed_r=3000, target=1)
     assert np.array_equal(np.bincount(ue, weights=ht, minlength=nu).astype(np.uint64), hu)
+
+
+# --------------------------------------------------------------------------
+# The ob estimator (Sec. 4.1): f_v(s,z) = sigma_sz(v) / sigma_sz, carried as
+# the nearest multiple of 2^-32 (ties up).
+# --------------------------------------------------------------------------
+def _round32(a, b):
+    """Nearest integer to 2^32 a / b, ties up (Python integers)."""
+    return (2 * a * (1 << 32) + b) // (2 * b)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_through_counts_against_bruteforce(seed):
+    """sigma_sz(v) = the number of optimal walks from s to z with v internal,
+    counted on the explicit walk list; their sum over v is the total internal
+    length of the optimal walks (every pair, every optimality)."""
+    u, v, t = synth.random_tiny(6, 16, t_hi=5, seed=5000 + seed, self_loops=True)
+    edges = BF.dedupe(u, v, t)
+    g = O.Graph(u, v, t, n=6)
+    for s in range(6):
+        sets = BF.optimal_sets(edges, 6, s)
+        for z in range(6):
+            if z == s:
+                continue
+            for opt in (0, 1, 2):
+                walks = sets[z][opt] if z in sets else []
+                sig, th = g.through(opt, s, z)
+                assert sig == len(walks)
+                want = [0] * 6
+                for vs, _ in walks:
+                    for x in set(vs[1:-1]):
+                        want[x] += 1
+                assert th == want, (s, z, opt)
+                assert sum(th) == sum(len(vs) - 2 for vs, _ in walks)
+
+
+def test_fixed32_rounding():
+    rng = np.random.default_rng(11)
+    cases = [(0, 1), (1, 1), (1, 2), (1, 3), (2, 3), (1, 1 << 33), (3, 1 << 34), (1, (1 << 33) + 1),
+             ((1 << 64) - 1, (1 << 64) - 1), ((1 << 127), (1 << 128) - 1), ((1 << 128) - 2, (1 << 128) - 1),
+             (1, (1 << 128) - 1), ((1 << 96) + 12345, (1 << 97) + 1)]
+    for _ in range(3000):
+        bits = int(rng.integers(1, 129))
+        b = int(rng.integers(1, 1 << 62)) if bits <= 62 else (int(rng.integers(1, 1 << 62)) << (bits - 62)) | 1
+        b = min(b, (1 << 128) - 1)
+        a = b * int(rng.integers(0, 1 << 30)) // (1 << 30)
+        cases.append((a, b))
+    for a, b in cases:
+        assert O.fixed32(a, b) == _round32(a, b), (a, b)
+
+
+@pytest.mark.parametrize("opt", [0, 1, 2])
+def test_ob_sums_recounted(opt):
+    """A fixed-r ob run recounted from the per-pair through counts with
+    Python's own rounding: hits, the wimpy maximum, N_R and the total."""
+    u, v, t = synth.uniform_small(n=40, m=500, seed=3)
+    g = O.Graph(u, v, t, n=40)
+    r, c, seed = 300, 7, 9
+    est, hits, info = g.estimate(opt, 0.05, 0.1, seed, c=c, fixed_r=r, estimator=1)
+    H = np.zeros(40, dtype=object); W = np.zeros(40, dtype=object)
+    S = np.zeros((c, 40), dtype=object)
+    tot = 0
+    for i in range(r):
+        s, z = O.draw_pair(40, seed, i)
+        sig, th = g.through(opt, s, z)
+        for x in range(40):
+            if th[x]:
+                q = _round32(th[x], sig)
+                H[x] += q
+                W[x] += (q * q + (1 << 31)) >> 32
+                tot += q
+                for j in range(c):
+                    S[j, x] += O.rademacher(seed, i, j) * q
+    assert [int(x) for x in hits] == list(H)
+    assert info["max_hits"] == max(W) and info["sum_int_len"] == tot
+    assert info["rade_num"] == sum(max(S[j]) for j in range(c))
+    assert np.array_equal(est, np.array([float(h) for h in H]) / (r * 4294967296.0))
+
+
+@pytest.mark.parametrize("opt", [0, 2])
+def test_ob_estimates_within_hoeffding(opt):
+    """The ob estimate is unbiased for b_v: against brute-force exact values,
+    max error within Hoeffding's bound (f in [0,1]) at delta = 1e-3."""
+    u, v, t = synth.random_tiny(7, 22, t_hi=6, seed=4200)
+    edges = BF.dedupe(u, v, t)
+    g = O.Graph(u, v, t, n=7)
+    r = 20000
+    est, _, _ = g.estimate(opt, 0.05, 0.1, 2, fixed_r=r, estimator=1)
+    exact = np.array([float(x) for x in BF.exact_bc(edges, 7, opt)])
+    assert np.abs(est - exact).max() <= math.sqrt(math.log(2 * 7 / 1e-3) / (2 * r))
+
+
+def test_ob_progressive_and_invalid():
+    u, v, t = synth.uniform_small(n=60, m=900, seed=6)
+    g = O.Graph(u, v, t, n=60)
+    est, hits, info = g.estimate(0, 0.05, 0.1, 4, estimator=1)
+    assert info["rounds"] >= 1 and info["r"] >= info["s1"] and (info["xi"] <= 0.05 or info["r"] >= info["omega"])
+    assert 0.0 <= est.min() and est.max() <= 1.0
+    for kw in (dict(target=1), dict(target=2), dict(fixed_r=1 << 30, c=2)):
+        with pytest.raises(O.OracleError):
+            g.estimate(0, 0.05, 0.1, 4, estimator=1, **kw)
