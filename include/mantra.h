@@ -71,6 +71,14 @@ typedef struct {
                             2 = of the m temporal edges, id = rank in (v,t,u) order.  An edge
                             counts once for every sampled path that traverses it, first and last
                             edge included.  Ids: mantra_graph_edges. */
+    int estimator;       /* 0 = trk (App. C): hits of one drawn optimal path per sample; 1 = ob
+                            (Sec. 4.1, target 0 only): every vertex v gets f_v = sigma_sz(v) /
+                            sigma_sz, the share of the optimal s-z paths with v internal, carried
+                            as the nearest multiple of 2^-32 (ties up) so that all sums are exact
+                            integers.  With ob, hits_out, info->max_hits (largest sum of the
+                            rounded f_v^2), info->rade_num and info->sum_int_len are in units of
+                            2^-32, est = hits / (r 2^32), and c * r must stay below 2^31
+                            (MANTRA_E_INVAL for fixed_r, or when omega exceeds it). */
 } mantra_opts;
 
 /* Diagnostics of one mantra_estimate call. */
@@ -208,7 +216,7 @@ int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, ui
  * clears what must start at zero.  Calls that overlap on the GPU (two streams,
  * two threads, two graphs) race on the array: serialise them.
  * Returns MANTRA_E_INVAL for pfm, for a graph whose search scratch does not
- * fit the fixed array (roughly 40 bytes per arrival slot plus 32 per node
+ * fit the fixed array (roughly 40 bytes per arrival slot plus 44 per node
  * for one CTA, plus 8 bytes per requested sample), and MANTRA_E_OVERFLOW
  * when a path count exceeds 64 bits (this variant has no 128-bit re-run). */
 int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt, uint64_t seed, uint32_t dom_pair,

@@ -625,7 +625,8 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
         }
         else { tb[nb] = t; ub[nb + 1] = ub[nb] + it.job.count; ++nb; }
         if (it.reduce) {
-            ri[nr] = ReduceItem{it.job.S, it.job.hits, it.job.fam, it.red_c, (long long*)(slot + SLOT_ROWMAX),
+            ri[nr] = ReduceItem{it.job.S, it.job.S64, it.job.ob ? it.job.wsq : it.job.hits, it.job.fam, it.red_c,
+                                (long long*)(slot + SLOT_ROWMAX),
                                 (u64*)(slot + SLOT_HMAX)};
             rs[nr + 1] = rs[nr] + it.red_c + 1;
             ++nr;
@@ -758,13 +759,15 @@ struct Problem {
     uint64_t fixed_r = 0, boot = 0;
     int dsched = 0, vhat_mode = 0;
     int fam_target = 0;       // mantra_opts.target: 0 nodes, 1 underlying edges, 2 temporal edges
+    int estimator = 0;        // mantra_opts.estimator: 0 trk (App. C), 1 ob (Sec. 4.1)
     double* est_out = nullptr;
     uint64_t* hits_out = nullptr;
     bool out_device = false;
     mantra_info* info_out = nullptr;
     // device state
     u64* hits = nullptr; int* S = nullptr; double* est = nullptr; uint64_t* ovf = nullptr;
-    size_t b_hits = 0, b_S = 0, b_est = 0, b_ovf = 0;
+    u64* wsq = nullptr;       // ob: sums of f^2 (the wimpy variance's numerators)
+    size_t b_hits = 0, b_S = 0, b_est = 0, b_ovf = 0, b_wsq = 0;
     uint64_t ovf_cap = 0;
     // progress: the current phase covers sample indices [phase_begin, phase_end);
     // pos = the next index to run (a phase may span several ticks)
@@ -785,8 +788,15 @@ struct Problem {
         if (out_device && !est_out) return MANTRA_E_INVAL;
         if (vhat_mode != 0 && vhat_mode != 1) return MANTRA_E_INVAL;
         if (fam_target < 0 || fam_target > 2) return MANTRA_E_INVAL;
+        if (estimator < 0 || estimator > 1 || (estimator == 1 && fam_target != 0)) return MANTRA_E_INVAL;
+        if (estimator == 1 && !ob_r_ok(fixed_r)) return MANTRA_E_INVAL;
         return MANTRA_OK;
     }
+
+    // ob sums are in units of 2^-32 (f_v carried as the nearest multiple):
+    // |N_R| <= c r 2^32 must fit int64, so c r < 2^31.
+    double scale() const { return estimator == 1 ? 4294967296.0 : 1.0; }
+    bool ob_r_ok(uint64_t rr) const { return (double)rr * (double)c < 2147483648.0; }
 
     // Size F of the estimated family (App. A for the edge families).
     uint32_t family() const { return fam_target == 0 ? G->n : (fam_target == 1 ? G->n_uedge : G->m); }
@@ -794,6 +804,7 @@ struct Problem {
     // bytes of device state held while the problem runs (admission footprint)
     size_t footprint() const {
         const size_t f = std::max<uint32_t>(family(), 1);
+        if (estimator == 1) return al256(f * 8) * 3 + al256((size_t)c * f * 8) + al256(8 * 4096);
         return al256(f * 8) * 2 + al256((size_t)c * f * 4) + al256(8 * 4096);
     }
 
@@ -812,13 +823,19 @@ struct Problem {
     int start(Engine& E) {
         t0 = now_s();
         const size_t f = std::max<uint32_t>(family(), 1);
-        b_hits = f * 8; b_S = (size_t)c * f * 4; b_est = f * 8;
+        b_hits = f * 8; b_S = (size_t)c * f * (estimator == 1 ? 8 : 4); b_est = f * 8;
         hits = (u64*)E.pool.get(b_hits);
         S = (int*)E.pool.get(b_S);
         est = out_device ? nullptr : (double*)E.pool.get(b_est);
         if (!hits || !S || (!out_device && !est)) return MANTRA_E_NOMEM;
         CU(cudaMemsetAsync(hits, 0, b_hits, E.sa));
         CU(cudaMemsetAsync(S, 0, b_S, E.sa));
+        if (estimator == 1) {
+            b_wsq = f * 8;
+            wsq = (u64*)E.pool.get(b_wsq);
+            if (!wsq) return MANTRA_E_NOMEM;
+            CU(cudaMemsetAsync(wsq, 0, b_wsq, E.sa));
+        }
         pos = 0; boot_sum_int = 0;
         if (fixed_r > 0) {
             phase = ROUND; target = fixed_r; r = 0;
@@ -841,13 +858,16 @@ struct Problem {
         j = Job{};
         j.seed = seed; j.opt = opt; j.c = c; j.hits = hits;
         j.target = fam_target; j.fam = family();
+        j.ob = estimator == 1; j.wsq = wsq;
         const uint64_t left = remaining();
         j.i0 = pos; j.count = std::min(left, quota);
         if (phase == BOOT) {
-            j.dom_pair = DOM_BOOT_PAIR; j.dom_path = DOM_BOOT_PATH; j.S = nullptr;
+            j.dom_pair = DOM_BOOT_PAIR; j.dom_path = DOM_BOOT_PATH; j.S = nullptr; j.S64 = nullptr;
             it->red_c = 0;
         } else {
-            j.dom_pair = DOM_PAIR; j.dom_path = DOM_PATH; j.S = S;
+            j.dom_pair = DOM_PAIR; j.dom_path = DOM_PATH;
+            if (j.ob) { j.S = nullptr; j.S64 = (long long*)S; }
+            else { j.S = S; j.S64 = nullptr; }
             it->red_c = c;
         }
         it->reduce = j.count == left;
@@ -870,11 +890,12 @@ struct Problem {
         reduces += 1;
         if (phase == BOOT) {
             // DrawSufficientSampleSize(G, s', delta/2) and SamplingSchedule
-            double v0 = (double)H / (double)sb;
-            double rho = (double)boot_sum_int / (double)sb;
+            double v0 = (double)H / ((double)sb * scale());
+            double rho = (double)boot_sum_int / ((double)sb * scale());
             if (v0 == 0.0 || rho == 0.0) { v0 = 1.0 / (double)sb; rho = std::max(rho, v0); }
             const double om = std::ceil(omega_closed_form(v0, rho, eps, delta / 2.0));
             if (!(om <= (double)RMAX)) return MANTRA_E_INVAL;
+            if (estimator == 1 && !ob_r_ok((uint64_t)std::max(om, 1.0))) return MANTRA_E_INVAL;
             omega = std::max<uint64_t>(1, (uint64_t)om);
             const double d1 = delta_of_round(delta, 1, dsched);
             if (sb >= omega || xi_given_R(0.0, v0, d1, (double)omega) > eps) s1 = omega;
@@ -888,6 +909,7 @@ struct Problem {
             }
             I.bootstrap = sb; I.omega = omega; I.s1 = s1; I.rho_hat = rho;
             CU(cudaMemsetAsync(hits, 0, b_hits, E.sa));
+            if (wsq) CU(cudaMemsetAsync(wsq, 0, b_wsq, E.sa));
             phase = ROUND; r = 0; pos = 0; target = s1; round = 0;
             return MANTRA_OK;
         }
@@ -899,13 +921,13 @@ struct Problem {
             std::memcpy(&x, slot + SLOT_ROWMAX + 8 * jj, 8);
             NR += x;
         }
-        const double W = (double)H / (double)r;
+        const double W = (double)H / ((double)r * scale());
         double di = delta_of_round(delta, round, dsched), vh = W;
         if (vhat_mode == 1) {            // variance bound from W, delta_i split evenly
             di /= 2.0;
             vh = wimpy_variance_bound(W, di, (double)r);
         }
-        const double xi = xi_from_mcera((double)NR / ((double)c * (double)r), W, vh, di, (double)r, (double)c);
+        const double xi = xi_from_mcera((double)NR / ((double)c * (double)r * scale()), W, vh, di, (double)r, (double)c);
         I.rounds = round; I.rade_num = NR; I.max_hits = H; I.xi = xi; I.vhat = vh;
         if (fixed_r > 0 || r >= omega || xi <= eps) { phase = DONE; return MANTRA_OK; }
         uint64_t nt = (uint64_t)std::ceil(growth * (double)target);
@@ -921,7 +943,7 @@ struct Problem {
         double* dst = out_device ? est_out : est;
         const uint32_t f = family();
         if (f > 0) {
-            CU(launch_normalise(hits, f, r, dst, E.sa));
+            CU(launch_normalise(hits, f, (double)r * scale(), dst, E.sa));
             if (!out_device) CU(cudaMemcpyAsync(est_out, est, (size_t)f * 8, cudaMemcpyDeviceToHost, E.sa));
             if (hits_out)
                 CU(cudaMemcpyAsync(hits_out, hits, (size_t)f * 8,
@@ -936,7 +958,8 @@ struct Problem {
 
     void release(Engine& E) {
         E.pool.put(hits, b_hits); E.pool.put(S, b_S); E.pool.put(est, b_est); E.pool.put(ovf, b_ovf);
-        hits = nullptr; S = nullptr; est = nullptr; ovf = nullptr; ovf_cap = 0;
+        E.pool.put(wsq, b_wsq);
+        hits = nullptr; S = nullptr; est = nullptr; ovf = nullptr; ovf_cap = 0; wsq = nullptr;
     }
 };
 
@@ -950,6 +973,7 @@ int problem_from(const mantra_graph* g, mantra_opt opt, double eps, double delta
     p->fixed_r = o.fixed_r; p->boot = o.bootstrap; p->dsched = o.delta_sched;
     p->vhat_mode = o.vhat_mode;
     p->fam_target = o.target;
+    p->estimator = o.estimator;
     p->est_out = est_out; p->hits_out = hits_out; p->out_device = o.out_device != 0; p->info_out = info;
     return p->validate();
 }

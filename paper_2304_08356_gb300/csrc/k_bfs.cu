@@ -31,6 +31,91 @@ namespace mantra {
 constexpr int IPT = 2;            // frontier states per thread in a segmented-scan tile
 constexpr int WALK_K = 2;         // edge windows with loads in flight per warp in the push
 
+// ob update of one sample (Sec. 4.1), all threads of the CTA: continuation
+// counts dl (the number of optimal ways from a state to z's endpoints) per
+// frontier position, backward from level d; sigma_sz(v) = sum over v's states
+// of sigma * dl (a path visits v once); then every internal v gets its ob
+// value.  dl: the (free) running-sum array, indexed by frontier position;
+// acc: per-vertex sums (zero on entry and exit); VB: vertex bitmap (zero on
+// entry and exit); tl: n entries.  Kept out of line so that the search's
+// register allocation does not carry it.
+template <bool WIDE, int BFS_NT>
+__device__ __noinline__ void bfs_ob_update(const DevGraph& g, const Job& job, uint32_t z, uint32_t d, uint32_t first,
+                                           u128 sigma, const uint32_t* rade, const uint32_t* F, const uint32_t* lev,
+                                           const uint32_t* N, const typename SigOps<WIDE>::T* sig,
+                                           typename SigOps<WIDE>::T* dl, typename SigOps<WIDE>::T* acc, uint32_t* VB,
+                                           uint32_t* tl, uint32_t* sh_nt) {
+    typedef typename SigOps<WIDE>::T Sig;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t P0 = lev[1], P1 = lev[d];  // positions of levels 1 .. d-1
+    for (uint32_t p = P0 + tid; p < P1; p += BFS_NT) dl[p] = (Sig)0;
+    if (tid == 0) *sh_nt = 0;
+    __syncthreads();
+    // adds x to the states of in-edge e's tail on level lv with times before t
+    auto to_preds = [&](uint32_t e, uint32_t t, uint32_t lv, Sig x) {
+        const uint32_t w = g.in_u[e];
+        const uint32_t* Fp = F + lev[lv];
+        const uint32_t Lp = lev[lv + 1] - lev[lv];
+        const uint32_t w1 = g.slot_ptr[w + 1];
+        for (uint32_t p = lower_bound_u32(Fp, 0, Lp, g.slot_ptr[w]); p < Lp; ++p) {
+            const uint32_t a2 = Fp[p];
+            if (a2 >= w1 || g.slot_t[a2] >= t) break;
+            SigOps<WIDE>::atomic_add(dl + lev[lv] + p, x);
+        }
+    };
+    {   // level d: z's endpoint states (sh: all on level d, sfm: the earliest), count 1
+        const uint32_t zs = g.slot_ptr[z], ze = g.slot_ptr[z + 1];
+        const uint32_t a0 = job.opt == 1 ? first : zs, a1 = job.opt == 1 ? first + 1 : ze;
+        for (uint32_t a = a0; a < a1; ++a) {
+            if (!((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u)) continue;
+            const uint32_t ta = g.slot_t[a];
+            for (uint32_t e = g.slot_in[a] + tid; e < g.slot_in[a + 1]; e += BFS_NT) to_preds(e, ta, d - 1, (Sig)1);
+        }
+    }
+    __syncthreads();
+    for (uint32_t lv = d - 1; lv >= 2; --lv) {
+        for (uint32_t p = lev[lv] + tid; p < lev[lv + 1]; p += BFS_NT) {
+            const Sig x = ldcg_sig(dl + p);
+            if (x == (Sig)0) continue;
+            const uint32_t b = F[p], tb = g.slot_t[b];
+            for (uint32_t e = g.slot_in[b]; e < g.slot_in[b + 1]; ++e) to_preds(e, tb, lv - 1, x);
+        }
+        __syncthreads();
+    }
+    // through counts per vertex; the first touch of v lists it (VB marks)
+    for (uint32_t p = P0 + tid; p < P1; p += BFS_NT) {
+        const Sig x = ldcg_sig(dl + p);
+        if (x == (Sig)0) continue;
+        const uint32_t a = F[p], v = g.slot_v[a];
+        SigOps<WIDE>::atomic_add(acc + v, (Sig)(sig[a] * x));   // <= sigma_sz: no wrap
+        const uint32_t bit = 1u << (v & 31);
+        if (!(atomicOr(VB + (v >> 5), bit) & bit)) tl[atomicAdd(sh_nt, 1u)] = v;
+    }
+    __syncthreads();
+    const uint32_t T = *sh_nt;
+    u64 my_sum = 0;
+    for (uint32_t p = tid; p < T; p += BFS_NT) {
+        const uint32_t v = tl[p];
+        const uint64_t q = ob_q(SigOps<WIDE>::wide(ldcg_sig(acc + v)), sigma);
+        acc[v] = (Sig)q;
+        atomicAnd(VB + (v >> 5), ~(1u << (v & 31)));
+        my_sum += q;
+    }
+    __syncthreads();
+    const uint32_t rows = 2 + (job.S64 ? job.c : 0);
+    for (uint32_t it = tid; it < T * rows; it += BFS_NT) {
+        const uint32_t p = it % T, row = it / T;
+        const uint32_t v = tl[p];
+        const uint64_t q = (uint64_t)acc[v];
+        if (q) ob_term(job, v, q, row, rade);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_sum += __shfl_xor_sync(0xFFFFFFFFu, my_sum, o);
+    if (lane == 0 && my_sum) atomicAdd(job.ctr + C_SUMINT, my_sum);
+    __syncthreads();
+    for (uint32_t p = tid; p < T; p += BFS_NT) acc[tl[p]] = (Sig)0;
+}
+
 // BFS_NT threads per CTA, 1024 / BFS_NT CTAs per SM at 64 registers.
 template <bool WIDE, int BFS_NT>
 __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks, const uint64_t* unit_start,
@@ -54,6 +139,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
     uint32_t* pathe = reinterpret_cast<uint32_t*>(region + ws.o_pathe);   // in-CSR index of path edge k
     uint32_t* VB = reinterpret_cast<uint32_t*>(region + ws.o_vb);   // vertex bitmap (stats)
     u64* segmap = reinterpret_cast<u64*>(region + ws.o_segmap);      // vertex -> (level stamp, frontier segment)
+    Sig* acc = reinterpret_cast<Sig*>(region + ws.o_acc);             // ob: through counts per vertex
     uint32_t* stamp_p = reinterpret_cast<uint32_t*>(region + ws.o_stamp);
 
     extern __shared__ uint32_t dyn_smem[];
@@ -74,6 +160,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
     __shared__ uint32_t sh_rade[4];
     __shared__ uint32_t sh_d, sh_len;
     __shared__ u128 sh_sigma;
+    __shared__ uint32_t sh_first, sh_nt;
     __shared__ uint32_t cs_off[BFS_NT + 1], cs_first[BFS_NT], cs_fb[BFS_NT], cs_fe[BFS_NT];   // range table
     __shared__ uint32_t sh_stamp, sh_wrap;
     __shared__ u64 sh_fcmax;
@@ -462,6 +549,16 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             }
             if (__any_sync(FULL, bad)) {
                 if (lane == 0) sh_ovf = 1;
+            } else if (job.ob) {
+                // ob (Sec. 4.1): no draw; sigma_sz and the endpoints go to the ob update
+                if (lane == 0) {
+                    sh_d = d;
+                    sh_first = first;
+                    sh_sigma = SigOps<WIDE>::wide(tot);
+                    uint32_t w4[4];
+                    philox_block(job.seed, i, DOM_RADE, 0, w4);
+                    sh_rade[0] = w4[0]; sh_rade[1] = w4[1]; sh_rade[2] = w4[2]; sh_rade[3] = w4[3];
+                }
             } else {
                 u128 x = 0;
                 uint32_t rng_ok = 1;
@@ -561,7 +658,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 else push_overflow(job, i);
             }
         } else if (!sh_err) {
-            const bool drawn = found && sh_len > 0;
+            const bool drawn = found && sh_len > 0 && !job.ob;
             // ---------------- hits and Rademacher sums ----------------
             const uint32_t nint = drawn ? family_count(job, sh_len) : 0u;
             if (job.hits && nint > 0) {
@@ -594,6 +691,11 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                         job.rec_edges[r * job.rec_cap + p] = pathe[p];
             }
         }
+
+        // ---------------- ob: the update of Sec. 4.1 (block-uniform condition) ----------------
+        if (job.ob && job.hits && found && !sh_ovf && !sh_err && sh_d >= 2)
+            bfs_ob_update<WIDE, BFS_NT>(g, job, z, sh_d, sh_first, sh_sigma, sh_rade, F, lev, N, sig, Fc, acc, VB,
+                                        seg_u, &sh_nt);
 
         // ---------------- cleanup: sigma of every touched slot, bitmaps ----------------
         for (uint32_t w = tid; w < words; w += BFS_NT) {
@@ -636,6 +738,7 @@ size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws) {
     ws->o_vb = o;      o = al(o + (size_t)((n + 31) / 32 + 1) * 4);
     ws->o_segmap = o;  o = al(o + (size_t)n * 8);
     ws->o_stamp = o;   o = al(o + 4);
+    ws->o_acc = o;     o = al(o + (size_t)n * 16);
     ws->o_nbits = o;   o = al(o + (size_t)ws->bits_words * 4);
     ws->n_cap = n;
     ws->o_bits = o;

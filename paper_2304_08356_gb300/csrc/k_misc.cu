@@ -2,6 +2,8 @@
 // final normalisation of the estimates.
 #include "mantra_dev.cuh"
 
+#include <climits>
+
 namespace mantra {
 
 constexpr int RED_NT = 512;
@@ -26,15 +28,20 @@ __global__ void __launch_bounds__(RED_NT) k_round_reduce(const ReduceItem* items
         const ReduceItem it = items[lo];
         const uint32_t j = row - row_start[lo];
         if (j < it.c) {
-            const int* r = it.S + (size_t)j * it.n;
-            int mx = INT_MIN;
-            for (uint32_t v = tid; v < it.n; v += RED_NT) mx = max(mx, r[v]);
+            long long mx = LLONG_MIN;
+            if (it.S64) {
+                const long long* r = it.S64 + (size_t)j * it.n;
+                for (uint32_t v = tid; v < it.n; v += RED_NT) mx = max(mx, r[v]);
+            } else {
+                const int* r = it.S + (size_t)j * it.n;
+                for (uint32_t v = tid; v < it.n; v += RED_NT) mx = max(mx, (long long)r[v]);
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
             if (lane == 0) red_i[wid] = mx;
             __syncthreads();
             if (wid == 0) {
-                long long x = (lane < RED_NT / 32) ? red_i[lane] : (long long)INT_MIN;
+                long long x = (lane < RED_NT / 32) ? red_i[lane] : LLONG_MIN;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
                 if (lane == 0) it.rowmax[j] = it.n ? x : 0;     // an empty family: 0
@@ -57,10 +64,11 @@ __global__ void __launch_bounds__(RED_NT) k_round_reduce(const ReduceItem* items
     }
 }
 
-// est_v = hits_v / r (Algorithm 1's return value), IEEE double division.
-__global__ void k_normalise(const u64* hits, uint32_t n, uint64_t r, double* est) {
+// est_v = hits_v / denom (Algorithm 1's return value), IEEE double division;
+// denom = r, or r 2^32 for the ob sums (exact in double).
+__global__ void k_normalise(const u64* hits, uint32_t n, double denom, double* est) {
     const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < n) est[v] = (double)hits[v] / (double)r;
+    if (v < n) est[v] = (double)hits[v] / denom;
 }
 
 cudaError_t launch_round_reduce(const ReduceItem* items, const uint32_t* row_start, const uint32_t* np, int grid,
@@ -69,8 +77,8 @@ cudaError_t launch_round_reduce(const ReduceItem* items, const uint32_t* row_sta
     return cudaGetLastError();
 }
 
-cudaError_t launch_normalise(const u64* hits, uint32_t n, uint64_t r, double* est, cudaStream_t st) {
-    k_normalise<<<(n + 255) / 256, 256, 0, st>>>(hits, n, r, est);
+cudaError_t launch_normalise(const u64* hits, uint32_t n, double denom, double* est, cudaStream_t st) {
+    k_normalise<<<(n + 255) / 256, 256, 0, st>>>(hits, n, denom, est);
     return cudaGetLastError();
 }
 

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
     uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path) + (size_t)lane * (ws.n_cap + 2);
     uint32_t* pathe = reinterpret_cast<uint32_t*>(region + ws.o_pathe) + (size_t)lane * (ws.n_cap + 2);
     uint32_t* list = reinterpret_cast<uint32_t*>(region + ws.o_list) + lane;     // list[p * 32]
+    Sig* dl = reinterpret_cast<Sig*>(region + ws.o_dl) + lane;               // ob: dl[v * 32]
     __shared__ __align__(16) Task sh_tasks[PFM_NT / 32];
     Task& T = sh_tasks[threadIdx.x >> 5];
     const uint32_t ntasks = *ntasks_p;
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
         const uint32_t te = live ? (stats ? NONE - 1 : g.tmax_in[z]) : 0;
 
         for (uint32_t v = 0; v < n; ++v) fa[(size_t)v * 32] = NONE;
+        if (job.ob) for (uint32_t v = 0; v < n; ++v) dl[(size_t)v * 32] = (Sig)0;
         if (live) { fa[(size_t)s * 32] = 0u; sig[(size_t)s * 32] = (Sig)1; hop[(size_t)s * 32] = 0u; }
         __syncwarp();
 
@@ -271,10 +273,48 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
             continue;
         }
 
+        // ---------------- ob (Sec. 4.1), one lane per sample ----------------
+        // continuation counts to z over the DAG edges (w, x, fa(x)), fa(w) < fa(x),
+        // by a backward walk of the stream from fa(z) (every edge out of x comes
+        // later in time than fa(x)); sigma_sz(v) = sigma(v) * continuations(v)
+        if (job.ob && job.hits && have && !ovf && live && fz != NONE) {
+            const u128 tot = SigOps<WIDE>::wide(sig[(size_t)z * 32]);
+            uint32_t w4[4];
+            philox_block(job.seed, i, DOM_RADE, 0, w4);
+            dl[(size_t)z * 32] = (Sig)1;
+            uint32_t nt = 0;                              // vertices listed in path
+            uint32_t e = upper_bound_u32(st_t, 0, g.m, fz - 1u);
+            const uint32_t e0 = lower_bound_u32(st_t, 0, g.m, ts);
+            while (e > e0) {
+                --e;
+                const uint32_t x = st_v[e], t = st_t[e];
+                if (fa[(size_t)x * 32] != t + 1u) continue;         // not x's earliest arrival
+                const Sig dx = dl[(size_t)x * 32];
+                if (dx == (Sig)0) continue;
+                const uint32_t w = st_u[e];
+                if (fa[(size_t)w * 32] > t) continue;               // needs fa(w) < t
+                if (dl[(size_t)w * 32] == (Sig)0 && w != s) path[nt++] = w;
+                dl[(size_t)w * 32] += dx;                           // <= sigma_sz: no wrap
+            }
+            u64 sum = 0;
+            for (uint32_t k = 0; k < nt; ++k) {
+                const uint32_t w = path[k];
+                const uint64_t q = ob_q(SigOps<WIDE>::wide((Sig)(sig[(size_t)w * 32] * dl[(size_t)w * 32])), tot);
+                dl[(size_t)w * 32] = (Sig)0;
+                if (!q) continue;
+                sum += q;
+                const uint32_t rows = 2 + (job.S64 ? job.c : 0);
+                for (uint32_t row = 0; row < rows; ++row) ob_term(job, w, q, row, w4);
+            }
+            dl[(size_t)z * 32] = (Sig)0;
+            dl[(size_t)s * 32] = (Sig)0;
+            if (sum) atomicAdd(job.ctr + C_SUMINT, sum);
+        }
+
         // ---------------- path draw, one lane per sample ----------------
         uint32_t len = 0, err = 0;
         u128 sigma_sz = 0;
-        if (have && !ovf && live && fz != NONE) {
+        if (have && !ovf && live && fz != NONE && !job.ob) {
             const Sig tot = sig[(size_t)z * 32];
             sigma_sz = SigOps<WIDE>::wide(tot);
             u128 x;
@@ -356,6 +396,7 @@ size_t pfm_region_bytes(uint32_t n, uint32_t list_cap, PfmWs* ws) {
     ws->o_path = o; o = al(o + (size_t)32 * (n + 2) * 4);
     ws->o_pathe = o; o = al(o + (size_t)32 * (n + 2) * 4);
     ws->o_list = o; o = al(o + (size_t)32 * list_cap * 4);
+    ws->o_dl = o;   o = al(o + (size_t)n * 32 * 16);
     return o;
 }
 

@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
     __shared__ uint32_t sh_L, sh_Gc, sh_ovf, sh_err, sh_len;
     __shared__ uint32_t sh_rade[4];
     __shared__ u64 sh_sigma;
+    __shared__ uint32_t sh_nt;
     __shared__ uint32_t cs_off[CHUNK + 1], cs_first[CHUNK], cs_u[CHUNK];   // range table of a chunk
     extern __shared__ __align__(16) uint32_t pc_dyn[];
 
@@ -76,6 +77,8 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
     uint32_t* Fl = reinterpret_cast<uint32_t*>(region + ws.o_list);      // frontier vertices
     uint32_t* path = reinterpret_cast<uint32_t*>(region + ws.o_path);
     uint32_t* pathe = reinterpret_cast<uint32_t*>(region + ws.o_pathe);   // in-CSR index of path edge k
+    u64* dl = reinterpret_cast<u64*>(region + ws.o_dl);                  // ob: continuation counts
+    uint32_t* kofs = reinterpret_cast<uint32_t*>(region + ws.o_kofs);    // ob: Kahn round offsets in Fl
 
     const uint32_t ntasks = *ntasks_p;
     u64* flush_ctr = nullptr;
@@ -84,9 +87,9 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
     for (uint32_t w = tid; w < ws.bits_words; w += PC_NT) NB[w] = 0u;
     __syncthreads();
 
-    // Compacts the next-frontier bitmap (nwords words) into Fl in vertex order
+    // Compacts the next-frontier bitmap (nwords words) into out in vertex order
     // and clears it; returns the number of vertices.  Contains barriers.
-    auto compact = [&](uint32_t nwords) -> uint32_t {
+    auto compact = [&](uint32_t nwords, uint32_t* out) -> uint32_t {
         const uint32_t per_w = (((nwords + PC_NW - 1) / PC_NW) + 31u) & ~31u;
         const uint32_t w_lo = min((uint32_t)wid * per_w, nwords), w_hi = min(w_lo + per_w, nwords);
         uint32_t cnt = 0;
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
             while (bits) {
                 const uint32_t b = __ffs(bits) - 1;
                 bits &= bits - 1;
-                Fl[pos++] = w * 32u + b;
+                out[pos++] = w * 32u + b;
             }
             off += __shfl_sync(FULL, incl, 31);
         }
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
         // ---- earliest arrivals ----
         uint32_t bound = live ? (stats ? NONE - 1u : g.tmax_in[z]) : 0u;
         while (live) {
-            const uint32_t L = compact(nwords);
+            const uint32_t L = compact(nwords, Fl);
             if (L == 0) break;
             if (tid == 0) ++my_rounds;
             for (uint32_t c0 = 0; c0 < L; c0 += CHUNK) {
@@ -316,13 +319,15 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                 }
             }
         }
+        // Kahn rounds are appended: round r's vertices are Fl[kofs[r] .. kofs[r+1])
+        uint32_t kb = 0, nr = 0;
         if (reached) {
             if (tid == 0) { sig[s] = 1ull; hop[s] = 0u; NB[s >> 5] |= 1u << (s & 31); }
             __syncthreads();
             for (;;) {
-                const uint32_t L = compact(nwords);
+                const uint32_t L = compact(nwords, Fl + kb);
                 if (L == 0) break;
-                if (tid == 0) ++my_rounds;
+                if (tid == 0) { ++my_rounds; kofs[nr] = kb; }
                 for (uint32_t c0 = 0; c0 < L; c0 += CHUNK) {
                     // [lo_prev(u), first t > bound): u's out-edges after its arrival
                     uint32_t u[2], lo[2], hi[2], key[2];
@@ -332,7 +337,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                         lo[j] = hi[j] = key[j] = 0u;
                         u[j] = NONE;
                         if (x < L) {
-                            const uint32_t uu = Fl[x];
+                            const uint32_t uu = Fl[kb + x];
                             u[j] = uu;
                             lo[j] = lo_prev[uu];
                             hi[j] = out_ptr[uu + 1];
@@ -351,7 +356,10 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                         if (atomicSub(pend + v, 1u) == 1u) atomicOr(NB + (v >> 5), 1u << (v & 31));
                     });
                 }
+                kb += L;
+                ++nr;
             }
+            if (tid == 0) kofs[nr] = kb;
         }
 
         if (stats) {
@@ -374,8 +382,15 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
         }
         __syncthreads();
 
-        // ---- backward draw (warp 0) ----
-        if (reached && !sh_ovf && wid == 0) {
+        // ---- backward draw (warp 0); ob: sigma_sz and the Rademacher bits only ----
+        if (reached && !sh_ovf && wid == 0 && job.ob) {
+            if (lane == 0) {
+                sh_sigma = __ldcg(sig + z);
+                uint32_t w4[4];
+                philox_block(job.seed, i, DOM_RADE, 0, w4);
+                sh_rade[0] = w4[0]; sh_rade[1] = w4[1]; sh_rade[2] = w4[2]; sh_rade[3] = w4[3];
+            }
+        } else if (reached && !sh_ovf && wid == 0) {
             const u64 tot = __ldcg(sig + z);
             u128 x = 0;
             uint32_t rng_ok = 1;
@@ -435,6 +450,55 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
             }
         }
         __syncthreads();
+
+        // ---- ob (Sec. 4.1): sigma_sz(v) = sigma(v) * continuations(v), the
+        // continuations counted over the prefix-foremost DAG in reverse Kahn
+        // order from z (block-uniform condition) ----
+        if (job.ob && job.hits && reached && !sh_ovf && !sh_err) {
+            for (uint32_t p = tid; p < kb; p += PC_NT) dl[Fl[p]] = 0ull;
+            if (tid == 0) sh_nt = 0;
+            __syncthreads();
+            if (tid == 0) dl[z] = 1ull;
+            __syncthreads();
+            for (int r = (int)nr - 1; r >= 0; --r) {
+                const uint32_t p1 = kofs[r + 1];
+                for (uint32_t p = kofs[r] + tid; p < p1; p += PC_NT) {
+                    const uint32_t v = Fl[p];
+                    if (v == s) continue;
+                    const u64 x = __ldcg(dl + v);
+                    if (!x) continue;
+                    const uint32_t fv = __ldcg(fat + v), a = ldv<FA_SMEM>(fsl + v);
+                    const uint32_t e1 = __ldg(g.slot_in + a + 1);
+                    for (uint32_t e = __ldg(g.slot_in + a); e < e1; ++e) {
+                        const uint32_t w = __ldg(g.in_u + e);
+                        if (__ldcg(fat + w) < fv) atomicAdd(dl + w, x);   // <= sigma_sz: no wrap
+                    }
+                }
+                __syncthreads();
+            }
+            // ob values of the internal vertices, into sig (no longer needed); the
+            // nonzero ones listed in path
+            u64 my_sum = 0;
+            for (uint32_t p = tid; p < kb; p += PC_NT) {
+                const uint32_t v = Fl[p];
+                if (v == s || v == z) continue;
+                const u64 x = __ldcg(dl + v);
+                if (!x) continue;
+                const uint64_t q = ob_q((u128)__ldcg(sig + v) * x, (u128)sh_sigma);
+                sig[v] = q;
+                path[atomicAdd(&sh_nt, 1u)] = v;
+                my_sum += q;
+            }
+            __syncthreads();
+            const uint32_t T = sh_nt, rows = 2 + (job.S64 ? job.c : 0);
+            for (uint32_t it = tid; it < T * rows; it += PC_NT) {
+                const uint32_t v = path[it % T];
+                ob_term(job, v, sig[v], it / T, sh_rade);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) my_sum += __shfl_xor_sync(FULL, my_sum, o);
+            if (lane == 0 && my_sum) atomicAdd(job.ctr + C_SUMINT, my_sum);
+        }
 
         if (sh_ovf) {
             if (tid == 0) push_overflow(job, i);
@@ -499,6 +563,8 @@ size_t pfm_cta_region_bytes(uint32_t n, bool fa_in_smem, PfmCtaWs* ws) {
     ws->o_list = o;  o = al(o + (size_t)(n + 1) * 4);
     ws->o_path = o;  o = al(o + (size_t)(n + 2) * 4);
     ws->o_pathe = o; o = al(o + (size_t)(n + 2) * 4);
+    ws->o_dl = o;    o = al(o + (size_t)n * 8);
+    ws->o_kofs = o;  o = al(o + (size_t)(n + 2) * 4);
     return o;
 }
 

@@ -74,6 +74,13 @@ struct Job {
     uint32_t fam;              // its size F (n, n_uedge or m)
     u64* hits;                 // F, or nullptr: no accumulation
     int* S;                    // c*F, row j at S + j*F, or nullptr
+    // ob estimator (Sec. 4.1; nodes only): instead of the drawn path's hits,
+    // every internal vertex v of an optimal path gets q = 2^32 sigma_sz(v) /
+    // sigma_sz rounded to nearest (ties up): hits[v] += q, wsq[v] += q^2 / 2^32
+    // (rounded the same way), S64[j][v] += lambda_j q.  No path is drawn.
+    int ob;
+    u64* wsq;                  // F (ob)
+    long long* S64;            // c*F (ob), or nullptr
     u64* ctr;                  // C_NCOUNT counters
     uint64_t* ovf_list;        // sample indices whose 64-bit path counts overflowed
     int* status;
@@ -229,6 +236,13 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
     *total = scratch[NT / 32 - 1];
     __syncthreads();
     return before + x - v;
+}
+
+// Loads through L2 (skipping L1) of path counts written by atomics.
+__device__ __forceinline__ u64 ldcg_sig(const u64* p) { return __ldcg(reinterpret_cast<const unsigned long long*>(p)); }
+__device__ __forceinline__ u128 ldcg_sig(const u128* p) {
+    const unsigned long long* w = reinterpret_cast<const unsigned long long*>(p);
+    return ((u128)__ldcg(w + 1) << 64) | (u128)__ldcg(w);
 }
 
 // Warp shuffles of 64- and 128-bit path counts.
@@ -461,6 +475,51 @@ __device__ __forceinline__ void lbs_walk_batched(const uint32_t* off, uint32_t G
 
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, ST_OK, code); }
 
+// ob value of a vertex: the integer nearest to 2^32 * thr / sig (ties up),
+// 0 <= thr <= sig, sig >= 1.  Counts below 2^64 take one 128-by-64-bit
+// division of thr * 2^32 + floor(sig / 2); wider counts a restoring division
+// of the 160-bit numerator, one quotient bit per step (the quotient has at
+// most 33 bits).
+__device__ __forceinline__ uint64_t ob_q(u128 thr, u128 sig) {
+    if ((uint64_t)(sig >> 64) == 0) {
+        const u128 num = (thr << 32) + (sig >> 1);
+        return (uint64_t)(num / (uint64_t)sig);
+    }
+    // numerator N = thr * 2^32 + floor(sig/2) as (nh : bits 128..159, nl : bits 0..127)
+    const u128 half = sig >> 1;
+    u128 nl = thr << 32;
+    uint64_t nh = (uint64_t)(thr >> 96);
+    nl += half;
+    if (nl < half) nh += 1;
+    // long division over the 33 low-order quotient positions: the partial
+    // remainder starts as N >> 32 (< 2 sig)
+    u128 rem = ((u128)nh << 96) | (nl >> 32);
+    uint64_t q = 0;
+    if (rem >= sig) { rem -= sig; q = 1; }
+    for (int b = 31; b >= 0; --b) {
+        const bool top = (uint64_t)(rem >> 127) != 0;
+        rem = (rem << 1) | (u128)((uint64_t)(nl >> b) & 1u);
+        q <<= 1;
+        if (top || rem >= sig) { rem -= sig; q |= 1u; }
+    }
+    return q;
+}
+
+// q^2 / 2^32 rounded to nearest (ties up): the ob value of f^2 (wimpy variance).
+__device__ __forceinline__ uint64_t ob_sq(uint64_t q) { return (uint64_t)(((u128)q * q + (1ull << 31)) >> 32); }
+
+// One (vertex, row) term of the ob update: row 0 hits, row 1 wsq, row 2 + j
+// the Rademacher sum of trial j.
+__device__ __forceinline__ void ob_term(const Job& job, uint32_t v, uint64_t q, uint32_t row, const uint32_t rade[4]) {
+    if (row == 0) atomicAdd(job.hits + v, (u64)q);
+    else if (row == 1) atomicAdd(job.wsq + v, (u64)ob_sq(q));
+    else if (job.S64) {
+        const uint32_t jj = row - 2;
+        const long long lq = ((rade[jj >> 5] >> (jj & 31)) & 1u) ? (long long)q : -(long long)q;
+        atomicAdd(reinterpret_cast<u64*>(job.S64 + (size_t)jj * job.fam + v), (u64)lq);
+    }
+}
+
 // Records sample i for the 128-bit / in-order re-run (a job without a list
 // reports a consistency error instead).
 __device__ __forceinline__ void push_overflow(const Job& job, uint64_t i) {
@@ -493,13 +552,14 @@ struct BfsWs {
     uint32_t bits_words; // capacity of each bitmap (words): ceil(A_max / 32)
     uint32_t n_cap;      // node capacity of a region
     int nt;              // threads per CTA (512 or 1024)
+    size_t o_acc;        // ob: per-vertex sums of through counts
 };
 
 // Per-warp scratch of the pfm search kernel.
 struct PfmWs {
     char* base;          // warp w uses base + w * stride
     size_t stride;
-    size_t o_fa, o_sig, o_hop, o_path, o_pathe, o_list;
+    size_t o_fa, o_sig, o_hop, o_path, o_pathe, o_list, o_dl;   // o_dl: ob continuation counts
     uint32_t n_cap;      // node capacity of a region (largest graph of the launch)
     uint32_t list_cap;   // contributing-edge entries per lane (deferred path counts)
 };
@@ -509,6 +569,7 @@ struct PfmCtaWs {
     char* base;          // CTA b uses base + b * stride
     size_t stride;
     size_t o_fa, o_bits, o_exp, o_fat, o_sig, o_hop, o_pend, o_list, o_path, o_pathe;
+    size_t o_dl, o_kofs; // ob: continuation counts per vertex, Kahn round offsets
     uint32_t n_cap;      // node capacity of a region
     uint32_t bits_words; // words of each bitmap: ceil(n_cap / 32)
     int fa_in_smem;      // arrival slots and bitmaps in dynamic shared memory
@@ -539,13 +600,14 @@ cudaError_t launch_pfm_cta(const Task* tasks, const uint64_t* unit_start, const 
 // One problem of a multi-problem round reduction.
 struct ReduceItem {
     const int* S;        // c rows of n (unused when c = 0)
-    const u64* hits;     // n
+    const long long* S64;// instead of S when set (ob sums)
+    const u64* hits;     // n: hits, or the ob wimpy sums
     uint32_t n, c;       // n: the family size (0: every maximum is 0)
     long long* rowmax;   // c results: max_v S[j][v]
     u64* hmax;           // max_v hits[v]
 };
 cudaError_t launch_round_reduce(const ReduceItem* items, const uint32_t* row_start, const uint32_t* np, int grid,
                                 cudaStream_t st);
-cudaError_t launch_normalise(const u64* hits, uint32_t n, uint64_t r, double* est, cudaStream_t st);
+cudaError_t launch_normalise(const u64* hits, uint32_t n, double denom, double* est, cudaStream_t st);
 
 }  // namespace mantra

@@ -31,7 +31,7 @@ class MantraError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("c", C.c_uint32), ("growth", C.c_double), ("fixed_r", C.c_uint64), ("bootstrap", C.c_uint64),
                 ("delta_sched", C.c_int), ("out_device", C.c_int), ("stream", C.c_void_p), ("vhat_mode", C.c_int),
-                ("target", C.c_int)]
+                ("target", C.c_int), ("estimator", C.c_int)]
 
 
 class Info(C.Structure):
@@ -167,12 +167,12 @@ class Graph:
             pass
 
     def estimate(self, opt, eps, delta, seed, c=0, growth=0.0, fixed_r=0, bootstrap=0, delta_sched=0,
-                 est_out=None, hits_out=None, stream=None, vhat_mode=0, target=0):
+                 est_out=None, hits_out=None, stream=None, vhat_mode=0, target=0, estimator=0):
         """mantra_estimate.  With est_out / hits_out given as integers they are
         device pointers (out_device = 1); otherwise host numpy arrays are
-        returned.  target: 0 nodes, 1 underlying edges, 2 temporal edges.
-        Returns (est, hits, info dict)."""
-        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, stream, vhat_mode, target)
+        returned.  target: 0 nodes, 1 underlying edges, 2 temporal edges;
+        estimator: 0 trk, 1 ob (hits in 2^-32 units).  Returns (est, hits, info dict)."""
+        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, stream, vhat_mode, target, estimator)
         info = Info()
         if isinstance(est_out, int):
             o.out_device = 1
@@ -223,7 +223,7 @@ class Graph:
 def estimate_batch(problems):
     """mantra_estimate_batch over a list of dicts with keys graph (Graph), opt,
     eps, delta, seed and optional c, growth, fixed_r, bootstrap, delta_sched,
-    vhat_mode, target.  Returns a list of (est, hits, info dict, status)."""
+    vhat_mode, target, estimator.  Returns a list of (est, hits, info dict, status)."""
     k = len(problems)
     arr = (Problem * k)()
     keep = []
@@ -231,7 +231,7 @@ def estimate_batch(problems):
     for x, p in enumerate(problems):
         g = p["graph"]
         o = Opts(p.get("c", 0), p.get("growth", 0.0), p.get("fixed_r", 0), p.get("bootstrap", 0),
-                 p.get("delta_sched", 0), 0, None, p.get("vhat_mode", 0), p.get("target", 0))
+                 p.get("delta_sched", 0), 0, None, p.get("vhat_mode", 0), p.get("target", 0), p.get("estimator", 0))
         F = g.family_size(p.get("target", 0))
         est = np.zeros(max(F, 1), np.float64)
         hits = np.zeros(max(F, 1), np.uint64)
@@ -264,8 +264,8 @@ class Server:
         self._n = {}
 
     def submit(self, graph, opt, eps, delta, seed, c=0, growth=0.0, fixed_r=0, bootstrap=0, delta_sched=0,
-               vhat_mode=0, target=0):
-        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, None, vhat_mode, target)
+               vhat_mode=0, target=0, estimator=0):
+        o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, None, vhat_mode, target, estimator)
         rid = C.c_uint64()
         _chk(lib().mantra_server_submit(self.h, graph.h, _opt(opt), eps, delta, seed, C.byref(o), C.byref(rid)),
              "mantra_server_submit")
