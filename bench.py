@@ -9,7 +9,10 @@ step, run as one mantra_estimate_batch (default) or as three mantra_estimate
 calls (--mode sequential; also timed after the main region on the same seeds).
 Metric: sampled (s,z) pairs per second, bootstrap and estimation samples of the
 three optimalities together.  Inputs are synthetic (the
-paper's data sets are not available).
+paper's data sets are not available).  After the timed region, one batched
+step each of temporal edge betweenness (App. A) and of the ob estimator
+(Sec. 4.1) on the same workload is reported under secondary.next_rows
+(--no-next skips them).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank runs its own steps on its own GPU (different seeds,
@@ -302,6 +305,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-next", action="store_true", help="skip the edge-betweenness and ob legs")
     ap.add_argument("--opts", default="sh,sfm,pfm", help="optimalities per step (profiling subsets)")
     ap.add_argument("--serve-graphs", type=int, default=16, help="serving leg: resident graphs (0: skip)")
     ap.add_argument("--serve-requests", type=int, default=120, help="serving leg: requests")
@@ -397,6 +401,28 @@ def main():
         seq_ms.append(e0.elapsed_time(e1))
     seq_rate = sum(i["r"] + i["bootstrap"] for st in seq_infos for i in st.values()) / (sum(seq_ms) / 1000.0)
 
+    # the same workload for the other estimators (edge betweenness over the
+    # temporal edges, App. A; the ob estimator, Sec. 4.1): one batched step each
+    next_rows = {}
+    for label, kw in (() if args.no_next else (("edge_betweenness_temporal", dict(target=2)),
+                                               ("ob_estimator", dict(estimator=1)))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = M.estimate_batch([dict(graph=g, opt=name, eps=EPS, delta=DELTA, seed=seed0 + 1000, c=C_TRIALS, **kw)
+                                for name in OPTS])
+        e1.record(stream)
+        e1.synchronize()
+        for (_, _, _, st) in res:
+            if st != 0:
+                raise M.MantraError(st, "mantra_estimate_batch (%s)" % label)
+        ms = e0.elapsed_time(e1)
+        n_s = sum(r[2]["r"] + r[2]["bootstrap"] for r in res)
+        next_rows[label] = {"pairs_per_s": n_s / (ms / 1000.0), "ms": ms,
+                            "r": {o: r[2]["r"] for o, r in zip(OPTS, res)},
+                            "kernel_ms": {o: r[2]["kernel_ms"] for o, r in zip(OPTS, res)}}
+
     # dominant kernel: search time per optimality family (sequential pass)
     pfm_kernel = "k_pfm" if os.environ.get("MANTRA_PFM_KERNEL") == "lane" else "k_pfm_cta"
     fam = {k: tuple(o for o in v_ if o in OPTS) for k, v_ in {"k_bfs": ("sh", "sfm"), pfm_kernel: ("pfm",)}.items()}
@@ -466,7 +492,7 @@ def main():
                            "per_opt_r": {o: [st[o]["r"] for st in infos_all] for o in OPTS}},
                 "secondary": {"temporal_edge_GBps": alg_gbps, "edges_per_s": edges / (total_ms / 1000.0),
                               "sequential_pairs_per_s": seq_rate, "sequential_kernel_ms": kms,
-                              "mode": args.mode},
+                              "mode": args.mode, "next_rows": next_rows},
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "timing": "sequential pass, tick events",
                              "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
