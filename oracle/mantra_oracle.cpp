@@ -20,6 +20,9 @@
 //                              probability 1/sigma_sz.
 //   Sec. 4.1, the ob estimator -- f_v(s,z) = sigma_sz(v) / sigma_sz, carried
 //                              as fixed point with 32 fraction bits.
+//   App. C, the RTB estimator  -- f_v(s) = 1/(n-1) sum_z sigma_sz(v) / sigma_sz
+//                              from one full search and a backward dependency
+//                              accumulation, each term in 2^-32 units.
 //   App. D, Algorithm 2     -- reach counts per hop, D_LB, D_tau, zeta, Psi.
 //
 // Readings where the paper is silent or garbled (same list in the design
@@ -496,6 +499,113 @@ uint64_t fixed32(u128 a, u128 b) {
     return q;
 }
 
+// floor(a * x / d + 1/2) for a <= d (d >= 1), x < 2^64: the quotient is at
+// most x + 1.  The product is formed exactly (192 bits as hi:lo) and divided
+// by schoolbook binary long division when it does not fit 128 bits.
+uint64_t muldiv_round(u128 a, uint64_t x, u128 d) {
+    const u128 M64 = ~(u128)0 >> 64;
+    if ((a >> 64) == 0) {                       // a * x < 2^128
+        const u128 nprod = a * (u128)x;
+        const u128 q0 = nprod / d, r0 = nprod % d;
+        return (uint64_t)q0 + ((r0 >= d - r0) ? 1u : 0u);   // 2 r0 >= d, without overflow
+    }
+    // 192-bit product: a = ah 2^64 + al, a x = ah x 2^64 + al x
+    const u128 al = a & M64, ah = a >> 64;
+    const u128 p0 = al * (u128)x, p1 = ah * (u128)x;
+    u128 lo = p0 + (p1 << 64);
+    u128 hi = (p1 >> 64) + ((lo < p0) ? 1 : 0);   // carry out of the low 128 bits
+    // long division of (hi:lo) by d, bit by bit from the top (hi < 2^64)
+    u128 rem = 0;
+    uint64_t q = 0;
+    for (int bit = 191; bit >= 0; --bit) {
+        const bool top = (rem >> 127) != 0;
+        const unsigned b = bit >= 128 ? (unsigned)((hi >> (bit - 128)) & 1) : (unsigned)((lo >> bit) & 1);
+        rem = (rem << 1) | b;
+        const bool ge = top || rem >= d;
+        if (ge) rem -= d;
+        if (bit < 64) q = (q << 1) | (ge ? 1u : 0u);
+        else if (ge) return ~(uint64_t)0;       // quotient >= 2^64: impossible for a <= d
+    }
+    const bool top = (rem >> 127) != 0;
+    return q + ((top || (rem << 1) >= d) ? 1u : 0u);
+}
+
+// One RTB sample (App. C): q[v] = f_v(s) in 2^-32 units for every v != s.
+// Full search from s.  sh / sfm: the endpoint states of a vertex v are its
+// states on its first level d_v (sfm: only the earliest of them), and
+// eps(b) = sigma(b) / sigma_{s,v_b} for an endpoint b, else 0.  pfm: every
+// reached vertex is its own endpoint (eps = 1).  Levels (or decreasing fa)
+// from the last down: for every optimal-DAG edge a -> b,
+//   delta(a) += round(sigma(a) * (eps(b) + delta(b)) / sigma(b)),
+// then f_v = round(sum of delta over v's states / (n-1)).
+int rtb_values(const Graph& G, int opt, uint64_t seed, uint64_t i, uint32_t dom, std::vector<uint64_t>* q) {
+    const uint32_t n = G.n;
+    q->assign(n, 0);
+    uint64_t s64;
+    if (!uniform_below64(n, seed, i, dom, &s64)) return E_RNG;
+    const uint32_t s = (uint32_t)s64;
+    const uint64_t ONE = (uint64_t)1 << 32;
+    std::vector<uint64_t> sum(n, 0);
+    if (opt == OPT_PFM) {
+        Search R = pfm_scan(G, s);
+        if (R.status != OK) return R.status;
+        std::vector<uint64_t> delta(n, 0);
+        std::vector<uint32_t> order;
+        for (uint32_t v = 0; v < n; ++v) if (v != s && R.fa[v] != POS_INF) order.push_back(v);
+        std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return R.fa[a] > R.fa[b]; });
+        for (uint32_t x : order) {
+            const uint64_t X = ONE + delta[x];
+            for (const auto& e : G.in[x]) {
+                const uint32_t w = e.first;
+                if ((int64_t)e.second != R.fa[x] || !(R.fa[w] < R.fa[x]) || w == s) continue;
+                delta[w] += muldiv_round(R.sig[w], X, R.sig[x]);
+            }
+        }
+        for (uint32_t v = 0; v < n; ++v) sum[v] = delta[v];
+    } else {
+        Search R = tbfs_levels(G, s, n);
+        if (R.status != OK) return R.status;
+        // first level and endpoint states per vertex
+        std::vector<uint32_t> dv(n, UINT32_MAX);
+        for (const auto& kv : R.st)
+            if (kv.first.first != s) dv[kv.first.first] = std::min(dv[kv.first.first], kv.second.level);
+        std::map<App, bool> is_end;
+        std::vector<u128> sv(n, 0);             // sigma_{s,v}
+        std::vector<bool> taken(n, false);
+        for (const auto& kv : R.st) {           // map order: by vertex, then ascending time
+            const uint32_t v = kv.first.first;
+            if (v == s || kv.second.level != dv[v]) continue;
+            if (opt == OPT_SFM && taken[v]) continue;
+            taken[v] = true;
+            is_end[kv.first] = true;
+            if (!add_checked(sv[v], kv.second.sigma, &sv[v])) return E_OVERFLOW;
+        }
+        uint32_t D = 0;
+        for (const auto& kv : R.st) D = std::max(D, kv.second.level);
+        std::map<App, uint64_t> delta;
+        for (uint32_t k = D; k >= 2; --k) {
+            for (const auto& kv : R.st) {
+                if (kv.second.level != k) continue;
+                const App b = kv.first;
+                uint64_t X = delta.count(b) ? delta[b] : 0;
+                if (is_end.count(b)) X += (uint64_t)fixed32(kv.second.sigma, sv[b.first]);
+                if (X == 0) continue;
+                for (const auto& e : G.in[b.first]) {
+                    if ((int64_t)e.second != b.second) continue;
+                    const uint32_t w = e.first;
+                    for (auto it = R.st.lower_bound(App(w, NEG_INF)); it != R.st.end() && it->first.first == w; ++it)
+                        if (it->second.level == k - 1 && it->first.second < b.second)
+                            delta[it->first] += muldiv_round(it->second.sigma, X, kv.second.sigma);
+                }
+            }
+        }
+        for (const auto& kv : delta) sum[kv.first.first] += kv.second;
+    }
+    for (uint32_t v = 0; v < n; ++v)
+        if (v != s && sum[v]) (*q)[v] = muldiv_round(1, sum[v], n - 1);
+    return OK;
+}
+
 // The ob functions of one sample (Sec. 4.1): q[v] = fixed32(sigma_sz(v), sigma_sz)
 // for the internal vertices v on some optimal path (all 0 when z is
 // unreachable).
@@ -702,6 +812,19 @@ void orc_edge_ids(const void* g, uint32_t* u, uint32_t* v, uint32_t* t, uint32_t
 
 // sigma_sz(v) for all v (lo/hi 64-bit halves, n entries each); returns the
 // status, sigma_sz in *sig_lo / *sig_hi.
+// RTB values of sample i (n entries, 2^-32 units).
+int orc_rtb_values(const void* g, int opt, uint64_t seed, uint64_t i, uint32_t dom, uint64_t* q) {
+    std::vector<uint64_t> v;
+    int st = rtb_values(*(const Graph*)g, opt, seed, i, dom, &v);
+    if (st != OK) return st;
+    for (size_t k = 0; k < v.size(); ++k) q[k] = v[k];
+    return OK;
+}
+
+uint64_t orc_muldiv_round(uint64_t a_lo, uint64_t a_hi, uint64_t x, uint64_t d_lo, uint64_t d_hi) {
+    return muldiv_round(((u128)a_hi << 64) | a_lo, x, ((u128)d_hi << 64) | d_lo);
+}
+
 int orc_through(const void* g, int opt, uint32_t s, uint32_t z, uint64_t* lo, uint64_t* hi, uint64_t* sig_lo,
                 uint64_t* sig_hi) {
     const Graph* G = (const Graph*)g;
@@ -745,7 +868,9 @@ double orc_omega_bound(double vhat, double rho, double eps, double delta) {
 // hits, S, N_R, the wimpy sums (of square32(q)) and sum_int_len are all in
 // 2^-32 units and est = hits / (r 2^32); no path is drawn.  ob needs c r < 2^31
 // (fixed_r, and omega) so that |N_R| fits int64; max_hits then reports the
-// largest wimpy sum.
+// largest wimpy sum.  2: RTB (App. C, nodes only): sample i is a source s
+// drawn uniformly from the pair stream's domain, f_v(s) from rtb_values, with
+// the same units and limits as ob.
 int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed, uint32_t c, double growth,
                  uint64_t fixed_r, uint64_t bootstrap, int delta_sched, int vhat_mode, int target, int estimator,
                  double* est, uint64_t* hits_out, orc_info* info) {
@@ -753,8 +878,8 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
     const uint32_t n = G->n;
     if (n < 2 || !(eps > 0 && eps < 1) || !(delta > 0 && delta < 1) || c < 1 || c > 128) return E_INVAL;
     if (target < 0 || target > 2) return E_INVAL;
-    if (estimator < 0 || estimator > 1 || (estimator == 1 && target != 0)) return E_INVAL;
-    const bool ob = estimator == 1;
+    if (estimator < 0 || estimator > 2 || (estimator != 0 && target != 0)) return E_INVAL;
+    const bool ob = estimator != 0;             // ob and RTB: fractional values in 2^-32 units
     // ob sums are in units of 2^-32; |N_R| <= c r 2^32 must fit int64
     const double scale = ob ? 4294967296.0 : 1.0;
     if (ob && (double)fixed_r * (double)c >= 2147483648.0) return E_INVAL;
@@ -778,12 +903,21 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
     // f^2 of an ob value q = 2^32 f, rounded back to 2^-32 units (ties up).
     auto square32 = [](uint64_t q) { return (uint64_t)(((u128)q * q + ((u128)1 << 31)) >> 32); };
     // Update step for samples [a, b): hits and Rademacher sums (Algorithm 1).
+    // the fractional functions of sample i (ob: pair (s,z); RTB: source s)
+    auto frac_values = [&](uint64_t i, uint32_t dom, std::vector<std::pair<uint32_t, uint64_t>>* vals) -> int {
+        if (estimator == 1) return ob_values(*G, opt, seed, i, dom, vals);
+        std::vector<uint64_t> q;
+        int st = rtb_values(*G, opt, seed, i, dom, &q);
+        vals->clear();
+        for (uint32_t v = 0; v < n; ++v) if (q[v]) vals->push_back(std::make_pair(v, q[v]));
+        return st;
+    };
     auto run = [&](uint64_t a, uint64_t b) -> int {
         std::vector<uint32_t> it;
         std::vector<std::pair<uint32_t, uint64_t>> vals;
         for (uint64_t i = a; i < b; ++i) {
             if (ob) {
-                int st = ob_values(*G, opt, seed, i, D_PAIR, &vals);
+                int st = frac_values(i, D_PAIR, &vals);
                 if (st != OK) return st;
                 for (const auto& vq : vals) {
                     hits[vq.first] += vq.second;
@@ -851,7 +985,7 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
         std::vector<std::pair<uint32_t, uint64_t>> vals;
         for (uint64_t i = 0; i < sb; ++i) {
             if (ob) {                       // hb: sum of f^2 (the wimpy numerator), sum_b: sum of f
-                int st = ob_values(*G, opt, seed, i, D_BOOT_PAIR, &vals);
+                int st = frac_values(i, D_BOOT_PAIR, &vals);
                 if (st != OK) return st;
                 for (const auto& vq : vals) { hb[vq.first] += square32(vq.second); sum_b += vq.second; }
                 continue;

@@ -78,6 +78,9 @@ def lib():
         L.orc_through.argtypes = [C.c_void_p, C.c_int, C.c_uint32, C.c_uint32, u64p, u64p, u64p, u64p]
         L.orc_fixed32.argtypes = [C.c_uint64] * 4
         L.orc_fixed32.restype = C.c_uint64
+        L.orc_rtb_values.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64, C.c_uint32, u64p]
+        L.orc_muldiv_round.argtypes = [C.c_uint64] * 5
+        L.orc_muldiv_round.restype = C.c_uint64
         L.orc_wimpy_variance_bound.argtypes = [C.c_double, C.c_double, C.c_double]
         L.orc_wimpy_variance_bound.restype = C.c_double
         L.orc_stats.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64, C.c_int, u64p, u32p]
@@ -216,7 +219,8 @@ class Graph:
     def estimate(self, opt, eps, delta, seed, c=25, growth=1.2, fixed_r=0, bootstrap=0, delta_sched=0, vhat_mode=0,
                  target=0, estimator=0):
         """Algorithm 1; target 0 nodes, 1 underlying edges, 2 temporal edges;
-        estimator 0 trk (App. C), 1 ob (Sec. 4.1; hits in 2^-32 units)."""
+        estimator 0 trk (App. C), 1 ob (Sec. 4.1), 2 RTB (App. C); ob and RTB
+        hits are in 2^-32 units."""
         F = self.n if target == 0 else (self.edge_ids()[4] if target == 1 else self.m)
         est = np.zeros(max(F, 1), np.float64)
         hits = np.zeros(max(F, 1), np.uint64)
@@ -233,6 +237,12 @@ class Graph:
         _chk(lib().orc_through(self.h, opt, s, z, _p(lo, C.c_uint64), _p(hi, C.c_uint64), C.byref(slo),
                                C.byref(shi)))
         return (shi.value << 64) | slo.value, [(int(b) << 64) | int(a) for a, b in zip(lo, hi)]
+
+    def rtb_values(self, opt, seed, i, dom=D_PAIR):
+        """RTB values f_v(s) of sample i in 2^-32 units (n entries)."""
+        q = np.zeros(self.n, np.uint64)
+        _chk(lib().orc_rtb_values(self.h, opt, seed, i, dom, _p(q, C.c_uint64)))
+        return q
 
     def stats_counts(self, opt, seed, r_s, all_sources=False):
         """(reach[0..D_LB], D_LB): cumulative reach counts per hop (Algorithm 2)."""
@@ -275,3 +285,9 @@ def fixed32(a: int, b: int) -> int:
     """The oracle's ob rounding: the integer nearest 2^32 a / b (ties up), 0 <= a <= b < 2^128."""
     M = (1 << 64) - 1
     return lib().orc_fixed32(a & M, a >> 64, b & M, b >> 64)
+
+
+def muldiv_round(a: int, x: int, d: int) -> int:
+    """The oracle's RTB rounding: floor(a x / d + 1/2), a <= d < 2^128, x < 2^64."""
+    M = (1 << 64) - 1
+    return lib().orc_muldiv_round(a & M, a >> 64, x, d & M, d >> 64)

@@ -491,3 +491,83 @@ def test_ob_progressive_and_invalid():
     for kw in (dict(target=1), dict(target=2), dict(fixed_r=1 << 30, c=2)):
         with pytest.raises(O.OracleError):
             g.estimate(0, 0.05, 0.1, 4, estimator=1, **kw)
+
+
+# --------------------------------------------------------------------------
+# The RTB estimator (App. C): f_v(s) = 1/(n-1) sum_z sigma_sz(v) / sigma_sz
+# from one full search and a backward dependency accumulation; every term
+# rounded to 2^-32 units.
+# --------------------------------------------------------------------------
+def test_muldiv_round():
+    rng = np.random.default_rng(5)
+    cases = [(0, 5, 1), (1, 1, 2), (1, 3, 2), (3, 1, 6), ((1 << 64) - 1, (1 << 64) - 1, (1 << 64) - 1),
+             ((1 << 127), (1 << 64) - 1, (1 << 128) - 1), ((1 << 128) - 2, 12345, (1 << 128) - 1)]
+    for _ in range(3000):
+        bits = int(rng.integers(1, 129))
+        d = (int(rng.integers(1, 1 << 62)) << max(bits - 62, 0)) | 1
+        d = min(d, (1 << 128) - 1)
+        a = d * int(rng.integers(0, 1 << 30)) // (1 << 30)
+        x = int(rng.integers(0, 1 << 63)) >> int(rng.integers(0, 63))
+        cases.append((a, x, d))
+    for a, x, d in cases:
+        assert O.muldiv_round(a, x, d) == (2 * a * x + d) // (2 * d), (a, x, d)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_rtb_values_against_bruteforce(seed):
+    """Every source of random tiny graphs, every optimality: the oracle's
+    2^-32-unit value of f_v(s) is within 64 units (1.5e-8) of the exact
+    rational from the brute-force optimal walk sets."""
+    n = 6
+    u, v, t = synth.random_tiny(n, 18, t_hi=5, seed=6000 + seed, self_loops=True)
+    edges = BF.dedupe(u, v, t)
+    g = O.Graph(u, v, t, n=n)
+    seen = set()
+    for i in range(200):
+        s = O.uniform64(n, 77, i, 0)
+        if s in seen:
+            continue
+        seen.add(s)
+        sets = BF.optimal_sets(edges, n, s)
+        for opt in (0, 1, 2):
+            want = [Fraction(0)] * n
+            for z, d in sets.items():
+                lst = d[opt]
+                if not lst:
+                    continue
+                for vs, _ in lst:
+                    for x in set(vs[1:-1]):
+                        want[x] += Fraction(1, len(lst) * (n - 1))
+            q = g.rtb_values(opt, 77, i)
+            for x in range(n):
+                assert abs(Fraction(int(q[x]), 1 << 32) - want[x]) <= Fraction(64, 1 << 32), (s, opt, x)
+        if len(seen) == n:
+            break
+    assert len(seen) == n
+
+
+@pytest.mark.parametrize("opt", [0, 1, 2])
+def test_rtb_estimates_within_hoeffding(opt):
+    """E[f_v(s)] over a uniform source is b_v: fixed-r RTB estimates against
+    brute-force exact betweenness, and the hit sums recounted from the
+    per-sample values."""
+    u, v, t = synth.random_tiny(7, 22, t_hi=6, seed=4300)
+    edges = BF.dedupe(u, v, t)
+    g = O.Graph(u, v, t, n=7)
+    r, seed = 8000, 4
+    est, hits, info = g.estimate(opt, 0.05, 0.1, seed, fixed_r=r, estimator=2, c=5)
+    exact = np.array([float(x) for x in BF.exact_bc(edges, 7, opt)])
+    assert np.abs(est - exact).max() <= math.sqrt(math.log(2 * 7 / 1e-3) / (2 * r))
+    tot = np.zeros(7, dtype=object)
+    for i in range(r):
+        tot += g.rtb_values(opt, seed, i).astype(object)
+    assert [int(x) for x in hits] == list(tot) and info["sum_int_len"] == int(sum(tot))
+
+
+def test_rtb_progressive_and_invalid():
+    u, v, t = synth.uniform_small(n=50, m=700, seed=9)
+    g = O.Graph(u, v, t, n=50)
+    est, hits, info = g.estimate(2, 0.05, 0.1, 4, estimator=2)
+    assert info["r"] >= info["s1"] and (info["xi"] <= 0.05 or info["r"] >= info["omega"])
+    with pytest.raises(O.OracleError):
+        g.estimate(0, 0.05, 0.1, 4, estimator=2, target=1)
