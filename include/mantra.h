@@ -78,7 +78,12 @@ typedef struct {
                             integers.  With ob, hits_out, info->max_hits (largest sum of the
                             rounded f_v^2), info->rade_num and info->sum_int_len are in units of
                             2^-32, est = hits / (r 2^32), and c * r must stay below 2^31
-                            (MANTRA_E_INVAL for fixed_r, or when omega exceeds it). */
+                            (MANTRA_E_INVAL for fixed_r, or when omega exceeds it).  2 = RTB
+                            (App. C, target 0 only): a sample is a source s drawn uniformly
+                            from the n vertices and every v != s gets f_v(s) = 1/(n-1) sum_z
+                            sigma_sz(v) / sigma_sz, from one untruncated search and a backward
+                            dependency accumulation in which every term is rounded to 2^-32;
+                            units and limits as for ob. */
 } mantra_opts;
 
 /* Diagnostics of one mantra_estimate call. */

@@ -277,6 +277,7 @@ struct Engine {
     char* bfs_mem = nullptr; BfsWs bws{}; int bfs_grid = 0; size_t bfs_smem = 0; uint32_t bfs_n = 0, bfs_A = 0;
     int bfs_grid_big = 0;      // resident 1024-thread CTAs (the regions of the first ones)
     int tick_bfs_nt = 512;     // sh/sfm CTA size of the current tick
+    bool tick_frac = false;    // the tick has an ob or RTB problem on the sh/sfm kernel
     char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; uint32_t pfm_n = 0, pfm_lcap = 0; uint64_t pfm_warps = 0;
     char* pc_mem = nullptr; PfmCtaWs pcws{}; int pc_grid = 0; uint32_t pc_n = 0;
     bool tick_cta = false;   // pfm samples of the current tick run one per CTA
@@ -288,8 +289,8 @@ struct Engine {
     int red_grid = 0;
     // captured ticks, one per pfm kernel (lane / CTA per sample)
     // captured ticks, by (pfm kernel, sh/sfm CTA size)
-    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
-    bool graph_ok[4] = {false, false, false, false};
+    cudaGraphExec_t gexec[8] = {};
+    bool graph_ok[8] = {};
     bool use_graph = true;
     DevPool pool;
 
@@ -316,7 +317,7 @@ struct Engine {
     }
 
     void invalidate_graph() {
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 8; ++k) {
             if (gexec[k]) cudaGraphExecDestroy(gexec[k]);
             gexec[k] = nullptr;
             graph_ok[k] = false;
@@ -462,7 +463,7 @@ struct Engine {
             BfsWs w = bws;
             w.nt = tick_bfs_nt;
             CU(launch_bfs((const Task*)(tab_d + o_tb), (const uint64_t*)(tab_d + o_ub), hdr + 0, work + 0, w,
-                          tick_bfs_nt == 1024 ? bfs_grid_big : bfs_grid, bfs_smem, wide, sa));
+                          tick_bfs_nt == 1024 ? bfs_grid_big : bfs_grid, bfs_smem, wide, tick_frac, sa));
             CU(cudaEventRecord(e_b1, sa));
         }
         if (tick_cta && !wide && pc_mem) {
@@ -487,7 +488,7 @@ struct Engine {
     int launch_tick(bool wide) {
         last_tick_graph = false;
         if (wide || !use_graph) return enqueue(wide);
-        const int gk = (tick_cta ? 1 : 0) + (tick_bfs_nt == 1024 ? 2 : 0);
+        const int gk = (tick_cta ? 1 : 0) + (tick_bfs_nt == 1024 ? 2 : 0) + (tick_frac ? 4 : 0);
         if (!graph_ok[gk]) {
             cudaGraph_t graph = nullptr;
             CU(cudaStreamBeginCapture(sa, cudaStreamCaptureModeThreadLocal));
@@ -577,7 +578,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     if ((rc = E.ensure_tables(std::max<uint32_t>(k, 1))) != MANTRA_OK) return rc;
     uint32_t bn = 0, bA = 0, pn = 0, plc = 0;
     uint64_t pwarps = 0, bsamples = 0;
-    bool any_b = false, any_p = false;
+    bool any_b = false, any_p = false, frac = false;
     for (const TickItem& it : items) {
         if (it.job.opt == MANTRA_PFM) {
             any_p = true; pn = std::max(pn, it.G->n); plc = std::max(plc, it.G->dg.cbound);
@@ -585,8 +586,10 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
         } else {
             any_b = true; bn = std::max(bn, it.G->n); bA = std::max(bA, it.G->A);
             bsamples += it.job.count;
+            frac |= it.job.ob || it.job.rtb;
         }
     }
+    E.tick_frac = frac;
     const bool cta = any_p && !wide && pfm_use_cta();
     if (any_b && (rc = E.ensure_bfs(bn, bA)) != MANTRA_OK) return rc;
     if (any_p && cta && (rc = E.ensure_pfm_cta(pn)) != MANTRA_OK) return rc;
@@ -625,7 +628,8 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
         }
         else { tb[nb] = t; ub[nb + 1] = ub[nb] + it.job.count; ++nb; }
         if (it.reduce) {
-            ri[nr] = ReduceItem{it.job.S, it.job.S64, it.job.ob ? it.job.wsq : it.job.hits, it.job.fam, it.red_c,
+            ri[nr] = ReduceItem{it.job.S, it.job.S64, (it.job.ob || it.job.rtb) ? it.job.wsq : it.job.hits, it.job.fam,
+                                it.red_c,
                                 (long long*)(slot + SLOT_ROWMAX),
                                 (u64*)(slot + SLOT_HMAX)};
             rs[nr + 1] = rs[nr] + it.red_c + 1;
@@ -759,7 +763,7 @@ struct Problem {
     uint64_t fixed_r = 0, boot = 0;
     int dsched = 0, vhat_mode = 0;
     int fam_target = 0;       // mantra_opts.target: 0 nodes, 1 underlying edges, 2 temporal edges
-    int estimator = 0;        // mantra_opts.estimator: 0 trk (App. C), 1 ob (Sec. 4.1)
+    int estimator = 0;        // mantra_opts.estimator: 0 trk (App. C), 1 ob (Sec. 4.1), 2 RTB (App. C)
     double* est_out = nullptr;
     uint64_t* hits_out = nullptr;
     bool out_device = false;
@@ -788,14 +792,14 @@ struct Problem {
         if (out_device && !est_out) return MANTRA_E_INVAL;
         if (vhat_mode != 0 && vhat_mode != 1) return MANTRA_E_INVAL;
         if (fam_target < 0 || fam_target > 2) return MANTRA_E_INVAL;
-        if (estimator < 0 || estimator > 1 || (estimator == 1 && fam_target != 0)) return MANTRA_E_INVAL;
-        if (estimator == 1 && !ob_r_ok(fixed_r)) return MANTRA_E_INVAL;
+        if (estimator < 0 || estimator > 2 || (estimator != 0 && fam_target != 0)) return MANTRA_E_INVAL;
+        if (estimator != 0 && !ob_r_ok(fixed_r)) return MANTRA_E_INVAL;
         return MANTRA_OK;
     }
 
-    // ob sums are in units of 2^-32 (f_v carried as the nearest multiple):
-    // |N_R| <= c r 2^32 must fit int64, so c r < 2^31.
-    double scale() const { return estimator == 1 ? 4294967296.0 : 1.0; }
+    // ob and RTB sums are in units of 2^-32 (f_v carried as the nearest
+    // multiple): |N_R| <= c r 2^32 must fit int64, so c r < 2^31.
+    double scale() const { return estimator != 0 ? 4294967296.0 : 1.0; }
     bool ob_r_ok(uint64_t rr) const { return (double)rr * (double)c < 2147483648.0; }
 
     // Size F of the estimated family (App. A for the edge families).
@@ -804,7 +808,7 @@ struct Problem {
     // bytes of device state held while the problem runs (admission footprint)
     size_t footprint() const {
         const size_t f = std::max<uint32_t>(family(), 1);
-        if (estimator == 1) return al256(f * 8) * 3 + al256((size_t)c * f * 8) + al256(8 * 4096);
+        if (estimator != 0) return al256(f * 8) * 3 + al256((size_t)c * f * 8) + al256(8 * 4096);
         return al256(f * 8) * 2 + al256((size_t)c * f * 4) + al256(8 * 4096);
     }
 
@@ -823,14 +827,14 @@ struct Problem {
     int start(Engine& E) {
         t0 = now_s();
         const size_t f = std::max<uint32_t>(family(), 1);
-        b_hits = f * 8; b_S = (size_t)c * f * (estimator == 1 ? 8 : 4); b_est = f * 8;
+        b_hits = f * 8; b_S = (size_t)c * f * (estimator != 0 ? 8 : 4); b_est = f * 8;
         hits = (u64*)E.pool.get(b_hits);
         S = (int*)E.pool.get(b_S);
         est = out_device ? nullptr : (double*)E.pool.get(b_est);
         if (!hits || !S || (!out_device && !est)) return MANTRA_E_NOMEM;
         CU(cudaMemsetAsync(hits, 0, b_hits, E.sa));
         CU(cudaMemsetAsync(S, 0, b_S, E.sa));
-        if (estimator == 1) {
+        if (estimator != 0) {
             b_wsq = f * 8;
             wsq = (u64*)E.pool.get(b_wsq);
             if (!wsq) return MANTRA_E_NOMEM;
@@ -858,7 +862,7 @@ struct Problem {
         j = Job{};
         j.seed = seed; j.opt = opt; j.c = c; j.hits = hits;
         j.target = fam_target; j.fam = family();
-        j.ob = estimator == 1; j.wsq = wsq;
+        j.ob = estimator == 1; j.rtb = estimator == 2; j.wsq = wsq;
         const uint64_t left = remaining();
         j.i0 = pos; j.count = std::min(left, quota);
         if (phase == BOOT) {
@@ -866,7 +870,7 @@ struct Problem {
             it->red_c = 0;
         } else {
             j.dom_pair = DOM_PAIR; j.dom_path = DOM_PATH;
-            if (j.ob) { j.S = nullptr; j.S64 = (long long*)S; }
+            if (estimator != 0) { j.S = nullptr; j.S64 = (long long*)S; }
             else { j.S = S; j.S64 = nullptr; }
             it->red_c = c;
         }
@@ -895,7 +899,7 @@ struct Problem {
             if (v0 == 0.0 || rho == 0.0) { v0 = 1.0 / (double)sb; rho = std::max(rho, v0); }
             const double om = std::ceil(omega_closed_form(v0, rho, eps, delta / 2.0));
             if (!(om <= (double)RMAX)) return MANTRA_E_INVAL;
-            if (estimator == 1 && !ob_r_ok((uint64_t)std::max(om, 1.0))) return MANTRA_E_INVAL;
+            if (estimator != 0 && !ob_r_ok((uint64_t)std::max(om, 1.0))) return MANTRA_E_INVAL;
             omega = std::max<uint64_t>(1, (uint64_t)om);
             const double d1 = delta_of_round(delta, 1, dsched);
             if (sb >= omega || xi_given_R(0.0, v0, d1, (double)omega) > eps) s1 = omega;

@@ -119,7 +119,7 @@ extern "C" int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt
     ws.stride = region;
     char* ub = scratch + kUnitOff;
     if (launch_bfs((const Task*)(scratch + kTaskOff), (const uint64_t*)ub, (const uint32_t*)(ub + 16), (u64*)(ub + 24),
-                   ws, grid, in_smem ? smem : 0, false, st) != cudaSuccess)
+                   ws, grid, in_smem ? smem : 0, false, false, st) != cudaSuccess)
         return MANTRA_E_CUDA;
 
     u64 h[9];

@@ -37,10 +37,9 @@ constexpr int WALK_K = 2;         // edge windows with loads in flight per warp 
 // of sigma * dl (a path visits v once); then every internal v gets its ob
 // value.  dl: the (free) running-sum array, indexed by frontier position;
 // acc: per-vertex sums (zero on entry and exit); VB: vertex bitmap (zero on
-// entry and exit); tl: n entries.  Kept out of line so that the search's
-// register allocation does not carry it.
+// entry and exit); tl: n entries.
 template <bool WIDE, int BFS_NT>
-__device__ __noinline__ void bfs_ob_update(const DevGraph& g, const Job& job, uint32_t z, uint32_t d, uint32_t first,
+__device__ __forceinline__ void bfs_ob_update(const DevGraph& g, const Job& job, uint32_t z, uint32_t d, uint32_t first,
                                            u128 sigma, const uint32_t* rade, const uint32_t* F, const uint32_t* lev,
                                            const uint32_t* N, const typename SigOps<WIDE>::T* sig,
                                            typename SigOps<WIDE>::T* dl, typename SigOps<WIDE>::T* acc, uint32_t* VB,
@@ -116,10 +115,164 @@ __device__ __noinline__ void bfs_ob_update(const DevGraph& g, const Job& job, ui
     for (uint32_t p = tid; p < T; p += BFS_NT) acc[tl[p]] = (Sig)0;
 }
 
-// BFS_NT threads per CTA, 1024 / BFS_NT CTAs per SM at 64 registers.
+// RTB update of one sample (App. C), all threads of the CTA, after a full
+// search from s with levels 1 .. D in F.  The endpoint states of a vertex v
+// are its states on its first level d_v (sfm: the earliest of them); eps(b) =
+// sigma(b) / sigma_{s,v_b} for an endpoint b.  From level D down, every state
+// b with X(b) = eps(b) + delta(b) > 0 adds round(sigma(a) X(b) / sigma(b)) to
+// delta(a) of each DAG predecessor a; f_v(s) = round(sum of delta over v's
+// states / (n-1)), all in 2^-32 units.  dl: per frontier position (the free
+// running-sum array); sv: sigma_{s,v} (zero on entry and exit); dsum:
+// per-vertex sums (zero on entry and exit); dv: first level per vertex (n
+// entries, overwritten); VB: vertex bitmap (zero on entry and exit); tl: n
+// entries.
 template <bool WIDE, int BFS_NT>
+__device__ __forceinline__ void bfs_rtb_update(const DevGraph& g, const Job& job, uint32_t s, uint64_t i, uint32_t D,
+                                            uint32_t* rade, const uint32_t* F, const uint32_t* lev,
+                                            const typename SigOps<WIDE>::T* sig, u64* dl, typename SigOps<WIDE>::T* sv,
+                                            u64* dsum, uint32_t* dv, uint32_t* VB, uint32_t* tl, uint32_t* sh_nt) {
+    typedef typename SigOps<WIDE>::T Sig;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t n = g.n;
+    const bool sfm = job.opt == 1;
+    for (uint32_t v = tid; v < n; v += BFS_NT) dv[v] = NONE;
+    if (tid == 0) {
+        *sh_nt = 0;
+        uint32_t w4[4];
+        philox_block(job.seed, i, DOM_RADE, 0, w4);
+        rade[0] = w4[0]; rade[1] = w4[1]; rade[2] = w4[2]; rade[3] = w4[3];
+    }
+    __syncthreads();
+    for (uint32_t k = 1; k <= D; ++k)
+        for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
+            const uint32_t v = g.slot_v[F[p]];
+            if (v != s) atomicMin(dv + v, k);
+        }
+    __syncthreads();
+    // a level lists a vertex's states together, in time order
+    auto is_end = [&](uint32_t p, uint32_t k, uint32_t v) -> bool {
+        if (v == s || dv[v] != k) return false;
+        return !sfm || p == lev[k] || g.slot_v[F[p - 1]] != v;
+    };
+    for (uint32_t k = 1; k <= D; ++k)
+        for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
+            const uint32_t a = F[p], v = g.slot_v[a];
+            if (is_end(p, k, v)) SigOps<WIDE>::atomic_add(sv + v, sig[a]);
+        }
+    __syncthreads();
+    auto eps_of = [&](uint32_t p, uint32_t k, uint32_t a, uint32_t v) -> u64 {
+        return is_end(p, k, v) ? ob_q(SigOps<WIDE>::wide(sig[a]), SigOps<WIDE>::wide(ldcg_sig(sv + v))) : 0ull;
+    };
+    for (uint32_t k = 1; k <= D; ++k)
+        for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
+            const uint32_t a = F[p];
+            dl[p] = eps_of(p, k, a, g.slot_v[a]);
+        }
+    __syncthreads();
+    for (uint32_t k = D; k >= 2; --k) {
+        const uint32_t* Fp = F + lev[k - 1];
+        const uint32_t Lp = lev[k] - lev[k - 1];
+        for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
+            const u64 X = __ldcg(reinterpret_cast<const unsigned long long*>(dl + p));
+            if (!X) continue;
+            const uint32_t b = F[p], tb = g.slot_t[b];
+            const u128 sb = SigOps<WIDE>::wide(sig[b]);
+            for (uint32_t e = g.slot_in[b]; e < g.slot_in[b + 1]; ++e) {
+                const uint32_t w = g.in_u[e], w1 = g.slot_ptr[w + 1];
+                for (uint32_t p2 = lower_bound_u32(Fp, 0, Lp, g.slot_ptr[w]); p2 < Lp; ++p2) {
+                    const uint32_t a2 = Fp[p2];
+                    if (a2 >= w1 || g.slot_t[a2] >= tb) break;
+                    const u64 term = muldiv_round(SigOps<WIDE>::wide(sig[a2]), X, sb);
+                    if (term) atomicAdd(dl + lev[k - 1] + p2, term);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // per-vertex dependency sums (X minus the endpoint share)
+    for (uint32_t k = 1; k <= D; ++k)
+        for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
+            const uint32_t a = F[p], v = g.slot_v[a];
+            if (v == s) continue;
+            const u64 d = __ldcg(reinterpret_cast<const unsigned long long*>(dl + p)) - eps_of(p, k, a, v);
+            if (!d) continue;
+            atomicAdd(dsum + v, d);
+            const uint32_t bit = 1u << (v & 31);
+            if (!(atomicOr(VB + (v >> 5), bit) & bit)) tl[atomicAdd(sh_nt, 1u)] = v;
+        }
+    __syncthreads();
+    const uint32_t T = *sh_nt;
+    u64 my_sum = 0;
+    for (uint32_t p = tid; p < T; p += BFS_NT) {
+        const uint32_t v = tl[p];
+        const uint64_t q = muldiv_round(1, __ldcg(reinterpret_cast<const unsigned long long*>(dsum + v)), n - 1);
+        dsum[v] = q;
+        atomicAnd(VB + (v >> 5), ~(1u << (v & 31)));
+        my_sum += q;
+    }
+    __syncthreads();
+    const uint32_t rows = 2 + (job.S64 ? job.c : 0);
+    for (uint32_t it = tid; it < T * rows; it += BFS_NT) {
+        const uint32_t v = tl[it % T];
+        const uint64_t q = dsum[v];
+        if (q) ob_term(job, v, q, it / T, rade);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_sum += __shfl_xor_sync(0xFFFFFFFFu, my_sum, o);
+    if (lane == 0 && my_sum) atomicAdd(job.ctr + C_SUMINT, my_sum);
+    __syncthreads();
+    for (uint32_t p = tid; p < T; p += BFS_NT) dsum[tl[p]] = 0ull;
+    for (uint32_t v = tid; v < n; v += BFS_NT)
+        if (dv[v] != NONE) sv[v] = (Sig)0;
+}
+
+// Per-sample inputs of the fractional updates (ob, RTB) and the CTA's region
+// arrays, kept in shared memory so that the out-of-line call carries two
+// arguments.
+struct FracCtx {
+    const Task* task;
+    const BfsWs* ws;
+    uint32_t s, z, D, first, nt;
+    uint64_t i;
+    u128 sigma;
+    uint32_t rade[4];
+};
+
+// The ob (mode 1) or RTB (mode 2) update of the CTA's current sample; the
+// region arrays are re-derived from the workspace.  Out of line, so that the
+// search's register allocation does not carry it.
+template <bool WIDE, int BFS_NT>
+__device__ __noinline__ void bfs_frac_update(int mode, FracCtx* x) {
+    typedef typename SigOps<WIDE>::T Sig;
+    const DevGraph& g = x->task->g;
+    const Job& job = x->task->job;
+    const BfsWs& ws = *x->ws;
+    char* region = ws.base + (size_t)blockIdx.x * ws.stride;
+    const uint32_t* F = reinterpret_cast<const uint32_t*>(region + ws.o_f);
+    const uint32_t* lev = reinterpret_cast<const uint32_t*>(region + ws.o_lev);
+    const uint32_t* N = reinterpret_cast<const uint32_t*>(region + ws.o_nbits);
+    uint32_t* seg_b = reinterpret_cast<uint32_t*>(region + ws.o_segb);
+    uint32_t* seg_u = reinterpret_cast<uint32_t*>(region + ws.o_segu);
+    uint32_t* VB = reinterpret_cast<uint32_t*>(region + ws.o_vb);
+    Sig* sig = reinterpret_cast<Sig*>(region + ws.o_sig);
+    Sig* Fc = reinterpret_cast<Sig*>(region + ws.o_fc);
+    Sig* acc = reinterpret_cast<Sig*>(region + ws.o_acc);
+    u64* acc2 = reinterpret_cast<u64*>(region + ws.o_acc2);
+    if (mode == 1)
+        bfs_ob_update<WIDE, BFS_NT>(g, job, x->z, x->D, x->first, x->sigma, x->rade, F, lev, N, sig, Fc, acc, VB,
+                                    seg_u, &x->nt);
+    else
+        bfs_rtb_update<WIDE, BFS_NT>(g, job, x->s, x->i, x->D, x->rade, F, lev, sig, reinterpret_cast<u64*>(Fc), acc,
+                                     acc2, seg_b, VB, seg_u, &x->nt);
+}
+
+// BFS_NT threads per CTA, 1024 / BFS_NT CTAs per SM at 64 registers.  FRAC:
+// the instantiation that also runs the ob and RTB updates (a tick with such a
+// problem launches it); the others report those jobs as a consistency error.
+template <bool WIDE, int BFS_NT, bool FRAC>
 __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks, const uint64_t* unit_start,
-                                                   const uint32_t* ntasks_p, u64* work, const BfsWs ws) {
+                                                   const uint32_t* ntasks_p, u64* work,
+                                                   const __grid_constant__ BfsWs ws) {
     typedef typename SigOps<WIDE>::T Sig;
     constexpr int BFS_NW = BFS_NT / 32;
     constexpr uint32_t FCAP = BFS_NT * 4;   // frontier states whose times and running sums fit in shared memory
@@ -140,6 +293,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
     uint32_t* VB = reinterpret_cast<uint32_t*>(region + ws.o_vb);   // vertex bitmap (stats)
     u64* segmap = reinterpret_cast<u64*>(region + ws.o_segmap);      // vertex -> (level stamp, frontier segment)
     Sig* acc = reinterpret_cast<Sig*>(region + ws.o_acc);             // ob: through counts per vertex
+    u64* acc2 = reinterpret_cast<u64*>(region + ws.o_acc2);           // RTB: dependency sums per vertex
     uint32_t* stamp_p = reinterpret_cast<uint32_t*>(region + ws.o_stamp);
 
     extern __shared__ uint32_t dyn_smem[];
@@ -160,7 +314,8 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
     __shared__ uint32_t sh_rade[4];
     __shared__ uint32_t sh_d, sh_len;
     __shared__ u128 sh_sigma;
-    __shared__ uint32_t sh_first, sh_nt;
+    __shared__ uint32_t sh_first;
+    __shared__ FracCtx sh_fx;
     __shared__ uint32_t cs_off[BFS_NT + 1], cs_first[BFS_NT], cs_fb[BFS_NT], cs_fe[BFS_NT];   // range table
     __shared__ uint32_t sh_stamp, sh_wrap;
     __shared__ u64 sh_fcmax;
@@ -230,18 +385,19 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
 
         uint32_t s, z;
         bool ok;
-        if (job.stats) {
+        if (job.stats || job.rtb) {       // a source only: Algorithm 2, or the RTB sample space V
             uint64_t x;
-            ok = draw_below64(n, job.seed, i, DOM_STATS, &x);
+            ok = draw_below64(n, job.seed, i, job.stats ? DOM_STATS : job.dom_pair, &x);
             s = (uint32_t)x; z = NONE;
         } else {
             ok = draw_pair(n, job.seed, i, job.dom_pair, &s, &z);
         }
         if (!ok) { if (tid == 0) set_status(job.status, ST_RNG); s = 0; z = 1; }
         const bool stats = job.stats != 0;
-        const uint32_t tz = stats ? NONE : g.tmax_in[z];
+        const bool full = stats || job.rtb;   // untruncated search (no target)
+        const uint32_t tz = full ? NONE : g.tmax_in[z];
         bool live = ok && (g.out_ptr[s + 1] > g.out_ptr[s]);
-        if (!stats && (g.slot_ptr[z + 1] == g.slot_ptr[z])) live = false;   // z has no in-edges
+        if (!full && (g.slot_ptr[z + 1] == g.slot_ptr[z])) live = false;   // z has no in-edges
 
         // ---------------- level loop ----------------
         uint32_t k = 0;
@@ -360,7 +516,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             if (sh_ovf) break;
 
             // ---- pull: does level k reach z? ----
-            if (!stats) {
+            if (!full) {
                 const uint32_t zs = g.slot_ptr[z], ze = g.slot_ptr[z + 1];
                 const uint32_t e_lo = g.slot_in[zs], e_hi = g.slot_in[ze];
                 const uint32_t* const g_in_u = g.in_u;
@@ -692,10 +848,23 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             }
         }
 
-        // ---------------- ob: the update of Sec. 4.1 (block-uniform condition) ----------------
-        if (job.ob && job.hits && found && !sh_ovf && !sh_err && sh_d >= 2)
-            bfs_ob_update<WIDE, BFS_NT>(g, job, z, sh_d, sh_first, sh_sigma, sh_rade, F, lev, N, sig, Fc, acc, VB,
-                                        seg_u, &sh_nt);
+        // ---------------- ob (Sec. 4.1) and RTB (App. C) updates (block-uniform conditions) ----------------
+        if constexpr (!FRAC) {
+            if ((job.ob || job.rtb) && tid == 0) set_status(job.status, ST_CHECK);
+        } else {
+            const int mode = (job.ob && job.hits && found && !sh_ovf && !sh_err && sh_d >= 2) ? 1
+                           : (job.rtb && job.hits && live && !sh_ovf && k >= 2) ? 2 : 0;
+            if (mode) {
+                if (tid == 0) {
+                    FracCtx& x = sh_fx;
+                    x.task = &sh_task; x.ws = &ws;
+                    x.s = s; x.z = z; x.i = i; x.D = mode == 1 ? sh_d : k; x.first = sh_first; x.sigma = sh_sigma;
+                    x.rade[0] = sh_rade[0]; x.rade[1] = sh_rade[1]; x.rade[2] = sh_rade[2]; x.rade[3] = sh_rade[3];
+                }
+                __syncthreads();
+                bfs_frac_update<WIDE, BFS_NT>(mode, &sh_fx);
+            }
+        }
 
         // ---------------- cleanup: sigma of every touched slot, bitmaps ----------------
         for (uint32_t w = tid; w < words; w += BFS_NT) {
@@ -739,6 +908,7 @@ size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws) {
     ws->o_segmap = o;  o = al(o + (size_t)n * 8);
     ws->o_stamp = o;   o = al(o + 4);
     ws->o_acc = o;     o = al(o + (size_t)n * 16);
+    ws->o_acc2 = o;    o = al(o + (size_t)n * 8);
     ws->o_nbits = o;   o = al(o + (size_t)ws->bits_words * 4);
     ws->n_cap = n;
     ws->o_bits = o;
@@ -752,13 +922,15 @@ size_t bfs_smem_bytes(uint32_t A) { return (size_t)((A + 31) / 32) * 4; }
 // Static shared memory of the nt-thread kernels (range table, task copy,
 // level scratch).
 size_t bfs_static_smem(int nt) {
-    cudaFuncAttributes a{}, b{};
-    const cudaError_t e1 = nt == 1024 ? cudaFuncGetAttributes(&a, k_bfs<false, 1024>)
-                                      : cudaFuncGetAttributes(&a, k_bfs<false, 512>);
-    const cudaError_t e2 = nt == 1024 ? cudaFuncGetAttributes(&b, k_bfs<true, 1024>)
-                                      : cudaFuncGetAttributes(&b, k_bfs<true, 512>);
-    if (e1 != cudaSuccess || e2 != cudaSuccess) return 96 * 1024;
-    return std::max(a.sharedSizeBytes, b.sharedSizeBytes);
+    cudaFuncAttributes a{}, b{}, c{};
+    const cudaError_t e1 = nt == 1024 ? cudaFuncGetAttributes(&a, k_bfs<false, 1024, false>)
+                                      : cudaFuncGetAttributes(&a, k_bfs<false, 512, false>);
+    const cudaError_t e2 = nt == 1024 ? cudaFuncGetAttributes(&b, k_bfs<true, 1024, true>)
+                                      : cudaFuncGetAttributes(&b, k_bfs<true, 512, true>);
+    const cudaError_t e3 = nt == 1024 ? cudaFuncGetAttributes(&c, k_bfs<false, 1024, true>)
+                                      : cudaFuncGetAttributes(&c, k_bfs<false, 512, true>);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return 96 * 1024;
+    return std::max(std::max(a.sharedSizeBytes, b.sharedSizeBytes), c.sharedSizeBytes);
 }
 
 // Raises (never lowers) the kernels' dynamic shared-memory limit, so callers
@@ -768,8 +940,9 @@ cudaError_t bfs_configure(size_t smem) {
     static size_t configured = 0;
     std::lock_guard<std::mutex> lock(mu);
     if (smem <= configured) return cudaSuccess;
-    const void* ks[4] = {(const void*)k_bfs<false, 512>, (const void*)k_bfs<true, 512>,
-                         (const void*)k_bfs<false, 1024>, (const void*)k_bfs<true, 1024>};
+    const void* ks[6] = {(const void*)k_bfs<false, 512, false>, (const void*)k_bfs<false, 512, true>,
+                         (const void*)k_bfs<true, 512, true>, (const void*)k_bfs<false, 1024, false>,
+                         (const void*)k_bfs<false, 1024, true>, (const void*)k_bfs<true, 1024, true>};
     for (const void* k : ks) {
         const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -779,18 +952,21 @@ cudaError_t bfs_configure(size_t smem) {
 }
 
 cudaError_t bfs_blocks_per_sm(int nt, size_t smem, int* out) {
-    return nt == 1024 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bfs<false, 1024>, 1024, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bfs<false, 512>, 512, smem);
+    return nt == 1024 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bfs<false, 1024, false>, 1024, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bfs<false, 512, false>, 512, smem);
 }
 
 cudaError_t launch_bfs(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
-                       const BfsWs& ws, int grid, size_t smem, bool wide, cudaStream_t st) {
+                       const BfsWs& ws, int grid, size_t smem, bool wide, bool frac, cudaStream_t st) {
+    // the 128-bit re-run always takes the FRAC instantiation
     if (ws.nt == 1024) {
-        if (wide) k_bfs<true, 1024><<<grid, 1024, smem, st>>>(tasks, unit_start, ntasks, work, ws);
-        else k_bfs<false, 1024><<<grid, 1024, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        if (wide) k_bfs<true, 1024, true><<<grid, 1024, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else if (frac) k_bfs<false, 1024, true><<<grid, 1024, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else k_bfs<false, 1024, false><<<grid, 1024, smem, st>>>(tasks, unit_start, ntasks, work, ws);
     } else {
-        if (wide) k_bfs<true, 512><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
-        else k_bfs<false, 512><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        if (wide) k_bfs<true, 512, true><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else if (frac) k_bfs<false, 512, true><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else k_bfs<false, 512, false><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
     }
     return cudaGetLastError();
 }

@@ -85,22 +85,23 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
         uint32_t s = 0, z = 1;
         bool ok = true;
         if (have) {
-            if (stats) {
+            if (stats || job.rtb) {
                 uint64_t x;
-                ok = draw_below64(n, job.seed, i, DOM_STATS, &x);
+                ok = draw_below64(n, job.seed, i, stats ? DOM_STATS : job.dom_pair, &x);
                 s = (uint32_t)x; z = NONE;
             } else {
                 ok = draw_pair(n, job.seed, i, job.dom_pair, &s, &z);
             }
-            if (!ok) { set_status(job.status, ST_RNG); s = 0; z = 1; }
+            if (!ok) { set_status(job.status, ST_RNG); s = 0; z = (stats || job.rtb) ? NONE : 1; }
         }
+        const bool full = stats || job.rtb;   // a source only, untruncated scan
         bool live = have && ok && g.out_ptr[s + 1] > g.out_ptr[s];
-        if (!stats && live && g.slot_ptr[z + 1] == g.slot_ptr[z]) live = false;
+        if (!full && live && g.slot_ptr[z + 1] == g.slot_ptr[z]) live = false;
         const uint32_t ts = live ? g.tmin_out[s] : NONE;
-        const uint32_t te = live ? (stats ? NONE - 1 : g.tmax_in[z]) : 0;
+        const uint32_t te = live ? (full ? NONE - 1 : g.tmax_in[z]) : 0;
 
         for (uint32_t v = 0; v < n; ++v) fa[(size_t)v * 32] = NONE;
-        if (job.ob) for (uint32_t v = 0; v < n; ++v) dl[(size_t)v * 32] = (Sig)0;
+        if (job.ob || job.rtb) for (uint32_t v = 0; v < n; ++v) dl[(size_t)v * 32] = (Sig)0;
         if (live) { fa[(size_t)s * 32] = 0u; sig[(size_t)s * 32] = (Sig)1; hop[(size_t)s * 32] = 0u; }
         __syncwarp();
 
@@ -311,10 +312,47 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
             if (sum) atomicAdd(job.ctr + C_SUMINT, sum);
         }
 
+        // ---------------- RTB (App. C), one lane per sample ----------------
+        // dependencies over the whole prefix-foremost DAG by a backward walk of
+        // the stream: an edge (w, x, fa(x)), fa(w) < fa(x), w != s, adds
+        // round(sigma(w) (1 + delta(x)) / sigma(x)) to delta(w) (x's edges out
+        // come later, so delta(x) is final); dl holds delta in 2^-32 units
+        if (job.rtb && job.hits && have && !ovf && live) {
+            uint32_t w4[4];
+            philox_block(job.seed, i, DOM_RADE, 0, w4);
+            uint32_t nt = 0;
+            uint32_t e = g.m;
+            const uint32_t e0 = lower_bound_u32(st_t, 0, g.m, ts);
+            while (e > e0) {
+                --e;
+                const uint32_t x = st_v[e], t = st_t[e];
+                if (fa[(size_t)x * 32] != t + 1u) continue;
+                const uint32_t w = st_u[e];
+                if (w == s || fa[(size_t)w * 32] > t) continue;
+                const uint64_t X = (1ull << 32) + (uint64_t)dl[(size_t)x * 32];
+                const uint64_t term = muldiv_round(SigOps<WIDE>::wide(sig[(size_t)w * 32]), X,
+                                                   SigOps<WIDE>::wide(sig[(size_t)x * 32]));
+                if (!term) continue;
+                if (dl[(size_t)w * 32] == (Sig)0) path[nt++] = w;
+                dl[(size_t)w * 32] += (Sig)term;
+            }
+            u64 sum = 0;
+            for (uint32_t k = 0; k < nt; ++k) {
+                const uint32_t w = path[k];
+                const uint64_t q = muldiv_round(1, (uint64_t)dl[(size_t)w * 32], n - 1);
+                dl[(size_t)w * 32] = (Sig)0;
+                if (!q) continue;
+                sum += q;
+                const uint32_t rows = 2 + (job.S64 ? job.c : 0);
+                for (uint32_t row = 0; row < rows; ++row) ob_term(job, w, q, row, w4);
+            }
+            if (sum) atomicAdd(job.ctr + C_SUMINT, sum);
+        }
+
         // ---------------- path draw, one lane per sample ----------------
         uint32_t len = 0, err = 0;
         u128 sigma_sz = 0;
-        if (have && !ovf && live && fz != NONE && !job.ob) {
+        if (have && !ovf && live && fz != NONE && !job.ob && !job.rtb) {
             const Sig tot = sig[(size_t)z * 32];
             sigma_sz = SigOps<WIDE>::wide(tot);
             u128 x;

@@ -202,16 +202,17 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
         const uint64_t i = job.idx_list ? job.idx_list[q] : job.i0 + q;
         uint32_t s, z;
         bool ok;
-        if (stats) {
+        const bool full = stats || job.rtb;   // a source only, untruncated search
+        if (full) {
             uint64_t x;
-            ok = draw_below64(n, job.seed, i, DOM_STATS, &x);
+            ok = draw_below64(n, job.seed, i, stats ? DOM_STATS : job.dom_pair, &x);
             s = (uint32_t)x; z = NONE;
         } else {
             ok = draw_pair(n, job.seed, i, job.dom_pair, &s, &z);
         }
-        if (!ok) { if (tid == 0) set_status(job.status, ST_RNG); s = 0; z = 1; }
+        if (!ok) { if (tid == 0) set_status(job.status, ST_RNG); s = 0; z = full ? NONE : 1; }
         bool live = ok && g.out_ptr[s + 1] > g.out_ptr[s];
-        if (!stats && live && g.slot_ptr[z + 1] == g.slot_ptr[z]) live = false;
+        if (!full && live && g.slot_ptr[z + 1] == g.slot_ptr[z]) live = false;
         const uint32_t* const out_ptr = g.out_ptr;
         const uint32_t* const out_t = g.out_t;
         const uint32_t* const out_v = g.out_v;
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
         __syncthreads();
 
         // ---- earliest arrivals ----
-        uint32_t bound = live ? (stats ? NONE - 1u : g.tmax_in[z]) : 0u;
+        uint32_t bound = live ? (full ? NONE - 1u : g.tmax_in[z]) : 0u;
         while (live) {
             const uint32_t L = compact(nwords, Fl);
             if (L == 0) break;
@@ -269,12 +270,12 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                     if (sl < atomicMin(fsl + v, sl)) atomicOr(NB + (v >> 5), 1u << (v & 31));
                 });
             }
-            if (!stats) {
+            if (!full) {
                 const uint32_t fz = ldv<FA_SMEM>(fsl + z);
                 if (fz != NONE) bound = min(bound, __ldg(slot_t + fz));
             }
         }
-        const bool reached = live && (stats || ldv<FA_SMEM>(fsl + z) != NONE);
+        const bool reached = live && (full || ldv<FA_SMEM>(fsl + z) != NONE);
 
         // fa' of every vertex, for the DAG tests of in-edges
         if (live) {
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
         // unreached), not into s
         if (tid == 0 && live) {
             const uint32_t ts = g.tmin_out[s];
-            const uint32_t te = stats ? NONE - 1u : (reached ? bound : g.tmax_in[z]);
+            const uint32_t te = full ? NONE - 1u : (reached ? bound : g.tmax_in[z]);
             if (ts <= te) {
                 const uint32_t a = lower_bound_u32(g.st_t, 0, g.m, ts), b = upper_bound_u32(g.st_t, a, g.m, te);
                 const uint32_t s0 = g.slot_ptr[s], s1 = g.slot_ptr[s + 1];
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                 philox_block(job.seed, i, DOM_RADE, 0, w4);
                 sh_rade[0] = w4[0]; sh_rade[1] = w4[1]; sh_rade[2] = w4[2]; sh_rade[3] = w4[3];
             }
-        } else if (reached && !sh_ovf && wid == 0) {
+        } else if (reached && !sh_ovf && wid == 0 && !job.rtb) {
             const u64 tot = __ldcg(sig + z);
             u128 x = 0;
             uint32_t rng_ok = 1;
@@ -485,6 +486,59 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                 const u64 x = __ldcg(dl + v);
                 if (!x) continue;
                 const uint64_t q = ob_q((u128)__ldcg(sig + v) * x, (u128)sh_sigma);
+                sig[v] = q;
+                path[atomicAdd(&sh_nt, 1u)] = v;
+                my_sum += q;
+            }
+            __syncthreads();
+            const uint32_t T = sh_nt, rows = 2 + (job.S64 ? job.c : 0);
+            for (uint32_t it = tid; it < T * rows; it += PC_NT) {
+                const uint32_t v = path[it % T];
+                ob_term(job, v, sig[v], it / T, sh_rade);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) my_sum += __shfl_xor_sync(FULL, my_sum, o);
+            if (lane == 0 && my_sum) atomicAdd(job.ctr + C_SUMINT, my_sum);
+        }
+
+        // ---- RTB (App. C): dependency accumulation over the whole prefix-foremost
+        // DAG in reverse Kahn order: every reached x != s is its own endpoint
+        // (share 1), delta(w) += round(sigma(w) (1 + delta(x)) / sigma(x)) over
+        // DAG edges w -> x, w != s; f_v = round(delta(v) / (n-1)), 2^-32 units ----
+        if (job.rtb && job.hits && reached && !sh_ovf) {
+            for (uint32_t p = tid; p < kb; p += PC_NT) dl[Fl[p]] = 0ull;
+            if (tid == 0) {
+                sh_nt = 0;
+                uint32_t w4[4];
+                philox_block(job.seed, i, DOM_RADE, 0, w4);
+                sh_rade[0] = w4[0]; sh_rade[1] = w4[1]; sh_rade[2] = w4[2]; sh_rade[3] = w4[3];
+            }
+            __syncthreads();
+            for (int r = (int)nr - 1; r >= 0; --r) {
+                const uint32_t p1 = kofs[r + 1];
+                for (uint32_t p = kofs[r] + tid; p < p1; p += PC_NT) {
+                    const uint32_t x = Fl[p];
+                    if (x == s) continue;
+                    const u64 X = (1ull << 32) + __ldcg(dl + x), sx = __ldcg(sig + x);
+                    const uint32_t fv = __ldcg(fat + x), a = ldv<FA_SMEM>(fsl + x);
+                    const uint32_t e1 = __ldg(g.slot_in + a + 1);
+                    for (uint32_t e = __ldg(g.slot_in + a); e < e1; ++e) {
+                        const uint32_t w = __ldg(g.in_u + e);
+                        if (w == s || __ldcg(fat + w) >= fv) continue;
+                        const u64 term = muldiv_round((u128)__ldcg(sig + w), X, (u128)sx);
+                        if (term) atomicAdd(dl + w, term);
+                    }
+                }
+                __syncthreads();
+            }
+            u64 my_sum = 0;
+            for (uint32_t p = tid; p < kb; p += PC_NT) {
+                const uint32_t v = Fl[p];
+                if (v == s) continue;
+                const u64 d = __ldcg(dl + v);
+                if (!d) continue;
+                const uint64_t q = muldiv_round(1, d, n - 1);
+                if (!q) continue;
                 sig[v] = q;
                 path[atomicAdd(&sh_nt, 1u)] = v;
                 my_sum += q;

@@ -79,8 +79,13 @@ struct Job {
     // sigma_sz rounded to nearest (ties up): hits[v] += q, wsq[v] += q^2 / 2^32
     // (rounded the same way), S64[j][v] += lambda_j q.  No path is drawn.
     int ob;
-    u64* wsq;                  // F (ob)
-    long long* S64;            // c*F (ob), or nullptr
+    // RTB estimator (App. C; nodes only): sample i is a source s (uniform over
+    // the n vertices, pair domain); a full search and a backward dependency
+    // accumulation give f_v(s) = 1/(n-1) sum_z sigma_sz(v) / sigma_sz, added
+    // like the ob values (every term in 2^-32 units).
+    int rtb;
+    u64* wsq;                  // F (ob, RTB)
+    long long* S64;            // c*F (ob, RTB), or nullptr
     u64* ctr;                  // C_NCOUNT counters
     uint64_t* ovf_list;        // sample indices whose 64-bit path counts overflowed
     int* status;
@@ -505,6 +510,35 @@ __device__ __forceinline__ uint64_t ob_q(u128 thr, u128 sig) {
     return q;
 }
 
+// floor(a * x / d + 1/2) for 0 <= a <= d (d >= 1), x < 2^64 (the result is at
+// most x + 1): the RTB dependency terms.  A 64-bit a and d take one 128-by-64
+// division; otherwise the 192-bit product is divided by a restoring division
+// over the 64 low quotient positions (the quotient fits 64 bits).
+__device__ __forceinline__ uint64_t muldiv_round(u128 a, uint64_t x, u128 d) {
+    if ((uint64_t)(a >> 64) == 0 && (uint64_t)(d >> 64) == 0) {
+        const u128 p = a * (u128)x;
+        const uint64_t dd = (uint64_t)d;
+        const uint64_t q = (uint64_t)(p / dd), r = (uint64_t)(p - (u128)q * dd);
+        return q + (r >= dd - r ? 1u : 0u);
+    }
+    // p = a * x as (ph : 64 high bits, pl : 128 low bits)
+    const u128 mlo = (u128)(uint64_t)a * x, mhi = (u128)(uint64_t)(a >> 64) * x;
+    const u128 pl = mlo + (mhi << 64);
+    const uint64_t ph = (uint64_t)(mhi >> 64) + (pl < mlo ? 1u : 0u);
+    // partial remainder p >> 64 (< d, as the quotient is below 2^64), then one
+    // low bit of p per quotient position
+    u128 rem = ((u128)ph << 64) | (pl >> 64);
+    uint64_t q = 0;
+    for (int b = 63; b >= 0; --b) {
+        const bool top = (uint64_t)(rem >> 127) != 0;
+        rem = (rem << 1) | (u128)((uint64_t)(pl >> b) & 1u);
+        q <<= 1;
+        if (top || rem >= d) { rem -= d; q |= 1u; }
+    }
+    const bool top = (uint64_t)(rem >> 127) != 0;
+    return q + ((top || (rem << 1) >= d) ? 1u : 0u);
+}
+
 // q^2 / 2^32 rounded to nearest (ties up): the ob value of f^2 (wimpy variance).
 __device__ __forceinline__ uint64_t ob_sq(uint64_t q) { return (uint64_t)(((u128)q * q + (1ull << 31)) >> 32); }
 
@@ -552,7 +586,8 @@ struct BfsWs {
     uint32_t bits_words; // capacity of each bitmap (words): ceil(A_max / 32)
     uint32_t n_cap;      // node capacity of a region
     int nt;              // threads per CTA (512 or 1024)
-    size_t o_acc;        // ob: per-vertex sums of through counts
+    size_t o_acc;        // ob: per-vertex sums of through counts; RTB: sigma_{s,v}
+    size_t o_acc2;       // RTB: per-vertex dependency sums
 };
 
 // Per-warp scratch of the pfm search kernel.
@@ -585,7 +620,7 @@ cudaError_t bfs_configure(size_t smem);
 // task_of_unit(unit_start, *ntasks, u); the first unused unit ends a CTA/warp.
 // sh/sfm: one unit per sample; pfm: one unit per 32 consecutive samples of a task.
 cudaError_t launch_bfs(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
-                       const BfsWs& ws, int grid, size_t smem, bool wide, cudaStream_t st);
+                       const BfsWs& ws, int grid, size_t smem, bool wide, bool frac, cudaStream_t st);
 size_t pfm_region_bytes(uint32_t n, uint32_t list_cap, PfmWs* ws);
 int pfm_threads();
 cudaError_t launch_pfm(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,

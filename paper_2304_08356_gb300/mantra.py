@@ -171,7 +171,7 @@ class Graph:
         """mantra_estimate.  With est_out / hits_out given as integers they are
         device pointers (out_device = 1); otherwise host numpy arrays are
         returned.  target: 0 nodes, 1 underlying edges, 2 temporal edges;
-        estimator: 0 trk, 1 ob (hits in 2^-32 units).  Returns (est, hits, info dict)."""
+        estimator: 0 trk, 1 ob, 2 RTB (ob and RTB hits in 2^-32 units).  Returns (est, hits, info dict)."""
         o = Opts(c, growth, fixed_r, bootstrap, delta_sched, 0, stream, vhat_mode, target, estimator)
         info = Info()
         if isinstance(est_out, int):

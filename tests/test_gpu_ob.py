@@ -113,7 +113,7 @@ def test_ob_batch_and_server(M):
 def test_ob_invalid(M):
     _, (u, v, t), n = _graphs()[0]
     g = M.Graph(u, v, t, n=n)
-    for kw in (dict(target=1), dict(target=2), dict(estimator=2), dict(fixed_r=1 << 30, c=2)):
+    for kw in (dict(target=1), dict(target=2), dict(estimator=3), dict(fixed_r=1 << 30, c=2)):
         kw.setdefault("estimator", 1)
         with pytest.raises(M.MantraError) as ei:
             g.estimate(0, 0.1, 0.1, 1, **kw)
