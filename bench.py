@@ -10,9 +10,10 @@ calls (--mode sequential; also timed after the main region on the same seeds).
 Metric: sampled (s,z) pairs per second, bootstrap and estimation samples of the
 three optimalities together.  Inputs are synthetic (the
 paper's data sets are not available).  After the timed region, one batched
-step each of temporal edge betweenness (App. A) and of the ob estimator
-(Sec. 4.1) on the same workload is reported under secondary.next_rows
-(--no-next skips them).
+step each of temporal edge betweenness (App. A), of the ob estimator
+(Sec. 4.1) and of the RTB estimator (App. C; its samples are sources, so
+its rate counts sources) on the same workload is reported under
+secondary.next_rows (--no-next skips them).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank runs its own steps on its own GPU (different seeds,
@@ -402,10 +403,12 @@ def main():
     seq_rate = sum(i["r"] + i["bootstrap"] for st in seq_infos for i in st.values()) / (sum(seq_ms) / 1000.0)
 
     # the same workload for the other estimators (edge betweenness over the
-    # temporal edges, App. A; the ob estimator, Sec. 4.1): one batched step each
+    # temporal edges, App. A; the ob estimator, Sec. 4.1; the RTB estimator,
+    # App. C, whose samples are sources): one batched step each
     next_rows = {}
     for label, kw in (() if args.no_next else (("edge_betweenness_temporal", dict(target=2)),
-                                               ("ob_estimator", dict(estimator=1)))):
+                                               ("ob_estimator", dict(estimator=1)),
+                                               ("rtb_estimator", dict(estimator=2)))):
         flush.zero_()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
