@@ -185,7 +185,9 @@ bool add_checked(u128 a, u128 b, u128* r) {
     return true;
 }
 
-enum { OPT_SH = 0, OPT_SFM = 1, OPT_PFM = 2 };
+// OPT_FSFM: foremost-first shortest-foremost (Buss et al.'s order, the other
+// reading of Def. 1(2)): the earliest arrival at z first, then the fewest hops.
+enum { OPT_SH = 0, OPT_SFM = 1, OPT_PFM = 2, OPT_FSFM = 3 };
 enum { OK = 0, E_INVAL = 1, E_OVERFLOW = 3, E_RNG = 7 };
 
 // Result of a forward search from s (truncated at z when z is given).
@@ -208,7 +210,7 @@ struct Search {
 // level-k appearances earlier than t (same sum, taken per edge).  With a
 // target z the search stops after the first level that holds an appearance
 // of z; with no target (z = n) it runs until the frontier is empty.
-Search tbfs_levels(const Graph& G, uint32_t s, uint32_t z) {
+Search tbfs_levels(const Graph& G, uint32_t s, uint32_t z, int64_t tmax = POS_INF) {
     Search R;
     App src(s, NEG_INF);
     R.st[src] = State{0, 1};
@@ -233,6 +235,7 @@ Search tbfs_levels(const Graph& G, uint32_t s, uint32_t z) {
             }
             for (const auto& e : G.out[u]) {                      // out[u] is sorted by time
                 int64_t t = e.second;
+                if (t > tmax) break;                              // beyond the time bound
                 size_t cnt = std::lower_bound(times.begin(), times.end(), t) - times.begin();
                 if (cnt == 0) continue;                           // no appearance of u before t
                 const u128 add = prefix[cnt - 1];
@@ -286,10 +289,16 @@ Search pfm_scan(const Graph& G, uint32_t s) {
 }
 
 // Endpoint appearances of z in the sh / sfm search, ascending in time.
-// sh keeps every appearance of z on level d; sfm only the earliest one.
+// sh keeps every appearance of z on level d; sfm only the earliest one;
+// fsfm the earliest appearance of z at any level (its level is R.d).
 std::vector<App> endpoints(const Search& R, uint32_t z, int opt) {
     std::vector<App> ends;
     if (R.d == 0) return ends;
+    if (opt == OPT_FSFM) {
+        auto it = R.st.lower_bound(App(z, NEG_INF));
+        if (it != R.st.end() && it->first.first == z) ends.push_back(it->first);
+        return ends;
+    }
     for (auto it = R.st.lower_bound(App(z, NEG_INF)); it != R.st.end() && it->first.first == z; ++it)
         if (it->second.level == R.d) ends.push_back(it->first);
     if (opt == OPT_SFM && !ends.empty()) ends.resize(1);
@@ -304,7 +313,20 @@ int count_paths(const Graph& G, int opt, uint32_t s, uint32_t z, Search* out, u1
         *sigma = (out->fa[z] == POS_INF) ? 0 : out->sig[z];
         return OK;
     }
-    *out = tbfs_levels(G, s, z);
+    if (opt == OPT_FSFM) {
+        // every appearance of z that some path reaches: search without the
+        // first-level stop, up to z's latest in-edge time; the earliest one
+        // is the endpoint, with the fewest hops (its level)
+        int64_t tz = -1;
+        for (const auto& e : G.in[z]) tz = std::max<int64_t>(tz, e.second);
+        *out = tbfs_levels(G, s, G.n, tz);
+        if (out->status != OK) return out->status;
+        out->d = 0;
+        auto it = out->st.lower_bound(App(z, NEG_INF));
+        if (z != s && it != out->st.end() && it->first.first == z) out->d = it->second.level;
+    } else {
+        *out = tbfs_levels(G, s, z);
+    }
     if (out->status != OK) return out->status;
     u128 tot = 0;
     for (const App& a : endpoints(*out, z, opt))
@@ -574,8 +596,13 @@ int rtb_values(const Graph& G, int opt, uint64_t seed, uint64_t i, uint32_t dom,
         std::vector<bool> taken(n, false);
         for (const auto& kv : R.st) {           // map order: by vertex, then ascending time
             const uint32_t v = kv.first.first;
-            if (v == s || kv.second.level != dv[v]) continue;
-            if (opt == OPT_SFM && taken[v]) continue;
+            if (v == s) continue;
+            if (opt == OPT_FSFM) {                // the earliest state of v, at any level
+                if (taken[v]) continue;
+            } else {
+                if (kv.second.level != dv[v]) continue;
+                if (opt == OPT_SFM && taken[v]) continue;
+            }
             taken[v] = true;
             is_end[kv.first] = true;
             if (!add_checked(sv[v], kv.second.sigma, &sv[v])) return E_OVERFLOW;
@@ -1046,11 +1073,38 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
     return OK;
 }
 
+// Hop distances from u (UINT32_MAX: unreached; u itself excluded).
+// sh / sfm: level of v's first appearance; fsfm: level of v's earliest
+// appearance; pfm: minimum hops among prefix-foremost paths.
+int distances_from(const Graph& G, int opt, uint32_t u, std::vector<uint32_t>* dist) {
+    const uint32_t n = G.n;
+    dist->assign(n, UINT32_MAX);
+    if (opt == OPT_PFM) {
+        Search R = pfm_scan(G, u);
+        if (R.status != OK) return R.status;
+        for (uint32_t v = 0; v < n; ++v) if (v != u && R.fa[v] != POS_INF) (*dist)[v] = R.hop[v];
+        return OK;
+    }
+    Search R = tbfs_levels(G, u, n);
+    if (R.status != OK) return R.status;
+    std::vector<bool> seen(n, false);
+    for (const auto& kv : R.st) {             // map order: by vertex, then ascending time
+        const uint32_t x = kv.first.first;
+        if (x == u) continue;
+        if (opt == OPT_FSFM) {                // hops of the earliest appearance
+            if (!seen[x]) (*dist)[x] = kv.second.level;
+            seen[x] = true;
+        } else {
+            (*dist)[x] = std::min((*dist)[x], kv.second.level);
+        }
+    }
+    return OK;
+}
+
 // Algorithm 2: r_s full searches from sources u_k (uniform in [0,n) from the
 // STATS stream, or every node once when all_sources != 0).  cnt[h] counts
-// reached nodes v != u at distance h; reach[h] = sum_{h' <= h} cnt[h'].
-// Distance: sh / sfm -- level of v's first appearance; pfm -- minimum hops
-// among prefix-foremost paths.  reach must hold n entries; returns D_LB.
+// reached nodes v != u at distance h (distances_from); reach[h] = sum_{h' <= h}
+// cnt[h'].  reach must hold n entries; returns D_LB.
 int orc_stats(const void* g, int opt, uint64_t seed, uint64_t r_s, int all_sources, uint64_t* reach,
               uint32_t* d_lb) {
     const Graph* G = (const Graph*)g;
@@ -1058,28 +1112,43 @@ int orc_stats(const void* g, int opt, uint64_t seed, uint64_t r_s, int all_sourc
     std::vector<uint64_t> cnt(n + 1, 0);
     uint32_t D = 0;
     uint64_t count = all_sources ? n : r_s;
+    std::vector<uint32_t> dist;
     for (uint64_t k = 0; k < count; ++k) {
         uint64_t u64;
         if (all_sources) u64 = k;
         else if (!uniform_below64(n, seed, k, D_STATS, &u64)) return E_RNG;
-        uint32_t u = (uint32_t)u64;
-        std::vector<uint32_t> dist(n, UINT32_MAX);
-        if (opt == OPT_PFM) {
-            Search R = pfm_scan(*G, u);
-            if (R.status != OK) return R.status;
-            for (uint32_t v = 0; v < n; ++v) if (v != u && R.fa[v] != POS_INF) dist[v] = R.hop[v];
-        } else {
-            Search R = tbfs_levels(*G, u, n);
-            if (R.status != OK) return R.status;
-            for (const auto& kv : R.st)
-                if (kv.first.first != u) dist[kv.first.first] = std::min(dist[kv.first.first], kv.second.level);
-        }
+        int st = distances_from(*G, opt, (uint32_t)u64, &dist);
+        if (st != OK) return st;
         for (uint32_t v = 0; v < n; ++v)
             if (dist[v] != UINT32_MAX) { cnt[dist[v]] += 1; D = std::max(D, dist[v]); }
     }
     uint64_t acc = 0;
     for (uint32_t h = 0; h < n; ++h) { acc += cnt[h]; reach[h] = acc; }
     *d_lb = D;
+    return OK;
+}
+
+// Temporal closeness from Algorithm 2's searches (the appendix remarks that
+// they give a fast closeness approximation; the harmonic form is the reading
+// used here): over the same r_s sources, sum[v] = sum_k round(2^32 / d(u_k, v))
+// (ties up; 0 when unreached or u_k = v), and
+//   closeness[v] = sum[v] n / (2^32 r_s (n-1)),
+// an unbiased estimate of 1/(n-1) sum_{u != v} 1/d(u,v) up to the rounding.
+int orc_closeness(const void* g, int opt, uint64_t seed, uint64_t r_s, uint64_t* sum, double* closeness) {
+    const Graph* G = (const Graph*)g;
+    const uint32_t n = G->n;
+    std::vector<uint32_t> dist;
+    for (uint32_t v = 0; v < n; ++v) sum[v] = 0;
+    for (uint64_t k = 0; k < r_s; ++k) {
+        uint64_t u64;
+        if (!uniform_below64(n, seed, k, D_STATS, &u64)) return E_RNG;
+        int st = distances_from(*G, opt, (uint32_t)u64, &dist);
+        if (st != OK) return st;
+        for (uint32_t v = 0; v < n; ++v)
+            if (dist[v] != UINT32_MAX) sum[v] += (((uint64_t)1 << 33) + dist[v]) / (2 * (uint64_t)dist[v]);
+    }
+    for (uint32_t v = 0; v < n; ++v)
+        closeness[v] = ((double)sum[v] * (double)n) / (4294967296.0 * (double)r_s * (double)(n - 1));
     return OK;
 }
 

@@ -85,6 +85,7 @@ def lib():
         L.orc_wimpy_variance_bound.restype = C.c_double
         L.orc_stats.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64, C.c_int, u64p, u32p]
         L.orc_exact_bc.argtypes = [C.c_void_p, C.c_int, dp]
+        L.orc_closeness.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64, u64p, dp]
         _lib = L
     return _lib
 
@@ -243,6 +244,13 @@ class Graph:
         q = np.zeros(self.n, np.uint64)
         _chk(lib().orc_rtb_values(self.h, opt, seed, i, dom, _p(q, C.c_uint64)))
         return q
+
+    def closeness(self, opt, seed, r_s):
+        """(per-vertex sums of round(2^32 / d), closeness estimates) over
+        Algorithm 2's r_s sources."""
+        sm = np.zeros(self.n, np.uint64); cl = np.zeros(self.n, np.float64)
+        _chk(lib().orc_closeness(self.h, opt, seed, r_s, _p(sm, C.c_uint64), _p(cl, C.c_double)))
+        return sm, cl
 
     def stats_counts(self, opt, seed, r_s, all_sources=False):
         """(reach[0..D_LB], D_LB): cumulative reach counts per hop (Algorithm 2)."""

@@ -7,7 +7,8 @@ from the full list by their definitions:
 * sh  -- walks s -> z with the minimum number of hops;
 * sfm -- among the sh walks, those with the earliest arrival at z;
 * pfm -- walks whose every prefix is foremost: each visited vertex is reached
-         at its earliest arrival time fa (the minimum arrival over all walks).
+         at its earliest arrival time fa (the minimum arrival over all walks);
+* fsfm -- the foremost walks (arrival fa(z)) with the minimum number of hops.
 
 A walk is a sequence of vertex appearances with strictly increasing times
 (Sec. 3); vertices may repeat in a walk, so nothing here assumes that
@@ -62,7 +63,10 @@ def optimal_sets(edges, n, s):
         arr = min(w[1][-1] for w in sh)
         sfm = [w for w in sh if w[1][-1] == arr]
         pfm = [w for w in lst if all(w[1][i] == fa.get(w[0][i]) for i in range(1, len(w[0])))]
-        res[z] = {0: sh, 1: sfm, 2: pfm}
+        fore = [w for w in lst if w[1][-1] == fa[z]]
+        hf = min(len(w[0]) - 1 for w in fore)
+        fsfm = [w for w in fore if len(w[0]) - 1 == hf]
+        res[z] = {0: sh, 1: sfm, 2: pfm, 3: fsfm}
     return res
 
 
@@ -111,11 +115,12 @@ def mean_internal(edges, n, opt):
 
 def distances(edges, n, opt):
     """d[(u, v)] for reachable v != u: minimum hops among optimal walks
-    (sh and sfm: minimum hops over all walks; pfm: minimum hops among pfm walks)."""
+    (sh and sfm: minimum hops over all walks; pfm: minimum hops among pfm walks;
+    fsfm: minimum hops among the foremost walks)."""
     d = {}
     for u in range(n):
         for z, sets in optimal_sets(edges, n, u).items():
-            lst = sets[2] if opt == 2 else sets[0]
+            lst = sets[opt] if opt in (2, 3) else sets[0]
             if lst:
                 d[(u, z)] = min(len(vs) - 1 for vs, _ in lst)
     return d

@@ -146,7 +146,7 @@ def test_bruteforce_sigma_and_bijection(seed):
         for z in range(n):
             if z == s:
                 continue
-            for opt in (0, 1, 2):
+            for opt in (0, 1, 2, 3):
                 want = sets[z][opt] if z in sets else []
                 sig, _ = g.sigma(opt, s, z)
                 assert sig == len(want), (opt, s, z)
@@ -159,7 +159,7 @@ def test_exact_bc_against_bruteforce_and_lemma1(seed):
     u, v, t = synth.random_tiny(6, 14, t_hi=5, seed=2000 + seed)
     edges = BF.dedupe(u, v, t)
     g = O.Graph(u, v, t, n=6)
-    for opt in (0, 1, 2):
+    for opt in (0, 1, 2, 3):
         want = BF.exact_bc(edges, 6, opt)
         got = g.exact_bc(opt)
         assert np.allclose(got, [float(x) for x in want], rtol=0, atol=1e-15)
@@ -190,7 +190,7 @@ def test_layered_dag_reduces_to_static_path_counts():
     for L in range(1, len(widths)):
         for b in ids[L]:
             cnt[b] = sum(cnt.get(a, 0) for (a, bb, _) in edges if bb == b)
-    for opt in (0, 1, 2):
+    for opt in (0, 1, 2, 3):
         assert g.sigma(opt, s, z)[0] == cnt[z]
 
 
@@ -201,7 +201,7 @@ def test_equal_timestamps_single_edge_paths():
     g = O.Graph(u, v, t, n=30)
     pairs = {(int(a), int(b)) for a, b in zip(u, v) if a != b}
     for (s, z) in [(0, 1), (2, 9), (5, 4)]:
-        for opt in (0, 1, 2):
+        for opt in (0, 1, 2, 3):
             assert g.sigma(opt, s, z)[0] == (1 if (s, z) in pairs else 0)
     est, hits, info = g.estimate(0, 0.1, 0.1, 1, fixed_r=300)
     assert hits.sum() == 0 and info["sum_int_len"] == 0
@@ -216,7 +216,7 @@ def test_estimate_invariants_and_mcera_recount():
     u, v, t = synth.uniform_small(n=40, m=500, t_hi=60, seed=11)
     g = O.Graph(u, v, t, n=40)
     r, c, seed = 300, 25, 17
-    for opt in (0, 1, 2):
+    for opt in (0, 1, 2, 3):
         est, hits, info = g.estimate(opt, 0.1, 0.1, seed, c=c, fixed_r=r)
         samples = g.samples(opt, seed, 0, r)
         # hits = number of samples whose drawn path has v internal
@@ -291,7 +291,7 @@ def test_stats_all_sources_against_bruteforce(seed):
     u, v, t = synth.random_tiny(n, 14, t_hi=6, seed=3000 + seed)
     edges = BF.dedupe(u, v, t)
     g = O.Graph(u, v, t, n=n)
-    for opt in (0, 1, 2):
+    for opt in (0, 1, 2, 3):
         d = BF.distances(edges, n, opt)
         reach, dlb = g.stats_counts(opt, 0, 0, all_sources=True)
         D = max(d.values()) if d else 0
@@ -339,7 +339,7 @@ def test_edge_ids_follow_the_drawn_paths(seed):
     assert sorted(zip(ev, et, eu)) == list(zip(ev, et, eu))
     und = sorted({(int(b), int(a)) for a, b in zip(eu, ev)})
     assert nu == len(und) and all(und[ue[e]] == (int(ev[e]), int(eu[e])) for e in range(g.m))
-    for opt in (0, 1, 2):
+    for opt in (0, 1, 2, 3):
         for (s, z, sig, path, pe) in g.samples(opt, 4, 0, 300, cap=8, edges=True):
             assert len(pe) == max(len(path) - 1, 0)
             ts = [int(et[e]) for e in pe]
@@ -353,7 +353,7 @@ def test_edge_betweenness_lemmas_on_bruteforce(seed):
     optimal path over all ordered pairs), exactly."""
     u, v, t = synth.random_tiny(6, 14, t_hi=5, seed=4000 + seed)
     edges = BF.dedupe(u, v, t)
-    for opt in (0, 1, 2):
+    for opt in (0, 1, 2, 3):
         bt = BF.exact_edge_bc(edges, 6, opt, temporal=True)
         bu = BF.exact_edge_bc(edges, 6, opt, temporal=False)
         agg = {}
@@ -414,7 +414,7 @@ def test_through_counts_against_bruteforce(seed):
         for z in range(6):
             if z == s:
                 continue
-            for opt in (0, 1, 2):
+            for opt in (0, 1, 2, 3):
                 walks = sets[z][opt] if z in sets else []
                 sig, th = g.through(opt, s, z)
                 assert sig == len(walks)
@@ -529,7 +529,7 @@ def test_rtb_values_against_bruteforce(seed):
             continue
         seen.add(s)
         sets = BF.optimal_sets(edges, n, s)
-        for opt in (0, 1, 2):
+        for opt in (0, 1, 2, 3):
             want = [Fraction(0)] * n
             for z, d in sets.items():
                 lst = d[opt]
@@ -571,3 +571,30 @@ def test_rtb_progressive_and_invalid():
     assert info["r"] >= info["s1"] and (info["xi"] <= 0.05 or info["r"] >= info["omega"])
     with pytest.raises(O.OracleError):
         g.estimate(0, 0.05, 0.1, 4, estimator=2, target=1)
+
+
+# --------------------------------------------------------------------------
+# Temporal closeness from Algorithm 2's searches (App. D remark; harmonic
+# reading): sum_k round(2^32 / d(u_k, v)) over the sampled sources.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("opt", [0, 1, 2, 3])
+def test_closeness_against_bruteforce(opt):
+    n = 7
+    u, v, t = synth.random_tiny(n, 24, t_hi=6, seed=4400 + opt)
+    edges = BF.dedupe(u, v, t)
+    g = O.Graph(u, v, t, n=n)
+    dist = BF.distances(edges, n, opt)
+    r_s, seed = 3000, 12
+    sm, cl = g.closeness(opt, seed, r_s)
+    want = [0] * n
+    for k in range(r_s):
+        src = O.uniform64(n, seed, k, 5)
+        for x in range(n):
+            d = dist.get((src, x))
+            if d:
+                want[x] += ((1 << 33) + d) // (2 * d)
+    assert [int(x) for x in sm] == want
+    assert np.array_equal(cl, np.array([(float(w) * n) / (4294967296.0 * r_s * (n - 1)) for w in want]))
+    exact = [sum(Fraction(1, dist[(a, x)]) for a in range(n) if (a, x) in dist) / (n - 1) for x in range(n)]
+    bound = n / (n - 1) * math.sqrt(math.log(2 * n / 1e-3) / (2 * r_s))
+    assert max(abs(cl[x] - float(exact[x])) for x in range(n)) <= bound
