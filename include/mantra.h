@@ -21,7 +21,10 @@
  * Optimalities (paper Sec. 3, Def. 1): MANTRA_SH shortest; MANTRA_SFM
  * shortest-foremost (minimum hops, then earliest arrival at z -- the reading
  * fixed by the worked example in the paper's App. A figure); MANTRA_PFM
- * prefix-foremost.  A temporal path uses strictly increasing times and starts
+ * prefix-foremost; MANTRA_FSFM the other reading of Def. 1(2), Buss et al.'s
+ * order: the earliest arrival at z first, then the fewest hops among those
+ * paths (Algorithm 2 distance: the hops of v's earliest appearance).  A
+ * temporal path uses strictly increasing times and starts
  * at (s, -inf); identical (u,v,t) triples are one edge; self loops are
  * dropped.
  */
@@ -37,7 +40,7 @@ extern "C" {
 
 typedef struct mantra_graph mantra_graph; /* opaque, device resident */
 
-typedef enum { MANTRA_SH = 0, MANTRA_SFM = 1, MANTRA_PFM = 2 } mantra_opt;
+typedef enum { MANTRA_SH = 0, MANTRA_SFM = 1, MANTRA_PFM = 2, MANTRA_FSFM = 3 } mantra_opt;
 
 enum {
     MANTRA_OK = 0,
@@ -189,6 +192,17 @@ int mantra_estimate_batch(mantra_problem* probs, uint32_t count);
  * hops among prefix-foremost paths. */
 int mantra_temporal_stats(const mantra_graph* g, mantra_opt opt, double eps, uint64_t seed, uint64_t r_override,
                           double tau, mantra_tstats* out, uint64_t* reach_out, uint32_t reach_cap);
+
+/* Temporal closeness from Algorithm 2's searches (the paper's App. D remarks
+ * that they approximate closeness; the harmonic form is the reading used
+ * here): the same r_s sources as mantra_temporal_stats (r_override, or
+ * ceil(ln n / eps^2)), each a full search.  sum_out[v] (or NULL): the sum
+ * over the sources u_k != v that reach v of round(2^32 / d(u_k, v)), ties up
+ * (the distance of mantra_temporal_stats); closeness_out[v] = sum[v] n /
+ * (2^32 r_s (n-1)) estimates 1/(n-1) sum_{u != v} 1/d(u, v).  *r_out (or
+ * NULL) receives r_s.  Host arrays of n entries. */
+int mantra_temporal_closeness(const mantra_graph* g, mantra_opt opt, double eps, uint64_t seed, uint64_t r_override,
+                              uint64_t* sum_out, double* closeness_out, uint64_t* r_out);
 
 /* Diagnostic: run the per-sample path computation of Algorithm 1's Update
  * step for sample indices i0 .. i0+count-1 of the given Philox domains

@@ -586,7 +586,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
         } else {
             any_b = true; bn = std::max(bn, it.G->n); bA = std::max(bA, it.G->A);
             bsamples += it.job.count;
-            frac |= it.job.ob || it.job.rtb;
+            frac |= it.job.ob || it.job.rtb || (it.job.stats && it.job.opt == 3);
         }
     }
     E.tick_frac = frac;
@@ -786,7 +786,7 @@ struct Problem {
     int validate() const {
         if (!G || (!est_out && !out_device)) return MANTRA_E_INVAL;
         if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0)) return MANTRA_E_INVAL;
-        if (opt != MANTRA_SH && opt != MANTRA_SFM && opt != MANTRA_PFM) return MANTRA_E_INVAL;
+        if (opt != MANTRA_SH && opt != MANTRA_SFM && opt != MANTRA_PFM && opt != MANTRA_FSFM) return MANTRA_E_INVAL;
         if (c < 1 || c > 128 || !(growth > 1.0)) return MANTRA_E_INVAL;
         if (fixed_r > RMAX) return MANTRA_E_INVAL;
         if (out_device && !est_out) return MANTRA_E_INVAL;
@@ -1328,44 +1328,62 @@ int mantra_estimate_batch(mantra_problem* probs, uint32_t count) {
     return first;
 }
 
-int mantra_temporal_stats(const mantra_graph* g, mantra_opt opt, double eps, uint64_t seed, uint64_t r_override,
-                          double tau, mantra_tstats* out, uint64_t* reach_out, uint32_t reach_cap) {
-    if (!g || !out) return MANTRA_E_INVAL;
-    if (!(eps > 0.0 && eps < 1.0) || !(tau >= 0.0 && tau <= 1.0)) return MANTRA_E_INVAL;
-    if (opt != MANTRA_SH && opt != MANTRA_SFM && opt != MANTRA_PFM) return MANTRA_E_INVAL;
+// Algorithm 2's searches: r_s full searches from sources drawn from the STATS
+// stream; hc[h] = reached (source, v) pairs at distance h, *dm = the largest
+// distance; with clos_out (n entries) also the per-vertex closeness sums.
+int stats_run(const mantra_graph* g, mantra_opt opt, uint64_t rs, uint64_t seed, std::vector<u64>* hc, u64* dm,
+              uint64_t* clos_out) {
+    if (opt != MANTRA_SH && opt != MANTRA_SFM && opt != MANTRA_PFM && opt != MANTRA_FSFM) return MANTRA_E_INVAL;
     Engine* E = nullptr;
     int rc;
     if ((rc = current_engine(g, &E)) != MANTRA_OK) return rc;
     std::lock_guard<std::mutex> lock(E->mu);
-    const double t0 = now_s();
     const uint32_t n = g->n;
-    const uint64_t rs = r_override ? r_override : (uint64_t)std::ceil(std::log((double)n) / (eps * eps));
     const size_t b_cnt = ((size_t)n + 2) * 8;
-    const size_t b_all = al256(b_cnt) + 256 + al256(rs * 8);
+    const size_t b_clos = clos_out ? al256((size_t)n * 8) : 0;
+    const size_t b_all = al256(b_cnt) + 256 + al256(rs * 8) + b_clos;
     char* blk = (char*)E->pool.get(b_all);
     if (!blk) return MANTRA_E_NOMEM;
     u64* cnt = (u64*)blk;
     u64* dmax = (u64*)(blk + al256(b_cnt));
+    u64* clos = clos_out ? (u64*)(blk + al256(b_cnt) + 256 + al256(rs * 8)) : nullptr;
     CU(cudaMemsetAsync(blk, 0, al256(b_cnt) + 256, E->sa));
+    if (clos) CU(cudaMemsetAsync(clos, 0, b_clos, E->sa));
     std::vector<TickItem> items(1);
     items[0].G = g;
     Job& j = items[0].job;
-    j.seed = seed; j.i0 = 0; j.count = rs; j.opt = (opt == MANTRA_PFM) ? MANTRA_PFM : MANTRA_SH;
-    j.stats = 1; j.cnt = cnt; j.dmax = dmax;
+    // sh and sfm share their distances (first level); fsfm and pfm have their own
+    j.seed = seed; j.i0 = 0; j.count = rs;
+    j.opt = (opt == MANTRA_PFM || opt == MANTRA_FSFM) ? (int)opt : (int)MANTRA_SH;
+    j.stats = 1; j.cnt = cnt; j.dmax = dmax; j.clos = clos;
     j.ovf_list = (uint64_t*)(blk + al256(b_cnt) + 256);       // pfm lists that overflowed: re-run in order
     TickResult TR;
     uint64_t* ovfs[1] = {j.ovf_list};
     rc = run_tick_full(*E, items, ovfs, &TR);
-    std::vector<u64> hc((size_t)n + 1);
-    u64 dm = 0;
+    hc->assign((size_t)n + 1, 0);
+    *dm = 0;
     if (rc == MANTRA_OK && TR.status[0] != MANTRA_OK) rc = TR.status[0];
     if (rc == MANTRA_OK) {
-        if (cudaMemcpyAsync(hc.data(), cnt, ((size_t)n + 1) * 8, cudaMemcpyDeviceToHost, E->sa) != cudaSuccess ||
-            cudaMemcpyAsync(&dm, dmax, 8, cudaMemcpyDeviceToHost, E->sa) != cudaSuccess ||
+        if (cudaMemcpyAsync(hc->data(), cnt, ((size_t)n + 1) * 8, cudaMemcpyDeviceToHost, E->sa) != cudaSuccess ||
+            cudaMemcpyAsync(dm, dmax, 8, cudaMemcpyDeviceToHost, E->sa) != cudaSuccess ||
+            (clos && cudaMemcpyAsync(clos_out, clos, (size_t)n * 8, cudaMemcpyDeviceToHost, E->sa) != cudaSuccess) ||
             cudaStreamSynchronize(E->sa) != cudaSuccess)
             rc = MANTRA_E_CUDA;
     }
     E->pool.put(blk, b_all);
+    return rc;
+}
+
+int mantra_temporal_stats(const mantra_graph* g, mantra_opt opt, double eps, uint64_t seed, uint64_t r_override,
+                          double tau, mantra_tstats* out, uint64_t* reach_out, uint32_t reach_cap) {
+    if (!g || !out) return MANTRA_E_INVAL;
+    if (!(eps > 0.0 && eps < 1.0) || !(tau >= 0.0 && tau <= 1.0)) return MANTRA_E_INVAL;
+    const double t0 = now_s();
+    const uint32_t n = g->n;
+    const uint64_t rs = r_override ? r_override : (uint64_t)std::ceil(std::log((double)n) / (eps * eps));
+    std::vector<u64> hc;
+    u64 dm = 0;
+    const int rc = stats_run(g, opt, rs, seed, &hc, &dm, nullptr);
     if (rc != MANTRA_OK) return rc;
     const uint32_t D = (uint32_t)dm;
     std::vector<u64> R((size_t)D + 1);
@@ -1394,11 +1412,30 @@ int mantra_temporal_stats(const mantra_graph* g, mantra_opt opt, double eps, uin
     return MANTRA_OK;
 }
 
+int mantra_temporal_closeness(const mantra_graph* g, mantra_opt opt, double eps, uint64_t seed, uint64_t r_override,
+                              uint64_t* sum_out, double* closeness_out, uint64_t* r_out) {
+    if (!g || !closeness_out) return MANTRA_E_INVAL;
+    if (!(eps > 0.0 && eps < 1.0)) return MANTRA_E_INVAL;
+    const uint32_t n = g->n;
+    const uint64_t rs = r_override ? r_override : (uint64_t)std::ceil(std::log((double)n) / (eps * eps));
+    std::vector<u64> hc;
+    std::vector<uint64_t> sum(n, 0);
+    u64 dm = 0;
+    const int rc = stats_run(g, opt, rs, seed, &hc, &dm, sum.data());
+    if (rc != MANTRA_OK) return rc;
+    for (uint32_t v = 0; v < n; ++v) {
+        if (sum_out) sum_out[v] = sum[v];
+        closeness_out[v] = ((double)sum[v] * (double)n) / (4294967296.0 * (double)rs * (double)(n - 1));
+    }
+    if (r_out) *r_out = rs;
+    return MANTRA_OK;
+}
+
 int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, uint32_t dom_pair, uint32_t dom_path,
                         uint64_t i0, uint64_t count, uint32_t* s_out, uint32_t* z_out, uint64_t* sigma_out,
                         uint32_t* len_out, uint32_t* nodes_out, uint32_t cap, uint32_t* edges_out) {
     if (!g || !s_out || !z_out || !sigma_out || !len_out || (cap > 0 && !nodes_out)) return MANTRA_E_INVAL;
-    if (opt != MANTRA_SH && opt != MANTRA_SFM && opt != MANTRA_PFM) return MANTRA_E_INVAL;
+    if (opt != MANTRA_SH && opt != MANTRA_SFM && opt != MANTRA_PFM && opt != MANTRA_FSFM) return MANTRA_E_INVAL;
     if (dom_pair > 5 || dom_path > 5) return MANTRA_E_INVAL;
     if (count == 0) return MANTRA_OK;
     Engine* E = nullptr;

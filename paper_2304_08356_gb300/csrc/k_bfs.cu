@@ -62,11 +62,13 @@ __device__ __forceinline__ void bfs_ob_update(const DevGraph& g, const Job& job,
             SigOps<WIDE>::atomic_add(dl + lev[lv] + p, x);
         }
     };
-    {   // level d: z's endpoint states (sh: all on level d, sfm: the earliest), count 1
+    {   // level d: z's endpoint states (sh: all on level d, sfm: the earliest;
+        // fsfm: z's earliest slot, on level d), count 1
         const uint32_t zs = g.slot_ptr[z], ze = g.slot_ptr[z + 1];
-        const uint32_t a0 = job.opt == 1 ? first : zs, a1 = job.opt == 1 ? first + 1 : ze;
+        const bool one = job.opt == 1 || job.opt == 3;
+        const uint32_t a0 = one ? first : zs, a1 = one ? first + 1 : ze;
         for (uint32_t a = a0; a < a1; ++a) {
-            if (!((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u)) continue;
+            if (job.opt != 3 && !((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u)) continue;
             const uint32_t ta = g.slot_t[a];
             for (uint32_t e = g.slot_in[a] + tid; e < g.slot_in[a + 1]; e += BFS_NT) to_preds(e, ta, d - 1, (Sig)1);
         }
@@ -117,7 +119,8 @@ __device__ __forceinline__ void bfs_ob_update(const DevGraph& g, const Job& job,
 
 // RTB update of one sample (App. C), all threads of the CTA, after a full
 // search from s with levels 1 .. D in F.  The endpoint states of a vertex v
-// are its states on its first level d_v (sfm: the earliest of them); eps(b) =
+// are its states on its first level d_v (sfm: the earliest of them; fsfm: its
+// earliest state at any level); eps(b) =
 // sigma(b) / sigma_{s,v_b} for an endpoint b.  From level D down, every state
 // b with X(b) = eps(b) + delta(b) > 0 adds round(sigma(a) X(b) / sigma(b)) to
 // delta(a) of each DAG predecessor a; f_v(s) = round(sum of delta over v's
@@ -134,7 +137,7 @@ __device__ __forceinline__ void bfs_rtb_update(const DevGraph& g, const Job& job
     typedef typename SigOps<WIDE>::T Sig;
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t n = g.n;
-    const bool sfm = job.opt == 1;
+    const bool sfm = job.opt == 1, fsfm = job.opt == 3;
     for (uint32_t v = tid; v < n; v += BFS_NT) dv[v] = NONE;
     if (tid == 0) {
         *sh_nt = 0;
@@ -143,15 +146,18 @@ __device__ __forceinline__ void bfs_rtb_update(const DevGraph& g, const Job& job
         rade[0] = w4[0]; rade[1] = w4[1]; rade[2] = w4[2]; rade[3] = w4[3];
     }
     __syncthreads();
+    // dv: first level of each vertex (fsfm: its earliest slot, the smallest id)
     for (uint32_t k = 1; k <= D; ++k)
         for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
-            const uint32_t v = g.slot_v[F[p]];
-            if (v != s) atomicMin(dv + v, k);
+            const uint32_t a = F[p], v = g.slot_v[a];
+            if (v != s) atomicMin(dv + v, fsfm ? a : k);
         }
     __syncthreads();
     // a level lists a vertex's states together, in time order
     auto is_end = [&](uint32_t p, uint32_t k, uint32_t v) -> bool {
-        if (v == s || dv[v] != k) return false;
+        if (v == s) return false;
+        if (fsfm) return F[p] == dv[v];
+        if (dv[v] != k) return false;
         return !sfm || p == lev[k] || g.slot_v[F[p - 1]] != v;
     };
     for (uint32_t k = 1; k <= D; ++k)
@@ -226,6 +232,43 @@ __device__ __forceinline__ void bfs_rtb_update(const DevGraph& g, const Job& job
         if (dv[v] != NONE) sv[v] = (Sig)0;
 }
 
+// Algorithm 2 reach counts for fsfm after a full search from s with levels
+// 1 .. D in F: the distance of v is the level of its earliest state (the
+// fewest hops among the foremost paths).  dv: n entries, overwritten.
+template <int BFS_NT>
+__device__ __forceinline__ void bfs_fsfm_reach(const DevGraph& g, const Job& job, uint32_t s, uint32_t D,
+                                               const uint32_t* F, const uint32_t* lev, uint32_t* dv) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (uint32_t v = tid; v < g.n; v += BFS_NT) dv[v] = NONE;
+    __syncthreads();
+    for (uint32_t k = 1; k <= D; ++k)
+        for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
+            const uint32_t a = F[p], v = g.slot_v[a];
+            if (v != s) atomicMin(dv + v, a);
+        }
+    __syncthreads();
+    for (uint32_t k = 1; k <= D; ++k) {
+        uint32_t cnt = 0;
+        for (uint32_t p0 = lev[k]; p0 < lev[k + 1]; p0 += BFS_NT) {
+            const uint32_t p = p0 + tid;
+            if (p < lev[k + 1]) {
+                const uint32_t a = F[p], v = g.slot_v[a];
+                if (v != s && dv[v] == a) {
+                    ++cnt;
+                    if (job.clos) atomicAdd(job.clos + v, recip32(k));
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+        if (lane == 0 && cnt) {
+            atomicAdd(job.cnt + k, (u64)cnt);
+            atomicMax(job.dmax, (u64)k);
+        }
+    }
+    __syncthreads();
+}
+
 // Per-sample inputs of the fractional updates (ob, RTB) and the CTA's region
 // arrays, kept in shared memory so that the out-of-line call carries two
 // arguments.
@@ -238,7 +281,8 @@ struct FracCtx {
     uint32_t rade[4];
 };
 
-// The ob (mode 1) or RTB (mode 2) update of the CTA's current sample; the
+// The ob (mode 1) or RTB (mode 2) update of the CTA's current sample, or the
+// fsfm reach counts of an Algorithm 2 search (mode 3); the
 // region arrays are re-derived from the workspace.  Out of line, so that the
 // search's register allocation does not carry it.
 template <bool WIDE, int BFS_NT>
@@ -261,6 +305,8 @@ __device__ __noinline__ void bfs_frac_update(int mode, FracCtx* x) {
     if (mode == 1)
         bfs_ob_update<WIDE, BFS_NT>(g, job, x->z, x->D, x->first, x->sigma, x->rade, F, lev, N, sig, Fc, acc, VB,
                                     seg_u, &x->nt);
+    else if (mode == 3)
+        bfs_fsfm_reach<BFS_NT>(g, job, x->s, x->D, F, lev, seg_b);
     else
         bfs_rtb_update<WIDE, BFS_NT>(g, job, x->s, x->i, x->D, x->rade, F, lev, sig, reinterpret_cast<u64*>(Fc), acc,
                                      acc2, seg_b, VB, seg_u, &x->nt);
@@ -315,6 +361,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
     __shared__ uint32_t sh_d, sh_len;
     __shared__ u128 sh_sigma;
     __shared__ uint32_t sh_first;
+    __shared__ uint32_t sh_zbest, sh_zmin, sh_zlev;   // fsfm: earliest slot of z so far, and its level
     __shared__ FracCtx sh_fx;
     __shared__ uint32_t cs_off[BFS_NT + 1], cs_first[BFS_NT], cs_fb[BFS_NT], cs_fe[BFS_NT];   // range table
     __shared__ uint32_t sh_stamp, sh_wrap;
@@ -366,6 +413,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             }
             sh_t = t;
             sh_found = 0; sh_ovf = 0; sh_err = 0; sh_d = 0; sh_len = 0; sh_sigma = 0;
+            sh_zbest = NONE; sh_zmin = NONE; sh_zlev = 0;
         }
         __syncthreads();
         if (sh_t < 0) break;
@@ -395,7 +443,12 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
         if (!ok) { if (tid == 0) set_status(job.status, ST_RNG); s = 0; z = 1; }
         const bool stats = job.stats != 0;
         const bool full = stats || job.rtb;   // untruncated search (no target)
+        // fsfm (foremost first, then fewest hops): no stop at z's first level;
+        // every state up to z's latest in-edge time, the endpoint is z's
+        // earliest slot found at any level
+        const bool fsfm = job.opt == 3 && !full;
         const uint32_t tz = full ? NONE : g.tmax_in[z];
+        const uint32_t zlo = full ? NONE : g.slot_ptr[z], zhi = full ? NONE : g.slot_ptr[z + 1];
         bool live = ok && (g.out_ptr[s + 1] > g.out_ptr[s]);
         if (!full && (g.slot_ptr[z + 1] == g.slot_ptr[z])) live = false;   // z has no in-edges
 
@@ -516,7 +569,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             if (sh_ovf) break;
 
             // ---- pull: does level k reach z? ----
-            if (!full) {
+            if (!full && !fsfm) {
                 const uint32_t zs = g.slot_ptr[z], ze = g.slot_ptr[z + 1];
                 const uint32_t e_lo = g.slot_in[zs], e_hi = g.slot_in[ze];
                 const uint32_t* const g_in_u = g.in_u;
@@ -565,7 +618,9 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                     const uint32_t u = seg_u[gi];
                     const uint32_t r0 = g_out_ptr[u], r1 = g_out_ptr[u + 1];
                     lo2[0] = r0; hi2[0] = (k == 0) ? r0 : r1; key2[0] = (k == 0) ? 0u : FtL[fb];
-                    lo2[1] = r0; hi2[1] = (tz == 0) ? r0 : r1; key2[1] = tz - 1u;
+                    lo2[1] = r0;
+                    if (fsfm) { hi2[1] = r1; key2[1] = tz; }          // z's own appearances come from the push
+                    else { hi2[1] = (tz == 0) ? r0 : r1; key2[1] = tz - 1u; }
                 }
                 upper_bounds<2>(g_out_t, lo2, hi2, key2);
                 const uint32_t first = lo2[0], last = lo2[1];
@@ -648,11 +703,15 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                     bits &= bits - 1;
                     const uint32_t a = w * 32u + b;
                     F[pos++] = a;
-                    if (stats) {
+                    if (fsfm && a >= zlo && a < zhi) atomicMin(&sh_zmin, a);
+                    if (stats && job.opt != 3) {
                         const uint32_t v = g_slot_v2[a];
                         if (v != s) {
                             const uint32_t old = atomicOr(VB + (v >> 5), 1u << (v & 31));
-                            if (!(old & (1u << (v & 31)))) ++newv;
+                            if (!(old & (1u << (v & 31)))) {
+                                ++newv;
+                                if (job.clos) atomicAdd(job.clos + v, recip32(k + 1));
+                            }
                         }
                     }
                 }
@@ -669,21 +728,24 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             if (tid == 0) lev[k + 2] = fbase + Lnext;
             if (tid == 0) my_snew += Lnext;
             __syncthreads();
+            if (fsfm && tid == 0 && sh_zmin < sh_zbest) { sh_zbest = sh_zmin; sh_zlev = k + 1; }
             if (Lnext == 0) break;
             k += 1;
             L = Lnext;
         }
+        if (fsfm && tid == 0 && sh_zbest != NONE) sh_found = 1;
         __syncthreads();
 
         // ---------------- path draw (warp 0) ----------------
         const bool found = sh_found && !sh_ovf;
         if (found && wid == 0) {
             const uint32_t FULL = 0xFFFFFFFFu;
-            const uint32_t d = k + 1;
+            const uint32_t d = fsfm ? sh_zlev : k + 1;
             const uint32_t zs = g.slot_ptr[z], ze = g.slot_ptr[z + 1];
             bool bad = false, err = false;
-            // endpoints: z's slots on level d, ascending in time (sfm: the first only)
-            uint32_t first = NONE;
+            // endpoints: z's slots on level d, ascending in time (sfm: the first
+            // only; fsfm: z's earliest slot, on its own level d)
+            uint32_t first = fsfm ? sh_zbest : NONE;
             for (uint32_t a0 = zs; a0 < ze && first == NONE; a0 += 32) {
                 const uint32_t a = a0 + lane;
                 const bool b = a < ze && ((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u);
@@ -691,7 +753,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 if (msk) first = a0 + __ffs(msk) - 1;
             }
             Sig tot = 0;
-            if (job.opt == 1) tot = sig[first];
+            if (job.opt == 1 || fsfm) tot = sig[first];
             else {
                 for (uint32_t a = zs + lane; a < ze; a += 32)
                     if ((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u) { const Sig sm = tot + sig[a]; bad |= sm < tot; tot = sm; }
@@ -723,10 +785,11 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 Sig xs = shfl_idx_w((Sig)x, 0);
                 if (!rng_ok) { err = true; if (lane == 0) set_status(job.status, ST_RNG); }
                 uint32_t cur = NONE;
-                const uint32_t ze_end = (job.opt == 1) ? first + 1 : ze;
-                for (uint32_t a0 = (job.opt == 1 ? first : zs); !err && a0 < ze_end && cur == NONE; a0 += 32) {
+                const bool one = job.opt == 1 || fsfm;
+                const uint32_t ze_end = one ? first + 1 : ze;
+                for (uint32_t a0 = (one ? first : zs); !err && a0 < ze_end && cur == NONE; a0 += 32) {
                     const uint32_t a = a0 + lane;
-                    const Sig wt = (a < ze_end && ((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u)) ? sig[a] : (Sig)0;
+                    const Sig wt = (a < ze_end && (fsfm || ((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u))) ? sig[a] : (Sig)0;
                     const Sig incl = warp_inclusive_sum(wt);
                     const unsigned msk = __ballot_sync(FULL, xs < incl);
                     if (msk) {
@@ -850,10 +913,11 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
 
         // ---------------- ob (Sec. 4.1) and RTB (App. C) updates (block-uniform conditions) ----------------
         if constexpr (!FRAC) {
-            if ((job.ob || job.rtb) && tid == 0) set_status(job.status, ST_CHECK);
+            if ((job.ob || job.rtb || (stats && job.opt == 3)) && tid == 0) set_status(job.status, ST_CHECK);
         } else {
             const int mode = (job.ob && job.hits && found && !sh_ovf && !sh_err && sh_d >= 2) ? 1
-                           : (job.rtb && job.hits && live && !sh_ovf && k >= 2) ? 2 : 0;
+                           : (job.rtb && job.hits && live && !sh_ovf && k >= 2) ? 2
+                           : (stats && job.opt == 3 && live && k >= 1) ? 3 : 0;
             if (mode) {
                 if (tid == 0) {
                     FracCtx& x = sh_fx;

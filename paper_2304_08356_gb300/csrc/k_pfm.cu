@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
                 const uint32_t h = r ? hop[(size_t)v * 32] : NONE;
                 const unsigned grp = __match_any_sync(FULL, h);
                 if (r && lane == __ffs(grp) - 1) atomicAdd(job.cnt + h, (u64)__popc(grp));
+                if (r && job.clos) atomicAdd(job.clos + v, recip32(h));
                 if (r && h > dloc) dloc = h;
             }
 #pragma unroll

@@ -372,6 +372,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                     const uint32_t h = r ? __ldcg(hop + v) : NONE;
                     const unsigned grp = __match_any_sync(FULL, h);
                     if (r && lane == __ffs(grp) - 1) atomicAdd(job.cnt + h, (u64)__popc(grp));
+                    if (r && job.clos) atomicAdd(job.clos + v, recip32(h));
                     if (r && h > dloc) dloc = h;
                 }
             }

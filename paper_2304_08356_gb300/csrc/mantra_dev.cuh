@@ -101,6 +101,7 @@ struct Job {
     int stats;
     u64* cnt;                  // n+1
     u64* dmax;
+    u64* clos;                 // or nullptr: n, per vertex sum over the searches of recip32(distance)
 };
 
 // One entry of a launch's task table: a graph and a range of its samples.
@@ -538,6 +539,10 @@ __device__ __forceinline__ uint64_t muldiv_round(u128 a, uint64_t x, u128 d) {
     const bool top = (uint64_t)(rem >> 127) != 0;
     return q + ((top || (rem << 1) >= d) ? 1u : 0u);
 }
+
+// 2^32 / d rounded to nearest (ties up), d >= 1: the closeness term of a
+// vertex at hop distance d.
+__device__ __forceinline__ u64 recip32(uint32_t d) { return ((1ull << 33) + d) / (2ull * d); }
 
 // q^2 / 2^32 rounded to nearest (ties up): the ob value of f^2 (wimpy variance).
 __device__ __forceinline__ uint64_t ob_sq(uint64_t q) { return (uint64_t)(((u128)q * q + (1ull << 31)) >> 32); }

@@ -14,8 +14,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmantra.so")
 
-SH, SFM, PFM = 0, 1, 2
-OPT_NAMES = {"sh": SH, "sfm": SFM, "pfm": PFM}
+SH, SFM, PFM, FSFM = 0, 1, 2, 3
+OPT_NAMES = {"sh": SH, "sfm": SFM, "pfm": PFM, "fsfm": FSFM}
 D_PAIR, D_PATH, D_RADE, D_BOOT_PAIR, D_BOOT_PATH, D_STATS = range(6)
 
 ERRORS = {0: "MANTRA_OK", 1: "MANTRA_E_INVAL", 2: "MANTRA_E_NOMEM", 3: "MANTRA_E_OVERFLOW", 4: "MANTRA_E_CUDA",
@@ -61,7 +61,7 @@ class TStats(C.Structure):
 
 
 EXPORTS = ["mantra_graph_load", "mantra_graph_info", "mantra_graph_edges", "mantra_graph_free", "mantra_estimate", "mantra_estimate_batch",
-           "mantra_temporal_stats", "mantra_sample_paths", "mantra_sample_paths_noalloc", "mantra_strerror",
+           "mantra_temporal_stats", "mantra_temporal_closeness", "mantra_sample_paths", "mantra_sample_paths_noalloc", "mantra_strerror",
            "mantra_server_create", "mantra_server_submit", "mantra_server_poll", "mantra_server_wait",
            "mantra_server_stats", "mantra_server_destroy"]
 
@@ -87,6 +87,8 @@ def lib():
     L.mantra_estimate_batch.argtypes = [C.POINTER(Problem), C.c_uint32]
     L.mantra_temporal_stats.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_uint64, C.c_double,
                                         C.POINTER(TStats), u64p, C.c_uint32]
+    L.mantra_temporal_closeness.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_uint64, u64p, dp,
+                                            u64p]
     L.mantra_sample_paths.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
                                       C.c_uint64, u32p, u32p, u64p, u32p, u32p, C.c_uint32, u32p]
     L.mantra_sample_paths_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
@@ -196,6 +198,14 @@ class Graph:
                                          _p(reach, C.c_uint64), cap), "mantra_temporal_stats")
         d = st.as_dict()
         return d, reach[:min(cap, d["d_lb"] + 1)].copy()
+
+    def temporal_closeness(self, opt, eps, seed, r_override=0):
+        """mantra_temporal_closeness -> (sums in 2^-32 units, closeness, r_s)."""
+        sm = np.zeros(max(self.n, 1), np.uint64); cl = np.zeros(max(self.n, 1), np.float64)
+        rs = C.c_uint64()
+        _chk(lib().mantra_temporal_closeness(self.h, _opt(opt), eps, seed, r_override, _p(sm, C.c_uint64),
+                                             _p(cl, C.c_double), C.byref(rs)), "mantra_temporal_closeness")
+        return sm[:self.n], cl[:self.n], rs.value
 
     def sample_paths(self, opt, seed, i0, count, dom_pair=D_PAIR, dom_path=D_PATH, cap=None, edges=False):
         """mantra_sample_paths -> list of (s, z, sigma, path) per sample; with
