@@ -586,7 +586,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
         } else {
             any_b = true; bn = std::max(bn, it.G->n); bA = std::max(bA, it.G->A);
             bsamples += it.job.count;
-            frac |= it.job.ob || it.job.rtb || (it.job.stats && it.job.opt == 3);
+            frac |= it.job.ob || it.job.rtb || it.job.opt == 3;
         }
     }
     E.tick_frac = frac;

@@ -313,8 +313,9 @@ __device__ __noinline__ void bfs_frac_update(int mode, FracCtx* x) {
 }
 
 // BFS_NT threads per CTA, 1024 / BFS_NT CTAs per SM at 64 registers.  FRAC:
-// the instantiation that also runs the ob and RTB updates (a tick with such a
-// problem launches it); the others report those jobs as a consistency error.
+// the instantiation that also runs the ob and RTB updates and fsfm (a tick
+// with such a problem launches it); the others report those jobs as a
+// consistency error.
 template <bool WIDE, int BFS_NT, bool FRAC>
 __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks, const uint64_t* unit_start,
                                                    const uint32_t* ntasks_p, u64* work,
@@ -446,9 +447,10 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
         // fsfm (foremost first, then fewest hops): no stop at z's first level;
         // every state up to z's latest in-edge time, the endpoint is z's
         // earliest slot found at any level
-        const bool fsfm = job.opt == 3 && !full;
+        // earliest slot found at any level (FRAC instantiation only)
+        const bool fsfm = FRAC && job.opt == 3 && !full;
         const uint32_t tz = full ? NONE : g.tmax_in[z];
-        const uint32_t zlo = full ? NONE : g.slot_ptr[z], zhi = full ? NONE : g.slot_ptr[z + 1];
+        const uint32_t zlo = fsfm ? g.slot_ptr[z] : 0u, zhi = fsfm ? g.slot_ptr[z + 1] : 0u;
         bool live = ok && (g.out_ptr[s + 1] > g.out_ptr[s]);
         if (!full && (g.slot_ptr[z + 1] == g.slot_ptr[z])) live = false;   // z has no in-edges
 
@@ -913,7 +915,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
 
         // ---------------- ob (Sec. 4.1) and RTB (App. C) updates (block-uniform conditions) ----------------
         if constexpr (!FRAC) {
-            if ((job.ob || job.rtb || (stats && job.opt == 3)) && tid == 0) set_status(job.status, ST_CHECK);
+            if ((job.ob || job.rtb || job.opt == 3) && tid == 0) set_status(job.status, ST_CHECK);
         } else {
             const int mode = (job.ob && job.hits && found && !sh_ovf && !sh_err && sh_d >= 2) ? 1
                            : (job.rtb && job.hits && live && !sh_ovf && k >= 2) ? 2
