@@ -250,19 +250,50 @@ def run_serving(M, graphs_uvt, reqs):
     return plain, served
 
 
-def cpu_oracle_rates(u, v, t, seed, budget_s=6.0):
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_rates(u, v, t, seed, budget_s=6.0, threads=1, graph=None):
     """Oracle pairs/s per optimality on a bounded prefix of the estimation
-    samples (single thread)."""
+    samples.  With threads > 1 the oracle's per-sample call runs on that many
+    host threads over disjoint sample indices (the call releases the GIL; the
+    oracle itself is unchanged), and the rate is samples / wall time."""
     from oracle import oracle as O
-    g = O.Graph(u, v, t)
+    g = graph if graph is not None else O.Graph(u, v, t)
     rates, counts = {}, {}
     for name in OPTS:
         opt = {"sh": 0, "sfm": 1, "pfm": 2}[name]
-        done, t0 = 0, time.perf_counter()
-        while time.perf_counter() - t0 < budget_s:
-            k = 1 if opt != 2 else 64
-            g.samples(opt, seed, done, k, cap=64)
-            done += k
+        k = 1 if opt != 2 else 64
+        lock = threading.Lock()
+        nxt = [0]
+        t0 = time.perf_counter()
+        deadline = t0 + budget_s
+
+        def worker():
+            done = 0
+            while time.perf_counter() < deadline:
+                with lock:
+                    i0 = nxt[0]
+                    nxt[0] += k
+                g.samples(opt, seed, i0, k, cap=64)
+                done += k
+            return done
+
+        if threads <= 1:
+            done = worker()
+        else:
+            ths, res = [], [0] * threads
+            for x in range(threads):
+                th = threading.Thread(target=lambda x=x: res.__setitem__(x, worker()))
+                th.start()
+                ths.append(th)
+            for th in ths:
+                th.join()
+            done = sum(res)
         dt = time.perf_counter() - t0
         rates[name] = done / dt
         counts[name] = done
@@ -274,14 +305,17 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    from oracle import oracle as O
     u, v, t = workload()
+    g = O.Graph(u, v, t)
+    cores = host_cores()
     per_step_budget = max(1.0, 20.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        cpu_oracle_rates(u, v, t, 1, budget_s=per_step_budget / 4)
+        cpu_oracle_rates(u, v, t, 1, budget_s=per_step_budget / 4, threads=cores, graph=g)
     # equal numbers of samples per optimality: time per sample triple = sum_o 1/rate_o
     tot_s, tot_n = 0.0, 0
     for k in range(args.steps):
-        rates, counts = cpu_oracle_rates(u, v, t, 100 + k, budget_s=per_step_budget / 3)
+        rates, counts = cpu_oracle_rates(u, v, t, 100 + k, budget_s=per_step_budget / 3, threads=cores, graph=g)
         tot_s += sum(1.0 / rates[o] for o in OPTS)
         tot_n += len(OPTS)
     value = tot_n / tot_s
@@ -289,10 +323,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_s / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step: the first estimation samples of sh, sfm and pfm, %.1f s each; "
-                                       "equal sample counts per optimality (harmonic mean of the rates)" %
-                                       (per_step_budget / 3)},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": "per step: the first estimation samples of sh, sfm and pfm on %d host "
+                                       "threads, %.1f s of wall time each; equal sample counts per optimality "
+                                       "(harmonic mean of the rates)" % (cores, per_step_budget / 3)},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -479,13 +513,22 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            rates, counts = cpu_oracle_rates(u, v, t, 1, budget_s=6.0)
+            from oracle import oracle as O
+            og = O.Graph(u, v, t)
+            cores = host_cores()
             per_opt = {o: sum(st[o]["r"] + st[o]["bootstrap"] for st in infos_all) for o in OPTS}
+            rates1, counts1 = cpu_oracle_rates(u, v, t, 1, budget_s=3.0, graph=og)
+            rates, counts = cpu_oracle_rates(u, v, t, 1, budget_s=3.0, threads=cores, graph=og)
             t_cpu = sum(per_opt[o] / rates[o] for o in OPTS)
-            cpu = {"value": sum(per_opt.values()) / t_cpu, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                   "sample": "first %d/%d/%d estimation samples (sh/sfm/pfm), ~6 s each, weighted by the GPU "
-                             "run's per-optimality sample counts" % (counts["sh"], counts["sfm"], counts["pfm"]),
-                   "per_opt_pairs_per_s": {o: round(rates[o], 2) for o in OPTS}}
+            t_cpu1 = sum(per_opt[o] / rates1[o] for o in OPTS)
+            cpu = {"value": sum(per_opt.values()) / t_cpu, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                   "sample": "first %d/%d/%d estimation samples (sh/sfm/pfm) on %d host threads, 3 s of wall time "
+                             "each, weighted by the GPU run's per-optimality sample counts"
+                             % (counts["sh"], counts["sfm"], counts["pfm"], cores),
+                   "per_opt_pairs_per_s": {o: round(rates[o], 2) for o in OPTS},
+                   "single_thread": {"value": sum(per_opt.values()) / t_cpu1, "cores": 1,
+                                     "sample": "first %d/%d/%d samples, 3 s each"
+                                               % (counts1["sh"], counts1["sfm"], counts1["pfm"])}}
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max * 1000.0 / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded Chung-Lu bursty)",

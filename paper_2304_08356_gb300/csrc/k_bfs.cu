@@ -446,7 +446,6 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
         const bool full = stats || job.rtb;   // untruncated search (no target)
         // fsfm (foremost first, then fewest hops): no stop at z's first level;
         // every state up to z's latest in-edge time, the endpoint is z's
-        // earliest slot found at any level
         // earliest slot found at any level (FRAC instantiation only)
         const bool fsfm = FRAC && job.opt == 3 && !full;
         const uint32_t tz = full ? NONE : g.tmax_in[z];
