@@ -47,6 +47,17 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct HostEdge { uint32_t t, u, v; };
 
+// Stable counting sort of a by key(e) in [0, nkeys); tmp: scratch of a's size.
+template <typename Key>
+void counting_sort(std::vector<HostEdge>& a, std::vector<HostEdge>& tmp, uint32_t nkeys, Key key) {
+    std::vector<size_t> pos((size_t)nkeys + 1, 0);
+    for (const HostEdge& e : a) pos[(size_t)key(e) + 1] += 1;
+    for (size_t k = 0; k < nkeys; ++k) pos[k + 1] += pos[k];
+    tmp.resize(a.size());
+    for (const HostEdge& e : a) tmp[pos[key(e)]++] = e;
+    a.swap(tmp);
+}
+
 // ---------------------------------------------------------------------------
 // Temporal-edge store (paper Sec. 3: the temporal graph; the paper's own code
 // keeps a sparse n x |T| table, here every arrival appearance (v,t) gets a
@@ -66,12 +77,14 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
         if (u[e] == v[e]) { ++loops; continue; }
         es.push_back(HostEdge{t[e], u[e], v[e]});
     }
-    auto by_tuv = [](const HostEdge& a, const HostEdge& b) {
-        if (a.t != b.t) return a.t < b.t;
-        if (a.u != b.u) return a.u < b.u;
-        return a.v < b.v;
-    };
-    std::sort(es.begin(), es.end(), by_tuv);
+    // (t, u, v) order by stable counting sorts on v, u, then t (two 16-bit
+    // digits): linear passes instead of a comparison sort
+    std::vector<HostEdge> tmp;
+    try { tmp.resize(es.size()); } catch (...) { return MANTRA_E_NOMEM; }
+    counting_sort(es, tmp, n, [](const HostEdge& e) { return e.v; });
+    counting_sort(es, tmp, n, [](const HostEdge& e) { return e.u; });
+    counting_sort(es, tmp, 1u << 16, [](const HostEdge& e) { return e.t & 0xFFFFu; });
+    counting_sort(es, tmp, 1u << 16, [](const HostEdge& e) { return e.t >> 16; });
     auto same = [](const HostEdge& a, const HostEdge& b) { return a.t == b.t && a.u == b.u && a.v == b.v; };
     const size_t before = es.size();
     es.erase(std::unique(es.begin(), es.end(), same), es.end());
@@ -82,13 +95,10 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
     std::vector<uint32_t> st_u(M), st_v(M), st_t(M);
     for (uint32_t e = 0; e < M; ++e) { st_u[e] = es[e].u; st_v[e] = es[e].v; st_t[e] = es[e].t; }
 
-    // in-CSR by (v, t, u) and slots
+    // in-CSR by (v, t, u) and slots: a stable sort by v of the (t, u, v) order
     std::vector<HostEdge> ein(es);
-    std::sort(ein.begin(), ein.end(), [](const HostEdge& a, const HostEdge& b) {
-        if (a.v != b.v) return a.v < b.v;
-        if (a.t != b.t) return a.t < b.t;
-        return a.u < b.u;
-    });
+    tmp.resize(ein.size());
+    counting_sort(ein, tmp, n, [](const HostEdge& e) { return e.v; });
     std::vector<uint32_t> in_u(M), in_slot(M), slot_t, slot_v, slot_in, slot_ptr(n + 1, 0);
     slot_t.reserve(M); slot_v.reserve(M); slot_in.reserve(M + 1);
     for (uint32_t e = 0; e < M; ++e) {
@@ -120,12 +130,9 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
     G->n_uedge = n_uedge;
 
     // out-CSR by (u, t, v)
-    std::vector<HostEdge> eo(std::move(ein));
-    std::sort(eo.begin(), eo.end(), [](const HostEdge& a, const HostEdge& b) {
-        if (a.u != b.u) return a.u < b.u;
-        if (a.t != b.t) return a.t < b.t;
-        return a.v < b.v;
-    });
+    // (u, t, v): a stable sort by u of the (t, u, v) order
+    std::vector<HostEdge> eo(es);
+    counting_sort(eo, tmp, n, [](const HostEdge& e) { return e.u; });
     std::vector<uint32_t> out_ptr(n + 1, 0), out_v(M), out_t(M), out_slot(M);
     for (uint32_t e = 0; e < M; ++e) {
         out_ptr[eo[e].u + 1] += 1;
