@@ -45,16 +45,38 @@ int cuda_fail(cudaError_t e, const char* what, int line) {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-struct HostEdge { uint32_t t, u, v; };
+struct HostEdge { uint32_t t, u, v, id; };   // id: position in the (t, u, v) stream
 
-// Stable counting sort of a by key(e) in [0, nkeys); tmp: scratch of a's size.
+// Stable counting sort of a by key(e) in [0, nkeys); tmp: scratch of a's
+// size.  Large inputs are split into contiguous chunks, one host thread each:
+// per-chunk counts, offsets in (key, chunk) order, per-chunk scatter -- the
+// same order as one pass over the whole array.
 template <typename Key>
 void counting_sort(std::vector<HostEdge>& a, std::vector<HostEdge>& tmp, uint32_t nkeys, Key key) {
-    std::vector<size_t> pos((size_t)nkeys + 1, 0);
-    for (const HostEdge& e : a) pos[(size_t)key(e) + 1] += 1;
-    for (size_t k = 0; k < nkeys; ++k) pos[k + 1] += pos[k];
-    tmp.resize(a.size());
-    for (const HostEdge& e : a) tmp[pos[key(e)]++] = e;
+    const size_t m = a.size();
+    tmp.resize(m);
+    unsigned T = std::min(16u, std::max(1u, std::thread::hardware_concurrency()));
+    if (m < ((size_t)1 << 17) || (size_t)nkeys * T > ((size_t)1 << 24)) T = 1;
+    const size_t chunk = (m + T - 1) / T;
+    std::vector<std::vector<size_t>> pos(T, std::vector<size_t>((size_t)nkeys, 0));
+    auto run = [&](auto fn) {
+        if (T == 1) { fn(0u); return; }
+        std::vector<std::thread> th;
+        for (unsigned x = 0; x < T; ++x) th.emplace_back(fn, x);
+        for (auto& h : th) h.join();
+    };
+    run([&](unsigned x) {
+        const size_t lo = std::min(m, x * chunk), hi = std::min(m, lo + chunk);
+        for (size_t k = lo; k < hi; ++k) pos[x][key(a[k])] += 1;
+    });
+    size_t acc = 0;
+    for (size_t b = 0; b < nkeys; ++b)
+        for (unsigned x = 0; x < T; ++x) { const size_t c = pos[x][b]; pos[x][b] = acc; acc += c; }
+    run([&](unsigned x) {
+        const size_t lo = std::min(m, x * chunk), hi = std::min(m, lo + chunk);
+        size_t* p = pos[x].data();
+        for (size_t k = lo; k < hi; ++k) tmp[p[key(a[k])]++] = a[k];
+    });
     a.swap(tmp);
 }
 
@@ -75,7 +97,7 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
     for (uint64_t e = 0; e < m; ++e) {
         if (u[e] >= n || v[e] >= n || t[e] > 0xFFFFFFFDu) return MANTRA_E_INVAL;
         if (u[e] == v[e]) { ++loops; continue; }
-        es.push_back(HostEdge{t[e], u[e], v[e]});
+        es.push_back(HostEdge{t[e], u[e], v[e], 0u});
     }
     // (t, u, v) order by stable counting sorts on v, u, then t (two 16-bit
     // digits): linear passes instead of a comparison sort
@@ -93,13 +115,17 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
     G->n = n; G->m = M; G->self_loops = loops; G->duplicates = before - es.size();
 
     std::vector<uint32_t> st_u(M), st_v(M), st_t(M);
-    for (uint32_t e = 0; e < M; ++e) { st_u[e] = es[e].u; st_v[e] = es[e].v; st_t[e] = es[e].t; }
+    for (uint32_t e = 0; e < M; ++e) {
+        st_u[e] = es[e].u; st_v[e] = es[e].v; st_t[e] = es[e].t;
+        es[e].id = e;
+    }
 
-    // in-CSR by (v, t, u) and slots: a stable sort by v of the (t, u, v) order
+    // in-CSR by (v, t, u) and slots: a stable sort by v of the (t, u, v) order;
+    // inpos[id] = the in-CSR index of stream edge id
     std::vector<HostEdge> ein(es);
     tmp.resize(ein.size());
     counting_sort(ein, tmp, n, [](const HostEdge& e) { return e.v; });
-    std::vector<uint32_t> in_u(M), in_slot(M), slot_t, slot_v, slot_in, slot_ptr(n + 1, 0);
+    std::vector<uint32_t> in_u(M), in_slot(M), inpos(M), slot_t, slot_v, slot_in, slot_ptr(n + 1, 0);
     slot_t.reserve(M); slot_v.reserve(M); slot_in.reserve(M + 1);
     for (uint32_t e = 0; e < M; ++e) {
         if (e == 0 || ein[e].v != ein[e - 1].v || ein[e].t != ein[e - 1].t) {
@@ -108,40 +134,40 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
         }
         in_u[e] = ein[e].u;
         in_slot[e] = (uint32_t)slot_t.size() - 1;
+        inpos[ein[e].id] = e;
     }
     const uint32_t A = (uint32_t)slot_t.size();
     slot_in.push_back(M);
     for (uint32_t x = 0; x < n; ++x) slot_ptr[x + 1] += slot_ptr[x];
     G->A = A;
 
-    // underlying-edge ids (App. A): the distinct in-neighbours of each v in
-    // ascending order get consecutive ids, v by v -- the rank of (v, u)
-    std::vector<uint32_t> in_uedge(M), nb;
-    uint32_t n_uedge = 0;
-    for (uint32_t x = 0; x < n; ++x) {
-        const uint32_t e_lo = slot_in[slot_ptr[x]], e_hi = slot_in[slot_ptr[x + 1]];
-        nb.assign(in_u.begin() + e_lo, in_u.begin() + e_hi);
-        std::sort(nb.begin(), nb.end());
-        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
-        for (uint32_t e = e_lo; e < e_hi; ++e)
-            in_uedge[e] = n_uedge + (uint32_t)(std::lower_bound(nb.begin(), nb.end(), in_u[e]) - nb.begin());
-        n_uedge += (uint32_t)nb.size();
-    }
-    G->n_uedge = n_uedge;
-
-    // out-CSR by (u, t, v)
-    // (u, t, v): a stable sort by u of the (t, u, v) order
+    // out-CSR by (u, t, v): a stable sort by u of the (t, u, v) order; each
+    // edge's head slot is the slot of its in-CSR position
     std::vector<HostEdge> eo(es);
     counting_sort(eo, tmp, n, [](const HostEdge& e) { return e.u; });
     std::vector<uint32_t> out_ptr(n + 1, 0), out_v(M), out_t(M), out_slot(M);
     for (uint32_t e = 0; e < M; ++e) {
         out_ptr[eo[e].u + 1] += 1;
         out_v[e] = eo[e].v; out_t[e] = eo[e].t;
-        const uint32_t* b = slot_t.data() + slot_ptr[eo[e].v];
-        const uint32_t* f = slot_t.data() + slot_ptr[eo[e].v + 1];
-        out_slot[e] = (uint32_t)(std::lower_bound(b, f, eo[e].t) - slot_t.data());
+        out_slot[e] = in_slot[inpos[eo[e].id]];
     }
     for (uint32_t x = 0; x < n; ++x) out_ptr[x + 1] += out_ptr[x];
+
+    // underlying-edge ids (App. A): the rank of (v, u) among the distinct
+    // ordered pairs -- a stable sort by v of the (u, t, v) order lists the
+    // edges by (v, u, t), so equal pairs are consecutive
+    std::vector<uint32_t> in_uedge(M);
+    uint32_t n_uedge = 0;
+    {
+        std::vector<HostEdge> evu(eo);
+        counting_sort(evu, tmp, n, [](const HostEdge& e) { return e.v; });
+        for (uint32_t e = 0; e < M; ++e) {
+            if (e > 0 && (evu[e].v != evu[e - 1].v || evu[e].u != evu[e - 1].u)) ++n_uedge;
+            in_uedge[inpos[evu[e].id]] = n_uedge;
+        }
+        if (M > 0) ++n_uedge;
+    }
+    G->n_uedge = n_uedge;
     std::vector<uint32_t> tmax_in(n, 0), tmin_out(n, 0);
     uint64_t cbound = 0;
     uint32_t max_slot_in = 0;
