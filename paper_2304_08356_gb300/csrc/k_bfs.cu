@@ -30,6 +30,7 @@ namespace mantra {
 
 constexpr int IPT = 2;            // frontier states per thread in a segmented-scan tile
 constexpr int WALK_K = 2;         // edge windows with loads in flight per warp in the push
+constexpr int CK = 8;             // bitmap words in flight per lane in the compaction and cleanup scans
 
 // ob update of one sample (Sec. 4.1), all threads of the CTA: continuation
 // counts dl (the number of optimal ways from a state to z's endpoints) per
@@ -666,7 +667,18 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             const uint32_t per_w = (((words + BFS_NW - 1) / BFS_NW) + 31u) & ~31u;
             const uint32_t w_lo = min((uint32_t)wid * per_w, words), w_hi = min(w_lo + per_w, words);
             uint32_t cnt = 0;
-            for (uint32_t w = w_lo + lane; w < w_hi; w += 32) cnt += __popc(__ldcg(N + w));
+            // CK words per lane in flight: the bitmap is read from L2, so the
+            // loads of a batch are issued before any is used
+            for (uint32_t w0 = w_lo + lane; w0 < w_hi; w0 += 32u * CK) {
+                uint32_t x[CK];
+#pragma unroll
+                for (int j = 0; j < CK; ++j) {
+                    const uint32_t w = w0 + 32u * j;
+                    x[j] = (w < w_hi) ? __ldcg(N + w) : 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < CK; ++j) cnt += __popc(x[j]);
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
             if (lane == 0) sm_wcnt[wid] = cnt;
@@ -687,36 +699,46 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             uint32_t off = fbase + sm_wcnt[wid];
             uint32_t newv = 0;
             const uint32_t* const g_slot_v2 = g.slot_v;
-            for (uint32_t w0 = w_lo; w0 < w_hi; w0 += 32) {
-                const uint32_t w = w0 + lane;
-                uint32_t bits = (w < w_hi) ? __ldcg(N + w) : 0u;
-                if (bits) { V[w] |= bits; N[w] = 0u; }
-                const uint32_t c = __popc(bits);
-                uint32_t incl = c;
+            for (uint32_t wb = w_lo; wb < w_hi; wb += 32u * CK) {
+                uint32_t xb[CK];
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                    if (lane >= o) incl += y;
+                for (int jj = 0; jj < CK; ++jj) {
+                    const uint32_t w = wb + 32u * jj + lane;
+                    xb[jj] = (w < w_hi) ? __ldcg(N + w) : 0u;
                 }
-                uint32_t pos = off + incl - c;
-                while (bits) {
-                    const uint32_t b = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const uint32_t a = w * 32u + b;
-                    F[pos++] = a;
-                    if (fsfm && a >= zlo && a < zhi) atomicMin(&sh_zmin, a);
-                    if (stats && job.opt != 3) {
-                        const uint32_t v = g_slot_v2[a];
-                        if (v != s) {
-                            const uint32_t old = atomicOr(VB + (v >> 5), 1u << (v & 31));
-                            if (!(old & (1u << (v & 31)))) {
-                                ++newv;
-                                if (job.clos) atomicAdd(job.clos + v, recip32(k + 1));
+#pragma unroll
+                for (int jj = 0; jj < CK; ++jj) {
+                    const uint32_t w = wb + 32u * jj + lane;
+                    uint32_t bits = xb[jj];
+                    if (__ballot_sync(0xFFFFFFFFu, bits != 0u) == 0u) continue;   // nothing in these 32 words
+                    if (bits) { V[w] |= bits; N[w] = 0u; }
+                    const uint32_t c = __popc(bits);
+                    uint32_t incl = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    uint32_t pos = off + incl - c;
+                    while (bits) {
+                        const uint32_t b = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const uint32_t a = w * 32u + b;
+                        F[pos++] = a;
+                        if (fsfm && a >= zlo && a < zhi) atomicMin(&sh_zmin, a);
+                        if (stats && job.opt != 3) {
+                            const uint32_t v = g_slot_v2[a];
+                            if (v != s) {
+                                const uint32_t old = atomicOr(VB + (v >> 5), 1u << (v & 31));
+                                if (!(old & (1u << (v & 31)))) {
+                                    ++newv;
+                                    if (job.clos) atomicAdd(job.clos + v, recip32(k + 1));
+                                }
                             }
                         }
                     }
+                    off += __shfl_sync(0xFFFFFFFFu, incl, 31);
                 }
-                off += __shfl_sync(0xFFFFFFFFu, incl, 31);
             }
             if (stats) {
 #pragma unroll
@@ -932,14 +954,26 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
         }
 
         // ---------------- cleanup: sigma of every touched slot, bitmaps ----------------
-        for (uint32_t w = tid; w < words; w += BFS_NT) {
-            uint32_t bits = V[w] | __ldcg(N + w);
-            if (bits) {
-                V[w] = 0u; N[w] = 0u;
-                while (bits && !stats) {
-                    const uint32_t b = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    sig[w * 32u + b] = (Sig)0;
+        for (uint32_t w0 = tid; w0 < words; w0 += BFS_NT * CK) {
+            uint32_t nb[CK];
+#pragma unroll
+            for (int j = 0; j < CK; ++j) {
+                const uint32_t w = w0 + BFS_NT * j;
+                nb[j] = (w < words) ? __ldcg(N + w) : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < CK; ++j) {
+                const uint32_t w = w0 + BFS_NT * j;
+                if (w >= words) break;
+                uint32_t bits = V[w] | nb[j];
+                if (bits) {
+                    V[w] = 0u;
+                    if (nb[j]) N[w] = 0u;
+                    while (bits && !stats) {
+                        const uint32_t b = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        sig[w * 32u + b] = (Sig)0;
+                    }
                 }
             }
         }
