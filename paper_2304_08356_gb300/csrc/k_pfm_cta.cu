@@ -38,6 +38,7 @@ namespace mantra {
 
 constexpr uint32_t SRC = NONE - 1u;        // fsl of the source
 constexpr int WALK_K = 2;                  // edge windows with loads in flight per warp
+constexpr int CK = 8;                      // vertices with loads in flight per thread in the O(n) passes
 
 template <bool SM>
 __device__ __forceinline__ uint32_t ldv(const uint32_t* p) {
@@ -279,9 +280,20 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
 
         // fa' of every vertex, for the DAG tests of in-edges
         if (live) {
-            for (uint32_t v = tid; v < n; v += PC_NT) {
-                const uint32_t f = ldv<FA_SMEM>(fsl + v);
-                fat[v] = f == SRC ? 0u : (f == NONE ? NONE : __ldg(slot_t + f) + 1u);
+            for (uint32_t v0 = tid; v0 < n; v0 += PC_NT * CK) {   // CK vertices' loads in flight
+                uint32_t f[CK], tt[CK];
+#pragma unroll
+                for (int j = 0; j < CK; ++j) {
+                    const uint32_t v = v0 + PC_NT * j;
+                    f[j] = v < n ? ldv<FA_SMEM>(fsl + v) : NONE;
+                }
+#pragma unroll
+                for (int j = 0; j < CK; ++j) tt[j] = (f[j] != NONE && f[j] != SRC) ? __ldg(slot_t + f[j]) : 0u;
+#pragma unroll
+                for (int j = 0; j < CK; ++j) {
+                    const uint32_t v = v0 + PC_NT * j;
+                    if (v < n) fat[v] = f[j] == SRC ? 0u : (f[j] == NONE ? NONE : tt[j] + 1u);
+                }
             }
             __syncthreads();
         }
@@ -289,14 +301,16 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
         // edges of the prefix-foremost scan window (same count as the lane kernel):
         // stream edges with tmin_out(s) <= t <= fa(z) (z's latest in-edge time when
         // unreached), not into s
-        if (tid == 0 && live) {
+        // (warp 0, warp-wide searches)
+        if (wid == 0 && live) {
             const uint32_t ts = g.tmin_out[s];
             const uint32_t te = full ? NONE - 1u : (reached ? bound : g.tmax_in[z]);
             if (ts <= te) {
-                const uint32_t a = lower_bound_u32(g.st_t, 0, g.m, ts), b = upper_bound_u32(g.st_t, a, g.m, te);
+                const uint32_t a = warp_lower_bound(g.st_t, 0, g.m, ts), b = warp_lower_bound(g.st_t, a, g.m, te + 1u);
                 const uint32_t s0 = g.slot_ptr[s], s1 = g.slot_ptr[s + 1];
-                const uint32_t sa = lower_bound_u32(g.slot_t, s0, s1, ts), sb = upper_bound_u32(g.slot_t, sa, s1, te);
-                my_escan += (u64)(b - a) - (u64)(g.slot_in[sb] - g.slot_in[sa]);
+                const uint32_t sa = warp_lower_bound(g.slot_t, s0, s1, ts);
+                const uint32_t sb = warp_lower_bound(g.slot_t, sa, s1, te + 1u);
+                if (lane == 0) my_escan += (u64)(b - a) - (u64)(g.slot_in[sb] - g.slot_in[sa]);
             }
         }
 
@@ -304,19 +318,29 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
         // pend(v) for every v with fa(v) <= bound; their sum is the scan's number
         // of path-count updates, counted also when z is not reached
         if (live) {
-            for (uint32_t v = tid; v < n; v += PC_NT) {
-                const uint32_t fv = __ldcg(fat + v);
-                if (fv == NONE || v == s || fv - 1u > bound) continue;
-                const uint32_t a = ldv<FA_SMEM>(fsl + v);
-                const uint32_t e1 = __ldg(g.slot_in + a + 1);
-                uint32_t c = 0;
-                for (uint32_t e = __ldg(g.slot_in + a); e < e1; ++e)
-                    if (__ldcg(fat + __ldg(g.in_u + e)) < fv) ++c;
-                my_eadd += c;
-                if (reached) {
-                    pend[v] = c;
-                    sig[v] = 0ull;
-                    hop[v] = NONE;
+            for (uint32_t v0 = tid; v0 < n; v0 += PC_NT * CK) {   // CK vertices' loads in flight
+                uint32_t fvs[CK];
+#pragma unroll
+                for (int j = 0; j < CK; ++j) {
+                    const uint32_t v = v0 + PC_NT * j;
+                    fvs[j] = v < n ? __ldcg(fat + v) : NONE;
+                }
+#pragma unroll
+                for (int j = 0; j < CK; ++j) {
+                    const uint32_t v = v0 + PC_NT * j;
+                    const uint32_t fv = fvs[j];
+                    if (fv == NONE || v == s || fv - 1u > bound) continue;
+                    const uint32_t a = ldv<FA_SMEM>(fsl + v);
+                    const uint32_t e1 = __ldg(g.slot_in + a + 1);
+                    uint32_t c = 0;
+                    for (uint32_t e = __ldg(g.slot_in + a); e < e1; ++e)
+                        if (__ldcg(fat + __ldg(g.in_u + e)) < fv) ++c;
+                    my_eadd += c;
+                    if (reached) {
+                        pend[v] = c;
+                        sig[v] = 0ull;
+                        hop[v] = NONE;
+                    }
                 }
             }
         }

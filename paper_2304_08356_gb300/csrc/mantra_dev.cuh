@@ -377,6 +377,29 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t 
     return lo;
 }
 
+// First index in [lo, hi) with a[idx] >= key, by the whole warp (same
+// arguments on every lane): each step every lane probes one of 32 evenly
+// spaced positions and a ballot narrows the range 32-fold, so a search costs
+// about log32 of the range in dependent loads instead of log2.
+__device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t* __restrict__ a, uint32_t lo, uint32_t hi,
+                                                     uint32_t key) {
+    const uint32_t lane = threadIdx.x & 31;
+    while (hi - lo > 32u) {
+        const uint32_t step = (hi - lo + 31u) / 32u;
+        const uint32_t idx = lo + lane * step;
+        const bool lt = idx < hi && __ldg(a + idx) < key;
+        const uint32_t c = __popc(__ballot_sync(0xFFFFFFFFu, lt));   // probes below key: a prefix
+        if (c == 0) return lo;
+        const uint32_t nlo = lo + (c - 1u) * step + 1u;
+        const uint32_t nhi = lo + c * step;
+        lo = nlo;
+        hi = min(hi, nhi);
+    }
+    const uint32_t idx = lo + lane;
+    const bool lt = idx < hi && __ldg(a + idx) < key;
+    return lo + __popc(__ballot_sync(0xFFFFFFFFu, lt));
+}
+
 // For each k: the first index in [lo[k], hi[k]) whose value exceeds key[k]
 // (hi[k] if none), left in lo[k].  The K searches advance together so their
 // loads overlap.
