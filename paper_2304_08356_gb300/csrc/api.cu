@@ -152,6 +152,17 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
         out_slot[e] = in_slot[inpos[eo[e].id]];
     }
     for (uint32_t x = 0; x < n; ++x) out_ptr[x + 1] += out_ptr[x];
+    // first out-edge of v later than each of v's arrival slots (both rows in
+    // time order): the searches' lower ends without a search
+    std::vector<uint32_t> slot_nout(A);
+    for (uint32_t x = 0; x < n; ++x) {
+        uint32_t q = out_ptr[x];
+        const uint32_t q1 = out_ptr[x + 1];
+        for (uint32_t a = slot_ptr[x]; a < slot_ptr[x + 1]; ++a) {
+            while (q < q1 && out_t[q] <= slot_t[a]) ++q;
+            slot_nout[a] = q;
+        }
+    }
 
     // underlying-edge ids (App. A): the rank of (v, u) among the distinct
     // ordered pairs -- a stable sort by v of the (u, t, v) order lists the
@@ -189,7 +200,7 @@ int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_
                   {&slot_v, &G->dg.slot_v}, {&slot_in, &G->dg.slot_in}, {&in_u, &G->dg.in_u},
                   {&in_slot, &G->dg.in_slot}, {&st_u, &G->dg.st_u}, {&st_v, &G->dg.st_v},
                   {&st_t, &G->dg.st_t}, {&tmax_in, &G->dg.tmax_in}, {&tmin_out, &G->dg.tmin_out},
-                  {&in_uedge, &G->dg.in_uedge}};
+                  {&in_uedge, &G->dg.in_uedge}, {&slot_nout, &G->dg.slot_nout}};
     size_t total = 0;
     for (auto& a : arrs) total += al256((a.h->size() + 1) * 4);
     if (cudaMalloc(&G->dmem, total) != cudaSuccess) return MANTRA_E_NOMEM;

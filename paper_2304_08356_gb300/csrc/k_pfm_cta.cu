@@ -249,9 +249,10 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                         const bool again = (ldv<FA_SMEM>(XB + (uu >> 5)) >> (uu & 31)) & 1u;
                         const uint32_t cap = again ? lo_prev[uu] : r1;
                         const uint32_t fu = ldv<FA_SMEM>(fsl + uu);
-                        lo[2 * j] = hi[2 * j] = r0;
-                        if (fu != SRC) { hi[2 * j] = r1; key[2 * j] = __ldg(slot_t + fu); }
-                        lo[2 * j + 1] = r0; hi[2 * j + 1] = cap; key[2 * j + 1] = bound;
+                        // first t > fa(u): the store's per-slot table, no search
+                        const uint32_t f0 = (fu != SRC) ? __ldg(g.slot_nout + fu) : r0;
+                        lo[2 * j] = hi[2 * j] = f0;
+                        lo[2 * j + 1] = min(f0, cap); hi[2 * j + 1] = cap; key[2 * j + 1] = bound;
                     }
                 }
                 upper_bounds<4>(out_t, lo, hi, key);

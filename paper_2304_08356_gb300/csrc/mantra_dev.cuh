@@ -11,6 +11,7 @@
 //   stream   by (t, u, v): st_u[m], st_v[m], st_t[m]
 //   tmax_in[n]  latest in-edge time of v (valid when v has a slot)
 //   tmin_out[n] earliest out-edge time of u (valid when u has out-edges)
+//   slot_nout[A] first out-edge of v later than slot (v, t): out-row index
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -59,6 +60,7 @@ struct DevGraph {
     const uint32_t* in_uedge;
     uint32_t n_uedge;       // distinct ordered pairs (u, v) with a temporal edge
     uint32_t pad_;
+    const uint32_t* slot_nout;   // per arrival slot (v, t): first index of v's out-row with time > t
 };
 
 // One launch over a range (or list) of sample indices.
