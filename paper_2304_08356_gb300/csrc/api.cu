@@ -323,7 +323,7 @@ struct Engine {
     int tick_bfs_nt = 512;     // sh/sfm CTA size of the current tick
     bool tick_frac = false;    // the tick has an ob or RTB problem on the sh/sfm kernel
     char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; uint32_t pfm_n = 0, pfm_lcap = 0; uint64_t pfm_warps = 0;
-    char* pc_mem = nullptr; PfmCtaWs pcws{}; int pc_grid = 0; uint32_t pc_n = 0;
+    char* pc_mem = nullptr; PfmCtaWs pcws{}; int pc_grid = 0; uint32_t pc_n = 0, pc_cb = 0;
     bool tick_cta = false;   // pfm samples of the current tick run one per CTA
     // tick tables
     uint32_t cap = 0;
@@ -464,9 +464,10 @@ struct Engine {
 
     // pfm with one CTA per sample: one region per resident CTA, at most a third
     // of free memory; arrival slots and flag bitmaps in shared memory when they fit.
-    int ensure_pfm_cta(uint32_t n) {
-        if (pc_mem && n <= pc_n) return MANTRA_OK;
+    int ensure_pfm_cta(uint32_t n, uint32_t cb) {
+        if (pc_mem && n <= pc_n && cb <= pc_cb) return MANTRA_OK;
         n = std::max(n, pc_n);
+        cb = std::max(cb, pc_cb);
         if (pc_mem) { cudaStreamSynchronize(sb); cudaStreamSynchronize(sa); cudaFree(pc_mem); pc_mem = nullptr; }
         // MANTRA_PFM_CTA_NT=256 takes 256-thread CTAs (four per SM);
         // MANTRA_PFM_CTA_SMEM=0 keeps the arrival state in global memory
@@ -475,7 +476,7 @@ struct Engine {
         const size_t smem = pfm_cta_smem_bytes(n);
         bool in_smem = smem + pfm_cta_static_smem(nt) + 1024 <= smem_optin;
         if (const char* env = std::getenv("MANTRA_PFM_CTA_SMEM")) in_smem = in_smem && env[0] != '0';
-        const size_t region = pfm_cta_region_bytes(n, in_smem, &pcws);
+        const size_t region = pfm_cta_region_bytes(n, cb, in_smem, &pcws);
         pcws.nt = nt;
         CU(pfm_cta_configure(in_smem ? smem : 0));
         int per_sm = 0;
@@ -489,6 +490,7 @@ struct Engine {
         pcws.stride = region;
         pc_grid = grid;
         pc_n = n;
+        pc_cb = cb;
         invalidate_graph();
         return MANTRA_OK;
     }
@@ -636,7 +638,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     E.tick_frac = frac;
     const bool cta = any_p && !wide && pfm_use_cta();
     if (any_b && (rc = E.ensure_bfs(bn, bA)) != MANTRA_OK) return rc;
-    if (any_p && cta && (rc = E.ensure_pfm_cta(pn)) != MANTRA_OK) return rc;
+    if (any_p && cta && (rc = E.ensure_pfm_cta(pn, plc)) != MANTRA_OK) return rc;
     if (any_p && !cta && (rc = E.ensure_pfm(pn, plc, pwarps)) != MANTRA_OK) return rc;
     E.tick_cta = cta;
     // sh/sfm CTA shape: 1024 threads for ticks of at most two samples per resident

@@ -10,10 +10,12 @@
 //             bound = the latest in-edge time of z, then fa(z) once z is
 //             reached (later edges reach no vertex earlier than z).
 //   counts    pfm paths use the edges (w, v, fa(v)) with fa(w) < fa(v): a DAG.
-//             pend(v) = number of such in-edges; a vertex whose in-edges are
-//             all counted is expanded (Kahn levels) and adds sigma(u) to
-//             sigma(v) over its DAG out-edges (hop(v) = min hop(u) + 1 for the
-//             Algorithm 2 searches).
+//             A scan of each reached vertex's arrival-slot in-edges finds them
+//             all: pend(v) = their number, and the DAG is stored as out-lists
+//             (per-tail counts, a scan, a fill).  A vertex whose in-edges are
+//             all counted is expanded (Kahn levels) over its list and adds
+//             sigma(u) to sigma(v) (hop(v) = min hop(u) + 1 for the Algorithm 2
+//             searches).
 //   draw      backward over DAG in-edges by ascending w, weight sigma(w)
 //             (App. C path sampler), then the Update step of Algorithm 1.
 // Path counts are 64-bit; a sample whose count overflows goes to the
@@ -58,6 +60,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
     __shared__ int sh_t;
     __shared__ uint64_t sh_q;
     __shared__ u64 sm_scan64[32];
+    __shared__ uint32_t sm_scan32[32];
     __shared__ uint32_t sm_wcnt[PC_NW];
     __shared__ uint32_t sh_L, sh_Gc, sh_ovf, sh_err, sh_len;
     __shared__ uint32_t sh_rade[4];
@@ -80,6 +83,8 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
     uint32_t* pathe = reinterpret_cast<uint32_t*>(region + ws.o_pathe);   // in-CSR index of path edge k
     u64* dl = reinterpret_cast<u64*>(region + ws.o_dl);                  // ob: continuation counts
     uint32_t* kofs = reinterpret_cast<uint32_t*>(region + ws.o_kofs);    // ob: Kahn round offsets in Fl
+    uint32_t* dcnt = reinterpret_cast<uint32_t*>(region + ws.o_dcnt);    // DAG out-list ends per vertex
+    uint32_t* dag = reinterpret_cast<uint32_t*>(region + ws.o_dag);      // DAG successors, grouped by tail
 
     const uint32_t ntasks = *ntasks_p;
     u64* flush_ctr = nullptr;
@@ -293,7 +298,10 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
 #pragma unroll
                 for (int j = 0; j < CK; ++j) {
                     const uint32_t v = v0 + PC_NT * j;
-                    if (v < n) fat[v] = f[j] == SRC ? 0u : (f[j] == NONE ? NONE : tt[j] + 1u);
+                    if (v < n) {
+                        fat[v] = f[j] == SRC ? 0u : (f[j] == NONE ? NONE : tt[j] + 1u);
+                        dcnt[v] = 0u;
+                    }
                 }
             }
             __syncthreads();
@@ -334,8 +342,13 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                     const uint32_t a = ldv<FA_SMEM>(fsl + v);
                     const uint32_t e1 = __ldg(g.slot_in + a + 1);
                     uint32_t c = 0;
-                    for (uint32_t e = __ldg(g.slot_in + a); e < e1; ++e)
-                        if (__ldcg(fat + __ldg(g.in_u + e)) < fv) ++c;
+                    for (uint32_t e = __ldg(g.slot_in + a); e < e1; ++e) {
+                        const uint32_t w = __ldg(g.in_u + e);
+                        if (__ldcg(fat + w) < fv) {
+                            ++c;
+                            if (reached) atomicAdd(dcnt + w, 1u);
+                        }
+                    }
                     my_eadd += c;
                     if (reached) {
                         pend[v] = c;
@@ -345,9 +358,38 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                 }
             }
         }
+        // The prefix-foremost DAG as out-lists (the in-edge scan above found every
+        // DAG edge): dcnt holds each vertex's out-degree, then an exclusive scan
+        // (a contiguous block of vertices per thread), then the fill advances it
+        // to each list's end, so u's successors are dag[(u ? dcnt[u-1] : 0) .. dcnt[u]).
+        if (reached) {
+            __syncthreads();
+            const uint32_t per = (n + PC_NT - 1) / PC_NT;
+            const uint32_t v_lo = min((uint32_t)tid * per, n), v_hi = min(v_lo + per, n);
+            uint32_t sum = 0;
+            for (uint32_t v = v_lo; v < v_hi; ++v) sum += __ldcg(dcnt + v);
+            uint32_t tot;
+            uint32_t run = block_exclusive_scan<PC_NT>(sum, &tot, sm_scan32);
+            for (uint32_t v = v_lo; v < v_hi; ++v) { const uint32_t c = __ldcg(dcnt + v); dcnt[v] = run; run += c; }
+            if (tot > ws.dag_cap && tid == 0) { sh_err = 1; set_status(job.status, ST_CHECK); }
+            __syncthreads();
+            if (tot <= ws.dag_cap) {
+                for (uint32_t v = tid; v < n; v += PC_NT) {
+                    const uint32_t fv = __ldcg(fat + v);
+                    if (fv == NONE || v == s || fv - 1u > bound) continue;
+                    const uint32_t a = ldv<FA_SMEM>(fsl + v);
+                    const uint32_t e1 = __ldg(g.slot_in + a + 1);
+                    for (uint32_t e = __ldg(g.slot_in + a); e < e1; ++e) {
+                        const uint32_t w = __ldg(g.in_u + e);
+                        if (__ldcg(fat + w) < fv) dag[atomicAdd(dcnt + w, 1u)] = v;
+                    }
+                }
+            }
+            __syncthreads();
+        }
         // Kahn rounds are appended: round r's vertices are Fl[kofs[r] .. kofs[r+1])
         uint32_t kb = 0, nr = 0;
-        if (reached) {
+        if (reached && !sh_err) {
             if (tid == 0) { sig[s] = 1ull; hop[s] = 0u; NB[s >> 5] |= 1u << (s & 31); }
             __syncthreads();
             for (;;) {
@@ -355,28 +397,23 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                 if (L == 0) break;
                 if (tid == 0) { ++my_rounds; kofs[nr] = kb; }
                 for (uint32_t c0 = 0; c0 < L; c0 += CHUNK) {
-                    // [lo_prev(u), first t > bound): u's out-edges after its arrival
-                    uint32_t u[2], lo[2], hi[2], key[2];
+                    // u's DAG successors
+                    uint32_t u[2], rl[2], rh[2];
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
                         const uint32_t x = c0 + (uint32_t)tid + (uint32_t)j * PC_NT;
-                        lo[j] = hi[j] = key[j] = 0u;
+                        rl[j] = rh[j] = 0u;
                         u[j] = NONE;
                         if (x < L) {
                             const uint32_t uu = Fl[kb + x];
                             u[j] = uu;
-                            lo[j] = lo_prev[uu];
-                            hi[j] = out_ptr[uu + 1];
-                            key[j] = bound;
+                            rl[j] = uu ? __ldcg(dcnt + uu - 1) : 0u;
+                            rh[j] = __ldcg(dcnt + uu);
                         }
                     }
-                    uint32_t rl[2] = {lo[0], lo[1]};
-                    upper_bounds<2>(out_t, lo, hi, key);
-                    const uint32_t rh[2] = {lo[0], lo[1]};
                     const uint32_t E = table(u, rl, rh);
                     if (tid == 0) my_x += E;
-                    expand(E, out_v, out_slot, [&](uint32_t uu, uint32_t v, uint32_t sl) {
-                        if (v == s || ldv<FA_SMEM>(fsl + v) != sl) return;   // not v's earliest arrival
+                    expand(E, dag, dag, [&](uint32_t uu, uint32_t v, uint32_t) {
                         if (stats) atomicMin(hop + v, __ldcg(hop + uu) + 1u);
                         else if (!SigOps<false>::atomic_add(sig + v, __ldcg(sig + uu))) sh_ovf = 1;
                         if (atomicSub(pend + v, 1u) == 1u) atomicOr(NB + (v >> 5), 1u << (v & 31));
@@ -410,14 +447,14 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
         __syncthreads();
 
         // ---- backward draw (warp 0); ob: sigma_sz and the Rademacher bits only ----
-        if (reached && !sh_ovf && wid == 0 && job.ob) {
+        if (reached && !sh_ovf && !sh_err && wid == 0 && job.ob) {
             if (lane == 0) {
                 sh_sigma = __ldcg(sig + z);
                 uint32_t w4[4];
                 philox_block(job.seed, i, DOM_RADE, 0, w4);
                 sh_rade[0] = w4[0]; sh_rade[1] = w4[1]; sh_rade[2] = w4[2]; sh_rade[3] = w4[3];
             }
-        } else if (reached && !sh_ovf && wid == 0 && !job.rtb) {
+        } else if (reached && !sh_ovf && !sh_err && wid == 0 && !job.rtb) {
             const u64 tot = __ldcg(sig + z);
             u128 x = 0;
             uint32_t rng_ok = 1;
@@ -627,7 +664,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
 // Region of one CTA (global memory).  The arrival slots and the two bitmaps
 // (next frontier, expanded before) are in shared memory instead when
 // fa_in_smem.
-size_t pfm_cta_region_bytes(uint32_t n, bool fa_in_smem, PfmCtaWs* ws) {
+size_t pfm_cta_region_bytes(uint32_t n, uint32_t dag_cap, bool fa_in_smem, PfmCtaWs* ws) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t o = 0;
     ws->n_cap = n;
@@ -645,6 +682,9 @@ size_t pfm_cta_region_bytes(uint32_t n, bool fa_in_smem, PfmCtaWs* ws) {
     ws->o_pathe = o; o = al(o + (size_t)(n + 2) * 4);
     ws->o_dl = o;    o = al(o + (size_t)n * 8);
     ws->o_kofs = o;  o = al(o + (size_t)(n + 2) * 4);
+    ws->o_dcnt = o;  o = al(o + (size_t)(n + 1) * 4);
+    ws->dag_cap = dag_cap;
+    ws->o_dag = o;   o = al(o + ((size_t)dag_cap + 1) * 4);
     return o;
 }
 

@@ -31,7 +31,8 @@ enum : int { ST_OK = 0, ST_OVERFLOW = 3, ST_TIMEOUT = 5, ST_CHECK = 6, ST_RNG = 
 
 // Counter slots of a launch (u64 each).
 // C_FSEG: sh/sfm frontier vertices; CTA pfm kernel: frontier rounds.
-// C_XEDGE: CTA pfm kernel, out-edges expanded (both passes); diagnostics only.
+// C_XEDGE: CTA pfm kernel, out-edges of the arrival expansions plus the DAG
+// edges of the Kahn pass; diagnostics only.
 enum : int { C_WORK = 0, C_SUMINT = 1, C_ESCAN = 2, C_EADD = 3, C_SNEW = 4, C_NOVF = 5, C_FSEG = 6, C_XEDGE = 7,
              C_NCOUNT = 8 };
 
@@ -635,6 +636,8 @@ struct PfmCtaWs {
     size_t stride;
     size_t o_fa, o_bits, o_exp, o_fat, o_sig, o_hop, o_pend, o_list, o_path, o_pathe;
     size_t o_dl, o_kofs; // ob: continuation counts per vertex, Kahn round offsets
+    size_t o_dcnt, o_dag;// the prefix-foremost DAG as out-lists: per-vertex ends, successors
+    uint32_t dag_cap;    // capacity of the successor array (>= cbound of every graph)
     uint32_t n_cap;      // node capacity of a region
     uint32_t bits_words; // words of each bitmap: ceil(n_cap / 32)
     int fa_in_smem;      // arrival slots and bitmaps in dynamic shared memory
@@ -655,7 +658,7 @@ size_t pfm_region_bytes(uint32_t n, uint32_t list_cap, PfmWs* ws);
 int pfm_threads();
 cudaError_t launch_pfm(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
                        const PfmWs& ws, int grid, bool wide, cudaStream_t st);
-size_t pfm_cta_region_bytes(uint32_t n, bool fa_in_smem, PfmCtaWs* ws);
+size_t pfm_cta_region_bytes(uint32_t n, uint32_t dag_cap, bool fa_in_smem, PfmCtaWs* ws);
 size_t pfm_cta_smem_bytes(uint32_t n);
 size_t pfm_cta_static_smem(int nt);
 cudaError_t pfm_cta_configure(size_t smem);
