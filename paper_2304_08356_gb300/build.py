@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmantra.so")
-SOURCES = ["api.cu", "api_noalloc.cu", "k_bfs.cu", "k_pfm.cu", "k_pfm_cta.cu", "k_misc.cu"]
+SOURCES = ["api.cu", "api_noalloc.cu", "store.cu", "k_bfs.cu", "k_pfm.cu", "k_pfm_cta.cu", "k_misc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I", INCLUDE, "-I", CSRC]
 

@@ -7,6 +7,7 @@
 // include/mantra.h.
 #include "mantra.h"
 #include "mantra_dev.cuh"
+#include "store.h"
 
 #include <algorithm>
 #include <chrono>
@@ -45,174 +46,35 @@ int cuda_fail(cudaError_t e, const char* what, int line) {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-struct HostEdge { uint32_t t, u, v, id; };   // id: position in the (t, u, v) stream
-
-// Stable counting sort of a by key(e) in [0, nkeys); tmp: scratch of a's
-// size.  Large inputs are split into contiguous chunks, one host thread each:
-// per-chunk counts, offsets in (key, chunk) order, per-chunk scatter -- the
-// same order as one pass over the whole array.
-template <typename Key>
-void counting_sort(std::vector<HostEdge>& a, std::vector<HostEdge>& tmp, uint32_t nkeys, Key key) {
-    const size_t m = a.size();
-    tmp.resize(m);
-    unsigned T = std::min(16u, std::max(1u, std::thread::hardware_concurrency()));
-    if (m < ((size_t)1 << 17) || (size_t)nkeys * T > ((size_t)1 << 24)) T = 1;
-    const size_t chunk = (m + T - 1) / T;
-    std::vector<std::vector<size_t>> pos(T, std::vector<size_t>((size_t)nkeys, 0));
-    auto run = [&](auto fn) {
-        if (T == 1) { fn(0u); return; }
-        std::vector<std::thread> th;
-        for (unsigned x = 0; x < T; ++x) th.emplace_back(fn, x);
-        for (auto& h : th) h.join();
-    };
-    run([&](unsigned x) {
-        const size_t lo = std::min(m, x * chunk), hi = std::min(m, lo + chunk);
-        for (size_t k = lo; k < hi; ++k) pos[x][key(a[k])] += 1;
-    });
-    size_t acc = 0;
-    for (size_t b = 0; b < nkeys; ++b)
-        for (unsigned x = 0; x < T; ++x) { const size_t c = pos[x][b]; pos[x][b] = acc; acc += c; }
-    run([&](unsigned x) {
-        const size_t lo = std::min(m, x * chunk), hi = std::min(m, lo + chunk);
-        size_t* p = pos[x].data();
-        for (size_t k = lo; k < hi; ++k) tmp[p[key(a[k])]++] = a[k];
-    });
-    a.swap(tmp);
-}
-
 // ---------------------------------------------------------------------------
 // Temporal-edge store (paper Sec. 3: the temporal graph; the paper's own code
 // keeps a sparse n x |T| table, here every arrival appearance (v,t) gets a
-// dense slot id).
+// dense slot id).  The host team of store.cu builds the arrays; this uploads
+// them into one device allocation, each array from its page-locked buffer.
 // ---------------------------------------------------------------------------
-int build_store(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_t m, uint32_t n, mantra_graph* G,
-                cudaStream_t st) {
-    if (n == 0) {
-        for (uint64_t e = 0; e < m; ++e) n = std::max(n, std::max(u[e], v[e]) + 1);
-    }
-    if (n < 2) return MANTRA_E_INVAL;
-    std::vector<HostEdge> es;
-    try { es.reserve(m); } catch (...) { return MANTRA_E_NOMEM; }
-    uint64_t loops = 0;
-    for (uint64_t e = 0; e < m; ++e) {
-        if (u[e] >= n || v[e] >= n || t[e] > 0xFFFFFFFDu) return MANTRA_E_INVAL;
-        if (u[e] == v[e]) { ++loops; continue; }
-        es.push_back(HostEdge{t[e], u[e], v[e], 0u});
-    }
-    // (t, u, v) order by stable counting sorts on v, u, then t (two 16-bit
-    // digits): linear passes instead of a comparison sort
-    std::vector<HostEdge> tmp;
-    try { tmp.resize(es.size()); } catch (...) { return MANTRA_E_NOMEM; }
-    counting_sort(es, tmp, n, [](const HostEdge& e) { return e.v; });
-    counting_sort(es, tmp, n, [](const HostEdge& e) { return e.u; });
-    counting_sort(es, tmp, 1u << 16, [](const HostEdge& e) { return e.t & 0xFFFFu; });
-    counting_sort(es, tmp, 1u << 16, [](const HostEdge& e) { return e.t >> 16; });
-    auto same = [](const HostEdge& a, const HostEdge& b) { return a.t == b.t && a.u == b.u && a.v == b.v; };
-    const size_t before = es.size();
-    es.erase(std::unique(es.begin(), es.end(), same), es.end());
-    if (es.size() >= 0xFFFFFFF0ull) return MANTRA_E_INVAL;
-    const uint32_t M = (uint32_t)es.size();
-    G->n = n; G->m = M; G->self_loops = loops; G->duplicates = before - es.size();
-
-    std::vector<uint32_t> st_u(M), st_v(M), st_t(M);
-    for (uint32_t e = 0; e < M; ++e) {
-        st_u[e] = es[e].u; st_v[e] = es[e].v; st_t[e] = es[e].t;
-        es[e].id = e;
-    }
-
-    // in-CSR by (v, t, u) and slots: a stable sort by v of the (t, u, v) order;
-    // inpos[id] = the in-CSR index of stream edge id
-    std::vector<HostEdge> ein(es);
-    tmp.resize(ein.size());
-    counting_sort(ein, tmp, n, [](const HostEdge& e) { return e.v; });
-    std::vector<uint32_t> in_u(M), in_slot(M), inpos(M), slot_t, slot_v, slot_in, slot_ptr(n + 1, 0);
-    slot_t.reserve(M); slot_v.reserve(M); slot_in.reserve(M + 1);
-    for (uint32_t e = 0; e < M; ++e) {
-        if (e == 0 || ein[e].v != ein[e - 1].v || ein[e].t != ein[e - 1].t) {
-            slot_t.push_back(ein[e].t); slot_v.push_back(ein[e].v); slot_in.push_back(e);
-            slot_ptr[ein[e].v + 1] += 1;
-        }
-        in_u[e] = ein[e].u;
-        in_slot[e] = (uint32_t)slot_t.size() - 1;
-        inpos[ein[e].id] = e;
-    }
-    const uint32_t A = (uint32_t)slot_t.size();
-    slot_in.push_back(M);
-    for (uint32_t x = 0; x < n; ++x) slot_ptr[x + 1] += slot_ptr[x];
-    G->A = A;
-
-    // out-CSR by (u, t, v): a stable sort by u of the (t, u, v) order; each
-    // edge's head slot is the slot of its in-CSR position
-    std::vector<HostEdge> eo(es);
-    counting_sort(eo, tmp, n, [](const HostEdge& e) { return e.u; });
-    std::vector<uint32_t> out_ptr(n + 1, 0), out_v(M), out_t(M), out_slot(M);
-    for (uint32_t e = 0; e < M; ++e) {
-        out_ptr[eo[e].u + 1] += 1;
-        out_v[e] = eo[e].v; out_t[e] = eo[e].t;
-        out_slot[e] = in_slot[inpos[eo[e].id]];
-    }
-    for (uint32_t x = 0; x < n; ++x) out_ptr[x + 1] += out_ptr[x];
-    // first out-edge of v later than each of v's arrival slots (both rows in
-    // time order): the searches' lower ends without a search
-    std::vector<uint32_t> slot_nout(A);
-    for (uint32_t x = 0; x < n; ++x) {
-        uint32_t q = out_ptr[x];
-        const uint32_t q1 = out_ptr[x + 1];
-        for (uint32_t a = slot_ptr[x]; a < slot_ptr[x + 1]; ++a) {
-            while (q < q1 && out_t[q] <= slot_t[a]) ++q;
-            slot_nout[a] = q;
-        }
-    }
-
-    // underlying-edge ids (App. A): the rank of (v, u) among the distinct
-    // ordered pairs -- a stable sort by v of the (u, t, v) order lists the
-    // edges by (v, u, t), so equal pairs are consecutive
-    std::vector<uint32_t> in_uedge(M);
-    uint32_t n_uedge = 0;
-    {
-        std::vector<HostEdge> evu(eo);
-        counting_sort(evu, tmp, n, [](const HostEdge& e) { return e.v; });
-        for (uint32_t e = 0; e < M; ++e) {
-            if (e > 0 && (evu[e].v != evu[e - 1].v || evu[e].u != evu[e - 1].u)) ++n_uedge;
-            in_uedge[inpos[evu[e].id]] = n_uedge;
-        }
-        if (M > 0) ++n_uedge;
-    }
-    G->n_uedge = n_uedge;
-    std::vector<uint32_t> tmax_in(n, 0), tmin_out(n, 0);
-    uint64_t cbound = 0;
-    uint32_t max_slot_in = 0;
-    for (uint32_t x = 0; x < n; ++x) {
-        if (slot_ptr[x + 1] > slot_ptr[x]) tmax_in[x] = slot_t[slot_ptr[x + 1] - 1];
-        if (out_ptr[x + 1] > out_ptr[x]) tmin_out[x] = out_t[out_ptr[x]];
-        uint32_t mx = 0;
-        for (uint32_t a = slot_ptr[x]; a < slot_ptr[x + 1]; ++a) mx = std::max(mx, slot_in[a + 1] - slot_in[a]);
-        cbound += mx;
-        max_slot_in = std::max(max_slot_in, mx);
-    }
-    G->dg.cbound = (uint32_t)std::min<uint64_t>(cbound, 0xFFFFFFFFull);
-    G->dg.max_slot_in = max_slot_in;
-
-    // one device allocation for the whole store
-    struct Arr { const std::vector<uint32_t>* h; const uint32_t** d; };
-    Arr arrs[] = {{&out_ptr, &G->dg.out_ptr}, {&out_v, &G->dg.out_v}, {&out_t, &G->dg.out_t},
-                  {&out_slot, &G->dg.out_slot}, {&slot_ptr, &G->dg.slot_ptr}, {&slot_t, &G->dg.slot_t},
-                  {&slot_v, &G->dg.slot_v}, {&slot_in, &G->dg.slot_in}, {&in_u, &G->dg.in_u},
-                  {&in_slot, &G->dg.in_slot}, {&st_u, &G->dg.st_u}, {&st_v, &G->dg.st_v},
-                  {&st_t, &G->dg.st_t}, {&tmax_in, &G->dg.tmax_in}, {&tmin_out, &G->dg.tmin_out},
-                  {&in_uedge, &G->dg.in_uedge}, {&slot_nout, &G->dg.slot_nout}};
+int upload_store(const StoreHost& H, mantra_graph* G, cudaStream_t st) {
+    const uint32_t** dst[SA_COUNT] = {};
+    dst[SA_OUT_PTR] = &G->dg.out_ptr;   dst[SA_OUT_V] = &G->dg.out_v;       dst[SA_OUT_T] = &G->dg.out_t;
+    dst[SA_OUT_SLOT] = &G->dg.out_slot; dst[SA_SLOT_PTR] = &G->dg.slot_ptr; dst[SA_SLOT_T] = &G->dg.slot_t;
+    dst[SA_SLOT_V] = &G->dg.slot_v;     dst[SA_SLOT_IN] = &G->dg.slot_in;   dst[SA_IN_U] = &G->dg.in_u;
+    dst[SA_IN_SLOT] = &G->dg.in_slot;   dst[SA_ST_U] = &G->dg.st_u;         dst[SA_ST_V] = &G->dg.st_v;
+    dst[SA_ST_T] = &G->dg.st_t;         dst[SA_TMAX_IN] = &G->dg.tmax_in;   dst[SA_TMIN_OUT] = &G->dg.tmin_out;
+    dst[SA_IN_UEDGE] = &G->dg.in_uedge; dst[SA_SLOT_NOUT] = &G->dg.slot_nout;
     size_t total = 0;
-    for (auto& a : arrs) total += al256((a.h->size() + 1) * 4);
+    for (int k = 0; k < SA_COUNT; ++k) total += al256((H.len[k] + 1) * 4);
     if (cudaMalloc(&G->dmem, total) != cudaSuccess) return MANTRA_E_NOMEM;
     size_t off = 0;
-    for (auto& a : arrs) {
+    for (int k = 0; k < SA_COUNT; ++k) {
         char* p = (char*)G->dmem + off;
-        if (!a.h->empty()) CU(cudaMemcpyAsync(p, a.h->data(), a.h->size() * 4, cudaMemcpyHostToDevice, st));
-        *a.d = (const uint32_t*)p;
-        off += al256((a.h->size() + 1) * 4);
+        if (H.len[k]) CU(cudaMemcpyAsync(p, H.arr[k], H.len[k] * 4, cudaMemcpyHostToDevice, st));
+        *dst[k] = (const uint32_t*)p;
+        off += al256((H.len[k] + 1) * 4);
     }
     CU(cudaStreamSynchronize(st));
-    G->dg.n = n; G->dg.A = A; G->dg.m = M; G->dg.n_uedge = n_uedge;
+    G->n = H.n; G->m = H.m; G->A = H.A; G->n_uedge = H.n_uedge;
+    G->self_loops = H.self_loops; G->duplicates = H.duplicates;
+    G->dg.n = H.n; G->dg.A = H.A; G->dg.m = H.m; G->dg.n_uedge = H.n_uedge;
+    G->dg.cbound = H.cbound; G->dg.max_slot_in = H.max_slot_in;
     return MANTRA_OK;
 }
 
@@ -311,6 +173,7 @@ struct TickOut {
 // ---------------------------------------------------------------------------
 struct Engine {
     std::mutex mu;
+    StoreBuilder store;        // host buffers of graph loads (mantra_graph_load)
     int device = -1, num_sms = 0;
     size_t smem_optin = 0;
     cudaStream_t sa = nullptr, sb = nullptr;
@@ -1279,7 +1142,10 @@ int mantra_graph_load(const uint32_t* u, const uint32_t* v, const uint32_t* t, u
     if (rc == MANTRA_OK) rc = engine_for(G->device, &E);
     if (rc == MANTRA_OK) {
         std::lock_guard<std::mutex> lock(E->mu);
-        rc = build_store(u, v, t, m, n, G, E->sa);
+        StoreHost H;
+        rc = E->store.build(u, v, t, m, n, &H);
+        if (rc == MANTRA_OK) rc = upload_store(H, G, E->sa);
+        E->store.trim();
     }
     if (rc != MANTRA_OK) { mantra_graph_free(G); return rc; }
     *out = G;
