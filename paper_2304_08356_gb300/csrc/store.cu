@@ -120,9 +120,10 @@ struct PingPong {
 
 // One stable counting pass of len records from pp.cur into the next buffer by
 // key(rec) in [0, K): per-thread digit counts over the thread's chunk, global
-// offsets in (digit, thread) order, per-thread scatter.
+// offsets in (digit, thread) order, per-thread scatter.  pos (or null)
+// receives each record's new index at pos[rec.id].
 template <class Key>
-void pass(Team& tm, unsigned x, Ctx& c, PingPong& pp, uint32_t len, uint32_t K, Key key) {
+void pass(Team& tm, unsigned x, Ctx& c, PingPong& pp, uint32_t len, uint32_t K, Key key, uint32_t* pos) {
     const unsigned T = tm.size();
     const Rec* src = pp.cur;
     Rec* dst = pp.buf[pp.next];
@@ -146,7 +147,15 @@ void pass(Team& tm, unsigned x, Ctx& c, PingPong& pp, uint32_t len, uint32_t K, 
             acc += k;
         }
     tm.sync();
-    for (uint64_t i = r.lo; i < r.hi; ++i) dst[my[key(src[i])]++] = src[i];
+    if (pos) {
+        for (uint64_t i = r.lo; i < r.hi; ++i) {
+            const uint32_t k = my[key(src[i])]++;
+            dst[k] = src[i];
+            pos[src[i].id] = k;
+        }
+    } else {
+        for (uint64_t i = r.lo; i < r.hi; ++i) dst[my[key(src[i])]++] = src[i];
+    }
     tm.sync();
     pp.cur = dst;
     pp.next ^= 1;
@@ -154,20 +163,22 @@ void pass(Team& tm, unsigned x, Ctx& c, PingPong& pp, uint32_t len, uint32_t K, 
 
 // Stable sort of the records by field F, whose values are < R: one pass when
 // R <= 2^16, else passes of equal digit widths of at most 16 bits, low first.
+// pos (or null): the last pass stores each record's final index at pos[id].
 template <Field F>
-void sort_field(Team& tm, unsigned x, Ctx& c, PingPong& pp, uint32_t len, uint64_t R) {
+void sort_field(Team& tm, unsigned x, Ctx& c, PingPong& pp, uint32_t len, uint64_t R, uint32_t* pos = nullptr) {
     uint32_t bits = 0;
     while (bits < 32 && ((R - 1) >> bits) != 0) ++bits;
     if (bits == 0) return;
     if (bits <= kDigitBits) {
-        pass(tm, x, c, pp, len, (uint32_t)R, [](const Rec& r) { return fval<F>(r); });
+        pass(tm, x, c, pp, len, (uint32_t)R, [](const Rec& r) { return fval<F>(r); }, pos);
         return;
     }
     const uint32_t np = (bits + kDigitBits - 1) / kDigitBits;
     const uint32_t w = (bits + np - 1) / np;
     for (uint32_t j = 0; j < np; ++j) {
         const uint32_t sh = j * w, wb = std::min(w, bits - sh), mask = (1u << wb) - 1;
-        pass(tm, x, c, pp, len, 1u << wb, [sh, mask](const Rec& r) { return (fval<F>(r) >> sh) & mask; });
+        pass(tm, x, c, pp, len, 1u << wb, [sh, mask](const Rec& r) { return (fval<F>(r) >> sh) & mask; },
+             j + 1 == np ? pos : nullptr);
     }
 }
 
@@ -335,7 +346,7 @@ int StoreBuilder::build(const uint32_t* u, const uint32_t* v, const uint32_t* t,
 
         // -- in-CSR (v, t, u): a stable pass by v of the stream; arrival slots
         PingPong pi{D, {X, Y}, 0};
-        sort_field<F_V>(tm, x, c, pi, M, N);
+        sort_field<F_V>(tm, x, c, pi, M, N, c.inpos);
         const Rec* I = pi.cur;
         {
             uint32_t* in_u = c.a[SA_IN_U];
@@ -343,7 +354,6 @@ int StoreBuilder::build(const uint32_t* u, const uint32_t* v, const uint32_t* t,
             for (uint64_t e = rm.lo; e < rm.hi; ++e) {
                 k += (e == 0 || I[e].v != I[e - 1].v || I[e].t != I[e - 1].t);
                 in_u[e] = I[e].u;
-                c.inpos[I[e].id] = (uint32_t)e;
             }
             c.p0[x] = k;
         }
@@ -386,22 +396,36 @@ int StoreBuilder::build(const uint32_t* u, const uint32_t* v, const uint32_t* t,
         // -- per slot: first out-edge of v later than the slot's time; per
         //    vertex: latest arrival, earliest departure, largest slot in-count
         {
-            const uint32_t *o_ptr = c.a[SA_OUT_PTR], *o_t = c.a[SA_OUT_T], *sl_v = c.a[SA_SLOT_V],
-                           *sl_t = c.a[SA_SLOT_T], *sl_ptr = c.a[SA_SLOT_PTR], *sl_in = c.a[SA_SLOT_IN];
+            const uint32_t *o_ptr = c.a[SA_OUT_PTR], *o_t = c.a[SA_OUT_T], *sl_t = c.a[SA_SLOT_T],
+                           *sl_ptr = c.a[SA_SLOT_PTR], *sl_in = c.a[SA_SLOT_IN];
             uint32_t* nout = c.a[SA_SLOT_NOUT];
-            const Range ra = part(A, T, x);
-            for (uint64_t a = ra.lo; a < ra.hi; ++a) {
-                const uint32_t w = sl_v[a];
-                nout[a] = (uint32_t)(std::upper_bound(o_t + o_ptr[w], o_t + o_ptr[w + 1], sl_t[a]) - o_t);
-            }
             uint32_t *tmax_in = c.a[SA_TMAX_IN], *tmin_out = c.a[SA_TMIN_OUT];
+            // vertices split by their slot + out-edge counts (a monotone prefix);
+            // each vertex merges its slot times with its out-row times
+            const uint64_t tot = (uint64_t)A + M;
+            auto first_w = [&](uint64_t target) {
+                uint64_t lo = 0, hi = N;
+                while (lo < hi) {
+                    const uint64_t mid = (lo + hi) / 2;
+                    if ((uint64_t)sl_ptr[mid] + o_ptr[mid] < target) lo = mid + 1;
+                    else hi = mid;
+                }
+                return lo;
+            };
+            const uint64_t wlo = x == 0 ? 0 : first_w(tot * x / T);
+            const uint64_t whi = x == T - 1 ? N : first_w(tot * (x + 1) / T);
             uint64_t cb = 0, mxs = 0;
-            const Range rv = part(N, T, x);
-            for (uint64_t w = rv.lo; w < rv.hi; ++w) {
-                tmax_in[w] = sl_ptr[w + 1] > sl_ptr[w] ? sl_t[sl_ptr[w + 1] - 1] : 0;
-                tmin_out[w] = o_ptr[w + 1] > o_ptr[w] ? o_t[o_ptr[w]] : 0;
-                uint32_t mx = 0;
-                for (uint32_t a = sl_ptr[w]; a < sl_ptr[w + 1]; ++a) mx = std::max(mx, sl_in[a + 1] - sl_in[a]);
+            for (uint64_t w = wlo; w < whi; ++w) {
+                const uint32_t a0 = sl_ptr[w], a1 = sl_ptr[w + 1], q1 = o_ptr[w + 1];
+                uint32_t q = o_ptr[w], mx = 0;
+                for (uint32_t a = a0; a < a1; ++a) {
+                    const uint32_t ta = sl_t[a];
+                    while (q < q1 && o_t[q] <= ta) ++q;
+                    nout[a] = q;
+                    mx = std::max(mx, sl_in[a + 1] - sl_in[a]);
+                }
+                tmax_in[w] = a1 > a0 ? sl_t[a1 - 1] : 0;
+                tmin_out[w] = q1 > o_ptr[w] ? o_t[o_ptr[w]] : 0;
                 cb += mx;
                 mxs = std::max<uint64_t>(mxs, mx);
             }
