@@ -758,8 +758,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                     off += __shfl_sync(0xFFFFFFFFu, incl, 31);
                 }
             }
-            if (use_ns && w_lo < w_hi) {   // this warp's words of N are zero again (a
-                // nonempty range starts on a 32-word boundary, so it owns its summary words)
+            if (use_ns) {   // this warp's words of N are zero again
                 __syncwarp();
                 for (uint32_t gq = (w_lo >> 5) + lane; gq < ((w_hi + 31u) >> 5); gq += 32u) sm_ns[gq] = 0u;
             }
