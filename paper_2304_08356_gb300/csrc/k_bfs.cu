@@ -31,7 +31,6 @@ namespace mantra {
 constexpr int IPT = 2;            // frontier states per thread in a segmented-scan tile
 constexpr int WALK_K = 2;         // edge windows with loads in flight per warp in the push
 constexpr int CK = 8;             // bitmap words in flight per lane in the compaction and cleanup scans
-constexpr uint32_t NSCAP = 1024;  // summary words: one bit per next-level bitmap word (up to 2^20 slots)
 
 // ob update of one sample (Sec. 4.1), all threads of the CTA: continuation
 // counts dl (the number of optimal ways from a state to z's endpoints) per
@@ -370,16 +369,11 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
     __shared__ uint32_t sh_stamp, sh_wrap;
     __shared__ u64 sh_fcmax;
     __shared__ uint32_t sm_Ft[WIDE ? 1 : FCAP];   // level times and running sums (64-bit counts, L <= FCAP)
-    // summary of the next-level bitmap: bit b of word g is set when word 32 g + b
-    // of N may be nonzero (every addition to N sets it; compaction and cleanup
-    // clear it), so the scans load only those words; used while A <= 2^20
-    __shared__ uint32_t sm_ns[NSCAP];
     __shared__ u64 sm_Fc[WIDE ? 1 : FCAP];
 
     if (ws.bits_in_smem) {
         for (uint32_t w = tid; w < ws.bits_words; w += BFS_NT) V[w] = 0u;
     }
-    for (uint32_t w = tid; w < NSCAP; w += BFS_NT) sm_ns[w] = 0u;
     if (tid == 0) sh_stamp = *stamp_p;
     // Next level stamp (segmap entries of older levels never match it) and the
     // level's scan scratch; on wrap-around the map is cleared once.
@@ -435,16 +429,6 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
         const Job& job = sh_task.job;
         const uint32_t n = g.n;
         const uint32_t words = (g.A + 31) >> 5;
-        const bool use_ns = words <= NSCAP * 32u;
-        // marks N's word of slot a in the summary (a read first: most marks are repeats)
-        auto mark_ns = [&](uint32_t a) {
-            if (!use_ns) return;
-            uint32_t* const p = sm_ns + (a >> 10);
-            const uint32_t b = 1u << ((a >> 5) & 31u);
-            if (!(*p & b)) atomicOr(p, b);
-        };
-        // N's word w may be nonzero
-        auto ns_has = [&](uint32_t w) { return !use_ns || ((sm_ns[w >> 5] >> (w & 31u)) & 1u); };
         if (job.ctr != flush_ctr) { flush(); flush_ctr = job.ctr; }
         const uint64_t q = sh_q;
         const uint64_t i = job.idx_list ? job.idx_list[q] : job.i0 + q;
@@ -611,7 +595,6 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                         if (have) {
                             if (!SigOps<WIDE>::atomic_add(sig + a, FcL[idx])) sh_ovf = 1;
                             atomicOr(N + (a >> 5), 1u << (a & 31));
-                            mark_ns(a);
                             sh_found = 1;
                         }
                     }
@@ -661,7 +644,6 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                     ++my_escan;
                     if (!((V[a >> 5] >> (a & 31)) & 1u)) {
                         atomicOr(N + (a >> 5), 1u << (a & 31));
-                        mark_ns(a);
                         if (!stats) {          // Algorithm 2 needs reach only, no path counts
                             const uint32_t rb = cs_fb[r], re = cs_fe[r];
                             uint32_t idx = rb;
@@ -692,7 +674,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
 #pragma unroll
                 for (int j = 0; j < CK; ++j) {
                     const uint32_t w = w0 + 32u * j;
-                    x[j] = (w < w_hi && ns_has(w)) ? __ldcg(N + w) : 0u;
+                    x[j] = (w < w_hi) ? __ldcg(N + w) : 0u;
                 }
 #pragma unroll
                 for (int j = 0; j < CK; ++j) cnt += __popc(x[j]);
@@ -722,7 +704,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
 #pragma unroll
                 for (int jj = 0; jj < CK; ++jj) {
                     const uint32_t w = wb + 32u * jj + lane;
-                    xb[jj] = (w < w_hi && ns_has(w)) ? __ldcg(N + w) : 0u;
+                    xb[jj] = (w < w_hi) ? __ldcg(N + w) : 0u;
                 }
 #pragma unroll
                 for (int jj = 0; jj < CK; ++jj) {
@@ -757,10 +739,6 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                     }
                     off += __shfl_sync(0xFFFFFFFFu, incl, 31);
                 }
-            }
-            if (use_ns) {   // this warp's words of N are zero again
-                __syncwarp();
-                for (uint32_t gq = (w_lo >> 5) + lane; gq < ((w_hi + 31u) >> 5); gq += 32u) sm_ns[gq] = 0u;
             }
             if (stats) {
 #pragma unroll
@@ -981,7 +959,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
 #pragma unroll
             for (int j = 0; j < CK; ++j) {
                 const uint32_t w = w0 + BFS_NT * j;
-                nb[j] = (w < words && ns_has(w)) ? __ldcg(N + w) : 0u;
+                nb[j] = (w < words) ? __ldcg(N + w) : 0u;
             }
 #pragma unroll
             for (int j = 0; j < CK; ++j) {
@@ -1003,9 +981,6 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             for (uint32_t w = tid; w < (n + 31) / 32; w += BFS_NT) VB[w] = 0u;
         }
         __syncthreads();
-        if (use_ns) {   // the next task's first barrier orders these before any mark
-            for (uint32_t gq = tid; gq < ((words + 31u) >> 5); gq += BFS_NT) sm_ns[gq] = 0u;
-        }
     }
     flush();
     if (tid == 0) *stamp_p = sh_stamp;
