@@ -270,7 +270,9 @@ struct Engine {
         // regions for the 512-thread shape (two CTAs per SM); the 1024-thread
         // shape (one per SM) uses the first of them
         const size_t smem = bfs_smem_bytes(A);
-        const bool in_smem = smem + std::max(bfs_static_smem(512), bfs_static_smem(1024)) + 1024 <= smem_optin;
+        bool in_smem = smem + std::max(bfs_static_smem(512), bfs_static_smem(1024)) + 1024 <= smem_optin;
+        // MANTRA_BFS_SMEM=0 keeps the visited bitmap in the region
+        if (const char* env = std::getenv("MANTRA_BFS_SMEM")) in_smem = in_smem && env[0] != '0';
         const size_t region = bfs_region_bytes(n, A, in_smem, &bws);
         CU(bfs_configure(in_smem ? smem : 0));
         int per_sm = 0, per_sm_big = 0;
