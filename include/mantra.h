@@ -126,9 +126,13 @@ typedef struct {
 
 /* Build the device-resident temporal-edge store from m host triples.
  * u, v, t: host arrays of m entries (copied; the caller keeps ownership).
- * n: number of nodes; 0 = max id + 1.  Ids must be < n, times <= 2^32-3.
+ * n: number of nodes; 0 = max id + 1.  Ids must be < n, times <= 2^32-3,
+ * fewer than 2^32-16 triples without self loops (else MANTRA_E_INVAL).
  * Duplicate triples are kept once, self loops dropped (counts reported by
- * mantra_graph_info).  Paper Sec. 3 (temporal graph). */
+ * mantra_graph_info).  The store is built on up to 16 host threads into
+ * host buffers that the device's engine keeps for later loads (page-locked
+ * while at most 256 MB, then uploaded by DMA).  Paper Sec. 3 (temporal
+ * graph). */
 int mantra_graph_load(const uint32_t* u, const uint32_t* v, const uint32_t* t, uint64_t m, uint32_t n,
                       mantra_graph** out);
 
