@@ -323,7 +323,12 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                                                    const __grid_constant__ BfsWs ws) {
     typedef typename SigOps<WIDE>::T Sig;
     constexpr int BFS_NW = BFS_NT / 32;
-    constexpr uint32_t FCAP = BFS_NT * 4;   // frontier states whose times and running sums fit in shared memory
+    // frontier states whose times and running sums fit in shared memory.  Kept
+    // small: with the visited bitmap of a 500k-slot graph, two 512-thread CTAs
+    // then fit the 164 KB shared-memory carveout and the SM keeps 92 KB of L1
+    // (the path-count and graph reads hit it); 4 * BFS_NT needed the 196 KB
+    // carveout (60 KB of L1) and measured 4 % slower
+    constexpr uint32_t FCAP = BFS_NT * 3 / 2;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     __shared__ __align__(16) Task sh_task;
     __shared__ int sh_t;
