@@ -240,6 +240,9 @@ int StoreBuilder::build(const uint32_t* u, const uint32_t* v, const uint32_t* t,
     if (!reserve(cnt_, (size_t)kMaxThreads * kMaxKeys * 4, false)) return MANTRA_E_NOMEM;
     unsigned want = std::min(kMaxThreads, std::max(1u, std::thread::hardware_concurrency()));
     if (m < ((uint64_t)1 << 16)) want = 1;
+    // MANTRA_STORE_THREADS=k: exactly k threads (1 .. 16), whatever the size
+    if (const char* env = std::getenv("MANTRA_STORE_THREADS"))
+        want = (unsigned)std::min<long>(kMaxThreads, std::max<long>(1, std::atol(env)));
 
     Ctx c;
     c.u = u; c.v = v; c.t = t; c.m = m; c.n = n;

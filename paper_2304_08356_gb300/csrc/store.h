@@ -39,6 +39,8 @@ public:
 
     // Builds the store of the m triples (u[e], v[e], t[e]); n = 0 takes the
     // largest id + 1.  Self loops are dropped and duplicate triples kept once.
+    // Threads: up to 16 (one below 2^16 triples); the environment variable
+    // MANTRA_STORE_THREADS=k sets k (1 .. 16) for any size.
     // Returns MANTRA_OK, MANTRA_E_INVAL (an id >= n, a time above 2^32 - 3,
     // n < 2, or 2^32 - 16 or more triples left after dropping self loops) or
     // MANTRA_E_NOMEM.  The arrays of *out stay valid until the next build() or

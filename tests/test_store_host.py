@@ -34,13 +34,17 @@ def driver(tmp_path_factory):
     return exe
 
 
-def run_builder(driver, tmp_path, u, v, t, n):
+def run_builder(driver, tmp_path, u, v, t, n, threads=None):
     src, dst = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     with open(src, "wb") as f:
         f.write(np.uint64(len(u)).tobytes() + np.uint32(n).tobytes())
         for a in (u, v, t):
             f.write(np.ascontiguousarray(a, dtype=np.uint32).tobytes())
-    subprocess.run([driver, src, dst], check=True)
+    env = dict(os.environ)
+    env.pop("MANTRA_STORE_THREADS", None)
+    if threads is not None:
+        env["MANTRA_STORE_THREADS"] = str(threads)
+    subprocess.run([driver, src, dst], check=True, env=env)
     raw = open(dst, "rb").read()
     rc = int(np.frombuffer(raw, np.int32, 1, 0)[0])
     sc = np.frombuffer(raw, np.uint32, 6, 4)
@@ -97,8 +101,8 @@ def definition(u, v, t, n):
     return d
 
 
-def check(driver, tmp_path, u, v, t, n=0):
-    got = run_builder(driver, tmp_path, u, v, t, n)
+def check(driver, tmp_path, u, v, t, n=0, threads=None):
+    got = run_builder(driver, tmp_path, u, v, t, n, threads)
     assert got["rc"] == 0
     ref = definition(u, v, t, n)
     for k in ("n", "m", "A", "n_uedge", "cbound", "max_slot_in", "self_loops", "duplicates"):
@@ -162,3 +166,16 @@ def test_store_invalid(driver, tmp_path, bad):
         u = v = t = np.zeros(0, np.int64)
         n = 0
     assert run_builder(driver, tmp_path, u, v, t, n)["rc"] == 1
+
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 16])
+def test_store_thread_counts(driver, tmp_path, threads):
+    """Any team size gives the same store, including teams with more threads
+    than records (empty chunks) and more threads than host cores."""
+    for seed, m, n, t_hi in ((7, 5, 4, 3), (8, 40, 30, 6), (9, 3000, 700, 1 << 18), (10, 70_000, 90_000, 1000)):
+        u, v, t = _random(seed, m, n, t_hi, loops=0.05, dup=0.1)
+        check(driver, tmp_path, u, v, t, threads=threads)
+    u, v, t = _random(11, 50, 20, 10)
+    u[7] = 20
+    assert run_builder(driver, tmp_path, u, v, t, 20, threads)["rc"] == 1
+
