@@ -497,8 +497,10 @@ def main():
         g2.free()
         e2e_s += time.perf_counter() - t0
     e2e_val = sum_over_ranks(float(e2e_n), world) / max(max_over_ranks(e2e_s, world), 1e-9)
-    h2d = 4 * (8 * g.m + 3 * g.slots + 4 * g.n + 3)
-    d2h = 3 * 8 * g.n
+    # the store's 17 uint32 arrays (9 of m entries, 4 of A, 4 of n, 3 extra
+    # row ends) go up; each problem's est (f64) and hits (u64) come back
+    h2d = 4 * (9 * g.m + 4 * g.slots + 4 * g.n + 3)
+    d2h = len(OPTS) * 16 * g.n
 
     serving = None
     if args.serve_graphs > 0 and rank == 0:
