@@ -271,8 +271,22 @@ struct Engine {
         // shape (one per SM) uses the first of them
         const size_t smem = bfs_smem_bytes(A);
         bool in_smem = smem + std::max(bfs_static_smem(512), bfs_static_smem(1024)) + 1024 <= smem_optin;
-        // MANTRA_BFS_SMEM=0 keeps the visited bitmap in the region
-        if (const char* env = std::getenv("MANTRA_BFS_SMEM")) in_smem = in_smem && env[0] != '0';
+        if (in_smem) {
+            // the bitmap goes to shared memory only while two 512-thread CTAs
+            // per SM stay resident: on a 798k-slot graph one CTA per SM with the
+            // bitmap took 64 ms where two without it took 49 ms
+            int with_bits = 0, without = 0;
+            CU(bfs_configure(smem));
+            CU(bfs_blocks_per_sm(512, smem, &with_bits));
+            CU(bfs_blocks_per_sm(512, 0, &without));
+            if (with_bits < without) in_smem = false;
+        }
+        // MANTRA_BFS_SMEM=0 keeps the visited bitmap in the region; =1 puts it
+        // in shared memory whenever it fits, whatever the residency
+        if (const char* env = std::getenv("MANTRA_BFS_SMEM")) {
+            if (env[0] == '0') in_smem = false;
+            else if (env[0] == '1') in_smem = smem + std::max(bfs_static_smem(512), bfs_static_smem(1024)) + 1024 <= smem_optin;
+        }
         const size_t region = bfs_region_bytes(n, A, in_smem, &bws);
         CU(bfs_configure(in_smem ? smem : 0));
         int per_sm = 0, per_sm_big = 0;
