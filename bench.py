@@ -47,6 +47,12 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.txt")
 
 
+def bench_config(world: int) -> dict:
+    """The config object of the bench line, the same for both arms."""
+    return {"workload": WORKLOAD, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "GPU arm: flushed between steps (256 MiB write), per-step CUDA events; reference arm: host cores"}
+
+
 def workload():
     from paper_2304_08356_gb300 import synth
     return synth.chung_lu_bursty(n=20000, m=500000, gamma=2.3, seed=1)
@@ -322,7 +328,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_s / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "data": "synthetic (seeded Chung-Lu bursty)", "config": bench_config(1),
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                              "sample": "per step: the first estimation samples of sh, sfm and pfm on %d host "
                                        "threads, %.1f s of wall time each; equal sample counts per optimality "
@@ -534,11 +540,10 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max * 1000.0 / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded Chung-Lu bursty)",
-                "config": {"workload": WORKLOAD, "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "flushed between steps (256 MiB write), per-step CUDA events",
-                           "samples_per_step": samples / args.steps,
-                           "per_opt_r": {o: [st[o]["r"] for st in infos_all] for o in OPTS}},
-                "secondary": {"temporal_edge_GBps": alg_gbps, "edges_per_s": edges / (total_ms / 1000.0),
+                "config": bench_config(world),
+                "secondary": {"samples_per_step": samples / args.steps,
+                              "per_opt_r": {o: [st[o]["r"] for st in infos_all] for o in OPTS},
+                              "temporal_edge_GBps": alg_gbps, "edges_per_s": edges / (total_ms / 1000.0),
                               "sequential_pairs_per_s": seq_rate, "sequential_kernel_ms": kms,
                               "mode": args.mode, "next_rows": next_rows},
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",

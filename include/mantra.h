@@ -102,15 +102,40 @@ typedef struct {
     double xi;               /* final supremum-deviation bound (Theorem 1) */
     double vhat;             /* final variance term of xi: W = H / r, or its bound (vhat_mode 1) */
     double rho_hat;          /* bootstrap estimate of the mean internal length */
-    uint64_t edges_scanned;  /* temporal edges examined by the searches (all samples) */
-    uint64_t sigma_adds;     /* path-count additions into states */
-    uint64_t states_new;     /* appearance states discovered (sh/sfm) */
+    /* Work counters, summed over every sample of the call (bootstrap included).
+     * Per sh / sfm sample (levels F_k = the states (v,t) at hop level k with t <
+     * tz = z's latest in-edge time, F_0 = {(s,-inf)}; the search stops on the
+     * level that reaches z, or when F_k is empty):
+     *   edges_scanned = per level k that is searched: z's in-edges (the pull
+     *                   test), plus, when level k is pushed, every out-edge
+     *                   (u,v,t) of each vertex u of F_k with t' < t < tz for
+     *                   u's earliest t' in F_k (all out-edges of s at k = 0);
+     *   sigma_adds    = those pushed edges whose head (v,t) is new on level k+1;
+     *   states_new    = |F_1| + ... + |F_K| over the pushed levels' successors;
+     *   frontier_vertices = distinct vertices of every searched level (1 for F_0).
+     * fsfm has no pull test and pushes out-edges with t <= tz.  Per pfm sample
+     * (fa = earliest arrival, te = fa(z), or tz when z is unreachable):
+     *   edges_scanned = time-sorted edges (u,v,t) with v != s and
+     *                   tmin_out(s) <= t <= te (the paper's scan window);
+     *   sigma_adds    = prefix-foremost DAG edges (w,v,fa(v)), v != s,
+     *                   fa(w) < fa(v) <= te;  states_new = frontier_vertices = 0.
+     * Samples with no out-edge at s or no in-edge at z count nothing. */
+    uint64_t edges_scanned;  /* E_scan (above) */
+    uint64_t sigma_adds;     /* U (above) */
+    uint64_t states_new;     /* S_new (above) */
     uint64_t wide_samples;   /* samples re-run with 128-bit path counts */
     double seconds;          /* wall time of the call */
     double kernel_ms;        /* device time of the search kernels (CUDA events) */
     uint64_t search_launches;/* search-kernel launches */
     uint64_t kernel_launches;/* all kernel launches of the call (search, reduction, normalisation) */
-    uint64_t alg_bytes;      /* algorithmic bytes of the search kernels (byte model in the design notes) */
+    uint64_t alg_bytes;      /* algorithmic bytes of the search kernels (64-bit path counts):
+                                sh / sfm: 24 * edges_scanned (12 B edge record, 4 B level test, 8 B
+                                path-count update) + 8 * frontier_vertices (row bounds) + 12 *
+                                states_new (state set-up and frontier entry);
+                                pfm: 4 * edges_scanned (fa(u) per sample and edge) + 12 *
+                                edges_scanned / 32 (the edge record, shared by 32 samples) + 24 *
+                                sigma_adds (sigma(u) read, sigma(v) read-modify-write) */
+    uint64_t frontier_vertices; /* F (above) */
 } mantra_info;
 
 /* Output of mantra_temporal_stats (paper App. D, Algorithm 2). */
@@ -228,10 +253,11 @@ int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, ui
  * risk its failure between requests.  The call allocates nothing: the search
  * scratch and launch counters live in one fixed 64 MiB __device__ array that
  * every GPU loading the library holds until exit.
- *   g: a graph loaded earlier with mantra_graph_load; s_dev, z_dev, len_dev:
+ *   g: a graph loaded earlier with mantra_graph_load, on the device that is
+ *   current for this call (MANTRA_E_INVAL otherwise); s_dev, z_dev, len_dev:
  *   count uint32 DEVICE buffers; sigma_dev: 2*count uint64 (low, high words);
  *   nodes_dev: count*cap uint32 (may be NULL when cap = 0); stream: a
- *   cudaStream_t or NULL (legacy default stream).  Outputs are those of
+ *   cudaStream_t of that same device, or NULL (legacy default stream).  Outputs are those of
  *   mantra_sample_paths, indexed by (sample index - i0).
  * The first call made on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.

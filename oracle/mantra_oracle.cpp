@@ -420,11 +420,95 @@ int unrank_path(const Graph& G, int opt, uint32_t s, uint32_t z, const Search& R
     return OK;
 }
 
+// ---------------------------------------------------------------------------
+// Work of one sample's search (the exact counters behind the algorithmic-byte
+// model of the measurement; no paper passage defines them, they restate what
+// the search of Sec. 3 / Def. 1 must touch).  tz = z's latest in-edge time.
+// sh / sfm / fsfm: F_k = the appearances (v,t) on hop level k with t < tz
+// (fsfm: t <= tz), F_0 = {(s,-inf)}.  sh / sfm search levels 0 .. d-1 when z
+// is reached on level d (levels 0 .. d-2 are expanded), or every non-empty
+// level when z is unreachable (all expanded); fsfm searches and expands every
+// non-empty level.
+//   escan  per searched level: |in(z)| (sh / sfm test whether the level
+//          reaches z); per expanded level: for each vertex u of F_k, the
+//          out-edges (u,v,t) with t > u's earliest time in F_k and t < tz
+//          (fsfm: t <= tz); every out-edge of s on level 0;
+//   eadd   those expanded edges whose head (v,t) is on level k+1;
+//   snew   the sizes of the levels that follow the expanded ones;
+//   fseg   the distinct vertices of every searched level (1 on level 0).
+// pfm: te = fa(z), or tz when z is unreachable;
+//   escan  edges (u,v,t) with v != s and (earliest out-edge time of s) <= t <= te;
+//   eadd   edges (w,v,t) with v != s, t = fa(v) <= te and fa(w) < fa(v)
+//          (the prefix-foremost DAG);  snew = fseg = 0.
+// A sample whose s has no out-edge, or whose z has no in-edge, counts nothing.
+// ---------------------------------------------------------------------------
+struct Work { uint64_t escan = 0, eadd = 0, snew = 0, fseg = 0; };
+
+void search_work(const Graph& G, int opt, uint32_t s, uint32_t z, const Search& R, Work* w) {
+    *w = Work();
+    if (G.out[s].empty() || G.in[z].empty()) return;
+    int64_t tz = -1;
+    for (const auto& e : G.in[z]) tz = std::max<int64_t>(tz, e.second);
+    if (opt == OPT_PFM) {
+        int64_t ts = POS_INF;
+        for (const auto& e : G.out[s]) ts = std::min<int64_t>(ts, e.second);
+        const int64_t te = (R.fa[z] == POS_INF) ? tz : R.fa[z];
+        for (const auto& e : G.edges) {
+            const uint32_t u = std::get<0>(e), v = std::get<1>(e);
+            const int64_t t = std::get<2>(e);
+            if (v == s) continue;
+            if (ts <= t && t <= te) w->escan += 1;
+            if (t == R.fa[v] && t <= te && R.fa[u] < R.fa[v]) w->eadd += 1;
+        }
+        return;
+    }
+    const bool fsfm = opt == OPT_FSFM;
+    auto keep = [&](int64_t t) { return fsfm ? t <= tz : t < tz; };
+    // the kept appearances by level
+    std::vector<std::vector<App>> lev(1, std::vector<App>(1, App(s, NEG_INF)));
+    for (const auto& kv : R.st) {
+        const uint32_t k = kv.second.level;
+        if (k == 0 || !keep(kv.first.second)) continue;
+        if (lev.size() <= k) lev.resize(k + 1);
+        lev[k].push_back(kv.first);
+    }
+    // searched levels 0 .. last_searched, expanded levels 0 .. last_expanded
+    int64_t last_searched, last_expanded;
+    const bool reached = !fsfm && R.d > 0;
+    if (reached) {
+        last_searched = (int64_t)R.d - 1;
+        last_expanded = (int64_t)R.d - 2;
+    } else {
+        int64_t K = 0;
+        for (size_t k = 0; k < lev.size(); ++k) if (!lev[k].empty()) K = (int64_t)k;
+        last_searched = last_expanded = K;
+    }
+    for (int64_t k = 0; k <= last_searched; ++k) {
+        // lev[k] is in map order: grouped by vertex, ascending in time
+        std::map<uint32_t, int64_t> first_time;
+        for (const App& a : lev[k]) if (!first_time.count(a.first)) first_time[a.first] = a.second;
+        w->fseg += first_time.size();
+        if (!fsfm) w->escan += G.in[z].size();
+        if (k > last_expanded) continue;
+        for (const auto& ut : first_time) {
+            for (const auto& e : G.out[ut.first]) {
+                const int64_t t = e.second;
+                if (!(t > ut.second) || !keep(t)) continue;
+                w->escan += 1;
+                auto it = R.st.find(App(e.first, t));
+                if (it != R.st.end() && it->second.level == (uint32_t)k + 1) w->eadd += 1;
+            }
+        }
+        if ((size_t)k + 1 < lev.size()) w->snew += lev[k + 1].size();
+    }
+}
+
 struct Sample {
     uint32_t s = 0, z = 0;
     u128 sigma = 0;
     std::vector<uint32_t> path;   // s .. z, empty when z is unreachable
     std::vector<uint32_t> edges;  // temporal edge ids of the path, s to z
+    Work work;                    // the search's work counters
 };
 
 // One sample of Algorithm 1's Update step: draw (s,z), count optimal paths,
@@ -435,6 +519,7 @@ int one_sample(const Graph& G, int opt, uint64_t seed, uint64_t i, uint32_t dom_
     Search R;
     int st = count_paths(G, opt, out->s, out->z, &R, &out->sigma);
     if (st != OK) return st;
+    search_work(G, opt, out->s, out->z, R, &out->work);
     out->path.clear();
     if (out->sigma == 0) return OK;                       // unreachable: empty path
     u128 x;
@@ -637,7 +722,7 @@ int rtb_values(const Graph& G, int opt, uint64_t seed, uint64_t i, uint32_t dom,
 // for the internal vertices v on some optimal path (all 0 when z is
 // unreachable).
 int ob_values(const Graph& G, int opt, uint64_t seed, uint64_t i, uint32_t dom_pair,
-              std::vector<std::pair<uint32_t, uint64_t>>* vals) {
+              std::vector<std::pair<uint32_t, uint64_t>>* vals, Work* work = nullptr) {
     vals->clear();
     uint32_t s, z;
     if (!draw_pair(G.n, seed, i, dom_pair, &s, &z)) return E_RNG;
@@ -645,6 +730,7 @@ int ob_values(const Graph& G, int opt, uint64_t seed, uint64_t i, uint32_t dom_p
     u128 sg;
     int st = count_paths(G, opt, s, z, &R, &sg);
     if (st != OK) return st;
+    if (work) search_work(G, opt, s, z, R, work);
     if (sg == 0) return OK;
     std::vector<u128> th;
     through_counts(G, opt, s, z, R, &th);
@@ -702,6 +788,9 @@ struct orc_info {
     uint64_t r, rounds, omega, s1, bootstrap, sum_int_len, max_hits;
     int64_t rade_num;
     double xi, vhat, rho_hat;
+    // work counters of the trk and ob searches (search_work), bootstrap
+    // included; 0 for RTB
+    uint64_t edges_scanned, sigma_adds, states_new, frontier_vertices;
 };
 
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) { philox4x32_10(ctr, key, out); }
@@ -825,6 +914,21 @@ int orc_samples(const void* g, int opt, uint64_t seed, uint64_t i0, uint64_t cou
     return OK;
 }
 
+// Work counters (search_work) of samples i0 .. i0+count-1 of the given
+// domains: out[4q .. 4q+3] = escan, eadd, snew, fseg of sample i0+q.
+int orc_work(const void* g, int opt, uint64_t seed, uint64_t i0, uint64_t count, uint32_t dom_pair,
+             uint32_t dom_path, uint64_t* out) {
+    const Graph* G = (const Graph*)g;
+    for (uint64_t q = 0; q < count; ++q) {
+        Sample S;
+        int st = one_sample(*G, opt, seed, i0 + q, dom_pair, dom_path, &S);
+        if (st != OK) return st;
+        out[4 * q] = S.work.escan; out[4 * q + 1] = S.work.eadd;
+        out[4 * q + 2] = S.work.snew; out[4 * q + 3] = S.work.fseg;
+    }
+    return OK;
+}
+
 // Edge ids: for temporal edge id e, its (u, v, t) and its underlying edge id;
 // *n_underlying = the number of underlying edges.
 void orc_edge_ids(const void* g, uint32_t* u, uint32_t* v, uint32_t* t, uint32_t* uedge, uint32_t* n_underlying) {
@@ -931,8 +1035,16 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
     auto square32 = [](uint64_t q) { return (uint64_t)(((u128)q * q + ((u128)1 << 31)) >> 32); };
     // Update step for samples [a, b): hits and Rademacher sums (Algorithm 1).
     // the fractional functions of sample i (ob: pair (s,z); RTB: source s)
+    auto count_work = [&](const Work& w) {
+        I.edges_scanned += w.escan; I.sigma_adds += w.eadd; I.states_new += w.snew; I.frontier_vertices += w.fseg;
+    };
     auto frac_values = [&](uint64_t i, uint32_t dom, std::vector<std::pair<uint32_t, uint64_t>>* vals) -> int {
-        if (estimator == 1) return ob_values(*G, opt, seed, i, dom, vals);
+        if (estimator == 1) {
+            Work w;
+            const int st = ob_values(*G, opt, seed, i, dom, vals, &w);
+            count_work(w);
+            return st;
+        }
         std::vector<uint64_t> q;
         int st = rtb_values(*G, opt, seed, i, dom, &q);
         vals->clear();
@@ -957,6 +1069,7 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
             Sample sm;
             int st = one_sample(*G, opt, seed, i, D_PAIR, D_PATH, &sm);
             if (st != OK) return st;
+            count_work(sm.work);
             items_of(sm, &it);
             for (uint32_t x : it) {
                 hits[x] += 1;
@@ -1020,6 +1133,7 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
             Sample sm;
             int st = one_sample(*G, opt, seed, i, D_BOOT_PAIR, D_BOOT_PATH, &sm);
             if (st != OK) return st;
+            count_work(sm.work);
             items_of(sm, &it);
             for (uint32_t x : it) { hb[x] += 1; sum_b += 1; }
         }

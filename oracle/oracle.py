@@ -37,7 +37,9 @@ def build(force: bool = False) -> str:
 class Info(C.Structure):
     _fields_ = [("r", C.c_uint64), ("rounds", C.c_uint64), ("omega", C.c_uint64), ("s1", C.c_uint64),
                 ("bootstrap", C.c_uint64), ("sum_int_len", C.c_uint64), ("max_hits", C.c_uint64),
-                ("rade_num", C.c_int64), ("xi", C.c_double), ("vhat", C.c_double), ("rho_hat", C.c_double)]
+                ("rade_num", C.c_int64), ("xi", C.c_double), ("vhat", C.c_double), ("rho_hat", C.c_double),
+                ("edges_scanned", C.c_uint64), ("sigma_adds", C.c_uint64), ("states_new", C.c_uint64),
+                ("frontier_vertices", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -66,6 +68,8 @@ def lib():
         L.orc_samples.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32,
                                   C.c_uint32, u32p, u32p, u64p, u64p, u32p, u32p, C.c_uint32, u32p]
         L.orc_edge_ids.argtypes = [C.c_void_p, u32p, u32p, u32p, u32p, u32p]
+        L.orc_work.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
+                               u64p]
         L.orc_sd_bound.restype = C.c_double
         L.orc_sd_bound.argtypes = [C.c_double] * 6
         L.orc_xi_from_R.restype = C.c_double
@@ -207,6 +211,14 @@ class Graph:
                 row = row + ([int(x) for x in pe[q * cap:q * cap + max(int(ln[q]) - 1, 0)]],)
             out.append(row)
         return out
+
+    def work(self, opt, seed, i0, count, dom_pair=D_PAIR, dom_path=D_PATH):
+        """Per-sample work counters of the searches (escan, eadd, snew, fseg),
+        an array of shape (count, 4); definitions in mantra_oracle.cpp
+        (search_work)."""
+        out = np.zeros(4 * count, np.uint64)
+        _chk(lib().orc_work(self.h, opt, seed, i0, count, dom_pair, dom_path, _p(out, C.c_uint64)))
+        return out.reshape(count, 4)
 
     def edge_ids(self):
         """(u, v, t, underlying id) per temporal edge id, and the number of

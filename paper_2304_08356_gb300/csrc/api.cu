@@ -882,6 +882,7 @@ struct Problem {
         I.kernel_ms = T.kernel_ms; I.search_launches = T.launches;
         I.kernel_launches = T.launches + reduces + (f > 0 ? 1 : 0);
         I.alg_bytes = alg_bytes_of(opt == MANTRA_PFM, T.escan, T.eadd, T.snew, T.fseg);
+        I.frontier_vertices = opt == MANTRA_PFM ? 0 : T.fseg;
         return MANTRA_OK;
     }
 
@@ -1116,15 +1117,19 @@ int take_result(Server* S, std::map<uint64_t, Request*>::iterator it, double* es
 namespace mantra {
 
 // Read-only view of a loaded graph for the library's other translation units.
-const DevGraph* graph_view(const mantra_graph* g, uint32_t* n, uint32_t* A, int* num_sms, size_t* smem_optin,
-                           std::mutex** mu) {
+int graph_view(const mantra_graph* g, const DevGraph** dg, int* device, uint32_t* n, uint32_t* A, int* num_sms,
+               size_t* smem_optin, std::mutex** mu) {
     Engine* E = nullptr;
-    engine_for(g->device, &E);
+    const int rc = engine_for(g->device, &E);
+    if (rc != MANTRA_OK) return rc;
+    if (!E) return MANTRA_E_CUDA;
+    *dg = &g->dg;
+    *device = g->device;
     *n = g->n; *A = g->A;
-    *num_sms = E ? E->num_sms : 1;
-    *smem_optin = E ? E->smem_optin : 48 * 1024;
-    *mu = E ? &E->mu : nullptr;
-    return &g->dg;
+    *num_sms = E->num_sms;
+    *smem_optin = E->smem_optin;
+    *mu = &E->mu;
+    return MANTRA_OK;
 }
 
 }  // namespace mantra

@@ -19,8 +19,8 @@
 #include <mutex>
 
 namespace mantra {
-const DevGraph* graph_view(const mantra_graph* g, uint32_t* n, uint32_t* A, int* num_sms, size_t* smem_optin,
-                           std::mutex** mu);
+int graph_view(const mantra_graph* g, const DevGraph** dg, int* device, uint32_t* n, uint32_t* A, int* num_sms,
+               size_t* smem_optin, std::mutex** mu);
 }
 using namespace mantra;
 
@@ -73,10 +73,16 @@ extern "C" int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt
     if (count == 0) return MANTRA_OK;
 
     uint32_t n = 0, A = 0;
-    int num_sms = 0;
+    int num_sms = 0, gdev = -1, cur = -1;
     size_t smem_optin = 0;
     std::mutex* gmu = nullptr;
-    const DevGraph* dg = graph_view(g, &n, &A, &num_sms, &smem_optin, &gmu);
+    const DevGraph* dg = nullptr;
+    const int vrc = graph_view(g, &dg, &gdev, &n, &A, &num_sms, &smem_optin, &gmu);
+    if (vrc != MANTRA_OK) return vrc;
+    // the scratch address, the launch and the stream all belong to the current
+    // device; the graph's store must live on that same device
+    if (cudaGetDevice(&cur) != cudaSuccess) return MANTRA_E_CUDA;
+    if (cur != gdev) return MANTRA_E_INVAL;
 
     // layout: [counters | task table (one task) | overflow list (count entries) | per-CTA search regions]
     const size_t smem = bfs_smem_bytes(A);

@@ -1037,13 +1037,18 @@ size_t bfs_static_smem(int nt) {
     return std::max(std::max(a.sharedSizeBytes, b.sharedSizeBytes), c.sharedSizeBytes);
 }
 
-// Raises (never lowers) the kernels' dynamic shared-memory limit, so callers
-// with different graph sizes do not undo each other's setting.
+// Raises (never lowers) the kernels' dynamic shared-memory limit on the
+// current device, so callers with different graph sizes do not undo each
+// other's setting.  The attribute is per device, so is the record of it.
 cudaError_t bfs_configure(size_t smem) {
     static std::mutex mu;
-    static size_t configured = 0;
+    static size_t configured[64] = {};
+    int dev = 0;
+    const cudaError_t ed = cudaGetDevice(&dev);
+    if (ed != cudaSuccess) return ed;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
-    if (smem <= configured) return cudaSuccess;
+    if (smem <= configured[dev]) return cudaSuccess;
     const void* ks[6] = {(const void*)k_bfs<false, 512, false>, (const void*)k_bfs<false, 512, true>,
                          (const void*)k_bfs<true, 512, true>, (const void*)k_bfs<false, 1024, false>,
                          (const void*)k_bfs<false, 1024, true>, (const void*)k_bfs<true, 1024, true>};
@@ -1051,7 +1056,7 @@ cudaError_t bfs_configure(size_t smem) {
         const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    configured = smem;
+    configured[dev] = smem;
     return cudaSuccess;
 }
 

@@ -699,16 +699,21 @@ size_t pfm_cta_static_smem(int nt) {
     return e == cudaSuccess ? a.sharedSizeBytes : 16384;
 }
 
-// Raises (never lowers) the dynamic shared-memory limit of the shared-memory variants.
+// Raises (never lowers) the dynamic shared-memory limit of the shared-memory
+// variants on the current device (the attribute, and its record, are per device).
 cudaError_t pfm_cta_configure(size_t smem) {
     static std::mutex mu;
-    static size_t configured = 0;
+    static size_t configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
-    if (smem <= configured) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_pfm_cta<512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem <= configured[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_pfm_cta<512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_pfm_cta<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) configured = smem;
+    if (e == cudaSuccess) configured[dev] = smem;
     return e;
 }
 
