@@ -265,8 +265,9 @@ int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, ui
  * clears what must start at zero.  Calls that overlap on the GPU (two streams,
  * two threads, two graphs) race on the array: serialise them.
  * Returns MANTRA_E_INVAL for pfm, for a graph whose search scratch does not
- * fit the fixed array (roughly 40 bytes per arrival slot plus 52 per node
- * for one CTA, plus 8 bytes per requested sample), and MANTRA_E_OVERFLOW
+ * fit the fixed array (roughly 40 bytes per arrival slot plus 52 per node,
+ * plus 16 per arrival slot of the vertex with the most slots, for one CTA,
+ * plus 8 bytes per requested sample), and MANTRA_E_OVERFLOW
  * when a path count exceeds 64 bits (this variant has no 128-bit re-run). */
 int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt, uint64_t seed, uint32_t dom_pair,
                                 uint32_t dom_path, uint64_t i0, uint64_t count, uint32_t* s_dev, uint32_t* z_dev,

@@ -74,7 +74,7 @@ int upload_store(const StoreHost& H, mantra_graph* G, cudaStream_t st) {
     G->n = H.n; G->m = H.m; G->A = H.A; G->n_uedge = H.n_uedge;
     G->self_loops = H.self_loops; G->duplicates = H.duplicates;
     G->dg.n = H.n; G->dg.A = H.A; G->dg.m = H.m; G->dg.n_uedge = H.n_uedge;
-    G->dg.cbound = H.cbound; G->dg.max_slot_in = H.max_slot_in;
+    G->dg.cbound = H.cbound; G->dg.max_slot_in = H.max_slot_in; G->dg.max_vslots = H.max_vslots;
     return MANTRA_OK;
 }
 
@@ -181,7 +181,7 @@ struct Engine {
     cudaEvent_t e_t0 = nullptr, e_t1 = nullptr;   // around a graph launch (events inside graphs cannot be timed)
     bool last_tick_graph = false;
     // search workspaces
-    char* bfs_mem = nullptr; BfsWs bws{}; int bfs_grid = 0; size_t bfs_smem = 0; uint32_t bfs_n = 0, bfs_A = 0;
+    char* bfs_mem = nullptr; BfsWs bws{}; int bfs_grid = 0; size_t bfs_smem = 0; uint32_t bfs_n = 0, bfs_A = 0, bfs_z = 0;
     int bfs_grid_big = 0;      // resident 1024-thread CTAs (the regions of the first ones)
     int tick_bfs_nt = 512;     // sh/sfm CTA size of the current tick
     bool tick_frac = false;    // the tick has an ob or RTB problem on the sh/sfm kernel
@@ -262,10 +262,11 @@ struct Engine {
     }
 
     // sh/sfm: one region per CTA, one CTA per SM, at most a third of free memory.
-    int ensure_bfs(uint32_t n, uint32_t A) {
-        if (bfs_mem && n <= bfs_n && A <= bfs_A) return MANTRA_OK;
+    int ensure_bfs(uint32_t n, uint32_t A, uint32_t zc) {
+        if (bfs_mem && n <= bfs_n && A <= bfs_A && zc <= bfs_z) return MANTRA_OK;
         n = std::max(n, bfs_n);
         A = std::max(A, bfs_A);
+        zc = std::max(zc, bfs_z);
         if (bfs_mem) { cudaStreamSynchronize(sa); cudaFree(bfs_mem); bfs_mem = nullptr; }
         // regions for the 512-thread shape (two CTAs per SM); the 1024-thread
         // shape (one per SM) uses the first of them
@@ -287,7 +288,7 @@ struct Engine {
             if (env[0] == '0') in_smem = false;
             else if (env[0] == '1') in_smem = smem + std::max(bfs_static_smem(512), bfs_static_smem(1024)) + 1024 <= smem_optin;
         }
-        const size_t region = bfs_region_bytes(n, A, in_smem, &bws);
+        const size_t region = bfs_region_bytes(n, A, zc, in_smem, &bws);
         CU(bfs_configure(in_smem ? smem : 0));
         int per_sm = 0, per_sm_big = 0;
         CU(bfs_blocks_per_sm(512, in_smem ? smem : 0, &per_sm));
@@ -304,7 +305,7 @@ struct Engine {
         bfs_grid = grid;
         bfs_grid_big = std::min(grid, num_sms * std::max(per_sm_big, 1));
         bfs_smem = in_smem ? smem : 0;
-        bfs_n = n; bfs_A = A;
+        bfs_n = n; bfs_A = A; bfs_z = zc;
         invalidate_graph();
         return MANTRA_OK;
     }
@@ -501,7 +502,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     const uint32_t k = (uint32_t)items.size();
     int rc;
     if ((rc = E.ensure_tables(std::max<uint32_t>(k, 1))) != MANTRA_OK) return rc;
-    uint32_t bn = 0, bA = 0, pn = 0, plc = 0;
+    uint32_t bn = 0, bA = 0, bz = 0, pn = 0, plc = 0;
     uint64_t pwarps = 0, bsamples = 0;
     bool any_b = false, any_p = false, frac = false;
     for (const TickItem& it : items) {
@@ -510,13 +511,14 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
             pwarps += (it.job.count + 31) / 32;
         } else {
             any_b = true; bn = std::max(bn, it.G->n); bA = std::max(bA, it.G->A);
+            bz = std::max(bz, it.G->dg.max_vslots);
             bsamples += it.job.count;
             frac |= it.job.ob || it.job.rtb || it.job.opt == 3;
         }
     }
     E.tick_frac = frac;
     const bool cta = any_p && !wide && pfm_use_cta();
-    if (any_b && (rc = E.ensure_bfs(bn, bA)) != MANTRA_OK) return rc;
+    if (any_b && (rc = E.ensure_bfs(bn, bA, bz)) != MANTRA_OK) return rc;
     if (any_p && cta && (rc = E.ensure_pfm_cta(pn, plc)) != MANTRA_OK) return rc;
     if (any_p && !cta && (rc = E.ensure_pfm(pn, plc, pwarps)) != MANTRA_OK) return rc;
     E.tick_cta = cta;

@@ -14,13 +14,20 @@
 //             reaches z, level k+1 is z's level d and the search stops (the
 //             last level is never pushed).
 //   push      every out-edge (u, v, t) of a frontier vertex with
-//             t_min'(u) < t < tmax_in(z) adds sigma of u's frontier
-//             appearances earlier than t to slot (v, t) unless that slot
-//             already has a level <= k.  Appearances at or after z's latest
-//             in-edge time cannot lie on an s-z path; they are not created.
+//             t_min'(u) < t < tmax_in(z) marks slot (v, t) for level k+1
+//             unless that slot already has a level <= k.  Appearances at or
+//             after z's latest in-edge time cannot lie on an s-z path; they
+//             are not created.
 //   compact   the next-level bitmap is compacted in slot order into F_{k+1}.
-// Visited/next bitmaps live in shared memory when 2*ceil(A/32) words fit,
-// else in per-CTA global scratch.
+//   count     each state b = (v, t) of F_{k+1} sums, over its in-edges
+//             (w, v, t), the path counts of w's level-k appearances earlier
+//             than t (Def. 1: sigma(b) is the number of shortest walks to b),
+//             and stores the sum at b's frontier position.
+// Path counts therefore live in frontier order (Fs, parallel to F): they are
+// written once, read in order by the next level's scan, and never cleared;
+// only z's endpoint slots, reached by the pull, keep per-slot counts (zsig).
+// The visited bitmap lives in shared memory when it fits (else in per-CTA
+// global scratch); the next-level bitmap is in the scratch.
 #include "mantra_dev.cuh"
 
 #include <algorithm>
@@ -36,7 +43,8 @@ constexpr int CK = 8;             // bitmap words in flight per lane in the comp
 // counts dl (the number of optimal ways from a state to z's endpoints) per
 // frontier position, backward from level d; sigma_sz(v) = sum over v's states
 // of sigma * dl (a path visits v once); then every internal v gets its ob
-// value.  dl: the (free) running-sum array, indexed by frontier position;
+// value.  sig: path counts by frontier position; dl: the (free) running-sum
+// array, indexed by frontier position;
 // acc: per-vertex sums (zero on entry and exit); VB: vertex bitmap (zero on
 // entry and exit); tl: n entries.
 template <bool WIDE, int BFS_NT>
@@ -89,7 +97,7 @@ __device__ __forceinline__ void bfs_ob_update(const DevGraph& g, const Job& job,
         const Sig x = ldcg_sig(dl + p);
         if (x == (Sig)0) continue;
         const uint32_t a = F[p], v = g.slot_v[a];
-        SigOps<WIDE>::atomic_add(acc + v, (Sig)(sig[a] * x));   // <= sigma_sz: no wrap
+        SigOps<WIDE>::atomic_add(acc + v, (Sig)(sig[p] * x));   // <= sigma_sz: no wrap
         const uint32_t bit = 1u << (v & 31);
         if (!(atomicOr(VB + (v >> 5), bit) & bit)) tl[atomicAdd(sh_nt, 1u)] = v;
     }
@@ -125,7 +133,8 @@ __device__ __forceinline__ void bfs_ob_update(const DevGraph& g, const Job& job,
 // sigma(b) / sigma_{s,v_b} for an endpoint b.  From level D down, every state
 // b with X(b) = eps(b) + delta(b) > 0 adds round(sigma(a) X(b) / sigma(b)) to
 // delta(a) of each DAG predecessor a; f_v(s) = round(sum of delta over v's
-// states / (n-1)), all in 2^-32 units.  dl: per frontier position (the free
+// states / (n-1)), all in 2^-32 units.  sig: path counts by frontier
+// position; dl: per frontier position (the free
 // running-sum array); sv: sigma_{s,v} (zero on entry and exit); dsum:
 // per-vertex sums (zero on entry and exit); dv: first level per vertex (n
 // entries, overwritten); VB: vertex bitmap (zero on entry and exit); tl: n
@@ -164,32 +173,32 @@ __device__ __forceinline__ void bfs_rtb_update(const DevGraph& g, const Job& job
     for (uint32_t k = 1; k <= D; ++k)
         for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
             const uint32_t a = F[p], v = g.slot_v[a];
-            if (is_end(p, k, v)) SigOps<WIDE>::atomic_add(sv + v, sig[a]);
+            if (is_end(p, k, v)) SigOps<WIDE>::atomic_add(sv + v, sig[p]);
         }
     __syncthreads();
-    auto eps_of = [&](uint32_t p, uint32_t k, uint32_t a, uint32_t v) -> u64 {
-        return is_end(p, k, v) ? ob_q(SigOps<WIDE>::wide(sig[a]), SigOps<WIDE>::wide(ldcg_sig(sv + v))) : 0ull;
+    auto eps_of = [&](uint32_t p, uint32_t k, uint32_t v) -> u64 {
+        return is_end(p, k, v) ? ob_q(SigOps<WIDE>::wide(sig[p]), SigOps<WIDE>::wide(ldcg_sig(sv + v))) : 0ull;
     };
     for (uint32_t k = 1; k <= D; ++k)
         for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
-            const uint32_t a = F[p];
-            dl[p] = eps_of(p, k, a, g.slot_v[a]);
+            dl[p] = eps_of(p, k, g.slot_v[F[p]]);
         }
     __syncthreads();
     for (uint32_t k = D; k >= 2; --k) {
         const uint32_t* Fp = F + lev[k - 1];
+        const Sig* Sp = sig + lev[k - 1];
         const uint32_t Lp = lev[k] - lev[k - 1];
         for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
             const u64 X = __ldcg(reinterpret_cast<const unsigned long long*>(dl + p));
             if (!X) continue;
             const uint32_t b = F[p], tb = g.slot_t[b];
-            const u128 sb = SigOps<WIDE>::wide(sig[b]);
+            const u128 sb = SigOps<WIDE>::wide(sig[p]);
             for (uint32_t e = g.slot_in[b]; e < g.slot_in[b + 1]; ++e) {
                 const uint32_t w = g.in_u[e], w1 = g.slot_ptr[w + 1];
                 for (uint32_t p2 = lower_bound_u32(Fp, 0, Lp, g.slot_ptr[w]); p2 < Lp; ++p2) {
                     const uint32_t a2 = Fp[p2];
                     if (a2 >= w1 || g.slot_t[a2] >= tb) break;
-                    const u64 term = muldiv_round(SigOps<WIDE>::wide(sig[a2]), X, sb);
+                    const u64 term = muldiv_round(SigOps<WIDE>::wide(Sp[p2]), X, sb);
                     if (term) atomicAdd(dl + lev[k - 1] + p2, term);
                 }
             }
@@ -201,7 +210,7 @@ __device__ __forceinline__ void bfs_rtb_update(const DevGraph& g, const Job& job
         for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
             const uint32_t a = F[p], v = g.slot_v[a];
             if (v == s) continue;
-            const u64 d = __ldcg(reinterpret_cast<const unsigned long long*>(dl + p)) - eps_of(p, k, a, v);
+            const u64 d = __ldcg(reinterpret_cast<const unsigned long long*>(dl + p)) - eps_of(p, k, v);
             if (!d) continue;
             atomicAdd(dsum + v, d);
             const uint32_t bit = 1u << (v & 31);
@@ -334,7 +343,8 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
     __shared__ int sh_t;
 
     char* region = ws.base + (size_t)blockIdx.x * ws.stride;
-    Sig* sig = reinterpret_cast<Sig*>(region + ws.o_sig);
+    Sig* Fs = reinterpret_cast<Sig*>(region + ws.o_sig);      // path count of the state at each frontier position
+    Sig* zsig = reinterpret_cast<Sig*>(region + ws.o_zsig);   // path counts of z's slots reached by the pull
     Sig* Fc = reinterpret_cast<Sig*>(region + ws.o_fc);
     uint32_t* F = reinterpret_cast<uint32_t*>(region + ws.o_f);
     uint32_t* Ft = reinterpret_cast<uint32_t*>(region + ws.o_ft);
@@ -370,9 +380,8 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
     __shared__ uint32_t sh_first;
     __shared__ uint32_t sh_zbest, sh_zmin, sh_zlev;   // fsfm: earliest slot of z so far, and its level
     __shared__ FracCtx sh_fx;
-    __shared__ uint32_t cs_off[BFS_NT + 1], cs_first[BFS_NT], cs_fb[BFS_NT], cs_fe[BFS_NT];   // range table
+    __shared__ uint32_t cs_off[BFS_NT + 1], cs_first[BFS_NT];   // range table
     __shared__ uint32_t sh_stamp, sh_wrap;
-    __shared__ u64 sh_fcmax;
     __shared__ uint32_t sm_Ft[WIDE ? 1 : FCAP];   // level times and running sums (64-bit counts, L <= FCAP)
     __shared__ u64 sm_Fc[WIDE ? 1 : FCAP];
 
@@ -387,7 +396,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             const uint32_t st = sh_stamp + 1u;
             sh_wrap = st == 0u;
             sh_stamp = st == 0u ? 1u : st;
-            sh_carry = (Sig)0; sh_scan_ovf = 0; sh_fcmax = 0;
+            sh_carry = (Sig)0; sh_scan_ovf = 0;
         }
         __syncthreads();
         if (sh_wrap) {
@@ -462,6 +471,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
         // ---------------- level loop ----------------
         uint32_t k = 0;
         uint32_t L = 1;                 // |F_k| (level 0: the virtual source)
+        uint32_t Fend = 0;              // end of the frontier lists (states of levels 1 .. k+1)
         if (tid == 0) { lev[0] = 0; lev[1] = 0; }
         __syncthreads();
         while (live) {
@@ -477,18 +487,17 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 if (tid == 0) {
                     seg_b[0] = 0; seg_u[0] = s; FcL[0] = (Sig)1; FtL[0] = 0; my_fseg += 1;
                     segmap[s] = ((u64)stamp << 32);
-                    sh_fcmax = 1;
                 }
                 __syncthreads();
                 G = 1;
             } else {
                 const uint32_t* Fk = F + lev[k];
+                const Sig* Fsk = Fs + lev[k];
                 // B1: frontier attributes, segment heads and per-vertex running sums
                 // of sigma.  Each thread takes IPT consecutive states of a tile: a
                 // thread-local segmented scan, one block-wide segmented scan of the
                 // thread aggregates, and the value carried into each thread.
                 uint32_t gbase = 0;
-                u64 fcmax = 0;
                 const uint32_t* const g_slot_v = g.slot_v;
                 const uint32_t* const g_slot_t = g.slot_t;
                 for (uint32_t it = 0; it < L; it += BFS_NT * IPT) {
@@ -505,7 +514,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                             if (i0 + q < L) {
                                 uq[q] = g_slot_v[aq[q]];
                                 FtL[i0 + q] = g_slot_t[aq[q]];
-                                vq[q] = sig[aq[q]];
+                                vq[q] = Fsk[i0 + q];
                             }
                         }
                     }
@@ -538,10 +547,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                         const uint32_t idx = i0 + q;
                         if ((hm >> q) & 1u) run = vq[q];
                         else { const Sig sm = run + vq[q]; bad |= sm < run; run = sm; }
-                        if (idx < L) {
-                            FcL[idx] = run;
-                            if (!WIDE && (u64)run > fcmax) fcmax = (u64)run;
-                        }
+                        if (idx < L) FcL[idx] = run;
                     }
                     if (bad) sh_scan_ovf = 1u;
                     uint32_t tot;
@@ -558,24 +564,15 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                     gbase += tot;
                 }
                 G = gbase;
-                if (!WIDE) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) fcmax = max(fcmax, (u64)__shfl_xor_sync(0xFFFFFFFFu, fcmax, o));
-                    if (lane == 0 && fcmax) atomicMax(&sh_fcmax, fcmax);
-                }
                 if (tid == 0) {
                     my_fseg += G;
                     if (sh_scan_ovf && !stats) sh_ovf = 1;
                 }
                 __syncthreads();
             }
-            // 64-bit path counts of the next level cannot wrap when every running sum
-            // times the largest in-edge count of a slot stays below 2^64: the push then
-            // adds without reading the old value back
-            const bool fast_add = !WIDE && __umul64hi(sh_fcmax, (u64)g.max_slot_in) == 0ull;
             if (sh_ovf) break;
 
-            // ---- pull: does level k reach z? ----
+            // ---- pull: does level k reach z?  (z's slots keep their counts in zsig) ----
             if (!full && !fsfm) {
                 const uint32_t zs = g.slot_ptr[z], ze = g.slot_ptr[z + 1];
                 const uint32_t e_lo = g.slot_in[zs], e_hi = g.slot_in[ze];
@@ -598,7 +595,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                             if (c == fb) have = false; else idx = c - 1;
                         }
                         if (have) {
-                            if (!SigOps<WIDE>::atomic_add(sig + a, FcL[idx])) sh_ovf = 1;
+                            if (!SigOps<WIDE>::atomic_add(zsig + (a - zs), FcL[idx])) sh_ovf = 1;
                             atomicOr(N + (a >> 5), 1u << (a & 31));
                             sh_found = 1;
                         }
@@ -618,10 +615,8 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             for (uint32_t c0 = 0; c0 < G; c0 += BFS_NT) {
                 const uint32_t gi = c0 + tid;
                 uint32_t lo2[2] = {0u, 0u}, hi2[2] = {0u, 0u}, key2[2] = {0u, 0u};
-                uint32_t fb = 0, fe = 0;
                 if (gi < G) {
-                    fb = seg_b[gi];
-                    fe = (gi + 1 < G) ? seg_b[gi + 1] : L;
+                    const uint32_t fb = seg_b[gi];
                     const uint32_t u = seg_u[gi];
                     const uint32_t r0 = g_out_ptr[u], r1 = g_out_ptr[u + 1];
                     lo2[0] = r0; hi2[0] = (k == 0) ? r0 : r1; key2[0] = (k == 0) ? 0u : FtL[fb];
@@ -637,7 +632,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                                                               sm_scan64);
                 if (cand > 0) {
                     const uint32_t x = (uint32_t)(ex >> 32);
-                    cs_first[x] = first; cs_off[x] = (uint32_t)ex; cs_fb[x] = fb; cs_fe[x] = fe;
+                    cs_first[x] = first; cs_off[x] = (uint32_t)ex;
                 }
                 const uint32_t Gc = (uint32_t)(tot >> 32), E = (uint32_t)tot;
                 if (tid == 0) cs_off[Gc] = E;
@@ -645,28 +640,15 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 const uint32_t per = ((E + BFS_NW * 32u - 1u) / (BFS_NW * 32u)) * 32u;
                 const uint32_t w_lo = min((uint32_t)wid * per, E), w_hi = min(w_lo + per, E);
                 lbs_walk_batched<WALK_K>(cs_off, Gc, cs_first, w_lo, w_hi, g_out_slot, g_out_t,
-                                         [&](uint32_t r, uint32_t, uint32_t a, uint32_t t) {
+                                         [&](uint32_t, uint32_t, uint32_t a, uint32_t) {
                     ++my_escan;
                     if (!((V[a >> 5] >> (a & 31)) & 1u)) {
                         atomicOr(N + (a >> 5), 1u << (a & 31));
-                        if (!stats) {          // Algorithm 2 needs reach only, no path counts
-                            const uint32_t rb = cs_fb[r], re = cs_fe[r];
-                            uint32_t idx = rb;
-                            if (re - rb > 1) idx = lower_bound_u32(FtL, rb, re, t) - 1;   // last Ft < t
-                            if constexpr (!WIDE) {
-                                if (fast_add) atomicAdd(sig + a, FcL[idx]);
-                                else if (!SigOps<WIDE>::atomic_add(sig + a, FcL[idx])) sh_ovf = 1;
-                            } else {
-                                if (!SigOps<WIDE>::atomic_add(sig + a, FcL[idx])) sh_ovf = 1;
-                            }
-                        }
                         ++my_eadd;
                     }
                 });
                 __syncthreads();
-                if (sh_ovf) break;
             }
-            if (sh_ovf) break;
 
             // ---- compact the next-level bitmap into F_{k+1} ----
             const uint32_t per_w = (((words + BFS_NW - 1) / BFS_NW) + 31u) & ~31u;
@@ -755,9 +737,48 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             }
             if (tid == 0) lev[k + 2] = fbase + Lnext;
             if (tid == 0) my_snew += Lnext;
+            Fend = fbase + Lnext;
             __syncthreads();
             if (fsfm && tid == 0 && sh_zmin < sh_zbest) { sh_zbest = sh_zmin; sh_zlev = k + 1; }
             if (Lnext == 0) break;
+
+            // ---- count: sigma of each new state b = (v, t) is the sum, over its
+            // in-edges (w, v, t) from level-k vertices, of the path counts of w's
+            // level-k appearances earlier than t (the running sum up to the last
+            // of them); stored at b's frontier position ----
+            if (!stats) {
+                const uint32_t* const c_slot_t = g.slot_t;
+                const uint32_t* const c_slot_in = g.slot_in;
+                const uint32_t* const c_in_u = g.in_u;
+                bool bad = false;
+                for (uint32_t p = fbase + tid; p < fbase + Lnext; p += BFS_NT) {
+                    const uint32_t a = F[p];
+                    const uint32_t ta = c_slot_t[a];
+                    const uint32_t e1 = c_slot_in[a + 1];
+                    Sig sum = (Sig)0;
+                    for (uint32_t e = c_slot_in[a]; e < e1; ++e) {
+                        const uint32_t w = c_in_u[e];
+                        const u64 mw = __ldcg(segmap + w);
+                        if ((uint32_t)(mw >> 32) != stamp) continue;        // w is not on level k
+                        uint32_t idx = 0;                                    // level 0: the source, count 1
+                        if (k > 0) {
+                            const uint32_t lo = (uint32_t)mw;
+                            const uint32_t fb = seg_b[lo], fe = (lo + 1 < G) ? seg_b[lo + 1] : L;
+                            const uint32_t c = lower_bound_u32(FtL, fb, fe, ta);   // first Ft >= ta
+                            if (c == fb) continue;                                // none earlier than ta
+                            idx = c - 1;
+                        }
+                        const Sig x = FcL[idx];
+                        const Sig s2 = sum + x;
+                        bad |= s2 < sum;
+                        sum = s2;
+                    }
+                    Fs[p] = sum;
+                }
+                if (bad) sh_ovf = 1;
+                __syncthreads();
+                if (sh_ovf) break;
+            }
             k += 1;
             L = Lnext;
         }
@@ -780,11 +801,16 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 const unsigned msk = __ballot_sync(FULL, b);
                 if (msk) first = a0 + __ffs(msk) - 1;
             }
+            // path count of an endpoint slot: sh / sfm from the pull's per-slot
+            // counts; fsfm's endpoint is a frontier state of level d
+            uint32_t zpos = 0;
+            if (fsfm) zpos = lev[d] + lower_bound_u32(F + lev[d], 0, lev[d + 1] - lev[d], first);
+            auto end_sig = [&](uint32_t a) -> Sig { return fsfm ? Fs[zpos] : ldcg_sig(zsig + (a - zs)); };
             Sig tot = 0;
-            if (job.opt == 1 || fsfm) tot = sig[first];
+            if (job.opt == 1 || fsfm) tot = end_sig(first);
             else {
                 for (uint32_t a = zs + lane; a < ze; a += 32)
-                    if ((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u) { const Sig sm = tot + sig[a]; bad |= sm < tot; tot = sm; }
+                    if ((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u) { const Sig sm = tot + end_sig(a); bad |= sm < tot; tot = sm; }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     const Sig y = shfl_xor_w(tot, o);
@@ -817,7 +843,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 const uint32_t ze_end = one ? first + 1 : ze;
                 for (uint32_t a0 = (one ? first : zs); !err && a0 < ze_end && cur == NONE; a0 += 32) {
                     const uint32_t a = a0 + lane;
-                    const Sig wt = (a < ze_end && (fsfm || ((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u))) ? sig[a] : (Sig)0;
+                    const Sig wt = (a < ze_end && (fsfm || ((__ldcg(N + (a >> 5)) >> (a & 31)) & 1u))) ? end_sig(a) : (Sig)0;
                     const Sig incl = warp_inclusive_sum(wt);
                     const unsigned msk = __ballot_sync(FULL, xs < incl);
                     if (msk) {
@@ -835,6 +861,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 while (!err && lvl > 1) {
                     const uint32_t tv = g.slot_t[cur];
                     const uint32_t* Fp = F + lev[lvl - 1];
+                    const Sig* Sp = Fs + lev[lvl - 1];
                     const uint32_t Lp = lev[lvl] - lev[lvl - 1];
                     const uint32_t e_lo = g.slot_in[cur], e_hi = g.slot_in[cur + 1];
                     uint32_t nxt = NONE;
@@ -849,7 +876,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                             for (uint32_t p = p0; p < Lp; ++p) {
                                 const uint32_t a2 = Fp[p];
                                 if (a2 >= ws1 || g.slot_t[a2] >= tv) break;
-                                wt += sig[a2];
+                                wt += Sp[p];
                             }
                         }
                         const Sig incl = warp_inclusive_sum(wt);
@@ -862,7 +889,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                                 for (uint32_t p = p0; p < Lp; ++p) {
                                     const uint32_t a2 = Fp[p];
                                     if (a2 >= ws1 || g.slot_t[a2] >= tv) break;
-                                    const Sig w2 = sig[a2];
+                                    const Sig w2 = Sp[p];
                                     if (xr < w2) { pick = a2; break; }
                                     xr -= w2;
                                 }
@@ -958,29 +985,28 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             }
         }
 
-        // ---------------- cleanup: sigma of every touched slot, bitmaps ----------------
-        for (uint32_t w0 = tid; w0 < words; w0 += BFS_NT * CK) {
-            uint32_t nb[CK];
-#pragma unroll
-            for (int j = 0; j < CK; ++j) {
-                const uint32_t w = w0 + BFS_NT * j;
-                nb[j] = (w < words) ? __ldcg(N + w) : 0u;
-            }
-#pragma unroll
-            for (int j = 0; j < CK; ++j) {
-                const uint32_t w = w0 + BFS_NT * j;
-                if (w >= words) break;
-                uint32_t bits = V[w] | nb[j];
-                if (bits) {
-                    V[w] = 0u;
-                    if (nb[j]) N[w] = 0u;
-                    while (bits && !stats) {
-                        const uint32_t b = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        sig[w * 32u + b] = (Sig)0;
-                    }
+        // ---------------- cleanup: z's slot counts, the bitmaps ----------------
+        // Every compaction cleared the next-level bitmap, so only the pull's bits
+        // (z's slots) can be left in it; the visited bitmap holds exactly the
+        // states of F[0 .. Fend).
+        if (live && !full && !fsfm) {
+            const uint32_t zs = g.slot_ptr[z], ze = g.slot_ptr[z + 1];   // ze > zs: z has an in-edge
+            for (uint32_t w = (zs >> 5) + tid; w <= ((ze - 1) >> 5); w += BFS_NT) {
+                uint32_t bits = __ldcg(N + w);
+                if (!bits) continue;
+                N[w] = 0u;
+                while (bits) {
+                    const uint32_t b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const uint32_t a = w * 32u + b;
+                    if (a >= zs && a < ze) zsig[a - zs] = (Sig)0;
                 }
             }
+        }
+        if (ws.bits_in_smem || Fend >= words) {
+            for (uint32_t w = tid; w < words; w += BFS_NT) V[w] = 0u;
+        } else {
+            for (uint32_t p = tid; p < Fend; p += BFS_NT) V[F[p] >> 5] = 0u;
         }
         if (stats) {
             for (uint32_t w = tid; w < (n + 31) / 32; w += BFS_NT) VB[w] = 0u;
@@ -994,12 +1020,15 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
 // Host-side launch helpers -------------------------------------------------
 
 // Region of one CTA.  The visited bitmap is in shared memory when
-// bits_in_smem; the next-level bitmap is always in the region.
-size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws) {
+// bits_in_smem; the next-level bitmap is always in the region.  The path
+// counts take one entry per frontier position (at most A states per search)
+// plus one per slot of z (at most zcap, the largest slot count of a vertex).
+size_t bfs_region_bytes(uint32_t n, uint32_t A, uint32_t zcap, bool bits_in_smem, BfsWs* ws) {
     ws->bits_words = (A + 31) / 32;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t o = 0;
     ws->o_sig = o;     o = al(o + (size_t)A * 16);
+    ws->o_zsig = o;    o = al(o + (size_t)std::max<uint32_t>(zcap, 1) * 16);
     ws->o_fc = o;      o = al(o + (size_t)(A + 1) * 16);
     ws->o_f = o;       o = al(o + (size_t)(A + 1) * 4);
     ws->o_ft = o;      o = al(o + (size_t)(A + 1) * 4);

@@ -60,7 +60,7 @@ struct DevGraph {
     uint32_t max_slot_in;   // largest in-edge count of one arrival slot
     const uint32_t* in_uedge;
     uint32_t n_uedge;       // distinct ordered pairs (u, v) with a temporal edge
-    uint32_t pad_;
+    uint32_t max_vslots;    // largest number of arrival slots of one vertex
     const uint32_t* slot_nout;   // per arrival slot (v, t): first index of v's out-row with time > t
 };
 
@@ -619,6 +619,7 @@ struct BfsWs {
     int nt;              // threads per CTA (512 or 1024)
     size_t o_acc;        // ob: per-vertex sums of through counts; RTB: sigma_{s,v}
     size_t o_acc2;       // RTB: per-vertex dependency sums
+    size_t o_zsig;       // path counts of z's slots reached by the pull (sh / sfm endpoints)
 };
 
 // Per-warp scratch of the pfm search kernel.
@@ -644,7 +645,7 @@ struct PfmCtaWs {
     int nt;              // threads per CTA (256 or 512)
 };
 
-size_t bfs_region_bytes(uint32_t n, uint32_t A, bool bits_in_smem, BfsWs* ws);
+size_t bfs_region_bytes(uint32_t n, uint32_t A, uint32_t zcap, bool bits_in_smem, BfsWs* ws);
 size_t bfs_smem_bytes(uint32_t A);
 size_t bfs_static_smem(int nt);
 cudaError_t bfs_blocks_per_sm(int nt, size_t smem, int* out);

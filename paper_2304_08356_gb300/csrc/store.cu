@@ -93,7 +93,8 @@ struct Ctx {
     const uint32_t *u = nullptr, *v = nullptr, *t = nullptr;
     uint64_t m = 0;
     uint32_t n = 0;
-    uint64_t p0[kMaxThreads] = {}, p1[kMaxThreads] = {}, p2[kMaxThreads] = {}, psum[kMaxThreads] = {};
+    uint64_t p0[kMaxThreads] = {}, p1[kMaxThreads] = {}, p2[kMaxThreads] = {}, p3[kMaxThreads] = {},
+             psum[kMaxThreads] = {};
     std::atomic<int> bad{0};
     int rc = MANTRA_OK;
     uint64_t m1 = 0, loops = 0, tmax = 0;   // triples without self loops, self loops, largest time
@@ -417,9 +418,10 @@ int StoreBuilder::build(const uint32_t* u, const uint32_t* v, const uint32_t* t,
             };
             const uint64_t wlo = x == 0 ? 0 : first_w(tot * x / T);
             const uint64_t whi = x == T - 1 ? N : first_w(tot * (x + 1) / T);
-            uint64_t cb = 0, mxs = 0;
+            uint64_t cb = 0, mxs = 0, mxv = 0;
             for (uint64_t w = wlo; w < whi; ++w) {
                 const uint32_t a0 = sl_ptr[w], a1 = sl_ptr[w + 1], q1 = o_ptr[w + 1];
+                mxv = std::max<uint64_t>(mxv, a1 - a0);
                 uint32_t q = o_ptr[w], mx = 0;
                 for (uint32_t a = a0; a < a1; ++a) {
                     const uint32_t ta = sl_t[a];
@@ -434,6 +436,7 @@ int StoreBuilder::build(const uint32_t* u, const uint32_t* v, const uint32_t* t,
             }
             c.p1[x] = cb;
             c.p2[x] = mxs;
+            c.p3[x] = mxv;
         }
 
         // -- underlying edges (App. A): a stable pass by v of the out-CSR order
@@ -463,11 +466,14 @@ int StoreBuilder::build(const uint32_t* u, const uint32_t* v, const uint32_t* t,
     out->n = N; out->m = M; out->A = A;
     out->self_loops = c.loops;
     out->duplicates = c.m1 - M;
-    uint64_t n_ue = 0, cb = 0, mxs = 0;
-    for (unsigned y = 0; y < kMaxThreads; ++y) { n_ue += c.p0[y]; cb += c.p1[y]; mxs = std::max(mxs, c.p2[y]); }
+    uint64_t n_ue = 0, cb = 0, mxs = 0, mxv = 0;
+    for (unsigned y = 0; y < kMaxThreads; ++y) {
+        n_ue += c.p0[y]; cb += c.p1[y]; mxs = std::max(mxs, c.p2[y]); mxv = std::max(mxv, c.p3[y]);
+    }
     out->n_uedge = M > 0 ? (uint32_t)(n_ue + 1) : 0;
     out->cbound = (uint32_t)std::min<uint64_t>(cb, 0xFFFFFFFFull);
     out->max_slot_in = (uint32_t)mxs;
+    out->max_vslots = (uint32_t)mxv;
     const size_t lens[SA_COUNT] = {(size_t)N + 1, M, M, M, (size_t)N + 1, A, A, (size_t)A + 1, M, M, M, M, M,
                                    N, N, M, A};
     for (int k = 0; k < SA_COUNT; ++k) { out->arr[k] = c.a[k]; out->len[k] = lens[k]; }

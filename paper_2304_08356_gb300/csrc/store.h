@@ -21,6 +21,7 @@ enum StoreArr : int {
 // entries, owned by the builder).
 struct StoreHost {
     uint32_t n = 0, m = 0, A = 0, n_uedge = 0, cbound = 0, max_slot_in = 0;
+    uint32_t max_vslots = 0;   // largest number of arrival slots of one vertex
     uint64_t self_loops = 0, duplicates = 0;
     const uint32_t* arr[SA_COUNT] = {};
     size_t len[SA_COUNT] = {};

@@ -2,7 +2,7 @@
 // Reads one graph (uint64 m, uint32 n, then u[m], v[m], t[m] as uint32),
 // builds the store twice with one builder (the second build reuses its
 // buffers) and writes: int32 rc; uint32 n, m, A, n_uedge, cbound,
-// max_slot_in; uint64 self_loops, duplicates; then per array in the order
+// max_slot_in, max_vslots, pad; uint64 self_loops, duplicates; then per array in the order
 // of the device block a uint64 length and the uint32 entries.
 #include "store.h"
 
@@ -28,10 +28,10 @@ int main(int argc, char** argv) {
     FILE* o = std::fopen(argv[2], "wb");
     if (!o) return 2;
     const int32_t rc32 = rc;
-    const uint32_t sc[6] = {H.n, H.m, H.A, H.n_uedge, H.cbound, H.max_slot_in};
+    const uint32_t sc[8] = {H.n, H.m, H.A, H.n_uedge, H.cbound, H.max_slot_in, H.max_vslots, 0u};
     const uint64_t cn[2] = {H.self_loops, H.duplicates};
     std::fwrite(&rc32, 4, 1, o);
-    std::fwrite(sc, 4, 6, o);
+    std::fwrite(sc, 4, 8, o);
     std::fwrite(cn, 8, 2, o);
     for (int k = 0; k < mantra::SA_COUNT; ++k) {
         const uint64_t len = rc == 0 ? H.len[k] : 0;

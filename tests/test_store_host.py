@@ -47,11 +47,11 @@ def run_builder(driver, tmp_path, u, v, t, n, threads=None):
     subprocess.run([driver, src, dst], check=True, env=env)
     raw = open(dst, "rb").read()
     rc = int(np.frombuffer(raw, np.int32, 1, 0)[0])
-    sc = np.frombuffer(raw, np.uint32, 6, 4)
-    cn = np.frombuffer(raw, np.uint64, 2, 28)
+    sc = np.frombuffer(raw, np.uint32, 8, 4)
+    cn = np.frombuffer(raw, np.uint64, 2, 36)
     out = dict(rc=rc, n=int(sc[0]), m=int(sc[1]), A=int(sc[2]), n_uedge=int(sc[3]), cbound=int(sc[4]),
-               max_slot_in=int(sc[5]), self_loops=int(cn[0]), duplicates=int(cn[1]))
-    off = 44
+               max_slot_in=int(sc[5]), max_vslots=int(sc[6]), self_loops=int(cn[0]), duplicates=int(cn[1]))
+    off = 52
     for name in NAMES:
         ln = int(np.frombuffer(raw, np.uint64, 1, off)[0])
         off += 8
@@ -97,7 +97,7 @@ def definition(u, v, t, n):
     per_slot = np.diff(d["slot_in"])
     vmax = np.zeros(n, np.int64)
     np.maximum.at(vmax, slot_v, per_slot)
-    d.update(cbound=int(vmax.sum()), max_slot_in=int(vmax.max(initial=0)))
+    d.update(cbound=int(vmax.sum()), max_slot_in=int(vmax.max(initial=0)), max_vslots=int(cnt_s.max(initial=0)))
     return d
 
 
@@ -105,7 +105,7 @@ def check(driver, tmp_path, u, v, t, n=0, threads=None):
     got = run_builder(driver, tmp_path, u, v, t, n, threads)
     assert got["rc"] == 0
     ref = definition(u, v, t, n)
-    for k in ("n", "m", "A", "n_uedge", "cbound", "max_slot_in", "self_loops", "duplicates"):
+    for k in ("n", "m", "A", "n_uedge", "cbound", "max_slot_in", "max_vslots", "self_loops", "duplicates"):
         assert got[k] == ref[k], k
     for name in NAMES:
         assert np.array_equal(got[name].astype(np.int64), np.asarray(ref[name], np.int64)), name
