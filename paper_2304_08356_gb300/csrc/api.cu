@@ -183,6 +183,7 @@ struct Engine {
     // search workspaces
     char* bfs_mem = nullptr; BfsWs bws{}; int bfs_grid = 0; size_t bfs_smem = 0; uint32_t bfs_n = 0, bfs_A = 0, bfs_z = 0;
     int bfs_grid_big = 0;      // resident 1024-thread CTAs (the regions of the first ones)
+    int bfs_grid_small = 0;    // resident 256-thread CTAs
     int tick_bfs_nt = 512;     // sh/sfm CTA size of the current tick
     bool tick_frac = false;    // the tick has an ob or RTB problem on the sh/sfm kernel
     char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; uint32_t pfm_n = 0, pfm_lcap = 0; uint64_t pfm_warps = 0;
@@ -196,8 +197,8 @@ struct Engine {
     int red_grid = 0;
     // captured ticks, one per pfm kernel (lane / CTA per sample)
     // captured ticks, by (pfm kernel, sh/sfm CTA size)
-    cudaGraphExec_t gexec[8] = {};
-    bool graph_ok[8] = {};
+    cudaGraphExec_t gexec[12] = {};
+    bool graph_ok[12] = {};
     bool use_graph = true;
     DevPool pool;
 
@@ -224,7 +225,7 @@ struct Engine {
     }
 
     void invalidate_graph() {
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < 12; ++k) {
             if (gexec[k]) cudaGraphExecDestroy(gexec[k]);
             gexec[k] = nullptr;
             graph_ok[k] = false;
@@ -290,11 +291,13 @@ struct Engine {
         }
         const size_t region = bfs_region_bytes(n, A, zc, in_smem, &bws);
         CU(bfs_configure(in_smem ? smem : 0));
-        int per_sm = 0, per_sm_big = 0;
+        int per_sm = 0, per_sm_big = 0, per_sm_small = 0;
         CU(bfs_blocks_per_sm(512, in_smem ? smem : 0, &per_sm));
         CU(bfs_blocks_per_sm(1024, in_smem ? smem : 0, &per_sm_big));
+        CU(bfs_blocks_per_sm(256, in_smem ? smem : 0, &per_sm_small));
         const size_t budget = free_device_bytes() / 3;
-        int grid = num_sms * std::max(per_sm, 1);
+        // regions for the largest resident grid of the three shapes
+        int grid = num_sms * std::max(std::max(per_sm, 1), std::max(per_sm_small, 1));
         // MANTRA_BFS_GRID caps the resident CTAs
         if (const char* env = std::getenv("MANTRA_BFS_GRID")) grid = std::max(1, std::min(grid, std::atoi(env)));
         if ((size_t)grid * region > budget) grid = (int)std::max<size_t>(1, budget / region);
@@ -302,8 +305,9 @@ struct Engine {
         CU(cudaMemsetAsync(bfs_mem, 0, (size_t)grid * region, sa));
         bws.base = bfs_mem;
         bws.stride = region;
-        bfs_grid = grid;
+        bfs_grid = std::min(grid, num_sms * std::max(per_sm, 1));
         bfs_grid_big = std::min(grid, num_sms * std::max(per_sm_big, 1));
+        bfs_grid_small = std::min(grid, num_sms * std::max(per_sm_small, 1));
         bfs_smem = in_smem ? smem : 0;
         bfs_n = n; bfs_A = A; bfs_z = zc;
         invalidate_graph();
@@ -389,7 +393,8 @@ struct Engine {
             BfsWs w = bws;
             w.nt = tick_bfs_nt;
             CU(launch_bfs((const Task*)(tab_d + o_tb), (const uint64_t*)(tab_d + o_ub), hdr + 0, work + 0, w,
-                          tick_bfs_nt == 1024 ? bfs_grid_big : bfs_grid, bfs_smem, wide, tick_frac, sa));
+                          tick_bfs_nt == 1024 ? bfs_grid_big : (tick_bfs_nt == 256 ? bfs_grid_small : bfs_grid),
+                          bfs_smem, wide, tick_frac, sa));
             CU(cudaEventRecord(e_b1, sa));
         }
         if (tick_cta && !wide && pc_mem) {
@@ -414,7 +419,7 @@ struct Engine {
     int launch_tick(bool wide) {
         last_tick_graph = false;
         if (wide || !use_graph) return enqueue(wide);
-        const int gk = (tick_cta ? 1 : 0) + (tick_bfs_nt == 1024 ? 2 : 0) + (tick_frac ? 4 : 0);
+        const int gk = (tick_cta ? 1 : 0) + (tick_bfs_nt == 1024 ? 2 : (tick_bfs_nt == 256 ? 4 : 0)) + (tick_frac ? 6 : 0);
         if (!graph_ok[gk]) {
             cudaGraph_t graph = nullptr;
             CU(cudaStreamBeginCapture(sa, cudaStreamCaptureModeThreadLocal));
@@ -528,7 +533,10 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     // 42.5 vs 40.4 ms for 26,702); MANTRA_BFS_NT=512|1024 forces one
     {
         int nt = bsamples <= 2ull * (uint64_t)E.bfs_grid_big ? 1024 : 512;
-        if (const char* env = std::getenv("MANTRA_BFS_NT")) nt = std::atoi(env) == 1024 ? 1024 : 512;
+        if (const char* env = std::getenv("MANTRA_BFS_NT")) {
+            const int v = std::atoi(env);
+            nt = v == 1024 ? 1024 : (v == 256 ? 256 : 512);
+        }
         E.tick_bfs_nt = nt;
     }
     // host tables

@@ -38,6 +38,34 @@ namespace mantra {
 constexpr int IPT = 2;            // frontier states per thread in a segmented-scan tile
 constexpr int WALK_K = 2;         // edge windows with loads in flight per warp in the push
 constexpr int CK = 8;             // bitmap words in flight per lane in the compaction and cleanup scans
+constexpr int CB = 4;             // new states per thread with loads in flight in the count pass
+constexpr uint32_t SUMW = 512;    // words of the next-level bitmap's summary (one bit per 2^sumshift bitmap words)
+
+// For each j: the first index in [lo[j], hi[j]) whose value is >= key[j]
+// (hi[j] if none), left in lo[j]; the K searches advance together so their
+// loads overlap.  Plain loads: the array is written by this kernel.
+template <int K>
+__device__ __forceinline__ void lower_bounds_rw(const uint32_t* a, uint32_t (&lo)[K], uint32_t (&hi)[K],
+                                                const uint32_t (&key)[K]) {
+    for (;;) {
+        bool any = false;
+        uint32_t mid[K], val[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const bool act = lo[j] < hi[j];
+            any |= act;
+            mid[j] = lo[j] + ((hi[j] - lo[j]) >> 1);
+            val[j] = act ? a[mid[j]] : 0u;
+        }
+        if (!any) break;
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (lo[j] < hi[j]) {
+                if (val[j] < key[j]) lo[j] = mid[j] + 1u;
+                else hi[j] = mid[j];
+            }
+    }
+}
 
 // ob update of one sample (Sec. 4.1), all threads of the CTA: continuation
 // counts dl (the number of optimal ways from a state to z's endpoints) per
@@ -384,10 +412,15 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
     __shared__ uint32_t sh_stamp, sh_wrap;
     __shared__ uint32_t sm_Ft[WIDE ? 1 : FCAP];   // level times and running sums (64-bit counts, L <= FCAP)
     __shared__ u64 sm_Fc[WIDE ? 1 : FCAP];
+    // summary of the next-level bitmap: bit i is set when bitmap words
+    // [i << sumshift, (i + 1) << sumshift) may hold a bit; the push marks it, the
+    // compaction loads only marked words and clears it
+    __shared__ uint32_t sm_nsum[SUMW];
 
     if (ws.bits_in_smem) {
         for (uint32_t w = tid; w < ws.bits_words; w += BFS_NT) V[w] = 0u;
     }
+    for (uint32_t w = tid; w < SUMW; w += BFS_NT) sm_nsum[w] = 0u;
     if (tid == 0) sh_stamp = *stamp_p;
     // Next level stamp (segmap entries of older levels never match it) and the
     // level's scan scratch; on wrap-around the map is cleared once.
@@ -443,6 +476,8 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
         const Job& job = sh_task.job;
         const uint32_t n = g.n;
         const uint32_t words = (g.A + 31) >> 5;
+        uint32_t sumshift = 0;             // smallest shift with every bitmap word covered by the summary
+        while ((((words + (1u << sumshift) - 1u) >> sumshift) + 31u) / 32u > SUMW) ++sumshift;
         if (job.ctr != flush_ctr) { flush(); flush_ctr = job.ctr; }
         const uint64_t q = sh_q;
         const uint64_t i = job.idx_list ? job.idx_list[q] : job.i0 + q;
@@ -644,6 +679,8 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                     ++my_escan;
                     if (!((V[a >> 5] >> (a & 31)) & 1u)) {
                         atomicOr(N + (a >> 5), 1u << (a & 31));
+                        const uint32_t sb = (a >> 5) >> sumshift, m = 1u << (sb & 31);
+                        if (!(sm_nsum[sb >> 5] & m)) atomicOr(sm_nsum + (sb >> 5), m);
                         ++my_eadd;
                     }
                 });
@@ -651,82 +688,76 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             }
 
             // ---- compact the next-level bitmap into F_{k+1} ----
-            const uint32_t per_w = (((words + BFS_NW - 1) / BFS_NW) + 31u) & ~31u;
-            const uint32_t w_lo = min((uint32_t)wid * per_w, words), w_hi = min(w_lo + per_w, words);
-            uint32_t cnt = 0;
-            // CK words per lane in flight: the bitmap is read from L2, so the
-            // loads of a batch are issued before any is used
-            for (uint32_t w0 = w_lo + lane; w0 < w_hi; w0 += 32u * CK) {
-                uint32_t x[CK];
+            // Thread t owns the summary words [t q, (t + 1) q); only the bitmap
+            // words that their set bits cover are loaded (CK loads in flight),
+            // once to count and once to write.  Thread order is slot order, so
+            // a block scan of the counts gives every thread its output offset.
+            const uint32_t nsw = (((words + (1u << sumshift) - 1u) >> sumshift) + 31u) >> 5;
+            const uint32_t q = (nsw + BFS_NT - 1) / BFS_NT;
+            const uint32_t s_lo = min((uint32_t)tid * q, nsw), s_hi = min(s_lo + q, nsw);
+            // body(w, N[w]) for every bitmap word w of this thread's marked groups, in order
+            auto for_marked = [&](auto&& body) {
+                for (uint32_t sw = s_lo; sw < s_hi; ++sw) {
+                    uint32_t m = sm_nsum[sw];
+                    if (sumshift == 0) {            // one bitmap word per summary bit
+                        while (m) {
+                            uint32_t w[CK], x[CK];
 #pragma unroll
-                for (int j = 0; j < CK; ++j) {
-                    const uint32_t w = w0 + 32u * j;
-                    x[j] = (w < w_hi) ? __ldcg(N + w) : 0u;
-                }
+                            for (int j = 0; j < CK; ++j) {
+                                w[j] = NONE;
+                                if (m) { w[j] = (sw << 5) + (uint32_t)(__ffs(m) - 1); m &= m - 1; }
+                            }
 #pragma unroll
-                for (int j = 0; j < CK; ++j) cnt += __popc(x[j]);
-            }
+                            for (int j = 0; j < CK; ++j) x[j] = (w[j] != NONE) ? __ldcg(N + w[j]) : 0u;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
-            if (lane == 0) sm_wcnt[wid] = cnt;
-            __syncthreads();
-            if (wid == 0) {
-                uint32_t x = (lane < BFS_NW) ? sm_wcnt[lane] : 0u, incl = x;
+                            for (int j = 0; j < CK; ++j) if (w[j] != NONE) body(w[j], x[j]);
+                        }
+                    } else {                        // 2^sumshift consecutive bitmap words per summary bit
+                        while (m) {
+                            const uint32_t g0 = ((sw << 5) + (uint32_t)(__ffs(m) - 1)) << sumshift;
+                            m &= m - 1;
+                            const uint32_t g1 = min(g0 + (1u << sumshift), words);
+                            for (uint32_t w0 = g0; w0 < g1; w0 += CK) {
+                                uint32_t x[CK];
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                if (lane < BFS_NW) sm_wcnt[lane] = incl - x;
-                if (lane == 31) sm_scan[0] = incl;
-            }
-            __syncthreads();
-            const uint32_t Lnext = sm_scan[0];
-            const uint32_t fbase = lev[k + 1];
-            uint32_t off = fbase + sm_wcnt[wid];
-            uint32_t newv = 0;
-            const uint32_t* const g_slot_v2 = g.slot_v;
-            for (uint32_t wb = w_lo; wb < w_hi; wb += 32u * CK) {
-                uint32_t xb[CK];
+                                for (int j = 0; j < CK; ++j) x[j] = (w0 + j < g1) ? __ldcg(N + w0 + j) : 0u;
 #pragma unroll
-                for (int jj = 0; jj < CK; ++jj) {
-                    const uint32_t w = wb + 32u * jj + lane;
-                    xb[jj] = (w < w_hi) ? __ldcg(N + w) : 0u;
-                }
-#pragma unroll
-                for (int jj = 0; jj < CK; ++jj) {
-                    const uint32_t w = wb + 32u * jj + lane;
-                    uint32_t bits = xb[jj];
-                    if (__ballot_sync(0xFFFFFFFFu, bits != 0u) == 0u) continue;   // nothing in these 32 words
-                    if (bits) { V[w] |= bits; N[w] = 0u; }
-                    const uint32_t c = __popc(bits);
-                    uint32_t incl = c;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    uint32_t pos = off + incl - c;
-                    while (bits) {
-                        const uint32_t b = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const uint32_t a = w * 32u + b;
-                        F[pos++] = a;
-                        if (fsfm && a >= zlo && a < zhi) atomicMin(&sh_zmin, a);
-                        if (stats && job.opt != 3) {
-                            const uint32_t v = g_slot_v2[a];
-                            if (v != s) {
-                                const uint32_t old = atomicOr(VB + (v >> 5), 1u << (v & 31));
-                                if (!(old & (1u << (v & 31)))) {
-                                    ++newv;
-                                    if (job.clos) atomicAdd(job.clos + v, recip32(k + 1));
-                                }
+                                for (int j = 0; j < CK; ++j) if (w0 + j < g1) body(w0 + j, x[j]);
                             }
                         }
                     }
-                    off += __shfl_sync(0xFFFFFFFFu, incl, 31);
                 }
-            }
+            };
+            uint32_t cnt = 0;
+            for_marked([&](uint32_t, uint32_t x) { cnt += __popc(x); });
+            uint32_t Lnext;
+            const uint32_t fbase = lev[k + 1];
+            uint32_t off = fbase + block_exclusive_scan<BFS_NT>(cnt, &Lnext, sm_scan);
+            uint32_t newv = 0;
+            const uint32_t* const g_slot_v2 = g.slot_v;
+            for_marked([&](uint32_t w, uint32_t bits) {
+                if (!bits) return;
+                V[w] |= bits;
+                N[w] = 0u;
+                while (bits) {
+                    const uint32_t b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const uint32_t a = w * 32u + b;
+                    F[off++] = a;
+                    if (fsfm && a >= zlo && a < zhi) atomicMin(&sh_zmin, a);
+                    if (stats && job.opt != 3) {
+                        const uint32_t v = g_slot_v2[a];
+                        if (v != s) {
+                            const uint32_t old = atomicOr(VB + (v >> 5), 1u << (v & 31));
+                            if (!(old & (1u << (v & 31)))) {
+                                ++newv;
+                                if (job.clos) atomicAdd(job.clos + v, recip32(k + 1));
+                            }
+                        }
+                    }
+                }
+            });
+            for (uint32_t sw = s_lo; sw < s_hi; ++sw) sm_nsum[sw] = 0u;   // read again by the next push, after barriers
             if (stats) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) newv += __shfl_xor_sync(0xFFFFFFFFu, newv, o);
@@ -750,30 +781,73 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 const uint32_t* const c_slot_t = g.slot_t;
                 const uint32_t* const c_slot_in = g.slot_in;
                 const uint32_t* const c_in_u = g.in_u;
-                bool bad = false;
-                for (uint32_t p = fbase + tid; p < fbase + Lnext; p += BFS_NT) {
-                    const uint32_t a = F[p];
-                    const uint32_t ta = c_slot_t[a];
-                    const uint32_t e1 = c_slot_in[a + 1];
-                    Sig sum = (Sig)0;
-                    for (uint32_t e = c_slot_in[a]; e < e1; ++e) {
-                        const uint32_t w = c_in_u[e];
-                        const u64 mw = __ldcg(segmap + w);
-                        if ((uint32_t)(mw >> 32) != stamp) continue;        // w is not on level k
-                        uint32_t idx = 0;                                    // level 0: the source, count 1
-                        if (k > 0) {
-                            const uint32_t lo = (uint32_t)mw;
-                            const uint32_t fb = seg_b[lo], fe = (lo + 1 < G) ? seg_b[lo + 1] : L;
-                            const uint32_t c = lower_bound_u32(FtL, fb, fe, ta);   // first Ft >= ta
-                            if (c == fb) continue;                                // none earlier than ta
-                            idx = c - 1;
-                        }
-                        const Sig x = FcL[idx];
-                        const Sig s2 = sum + x;
-                        bad |= s2 < sum;
-                        sum = s2;
+                // the count one in-edge (tail w, head time ta, w's map entry mw) adds
+                auto term = [&](uint32_t ta, u64 mw, Sig* x) -> bool {
+                    if ((uint32_t)(mw >> 32) != stamp) return false;         // w is not on level k
+                    uint32_t idx = 0;                                        // level 0: the source, count 1
+                    if (k > 0) {
+                        const uint32_t lo = (uint32_t)mw;
+                        const uint32_t fb = seg_b[lo], fe = (lo + 1 < G) ? seg_b[lo + 1] : L;
+                        const uint32_t c = lower_bound_u32(FtL, fb, fe, ta);  // first Ft >= ta
+                        if (c == fb) return false;                           // none earlier than ta
+                        idx = c - 1;
                     }
-                    Fs[p] = sum;
+                    *x = FcL[idx];
+                    return true;
+                };
+                const uint32_t fend = fbase + Lnext;
+                bool bad = false;
+                // CB states per thread, each stage's loads issued for all of them
+                // before any is used; a new state has at least one in-edge
+                for (uint32_t p0 = fbase + tid; p0 < fend; p0 += BFS_NT * CB) {
+                    uint32_t ta[CB], e0[CB], e1[CB], fb[CB], lo[CB], hi[CB];
+                    u64 mw[CB];
+                    // the state's slot, its time and in-edge range, the first
+                    // in-edge's tail and its map entry
+#pragma unroll
+                    for (int j = 0; j < CB; ++j) {
+                        const uint32_t p = p0 + (uint32_t)j * BFS_NT;
+                        lo[j] = p < fend ? F[p] : NONE;
+                    }
+#pragma unroll
+                    for (int j = 0; j < CB; ++j) {
+                        ta[j] = e0[j] = e1[j] = 0u;
+                        if (lo[j] != NONE) { ta[j] = c_slot_t[lo[j]]; e0[j] = c_slot_in[lo[j]]; e1[j] = c_slot_in[lo[j] + 1]; }
+                    }
+#pragma unroll
+                    for (int j = 0; j < CB; ++j) hi[j] = (e1[j] > e0[j]) ? c_in_u[e0[j]] : 0u;
+#pragma unroll
+                    for (int j = 0; j < CB; ++j) mw[j] = (e1[j] > e0[j]) ? __ldcg(segmap + hi[j]) : 0ull;
+                    // the tail's segment on level k, then the first of its times >= ta
+#pragma unroll
+                    for (int j = 0; j < CB; ++j) {
+                        const bool on = e1[j] > e0[j] && (uint32_t)(mw[j] >> 32) == stamp;
+                        fb[j] = lo[j] = hi[j] = 0u;
+                        if (on) {
+                            if (k > 0) {
+                                const uint32_t sg = (uint32_t)mw[j];
+                                fb[j] = lo[j] = seg_b[sg];
+                                hi[j] = (sg + 1 < G) ? seg_b[sg + 1] : L;
+                            } else {
+                                hi[j] = 1u;               // level 0: the source, count 1 (FcL[0])
+                            }
+                        }
+                    }
+                    if (k > 0) lower_bounds_rw<CB>(FtL, lo, hi, ta);
+#pragma unroll
+                    for (int j = 0; j < CB; ++j) {
+                        if (e1[j] <= e0[j]) continue;
+                        Sig sum = (Sig)0, x;
+                        if (k == 0) { if (hi[j]) sum = FcL[0]; }
+                        else if (lo[j] > fb[j]) sum = FcL[lo[j] - 1];
+                        for (uint32_t e = e0[j] + 1; e < e1[j]; ++e) {
+                            if (!term(ta[j], __ldcg(segmap + c_in_u[e]), &x)) continue;
+                            const Sig s2 = sum + x;
+                            bad |= s2 < sum;
+                            sum = s2;
+                        }
+                        Fs[p0 + (uint32_t)j * BFS_NT] = sum;
+                    }
                 }
                 if (bad) sh_ovf = 1;
                 __syncthreads();
@@ -1057,10 +1131,13 @@ size_t bfs_smem_bytes(uint32_t A) { return (size_t)((A + 31) / 32) * 4; }
 size_t bfs_static_smem(int nt) {
     cudaFuncAttributes a{}, b{}, c{};
     const cudaError_t e1 = nt == 1024 ? cudaFuncGetAttributes(&a, k_bfs<false, 1024, false>)
+                         : nt == 256  ? cudaFuncGetAttributes(&a, k_bfs<false, 256, false>)
                                       : cudaFuncGetAttributes(&a, k_bfs<false, 512, false>);
     const cudaError_t e2 = nt == 1024 ? cudaFuncGetAttributes(&b, k_bfs<true, 1024, true>)
+                         : nt == 256  ? cudaFuncGetAttributes(&b, k_bfs<true, 256, true>)
                                       : cudaFuncGetAttributes(&b, k_bfs<true, 512, true>);
     const cudaError_t e3 = nt == 1024 ? cudaFuncGetAttributes(&c, k_bfs<false, 1024, true>)
+                         : nt == 256  ? cudaFuncGetAttributes(&c, k_bfs<false, 256, true>)
                                       : cudaFuncGetAttributes(&c, k_bfs<false, 512, true>);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return 96 * 1024;
     return std::max(std::max(a.sharedSizeBytes, b.sharedSizeBytes), c.sharedSizeBytes);
@@ -1078,9 +1155,11 @@ cudaError_t bfs_configure(size_t smem) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
     if (smem <= configured[dev]) return cudaSuccess;
-    const void* ks[6] = {(const void*)k_bfs<false, 512, false>, (const void*)k_bfs<false, 512, true>,
+    const void* ks[9] = {(const void*)k_bfs<false, 512, false>, (const void*)k_bfs<false, 512, true>,
                          (const void*)k_bfs<true, 512, true>, (const void*)k_bfs<false, 1024, false>,
-                         (const void*)k_bfs<false, 1024, true>, (const void*)k_bfs<true, 1024, true>};
+                         (const void*)k_bfs<false, 1024, true>, (const void*)k_bfs<true, 1024, true>,
+                         (const void*)k_bfs<false, 256, false>, (const void*)k_bfs<false, 256, true>,
+                         (const void*)k_bfs<true, 256, true>};
     for (const void* k : ks) {
         const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -1090,8 +1169,9 @@ cudaError_t bfs_configure(size_t smem) {
 }
 
 cudaError_t bfs_blocks_per_sm(int nt, size_t smem, int* out) {
-    return nt == 1024 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bfs<false, 1024, false>, 1024, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bfs<false, 512, false>, 512, smem);
+    if (nt == 1024) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bfs<false, 1024, false>, 1024, smem);
+    if (nt == 256) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bfs<false, 256, false>, 256, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bfs<false, 512, false>, 512, smem);
 }
 
 cudaError_t launch_bfs(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
@@ -1101,6 +1181,10 @@ cudaError_t launch_bfs(const Task* tasks, const uint64_t* unit_start, const uint
         if (wide) k_bfs<true, 1024, true><<<grid, 1024, smem, st>>>(tasks, unit_start, ntasks, work, ws);
         else if (frac) k_bfs<false, 1024, true><<<grid, 1024, smem, st>>>(tasks, unit_start, ntasks, work, ws);
         else k_bfs<false, 1024, false><<<grid, 1024, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+    } else if (ws.nt == 256) {
+        if (wide) k_bfs<true, 256, true><<<grid, 256, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else if (frac) k_bfs<false, 256, true><<<grid, 256, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else k_bfs<false, 256, false><<<grid, 256, smem, st>>>(tasks, unit_start, ntasks, work, ws);
     } else {
         if (wide) k_bfs<true, 512, true><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
         else if (frac) k_bfs<false, 512, true><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
