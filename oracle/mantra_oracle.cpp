@@ -49,6 +49,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <set>
 #include <tuple>
 #include <utility>
@@ -166,10 +167,31 @@ struct Graph {
     uint64_t duplicates = 0;
     // Edge betweenness (App. A): temporal edge (u,v,t) -> id = its rank in
     // (v,t,u) order; underlying edge (u,v) -> id = its rank in (v,u) order.
-    std::map<std::tuple<uint32_t, uint32_t, uint32_t>, uint32_t> tid;   // key (v,t,u)
-    std::map<std::pair<uint32_t, uint32_t>, uint32_t> uid;              // key (v,u)
-    std::vector<uint32_t> t2u;                                          // temporal id -> underlying id
+    // Built on first use (edge_ids), once, by whichever thread needs them.
+    mutable std::once_flag ids_once;
+    mutable std::map<std::tuple<uint32_t, uint32_t, uint32_t>, uint32_t> tid;   // key (v,t,u)
+    mutable std::map<std::pair<uint32_t, uint32_t>, uint32_t> uid;              // key (v,u)
+    mutable std::vector<uint32_t> t2u;                                          // temporal id -> underlying id
 };
+
+// The edge ids of the Graph (ranks of the deduplicated triples in (v,t,u)
+// order, of the distinct pairs in (v,u) order).
+const Graph& edge_ids(const Graph& G) {
+    std::call_once(G.ids_once, [&G]() {
+        for (const auto& e : G.edges) {                                  // (u,v,t)
+            G.tid[std::make_tuple(std::get<1>(e), std::get<2>(e), std::get<0>(e))] = 0;
+            G.uid[std::make_pair(std::get<1>(e), std::get<0>(e))] = 0;
+        }
+        uint32_t r = 0;
+        for (auto& kv : G.tid) kv.second = r++;
+        r = 0;
+        for (auto& kv : G.uid) kv.second = r++;
+        G.t2u.assign(G.tid.size(), 0);
+        for (const auto& kv : G.tid)
+            G.t2u[kv.second] = G.uid.at(std::make_pair(std::get<0>(kv.first), std::get<2>(kv.first)));
+    });
+    return G;
+}
 
 const int64_t NEG_INF = -1;                 // the source appearance (s, -inf)
 const int64_t POS_INF = INT64_MAX;
@@ -512,9 +534,10 @@ struct Sample {
 };
 
 // One sample of Algorithm 1's Update step: draw (s,z), count optimal paths,
-// draw x uniform in [0, sigma_sz), unrank the path.
+// draw x uniform in [0, sigma_sz), unrank the path (and, with want_edges, list
+// the temporal edge ids of its edges).
 int one_sample(const Graph& G, int opt, uint64_t seed, uint64_t i, uint32_t dom_pair, uint32_t dom_path,
-               Sample* out) {
+               Sample* out, bool want_edges = false) {
     if (!draw_pair(G.n, seed, i, dom_pair, &out->s, &out->z)) return E_RNG;
     Search R;
     int st = count_paths(G, opt, out->s, out->z, &R, &out->sigma);
@@ -528,8 +551,9 @@ int one_sample(const Graph& G, int opt, uint64_t seed, uint64_t i, uint32_t dom_
     int st2 = unrank_path(G, opt, out->s, out->z, R, x, &out->path, &times);
     if (st2 != OK) return st2;
     out->edges.clear();
-    for (size_t k = 0; k + 1 < out->path.size(); ++k)          // edge (path[k], path[k+1], times[k+1])
-        out->edges.push_back(G.tid.at(std::make_tuple(out->path[k + 1], (uint32_t)times[k + 1], out->path[k])));
+    if (want_edges)
+        for (size_t k = 0; k + 1 < out->path.size(); ++k)      // edge (path[k], path[k+1], times[k+1])
+            out->edges.push_back(edge_ids(G).tid.at(std::make_tuple(out->path[k + 1], (uint32_t)times[k + 1], out->path[k])));
     return OK;
 }
 
@@ -810,11 +834,17 @@ void* orc_graph_new(const uint32_t* u, const uint32_t* v, const uint32_t* t, uin
     uint32_t nn = n;
     if (nn == 0) for (uint64_t e = 0; e < m; ++e) nn = std::max(nn, std::max(u[e], v[e]) + 1);
     G->n = nn;
-    std::set<std::tuple<uint32_t, uint32_t, uint32_t>> seen;       // keyed (t,u,v)
+    // the distinct (t,u,v) triples without self loops, ascending
+    std::vector<std::tuple<uint32_t, uint32_t, uint32_t>> seen;
+    seen.reserve(m);
     for (uint64_t e = 0; e < m; ++e) {
         if (u[e] == v[e]) { G->self_loops++; continue; }
-        if (!seen.insert(std::make_tuple(t[e], u[e], v[e])).second) G->duplicates++;
+        seen.push_back(std::make_tuple(t[e], u[e], v[e]));
     }
+    std::sort(seen.begin(), seen.end());
+    const size_t all = seen.size();
+    seen.erase(std::unique(seen.begin(), seen.end()), seen.end());
+    G->duplicates = all - seen.size();
     G->out.assign(nn, {});
     G->in.assign(nn, {});
     for (const auto& k : seen) {                                  // ascending (t,u,v)
@@ -823,17 +853,6 @@ void* orc_graph_new(const uint32_t* u, const uint32_t* v, const uint32_t* t, uin
         G->out[uu].push_back(std::make_pair(vv, tt));             // so out[u] ascends in t
         G->in[vv].push_back(std::make_pair(uu, tt));
     }
-    for (const auto& k : seen) {
-        G->tid[std::make_tuple(std::get<2>(k), std::get<0>(k), std::get<1>(k))] = 0;
-        G->uid[std::make_pair(std::get<2>(k), std::get<1>(k))] = 0;
-    }
-    uint32_t r = 0;
-    for (auto& kv : G->tid) kv.second = r++;
-    r = 0;
-    for (auto& kv : G->uid) kv.second = r++;
-    G->t2u.assign(G->tid.size(), 0);
-    for (const auto& kv : G->tid)
-        G->t2u[kv.second] = G->uid.at(std::make_pair(std::get<0>(kv.first), std::get<2>(kv.first)));
     return G;
 }
 
@@ -842,9 +861,12 @@ void orc_graph_free(void* g) { delete (Graph*)g; }
 void orc_graph_info(const void* g, uint32_t* n, uint64_t* m, uint64_t* slots, uint64_t* self_loops,
                     uint64_t* duplicates) {
     const Graph* G = (const Graph*)g;
-    std::set<std::pair<uint32_t, uint32_t>> apps;
-    for (const auto& e : G->edges) apps.insert(std::make_pair(std::get<1>(e), std::get<2>(e)));
-    *n = G->n; *m = G->edges.size(); *slots = apps.size();
+    std::vector<std::pair<uint32_t, uint32_t>> apps;             // arrival appearances (v,t)
+    apps.reserve(G->edges.size());
+    for (const auto& e : G->edges) apps.push_back(std::make_pair(std::get<1>(e), std::get<2>(e)));
+    std::sort(apps.begin(), apps.end());
+    *n = G->n; *m = G->edges.size();
+    *slots = std::unique(apps.begin(), apps.end()) - apps.begin();
     *self_loops = G->self_loops; *duplicates = G->duplicates;
 }
 
@@ -901,7 +923,7 @@ int orc_samples(const void* g, int opt, uint64_t seed, uint64_t i0, uint64_t cou
     const Graph* G = (const Graph*)g;
     for (uint64_t q = 0; q < count; ++q) {
         Sample S;
-        int st = one_sample(*G, opt, seed, i0 + q, dom_pair, dom_path, &S);
+        int st = one_sample(*G, opt, seed, i0 + q, dom_pair, dom_path, &S, path_edges != nullptr);
         if (st != OK) return st;
         s[q] = S.s; z[q] = S.z;
         sig_lo[q] = (uint64_t)S.sigma; sig_hi[q] = (uint64_t)(S.sigma >> 64);
@@ -932,7 +954,7 @@ int orc_work(const void* g, int opt, uint64_t seed, uint64_t i0, uint64_t count,
 // Edge ids: for temporal edge id e, its (u, v, t) and its underlying edge id;
 // *n_underlying = the number of underlying edges.
 void orc_edge_ids(const void* g, uint32_t* u, uint32_t* v, uint32_t* t, uint32_t* uedge, uint32_t* n_underlying) {
-    const Graph* G = (const Graph*)g;
+    const Graph* G = &edge_ids(*(const Graph*)g);
     for (const auto& kv : G->tid) {
         const uint32_t e = kv.second;
         v[e] = std::get<0>(kv.first); t[e] = std::get<1>(kv.first); u[e] = std::get<2>(kv.first);
@@ -1014,6 +1036,7 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
     // ob sums are in units of 2^-32; |N_R| <= c r 2^32 must fit int64
     const double scale = ob ? 4294967296.0 : 1.0;
     if (ob && (double)fixed_r * (double)c >= 2147483648.0) return E_INVAL;
+    if (target != 0) edge_ids(*G);
     const uint32_t F = target == 0 ? n : (uint32_t)(target == 1 ? G->uid.size() : G->tid.size());
     std::vector<uint64_t> hits(F, 0);
     std::vector<uint64_t> wsq(F, 0);                                        // ob: sum_i f_x(s_i)^2 (2^-32 units)
@@ -1067,7 +1090,7 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
                 continue;
             }
             Sample sm;
-            int st = one_sample(*G, opt, seed, i, D_PAIR, D_PATH, &sm);
+            int st = one_sample(*G, opt, seed, i, D_PAIR, D_PATH, &sm, target != 0);
             if (st != OK) return st;
             count_work(sm.work);
             items_of(sm, &it);
@@ -1131,7 +1154,7 @@ int orc_estimate(const void* g, int opt, double eps, double delta, uint64_t seed
                 continue;
             }
             Sample sm;
-            int st = one_sample(*G, opt, seed, i, D_BOOT_PAIR, D_BOOT_PATH, &sm);
+            int st = one_sample(*G, opt, seed, i, D_BOOT_PAIR, D_BOOT_PATH, &sm, target != 0);
             if (st != OK) return st;
             count_work(sm.work);
             items_of(sm, &it);

@@ -182,6 +182,7 @@ struct Engine {
     bool last_tick_graph = false;
     // search workspaces
     char* bfs_mem = nullptr; BfsWs bws{}; int bfs_grid = 0; size_t bfs_smem = 0; uint32_t bfs_n = 0, bfs_A = 0, bfs_z = 0;
+    bool bfs_dl = false;       // the regions carry the ob / RTB scratch
     int bfs_grid_big = 0;      // resident 1024-thread CTAs (the regions of the first ones)
     int bfs_grid_small = 0;    // resident 256-thread CTAs
     int tick_bfs_nt = 512;     // sh/sfm CTA size of the current tick
@@ -262,12 +263,14 @@ struct Engine {
         return MANTRA_OK;
     }
 
-    // sh/sfm: one region per CTA, one CTA per SM, at most a third of free memory.
-    int ensure_bfs(uint32_t n, uint32_t A, uint32_t zc) {
-        if (bfs_mem && n <= bfs_n && A <= bfs_A && zc <= bfs_z) return MANTRA_OK;
+    // sh/sfm: one region per resident CTA (the largest grid of the CTA shapes),
+    // at most 60 % of free memory.
+    int ensure_bfs(uint32_t n, uint32_t A, uint32_t zc, bool dl) {
+        if (bfs_mem && n <= bfs_n && A <= bfs_A && zc <= bfs_z && (!dl || bfs_dl)) return MANTRA_OK;
         n = std::max(n, bfs_n);
         A = std::max(A, bfs_A);
         zc = std::max(zc, bfs_z);
+        dl = dl || bfs_dl;
         if (bfs_mem) { cudaStreamSynchronize(sa); cudaFree(bfs_mem); bfs_mem = nullptr; }
         // regions for the 512-thread shape (two CTAs per SM); the 1024-thread
         // shape (one per SM) uses the first of them
@@ -289,13 +292,16 @@ struct Engine {
             if (env[0] == '0') in_smem = false;
             else if (env[0] == '1') in_smem = smem + std::max(bfs_static_smem(512), bfs_static_smem(1024)) + 1024 <= smem_optin;
         }
-        const size_t region = bfs_region_bytes(n, A, zc, in_smem, &bws);
+        const size_t region = bfs_region_bytes(n, A, zc, in_smem, dl, &bws);
         CU(bfs_configure(in_smem ? smem : 0));
         int per_sm = 0, per_sm_big = 0, per_sm_small = 0;
         CU(bfs_blocks_per_sm(512, in_smem ? smem : 0, &per_sm));
         CU(bfs_blocks_per_sm(1024, in_smem ? smem : 0, &per_sm_big));
         CU(bfs_blocks_per_sm(256, in_smem ? smem : 0, &per_sm_small));
-        const size_t budget = free_device_bytes() / 3;
+        // the search regions may take 60 % of free memory: on the n = 10^6,
+        // m = 2*10^7 graph one region is about half a GB and every SM should
+        // keep its resident CTAs
+        const size_t budget = (size_t)((double)free_device_bytes() * 0.6);
         // regions for the largest resident grid of the three shapes
         int grid = num_sms * std::max(std::max(per_sm, 1), std::max(per_sm_small, 1));
         // MANTRA_BFS_GRID caps the resident CTAs
@@ -309,7 +315,7 @@ struct Engine {
         bfs_grid_big = std::min(grid, num_sms * std::max(per_sm_big, 1));
         bfs_grid_small = std::min(grid, num_sms * std::max(per_sm_small, 1));
         bfs_smem = in_smem ? smem : 0;
-        bfs_n = n; bfs_A = A; bfs_z = zc;
+        bfs_n = n; bfs_A = A; bfs_z = zc; bfs_dl = dl;
         invalidate_graph();
         return MANTRA_OK;
     }
@@ -509,7 +515,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     if ((rc = E.ensure_tables(std::max<uint32_t>(k, 1))) != MANTRA_OK) return rc;
     uint32_t bn = 0, bA = 0, bz = 0, pn = 0, plc = 0;
     uint64_t pwarps = 0, bsamples = 0;
-    bool any_b = false, any_p = false, frac = false;
+    bool any_b = false, any_p = false, frac = false, dl = false;
     for (const TickItem& it : items) {
         if (it.job.opt == MANTRA_PFM) {
             any_p = true; pn = std::max(pn, it.G->n); plc = std::max(plc, it.G->dg.cbound);
@@ -519,11 +525,12 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
             bz = std::max(bz, it.G->dg.max_vslots);
             bsamples += it.job.count;
             frac |= it.job.ob || it.job.rtb || it.job.opt == 3;
+            dl |= it.job.ob || it.job.rtb;
         }
     }
     E.tick_frac = frac;
     const bool cta = any_p && !wide && pfm_use_cta();
-    if (any_b && (rc = E.ensure_bfs(bn, bA, bz)) != MANTRA_OK) return rc;
+    if (any_b && (rc = E.ensure_bfs(bn, bA, bz, dl)) != MANTRA_OK) return rc;
     if (any_p && cta && (rc = E.ensure_pfm_cta(pn, plc)) != MANTRA_OK) return rc;
     if (any_p && !cta && (rc = E.ensure_pfm(pn, plc, pwarps)) != MANTRA_OK) return rc;
     E.tick_cta = cta;

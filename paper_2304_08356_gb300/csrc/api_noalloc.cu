@@ -88,7 +88,7 @@ extern "C" int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt
     const size_t smem = bfs_smem_bytes(A);
     const bool in_smem = smem + bfs_static_smem(512) + 1024 <= smem_optin;
     BfsWs ws{};
-    const size_t region = bfs_region_bytes(n, A, dg->max_vslots, in_smem, &ws);
+    const size_t region = bfs_region_bytes(n, A, dg->max_vslots, in_smem, false, &ws);
     ws.nt = 512;
     const size_t head = kHeadBytes + round256(count * 8);
     if (head >= kScratchBytes || region > kScratchBytes - head) return MANTRA_E_INVAL;   // exceeds the fixed scratch

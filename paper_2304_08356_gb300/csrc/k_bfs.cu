@@ -41,6 +41,18 @@ constexpr int CK = 8;             // bitmap words in flight per lane in the comp
 constexpr int CB = 4;             // new states per thread with loads in flight in the count pass
 constexpr uint32_t SUMW = 512;    // words of the next-level bitmap's summary (one bit per 2^sumshift bitmap words)
 
+// Path count of the state at frontier position p, from the running sums
+// that the level's scan leaves in place (cum[p] = the sum of sigma over
+// p's vertex's states of the level up to p); lv0 is the first position of
+// p's level.
+template <typename Sig>
+__device__ __forceinline__ Sig sigma_at(const Sig* cum, const uint32_t* F, const uint32_t* slot_v, uint32_t p,
+                                        uint32_t lv0) {
+    const Sig c = cum[p];
+    if (p == lv0 || slot_v[F[p - 1]] != slot_v[F[p]]) return c;
+    return c - cum[p - 1];
+}
+
 // For each j: the first index in [lo[j], hi[j]) whose value is >= key[j]
 // (hi[j] if none), left in lo[j]; the K searches advance together so their
 // loads overlap.  Plain loads: the array is written by this kernel.
@@ -71,8 +83,8 @@ __device__ __forceinline__ void lower_bounds_rw(const uint32_t* a, uint32_t (&lo
 // counts dl (the number of optimal ways from a state to z's endpoints) per
 // frontier position, backward from level d; sigma_sz(v) = sum over v's states
 // of sigma * dl (a path visits v once); then every internal v gets its ob
-// value.  sig: path counts by frontier position; dl: the (free) running-sum
-// array, indexed by frontier position;
+// value.  sig: running sums of the path counts by frontier position (see
+// sigma_at); dl: per frontier position (scratch of the ob and RTB updates);
 // acc: per-vertex sums (zero on entry and exit); VB: vertex bitmap (zero on
 // entry and exit); tl: n entries.
 template <bool WIDE, int BFS_NT>
@@ -121,14 +133,16 @@ __device__ __forceinline__ void bfs_ob_update(const DevGraph& g, const Job& job,
         __syncthreads();
     }
     // through counts per vertex; the first touch of v lists it (VB marks)
-    for (uint32_t p = P0 + tid; p < P1; p += BFS_NT) {
-        const Sig x = ldcg_sig(dl + p);
-        if (x == (Sig)0) continue;
-        const uint32_t a = F[p], v = g.slot_v[a];
-        SigOps<WIDE>::atomic_add(acc + v, (Sig)(sig[p] * x));   // <= sigma_sz: no wrap
-        const uint32_t bit = 1u << (v & 31);
-        if (!(atomicOr(VB + (v >> 5), bit) & bit)) tl[atomicAdd(sh_nt, 1u)] = v;
-    }
+    for (uint32_t lv = 1; lv < d; ++lv)
+        for (uint32_t p = lev[lv] + tid; p < lev[lv + 1]; p += BFS_NT) {
+            const Sig x = ldcg_sig(dl + p);
+            if (x == (Sig)0) continue;
+            const uint32_t a = F[p], v = g.slot_v[a];
+            const Sig sp = sigma_at(sig, F, g.slot_v, p, lev[lv]);
+            SigOps<WIDE>::atomic_add(acc + v, (Sig)(sp * x));   // <= sigma_sz: no wrap
+            const uint32_t bit = 1u << (v & 31);
+            if (!(atomicOr(VB + (v >> 5), bit) & bit)) tl[atomicAdd(sh_nt, 1u)] = v;
+        }
     __syncthreads();
     const uint32_t T = *sh_nt;
     u64 my_sum = 0;
@@ -161,9 +175,9 @@ __device__ __forceinline__ void bfs_ob_update(const DevGraph& g, const Job& job,
 // sigma(b) / sigma_{s,v_b} for an endpoint b.  From level D down, every state
 // b with X(b) = eps(b) + delta(b) > 0 adds round(sigma(a) X(b) / sigma(b)) to
 // delta(a) of each DAG predecessor a; f_v(s) = round(sum of delta over v's
-// states / (n-1)), all in 2^-32 units.  sig: path counts by frontier
-// position; dl: per frontier position (the free
-// running-sum array); sv: sigma_{s,v} (zero on entry and exit); dsum:
+// states / (n-1)), all in 2^-32 units.  sig: running sums of the path counts
+// by frontier position (see sigma_at); dl: per frontier position (scratch of
+// the ob and RTB updates); sv: sigma_{s,v} (zero on entry and exit); dsum:
 // per-vertex sums (zero on entry and exit); dv: first level per vertex (n
 // entries, overwritten); VB: vertex bitmap (zero on entry and exit); tl: n
 // entries.
@@ -201,11 +215,12 @@ __device__ __forceinline__ void bfs_rtb_update(const DevGraph& g, const Job& job
     for (uint32_t k = 1; k <= D; ++k)
         for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
             const uint32_t a = F[p], v = g.slot_v[a];
-            if (is_end(p, k, v)) SigOps<WIDE>::atomic_add(sv + v, sig[p]);
+            if (is_end(p, k, v)) SigOps<WIDE>::atomic_add(sv + v, sigma_at(sig, F, g.slot_v, p, lev[k]));
         }
     __syncthreads();
     auto eps_of = [&](uint32_t p, uint32_t k, uint32_t v) -> u64 {
-        return is_end(p, k, v) ? ob_q(SigOps<WIDE>::wide(sig[p]), SigOps<WIDE>::wide(ldcg_sig(sv + v))) : 0ull;
+        return is_end(p, k, v) ? ob_q(SigOps<WIDE>::wide(sigma_at(sig, F, g.slot_v, p, lev[k])),
+                                      SigOps<WIDE>::wide(ldcg_sig(sv + v))) : 0ull;
     };
     for (uint32_t k = 1; k <= D; ++k)
         for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
@@ -220,13 +235,15 @@ __device__ __forceinline__ void bfs_rtb_update(const DevGraph& g, const Job& job
             const u64 X = __ldcg(reinterpret_cast<const unsigned long long*>(dl + p));
             if (!X) continue;
             const uint32_t b = F[p], tb = g.slot_t[b];
-            const u128 sb = SigOps<WIDE>::wide(sig[p]);
+            const u128 sb = SigOps<WIDE>::wide(sigma_at(sig, F, g.slot_v, p, lev[k]));
             for (uint32_t e = g.slot_in[b]; e < g.slot_in[b + 1]; ++e) {
                 const uint32_t w = g.in_u[e], w1 = g.slot_ptr[w + 1];
-                for (uint32_t p2 = lower_bound_u32(Fp, 0, Lp, g.slot_ptr[w]); p2 < Lp; ++p2) {
+                const uint32_t ph = lower_bound_u32(Fp, 0, Lp, g.slot_ptr[w]);   // w's first state on level k-1
+                for (uint32_t p2 = ph; p2 < Lp; ++p2) {
                     const uint32_t a2 = Fp[p2];
                     if (a2 >= w1 || g.slot_t[a2] >= tb) break;
-                    const u64 term = muldiv_round(SigOps<WIDE>::wide(Sp[p2]), X, sb);
+                    const Sig s2 = p2 == ph ? Sp[p2] : (Sig)(Sp[p2] - Sp[p2 - 1]);
+                    const u64 term = muldiv_round(SigOps<WIDE>::wide(s2), X, sb);
                     if (term) atomicAdd(dl + lev[k - 1] + p2, term);
                 }
             }
@@ -371,9 +388,11 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
     __shared__ int sh_t;
 
     char* region = ws.base + (size_t)blockIdx.x * ws.stride;
-    Sig* Fs = reinterpret_cast<Sig*>(region + ws.o_sig);      // path count of the state at each frontier position
+    // per frontier position: the state's path count, written by the count pass,
+    // then replaced in place by the level's scan with the running sum over the
+    // vertex's states of the level up to it (sigma_at recovers the count)
+    Sig* Fs = reinterpret_cast<Sig*>(region + ws.o_sig);
     Sig* zsig = reinterpret_cast<Sig*>(region + ws.o_zsig);   // path counts of z's slots reached by the pull
-    Sig* Fc = reinterpret_cast<Sig*>(region + ws.o_fc);
     uint32_t* F = reinterpret_cast<uint32_t*>(region + ws.o_f);
     uint32_t* Ft = reinterpret_cast<uint32_t*>(region + ws.o_ft);
     uint32_t* lev = reinterpret_cast<uint32_t*>(region + ws.o_lev);
@@ -512,10 +531,12 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
         while (live) {
             // ---- segments of level k ----
             uint32_t G;
-            // this level's frontier times and running sums: shared memory when they fit
-            const bool fsm = !WIDE && L <= FCAP;
+            // this level's frontier times and running sums: shared memory when they
+            // fit (always for level 0, the virtual source, which has no position)
+            const bool fsm = k == 0 || (!WIDE && L <= FCAP);
             uint32_t* const FtL = fsm ? sm_Ft : Ft;
-            Sig* const FcL = fsm ? reinterpret_cast<Sig*>(sm_Fc) : Fc;
+            Sig* const FsL = Fs + lev[k];
+            Sig* const FcL = fsm ? reinterpret_cast<Sig*>(sm_Fc) : FsL;
             advance_stamp();
             const uint32_t stamp = sh_stamp;
             if (k == 0) {
@@ -527,7 +548,6 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 G = 1;
             } else {
                 const uint32_t* Fk = F + lev[k];
-                const Sig* Fsk = Fs + lev[k];
                 // B1: frontier attributes, segment heads and per-vertex running sums
                 // of sigma.  Each thread takes IPT consecutive states of a tile: a
                 // thread-local segmented scan, one block-wide segmented scan of the
@@ -549,7 +569,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                             if (i0 + q < L) {
                                 uq[q] = g_slot_v[aq[q]];
                                 FtL[i0 + q] = g_slot_t[aq[q]];
-                                vq[q] = Fsk[i0 + q];
+                                vq[q] = FsL[i0 + q];
                             }
                         }
                     }
@@ -582,7 +602,10 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                         const uint32_t idx = i0 + q;
                         if ((hm >> q) & 1u) run = vq[q];
                         else { const Sig sm = run + vq[q]; bad |= sm < run; run = sm; }
-                        if (idx < L) FcL[idx] = run;
+                        if (idx < L) {
+                            FcL[idx] = run;
+                            if (fsm) FsL[idx] = run;   // the running sums stay in place for the draw and the updates
+                        }
                     }
                     if (bad) sh_scan_ovf = 1u;
                     uint32_t tot;
@@ -877,9 +900,12 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             }
             // path count of an endpoint slot: sh / sfm from the pull's per-slot
             // counts; fsfm's endpoint is a frontier state of level d
-            uint32_t zpos = 0;
-            if (fsfm) zpos = lev[d] + lower_bound_u32(F + lev[d], 0, lev[d + 1] - lev[d], first);
-            auto end_sig = [&](uint32_t a) -> Sig { return fsfm ? Fs[zpos] : ldcg_sig(zsig + (a - zs)); };
+            Sig zfs = 0;
+            if (fsfm) {
+                const uint32_t zpos = lev[d] + lower_bound_u32(F + lev[d], 0, lev[d + 1] - lev[d], first);
+                zfs = sigma_at(Fs, F, g.slot_v, zpos, lev[d]);
+            }
+            auto end_sig = [&](uint32_t a) -> Sig { return fsfm ? zfs : ldcg_sig(zsig + (a - zs)); };
             Sig tot = 0;
             if (job.opt == 1 || fsfm) tot = end_sig(first);
             else {
@@ -941,17 +967,20 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                     uint32_t nxt = NONE;
                     for (uint32_t e0 = e_lo; e0 < e_hi && nxt == NONE; e0 += 32) {
                         const uint32_t e = e0 + lane;
+                        // w's states on level lvl-1 earlier than tv are positions
+                        // [p0, p1) from w's first (Sp: running sums from p0)
                         Sig wt = 0;
-                        uint32_t p0 = 0, ws1 = 0;
+                        uint32_t p0 = 0, p1 = 0;
                         if (e < e_hi) {
                             const uint32_t w = g.in_u[e];
-                            ws1 = g.slot_ptr[w + 1];
-                            p0 = lower_bound_u32(Fp, 0, Lp, g.slot_ptr[w]);
-                            for (uint32_t p = p0; p < Lp; ++p) {
-                                const uint32_t a2 = Fp[p];
+                            const uint32_t ws1 = g.slot_ptr[w + 1];
+                            p0 = p1 = lower_bound_u32(Fp, 0, Lp, g.slot_ptr[w]);
+                            while (p1 < Lp) {
+                                const uint32_t a2 = Fp[p1];
                                 if (a2 >= ws1 || g.slot_t[a2] >= tv) break;
-                                wt += Sp[p];
+                                ++p1;
                             }
+                            if (p1 > p0) wt = Sp[p1 - 1];
                         }
                         const Sig incl = warp_inclusive_sum(wt);
                         const unsigned msk = __ballot_sync(FULL, xs < incl);
@@ -960,12 +989,12 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                             uint32_t pick = NONE;
                             Sig xr = xs - (incl - wt);
                             if (lane == l) {
-                                for (uint32_t p = p0; p < Lp; ++p) {
-                                    const uint32_t a2 = Fp[p];
-                                    if (a2 >= ws1 || g.slot_t[a2] >= tv) break;
-                                    const Sig w2 = Sp[p];
-                                    if (xr < w2) { pick = a2; break; }
-                                    xr -= w2;
+                                for (uint32_t p = p0; p < p1; ++p) {
+                                    if (xr < Sp[p]) {
+                                        pick = Fp[p];
+                                        if (p > p0) xr -= Sp[p - 1];
+                                        break;
+                                    }
                                 }
                             }
                             nxt = __shfl_sync(FULL, pick, l);
@@ -1047,7 +1076,9 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             const int mode = (job.ob && job.hits && found && !sh_ovf && !sh_err && sh_d >= 2) ? 1
                            : (job.rtb && job.hits && live && !sh_ovf && k >= 2) ? 2
                            : (stats && job.opt == 3 && live && k >= 1) ? 3 : 0;
-            if (mode) {
+            if ((mode == 1 || mode == 2) && !ws.has_dl) {
+                if (tid == 0) set_status(job.status, ST_CHECK);   // a workspace without the updates' scratch
+            } else if (mode) {
                 if (tid == 0) {
                     FracCtx& x = sh_fx;
                     x.task = &sh_task; x.ws = &ws;
@@ -1097,13 +1128,21 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
 // bits_in_smem; the next-level bitmap is always in the region.  The path
 // counts take one entry per frontier position (at most A states per search)
 // plus one per slot of z (at most zcap, the largest slot count of a vertex).
-size_t bfs_region_bytes(uint32_t n, uint32_t A, uint32_t zcap, bool bits_in_smem, BfsWs* ws) {
+// With dl, the scratch of the ob and RTB updates (one entry per position and
+// two per vertex) is added.
+size_t bfs_region_bytes(uint32_t n, uint32_t A, uint32_t zcap, bool bits_in_smem, bool dl, BfsWs* ws) {
     ws->bits_words = (A + 31) / 32;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t o = 0;
     ws->o_sig = o;     o = al(o + (size_t)A * 16);
     ws->o_zsig = o;    o = al(o + (size_t)std::max<uint32_t>(zcap, 1) * 16);
-    ws->o_fc = o;      o = al(o + (size_t)(A + 1) * 16);
+    ws->o_fc = ws->o_acc = ws->o_acc2 = 0;
+    ws->has_dl = dl ? 1 : 0;
+    if (dl) {
+        ws->o_fc = o;      o = al(o + (size_t)(A + 1) * 16);
+        ws->o_acc = o;     o = al(o + (size_t)n * 16);
+        ws->o_acc2 = o;    o = al(o + (size_t)n * 8);
+    }
     ws->o_f = o;       o = al(o + (size_t)(A + 1) * 4);
     ws->o_ft = o;      o = al(o + (size_t)(A + 1) * 4);
     ws->o_lev = o;     o = al(o + (size_t)(n + 3) * 4);
@@ -1114,8 +1153,6 @@ size_t bfs_region_bytes(uint32_t n, uint32_t A, uint32_t zcap, bool bits_in_smem
     ws->o_vb = o;      o = al(o + (size_t)((n + 31) / 32 + 1) * 4);
     ws->o_segmap = o;  o = al(o + (size_t)n * 8);
     ws->o_stamp = o;   o = al(o + 4);
-    ws->o_acc = o;     o = al(o + (size_t)n * 16);
-    ws->o_acc2 = o;    o = al(o + (size_t)n * 8);
     ws->o_nbits = o;   o = al(o + (size_t)ws->bits_words * 4);
     ws->n_cap = n;
     ws->o_bits = o;

@@ -620,6 +620,7 @@ struct BfsWs {
     size_t o_acc;        // ob: per-vertex sums of through counts; RTB: sigma_{s,v}
     size_t o_acc2;       // RTB: per-vertex dependency sums
     size_t o_zsig;       // path counts of z's slots reached by the pull (sh / sfm endpoints)
+    int has_dl;          // the ob / RTB scratch (o_fc, o_acc, o_acc2) is allocated
 };
 
 // Per-warp scratch of the pfm search kernel.
@@ -645,7 +646,7 @@ struct PfmCtaWs {
     int nt;              // threads per CTA (256 or 512)
 };
 
-size_t bfs_region_bytes(uint32_t n, uint32_t A, uint32_t zcap, bool bits_in_smem, BfsWs* ws);
+size_t bfs_region_bytes(uint32_t n, uint32_t A, uint32_t zcap, bool bits_in_smem, bool dl, BfsWs* ws);
 size_t bfs_smem_bytes(uint32_t A);
 size_t bfs_static_smem(int nt);
 cudaError_t bfs_blocks_per_sm(int nt, size_t smem, int* out);
