@@ -15,6 +15,18 @@ step each of temporal edge betweenness (App. A), of the ob estimator
 its rate counts sources) on the same workload is reported under
 secondary.next_rows (--no-next skips them).
 
+Other workloads, after the headline, on one GPU (each leg has a flag that
+skips it):
+* secondary.large_graph: Chung-Lu n = 10^6, gamma 2.1, 2*10^7 edges with t
+  uniform in [0, 2^24) -- one Algorithm 1 run each of sfm and pfm at
+  eps = 0.005, Algorithm 2 at r_s = 256, per-kernel rooflines, the oracle on
+  the host cores for pfm (--no-large);
+* secondary.batch_256: 256 uneven bursty graphs in one mantra_estimate_batch
+  against 256 sequential calls (--no-batch256);
+* serving: 64 resident graphs (n log-spaced in [1000, 200000], m = 25 n),
+  2,000 Poisson requests at 200/s, served (continuous batching) against one
+  request at a time (--serve-graphs 0 skips it).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank runs its own steps on its own GPU (different seeds,
 no collective on the data path); value = all ranks' samples / max-rank time.
@@ -166,7 +178,7 @@ def recorded_traffic(kernel: str, alg_bytes_per_launch: float):
     ratio times its algorithmic bytes."""
     if not os.path.exists(TRAFFIC):
         return None
-    dig = kernel_source_digest(kernel)
+    dig = kernel_source_digest(kernel.split("@")[0])
     for line in open(TRAFFIC):
         f = line.split()
         if len(f) >= 3 and not line.startswith("#") and f[0] == kernel and f[1] == dig:
@@ -256,6 +268,127 @@ def run_serving(M, graphs_uvt, reqs):
     return plain, served
 
 
+LARGE = ("chung_lu_uniform_t n=1000000 gamma=2.1 m=20000000 t<2^24; Algorithm 1 sfm and pfm at eps=0.005 "
+         "delta=0.1 c=25; Algorithm 2 pfm and sfm at eps=0.01 r_s=256")
+BATCH = "256 bursty Chung-Lu graphs, n log-uniform in [500, 50000], m = 20 n, optimality g mod 3, eps=0.02 delta=0.1 c=25"
+
+
+def kernel_rooflines(info, opt, peak, ms=None):
+    """Achieved GB/s of the search kernels of one Algorithm 1 run, from the
+    library's counters (byte models of include/mantra.h) and kernel time."""
+    ms = info["kernel_ms"] if ms is None else ms
+    out = {}
+    if opt == "pfm":
+        own = 12 * info["edges_expanded"] + 24 * info["sigma_adds"]
+        out["k_pfm_cta"] = {"achieved": info["alg_bytes"] / (ms / 1e3) / 1e9,
+                            "achieved_own_model": own / (ms / 1e3) / 1e9,
+                            "alg_bytes": info["alg_bytes"], "own_model_bytes": own, "ms": ms,
+                            "launches": info["search_launches"]}
+        out["k_pfm_cta"]["frac"] = out["k_pfm_cta"]["achieved"] / peak
+        out["k_pfm_cta"]["frac_own_model"] = out["k_pfm_cta"]["achieved_own_model"] / peak
+    else:
+        out["k_bfs"] = {"achieved": info["alg_bytes"] / (ms / 1e3) / 1e9, "alg_bytes": info["alg_bytes"], "ms": ms,
+                        "launches": info["search_launches"]}
+        out["k_bfs"]["frac"] = out["k_bfs"]["achieved"] / peak
+    for k in out:
+        tr = recorded_traffic(k + "@large", out[k]["alg_bytes"] / max(1, out[k]["launches"]))
+        out[k]["traffic_per_launch"] = tr
+        out[k]["unit"] = "GB/s"
+    return out
+
+
+def run_large(M, torch, peak, cpu=True):
+    """Config 3 (the HBM-bound case): one Algorithm 1 run each of sfm and pfm
+    at eps = 0.005 after a warm-up, device outputs, L2 flushed before each,
+    CUDA events on the library's stream; then Algorithm 2 with r_s = 256."""
+    from paper_2304_08356_gb300 import synth
+    u, v, t = synth.chung_lu_uniform_t(n=1_000_000, m=20_000_000, gamma=2.1, seed=1)
+    g = M.Graph(u, v, t, n=1_000_000)
+    st = torch.cuda.Stream()
+    est = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    hits = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for opt in ("sfm", "pfm"):
+        g.estimate(opt, 0.05, DELTA, 7, c=C_TRIALS, fixed_r=600, est_out=est.data_ptr(), hits_out=hits.data_ptr(),
+                   stream=st.cuda_stream)
+    torch.cuda.synchronize()
+    infos, ms = {}, {}
+    for opt in ("sfm", "pfm"):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _, _, infos[opt] = g.estimate(opt, 0.005, DELTA, 2024, c=C_TRIALS, est_out=est.data_ptr(),
+                                      hits_out=hits.data_ptr(), stream=st.cuda_stream)
+        e1.record(st)
+        e1.synchronize()
+        ms[opt] = e0.elapsed_time(e1)
+    stats = {}
+    for opt in ("pfm", "sfm"):
+        s_, _ = g.temporal_stats(opt, 0.01, 4, r_override=256)
+        stats[opt] = {k: s_[k] for k in ("d_lb", "d_tau", "zeta", "psi", "r", "seconds")}
+    n_s = {o: infos[o]["r"] + infos[o]["bootstrap"] for o in infos}
+    roof = {}
+    for o in ("sfm", "pfm"):
+        roof.update(kernel_rooflines(infos[o], o, peak))
+    out = {"workload": LARGE, "pairs_per_s": sum(n_s.values()) / (sum(ms.values()) / 1e3),
+           "per_opt": {o: {"pairs_per_s": n_s[o] / (ms[o] / 1e3), "ms": ms[o], "r": infos[o]["r"],
+                           "omega": infos[o]["omega"], "rounds": infos[o]["rounds"],
+                           "temporal_edge_GBps": infos[o]["alg_bytes"] / (ms[o] / 1e3) / 1e9,
+                           "edges_per_s": infos[o]["edges_scanned"] / (ms[o] / 1e3)} for o in infos},
+           "algorithm2_r_s_256": stats, "roofline": roof,
+           "l2": "flushed before each run (256 MiB write); CUDA events around each Algorithm 1 run"}
+    if cpu:
+        # the oracle on the host cores over the first pfm estimation samples of the
+        # same run (an sfm oracle search at this size takes minutes per sample)
+        from oracle import oracle as O
+        og = O.Graph(u, v, t, n=1_000_000)
+        cores = host_cores()
+        rates, counts = cpu_oracle_rates(u, v, t, 2024, budget_s=20.0, threads=cores, graph=og, opts=("pfm",))
+        out["cpu_baseline"] = {"value": rates["pfm"], "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                               "sample": "first %d pfm estimation samples of the same seed on %d host threads, "
+                                         "20 s of wall time; sfm not timed (minutes per oracle sample)"
+                                         % (counts["pfm"], cores),
+                               "gpu_pfm_pairs_per_s": n_s["pfm"] / (ms["pfm"] / 1e3)}
+    g.free()
+    del flush, est, hits
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch256(M, torch):
+    """Config 4: 256 uneven graphs, every problem's Algorithm 1 in one
+    mantra_estimate_batch (one persistent launch per kernel family and tick)
+    against 256 sequential mantra_estimate calls on the same arguments."""
+    from paper_2304_08356_gb300 import synth
+    inst = synth.batch_instances()
+    gs = [M.Graph(*uvt) for uvt in inst]
+    names = ("sh", "sfm", "pfm")
+    probs = [dict(graph=gs[k], opt=names[k % 3], eps=0.02, delta=DELTA, seed=77 + k, c=C_TRIALS)
+             for k in range(len(gs))]
+    M.estimate_batch([dict(p, seed=1) for p in probs[:8]])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = M.estimate_batch(probs)
+    t_batch = time.perf_counter() - t0
+    for r in res:
+        if r[3] != 0:
+            raise M.MantraError(r[3], "mantra_estimate_batch (256 graphs)")
+    n_b = sum(r[2]["r"] + r[2]["bootstrap"] for r in res)
+    t0 = time.perf_counter()
+    n_q, same = 0, True
+    for p, r in zip(probs, res):
+        _, h, info = p["graph"].estimate(p["opt"], p["eps"], p["delta"], p["seed"], c=C_TRIALS)
+        n_q += info["r"] + info["bootstrap"]
+        same = same and bool(np.array_equal(h, r[1]))
+    t_seq = time.perf_counter() - t0
+    for g in gs:
+        g.free()
+    return {"workload": BATCH, "batched": {"pairs_per_s": n_b / t_batch, "s": t_batch},
+            "sequential": {"pairs_per_s": n_q / t_seq, "s": t_seq}, "samples": n_b,
+            "batched_equals_sequential": same, "timing": "host wall clock around each whole call sequence"}
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -263,7 +396,7 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def cpu_oracle_rates(u, v, t, seed, budget_s=6.0, threads=1, graph=None):
+def cpu_oracle_rates(u, v, t, seed, budget_s=6.0, threads=1, graph=None, opts=None):
     """Oracle pairs/s per optimality on a bounded prefix of the estimation
     samples.  With threads > 1 the oracle's per-sample call runs on that many
     host threads over disjoint sample indices (the call releases the GIL; the
@@ -271,7 +404,7 @@ def cpu_oracle_rates(u, v, t, seed, budget_s=6.0, threads=1, graph=None):
     from oracle import oracle as O
     g = graph if graph is not None else O.Graph(u, v, t)
     rates, counts = {}, {}
-    for name in OPTS:
+    for name in (opts or OPTS):
         opt = {"sh": 0, "sfm": 1, "pfm": 2}[name]
         k = 1 if opt != 2 else 64
         lock = threading.Lock()
@@ -348,9 +481,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-next", action="store_true", help="skip the edge-betweenness and ob legs")
     ap.add_argument("--opts", default="sh,sfm,pfm", help="optimalities per step (profiling subsets)")
-    ap.add_argument("--serve-graphs", type=int, default=16, help="serving leg: resident graphs (0: skip)")
-    ap.add_argument("--serve-requests", type=int, default=120, help="serving leg: requests")
-    ap.add_argument("--serve-nmax", type=int, default=20000, help="serving leg: largest graph's n")
+    ap.add_argument("--serve-graphs", type=int, default=64, help="serving leg: resident graphs (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="serving leg: requests")
+    ap.add_argument("--serve-nmax", type=int, default=200000, help="serving leg: largest graph's n")
+    ap.add_argument("--no-large", action="store_true", help="skip the n = 10^6, m = 2*10^7 leg")
+    ap.add_argument("--no-batch256", action="store_true", help="skip the 256-graph batching leg")
     ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
                     help="batched: one mantra_estimate_batch over the optimalities per step; "
                          "sequential: one mantra_estimate per optimality")
@@ -517,6 +652,13 @@ def main():
                                "{0.05, 0.02, 0.01}, delta 0.1" % (len(sg), args.serve_nmax, len(sr)),
                    "served": served, "plain": plain}
 
+    large = batch256 = None
+    if rank == 0 and world == 1:
+        if not args.no_large:
+            large = run_large(M, torch, peak, cpu=not args.no_cpu_baseline)
+        if not args.no_batch256:
+            batch256 = run_batch256(M, torch)
+
     line = None
     if rank == 0:
         cpu = None
@@ -545,7 +687,8 @@ def main():
                               "per_opt_r": {o: [st[o]["r"] for st in infos_all] for o in OPTS},
                               "temporal_edge_GBps": alg_gbps, "edges_per_s": edges / (total_ms / 1000.0),
                               "sequential_pairs_per_s": seq_rate, "sequential_kernel_ms": kms,
-                              "mode": args.mode, "next_rows": next_rows},
+                              "mode": args.mode, "next_rows": next_rows,
+                              "large_graph": large, "batch_256": batch256},
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "timing": "sequential pass, tick events",
                              "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},

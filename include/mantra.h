@@ -136,6 +136,11 @@ typedef struct {
                                 edges_scanned / 32 (the edge record, shared by 32 samples) + 24 *
                                 sigma_adds (sigma(u) read, sigma(v) read-modify-write) */
     uint64_t frontier_vertices; /* F (above) */
+    uint64_t edges_expanded; /* pfm, one CTA per sample (the default pfm kernel): out-edges walked by
+                                the earliest-arrival rounds plus prefix-foremost DAG edges walked by the
+                                path-count pass; that kernel's own algorithmic bytes are 12 per walked
+                                edge (8 B record, 4 B arrival test or count read) + 24 * sigma_adds.
+                                0 for sh / sfm and for the stream-scan kernel */
 } mantra_info;
 
 /* Output of mantra_temporal_stats (paper App. D, Algorithm 2). */

@@ -134,10 +134,11 @@ constexpr size_t SLOT_BYTES = 1152;
 constexpr size_t SLOT_STATUS = 64, SLOT_HMAX = 72, SLOT_ROWMAX = 80;
 
 struct LaunchTotals {
-    uint64_t sum_int = 0, escan = 0, eadd = 0, snew = 0, fseg = 0, wide = 0, launches = 0;
+    uint64_t sum_int = 0, escan = 0, eadd = 0, snew = 0, fseg = 0, xedge = 0, wide = 0, launches = 0;
     double kernel_ms = 0;
     void add_counters(const u64* c) {
         sum_int += c[C_SUMINT]; escan += c[C_ESCAN]; eadd += c[C_EADD]; snew += c[C_SNEW]; fseg += c[C_FSEG];
+        xedge += c[C_XEDGE];
     }
 };
 
@@ -826,7 +827,7 @@ struct Problem {
     // the reduction outputs when the tick completed the phase).
     int consume(Engine& E, const char* slot, const LaunchTotals& tt, uint64_t count) {
         T.kernel_ms += tt.kernel_ms; T.launches += tt.launches; T.escan += tt.escan; T.eadd += tt.eadd;
-        T.snew += tt.snew; T.fseg += tt.fseg; T.wide += tt.wide;
+        T.snew += tt.snew; T.fseg += tt.fseg; T.xedge += tt.xedge; T.wide += tt.wide;
         if (phase == BOOT) boot_sum_int += tt.sum_int;
         else T.sum_int += tt.sum_int;
         pos += count;
@@ -900,6 +901,7 @@ struct Problem {
         I.kernel_launches = T.launches + reduces + (f > 0 ? 1 : 0);
         I.alg_bytes = alg_bytes_of(opt == MANTRA_PFM, T.escan, T.eadd, T.snew, T.fseg);
         I.frontier_vertices = opt == MANTRA_PFM ? 0 : T.fseg;
+        I.edges_expanded = opt == MANTRA_PFM ? T.xedge : 0;
         return MANTRA_OK;
     }
 

@@ -41,7 +41,7 @@ class Info(C.Structure):
                 ("edges_scanned", C.c_uint64), ("sigma_adds", C.c_uint64), ("states_new", C.c_uint64),
                 ("wide_samples", C.c_uint64), ("seconds", C.c_double), ("kernel_ms", C.c_double),
                 ("search_launches", C.c_uint64), ("kernel_launches", C.c_uint64), ("alg_bytes", C.c_uint64),
-                ("frontier_vertices", C.c_uint64)]
+                ("frontier_vertices", C.c_uint64), ("edges_expanded", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

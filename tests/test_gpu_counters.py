@@ -57,6 +57,11 @@ def test_pfm_kernels_counters_equal_oracle(M, kernel, monkeypatch):
     _, _, info = g.estimate(2, 0.05, 0.1, 7, fixed_r=700)
     _, _, oinfo = o.estimate(2, 0.05, 0.1, 7, fixed_r=700)
     _check(info, oinfo, 2)
+    # the CTA kernel's walked edges include every DAG edge it counts paths over
+    if kernel == "cta":
+        assert info["edges_expanded"] >= info["sigma_adds"] > 0
+    else:
+        assert info["edges_expanded"] == 0
 
 
 @pytest.mark.parametrize("opt", [0, 1, 2, 3])
