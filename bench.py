@@ -304,6 +304,7 @@ def run_large(M, torch, peak, cpu=True):
     from paper_2304_08356_gb300 import synth
     u, v, t = synth.chung_lu_uniform_t(n=1_000_000, m=20_000_000, gamma=2.1, seed=1)
     g = M.Graph(u, v, t, n=1_000_000)
+    tuned = g.tune()
     st = torch.cuda.Stream()
     est = torch.empty(g.n, dtype=torch.float64, device="cuda")
     hits = torch.empty(g.n, dtype=torch.int64, device="cuda")
@@ -336,7 +337,7 @@ def run_large(M, torch, peak, cpu=True):
                            "omega": infos[o]["omega"], "rounds": infos[o]["rounds"],
                            "temporal_edge_GBps": infos[o]["alg_bytes"] / (ms[o] / 1e3) / 1e9,
                            "edges_per_s": infos[o]["edges_scanned"] / (ms[o] / 1e3)} for o in infos},
-           "algorithm2_r_s_256": stats, "roofline": roof,
+           "algorithm2_r_s_256": stats, "roofline": roof, "autotune": tuned,
            "l2": "flushed before each run (256 MiB write); CUDA events around each Algorithm 1 run"}
     if cpu:
         # the oracle on the host cores over the first pfm estimation samples of the
@@ -511,6 +512,7 @@ def main():
 
     u, v, t = workload()
     g = M.Graph(u, v, t)
+    tuned = g.tune()          # the autotuner's launch choices for this graph (results do not depend on them)
     stream = torch.cuda.Stream()
     est_dev = torch.empty(g.n, dtype=torch.float64, device="cuda")
     hits_dev = torch.empty(g.n, dtype=torch.int64, device="cuda")
@@ -687,7 +689,7 @@ def main():
                               "per_opt_r": {o: [st[o]["r"] for st in infos_all] for o in OPTS},
                               "temporal_edge_GBps": alg_gbps, "edges_per_s": edges / (total_ms / 1000.0),
                               "sequential_pairs_per_s": seq_rate, "sequential_kernel_ms": kms,
-                              "mode": args.mode, "next_rows": next_rows,
+                              "mode": args.mode, "next_rows": next_rows, "autotune": tuned,
                               "large_graph": large, "batch_256": batch256},
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "timing": "sequential pass, tick events",

@@ -218,6 +218,39 @@ typedef struct {
  * first failing problem's status (each problem's own status is in .status). */
 int mantra_estimate_batch(mantra_problem* probs, uint32_t count);
 
+/* Autotuner (no counterpart in the paper; it sets how the library runs, not
+ * what it computes).  For one graph it times the launch choices of the two
+ * search kernels on probes -- fixed-r estimates of the graph itself, one per
+ * candidate and the same seed for all, each timed by the library's CUDA events
+ * -- and keeps the fastest for that graph:
+ *   sh / sfm (k_bfs): CTA size 256, 512 or 1024 threads (how many samples run
+ *     at once per SM, and the frontier tile a CTA scans per pass) x the
+ *     visited bitmap in shared or in global memory (shared only where it fits);
+ *   pfm (CTA kernel): CTA size 256 or 512 x the arrival state in shared or in
+ *     global memory.
+ * A probe is sized like one of Algorithm 1's large rounds: about 100 ms of
+ * kernel time by a calibration run of the defaults, between 8 and 64 samples
+ * per SM.  Every candidate runs within the same workspace, whose size is bounded by
+ * the engine's share of free device memory.  Later calls whose largest graph
+ * of that kernel family is g use g's choice (ticks of small bootstraps keep
+ * their 1024-thread shape).  Results never depend on the choice: sample i
+ * draws from Philox counters fixed by (seed, i).  Call it before sharing g
+ * between threads; a tuned graph can be tuned again. */
+typedef struct {
+    uint32_t bfs_threads;        /* chosen sh/sfm CTA size */
+    uint32_t bfs_bitmap_shared;  /* 1: the visited bitmap in shared memory */
+    uint32_t pfm_threads;        /* chosen pfm CTA size */
+    uint32_t pfm_state_shared;   /* 1: the arrival state in shared memory */
+    uint32_t bfs_resident_ctas;  /* samples in flight of the choice (resident CTAs) */
+    uint32_t pfm_resident_ctas;
+    double bfs_ms, bfs_default_ms;   /* sh probe kernel time: the choice, the defaults */
+    double pfm_ms, pfm_default_ms;   /* pfm probe kernel time: the choice, the defaults */
+    uint64_t probe_samples;      /* samples per sh probe run */
+    uint64_t pfm_probe_samples;  /* samples per pfm probe run */
+} mantra_tune_result;
+
+int mantra_tune(mantra_graph* g, mantra_tune_result* out);
+
 /* Algorithm 2: r_s = r_override (or ceil(ln n / eps^2) when 0) full searches
  * from sources drawn uniformly from [0,n) (Philox domain 5).  reach_out (or
  * NULL): reach_cap entries, reach_out[h] = number of (source, v != source)

@@ -25,12 +25,22 @@
 
 using namespace mantra;
 
+// Launch choices of the search kernels for one graph (mantra_tune); 0 / -1
+// leave the engine's defaults.
+struct Knobs {
+    int bfs_nt = 0;      // sh/sfm CTA size: 256, 512 or 1024
+    int bfs_smem = -1;   // visited bitmap: 1 shared memory, 0 global
+    int pfm_nt = 0;      // pfm CTA size: 256 or 512
+    int pfm_smem = -1;   // pfm arrival state: 1 shared memory, 0 global
+};
+
 struct mantra_graph {
     uint32_t n = 0, A = 0, m = 0, n_uedge = 0;
     uint64_t self_loops = 0, duplicates = 0;
     DevGraph dg{};
     void* dmem = nullptr;
     int device = 0;
+    Knobs knobs;         // set by mantra_tune
 };
 
 namespace {
@@ -182,14 +192,24 @@ struct Engine {
     cudaEvent_t e_t0 = nullptr, e_t1 = nullptr;   // around a graph launch (events inside graphs cannot be timed)
     bool last_tick_graph = false;
     // search workspaces
-    char* bfs_mem = nullptr; BfsWs bws{}; int bfs_grid = 0; size_t bfs_smem = 0; uint32_t bfs_n = 0, bfs_A = 0, bfs_z = 0;
+    // sh/sfm: regions for the largest resident grid of any CTA shape (s: 0 =
+    // 256, 1 = 512, 2 = 1024 threads) and visited-bitmap placement (p: 0 =
+    // global, 1 = shared memory); bfs_grids[s][p] = resident CTAs (0: the
+    // placement does not fit)
+    char* bfs_mem = nullptr; BfsWs bws{}; size_t bfs_smem = 0; uint32_t bfs_n = 0, bfs_A = 0, bfs_z = 0;
+    int bfs_grids[3][2] = {};
+    int bfs_rule_smem = 0;     // default placement: shared only while it keeps the 512-thread residency
+    int bfs_grid = 0;          // resident CTAs of the default (512 threads, default placement)
     bool bfs_dl = false;       // the regions carry the ob / RTB scratch
-    int bfs_grid_big = 0;      // resident 1024-thread CTAs (the regions of the first ones)
-    int bfs_grid_small = 0;    // resident 256-thread CTAs
     int tick_bfs_nt = 512;     // sh/sfm CTA size of the current tick
+    int tick_bfs_sm = 0;       // its bitmap placement
     bool tick_frac = false;    // the tick has an ob or RTB problem on the sh/sfm kernel
     char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; uint32_t pfm_n = 0, pfm_lcap = 0; uint64_t pfm_warps = 0;
+    // pfm, one CTA per sample: shapes 0 = 256, 1 = 512 threads, placements as above
     char* pc_mem = nullptr; PfmCtaWs pcws{}; int pc_grid = 0; uint32_t pc_n = 0, pc_cb = 0;
+    int pc_grids[2][2] = {};
+    size_t pc_smem = 0;
+    int tick_pc_nt = 512, tick_pc_sm = 0;
     bool tick_cta = false;   // pfm samples of the current tick run one per CTA
     // tick tables
     uint32_t cap = 0;
@@ -197,10 +217,8 @@ struct Engine {
     char* slot_h = nullptr; char* slot_d = nullptr;
     size_t o_hdr = 0, o_work = 0, o_ub = 0, o_up = 0, o_tb = 0, o_tp = 0, o_ri = 0, o_rs = 0;
     int red_grid = 0;
-    // captured ticks, one per pfm kernel (lane / CTA per sample)
-    // captured ticks, by (pfm kernel, sh/sfm CTA size)
-    cudaGraphExec_t gexec[12] = {};
-    bool graph_ok[12] = {};
+    // captured ticks, by launch configuration (tick_key)
+    std::map<int, cudaGraphExec_t> gexec;
     bool use_graph = true;
     DevPool pool;
 
@@ -227,11 +245,16 @@ struct Engine {
     }
 
     void invalidate_graph() {
-        for (int k = 0; k < 12; ++k) {
-            if (gexec[k]) cudaGraphExecDestroy(gexec[k]);
-            gexec[k] = nullptr;
-            graph_ok[k] = false;
-        }
+        for (auto& kv : gexec)
+            if (kv.second) cudaGraphExecDestroy(kv.second);
+        gexec.clear();
+    }
+
+    static int shape_of(int nt) { return nt == 256 ? 0 : (nt == 1024 ? 2 : 1); }
+
+    int tick_key() const {
+        return (tick_cta ? 1 : 0) | (shape_of(tick_bfs_nt) << 1) | (tick_bfs_sm << 3) | ((tick_frac ? 1 : 0) << 4) |
+               ((tick_pc_nt == 256 ? 0 : 1) << 5) | (tick_pc_sm << 6);
     }
 
     // Table block layout: header | 2 work counters | unit starts (bfs, pfm) |
@@ -264,8 +287,9 @@ struct Engine {
         return MANTRA_OK;
     }
 
-    // sh/sfm: one region per resident CTA (the largest grid of the CTA shapes),
-    // at most 60 % of free memory.
+    // sh/sfm: one region per resident CTA of the largest grid over CTA shapes
+    // and bitmap placements, at most 60 % of free memory.  Every region holds
+    // a global visited bitmap as well, so the placement is chosen per launch.
     int ensure_bfs(uint32_t n, uint32_t A, uint32_t zc, bool dl) {
         if (bfs_mem && n <= bfs_n && A <= bfs_A && zc <= bfs_z && (!dl || bfs_dl)) return MANTRA_OK;
         n = std::max(n, bfs_n);
@@ -273,38 +297,35 @@ struct Engine {
         zc = std::max(zc, bfs_z);
         dl = dl || bfs_dl;
         if (bfs_mem) { cudaStreamSynchronize(sa); cudaFree(bfs_mem); bfs_mem = nullptr; }
-        // regions for the 512-thread shape (two CTAs per SM); the 1024-thread
-        // shape (one per SM) uses the first of them
+        const int nts[3] = {256, 512, 1024};
         const size_t smem = bfs_smem_bytes(A);
-        bool in_smem = smem + std::max(bfs_static_smem(512), bfs_static_smem(1024)) + 1024 <= smem_optin;
-        if (in_smem) {
-            // the bitmap goes to shared memory only while two 512-thread CTAs
-            // per SM stay resident: on a 798k-slot graph one CTA per SM with the
-            // bitmap took 64 ms where two without it took 49 ms
-            int with_bits = 0, without = 0;
-            CU(bfs_configure(smem));
-            CU(bfs_blocks_per_sm(512, smem, &with_bits));
-            CU(bfs_blocks_per_sm(512, 0, &without));
-            if (with_bits < without) in_smem = false;
+        size_t stat = 0;
+        for (int nt : nts) stat = std::max(stat, bfs_static_smem(nt));
+        const bool fit = smem + stat + 1024 <= smem_optin;
+        if (fit) CU(bfs_configure(smem));
+        int per[3][2] = {};
+        for (int s = 0; s < 3; ++s) {
+            CU(bfs_blocks_per_sm(nts[s], 0, &per[s][0]));
+            if (fit) CU(bfs_blocks_per_sm(nts[s], smem, &per[s][1]));
         }
-        // MANTRA_BFS_SMEM=0 keeps the visited bitmap in the region; =1 puts it
-        // in shared memory whenever it fits, whatever the residency
+        // default placement: the bitmap goes to shared memory only while two
+        // 512-thread CTAs per SM stay resident (on a 798k-slot graph one CTA per
+        // SM with the bitmap took 64 ms where two without it took 49 ms);
+        // MANTRA_BFS_SMEM=0 forces global memory, =1 shared whenever it fits
+        bfs_rule_smem = (fit && per[1][1] >= per[1][0]) ? 1 : 0;
         if (const char* env = std::getenv("MANTRA_BFS_SMEM")) {
-            if (env[0] == '0') in_smem = false;
-            else if (env[0] == '1') in_smem = smem + std::max(bfs_static_smem(512), bfs_static_smem(1024)) + 1024 <= smem_optin;
+            if (env[0] == '0') bfs_rule_smem = 0;
+            else if (env[0] == '1') bfs_rule_smem = fit ? 1 : 0;
         }
-        const size_t region = bfs_region_bytes(n, A, zc, in_smem, dl, &bws);
-        CU(bfs_configure(in_smem ? smem : 0));
-        int per_sm = 0, per_sm_big = 0, per_sm_small = 0;
-        CU(bfs_blocks_per_sm(512, in_smem ? smem : 0, &per_sm));
-        CU(bfs_blocks_per_sm(1024, in_smem ? smem : 0, &per_sm_big));
-        CU(bfs_blocks_per_sm(256, in_smem ? smem : 0, &per_sm_small));
+        const size_t region = bfs_region_bytes(n, A, zc, false, dl, &bws);
         // the search regions may take 60 % of free memory: on the n = 10^6,
         // m = 2*10^7 graph one region is about half a GB and every SM should
         // keep its resident CTAs
         const size_t budget = (size_t)((double)free_device_bytes() * 0.6);
-        // regions for the largest resident grid of the three shapes
-        int grid = num_sms * std::max(std::max(per_sm, 1), std::max(per_sm_small, 1));
+        int grid = 0;
+        for (int s = 0; s < 3; ++s)
+            for (int p = 0; p < 2; ++p) grid = std::max(grid, num_sms * per[s][p]);
+        grid = std::max(grid, 1);
         // MANTRA_BFS_GRID caps the resident CTAs
         if (const char* env = std::getenv("MANTRA_BFS_GRID")) grid = std::max(1, std::min(grid, std::atoi(env)));
         if ((size_t)grid * region > budget) grid = (int)std::max<size_t>(1, budget / region);
@@ -312,10 +333,10 @@ struct Engine {
         CU(cudaMemsetAsync(bfs_mem, 0, (size_t)grid * region, sa));
         bws.base = bfs_mem;
         bws.stride = region;
-        bfs_grid = std::min(grid, num_sms * std::max(per_sm, 1));
-        bfs_grid_big = std::min(grid, num_sms * std::max(per_sm_big, 1));
-        bfs_grid_small = std::min(grid, num_sms * std::max(per_sm_small, 1));
-        bfs_smem = in_smem ? smem : 0;
+        for (int s = 0; s < 3; ++s)
+            for (int p = 0; p < 2; ++p) bfs_grids[s][p] = per[s][p] > 0 ? std::min(grid, num_sms * per[s][p]) : 0;
+        bfs_grid = bfs_grids[1][bfs_rule_smem];
+        bfs_smem = fit ? smem : 0;
         bfs_n = n; bfs_A = A; bfs_z = zc; bfs_dl = dl;
         invalidate_graph();
         return MANTRA_OK;
@@ -353,33 +374,39 @@ struct Engine {
         return MANTRA_OK;
     }
 
-    // pfm with one CTA per sample: one region per resident CTA, at most a third
-    // of free memory; arrival slots and flag bitmaps in shared memory when they fit.
+    // pfm with one CTA per sample: one region per resident CTA of the largest
+    // grid over CTA shapes and state placements, at most a third of free
+    // memory.  Every region holds the arrival state in global memory as well,
+    // so the placement (shared memory when it fits) is chosen per launch.
     int ensure_pfm_cta(uint32_t n, uint32_t cb) {
         if (pc_mem && n <= pc_n && cb <= pc_cb) return MANTRA_OK;
         n = std::max(n, pc_n);
         cb = std::max(cb, pc_cb);
         if (pc_mem) { cudaStreamSynchronize(sb); cudaStreamSynchronize(sa); cudaFree(pc_mem); pc_mem = nullptr; }
-        // MANTRA_PFM_CTA_NT=256 takes 256-thread CTAs (four per SM);
-        // MANTRA_PFM_CTA_SMEM=0 keeps the arrival state in global memory
-        int nt = 512;
-        if (const char* env = std::getenv("MANTRA_PFM_CTA_NT")) nt = std::atoi(env) == 256 ? 256 : 512;
+        const int nts[2] = {256, 512};
         const size_t smem = pfm_cta_smem_bytes(n);
-        bool in_smem = smem + pfm_cta_static_smem(nt) + 1024 <= smem_optin;
-        if (const char* env = std::getenv("MANTRA_PFM_CTA_SMEM")) in_smem = in_smem && env[0] != '0';
-        const size_t region = pfm_cta_region_bytes(n, cb, in_smem, &pcws);
-        pcws.nt = nt;
-        CU(pfm_cta_configure(in_smem ? smem : 0));
-        int per_sm = 0;
-        CU(pfm_cta_blocks_per_sm(nt, in_smem, in_smem ? smem : 0, &per_sm));
-        int grid = num_sms * std::max(per_sm, 1);
+        const bool fit = smem + std::max(pfm_cta_static_smem(256), pfm_cta_static_smem(512)) + 1024 <= smem_optin;
+        if (fit) CU(pfm_cta_configure(smem));
+        int per[2][2] = {};
+        for (int s = 0; s < 2; ++s) {
+            CU(pfm_cta_blocks_per_sm(nts[s], false, 0, &per[s][0]));
+            if (fit) CU(pfm_cta_blocks_per_sm(nts[s], true, smem, &per[s][1]));
+        }
+        const size_t region = pfm_cta_region_bytes(n, cb, false, &pcws);
+        int grid = 0;
+        for (int s = 0; s < 2; ++s)
+            for (int p = 0; p < 2; ++p) grid = std::max(grid, num_sms * per[s][p]);
+        grid = std::max(grid, 1);
         if (const char* env = std::getenv("MANTRA_PFM_GRID")) grid = std::max(1, std::min(grid, std::atoi(env)));
         const size_t budget = free_device_bytes() / 3;
         if ((size_t)grid * region > budget) grid = (int)std::max<size_t>(1, budget / region);
         if (cudaMalloc(&pc_mem, (size_t)grid * region) != cudaSuccess) { pc_mem = nullptr; return MANTRA_E_NOMEM; }
         pcws.base = pc_mem;
         pcws.stride = region;
-        pc_grid = grid;
+        for (int s = 0; s < 2; ++s)
+            for (int p = 0; p < 2; ++p) pc_grids[s][p] = per[s][p] > 0 ? std::min(grid, num_sms * per[s][p]) : 0;
+        pc_grid = pc_grids[1][fit ? 1 : 0];
+        pc_smem = fit ? smem : 0;
         pc_n = n;
         pc_cb = cb;
         invalidate_graph();
@@ -399,15 +426,19 @@ struct Engine {
             CU(cudaEventRecord(e_b0, sa));
             BfsWs w = bws;
             w.nt = tick_bfs_nt;
+            w.bits_in_smem = tick_bfs_sm;
             CU(launch_bfs((const Task*)(tab_d + o_tb), (const uint64_t*)(tab_d + o_ub), hdr + 0, work + 0, w,
-                          tick_bfs_nt == 1024 ? bfs_grid_big : (tick_bfs_nt == 256 ? bfs_grid_small : bfs_grid),
-                          bfs_smem, wide, tick_frac, sa));
+                          bfs_grids[shape_of(tick_bfs_nt)][tick_bfs_sm], tick_bfs_sm ? bfs_smem : 0, wide, tick_frac,
+                          sa));
             CU(cudaEventRecord(e_b1, sa));
         }
         if (tick_cta && !wide && pc_mem) {
             CU(cudaEventRecord(e_p0, sb));
-            CU(launch_pfm_cta((const Task*)(tab_d + o_tp), (const uint64_t*)(tab_d + o_up), hdr + 1, work + 1, pcws,
-                              pc_grid, sb));
+            PfmCtaWs w = pcws;
+            w.nt = tick_pc_nt;
+            w.fa_in_smem = tick_pc_sm;
+            CU(launch_pfm_cta((const Task*)(tab_d + o_tp), (const uint64_t*)(tab_d + o_up), hdr + 1, work + 1, w,
+                              pc_grids[tick_pc_nt == 256 ? 0 : 1][tick_pc_sm], sb));
             CU(cudaEventRecord(e_p1, sb));
         } else if (!tick_cta && pfm_mem) {
             CU(cudaEventRecord(e_p0, sb));
@@ -426,8 +457,8 @@ struct Engine {
     int launch_tick(bool wide) {
         last_tick_graph = false;
         if (wide || !use_graph) return enqueue(wide);
-        const int gk = (tick_cta ? 1 : 0) + (tick_bfs_nt == 1024 ? 2 : (tick_bfs_nt == 256 ? 4 : 0)) + (tick_frac ? 6 : 0);
-        if (!graph_ok[gk]) {
+        const int gk = tick_key();
+        if (!gexec.count(gk)) {
             cudaGraph_t graph = nullptr;
             CU(cudaStreamBeginCapture(sa, cudaStreamCaptureModeThreadLocal));
             const int rc = enqueue(false);
@@ -437,10 +468,11 @@ struct Engine {
                 use_graph = false;                    // capture unavailable: run the same work directly
                 return enqueue(false);
             }
-            const cudaError_t ei = cudaGraphInstantiate(&gexec[gk], graph, 0);
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t ei = cudaGraphInstantiate(&ex, graph, 0);
             cudaGraphDestroy(graph);
-            if (ei != cudaSuccess) { gexec[gk] = nullptr; use_graph = false; return enqueue(false); }
-            graph_ok[gk] = true;
+            if (ei != cudaSuccess) { use_graph = false; return enqueue(false); }
+            gexec[gk] = ex;
         }
         CU(cudaEventRecord(e_t0, sa));
         CU(cudaGraphLaunch(gexec[gk], sa));
@@ -515,15 +547,19 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     int rc;
     if ((rc = E.ensure_tables(std::max<uint32_t>(k, 1))) != MANTRA_OK) return rc;
     uint32_t bn = 0, bA = 0, bz = 0, pn = 0, plc = 0;
+    const mantra_graph* gb = nullptr;   // the tick's largest sh/sfm graph: its knobs apply
+    const mantra_graph* gp = nullptr;   // the tick's largest pfm graph
     uint64_t pwarps = 0, bsamples = 0;
     bool any_b = false, any_p = false, frac = false, dl = false;
     for (const TickItem& it : items) {
         if (it.job.opt == MANTRA_PFM) {
             any_p = true; pn = std::max(pn, it.G->n); plc = std::max(plc, it.G->dg.cbound);
+            if (!gp || it.G->n > gp->n) gp = it.G;
             pwarps += (it.job.count + 31) / 32;
         } else {
             any_b = true; bn = std::max(bn, it.G->n); bA = std::max(bA, it.G->A);
             bz = std::max(bz, it.G->dg.max_vslots);
+            if (!gb || it.G->A > gb->A) gb = it.G;
             bsamples += it.job.count;
             frac |= it.job.ob || it.job.rtb || it.job.opt == 3;
             dl |= it.job.ob || it.job.rtb;
@@ -538,14 +574,33 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     // sh/sfm CTA shape: 1024 threads for ticks of at most two samples per resident
     // 1024-thread CTA (shorter per-sample latency), else two 512-thread CTAs per SM
     // (measured on the n = 20,000 bursty graph: 1.9 vs 2.7 ms for 231 samples,
-    // 42.5 vs 40.4 ms for 26,702); MANTRA_BFS_NT=512|1024 forces one
-    {
-        int nt = bsamples <= 2ull * (uint64_t)E.bfs_grid_big ? 1024 : 512;
+    // 42.5 vs 40.4 ms for 26,702), or the shape and bitmap placement mantra_tune
+    // chose for the graph; MANTRA_BFS_NT=256|512|1024 forces a shape
+    if (any_b) {
+        const bool small = bsamples <= 2ull * (uint64_t)E.bfs_grids[2][E.bfs_rule_smem];
+        int nt = small ? 1024 : 512, sm = E.bfs_rule_smem;
+        if (gb && !small && gb->knobs.bfs_nt) nt = gb->knobs.bfs_nt;
+        if (gb && !small && gb->knobs.bfs_smem >= 0) sm = gb->knobs.bfs_smem;
         if (const char* env = std::getenv("MANTRA_BFS_NT")) {
             const int v = std::atoi(env);
             nt = v == 1024 ? 1024 : (v == 256 ? 256 : 512);
         }
+        if (!E.bfs_grids[Engine::shape_of(nt)][sm]) sm = 0;   // the placement does not fit this shape
         E.tick_bfs_nt = nt;
+        E.tick_bfs_sm = sm;
+    }
+    // pfm CTA shape and arrival-state placement: 512 threads with the state in
+    // shared memory when it fits, or the graph's tuned choice;
+    // MANTRA_PFM_CTA_NT=256 and MANTRA_PFM_CTA_SMEM=0 force the others
+    if (any_p && cta) {
+        int nt = 512, sm = E.pc_grids[1][1] ? 1 : 0;
+        if (gp && gp->knobs.pfm_nt) nt = gp->knobs.pfm_nt;
+        if (gp && gp->knobs.pfm_smem >= 0) sm = gp->knobs.pfm_smem;
+        if (const char* env = std::getenv("MANTRA_PFM_CTA_NT")) nt = std::atoi(env) == 256 ? 256 : 512;
+        if (const char* env = std::getenv("MANTRA_PFM_CTA_SMEM")) sm = env[0] == '0' ? 0 : sm;
+        if (!E.pc_grids[nt == 256 ? 0 : 1][sm]) sm = 0;
+        E.tick_pc_nt = nt;
+        E.tick_pc_sm = sm;
     }
     // host tables
     uint32_t* hdr = (uint32_t*)(E.tab_h + E.o_hdr);
@@ -1248,6 +1303,83 @@ int mantra_estimate(const mantra_graph* g, mantra_opt opt, double eps, double de
     StreamJoin join(*E, opts ? opts->stream : nullptr);
     std::vector<Problem*> ps{&p};
     return run_problems(*E, ps);
+}
+
+int mantra_tune(mantra_graph* g, mantra_tune_result* out) {
+    if (!g || !out) return MANTRA_E_INVAL;
+    Engine* E = nullptr;
+    int rc = current_engine(g, &E);
+    if (rc != MANTRA_OK) return rc;
+    // probes: fixed-r estimates with the same seed for every candidate; a
+    // candidate's time is the smaller kernel time of two runs (the first run of
+    // a configuration also allocates).  The knobs serve Algorithm 1's large
+    // rounds, so a probe is sized like one: about 100 ms of kernel time by a
+    // calibration run of the defaults, between 8 and 64 samples per SM.
+    const uint64_t r_lo = 8ull * (uint64_t)E->num_sms, r_hi = 64ull * (uint64_t)E->num_sms;
+    uint64_t r = r_lo;
+    std::vector<double> est(std::max<uint32_t>(g->n, 1));
+    auto probe = [&](mantra_opt opt, const Knobs& k, double* ms) -> int {
+        g->knobs = k;
+        mantra_opts o{};
+        o.c = 25;
+        o.fixed_r = r;
+        *ms = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
+            mantra_info I{};
+            const int st = mantra_estimate(g, opt, 0.05, 0.1, 0x7E57ull, &o, est.data(), nullptr, &I);
+            if (st != MANTRA_OK) return st;
+            *ms = std::min(*ms, I.kernel_ms);
+        }
+        return MANTRA_OK;
+    };
+    const Knobs none{};
+    Knobs best{};
+    auto size_probe = [&](mantra_opt opt) -> int {
+        r = r_lo;
+        double ms = 0;
+        const int st = probe(opt, none, &ms);
+        if (st != MANTRA_OK) return st;
+        const double per = ms > 0 ? ms / (double)r_lo : 0.0;
+        r = per > 0 ? (uint64_t)std::min<double>((double)r_hi, std::max<double>((double)r_lo, 100.0 / per)) : r_hi;
+        return MANTRA_OK;
+    };
+    // sh/sfm: CTA shape x visited-bitmap placement (shared memory only where it fits)
+    if ((rc = size_probe(MANTRA_SH)) != MANTRA_OK) { g->knobs = none; return rc; }
+    out->probe_samples = r;
+    if ((rc = probe(MANTRA_SH, none, &out->bfs_default_ms)) != MANTRA_OK) { g->knobs = none; return rc; }
+    out->bfs_ms = 1e300;
+    for (int nt : {256, 512, 1024})
+        for (int sm = 0; sm < 2; ++sm) {
+            if (!E->bfs_grids[Engine::shape_of(nt)][sm]) continue;
+            Knobs k = none;
+            k.bfs_nt = nt; k.bfs_smem = sm;
+            double ms = 0;
+            if ((rc = probe(MANTRA_SH, k, &ms)) != MANTRA_OK) { g->knobs = none; return rc; }
+            if (ms < out->bfs_ms) { out->bfs_ms = ms; best.bfs_nt = nt; best.bfs_smem = sm; }
+        }
+    // pfm (one CTA per sample): CTA shape x arrival-state placement
+    if ((rc = size_probe(MANTRA_PFM)) != MANTRA_OK) { g->knobs = none; return rc; }
+    out->pfm_probe_samples = r;
+    if ((rc = probe(MANTRA_PFM, none, &out->pfm_default_ms)) != MANTRA_OK) { g->knobs = none; return rc; }
+    out->pfm_ms = 1e300;
+    for (int nt : {256, 512})
+        for (int sm = 0; sm < 2; ++sm) {
+            if (!E->pc_grids[nt == 256 ? 0 : 1][sm]) continue;
+            Knobs k = none;
+            k.pfm_nt = nt; k.pfm_smem = sm;
+            double ms = 0;
+            if ((rc = probe(MANTRA_PFM, k, &ms)) != MANTRA_OK) { g->knobs = none; return rc; }
+            if (ms < out->pfm_ms) { out->pfm_ms = ms; best.pfm_nt = nt; best.pfm_smem = sm; }
+        }
+    g->knobs = best;
+    out->bfs_threads = (uint32_t)best.bfs_nt;
+    out->bfs_bitmap_shared = best.bfs_smem > 0 ? 1u : 0u;
+    out->pfm_threads = (uint32_t)best.pfm_nt;               // 0: the stream-scan pfm kernel is forced
+    out->pfm_state_shared = best.pfm_smem > 0 ? 1u : 0u;
+    out->bfs_resident_ctas = best.bfs_nt ? (uint32_t)E->bfs_grids[Engine::shape_of(best.bfs_nt)][best.bfs_smem] : 0u;
+    out->pfm_resident_ctas = best.pfm_nt ? (uint32_t)E->pc_grids[best.pfm_nt == 256 ? 0 : 1][best.pfm_smem] : 0u;
+    if (!best.pfm_nt) out->pfm_ms = out->pfm_default_ms;
+    return MANTRA_OK;
 }
 
 int mantra_estimate_batch(mantra_problem* probs, uint32_t count) {

@@ -47,6 +47,16 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("bfs_threads", C.c_uint32), ("bfs_bitmap_shared", C.c_uint32), ("pfm_threads", C.c_uint32),
+                ("pfm_state_shared", C.c_uint32), ("bfs_resident_ctas", C.c_uint32), ("pfm_resident_ctas", C.c_uint32),
+                ("bfs_ms", C.c_double), ("bfs_default_ms", C.c_double), ("pfm_ms", C.c_double),
+                ("pfm_default_ms", C.c_double), ("probe_samples", C.c_uint64), ("pfm_probe_samples", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Problem(C.Structure):
     _fields_ = [("graph", C.c_void_p), ("opt", C.c_int), ("eps", C.c_double), ("delta", C.c_double),
                 ("seed", C.c_uint64), ("opts", C.POINTER(Opts)), ("est_out", C.c_void_p), ("hits_out", C.c_void_p),
@@ -61,7 +71,8 @@ class TStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["mantra_graph_load", "mantra_graph_info", "mantra_graph_edges", "mantra_graph_free", "mantra_estimate", "mantra_estimate_batch",
+EXPORTS = ["mantra_graph_load", "mantra_graph_info", "mantra_graph_edges", "mantra_graph_free", "mantra_estimate",
+           "mantra_estimate_batch", "mantra_tune",
            "mantra_temporal_stats", "mantra_temporal_closeness", "mantra_sample_paths", "mantra_sample_paths_noalloc", "mantra_strerror",
            "mantra_server_create", "mantra_server_submit", "mantra_server_poll", "mantra_server_wait",
            "mantra_server_stats", "mantra_server_destroy"]
@@ -86,6 +97,7 @@ def lib():
     L.mantra_estimate.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_uint64, C.POINTER(Opts),
                                   C.c_void_p, C.c_void_p, C.POINTER(Info)]
     L.mantra_estimate_batch.argtypes = [C.POINTER(Problem), C.c_uint32]
+    L.mantra_tune.argtypes = [C.c_void_p, C.POINTER(TuneResult)]
     L.mantra_temporal_stats.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_uint64, C.c_double,
                                         C.POINTER(TStats), u64p, C.c_uint32]
     L.mantra_temporal_closeness.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_uint64, u64p, dp,
@@ -207,6 +219,13 @@ class Graph:
         _chk(lib().mantra_temporal_closeness(self.h, _opt(opt), eps, seed, r_override, _p(sm, C.c_uint64),
                                              _p(cl, C.c_double), C.byref(rs)), "mantra_temporal_closeness")
         return sm[:self.n], cl[:self.n], rs.value
+
+    def tune(self):
+        """mantra_tune: time the search kernels' launch choices on this graph
+        and keep the fastest; returns the choice and the probe times."""
+        out = TuneResult()
+        _chk(lib().mantra_tune(self.h, C.byref(out)), "mantra_tune")
+        return out.as_dict()
 
     def sample_paths(self, opt, seed, i0, count, dom_pair=D_PAIR, dom_path=D_PATH, cap=None, edges=False):
         """mantra_sample_paths -> list of (s, z, sigma, path) per sample; with
