@@ -31,8 +31,14 @@ struct Knobs {
     int bfs_nt = 0;      // sh/sfm CTA size: 256, 512 or 1024
     int bfs_smem = -1;   // visited bitmap: 1 shared memory, 0 global
     int pfm_nt = 0;      // pfm CTA size: 256 or 512
-    int pfm_smem = -1;   // pfm arrival state: 1 shared memory, 0 global
+    int pfm_mode = -1;   // pfm arrival state: 1 shared memory, 0 global, 2 global with the out-edge tiles
+                         // staged in shared memory by bulk copies
 };
+
+// Out-edges per chunk the staged pfm variant copies into shared memory (the
+// out_v and out_slot tiles, 32 KB each; a chunk with more edges is walked from
+// global memory).
+constexpr uint32_t PFM_STAGE_CAP = 8192;
 
 struct mantra_graph {
     uint32_t n = 0, A = 0, m = 0, n_uedge = 0;
@@ -205,9 +211,10 @@ struct Engine {
     int tick_bfs_sm = 0;       // its bitmap placement
     bool tick_frac = false;    // the tick has an ob or RTB problem on the sh/sfm kernel
     char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; uint32_t pfm_n = 0, pfm_lcap = 0; uint64_t pfm_warps = 0;
-    // pfm, one CTA per sample: shapes 0 = 256, 1 = 512 threads, placements as above
+    // pfm, one CTA per sample: shapes 0 = 256, 1 = 512 threads; modes 0 = state
+    // in global memory, 1 = in shared memory, 2 = global with staged edge tiles
     char* pc_mem = nullptr; PfmCtaWs pcws{}; int pc_grid = 0; uint32_t pc_n = 0, pc_cb = 0;
-    int pc_grids[2][2] = {};
+    int pc_grids[2][3] = {};
     size_t pc_smem = 0;
     int tick_pc_nt = 512, tick_pc_sm = 0;
     bool tick_cta = false;   // pfm samples of the current tick run one per CTA
@@ -254,7 +261,7 @@ struct Engine {
 
     int tick_key() const {
         return (tick_cta ? 1 : 0) | (shape_of(tick_bfs_nt) << 1) | (tick_bfs_sm << 3) | ((tick_frac ? 1 : 0) << 4) |
-               ((tick_pc_nt == 256 ? 0 : 1) << 5) | (tick_pc_sm << 6);
+               ((tick_pc_nt == 256 ? 0 : 1) << 5) | (tick_pc_sm << 6);   // tick_pc_sm: the pfm mode (2 bits)
     }
 
     // Table block layout: header | 2 work counters | unit starts (bfs, pfm) |
@@ -387,15 +394,18 @@ struct Engine {
         const size_t smem = pfm_cta_smem_bytes(n);
         const bool fit = smem + std::max(pfm_cta_static_smem(256), pfm_cta_static_smem(512)) + 1024 <= smem_optin;
         if (fit) CU(pfm_cta_configure(smem));
-        int per[2][2] = {};
+        const size_t stage = pfm_cta_stage_bytes(PFM_STAGE_CAP);
+        CU(pfm_cta_configure(std::max(fit ? smem : 0, stage)));
+        int per[2][3] = {};
         for (int s = 0; s < 2; ++s) {
             CU(pfm_cta_blocks_per_sm(nts[s], false, 0, &per[s][0]));
             if (fit) CU(pfm_cta_blocks_per_sm(nts[s], true, smem, &per[s][1]));
+            CU(pfm_cta_blocks_per_sm(nts[s], false, stage, &per[s][2]));
         }
         const size_t region = pfm_cta_region_bytes(n, cb, false, &pcws);
         int grid = 0;
         for (int s = 0; s < 2; ++s)
-            for (int p = 0; p < 2; ++p) grid = std::max(grid, num_sms * per[s][p]);
+            for (int p = 0; p < 3; ++p) grid = std::max(grid, num_sms * per[s][p]);
         grid = std::max(grid, 1);
         if (const char* env = std::getenv("MANTRA_PFM_GRID")) grid = std::max(1, std::min(grid, std::atoi(env)));
         const size_t budget = free_device_bytes() / 3;
@@ -404,7 +414,7 @@ struct Engine {
         pcws.base = pc_mem;
         pcws.stride = region;
         for (int s = 0; s < 2; ++s)
-            for (int p = 0; p < 2; ++p) pc_grids[s][p] = per[s][p] > 0 ? std::min(grid, num_sms * per[s][p]) : 0;
+            for (int p = 0; p < 3; ++p) pc_grids[s][p] = per[s][p] > 0 ? std::min(grid, num_sms * per[s][p]) : 0;
         pc_grid = pc_grids[1][fit ? 1 : 0];
         pc_smem = fit ? smem : 0;
         pc_n = n;
@@ -436,7 +446,8 @@ struct Engine {
             CU(cudaEventRecord(e_p0, sb));
             PfmCtaWs w = pcws;
             w.nt = tick_pc_nt;
-            w.fa_in_smem = tick_pc_sm;
+            w.fa_in_smem = tick_pc_sm == 1 ? 1 : 0;
+            w.stage_cap = tick_pc_sm == 2 ? PFM_STAGE_CAP : 0u;
             CU(launch_pfm_cta((const Task*)(tab_d + o_tp), (const uint64_t*)(tab_d + o_up), hdr + 1, work + 1, w,
                               pc_grids[tick_pc_nt == 256 ? 0 : 1][tick_pc_sm], sb));
             CU(cudaEventRecord(e_p1, sb));
@@ -589,15 +600,17 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
         E.tick_bfs_nt = nt;
         E.tick_bfs_sm = sm;
     }
-    // pfm CTA shape and arrival-state placement: 512 threads with the state in
-    // shared memory when it fits, or the graph's tuned choice;
-    // MANTRA_PFM_CTA_NT=256 and MANTRA_PFM_CTA_SMEM=0 force the others
+    // pfm CTA shape and arrival-state mode: 512 threads with the state in shared
+    // memory when it fits, or the graph's tuned choice; MANTRA_PFM_CTA_NT=256,
+    // MANTRA_PFM_CTA_SMEM=0 (global state) and MANTRA_PFM_STAGE=1 (global state,
+    // staged edge tiles) force the others
     if (any_p && cta) {
         int nt = 512, sm = E.pc_grids[1][1] ? 1 : 0;
         if (gp && gp->knobs.pfm_nt) nt = gp->knobs.pfm_nt;
-        if (gp && gp->knobs.pfm_smem >= 0) sm = gp->knobs.pfm_smem;
+        if (gp && gp->knobs.pfm_mode >= 0) sm = gp->knobs.pfm_mode;
         if (const char* env = std::getenv("MANTRA_PFM_CTA_NT")) nt = std::atoi(env) == 256 ? 256 : 512;
         if (const char* env = std::getenv("MANTRA_PFM_CTA_SMEM")) sm = env[0] == '0' ? 0 : sm;
+        if (const char* env = std::getenv("MANTRA_PFM_STAGE")) sm = env[0] == '1' ? 2 : (sm == 2 ? 0 : sm);
         if (!E.pc_grids[nt == 256 ? 0 : 1][sm]) sm = 0;
         E.tick_pc_nt = nt;
         E.tick_pc_sm = sm;
@@ -1363,21 +1376,22 @@ int mantra_tune(mantra_graph* g, mantra_tune_result* out) {
     if ((rc = probe(MANTRA_PFM, none, &out->pfm_default_ms)) != MANTRA_OK) { g->knobs = none; return rc; }
     out->pfm_ms = 1e300;
     for (int nt : {256, 512})
-        for (int sm = 0; sm < 2; ++sm) {
+        for (int sm = 0; sm < 3; ++sm) {
             if (!E->pc_grids[nt == 256 ? 0 : 1][sm]) continue;
             Knobs k = none;
-            k.pfm_nt = nt; k.pfm_smem = sm;
+            k.pfm_nt = nt; k.pfm_mode = sm;
             double ms = 0;
             if ((rc = probe(MANTRA_PFM, k, &ms)) != MANTRA_OK) { g->knobs = none; return rc; }
-            if (ms < out->pfm_ms) { out->pfm_ms = ms; best.pfm_nt = nt; best.pfm_smem = sm; }
+            if (ms < out->pfm_ms) { out->pfm_ms = ms; best.pfm_nt = nt; best.pfm_mode = sm; }
         }
     g->knobs = best;
     out->bfs_threads = (uint32_t)best.bfs_nt;
     out->bfs_bitmap_shared = best.bfs_smem > 0 ? 1u : 0u;
     out->pfm_threads = (uint32_t)best.pfm_nt;               // 0: the stream-scan pfm kernel is forced
-    out->pfm_state_shared = best.pfm_smem > 0 ? 1u : 0u;
+    out->pfm_state_shared = best.pfm_mode == 1 ? 1u : 0u;
+    out->pfm_staged = best.pfm_mode == 2 ? 1u : 0u;
     out->bfs_resident_ctas = best.bfs_nt ? (uint32_t)E->bfs_grids[Engine::shape_of(best.bfs_nt)][best.bfs_smem] : 0u;
-    out->pfm_resident_ctas = best.pfm_nt ? (uint32_t)E->pc_grids[best.pfm_nt == 256 ? 0 : 1][best.pfm_smem] : 0u;
+    out->pfm_resident_ctas = best.pfm_nt ? (uint32_t)E->pc_grids[best.pfm_nt == 256 ? 0 : 1][best.pfm_mode] : 0u;
     if (!best.pfm_nt) out->pfm_ms = out->pfm_default_ms;
     return MANTRA_OK;
 }

@@ -48,6 +48,41 @@ __device__ __forceinline__ uint32_t ldv(const uint32_t* p) {
     return __ldcg(p);
 }
 
+// ---- bulk copies (TMA engine) of out-edge tiles into shared memory ----
+// One mbarrier per CTA tracks a chunk's copies by their byte count (expect_tx
+// by one thread, complete_tx by every copy).  Addresses and sizes are 16-byte
+// multiples by construction (see the staged table).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Waits for the mbarrier phase with the given parity, at most about a second
+// of polls (each poll may suspend the thread for a while); false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 // PC_NT threads per CTA, 1024 / PC_NT CTAs per SM at 64 registers.
 template <int PC_NT, bool FA_SMEM>
 __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tasks, const uint64_t* unit_start,
@@ -67,7 +102,14 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
     __shared__ u64 sh_sigma;
     __shared__ uint32_t sh_nt;
     __shared__ uint32_t cs_off[CHUNK + 1], cs_first[CHUNK], cs_u[CHUNK];   // range table of a chunk
-    extern __shared__ __align__(16) uint32_t pc_dyn[];
+    __shared__ __align__(8) uint64_t sh_mbar;     // completion of a chunk's staged edge tiles
+    extern __shared__ __align__(128) uint32_t pc_dyn[];
+    // global-state variant with staging: out_v and out_slot tiles of a chunk's
+    // ranges, ws.stage_cap entries each, filled by bulk copies
+    uint32_t* const stg_v = pc_dyn;
+    uint32_t* const stg_s = pc_dyn + ws.stage_cap;
+    const bool stage = !FA_SMEM && ws.stage_cap > 0;
+    uint32_t stage_par = 0;                        // parity of the mbarrier phase to wait for
 
     char* region = ws.base + (size_t)blockIdx.x * ws.stride;
     uint32_t* fsl = FA_SMEM ? pc_dyn : reinterpret_cast<uint32_t*>(region + ws.o_fa);
@@ -91,6 +133,10 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
     u64 my_escan = 0, my_eadd = 0, my_x = 0, my_rounds = 0;   // my_x, my_rounds: thread 0
     // the next-frontier bitmap is all zero between samples (compaction clears what it reads)
     for (uint32_t w = tid; w < ws.bits_words; w += PC_NT) NB[w] = 0u;
+    if (tid == 0 && stage) {
+        mbar_init(&sh_mbar, 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
 
     // Compacts the next-frontier bitmap (nwords words) into out in vertex order
@@ -154,6 +200,45 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
         const uint32_t Gc = (uint32_t)(tot >> 32), E = (uint32_t)tot;
         if (tid == 0) { cs_off[Gc] = E; sh_Gc = Gc; }
         __syncthreads();
+        return E;
+    };
+
+    // As table, and with staging on, the ranges' out_v / out_slot entries are
+    // copied into the shared tiles by bulk copies when the chunk's tiles fit:
+    // a range [lo, hi) is copied as [lo & ~3, (hi + 3) & ~3) (16-byte aligned
+    // start, length a multiple of 16 bytes; the store's arrays start 256-byte
+    // aligned in one allocation, so the rounded copy stays inside it), and
+    // cs_first then indexes the tiles.  *staged tells which.  Barriers inside.
+    auto table_staged = [&](const uint32_t (&u)[2], const uint32_t (&lo)[2], const uint32_t (&hi)[2],
+                            const uint32_t* g_out_v, const uint32_t* g_out_slot, bool* staged) -> uint32_t {
+        const uint32_t c0 = hi[0] > lo[0] ? hi[0] - lo[0] : 0u, c1 = hi[1] > lo[1] ? hi[1] - lo[1] : 0u;
+        const uint32_t nr = (c0 > 0) + (c1 > 0);
+        const uint32_t a0 = lo[0] & ~3u, a1 = lo[1] & ~3u;
+        const uint32_t s0 = c0 > 0 ? ((hi[0] + 3u) & ~3u) - a0 : 0u, s1 = c1 > 0 ? ((hi[1] + 3u) & ~3u) - a1 : 0u;
+        u64 tot;
+        const u64 ex = block_exclusive_scan64<PC_NT>(((u64)nr << 32) | (c0 + c1), &tot, sm_scan64);
+        uint32_t stot;
+        const uint32_t so = block_exclusive_scan<PC_NT>(s0 + s1, &stot, sm_scan32);   // tile offsets (entries)
+        const bool st = stot > 0 && stot <= ws.stage_cap;                               // block-uniform
+        if (st) {
+            fence_proxy_async_smem();   // the previous chunk's tile reads (before the scans' barriers) come first
+            if (tid == 0) mbar_arrive_expect_tx(&sh_mbar, stot * 8u);
+            if (s0) {
+                bulk_g2s(stg_v + so, g_out_v + a0, s0 * 4u, &sh_mbar);
+                bulk_g2s(stg_s + so, g_out_slot + a0, s0 * 4u, &sh_mbar);
+            }
+            if (s1) {
+                bulk_g2s(stg_v + so + s0, g_out_v + a1, s1 * 4u, &sh_mbar);
+                bulk_g2s(stg_s + so + s0, g_out_slot + a1, s1 * 4u, &sh_mbar);
+            }
+        }
+        uint32_t gi = (uint32_t)(ex >> 32), e = (uint32_t)ex;
+        if (c0 > 0) { cs_first[gi] = st ? so + (lo[0] - a0) : lo[0]; cs_off[gi] = e; cs_u[gi] = u[0]; ++gi; e += c0; }
+        if (c1 > 0) { cs_first[gi] = st ? so + s0 + (lo[1] - a1) : lo[1]; cs_off[gi] = e; cs_u[gi] = u[1]; }
+        const uint32_t Gc = (uint32_t)(tot >> 32), E = (uint32_t)tot;
+        if (tid == 0) { cs_off[Gc] = E; sh_Gc = Gc; }
+        __syncthreads();
+        *staged = st;
         return E;
     };
 
@@ -270,12 +355,41 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                         atomicOr(XB + (u[j] >> 5), 1u << (u[j] & 31));
                     }
                 }
-                const uint32_t E = table(u, rl, rh);
-                if (tid == 0) my_x += E;
-                expand(E, out_v, out_slot, [&](uint32_t, uint32_t v, uint32_t sl) {
+                auto relax = [&](uint32_t, uint32_t v, uint32_t sl) {
                     if (v == s || sl >= ldv<FA_SMEM>(fsl + v)) return;
                     if (sl < atomicMin(fsl + v, sl)) atomicOr(NB + (v >> 5), 1u << (v & 31));
-                });
+                };
+                if (stage) {
+                    bool staged = false;
+                    const uint32_t E = table_staged(u, rl, rh, out_v, out_slot, &staged);
+                    if (tid == 0) my_x += E;
+                    if (!staged) {
+                        expand(E, out_v, out_slot, relax);
+                    } else {
+                        // every thread waits for the chunk's tiles; a wait that runs out
+                        // reports a timeout, waits once more for the copies in flight and
+                        // ends the CTA (block-uniform)
+                        const bool ok = mbar_wait_bounded(&sh_mbar, stage_par);
+                        if (__syncthreads_or(!ok)) {
+                            if (tid == 0) set_status(job.status, ST_TIMEOUT);
+                            mbar_wait_bounded(&sh_mbar, stage_par);
+                            __syncthreads();
+                            return;
+                        }
+                        stage_par ^= 1u;
+                        const uint32_t per = ((E + PC_NW * 32u - 1u) / (PC_NW * 32u)) * 32u;
+                        const uint32_t w_lo = min((uint32_t)wid * per, E), w_hi = min(w_lo + per, E);
+                        lbs_walk_batched<WALK_K, false>(cs_off, sh_Gc, cs_first, w_lo, w_hi, stg_v, stg_s,
+                                                        [&](uint32_t r, uint32_t, uint32_t v, uint32_t sl) {
+                                                            relax(cs_u[r], v, sl);
+                                                        });
+                        __syncthreads();
+                    }
+                } else {
+                    const uint32_t E = table(u, rl, rh);
+                    if (tid == 0) my_x += E;
+                    expand(E, out_v, out_slot, relax);
+                }
             }
             if (!full) {
                 const uint32_t fz = ldv<FA_SMEM>(fsl + z);
@@ -691,6 +805,10 @@ size_t pfm_cta_region_bytes(uint32_t n, uint32_t dag_cap, bool fa_in_smem, PfmCt
 // Dynamic shared memory of the variant with the arrival state in shared memory.
 size_t pfm_cta_smem_bytes(uint32_t n) { return ((size_t)n + 2 * ((n + 31) / 32)) * 4; }
 
+// Dynamic shared memory of the global-state variant's staged edge tiles
+// (out_v and out_slot, cap entries each; cap a multiple of 4).
+size_t pfm_cta_stage_bytes(uint32_t cap) { return (size_t)cap * 8; }
+
 // Static shared memory of the kernel (range table, task copy, scratch).
 size_t pfm_cta_static_smem(int nt) {
     cudaFuncAttributes a{};
@@ -710,30 +828,33 @@ cudaError_t pfm_cta_configure(size_t smem) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
     if (smem <= configured[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_pfm_cta<512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pfm_cta<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) configured[dev] = smem;
-    return e;
+    const void* ks[4] = {(const void*)k_pfm_cta<512, true>, (const void*)k_pfm_cta<256, true>,
+                         (const void*)k_pfm_cta<512, false>, (const void*)k_pfm_cta<256, false>};
+    for (const void* k : ks) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    configured[dev] = smem;
+    return cudaSuccess;
 }
 
 cudaError_t pfm_cta_blocks_per_sm(int nt, bool fa_in_smem, size_t smem, int* out) {
     if (nt == 256)
         return fa_in_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<256, true>, 256, smem)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<256, false>, 256, 0);
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<256, false>, 256, smem);
     return fa_in_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<512, true>, 512, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<512, false>, 512, 0);
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<512, false>, 512, smem);
 }
 
 cudaError_t launch_pfm_cta(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
                            const PfmCtaWs& ws, int grid, cudaStream_t st) {
-    const size_t smem = ws.fa_in_smem ? pfm_cta_smem_bytes(ws.n_cap) : 0;
+    const size_t smem = ws.fa_in_smem ? pfm_cta_smem_bytes(ws.n_cap) : pfm_cta_stage_bytes(ws.stage_cap);
     if (ws.nt == 256) {
         if (ws.fa_in_smem) k_pfm_cta<256, true><<<grid, 256, smem, st>>>(tasks, unit_start, ntasks, work, ws);
-        else k_pfm_cta<256, false><<<grid, 256, 0, st>>>(tasks, unit_start, ntasks, work, ws);
+        else k_pfm_cta<256, false><<<grid, 256, smem, st>>>(tasks, unit_start, ntasks, work, ws);
     } else {
         if (ws.fa_in_smem) k_pfm_cta<512, true><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
-        else k_pfm_cta<512, false><<<grid, 512, 0, st>>>(tasks, unit_start, ntasks, work, ws);
+        else k_pfm_cta<512, false><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
     }
     return cudaGetLastError();
 }

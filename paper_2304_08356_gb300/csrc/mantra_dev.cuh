@@ -461,8 +461,10 @@ __device__ __forceinline__ void lbs_walk(const uint32_t* off, uint32_t Gc, uint3
 // and edge index of every edge of the K windows come from the table first
 // (shared memory), then pa[e] and pb[e] are loaded for all of them, then
 // edge(g, e, pa[e], pb[e]) runs for each valid edge -- K times the loads in
-// flight per warp.  first[g] is the first edge of range g.
-template <int K, typename F>
+// flight per warp.  first[g] is the first edge of range g.  RO: pa and pb
+// are read-only for the kernel's lifetime (read-only data path); otherwise
+// plain loads (e.g. shared-memory tiles).
+template <int K, bool RO = true, typename F>
 __device__ __forceinline__ void lbs_walk_batched(const uint32_t* off, uint32_t Gc, const uint32_t* first, uint32_t w_lo,
                                                  uint32_t w_hi, const uint32_t* __restrict__ pa,
                                                  const uint32_t* __restrict__ pb, F edge) {
@@ -496,8 +498,13 @@ __device__ __forceinline__ void lbs_walk_batched(const uint32_t* off, uint32_t G
         uint32_t va[K], vb[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            va[k] = ok[k] ? __ldg(pa + ee[k]) : 0u;
-            vb[k] = ok[k] ? __ldg(pb + ee[k]) : 0u;
+            if constexpr (RO) {
+                va[k] = ok[k] ? __ldg(pa + ee[k]) : 0u;
+                vb[k] = ok[k] ? __ldg(pb + ee[k]) : 0u;
+            } else {
+                va[k] = ok[k] ? pa[ee[k]] : 0u;
+                vb[k] = ok[k] ? pb[ee[k]] : 0u;
+            }
         }
 #pragma unroll
         for (int k = 0; k < K; ++k)
@@ -644,6 +651,7 @@ struct PfmCtaWs {
     uint32_t bits_words; // words of each bitmap: ceil(n_cap / 32)
     int fa_in_smem;      // arrival slots and bitmaps in dynamic shared memory
     int nt;              // threads per CTA (256 or 512)
+    uint32_t stage_cap;  // global-state variant: out-edges per chunk staged in shared memory by bulk copies (0: none)
 };
 
 size_t bfs_region_bytes(uint32_t n, uint32_t A, uint32_t zcap, bool bits_in_smem, bool dl, BfsWs* ws);
@@ -662,6 +670,7 @@ cudaError_t launch_pfm(const Task* tasks, const uint64_t* unit_start, const uint
                        const PfmWs& ws, int grid, bool wide, cudaStream_t st);
 size_t pfm_cta_region_bytes(uint32_t n, uint32_t dag_cap, bool fa_in_smem, PfmCtaWs* ws);
 size_t pfm_cta_smem_bytes(uint32_t n);
+size_t pfm_cta_stage_bytes(uint32_t cap);
 size_t pfm_cta_static_smem(int nt);
 cudaError_t pfm_cta_configure(size_t smem);
 cudaError_t pfm_cta_blocks_per_sm(int nt, bool fa_in_smem, size_t smem, int* out);

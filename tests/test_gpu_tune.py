@@ -39,10 +39,14 @@ def test_bfs_shapes_and_placements_equal_oracle(M, bursty, monkeypatch, nt, smem
 
 
 @pytest.mark.parametrize("nt", ["256", "512"])
-@pytest.mark.parametrize("smem", ["0", "1"])
+@pytest.mark.parametrize("smem", ["0", "1", "staged"])
 def test_pfm_cta_shapes_and_placements_equal_oracle(M, bursty, monkeypatch, nt, smem):
+    """Arrival state in shared memory, in global memory, and in global memory
+    with each chunk's out-edge tiles copied into shared memory by bulk copies
+    (chunks whose tiles exceed the staging capacity walk global memory)."""
     monkeypatch.setenv("MANTRA_PFM_CTA_NT", nt)
-    monkeypatch.setenv("MANTRA_PFM_CTA_SMEM", smem)
+    monkeypatch.setenv("MANTRA_PFM_CTA_SMEM", "0" if smem == "staged" else smem)
+    monkeypatch.setenv("MANTRA_PFM_STAGE", "1" if smem == "staged" else "0")
     g = M.Graph(*bursty)
     o = O.Graph(*bursty)
     _, hits, info = g.estimate(2, 0.05, 0.1, 3, fixed_r=2000)
@@ -57,7 +61,7 @@ def test_tuned_estimates_equal_untuned(M, bursty):
     before = {opt: g.estimate(opt, 0.05, 0.1, 11)[1:] for opt in (0, 1, 2, 3)}
     res = g.tune()
     assert res["bfs_threads"] in (256, 512, 1024) and res["pfm_threads"] in (256, 512)
-    assert res["bfs_bitmap_shared"] in (0, 1) and res["pfm_state_shared"] in (0, 1)
+    assert res["bfs_bitmap_shared"] in (0, 1) and res["pfm_state_shared"] in (0, 1) and res["pfm_staged"] in (0, 1)
     assert res["bfs_resident_ctas"] > 0 and res["pfm_resident_ctas"] > 0 and res["probe_samples"] >= 1024
     for k in ("bfs_ms", "bfs_default_ms", "pfm_ms", "pfm_default_ms"):
         assert 0.0 < res[k] < 1e6, k
