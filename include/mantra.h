@@ -48,7 +48,8 @@ enum {
     MANTRA_E_NOMEM = 2,    /* device or host allocation failed */
     MANTRA_E_OVERFLOW = 3, /* a path count sigma_sz exceeded 2^128 - 1 */
     MANTRA_E_CUDA = 4,     /* a CUDA runtime call failed */
-    MANTRA_E_TIMEOUT = 5,  /* reserved: a bounded device wait gave up */
+    MANTRA_E_TIMEOUT = 5,  /* a bounded wait gave up: the staged pfm variant's wait for its bulk copies,
+                              or mantra_server_wait */
     MANTRA_E_CHECK = 6,    /* an internal consistency check failed on the device */
     MANTRA_E_RNG = 7,      /* 65536 consecutive rejections in a uniform draw */
     MANTRA_PENDING = 8     /* serving: the request has not finished yet (not an error) */

@@ -133,16 +133,25 @@ __device__ __forceinline__ void bfs_ob_update(const DevGraph& g, const Job& job,
         __syncthreads();
     }
     // through counts per vertex; the first touch of v lists it (VB marks)
-    for (uint32_t lv = 1; lv < d; ++lv)
-        for (uint32_t p = lev[lv] + tid; p < lev[lv + 1]; p += BFS_NT) {
-            const Sig x = ldcg_sig(dl + p);
-            if (x == (Sig)0) continue;
-            const uint32_t a = F[p], v = g.slot_v[a];
-            const Sig sp = sigma_at(sig, F, g.slot_v, p, lev[lv]);
-            SigOps<WIDE>::atomic_add(acc + v, (Sig)(sp * x));   // <= sigma_sz: no wrap
-            const uint32_t bit = 1u << (v & 31);
-            if (!(atomicOr(VB + (v >> 5), bit) & bit)) tl[atomicAdd(sh_nt, 1u)] = v;
+    // (a vertex's states of a level sit on consecutive lanes: one atomic per run)
+    for (uint32_t lv = 1; lv < d; ++lv) {
+        const uint32_t pe = lev[lv + 1];
+        for (uint32_t p0 = lev[lv] + (uint32_t)(tid & ~31); p0 < pe; p0 += BFS_NT) {
+            const uint32_t p = p0 + lane;
+            uint32_t v = NONE;
+            Sig val = (Sig)0;
+            if (p < pe) {
+                const Sig x = ldcg_sig(dl + p);
+                v = g.slot_v[F[p]];
+                if (x != (Sig)0) val = (Sig)(sigma_at(sig, F, g.slot_v, p, lev[lv]) * x);   // <= sigma_sz: no wrap
+            }
+            warp_run_add<Sig>(v, val, [&](uint32_t vv, Sig tot) {
+                SigOps<WIDE>::atomic_add(acc + vv, tot);
+                const uint32_t bit = 1u << (vv & 31);
+                if (!(atomicOr(VB + (vv >> 5), bit) & bit)) tl[atomicAdd(sh_nt, 1u)] = vv;
+            });
         }
+    }
     __syncthreads();
     const uint32_t T = *sh_nt;
     u64 my_sum = 0;
@@ -212,11 +221,19 @@ __device__ __forceinline__ void bfs_rtb_update(const DevGraph& g, const Job& job
         if (dv[v] != k) return false;
         return !sfm || p == lev[k] || g.slot_v[F[p - 1]] != v;
     };
-    for (uint32_t k = 1; k <= D; ++k)
-        for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
-            const uint32_t a = F[p], v = g.slot_v[a];
-            if (is_end(p, k, v)) SigOps<WIDE>::atomic_add(sv + v, sigma_at(sig, F, g.slot_v, p, lev[k]));
+    for (uint32_t k = 1; k <= D; ++k) {
+        const uint32_t pe = lev[k + 1];
+        for (uint32_t p0 = lev[k] + (uint32_t)(tid & ~31); p0 < pe; p0 += BFS_NT) {   // one atomic per run
+            const uint32_t p = p0 + lane;
+            uint32_t v = NONE;
+            Sig val = (Sig)0;
+            if (p < pe) {
+                v = g.slot_v[F[p]];
+                if (is_end(p, k, v)) val = sigma_at(sig, F, g.slot_v, p, lev[k]);
+            }
+            warp_run_add<Sig>(v, val, [&](uint32_t vv, Sig tot) { SigOps<WIDE>::atomic_add(sv + vv, tot); });
         }
+    }
     __syncthreads();
     auto eps_of = [&](uint32_t p, uint32_t k, uint32_t v) -> u64 {
         return is_end(p, k, v) ? ob_q(SigOps<WIDE>::wide(sigma_at(sig, F, g.slot_v, p, lev[k])),
@@ -251,16 +268,23 @@ __device__ __forceinline__ void bfs_rtb_update(const DevGraph& g, const Job& job
         __syncthreads();
     }
     // per-vertex dependency sums (X minus the endpoint share)
-    for (uint32_t k = 1; k <= D; ++k)
-        for (uint32_t p = lev[k] + tid; p < lev[k + 1]; p += BFS_NT) {
-            const uint32_t a = F[p], v = g.slot_v[a];
-            if (v == s) continue;
-            const u64 d = __ldcg(reinterpret_cast<const unsigned long long*>(dl + p)) - eps_of(p, k, v);
-            if (!d) continue;
-            atomicAdd(dsum + v, d);
-            const uint32_t bit = 1u << (v & 31);
-            if (!(atomicOr(VB + (v >> 5), bit) & bit)) tl[atomicAdd(sh_nt, 1u)] = v;
+    for (uint32_t k = 1; k <= D; ++k) {
+        const uint32_t pe = lev[k + 1];
+        for (uint32_t p0 = lev[k] + (uint32_t)(tid & ~31); p0 < pe; p0 += BFS_NT) {   // one atomic per run
+            const uint32_t p = p0 + lane;
+            uint32_t v = NONE;
+            u64 val = 0;
+            if (p < pe) {
+                v = g.slot_v[F[p]];
+                if (v != s) val = __ldcg(reinterpret_cast<const unsigned long long*>(dl + p)) - eps_of(p, k, v);
+            }
+            warp_run_add<u64>(v, val, [&](uint32_t vv, u64 tot) {
+                atomicAdd(dsum + vv, tot);
+                const uint32_t bit = 1u << (vv & 31);
+                if (!(atomicOr(VB + (vv >> 5), bit) & bit)) tl[atomicAdd(sh_nt, 1u)] = vv;
+            });
         }
+    }
     __syncthreads();
     const uint32_t T = *sh_nt;
     u64 my_sum = 0;

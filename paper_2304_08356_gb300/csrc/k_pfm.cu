@@ -393,22 +393,33 @@ __global__ void __launch_bounds__(PFM_NT) k_pfm(const Task* tasks, const uint64_
             if (WIDE) set_status(job.status, ST_OVERFLOW);
             else push_overflow(job, i);
         }
-        if (have && !ovf && !err) {
-            const uint32_t nint = family_count(job, len);
-            if (job.hits && nint > 0) {
-                uint32_t w4[4];
-                philox_block(job.seed, i, DOM_RADE, 0, w4);
-                for (uint32_t k = 0; k < nint; ++k) {
-                    const uint32_t x = family_item(job, g, path, pathe, k);
-                    atomicAdd(job.hits + x, 1ull);
-                    if (job.S)
-                        for (uint32_t jj = 0; jj < job.c; ++jj) {
-                            const int lam = ((w4[jj >> 5] >> (jj & 31)) & 1u) ? 1 : -1;
-                            atomicAdd(job.S + (size_t)jj * job.fam + x, lam);
-                        }
-                }
-                atomicAdd(job.ctr + C_SUMINT, (u64)nint);
+        // ---- hits and Rademacher sums of the warp's 32 samples, warp-aggregated:
+        // in step k every lane adds its path's k-th entry; lanes adding to the
+        // same entry combine (their count, and per trial the sum of their
+        // signs), and one lane issues the atomic ----
+        {
+            const uint32_t nint = (have && !ovf && !err && job.hits) ? family_count(job, len) : 0u;
+            uint32_t w4[4] = {0u, 0u, 0u, 0u};
+            if (nint > 0) philox_block(job.seed, i, DOM_RADE, 0, w4);
+            const uint32_t kmax = __reduce_max_sync(FULL, nint);
+            for (uint32_t k = 0; k < kmax; ++k) {
+                const bool act = k < nint;
+                const uint32_t x = act ? family_item(job, g, path, pathe, k) : 0u;
+                const u64 key = act ? (u64)x : ((1ull << 32) | (u64)lane);   // idle lanes never match
+                const unsigned grp = __match_any_sync(FULL, key);
+                const bool lead = act && lane == __ffs(grp) - 1;
+                if (lead) atomicAdd(job.hits + x, (u64)__popc(grp));
+                if (job.S)
+                    for (uint32_t jj = 0; jj < job.c; ++jj) {
+                        const unsigned plus = __ballot_sync(FULL, act && ((w4[jj >> 5] >> (jj & 31)) & 1u));
+                        const int sum = 2 * __popc(grp & plus) - __popc(grp);   // lambda = +1 / -1 per lane
+                        if (lead && sum) atomicAdd(job.S + (size_t)jj * job.fam + x, sum);
+                    }
             }
+            const uint32_t tot = __reduce_add_sync(FULL, nint);
+            if (lane == 0 && tot) atomicAdd(job.ctr + C_SUMINT, (u64)tot);
+        }
+        if (have && !ovf && !err) {
             if (job.rec_len) {
                 const uint64_t r = i - job.i0;
                 job.rec_s[r] = s; job.rec_z[r] = z;

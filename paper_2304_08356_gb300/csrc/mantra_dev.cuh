@@ -265,10 +265,35 @@ __device__ __forceinline__ u128 shfl_idx_w(u128 x, int l) {
     const u64 lo = __shfl_sync(0xFFFFFFFFu, (u64)x, l), hi = __shfl_sync(0xFFFFFFFFu, (u64)(x >> 64), l);
     return ((u128)hi << 64) | lo;
 }
+__device__ __forceinline__ u64 shfl_down_w(u64 x, int o) { return __shfl_down_sync(0xFFFFFFFFu, x, o); }
+__device__ __forceinline__ u128 shfl_down_w(u128 x, int o) {
+    const u64 lo = __shfl_down_sync(0xFFFFFFFFu, (u64)x, o), hi = __shfl_down_sync(0xFFFFFFFFu, (u64)(x >> 64), o);
+    return ((u128)hi << 64) | lo;
+}
 __device__ __forceinline__ u64 shfl_xor_w(u64 x, int o) { return __shfl_xor_sync(0xFFFFFFFFu, x, o); }
 __device__ __forceinline__ u128 shfl_xor_w(u128 x, int o) {
     const u64 lo = __shfl_xor_sync(0xFFFFFFFFu, (u64)x, o), hi = __shfl_xor_sync(0xFFFFFFFFu, (u64)(x >> 64), o);
     return ((u128)hi << 64) | lo;
+}
+
+// Warp-aggregated addition for runs of lanes: consecutive lanes holding the
+// same key form a run (a frontier lists a vertex's states next to each other),
+// a segmented reduction over each run sums their values, and the run's first
+// lane calls add(key, total) -- one atomic per run instead of one per lane.
+// Lanes with nothing to add pass x = 0 (whatever their key, they change no
+// total).  Every lane of the warp calls it.
+template <typename T, typename AddF>
+__device__ __forceinline__ void warp_run_add(uint32_t key, T x, AddF add) {
+    const int lane = threadIdx.x & 31;
+    T sum = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = shfl_down_w(sum, o);
+        const uint32_t ky = __shfl_down_sync(0xFFFFFFFFu, key, o);
+        if (lane + o < 32 && ky == key) sum += y;
+    }
+    const uint32_t kp = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+    if ((lane == 0 || kp != key) && sum != (T)0) add(key, sum);
 }
 
 // Inclusive warp scan of unsigned path counts (callers guarantee no wrap).
