@@ -486,6 +486,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000, help="serving leg: requests")
     ap.add_argument("--serve-nmax", type=int, default=200000, help="serving leg: largest graph's n")
     ap.add_argument("--no-large", action="store_true", help="skip the n = 10^6, m = 2*10^7 leg")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="run the bench graph with the default launch choices (no mantra_tune probes)")
     ap.add_argument("--no-batch256", action="store_true", help="skip the 256-graph batching leg")
     ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
                     help="batched: one mantra_estimate_batch over the optimalities per step; "
@@ -512,7 +514,7 @@ def main():
 
     u, v, t = workload()
     g = M.Graph(u, v, t)
-    tuned = g.tune()          # the autotuner's launch choices for this graph (results do not depend on them)
+    tuned = None if args.no_tune else g.tune()   # the autotuner's launch choices (results do not depend on them)
     stream = torch.cuda.Stream()
     est_dev = torch.empty(g.n, dtype=torch.float64, device="cuda")
     hits_dev = torch.empty(g.n, dtype=torch.int64, device="cuda")
