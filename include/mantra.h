@@ -228,8 +228,10 @@ int mantra_estimate_batch(mantra_problem* probs, uint32_t count);
  *     at once per SM, and the frontier tile a CTA scans per pass) x the
  *     visited bitmap in shared or in global memory (shared only where it fits);
  *   pfm (CTA kernel): CTA size 256 or 512 x the arrival state in shared
- *     memory, in global memory, or in global memory with each chunk's
- *     out-edge tiles copied into shared memory by bulk (TMA) copies.
+ *     memory (as 32-bit arrival slots, or as 16-bit offsets within each
+ *     vertex's slots when no vertex has more than 65,534 slots), in global
+ *     memory, or in global memory with each chunk's out-edge tiles copied
+ *     into shared memory by bulk (TMA) copies.
  * A probe is sized like one of Algorithm 1's large rounds: about 100 ms of
  * kernel time by a calibration run of the defaults, between 8 and 64 samples
  * per SM.  Every candidate runs within the same workspace, whose size is bounded by
@@ -250,7 +252,7 @@ typedef struct {
     uint64_t probe_samples;      /* samples per sh probe run */
     uint64_t pfm_probe_samples;  /* samples per pfm probe run */
     uint32_t pfm_staged;         /* 1: global state with the edge tiles staged by bulk copies */
-    uint32_t pad_;
+    uint32_t pfm_state16;        /* 1: the shared arrival state as 16-bit slot offsets */
 } mantra_tune_result;
 
 int mantra_tune(mantra_graph* g, mantra_tune_result* out);

@@ -76,6 +76,8 @@ int upload_store(const StoreHost& H, mantra_graph* G, cudaStream_t st) {
     dst[SA_IN_SLOT] = &G->dg.in_slot;   dst[SA_ST_U] = &G->dg.st_u;         dst[SA_ST_V] = &G->dg.st_v;
     dst[SA_ST_T] = &G->dg.st_t;         dst[SA_TMAX_IN] = &G->dg.tmax_in;   dst[SA_TMIN_OUT] = &G->dg.tmin_out;
     dst[SA_IN_UEDGE] = &G->dg.in_uedge; dst[SA_SLOT_NOUT] = &G->dg.slot_nout;
+    const uint32_t* loff_words = nullptr;   // 16-bit entries, two per word
+    dst[SA_OUT_LOFF] = &loff_words;
     size_t total = 0;
     for (int k = 0; k < SA_COUNT; ++k) total += al256((H.len[k] + 1) * 4);
     if (cudaMalloc(&G->dmem, total) != cudaSuccess) return MANTRA_E_NOMEM;
@@ -87,6 +89,7 @@ int upload_store(const StoreHost& H, mantra_graph* G, cudaStream_t st) {
         off += al256((H.len[k] + 1) * 4);
     }
     CU(cudaStreamSynchronize(st));
+    G->dg.out_loff = reinterpret_cast<const unsigned short*>(loff_words);
     G->n = H.n; G->m = H.m; G->A = H.A; G->n_uedge = H.n_uedge;
     G->self_loops = H.self_loops; G->duplicates = H.duplicates;
     G->dg.n = H.n; G->dg.A = H.A; G->dg.m = H.m; G->dg.n_uedge = H.n_uedge;
@@ -212,9 +215,10 @@ struct Engine {
     bool tick_frac = false;    // the tick has an ob or RTB problem on the sh/sfm kernel
     char* pfm_mem = nullptr; PfmWs pws{}; int pfm_grid = 0; uint32_t pfm_n = 0, pfm_lcap = 0; uint64_t pfm_warps = 0;
     // pfm, one CTA per sample: shapes 0 = 256, 1 = 512 threads; modes 0 = state
-    // in global memory, 1 = in shared memory, 2 = global with staged edge tiles
+    // in global memory, 1 = in shared memory, 2 = global with staged edge tiles,
+    // 3 = in shared memory as 16-bit slot offsets
     char* pc_mem = nullptr; PfmCtaWs pcws{}; int pc_grid = 0; uint32_t pc_n = 0, pc_cb = 0;
-    int pc_grids[2][3] = {};
+    int pc_grids[2][4] = {};
     size_t pc_smem = 0;
     int tick_pc_nt = 512, tick_pc_sm = 0;
     bool tick_cta = false;   // pfm samples of the current tick run one per CTA
@@ -391,21 +395,22 @@ struct Engine {
         cb = std::max(cb, pc_cb);
         if (pc_mem) { cudaStreamSynchronize(sb); cudaStreamSynchronize(sa); cudaFree(pc_mem); pc_mem = nullptr; }
         const int nts[2] = {256, 512};
-        const size_t smem = pfm_cta_smem_bytes(n);
-        const bool fit = smem + std::max(pfm_cta_static_smem(256), pfm_cta_static_smem(512)) + 1024 <= smem_optin;
-        if (fit) CU(pfm_cta_configure(smem));
+        const size_t smem = pfm_cta_smem_bytes(n, false), smem16 = pfm_cta_smem_bytes(n, true);
+        const size_t stat = std::max(pfm_cta_static_smem(256), pfm_cta_static_smem(512)) + 1024;
+        const bool fit = smem + stat <= smem_optin, fit16 = smem16 + stat <= smem_optin;
         const size_t stage = pfm_cta_stage_bytes(PFM_STAGE_CAP);
-        CU(pfm_cta_configure(std::max(fit ? smem : 0, stage)));
-        int per[2][3] = {};
+        CU(pfm_cta_configure(std::max({fit ? smem : 0, fit16 ? smem16 : 0, stage})));
+        int per[2][4] = {};
         for (int s = 0; s < 2; ++s) {
-            CU(pfm_cta_blocks_per_sm(nts[s], false, 0, &per[s][0]));
-            if (fit) CU(pfm_cta_blocks_per_sm(nts[s], true, smem, &per[s][1]));
-            CU(pfm_cta_blocks_per_sm(nts[s], false, stage, &per[s][2]));
+            CU(pfm_cta_blocks_per_sm(nts[s], 0, 0, &per[s][0]));
+            if (fit) CU(pfm_cta_blocks_per_sm(nts[s], 1, smem, &per[s][1]));
+            CU(pfm_cta_blocks_per_sm(nts[s], 0, stage, &per[s][2]));
+            if (fit16) CU(pfm_cta_blocks_per_sm(nts[s], 2, smem16, &per[s][3]));
         }
         const size_t region = pfm_cta_region_bytes(n, cb, false, &pcws);
         int grid = 0;
         for (int s = 0; s < 2; ++s)
-            for (int p = 0; p < 3; ++p) grid = std::max(grid, num_sms * per[s][p]);
+            for (int p = 0; p < 4; ++p) grid = std::max(grid, num_sms * per[s][p]);
         grid = std::max(grid, 1);
         if (const char* env = std::getenv("MANTRA_PFM_GRID")) grid = std::max(1, std::min(grid, std::atoi(env)));
         const size_t budget = free_device_bytes() / 3;
@@ -414,7 +419,7 @@ struct Engine {
         pcws.base = pc_mem;
         pcws.stride = region;
         for (int s = 0; s < 2; ++s)
-            for (int p = 0; p < 3; ++p) pc_grids[s][p] = per[s][p] > 0 ? std::min(grid, num_sms * per[s][p]) : 0;
+            for (int p = 0; p < 4; ++p) pc_grids[s][p] = per[s][p] > 0 ? std::min(grid, num_sms * per[s][p]) : 0;
         pc_grid = pc_grids[1][fit ? 1 : 0];
         pc_smem = fit ? smem : 0;
         pc_n = n;
@@ -446,7 +451,7 @@ struct Engine {
             CU(cudaEventRecord(e_p0, sb));
             PfmCtaWs w = pcws;
             w.nt = tick_pc_nt;
-            w.fa_in_smem = tick_pc_sm == 1 ? 1 : 0;
+            w.fa_in_smem = tick_pc_sm == 1 ? 1 : (tick_pc_sm == 3 ? 2 : 0);
             w.stage_cap = tick_pc_sm == 2 ? PFM_STAGE_CAP : 0u;
             CU(launch_pfm_cta((const Task*)(tab_d + o_tp), (const uint64_t*)(tab_d + o_up), hdr + 1, work + 1, w,
                               pc_grids[tick_pc_nt == 256 ? 0 : 1][tick_pc_sm], sb));
@@ -528,13 +533,17 @@ double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
     return ms;
 }
 
-void log_item(const TickItem& it, bool wide, bool cta, const u64* c, double ms) {
+// One line per tick item on stderr (MANTRA_LOG_LAUNCHES): kernel, launch
+// shape (threads) and state mode (k_bfs: bitmap placement; k_pfm_cta: the
+// engine's mode 0..3), the item's counters and algorithmic bytes, the
+// kernel's event time.
+void log_item(const TickItem& it, bool wide, bool cta, int nt, int mode, const u64* c, double ms) {
     static const bool on = std::getenv("MANTRA_LOG_LAUNCHES") != nullptr;
     if (!on) return;
     const bool pfm = it.job.opt == MANTRA_PFM;
-    std::fprintf(stderr, "mantra-launch kernel=%s%s samples=%llu escan=%llu eadd=%llu snew=%llu fseg=%llu "
-                 "xedge=%llu alg_bytes=%llu ms=%.4f\n", pfm ? (cta ? "k_pfm_cta" : "k_pfm") : "k_bfs",
-                 wide ? "<wide>" : "", (unsigned long long)it.job.count, (unsigned long long)c[C_ESCAN],
+    std::fprintf(stderr, "mantra-launch kernel=%s%s nt=%d mode=%d samples=%llu escan=%llu eadd=%llu snew=%llu "
+                 "fseg=%llu xedge=%llu alg_bytes=%llu ms=%.4f\n", pfm ? (cta ? "k_pfm_cta" : "k_pfm") : "k_bfs",
+                 wide ? "<wide>" : "", nt, mode, (unsigned long long)it.job.count, (unsigned long long)c[C_ESCAN],
                  (unsigned long long)c[C_EADD], (unsigned long long)c[C_SNEW], (unsigned long long)c[C_FSEG],
                  (unsigned long long)c[C_XEDGE],
                  (unsigned long long)alg_bytes_of(pfm, c[C_ESCAN], c[C_EADD], c[C_SNEW], c[C_FSEG]), ms);
@@ -557,7 +566,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     const uint32_t k = (uint32_t)items.size();
     int rc;
     if ((rc = E.ensure_tables(std::max<uint32_t>(k, 1))) != MANTRA_OK) return rc;
-    uint32_t bn = 0, bA = 0, bz = 0, pn = 0, plc = 0;
+    uint32_t bn = 0, bA = 0, bz = 0, pn = 0, plc = 0, pz = 0;
     const mantra_graph* gb = nullptr;   // the tick's largest sh/sfm graph: its knobs apply
     const mantra_graph* gp = nullptr;   // the tick's largest pfm graph
     uint64_t pwarps = 0, bsamples = 0;
@@ -565,6 +574,7 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     for (const TickItem& it : items) {
         if (it.job.opt == MANTRA_PFM) {
             any_p = true; pn = std::max(pn, it.G->n); plc = std::max(plc, it.G->dg.cbound);
+            pz = std::max(pz, it.G->dg.max_vslots);
             if (!gp || it.G->n > gp->n) gp = it.G;
             pwarps += (it.job.count + 31) / 32;
         } else {
@@ -602,16 +612,25 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
     }
     // pfm CTA shape and arrival-state mode: 512 threads with the state in shared
     // memory when it fits, or the graph's tuned choice; MANTRA_PFM_CTA_NT=256,
-    // MANTRA_PFM_CTA_SMEM=0 (global state) and MANTRA_PFM_STAGE=1 (global state,
-    // staged edge tiles) force the others
+    // MANTRA_PFM_CTA_SMEM=0 (global state), =16 (shared, 16-bit offsets) and
+    // MANTRA_PFM_STAGE=1 (global state, staged edge tiles) force the others.
+    // The 16-bit state needs every pfm graph of the tick to have at most
+    // 0xFFFE slots per vertex.
     if (any_p && cta) {
-        int nt = 512, sm = E.pc_grids[1][1] ? 1 : 0;
+        int nt = 512, sm = E.pc_grids[1][1] || E.pc_grids[1][3] ? 1 : 0;
         if (gp && gp->knobs.pfm_nt) nt = gp->knobs.pfm_nt;
         if (gp && gp->knobs.pfm_mode >= 0) sm = gp->knobs.pfm_mode;
         if (const char* env = std::getenv("MANTRA_PFM_CTA_NT")) nt = std::atoi(env) == 256 ? 256 : 512;
-        if (const char* env = std::getenv("MANTRA_PFM_CTA_SMEM")) sm = env[0] == '0' ? 0 : sm;
+        if (const char* env = std::getenv("MANTRA_PFM_CTA_SMEM"))
+            sm = env[0] == '0' ? 0 : (std::atoi(env) == 16 ? 3 : (sm == 3 ? 1 : sm));
         if (const char* env = std::getenv("MANTRA_PFM_STAGE")) sm = env[0] == '1' ? 2 : (sm == 2 ? 0 : sm);
-        if (!E.pc_grids[nt == 256 ? 0 : 1][sm]) sm = 0;
+        const int sh = nt == 256 ? 0 : 1;
+        if (sm == 3 && pz > PFM_W16_MAX_VSLOTS) sm = 1;
+        // the untuned shared state: 16-bit offsets where they keep more CTAs resident
+        if (sm == 1 && !(gp && gp->knobs.pfm_mode >= 0) && pz <= PFM_W16_MAX_VSLOTS &&
+            E.pc_grids[sh][3] > E.pc_grids[sh][1])
+            sm = 3;
+        if (!E.pc_grids[sh][sm]) sm = 0;
         E.tick_pc_nt = nt;
         E.tick_pc_sm = sm;
     }
@@ -665,8 +684,11 @@ int run_tick(Engine& E, std::vector<TickItem>& items, bool wide, TickOut* out) {
         out->pfm_ms = out->had_pfm ? elapsed_ms(E.e_p0, E.e_p1) : 0.0;
     }
     for (uint32_t x = 0; x < k; ++x)
-        log_item(items[x], wide, cta, (const u64*)out->slot[x],
-                 items[x].job.opt == MANTRA_PFM ? out->pfm_ms : out->bfs_ms);
+        if (items[x].job.opt == MANTRA_PFM)
+            log_item(items[x], wide, cta, cta ? E.tick_pc_nt : 32, cta ? E.tick_pc_sm : 0, (const u64*)out->slot[x],
+                     out->pfm_ms);
+        else
+            log_item(items[x], wide, cta, E.tick_bfs_nt, E.tick_bfs_sm, (const u64*)out->slot[x], out->bfs_ms);
     return MANTRA_OK;
 }
 
@@ -1376,8 +1398,9 @@ int mantra_tune(mantra_graph* g, mantra_tune_result* out) {
     if ((rc = probe(MANTRA_PFM, none, &out->pfm_default_ms)) != MANTRA_OK) { g->knobs = none; return rc; }
     out->pfm_ms = 1e300;
     for (int nt : {256, 512})
-        for (int sm = 0; sm < 3; ++sm) {
+        for (int sm = 0; sm < 4; ++sm) {
             if (!E->pc_grids[nt == 256 ? 0 : 1][sm]) continue;
+            if (sm == 3 && g->dg.max_vslots > PFM_W16_MAX_VSLOTS) continue;
             Knobs k = none;
             k.pfm_nt = nt; k.pfm_mode = sm;
             double ms = 0;
@@ -1388,8 +1411,9 @@ int mantra_tune(mantra_graph* g, mantra_tune_result* out) {
     out->bfs_threads = (uint32_t)best.bfs_nt;
     out->bfs_bitmap_shared = best.bfs_smem > 0 ? 1u : 0u;
     out->pfm_threads = (uint32_t)best.pfm_nt;               // 0: the stream-scan pfm kernel is forced
-    out->pfm_state_shared = best.pfm_mode == 1 ? 1u : 0u;
+    out->pfm_state_shared = best.pfm_mode == 1 || best.pfm_mode == 3 ? 1u : 0u;
     out->pfm_staged = best.pfm_mode == 2 ? 1u : 0u;
+    out->pfm_state16 = best.pfm_mode == 3 ? 1u : 0u;
     out->bfs_resident_ctas = best.bfs_nt ? (uint32_t)E->bfs_grids[Engine::shape_of(best.bfs_nt)][best.bfs_smem] : 0u;
     out->pfm_resident_ctas = best.pfm_nt ? (uint32_t)E->pc_grids[best.pfm_nt == 256 ? 0 : 1][best.pfm_mode] : 0u;
     if (!best.pfm_nt) out->pfm_ms = out->pfm_default_ms;

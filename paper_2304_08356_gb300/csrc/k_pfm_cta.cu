@@ -32,6 +32,15 @@
 // out-edge of each expansion is kept (lo_prev), so a re-expansion and the
 // Kahn pass need at most one search of an out-row; searches of several
 // vertices run interleaved.
+//
+// State modes (template FA): 0 -- fsl and the two bitmaps in a global-memory
+// region; 1 -- in shared memory; 2 -- in shared memory with fsl(v) kept as
+// the 16-bit offset of the slot within v's slots (slot_ptr(v) + offset is
+// the slot; 0xFFFF unreached, 0xFFFE the source), which halves the largest
+// shared-memory array so that more CTAs, or more L1, fit per SM.  Mode 2
+// needs every vertex to have at most 0xFFFE slots; its expansion reads the
+// store's per-edge head offsets (out_loff) instead of out_slot, and the
+// arrival minimum is a compare-and-swap loop on the 16-bit entry.
 #include "mantra_dev.cuh"
 
 #include <mutex>
@@ -39,6 +48,8 @@
 namespace mantra {
 
 constexpr uint32_t SRC = NONE - 1u;        // fsl of the source
+constexpr uint32_t O16_NONE = 0xFFFFu;     // mode 2: unreached
+constexpr uint32_t O16_SRC = 0xFFFEu;      // mode 2: the source
 constexpr int WALK_K = 2;                  // edge windows with loads in flight per warp
 constexpr int CK = 8;                      // vertices with loads in flight per thread in the O(n) passes
 
@@ -83,12 +94,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
-// PC_NT threads per CTA, 1024 / PC_NT CTAs per SM at 64 registers.
-template <int PC_NT, bool FA_SMEM>
+// PC_NT threads per CTA, 1024 / PC_NT CTAs per SM at 64 registers; FA the
+// state mode.
+template <int PC_NT, int FA>
 __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tasks, const uint64_t* unit_start,
                                                                 const uint32_t* ntasks_p, u64* work, const PfmCtaWs ws) {
     constexpr int PC_NW = PC_NT / 32;
     constexpr uint32_t CHUNK = 2 * PC_NT;      // frontier vertices per range table
+    constexpr bool FA_SMEM = FA != 0;          // state in shared memory
+    constexpr bool W16 = FA == 2;              // fsl as 16-bit slot offsets
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const uint32_t FULL = 0xFFFFFFFFu;
     __shared__ __align__(16) Task sh_task;
@@ -112,8 +126,10 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
     uint32_t stage_par = 0;                        // parity of the mbarrier phase to wait for
 
     char* region = ws.base + (size_t)blockIdx.x * ws.stride;
-    uint32_t* fsl = FA_SMEM ? pc_dyn : reinterpret_cast<uint32_t*>(region + ws.o_fa);
-    uint32_t* NB = FA_SMEM ? pc_dyn + ws.n_cap : reinterpret_cast<uint32_t*>(region + ws.o_bits);  // next frontier
+    uint32_t* fsl = FA == 1 ? pc_dyn : reinterpret_cast<uint32_t*>(region + ws.o_fa);
+    unsigned short* const fso = reinterpret_cast<unsigned short*>(pc_dyn);   // mode 2
+    const uint32_t fa_words = W16 ? (ws.n_cap + 1) / 2 : ws.n_cap;           // shared words of the state
+    uint32_t* NB = FA_SMEM ? pc_dyn + fa_words : reinterpret_cast<uint32_t*>(region + ws.o_bits);  // next frontier
     uint32_t* XB = NB + ws.bits_words;                                                              // expanded before
     uint32_t* lo_prev = reinterpret_cast<uint32_t*>(region + ws.o_exp);  // first out-edge of the last expansion
     uint32_t* fat = reinterpret_cast<uint32_t*>(region + ws.o_fat);      // fa' = fa + 1 (0: s, NONE: unreached)
@@ -247,7 +263,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
     // with a barrier.
     // edge(u, v, slot) for every out-edge (u, v) of the table, head's arrival slot
     // loaded; WALK_K windows of loads in flight per warp.
-    auto expand = [&](uint32_t E, const uint32_t* out_v, const uint32_t* out_slot, auto edge) {
+    auto expand = [&](uint32_t E, const uint32_t* out_v, auto out_slot, auto edge) {
         const uint32_t per = ((E + PC_NW * 32u - 1u) / (PC_NW * 32u)) * 32u;
         const uint32_t w_lo = min((uint32_t)wid * per, E), w_hi = min(w_lo + per, E);
         lbs_walk_batched<WALK_K>(cs_off, sh_Gc, cs_first, w_lo, w_hi, out_v, out_slot,
@@ -309,11 +325,32 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
         const uint32_t* const out_v = g.out_v;
         const uint32_t* const out_slot = g.out_slot;
         const uint32_t* const slot_t = g.slot_t;
+        // v's arrival slot (NONE: unreached, SRC: the source), and whether v is reached
+        auto slot_of = [&](uint32_t v) -> uint32_t {
+            if constexpr (W16) {
+                const uint32_t x = fso[v];
+                return x >= O16_SRC ? (x == O16_NONE ? NONE : SRC) : __ldg(g.slot_ptr + v) + x;
+            } else {
+                return ldv<FA_SMEM>(fsl + v);
+            }
+        };
+        auto reached_v = [&](uint32_t v) -> bool {
+            if constexpr (W16) return fso[v] != O16_NONE;
+            else return ldv<FA_SMEM>(fsl + v) != NONE;
+        };
 
-        for (uint32_t v = tid; v < n; v += PC_NT) fsl[v] = NONE;
+        if constexpr (W16) {
+            for (uint32_t w = tid; w < (n + 1) / 2; w += PC_NT) pc_dyn[w] = 0xFFFFFFFFu;
+        } else {
+            for (uint32_t v = tid; v < n; v += PC_NT) fsl[v] = NONE;
+        }
         for (uint32_t w = tid; w < nwords; w += PC_NT) XB[w] = 0u;
         __syncthreads();
-        if (tid == 0 && live) { fsl[s] = SRC; NB[s >> 5] |= 1u << (s & 31); }
+        if (tid == 0 && live) {
+            if constexpr (W16) fso[s] = (unsigned short)O16_SRC;
+            else fsl[s] = SRC;
+            NB[s >> 5] |= 1u << (s & 31);
+        }
         __syncthreads();
 
         // ---- earliest arrivals ----
@@ -338,7 +375,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                         const uint32_t r0 = out_ptr[uu], r1 = out_ptr[uu + 1];
                         const bool again = (ldv<FA_SMEM>(XB + (uu >> 5)) >> (uu & 31)) & 1u;
                         const uint32_t cap = again ? lo_prev[uu] : r1;
-                        const uint32_t fu = ldv<FA_SMEM>(fsl + uu);
+                        const uint32_t fu = slot_of(uu);
                         // first t > fa(u): the store's per-slot table, no search
                         const uint32_t f0 = (fu != SRC) ? __ldg(g.slot_nout + fu) : r0;
                         lo[2 * j] = hi[2 * j] = f0;
@@ -355,9 +392,20 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                         atomicOr(XB + (u[j] >> 5), 1u << (u[j] & 31));
                     }
                 }
+                // sl: the head's arrival slot (mode 2: its offset within v's slots)
                 auto relax = [&](uint32_t, uint32_t v, uint32_t sl) {
-                    if (v == s || sl >= ldv<FA_SMEM>(fsl + v)) return;
-                    if (sl < atomicMin(fsl + v, sl)) atomicOr(NB + (v >> 5), 1u << (v & 31));
+                    if constexpr (W16) {
+                        if (v == s) return;
+                        uint32_t old = fso[v];
+                        while (sl < old) {
+                            const uint32_t prev = atomicCAS(fso + v, (unsigned short)old, (unsigned short)sl);
+                            if (prev == old) { atomicOr(NB + (v >> 5), 1u << (v & 31)); return; }
+                            old = prev;
+                        }
+                    } else {
+                        if (v == s || sl >= ldv<FA_SMEM>(fsl + v)) return;
+                        if (sl < atomicMin(fsl + v, sl)) atomicOr(NB + (v >> 5), 1u << (v & 31));
+                    }
                 };
                 if (stage) {
                     bool staged = false;
@@ -388,15 +436,16 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                 } else {
                     const uint32_t E = table(u, rl, rh);
                     if (tid == 0) my_x += E;
-                    expand(E, out_v, out_slot, relax);
+                    if constexpr (W16) expand(E, out_v, g.out_loff, relax);
+                    else expand(E, out_v, out_slot, relax);
                 }
             }
             if (!full) {
-                const uint32_t fz = ldv<FA_SMEM>(fsl + z);
+                const uint32_t fz = slot_of(z);
                 if (fz != NONE) bound = min(bound, __ldg(slot_t + fz));
             }
         }
-        const bool reached = live && (full || ldv<FA_SMEM>(fsl + z) != NONE);
+        const bool reached = live && (full || reached_v(z));
 
         // fa' of every vertex, for the DAG tests of in-edges
         if (live) {
@@ -405,7 +454,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
 #pragma unroll
                 for (int j = 0; j < CK; ++j) {
                     const uint32_t v = v0 + PC_NT * j;
-                    f[j] = v < n ? ldv<FA_SMEM>(fsl + v) : NONE;
+                    f[j] = v < n ? slot_of(v) : NONE;
                 }
 #pragma unroll
                 for (int j = 0; j < CK; ++j) tt[j] = (f[j] != NONE && f[j] != SRC) ? __ldg(slot_t + f[j]) : 0u;
@@ -453,7 +502,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                     const uint32_t v = v0 + PC_NT * j;
                     const uint32_t fv = fvs[j];
                     if (fv == NONE || v == s || fv - 1u > bound) continue;
-                    const uint32_t a = ldv<FA_SMEM>(fsl + v);
+                    const uint32_t a = slot_of(v);
                     const uint32_t e1 = __ldg(g.slot_in + a + 1);
                     uint32_t c = 0;
                     for (uint32_t e = __ldg(g.slot_in + a); e < e1; ++e) {
@@ -491,7 +540,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                 for (uint32_t v = tid; v < n; v += PC_NT) {
                     const uint32_t fv = __ldcg(fat + v);
                     if (fv == NONE || v == s || fv - 1u > bound) continue;
-                    const uint32_t a = ldv<FA_SMEM>(fsl + v);
+                    const uint32_t a = slot_of(v);
                     const uint32_t e1 = __ldg(g.slot_in + a + 1);
                     for (uint32_t e = __ldg(g.slot_in + a); e < e1; ++e) {
                         const uint32_t w = __ldg(g.in_u + e);
@@ -544,7 +593,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
             if (reached) {
                 for (uint32_t v0 = 0; v0 < n; v0 += PC_NT) {
                     const uint32_t v = v0 + tid;
-                    const bool r = v < n && v != s && ldv<FA_SMEM>(fsl + v) != NONE;
+                    const bool r = v < n && v != s && reached_v(v);
                     const uint32_t h = r ? __ldcg(hop + v) : NONE;
                     const unsigned grp = __match_any_sync(FULL, h);
                     if (r && lane == __ffs(grp) - 1) atomicAdd(job.cnt + h, (u64)__popc(grp));
@@ -581,7 +630,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
             if (lane == 0) path[0] = z;
             while (!err && v != s) {
                 const uint32_t fv = __ldcg(fat + v);
-                const uint32_t a = ldv<FA_SMEM>(fsl + v);
+                const uint32_t a = slot_of(v);
                 const uint32_t e_lo = g.slot_in[a], e_hi = g.slot_in[a + 1];
                 uint32_t nxt = NONE, ech = NONE;
                 for (uint32_t e0 = e_lo; e0 < e_hi; e0 += 32) {
@@ -645,7 +694,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                     if (v == s) continue;
                     const u64 x = __ldcg(dl + v);
                     if (!x) continue;
-                    const uint32_t fv = __ldcg(fat + v), a = ldv<FA_SMEM>(fsl + v);
+                    const uint32_t fv = __ldcg(fat + v), a = slot_of(v);
                     const uint32_t e1 = __ldg(g.slot_in + a + 1);
                     for (uint32_t e = __ldg(g.slot_in + a); e < e1; ++e) {
                         const uint32_t w = __ldg(g.in_u + e);
@@ -697,7 +746,7 @@ __global__ void __launch_bounds__(PC_NT, 1024 / PC_NT) k_pfm_cta(const Task* tas
                     const uint32_t x = Fl[p];
                     if (x == s) continue;
                     const u64 X = (1ull << 32) + __ldcg(dl + x), sx = __ldcg(sig + x);
-                    const uint32_t fv = __ldcg(fat + x), a = ldv<FA_SMEM>(fsl + x);
+                    const uint32_t fv = __ldcg(fat + x), a = slot_of(x);
                     const uint32_t e1 = __ldg(g.slot_in + a + 1);
                     for (uint32_t e = __ldg(g.slot_in + a); e < e1; ++e) {
                         const uint32_t w = __ldg(g.in_u + e);
@@ -802,8 +851,11 @@ size_t pfm_cta_region_bytes(uint32_t n, uint32_t dag_cap, bool fa_in_smem, PfmCt
     return o;
 }
 
-// Dynamic shared memory of the variant with the arrival state in shared memory.
-size_t pfm_cta_smem_bytes(uint32_t n) { return ((size_t)n + 2 * ((n + 31) / 32)) * 4; }
+// Dynamic shared memory of the variants with the arrival state in shared
+// memory: 32-bit slots (mode 1) or 16-bit offsets (mode 2), then the bitmaps.
+size_t pfm_cta_smem_bytes(uint32_t n, bool w16) {
+    return ((size_t)(w16 ? (n + 1) / 2 : n) + 2 * ((n + 31) / 32)) * 4;
+}
 
 // Dynamic shared memory of the global-state variant's staged edge tiles
 // (out_v and out_slot, cap entries each; cap a multiple of 4).
@@ -812,8 +864,8 @@ size_t pfm_cta_stage_bytes(uint32_t cap) { return (size_t)cap * 8; }
 // Static shared memory of the kernel (range table, task copy, scratch).
 size_t pfm_cta_static_smem(int nt) {
     cudaFuncAttributes a{};
-    const cudaError_t e = nt == 256 ? cudaFuncGetAttributes(&a, k_pfm_cta<256, true>)
-                                    : cudaFuncGetAttributes(&a, k_pfm_cta<512, true>);
+    const cudaError_t e = nt == 256 ? cudaFuncGetAttributes(&a, k_pfm_cta<256, 1>)
+                                    : cudaFuncGetAttributes(&a, k_pfm_cta<512, 1>);
     return e == cudaSuccess ? a.sharedSizeBytes : 16384;
 }
 
@@ -828,8 +880,9 @@ cudaError_t pfm_cta_configure(size_t smem) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
     if (smem <= configured[dev]) return cudaSuccess;
-    const void* ks[4] = {(const void*)k_pfm_cta<512, true>, (const void*)k_pfm_cta<256, true>,
-                         (const void*)k_pfm_cta<512, false>, (const void*)k_pfm_cta<256, false>};
+    const void* ks[6] = {(const void*)k_pfm_cta<512, 1>, (const void*)k_pfm_cta<256, 1>,
+                         (const void*)k_pfm_cta<512, 2>, (const void*)k_pfm_cta<256, 2>,
+                         (const void*)k_pfm_cta<512, 0>, (const void*)k_pfm_cta<256, 0>};
     for (const void* k : ks) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -838,23 +891,30 @@ cudaError_t pfm_cta_configure(size_t smem) {
     return cudaSuccess;
 }
 
-cudaError_t pfm_cta_blocks_per_sm(int nt, bool fa_in_smem, size_t smem, int* out) {
-    if (nt == 256)
-        return fa_in_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<256, true>, 256, smem)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<256, false>, 256, smem);
-    return fa_in_smem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<512, true>, 512, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<512, false>, 512, smem);
+// fa: the state mode (0 global, 1 shared 32-bit, 2 shared 16-bit).
+cudaError_t pfm_cta_blocks_per_sm(int nt, int fa, size_t smem, int* out) {
+    if (nt == 256) {
+        if (fa == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<256, 1>, 256, smem);
+        if (fa == 2) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<256, 2>, 256, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<256, 0>, 256, smem);
+    }
+    if (fa == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<512, 1>, 512, smem);
+    if (fa == 2) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<512, 2>, 512, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_pfm_cta<512, 0>, 512, smem);
 }
 
 cudaError_t launch_pfm_cta(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
                            const PfmCtaWs& ws, int grid, cudaStream_t st) {
-    const size_t smem = ws.fa_in_smem ? pfm_cta_smem_bytes(ws.n_cap) : pfm_cta_stage_bytes(ws.stage_cap);
+    const int fa = ws.fa_in_smem;
+    const size_t smem = fa ? pfm_cta_smem_bytes(ws.n_cap, fa == 2) : pfm_cta_stage_bytes(ws.stage_cap);
     if (ws.nt == 256) {
-        if (ws.fa_in_smem) k_pfm_cta<256, true><<<grid, 256, smem, st>>>(tasks, unit_start, ntasks, work, ws);
-        else k_pfm_cta<256, false><<<grid, 256, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        if (fa == 1) k_pfm_cta<256, 1><<<grid, 256, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else if (fa == 2) k_pfm_cta<256, 2><<<grid, 256, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else k_pfm_cta<256, 0><<<grid, 256, smem, st>>>(tasks, unit_start, ntasks, work, ws);
     } else {
-        if (ws.fa_in_smem) k_pfm_cta<512, true><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
-        else k_pfm_cta<512, false><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        if (fa == 1) k_pfm_cta<512, 1><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else if (fa == 2) k_pfm_cta<512, 2><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
+        else k_pfm_cta<512, 0><<<grid, 512, smem, st>>>(tasks, unit_start, ntasks, work, ws);
     }
     return cudaGetLastError();
 }

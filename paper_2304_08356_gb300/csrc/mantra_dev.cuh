@@ -12,6 +12,7 @@
 //   tmax_in[n]  latest in-edge time of v (valid when v has a slot)
 //   tmin_out[n] earliest out-edge time of u (valid when u has out-edges)
 //   slot_nout[A] first out-edge of v later than slot (v, t): out-row index
+//   out_loff[m]  16-bit: out_slot[e] - slot_ptr[out_v[e]] (clamped to 0xFFFF)
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -62,7 +63,13 @@ struct DevGraph {
     uint32_t n_uedge;       // distinct ordered pairs (u, v) with a temporal edge
     uint32_t max_vslots;    // largest number of arrival slots of one vertex
     const uint32_t* slot_nout;   // per arrival slot (v, t): first index of v's out-row with time > t
+    const unsigned short* out_loff;   // per out-edge: its head's slot offset within the head's slots
+                                      // (out_slot - slot_ptr[out_v], 0xFFFF when above)
 };
+
+// Largest number of arrival slots of one vertex for the CTA pfm kernel's
+// 16-bit state (offsets 0xFFFE and 0xFFFF are reserved).
+constexpr uint32_t PFM_W16_MAX_VSLOTS = 0xFFFEu;
 
 // One launch over a range (or list) of sample indices.
 struct Job {
@@ -488,11 +495,12 @@ __device__ __forceinline__ void lbs_walk(const uint32_t* off, uint32_t Gc, uint3
 // edge(g, e, pa[e], pb[e]) runs for each valid edge -- K times the loads in
 // flight per warp.  first[g] is the first edge of range g.  RO: pa and pb
 // are read-only for the kernel's lifetime (read-only data path); otherwise
-// plain loads (e.g. shared-memory tiles).
-template <int K, bool RO = true, typename F>
+// plain loads (e.g. shared-memory tiles).  pb holds 32-bit or 16-bit
+// entries (TB).
+template <int K, bool RO = true, typename TB = uint32_t, typename F>
 __device__ __forceinline__ void lbs_walk_batched(const uint32_t* off, uint32_t Gc, const uint32_t* first, uint32_t w_lo,
                                                  uint32_t w_hi, const uint32_t* __restrict__ pa,
-                                                 const uint32_t* __restrict__ pb, F edge) {
+                                                 const TB* __restrict__ pb, F edge) {
     const uint32_t lane = threadIdx.x & 31;
     if (w_lo >= w_hi) return;
     uint32_t lo = 0, hi = Gc;                 // off[lo] <= w_lo < off[hi]
@@ -674,7 +682,8 @@ struct PfmCtaWs {
     uint32_t dag_cap;    // capacity of the successor array (>= cbound of every graph)
     uint32_t n_cap;      // node capacity of a region
     uint32_t bits_words; // words of each bitmap: ceil(n_cap / 32)
-    int fa_in_smem;      // arrival slots and bitmaps in dynamic shared memory
+    int fa_in_smem;      // state mode: 0 global region; arrival state and bitmaps in dynamic shared
+                         // memory, 1 as 32-bit slots, 2 as 16-bit offsets within each vertex's slots
     int nt;              // threads per CTA (256 or 512)
     uint32_t stage_cap;  // global-state variant: out-edges per chunk staged in shared memory by bulk copies (0: none)
 };
@@ -694,11 +703,11 @@ int pfm_threads();
 cudaError_t launch_pfm(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
                        const PfmWs& ws, int grid, bool wide, cudaStream_t st);
 size_t pfm_cta_region_bytes(uint32_t n, uint32_t dag_cap, bool fa_in_smem, PfmCtaWs* ws);
-size_t pfm_cta_smem_bytes(uint32_t n);
+size_t pfm_cta_smem_bytes(uint32_t n, bool w16);
 size_t pfm_cta_stage_bytes(uint32_t cap);
 size_t pfm_cta_static_smem(int nt);
 cudaError_t pfm_cta_configure(size_t smem);
-cudaError_t pfm_cta_blocks_per_sm(int nt, bool fa_in_smem, size_t smem, int* out);
+cudaError_t pfm_cta_blocks_per_sm(int nt, int fa, size_t smem, int* out);
 cudaError_t launch_pfm_cta(const Task* tasks, const uint64_t* unit_start, const uint32_t* ntasks, u64* work,
                            const PfmCtaWs& ws, int grid, cudaStream_t st);
 // One problem of a multi-problem round reduction.

@@ -288,7 +288,7 @@ int StoreBuilder::build(const uint32_t* u, const uint32_t* v, const uint32_t* t,
             } else {
                 const uint64_t m1 = c.m1;
                 const size_t lens[SA_COUNT] = {(size_t)N + 1, m1, m1, m1, (size_t)N + 1, m1, m1, m1 + 1, m1,
-                                               m1, m1, m1, m1, N, N, m1, m1};
+                                               m1, m1, m1, m1, N, N, m1, m1, (m1 + 1) / 2};
                 size_t total = 0;
                 for (int k = 0; k < SA_COUNT; ++k) { cap[k] = (lens[k] + 64) & ~(size_t)63; total += cap[k]; }
                 const size_t recs = std::max<uint64_t>(m1, 1);
@@ -404,6 +404,8 @@ int StoreBuilder::build(const uint32_t* u, const uint32_t* v, const uint32_t* t,
                            *sl_ptr = c.a[SA_SLOT_PTR], *sl_in = c.a[SA_SLOT_IN];
             uint32_t* nout = c.a[SA_SLOT_NOUT];
             uint32_t *tmax_in = c.a[SA_TMAX_IN], *tmin_out = c.a[SA_TMIN_OUT];
+            const uint32_t *o_v = c.a[SA_OUT_V], *o_s = c.a[SA_OUT_SLOT];
+            uint16_t* loff = reinterpret_cast<uint16_t*>(c.a[SA_OUT_LOFF]);
             // vertices split by their slot + out-edge counts (a monotone prefix);
             // each vertex merges its slot times with its out-row times
             const uint64_t tot = (uint64_t)A + M;
@@ -429,6 +431,8 @@ int StoreBuilder::build(const uint32_t* u, const uint32_t* v, const uint32_t* t,
                     nout[a] = q;
                     mx = std::max(mx, sl_in[a + 1] - sl_in[a]);
                 }
+                for (uint32_t e = o_ptr[w]; e < q1; ++e)   // heads' slot offsets (16-bit entries)
+                    loff[e] = (uint16_t)std::min<uint32_t>(o_s[e] - sl_ptr[o_v[e]], 0xFFFFu);
                 tmax_in[w] = a1 > a0 ? sl_t[a1 - 1] : 0;
                 tmin_out[w] = q1 > o_ptr[w] ? o_t[o_ptr[w]] : 0;
                 cb += mx;
@@ -474,8 +478,9 @@ int StoreBuilder::build(const uint32_t* u, const uint32_t* v, const uint32_t* t,
     out->cbound = (uint32_t)std::min<uint64_t>(cb, 0xFFFFFFFFull);
     out->max_slot_in = (uint32_t)mxs;
     out->max_vslots = (uint32_t)mxv;
+    if (M & 1) reinterpret_cast<uint16_t*>(c.a[SA_OUT_LOFF])[M] = 0;
     const size_t lens[SA_COUNT] = {(size_t)N + 1, M, M, M, (size_t)N + 1, A, A, (size_t)A + 1, M, M, M, M, M,
-                                   N, N, M, A};
+                                   N, N, M, A, ((size_t)M + 1) / 2};
     for (int k = 0; k < SA_COUNT; ++k) { out->arr[k] = c.a[k]; out->len[k] = lens[k]; }
     return MANTRA_OK;
 }

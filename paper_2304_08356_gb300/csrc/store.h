@@ -14,8 +14,12 @@ namespace mantra {
 // The store's arrays, in the order of the device block.
 enum StoreArr : int {
     SA_OUT_PTR, SA_OUT_V, SA_OUT_T, SA_OUT_SLOT, SA_SLOT_PTR, SA_SLOT_T, SA_SLOT_V, SA_SLOT_IN, SA_IN_U,
-    SA_IN_SLOT, SA_ST_U, SA_ST_V, SA_ST_T, SA_TMAX_IN, SA_TMIN_OUT, SA_IN_UEDGE, SA_SLOT_NOUT, SA_COUNT
+    SA_IN_SLOT, SA_ST_U, SA_ST_V, SA_ST_T, SA_TMAX_IN, SA_TMIN_OUT, SA_IN_UEDGE, SA_SLOT_NOUT, SA_OUT_LOFF, SA_COUNT
 };
+// SA_OUT_LOFF holds 16-bit entries, two per uint32 word (entry e in the low
+// half of word e / 2 when e is even): per out-edge, the offset of its head's
+// arrival slot within the head's slots, min(out_slot - slot_ptr[out_v],
+// 0xFFFF); a trailing odd half is 0.
 
 // Result of a build: sizes, counters and the host arrays (each len[k] uint32
 // entries, owned by the builder).

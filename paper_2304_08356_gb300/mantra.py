@@ -52,7 +52,7 @@ class TuneResult(C.Structure):
                 ("pfm_state_shared", C.c_uint32), ("bfs_resident_ctas", C.c_uint32), ("pfm_resident_ctas", C.c_uint32),
                 ("bfs_ms", C.c_double), ("bfs_default_ms", C.c_double), ("pfm_ms", C.c_double),
                 ("pfm_default_ms", C.c_double), ("probe_samples", C.c_uint64), ("pfm_probe_samples", C.c_uint64),
-                ("pfm_staged", C.c_uint32), ("pad_", C.c_uint32)]
+                ("pfm_staged", C.c_uint32), ("pfm_state16", C.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

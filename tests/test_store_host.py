@@ -18,7 +18,7 @@ from paper_2304_08356_gb300 import synth
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2304_08356_gb300", "csrc")
 NAMES = ["out_ptr", "out_v", "out_t", "out_slot", "slot_ptr", "slot_t", "slot_v", "slot_in", "in_u", "in_slot",
-         "st_u", "st_v", "st_t", "tmax_in", "tmin_out", "in_uedge", "slot_nout"]
+         "st_u", "st_v", "st_t", "tmax_in", "tmin_out", "in_uedge", "slot_nout", "out_loff"]
 
 
 @pytest.fixture(scope="module")
@@ -94,6 +94,11 @@ def definition(u, v, t, n):
     d["tmin_out"] = np.where(cnt_o > 0, out_t[np.minimum(out_ptr[:-1], max(M - 1, 0))] if M else 0, 0)
     # first out-edge of v later than each slot (v, t): rows are in time order
     d["slot_nout"] = np.searchsorted((out_u << 32) | out_t, (slot_v << 32) | slot_t, side="right")
+    # per out-edge, the head's slot offset within the head's slots (16-bit,
+    # clamped to 0xFFFF), two entries per uint32 word, a trailing half 0
+    loff = np.zeros(2 * ((M + 1) // 2), np.uint16)
+    loff[:M] = np.minimum(d["out_slot"] - slot_ptr[d["out_v"]], 0xFFFF)
+    d["out_loff"] = loff.view(np.uint32)
     per_slot = np.diff(d["slot_in"])
     vmax = np.zeros(n, np.int64)
     np.maximum.at(vmax, slot_v, per_slot)
@@ -178,4 +183,20 @@ def test_store_thread_counts(driver, tmp_path, threads):
     u, v, t = _random(11, 50, 20, 10)
     u[7] = 20
     assert run_builder(driver, tmp_path, u, v, t, 20, threads)["rc"] == 1
+
+
+def test_store_head_offsets_clamp(driver, tmp_path):
+    """A vertex with more than 65,535 arrival slots: its heads' offsets above
+    0xFFFF are clamped (the 16-bit search state is then not used), the others
+    are exact; an odd edge count leaves the trailing half word 0."""
+    k = 70001
+    u = np.concatenate([np.zeros(k, np.int64), [1, 1, 2, 3]])
+    v = np.concatenate([np.ones(k, np.int64), [2, 3, 3, 2]])
+    t = np.concatenate([np.arange(1, k + 1), [5, 70000, 9, 11]])
+    got = check(driver, tmp_path, u, v, t)
+    m = got["m"]
+    assert got["max_vslots"] == k and m == k + 4 and m % 2 == 1
+    lo = got["out_loff"].view(np.uint16)
+    assert len(lo) == m + 1 and lo[m] == 0
+    assert (lo[:m] == 0xFFFF).sum() == k - 0xFFFF
 
