@@ -320,10 +320,15 @@ int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt, uint64_t 
 
 /* ---- Serving (continuous batching over resident graphs) ----
  * A server owns a host thread that runs Algorithm 1 for many requests at
- * once.  Requests queue in arrival order and are admitted while their device
- * state (hits, Rademacher sums, estimates: about 16 + 4c bytes per entry of
- * the estimated family)
- * fits `hbm_budget` bytes (0 = half of free device memory) and fewer than
+ * once.  Requests queue in arrival order and are admitted while the device
+ * state of the running requests and the candidate fits `hbm_budget` bytes
+ * (0 = half of free device memory): each request's own buffers (hits,
+ * Rademacher sums, estimates: about 16 + 4c bytes per entry of the estimated
+ * family) plus the search workspaces shared by all, sized for the largest
+ * graph of each search family (sh/sfm; pfm) among them, counted for four
+ * CTAs per SM (per CTA about 24 bytes per arrival slot and 28 per node for
+ * sh/sfm, 40 and 52 with the ob / RTB scratch; 56 per node plus 4 per unit
+ * of the graph's path-count bound for pfm), and fewer than
  * `max_active` (0 = 256) run; a request is always admitted when none is
  * running.  Each tick launches the pending samples of every running request
  * together; finished requests leave between ticks and queued ones join at the
@@ -348,7 +353,9 @@ int mantra_server_poll(mantra_server* srv, uint64_t req_id, double* est_out, uin
 int mantra_server_wait(mantra_server* srv, uint64_t req_id, double timeout_s, double* est_out, uint64_t* hits_out,
                        mantra_info* info);
 
-/* Queue length, running requests, finished requests, ticks run, admitted footprint. */
+/* Queue length, running requests, finished requests, ticks run, and the
+ * running requests' admitted device state (their buffers plus the shared
+ * search workspaces as counted for admission; 0 when none runs). */
 int mantra_server_stats(mantra_server* srv, uint64_t* queued, uint64_t* active, uint64_t* finished,
                         uint64_t* ticks, uint64_t* bytes_in_use);
 

@@ -301,6 +301,19 @@ struct Engine {
     // sh/sfm: one region per resident CTA of the largest grid over CTA shapes
     // and bitmap placements, at most 60 % of free memory.  Every region holds
     // a global visited bitmap as well, so the placement is chosen per launch.
+    // Device bytes of the search workspaces for graphs with these maxima (sh/sfm:
+    // n, A, slots per vertex, ob/RTB scratch; pfm: n, cbound), at the largest
+    // grid of any CTA shape (four 256-thread CTAs per SM) and without the
+    // free-memory caps of ensure_bfs / ensure_pfm_cta: an upper estimate of what
+    // those allocate.
+    size_t ws_estimate(uint32_t n, uint32_t A, uint32_t zc, bool dl, uint32_t pn, uint32_t cb) const {
+        size_t b = 0;
+        const size_t grid = 4 * (size_t)std::max(num_sms, 1);
+        if (n) { BfsWs w{}; b += grid * bfs_region_bytes(n, A, zc, false, dl, &w); }
+        if (pn) { PfmCtaWs w{}; b += grid * pfm_cta_region_bytes(pn, cb, false, &w); }
+        return b;
+    }
+
     int ensure_bfs(uint32_t n, uint32_t A, uint32_t zc, bool dl) {
         if (bfs_mem && n <= bfs_n && A <= bfs_A && zc <= bfs_z && (!dl || bfs_dl)) return MANTRA_OK;
         n = std::max(n, bfs_n);
@@ -1110,8 +1123,10 @@ int current_engine(const mantra_graph* g, Engine** E) {
 
 // ---------------------------------------------------------------------------
 // Serving loop (continuous batching).  Requests wait in a FIFO queue and are
-// admitted while their device-state footprint fits the budget (one request is
-// always admitted when none is running).  A tick carries a bounded number of
+// admitted while the device state fits the budget: the running requests' own
+// buffers plus the search workspaces sized for the largest running graph of
+// each search family, the candidate included (one request is always admitted
+// when none is running).  A tick carries a bounded number of
 // samples per search family, about SERVER_TICK_PER_CTA per resident CTA,
 // handed out in arrival order: the oldest running requests get their whole
 // pending range first (a round may span ticks), so requests complete close
@@ -1146,12 +1161,31 @@ struct Server {
     bool stop = false;
     std::thread th;
 
+    // Search workspace for the running requests and (if given) one more.
+    size_t ws_for(const Request* extra) const {
+        uint32_t n = 0, A = 0, z = 0, pn = 0, cb = 0;
+        bool dl = false;
+        auto add = [&](const Request* r) {
+            const mantra_graph* G = r->p.G;
+            if (!G) return;
+            if (r->p.opt == MANTRA_PFM) {
+                pn = std::max(pn, G->n); cb = std::max(cb, G->dg.cbound);
+            } else {
+                n = std::max(n, G->n); A = std::max(A, G->A); z = std::max(z, G->dg.max_vslots);
+                dl = dl || r->p.estimator != 0;
+            }
+        };
+        for (const Request* r : active) add(r);
+        if (extra) add(extra);
+        return E->ws_estimate(n, A, z, dl, pn, cb);
+    }
+
     void loop() {
         std::unique_lock<std::mutex> lk(mu);
         while (true) {
             while (!queue.empty() && active.size() < max_active) {
                 Request* r = queue.front();
-                if (!active.empty() && used + r->footprint > budget) break;
+                if (!active.empty() && used + r->footprint + ws_for(r) > budget) break;
                 queue.pop_front();
                 r->state = 1;
                 used += r->footprint;
@@ -1693,7 +1727,7 @@ int mantra_server_stats(mantra_server* srv, uint64_t* queued, uint64_t* active, 
     if (active) *active = S->active.size();
     if (finished) *finished = S->finished;
     if (ticks) *ticks = S->ticks;
-    if (bytes_in_use) *bytes_in_use = S->used;
+    if (bytes_in_use) *bytes_in_use = S->active.empty() ? 0 : S->used + S->ws_for(nullptr);
     return MANTRA_OK;
 }
 

@@ -84,6 +84,37 @@ def test_admission_budget_and_poll(M, graphs):
         assert np.array_equal(done[i][1], h2)
 
 
+def test_admission_counts_the_search_workspace(M, graphs):
+    """The shared search workspace counts against the budget: it is at least
+    four CTAs per SM (>= 100 SMs) x 24 bytes per arrival slot, so a budget of
+    that size admits one sh request at a time although the requests' own
+    buffers are far smaller; the reported device state includes it."""
+    _, gs = graphs
+    g = gs[1]
+    lower = 400 * 24 * g.slots
+    srv = M.Server(hbm_budget=lower, max_active=0)
+    ids = [srv.submit(g, 0, 0.07, 0.1, 21 + k) for k in range(3)]
+    seen_active, seen_bytes, done = 0, 0, {}
+    t0 = time.time()
+    while len(done) < len(ids) and time.time() - t0 < 300:
+        st = srv.stats()
+        seen_active = max(seen_active, st["active"])
+        if st["active"]:
+            seen_bytes = max(seen_bytes, st["bytes_in_use"])
+        for i in ids:
+            if i not in done:
+                r = srv.poll(i)
+                if r is not None:
+                    done[i] = r
+        time.sleep(0.001)
+    srv.close()
+    assert len(done) == len(ids) and seen_active <= 1
+    assert seen_bytes == 0 or seen_bytes >= lower
+    for k, i in enumerate(ids):
+        _, h2, _ = g.estimate(0, 0.07, 0.1, 21 + k)
+        assert np.array_equal(done[i][1], h2)
+
+
 def test_invalid_request_rejected(M, graphs):
     _, gs = graphs
     srv = M.Server()
