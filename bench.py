@@ -472,6 +472,32 @@ def run_reference(args):
     return 0
 
 
+def run_probe(M, args):
+    """Kernel time of fixed-r estimates (one warm run, best of 3), one JSON line."""
+    from paper_2304_08356_gb300 import synth
+    if args.probe_graph:
+        n, m = (int(x) for x in args.probe_graph.split(","))
+        u, v, t = synth.chung_lu_bursty(n=n, m=m, seed=77)
+        wl = "bursty Chung-Lu n=%d, m=%d contacts, seed 77" % (n, m)
+    else:
+        u, v, t = workload()
+        wl = WORKLOAD
+    g = M.Graph(u, v, t)
+    out = {}
+    for name in OPTS:
+        g.estimate(name, EPS, DELTA, 7, c=C_TRIALS, fixed_r=args.probe)
+        best, info, hits = 1e300, None, None
+        for _ in range(3):
+            _, hits, info = g.estimate(name, EPS, DELTA, 7, c=C_TRIALS, fixed_r=args.probe)
+            best = min(best, info["kernel_ms"])
+        out[name] = {"kernel_ms": round(best, 3), "r": args.probe, "edges_expanded": info["edges_expanded"],
+                     "alg_bytes": info["alg_bytes"], "hits_sha256_16": hashlib.sha256(hits.tobytes()).hexdigest()[:16]}
+    print(json.dumps({"probe": out, "workload": wl,
+                      "launch_env": {k: v_ for k, v_ in os.environ.items() if k.startswith("MANTRA_")}}))
+    g.free()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -492,6 +518,12 @@ def main():
     ap.add_argument("--mode", default="batched", choices=["batched", "sequential"],
                     help="batched: one mantra_estimate_batch over the optimalities per step; "
                          "sequential: one mantra_estimate per optimality")
+    ap.add_argument("--probe", type=int, default=0,
+                    help="instead of the bench: time a fixed-r estimate of this many samples per optimality "
+                         "(best kernel time of 3 after one warm run, default or MANTRA_* launch choices) and exit")
+    ap.add_argument("--probe-graph", default="",
+                    help="with --probe: N,M for a bursty Chung-Lu graph of N nodes and M contacts (seed 77) "
+                         "instead of the bench graph")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -512,6 +544,8 @@ def main():
     barrier(world)
     import paper_2304_08356_gb300.mantra as M
 
+    if args.probe:
+        return run_probe(M, args)
     u, v, t = workload()
     g = M.Graph(u, v, t)
     tuned = None if args.no_tune else g.tune()   # the autotuner's launch choices (results do not depend on them)
