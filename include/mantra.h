@@ -326,9 +326,10 @@ int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt, uint64_t 
  * Rademacher sums, estimates: about 16 + 4c bytes per entry of the estimated
  * family) plus the search workspaces shared by all, sized for the largest
  * graph of each search family (sh/sfm; pfm) among them, counted for four
- * CTAs per SM (per CTA about 24 bytes per arrival slot and 28 per node for
- * sh/sfm, 40 and 52 with the ob / RTB scratch; 56 per node plus 4 per unit
- * of the graph's path-count bound for pfm), and fewer than
+ * (sh/sfm) or six (pfm) CTAs per SM (per CTA about 24 bytes per arrival
+ * slot and 28 per node for sh/sfm, 40 and 52 with the ob / RTB scratch; 56
+ * per node plus 4 per unit of the graph's path-count bound for pfm), and
+ * fewer than
  * `max_active` (0 = 256) run; a request is always admitted when none is
  * running.  Each tick launches the pending samples of every running request
  * together; finished requests leave between ticks and queued ones join at the

@@ -303,14 +303,14 @@ struct Engine {
     // a global visited bitmap as well, so the placement is chosen per launch.
     // Device bytes of the search workspaces for graphs with these maxima (sh/sfm:
     // n, A, slots per vertex, ob/RTB scratch; pfm: n, cbound), at the largest
-    // grid of any CTA shape (four 256-thread CTAs per SM) and without the
-    // free-memory caps of ensure_bfs / ensure_pfm_cta: an upper estimate of what
-    // those allocate.
+    // grid of any CTA shape (256-thread CTAs: four per SM for k_bfs, six for
+    // k_pfm_cta) and without the free-memory caps of ensure_bfs /
+    // ensure_pfm_cta: an upper estimate of what those allocate.
     size_t ws_estimate(uint32_t n, uint32_t A, uint32_t zc, bool dl, uint32_t pn, uint32_t cb) const {
         size_t b = 0;
-        const size_t grid = 4 * (size_t)std::max(num_sms, 1);
-        if (n) { BfsWs w{}; b += grid * bfs_region_bytes(n, A, zc, false, dl, &w); }
-        if (pn) { PfmCtaWs w{}; b += grid * pfm_cta_region_bytes(pn, cb, false, &w); }
+        const size_t sms = (size_t)std::max(num_sms, 1);
+        if (n) { BfsWs w{}; b += 4 * sms * bfs_region_bytes(n, A, zc, false, dl, &w); }
+        if (pn) { PfmCtaWs w{}; b += 6 * sms * pfm_cta_region_bytes(pn, cb, false, &w); }
         return b;
     }
 
