@@ -309,7 +309,7 @@ int mantra_sample_paths(const mantra_graph* g, mantra_opt opt, uint64_t seed, ui
  * clears what must start at zero.  Calls that overlap on the GPU (two streams,
  * two threads, two graphs) race on the array: serialise them.
  * Returns MANTRA_E_INVAL for pfm, for a graph whose search scratch does not
- * fit the fixed array (roughly 40 bytes per arrival slot plus 52 per node,
+ * fit the fixed array (roughly 44 bytes per arrival slot plus 52 per node,
  * plus 16 per arrival slot of the vertex with the most slots, for one CTA,
  * plus 8 bytes per requested sample), and MANTRA_E_OVERFLOW
  * when a path count exceeds 64 bits (this variant has no 128-bit re-run). */
@@ -326,8 +326,8 @@ int mantra_sample_paths_noalloc(const mantra_graph* g, mantra_opt opt, uint64_t 
  * Rademacher sums, estimates: about 16 + 4c bytes per entry of the estimated
  * family) plus the search workspaces shared by all, sized for the largest
  * graph of each search family (sh/sfm; pfm) among them, counted for four
- * (sh/sfm) or six (pfm) CTAs per SM (per CTA about 24 bytes per arrival
- * slot and 28 per node for sh/sfm, 40 and 52 with the ob / RTB scratch; 56
+ * (sh/sfm) or six (pfm) CTAs per SM (per CTA about 28 bytes per arrival
+ * slot and 28 per node for sh/sfm, 44 and 52 with the ob / RTB scratch; 56
  * per node plus 4 per unit of the graph's path-count bound for pfm), and
  * fewer than
  * `max_active` (0 = 256) run; a request is always admitted when none is

@@ -418,7 +418,10 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
     Sig* Fs = reinterpret_cast<Sig*>(region + ws.o_sig);
     Sig* zsig = reinterpret_cast<Sig*>(region + ws.o_zsig);   // path counts of z's slots reached by the pull
     uint32_t* F = reinterpret_cast<uint32_t*>(region + ws.o_f);
+    // per frontier position: the state's time and vertex, written by the count
+    // pass with its path count (Algorithm 2 searches: the time by the scan)
     uint32_t* Ft = reinterpret_cast<uint32_t*>(region + ws.o_ft);
+    uint32_t* Fu = reinterpret_cast<uint32_t*>(region + ws.o_fu);
     uint32_t* lev = reinterpret_cast<uint32_t*>(region + ws.o_lev);
     uint32_t* seg_b = reinterpret_cast<uint32_t*>(region + ws.o_segb);
     uint32_t* seg_u = reinterpret_cast<uint32_t*>(region + ws.o_segu);
@@ -558,7 +561,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             // this level's frontier times and running sums: shared memory when they
             // fit (always for level 0, the virtual source, which has no position)
             const bool fsm = k == 0 || (!WIDE && L <= FCAP);
-            uint32_t* const FtL = fsm ? sm_Ft : Ft;
+            uint32_t* const FtL = fsm ? sm_Ft : Ft + lev[k];
             Sig* const FsL = Fs + lev[k];
             Sig* const FcL = fsm ? reinterpret_cast<Sig*>(sm_Fc) : FsL;
             advance_stamp();
@@ -576,14 +579,31 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 // of sigma.  Each thread takes IPT consecutive states of a tile: a
                 // thread-local segmented scan, one block-wide segmented scan of the
                 // thread aggregates, and the value carried into each thread.
+                // The count pass left each state's vertex and time beside its count
+                // (coalesced loads; large levels use the times in place); Algorithm 2
+                // searches have no count pass and look them up from the slot ids.
                 uint32_t gbase = 0;
                 const uint32_t* const g_slot_v = g.slot_v;
                 const uint32_t* const g_slot_t = g.slot_t;
+                const uint32_t* const FuK = Fu + lev[k];
+                const uint32_t* const FtK = Ft + lev[k];
                 for (uint32_t it = 0; it < L; it += BFS_NT * IPT) {
                     const uint32_t i0 = it + (uint32_t)tid * IPT;
                     uint32_t uq[IPT];
                     Sig vq[IPT];
-                    {
+                    uint32_t uprev;
+                    if (!stats) {
+#pragma unroll
+                        for (int q = 0; q < IPT; ++q) {
+                            uq[q] = 0u; vq[q] = (Sig)0;
+                            if (i0 + q < L) {
+                                uq[q] = FuK[i0 + q];
+                                if (fsm) FtL[i0 + q] = FtK[i0 + q];
+                                vq[q] = FsL[i0 + q];
+                            }
+                        }
+                        uprev = (i0 > 0 && i0 < L) ? FuK[i0 - 1] : NONE;
+                    } else {
                         uint32_t aq[IPT];
 #pragma unroll
                         for (int q = 0; q < IPT; ++q) aq[q] = (i0 + q < L) ? Fk[i0 + q] : 0u;
@@ -596,8 +616,8 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                                 vq[q] = FsL[i0 + q];
                             }
                         }
+                        uprev = (i0 > 0 && i0 < L) ? g_slot_v[Fk[i0 - 1]] : NONE;
                     }
-                    const uint32_t uprev = (i0 > 0 && i0 < L) ? g_slot_v[Fk[i0 - 1]] : NONE;
                     // heads (bit q): a state whose vertex differs from the previous state's
                     // (states past L are heads of value 0); agg = the thread's running sum
                     // since its last head
@@ -826,6 +846,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
             // of them); stored at b's frontier position ----
             if (!stats) {
                 const uint32_t* const c_slot_t = g.slot_t;
+                const uint32_t* const c_slot_v = g.slot_v;
                 const uint32_t* const c_slot_in = g.slot_in;
                 const uint32_t* const c_in_u = g.in_u;
                 // the count one in-edge (tail w, head time ta, w's map entry mw) adds
@@ -847,7 +868,7 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                 // CB states per thread, each stage's loads issued for all of them
                 // before any is used; a new state has at least one in-edge
                 for (uint32_t p0 = fbase + tid; p0 < fend; p0 += BFS_NT * CB) {
-                    uint32_t ta[CB], e0[CB], e1[CB], fb[CB], lo[CB], hi[CB];
+                    uint32_t ta[CB], e0[CB], e1[CB], fb[CB], lo[CB], hi[CB], uv[CB];
                     u64 mw[CB];
                     // the state's slot, its time and in-edge range, the first
                     // in-edge's tail and its map entry
@@ -858,8 +879,16 @@ __global__ void __launch_bounds__(BFS_NT, 1024 / BFS_NT) k_bfs(const Task* tasks
                     }
 #pragma unroll
                     for (int j = 0; j < CB; ++j) {
-                        ta[j] = e0[j] = e1[j] = 0u;
-                        if (lo[j] != NONE) { ta[j] = c_slot_t[lo[j]]; e0[j] = c_slot_in[lo[j]]; e1[j] = c_slot_in[lo[j] + 1]; }
+                        ta[j] = e0[j] = e1[j] = uv[j] = 0u;
+                        if (lo[j] != NONE) {
+                            ta[j] = c_slot_t[lo[j]]; uv[j] = c_slot_v[lo[j]];
+                            e0[j] = c_slot_in[lo[j]]; e1[j] = c_slot_in[lo[j] + 1];
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < CB; ++j) {
+                        const uint32_t p = p0 + (uint32_t)j * BFS_NT;
+                        if (p < fend) { Ft[p] = ta[j]; Fu[p] = uv[j]; }
                     }
 #pragma unroll
                     for (int j = 0; j < CB; ++j) hi[j] = (e1[j] > e0[j]) ? c_in_u[e0[j]] : 0u;
@@ -1169,6 +1198,7 @@ size_t bfs_region_bytes(uint32_t n, uint32_t A, uint32_t zcap, bool bits_in_smem
     }
     ws->o_f = o;       o = al(o + (size_t)(A + 1) * 4);
     ws->o_ft = o;      o = al(o + (size_t)(A + 1) * 4);
+    ws->o_fu = o;      o = al(o + (size_t)(A + 1) * 4);
     ws->o_lev = o;     o = al(o + (size_t)(n + 3) * 4);
     ws->o_segb = o;    o = al(o + (size_t)(n + 2) * 4);
     ws->o_segu = o;    o = al(o + (size_t)(n + 2) * 4);

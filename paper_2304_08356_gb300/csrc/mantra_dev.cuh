@@ -653,6 +653,7 @@ struct BfsWs {
     char* base;          // CTA b uses base + b * stride
     size_t stride;
     size_t o_sig, o_fc, o_f, o_ft, o_lev, o_segb, o_segu, o_path, o_pathe, o_bits, o_vb, o_segmap, o_stamp, o_nbits;
+    size_t o_fu;         // per frontier position: the state's vertex (written by the count pass)
     int bits_in_smem;    // visited bitmap in dynamic shared memory (the next-level bitmap is in the region)
     uint32_t bits_words; // capacity of each bitmap (words): ceil(A_max / 32)
     uint32_t n_cap;      // node capacity of a region
