@@ -35,7 +35,7 @@
 
 namespace mantra {
 
-constexpr int IPT = 2;            // frontier states per thread in a segmented-scan tile
+constexpr int IPT = 4;            // frontier states per thread in a segmented-scan tile
 constexpr int WALK_K = 2;         // edge windows with loads in flight per warp in the push
 constexpr int CK = 8;             // bitmap words in flight per lane in the compaction and cleanup scans
 constexpr int CB = 4;             // new states per thread with loads in flight in the count pass
